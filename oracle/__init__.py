@@ -1,0 +1,31 @@
+"""CPU oracle for the periodic corrector problem on a random checkerboard.
+
+TEST INFRASTRUCTURE ONLY. Only ``tests/``, ``__graft_entry__.smoke()`` and the
+``cpu_baseline`` / ``--impl reference`` legs of ``bench.py`` may import this
+package. The GPU product path (``paper_2007_06524_gb300``) never imports it and
+shares no code, table or constant generator with it.
+
+Everything here is plain FP64 numpy / scipy, written to be checked against the
+paper (Khoromskaia & Khoromskij, "Tensor-based techniques for fast
+discretization and solution of 3D elliptic equations with random
+coefficients", arXiv 2007.06524) by eye:
+
+* ``rng``          -- SplitMix64 counter stream and the checkerboard cell phases
+                      (coefficient model, Sec. 2, Eq. 3).
+* ``assembly``     -- stiffness matrix as the paper's Kronecker sum over cells
+                      (Sec. 3.3, Eqs. 16-18) and as the equivalent edge form
+                      sum_d D_d^T diag(a_d) D_d; right-hand sides (Eq. 8).
+* ``precond``      -- Laplacian eigenvalues (Eqs. 28-29), the pseudo-inverse
+                      core tensor G^+ (Eqs. 32-33), its rank-R canonical
+                      approximation (Eq. 34, Lemma 4.2) and the FFT apply
+                      (Eq. 31).
+* ``pcg``          -- CG / PCG on the zero-mean subspace (Eqs. 24-25) and the
+                      tight / dense reference solves.
+* ``homogenized``  -- the homogenized matrix (Eqs. 21-23).
+* ``dual2d``       -- an independent 2D cell-centred scheme used only to pin the
+                      node scheme through discrete Keller duality.
+
+Parity status of each function is stated in its docstring; the one reading
+with no external pin (the rank-R quadrature recipe) says "parity unpinned"
+where it applies.
+"""

@@ -1,0 +1,52 @@
+"""One realization of the corrector problem, end to end on the CPU.
+
+Test infrastructure only (see ``oracle/__init__``).
+
+realization(...) -> cells, edge coefficients, stiffness matrix, right-hand
+sides; solve_correctors(...) -> the three zero-mean correctors and A_hom.
+"""
+from __future__ import annotations
+
+from dataclasses import dataclass
+
+import numpy as np
+
+from . import assembly, homogenized, pcg, precond, rng
+
+
+@dataclass
+class Realization:
+    L: int
+    n: int
+    N: int
+    phase: np.ndarray      # (L,L,L) uint8
+    cellval: np.ndarray    # (L,L,L) float64
+    a_edges: np.ndarray    # (3,N,N,N) float64
+    A: object              # scipy CSR, N^3 x N^3
+    b: list                # three flat RHS vectors
+
+
+def realization(L: int, n: int, seed: int, a_lo: float, a_hi: float, p_hi: float = 0.5,
+                phase: np.ndarray | None = None) -> Realization:
+    if phase is None:
+        phase = rng.cell_phases_vec(L, seed, p_hi) if L > 16 else rng.cell_phases(L, seed, p_hi)
+    cellval = rng.cell_values(phase, a_lo, a_hi)
+    a_edges = assembly.edge_coefficients(cellval, n)
+    A = assembly.stiffness_edges(a_edges)
+    b = [assembly.rhs(a_edges, i) for i in range(3)]
+    return Realization(L, n, L * n, phase, cellval, a_edges, A, b)
+
+
+def solve_correctors(re: Realization, dirs=(0, 1, 2), rank: int = 0, tol: float = 1e-13):
+    """PCG-solve A psi_i = b_i for the requested directions; returns
+    (psis list (None where not solved), iterations list, A_hom)."""
+    P = pcg.fft_preconditioner(re.N, rank)
+    psis, its = [None, None, None], [None, None, None]
+    for i in dirs:
+        x, it, _ = pcg.pcg(re.A, re.b[i], P, tol=tol, maxit=5000)
+        psis[i] = x.reshape(re.N, re.N, re.N)
+        its[i] = it
+    return psis, its, homogenized.ahom_edge(re.a_edges, psis)
+
+
+__all__ = ["Realization", "realization", "solve_correctors", "precond"]

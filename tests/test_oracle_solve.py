@@ -1,0 +1,137 @@
+"""Pins for the oracle's solves and homogenized matrix.
+
+* dense least-squares solve on tiny grids (library routine, independent of CG);
+* manufactured solution (known psi*, b = A psi*) recovered by PCG;
+* the same solution from plain CG, exact-PCG and rank-R PCG;
+* laminate closed form: harmonic mean across layers, arithmetic mean along;
+* 2D checkerboard through discrete Keller duality against an independent
+  voxel scheme: A_node * A_vox = alpha * beta, and A[s] R A[1/s] R^T = I;
+* Wiener bounds, symmetry, axis-permutation covariance, shift invariance;
+* iteration counts almost flat in N (Lemma 4.1).
+"""
+import numpy as np
+import pytest
+
+from oracle import assembly, dual2d, homogenized, pcg, problem, rng
+
+
+def test_dense_solve_agrees_with_pcg():
+    re = problem.realization(3, 2, seed=4, a_lo=1.0, a_hi=10.0)
+    for i in range(3):
+        xd = pcg.dense_solve(re.A, re.b[i])
+        x, it, rel = pcg.pcg(re.A, re.b[i], pcg.fft_preconditioner(re.N, 0), tol=1e-13)
+        assert rel < 1e-13
+        assert np.linalg.norm(x - xd) / np.linalg.norm(xd) < 1e-11
+
+
+def test_manufactured_solution():
+    re = problem.realization(4, 4, seed=1, a_lo=1.0, a_hi=100.0)
+    N = re.N
+    j = np.arange(N)
+    psi = (np.cos(2 * np.pi * (j[:, None, None] + 2 * j[None, :, None]) / N)
+           + np.sin(2 * np.pi * 3 * j[None, None, :] / N) + 0.3)
+    b = assembly.apply_stencil(re.a_edges, psi).ravel()
+    x, it, rel = pcg.pcg(re.A, b, pcg.fft_preconditioner(N, 0), tol=1e-13)
+    ref = psi.ravel() - psi.mean()
+    assert np.linalg.norm(x - ref) / np.linalg.norm(ref) < 1e-10
+
+
+def test_cg_exact_and_rank_r_reach_same_solution():
+    re = problem.realization(4, 2, seed=2, a_lo=1.0, a_hi=10.0)
+    sols = []
+    for P in (None, pcg.fft_preconditioner(re.N, 0), pcg.fft_preconditioner(re.N, 6), pcg.fft_preconditioner(re.N, 12)):
+        x, it, rel = pcg.pcg(re.A, re.b[0], P, tol=1e-12, maxit=5000)
+        sols.append(x)
+    for s in sols[1:]:
+        assert np.linalg.norm(s - sols[0]) / np.linalg.norm(sols[0]) < 1e-9
+
+
+def test_laminate_closed_form():
+    L, n = 4, 4
+    vals = np.array([1.0, 10.0, 3.0, 100.0])
+    cv = np.broadcast_to(vals[:, None, None], (L, L, L)).copy()   # layers along x1
+    re = problem.realization(L, n, 0, 1.0, 1.0, phase=np.zeros((L, L, L), np.uint8))
+    a = assembly.edge_coefficients(cv, n)
+    A = assembly.stiffness_edges(a)
+    psis = []
+    for i in range(3):
+        b = assembly.rhs(a, i)
+        x = np.zeros_like(b) if np.abs(b).max() == 0 else pcg.pcg(A, b, pcg.fft_preconditioner(re.N, 0), tol=1e-14)[0]
+        psis.append(x.reshape(a.shape[1:]))
+    H = homogenized.ahom_edge(a, psis)
+    hm = len(vals) / np.sum(1 / vals)
+    am = vals.mean()
+    assert abs(H[0, 0] - hm) < 1e-12 * hm
+    assert abs(H[1, 1] - am) < 1e-12 and abs(H[2, 2] - am) < 1e-12
+    assert np.abs(H - np.diag(np.diag(H))).max() < 1e-12
+
+
+def _node2d(cells2d, n, lo=None):
+    """3D node scheme on an x3-invariant field -> its 2x2 block."""
+    L = cells2d.shape[0]
+    cv = np.repeat(cells2d[:, :, None], L, axis=2)
+    a = assembly.edge_coefficients(cv, n)
+    A = assembly.stiffness_edges(a)
+    N = L * n
+    psis = [None, None, None]
+    for i in range(2):
+        psis[i] = pcg.pcg(A, assembly.rhs(a, i), pcg.fft_preconditioner(N, 0), tol=1e-14, maxit=5000)[0].reshape(N, N, N)
+    H = homogenized.ahom_edge(a, psis)
+    return H[:2, :2], psis, a
+
+
+@pytest.mark.parametrize("n", [2, 4])
+def test_checkerboard_duality(n):
+    al, be = 1.0, 10.0
+    cb = np.array([[al, be], [be, al]])
+    Hn, psis, _ = _node2d(cb, n)
+    # x3-invariance of the 3D solution
+    assert np.abs(psis[0] - psis[0][:, :, :1]).max() < 1e-10
+    V2 = np.repeat(np.repeat(cb, n, 0), n, 1)
+    Hv = dual2d.ahom_voxel_2d(V2)
+    assert abs(Hn[0, 0] * Hv[0, 0] - al * be) < 1e-9 * al * be
+    # classical limit sqrt(alpha beta) lies strictly between the two discrete values
+    assert Hv[0, 0] < np.sqrt(al * be) < Hn[0, 0]
+
+
+def test_keller_duality_random_field():
+    cells = rng.cell_values(rng.cell_phases(4, 3), 1.0, 7.0)[:, :, 0]
+    n = 2
+    Hn, _, _ = _node2d(cells, n)
+    V2 = np.repeat(np.repeat(cells, n, 0), n, 1)
+    Hv = dual2d.ahom_voxel_2d(1.0 / V2)
+    Rm = np.array([[0.0, -1.0], [1.0, 0.0]])
+    assert np.allclose(Hn @ Rm @ Hv @ Rm.T, np.eye(2), atol=1e-10)
+
+
+def test_wiener_bounds_symmetry_and_forms():
+    re = problem.realization(4, 4, seed=0, a_lo=1.0, a_hi=10.0)
+    psis, its, H = problem.solve_correctors(re, tol=1e-13)
+    vals = re.cellval.ravel()
+    hm, am = 1 / np.mean(1 / vals), vals.mean()
+    for i in range(3):
+        assert hm <= H[i, i] <= am
+    assert np.abs(H - H.T).max() < 1e-10
+    H2 = homogenized.ahom_rhs_form(re.a_edges, [b.reshape(psis[0].shape) for b in re.b], psis)
+    He = homogenized.ahom_energy(re.a_edges, psis)
+    assert np.abs(H - H2).max() < 1e-12 and np.abs(H - He).max() < 1e-10
+
+
+def test_axis_permutation_and_shift():
+    re = problem.realization(4, 2, seed=5, a_lo=1.0, a_hi=10.0)
+    _, _, H = problem.solve_correctors(re, tol=1e-13)
+    perm = (2, 0, 1)
+    re2 = problem.realization(4, 2, 0, 1.0, 10.0, phase=np.transpose(re.phase, perm))
+    _, _, H2 = problem.solve_correctors(re2, tol=1e-13)
+    assert np.allclose(H2, H[np.ix_(perm, perm)], atol=1e-10)
+    re3 = problem.realization(4, 2, 0, 1.0, 10.0, phase=np.roll(re.phase, (1, 2, 3), axis=(0, 1, 2)))
+    _, _, H3 = problem.solve_correctors(re3, tol=1e-13)
+    assert np.allclose(H3, H, atol=1e-10)
+
+
+def test_iterations_flat_in_grid():
+    its = []
+    for n in (2, 4, 8):
+        re = problem.realization(4, n, seed=0, a_lo=1.0, a_hi=10.0)
+        its.append(pcg.pcg(re.A, re.b[0], pcg.fft_preconditioner(re.N, 0), tol=1e-8)[1])
+    assert max(its) <= 1.5 * min(its) + 2
