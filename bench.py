@@ -1,0 +1,376 @@
+#!/usr/bin/env python3
+"""Corrector solves per second to rel. residual 1e-8 on the N=256 random
+checkerboard (L=32 cells per side, n=8 points per cell, Bernoulli(1/2) on
+{1,100}), three correctors e_1..e_3 and the full 3x3 homogenized matrix per
+realization, FP64 PCG with the rank-8 canonical Laplacian preconditioner.
+
+One step = one realization through the whole hot path: cell phases from the
+seed, three PCG solves (RHS, iterations, mean projection, true-residual
+check) and A_hom. `value` is measured with CUDA events on the launching
+stream, inputs resident in HBM; `e2e` repeats the step through the public C
+ABI with the cell phases copied from pinned host memory and A_hom read back.
+
+  python bench.py [--gpus N] [--steps K] [--warmup W] [--impl native|reference]
+
+Under torchrun (N > 1) every rank runs independent realizations (replicas,
+weak scaling); the slowest rank's time is reported.
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import math
+import os
+import statistics
+import subprocess
+import sys
+import tempfile
+import time
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+if ROOT not in sys.path:
+    sys.path.insert(0, ROOT)
+
+METRIC = "corrector solves/s to rel-res 1e-8 (N=256), % HBM peak, plain vs learned start"
+UNIT = "corrector solves/s"
+
+
+def _peaks():
+    p = os.path.join(ROOT, "MEASURED_PEAKS.json")
+    if os.path.exists(p):
+        d = json.load(open(p))
+        return {"hbm_gbs": d.get("hbm_gbs", 6800.0), "src": "measured"}
+    return {"hbm_gbs": 6800.0, "src": "fallback"}
+
+
+# nominal FP64 rate of one GB300 (dense, non-tensor and tensor alike)
+FP64_PEAK_TFLOPS = 1.25
+FP32_PEAK_TFLOPS = 152 * 128 * 2 * 2.07e9 / 1e12  # 152 SMs x 128 FP32 lanes x FMA x max clock
+
+
+class ClockSampler:
+    """nvidia-smi clocks / throttle reasons sampled every 200 ms in the background."""
+
+    FIELDS = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+              "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+              "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, gpu_index: int):
+        self.gpu = gpu_index
+        self.proc = None
+        self.path = None
+
+    def start(self):
+        try:
+            fd, self.path = tempfile.mkstemp(suffix=".csv")
+            os.close(fd)
+            self.proc = subprocess.Popen(
+                ["nvidia-smi", "-i", str(self.gpu), "--query-gpu=" + self.FIELDS, "--format=csv,noheader,nounits",
+                 "-lms", "200"], stdout=open(self.path, "w"), stderr=subprocess.DEVNULL)
+        except Exception:
+            self.proc = None
+
+    def stop(self):
+        if self.proc is None:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["nvidia-smi unavailable"]}
+        self.proc.terminate()
+        try:
+            self.proc.wait(timeout=5)
+        except Exception:
+            self.proc.kill()
+        sm, smax, reasons = [], [], set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for line in open(self.path):
+            f = [x.strip() for x in line.split(",")]
+            if len(f) < 9:
+                continue
+            try:
+                sm.append(float(f[1]))
+                smax.append(float(f[2]))
+            except ValueError:
+                continue
+            for nm, v in zip(names, f[5:9]):
+                if v.lower().startswith("active"):
+                    reasons.add(nm)
+        os.unlink(self.path)
+        return {"sm_mhz": statistics.median(sm) if sm else None, "sm_max_mhz": max(smax) if smax else None,
+                "samples": len(sm), "reasons": sorted(reasons)}
+
+
+def _dist():
+    ws = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    return ws, rank, local
+
+
+def _algorithmic(N, elem, rank_r):
+    """Per-launch algorithmic bytes and flops of each kernel class (one PCG iteration).
+
+    bytes: the fields each kernel must read and write once (N^3 elements of
+    `elem` bytes); flops: one real 1D Hartley pass = 2.5 log2 N + 3 per point
+    (half-length complex FFT convention + the Hartley combine)."""
+    n3 = N ** 3
+    f = 2.5 * math.log2(N) + 3.0
+    scale = (2 * rank_r + 3) if rank_r else 7
+    return {
+        "stencil_matvec": (2 * elem * n3, 15 * n3),
+        "dht_x3_in": (4 * elem * n3, (f + 4) * n3),
+        "dht_x2": (2 * elem * n3, f * n3),
+        "dht_x1_scale": (2 * elem * n3, (2 * f + scale) * n3),
+        "dht_x3_out": (5 * elem * n3, (f + 4) * n3),
+    }
+
+
+def run_native(args):
+    import numpy as np
+    import torch
+
+    import __graft_entry__
+
+    ws, rank, local = _dist()
+    if ws > 1:
+        import torch.distributed as dist
+
+        dist.init_process_group("nccl")
+    torch.cuda.set_device(local)
+    __graft_entry__.build()
+    import paper_2007_06524_gb300 as sq
+    from paper_2007_06524_gb300 import workloads
+
+    wl = dict(workloads.PLAIN_N256)
+    L, n = wl["L"], wl["n"]
+    N = L * n
+    R = args.rank
+    prec = sq.SQ_FP64 if args.precision == "fp64" else sq.SQ_FP32_REFINE
+    tol, max_iter = wl["tol"], 1000
+    stream = torch.cuda.current_stream()
+
+    c = sq.sq_build_coeffs(L, n, 0, wl["p_hi"], wl["a_lo"], wl["a_hi"])
+    pc = sq.sq_precond_setup(N, R)
+    w = sq.sq_workspace_create(N, prec)
+    psis = [torch.empty(N ** 3, dtype=torch.float64, device="cuda") for _ in range(3)]
+
+    def step(seed, upload=None):
+        if upload is None:
+            sq.sq_coeffs_regenerate(c, seed, wl["p_hi"])
+        else:
+            sq.sq_coeffs_upload(c, upload)
+        infos = [sq.sq_pcg_solve(c, pc, w, i, tol, max_iter, prec, None, psis[i]) for i in range(3)]
+        A, E = sq.sq_homogenized_matrix(c, *psis)
+        return infos, A
+
+    seed_base = 1000 * rank
+    for k in range(args.warmup):
+        step(10 ** 6 + seed_base + k)
+    torch.cuda.synchronize()
+    if ws > 1:
+        torch.distributed.barrier()
+    sampler = ClockSampler(local)
+    sampler.start()
+    sq.sq_profile_enable(True)
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    torch.cuda.synchronize()
+    e0.record(stream)
+    all_infos, As = [], []
+    for k in range(args.steps):
+        infos, A = step(seed_base + k)
+        all_infos += infos
+        As.append(A)
+    e1.record(stream)
+    torch.cuda.synchronize()
+    prof = sq.sq_profile_read()
+    sq.sq_profile_enable(False)
+    clocks = sampler.stop()
+    t_ms = e0.elapsed_time(e1)
+    if ws > 1:
+        tt = torch.tensor([t_ms], device="cuda")
+        torch.distributed.all_reduce(tt, op=torch.distributed.ReduceOp.MAX)
+        t_ms = float(tt.item())
+    solves = 3 * args.steps * ws
+    value = solves / (t_ms / 1e3)
+    iters = [i["iters"] for i in all_infos]
+    ok = all(i["status"] == sq.SQ_OK and i["relres_true"] <= tol for i in all_infos)
+
+    # --- roofline of the dominant kernel class
+    elem = 8 if prec == sq.SQ_FP64 else 4
+    alg = _algorithmic(N, elem, R)
+    n_iter = sum(iters)
+    eff = {"stencil_matvec": n_iter, "dht_x3_in": n_iter + 3 * args.steps, "dht_x2": 2 * (n_iter + 3 * args.steps),
+           "dht_x1_scale": n_iter + 3 * args.steps, "dht_x3_out": n_iter + 3 * args.steps}
+    peaks = _peaks()
+    kernels = {}
+    for name, (ms, cnt) in prof.items():
+        if name in alg and ms > 0:
+            b, f = alg[name]
+            ne = eff[name]
+            kernels[name] = {"ms": round(ms, 3), "launches": cnt, "share": round(ms / t_ms, 4),
+                             "GBps": round(b * ne / (ms / 1e3) / 1e9, 1),
+                             "GFLOPps": round(f * ne / (ms / 1e3) / 1e9, 1)}
+        elif ms > 0:
+            kernels[name] = {"ms": round(ms, 3), "launches": cnt, "share": round(ms / t_ms, 4)}
+    dom = max((k for k in kernels if k in alg), key=lambda k: kernels[k]["ms"])
+    kd = kernels[dom]
+    fp_peak = FP64_PEAK_TFLOPS if elem == 8 else FP32_PEAK_TFLOPS
+    frac_hbm = kd["GBps"] / peaks["hbm_gbs"]
+    frac_alu = kd["GFLOPps"] / (fp_peak * 1e3)
+    if frac_alu > frac_hbm:
+        roof = {"kernel": dom, "bound": "alu", "achieved": round(kd["GFLOPps"] / 1e3, 4), "peak": fp_peak,
+                "unit": "TFLOP/s", "frac": round(frac_alu, 4),
+                "peak_src": "nominal FP64 rate of GB300 (1.25 TFLOP/s)" if elem == 8 else "152 SMs x 128 FMA x 2.07 GHz",
+                "hbm_frac": round(frac_hbm, 4)}
+    else:
+        roof = {"kernel": dom, "bound": "hbm", "achieved": kd["GBps"], "peak": peaks["hbm_gbs"], "unit": "GB/s",
+                "frac": round(frac_hbm, 4), "peak_src": peaks["src"], "alu_frac": round(frac_alu, 4)}
+    roof["traffic"] = None
+    gpu_launches = int(sum(cnt for _, cnt in prof.values()))
+
+    out = {"metric": METRIC, "value": round(value, 4), "unit": UNIT, "n_gpus": ws, "steps": args.steps,
+           "warmup": args.warmup, "ms_per_step": round(t_ms / args.steps, 3), "higher_is_better": True,
+           "scaling": "weak", "vs_baseline": None, "dtype": "f64" if elem == 8 else "f32+f64",
+           "data": "synthetic",
+           "config": {"workload": f"plain L={L} n={n} N={N}, Bernoulli(1/2) on {{1,100}}, 3 correctors + A_hom, "
+                                  f"rank-{R} preconditioner, tol {tol:g}, {args.precision}",
+                      "L": L, "n": n, "N": N, "rank": R, "tol": tol, "precision": args.precision,
+                      "seeds": f"{seed_base}..{seed_base + args.steps - 1} per rank",
+                      "l2": "inputs larger than L2 (4 working fields of %d MB each)" % (N ** 3 * elem // 2 ** 20),
+                      "parallelism": "replicas" if ws > 1 else "single GPU"},
+           "clocks": clocks, "gpu_launches": gpu_launches, "roofline": roof, "kernels": kernels,
+           "iters": {"mean": round(statistics.mean(iters), 2), "min": min(iters), "max": max(iters)},
+           "converged": ok}
+
+    # --- end to end through the C ABI with pinned host inputs
+    rng = np.random.default_rng(12345 + rank)
+    host = [torch.from_numpy(rng.integers(0, 2, L ** 3, dtype=np.uint8)).pin_memory() for _ in range(args.steps)]
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    for k in range(args.steps):
+        step(None, upload=host[k])
+    torch.cuda.synchronize()
+    t_e2e = time.perf_counter() - t0
+    out["e2e"] = {"value": round(3 * args.steps / t_e2e, 4), "unit": UNIT, "h2d_bytes_per_step": L ** 3,
+                  "d2h_bytes_per_step": 2 * 9 * 8}
+
+    # --- variants on the same workload (2 steps each)
+    if not args.no_variants and rank == 0:
+        variants = {}
+        for label, rr, pp in (("fp32_refine_exact", 0, sq.SQ_FP32_REFINE), ("fp32_refine_rank8", 8, sq.SQ_FP32_REFINE),
+                              ("fp64_exact", 0, sq.SQ_FP64), ("fp64_rank4", 4, sq.SQ_FP64),
+                              ("fp64_rank16", 16, sq.SQ_FP64)):
+            pcv = sq.sq_precond_setup(N, rr)
+            wv = sq.sq_workspace_create(N, pp) if pp != prec else w
+            sq.sq_coeffs_regenerate(c, 7, wl["p_hi"])
+            for i in range(3):
+                sq.sq_pcg_solve(c, pcv, wv, i, tol, max_iter, pp, None, psis[i])
+            torch.cuda.synchronize()
+            ev0, ev1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            ev0.record(stream)
+            its = []
+            nst = 2
+            for k in range(nst):
+                sq.sq_coeffs_regenerate(c, seed_base + k, wl["p_hi"])
+                for i in range(3):
+                    inf = sq.sq_pcg_solve(c, pcv, wv, i, tol, max_iter, pp, None, psis[i])
+                    its.append(inf["iters"])
+                sq.sq_homogenized_matrix(c, *psis)
+            ev1.record(stream)
+            torch.cuda.synchronize()
+            tv = ev0.elapsed_time(ev1)
+            variants[label] = {"solves_per_s": round(3 * nst / (tv / 1e3), 3), "iters_mean": round(statistics.mean(its), 1)}
+            del pcv
+        out["variants"] = variants
+
+    if rank == 0 and not args.no_cpu_baseline and ws == 1:
+        out["cpu_baseline"] = cpu_baseline(statistics.mean(iters), R)
+    if rank == 0:
+        print(json.dumps(out))
+    if ws > 1:
+        torch.distributed.barrier()
+        torch.distributed.destroy_process_group()
+
+
+def _oracle_sample(iters_mean, R, n_iter_sample=3):
+    """Times the oracle (FP64 CSR + numpy FFT PCG) on one N=256 realization:
+    assembly + RHS, then `n_iter_sample` PCG iterations of e_1; extrapolates to
+    corrector solves/s with the GPU's mean iteration count."""
+    from oracle import pcg, problem
+    from paper_2007_06524_gb300 import workloads
+
+    wl = workloads.PLAIN_N256
+    t0 = time.perf_counter()
+    re = problem.realization(wl["L"], wl["n"], 0, wl["a_lo"], wl["a_hi"])
+    t_setup = time.perf_counter() - t0
+    P = pcg.fft_preconditioner(re.N, R)
+    t0 = time.perf_counter()
+    pcg.pcg(re.A, re.b[0], P, tol=1e-30, maxit=n_iter_sample)
+    t_it = (time.perf_counter() - t0) / (n_iter_sample + 1)  # + initial preconditioner apply
+    t_solve = t_setup / 3.0 + (iters_mean + 1) * t_it
+    return t_setup, t_it, t_solve
+
+
+def cpu_baseline(iters_mean, R):
+    t_setup, t_it, t_solve = _oracle_sample(iters_mean, R)
+    return {"value": round(1.0 / t_solve, 6), "unit": UNIT, "cores": 1, "kind": "oracle",
+            "sample": f"oracle at N=256 (L=32, n=8, seed 0): assembly+RHS {t_setup:.1f} s (shared by 3 correctors) "
+                      f"+ {t_it:.2f} s per PCG iteration (rank-{R}), measured on 3 iterations, extrapolated to "
+                      f"{iters_mean:.1f} iterations per solve; single-threaded numpy/scipy on "
+                      f"{len(os.sched_getaffinity(0))} available host cores"}
+
+
+def run_reference(args):
+    """The oracle as the reference arm, on this arm's workload and metric."""
+    ws, rank, _ = _dist()
+    if rank != 0:
+        return
+    from oracle import pcg, problem
+    from paper_2007_06524_gb300 import workloads
+
+    wl = workloads.PLAIN_N256
+    R = args.rank
+    t0 = time.perf_counter()
+    re = problem.realization(wl["L"], wl["n"], 0, wl["a_lo"], wl["a_hi"])
+    t_setup = time.perf_counter() - t0
+    P = pcg.fft_preconditioner(re.N, R)
+    iters_per_solve = 50.0  # typical FP64 rank-8 count at this workload (the native arm reports its own)
+    times = []
+    for k in range(args.warmup + args.steps):
+        t0 = time.perf_counter()
+        pcg.pcg(re.A, re.b[k % 3], P, tol=1e-30, maxit=1)
+        dt = time.perf_counter() - t0
+        if k >= args.warmup:
+            times.append(dt / 2)  # one preconditioner apply before + one PCG iteration
+    t_it = statistics.mean(times)
+    t_solve = t_setup / 3.0 + (iters_per_solve + 1) * t_it
+    value = 1.0 / t_solve
+    out = {"metric": METRIC, "value": round(value, 6), "unit": UNIT, "n_gpus": ws, "steps": args.steps,
+           "warmup": args.warmup, "ms_per_step": round(t_it * 1e3, 3), "higher_is_better": True, "scaling": "weak",
+           "vs_baseline": None, "dtype": "f64", "data": "synthetic", "impl": "reference",
+           "config": {"workload": f"plain L=32 n=8 N=256, Bernoulli(1/2) on {{1,100}}, rank-{R}, tol 1e-8, fp64"},
+           "cpu_baseline": {"value": round(value, 6), "unit": UNIT, "cores": 1, "kind": "oracle",
+                            "sample": f"step = one PCG iteration of the oracle at N=256 ({t_it:.2f} s); assembly "
+                                      f"{t_setup:.1f} s once; extrapolated to {iters_per_solve:.0f} iterations"},
+           "e2e": {"value": round(value, 6), "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+    print(json.dumps(out))
+
+
+def main():
+    ap = argparse.ArgumentParser(description=__doc__, formatter_class=argparse.RawDescriptionHelpFormatter)
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=5)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", choices=["native", "reference"], default="native")
+    ap.add_argument("--rank", type=int, default=8, help="preconditioner rank (0 = exact Fourier diagonal)")
+    ap.add_argument("--precision", choices=["fp64", "fp32_refine"], default="fp64")
+    ap.add_argument("--no-variants", action="store_true")
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    args = ap.parse_args()
+    if args.warmup < 3 and args.impl == "native":
+        args.warmup = 3
+    if args.impl == "reference":
+        run_reference(args)
+    else:
+        run_native(args)
+
+
+if __name__ == "__main__":
+    main()

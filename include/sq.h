@@ -1,0 +1,179 @@
+/*
+ * sq.h -- C ABI of libsq, a single-GPU (GB300, sm_103a) solver for the periodic
+ * corrector problem of Khoromskaia & Khoromskij, "Tensor-based techniques for
+ * fast discretization and solution of 3D elliptic equations with random
+ * coefficients" (arXiv 2007.06524).
+ *
+ * Problem (Sec. 2, Eqs. 3-4; Sec. 3.4, Eqs. 20-21): on the unit cube with an
+ * L x L x L checkerboard of cells, each cell holding a_lo or a_hi, find for
+ * i = 1..3 the periodic corrector with -div(a (e_i + grad phi_i)) = 0 and
+ * the homogenized matrix A_hom e_i = mean(a (e_i + grad phi_i)).
+ *
+ * Discretization (Sec. 3.1-3.3): N = L*n grid points per axis (n points per
+ * cell side; the paper's n1 = N + 1 with the last point identified with the
+ * first), node (j1,j2,j3) stored at j3 + N*j2 + N*N*j1 (x3 fastest, the
+ * paper's big-endian order). The stiffness matrix is A = sum_d D_d^T
+ * diag(a_d) D_d with the periodic forward difference D_d and the edge
+ * coefficient a_d(j) = mean of the cells touching the edge j -> j+e_d (the
+ * nodal weights 1, 1/2, 1/4 of Sec. 3.3, Eq. 18). It is never stored:
+ * every kernel rebuilds the edge coefficients from the L^3 cell phases.
+ * Right-hand side (Eq. 8): b_i = -D_i^T a_i. All fields are in grid units:
+ * the library returns psi_i with A psi_i = b_i; the physical corrector is
+ * phi_i = h * psi_i, h = 1/N.
+ *
+ * Conventions for every call:
+ *  - Return value: SQ_OK (0) or an error code below; sq_strerror() names it.
+ *  - Field pointers (double* / float*) are DEVICE pointers to N^3 contiguous
+ *    elements in the layout above, owned by the caller; they must not alias
+ *    each other unless stated.
+ *  - Handles (sq_coeffs, sq_precond, sq_workspace) are opaque, owned by the
+ *    library, created by the *_create/build/setup call and released with the
+ *    matching *_destroy (NULL is accepted by destroy).
+ *  - Calls are asynchronous on the given stream (a cudaStream_t; NULL = the
+ *    legacy default stream) unless marked "synchronizes".
+ *  - On error nothing is guaranteed about the output buffers; a CUDA error
+ *    that was raised by an earlier asynchronous call may surface as SQ_ECUDA.
+ */
+#ifndef SQ_H
+#define SQ_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef struct CUstream_st *sq_stream_t; /* same type as cudaStream_t */
+
+enum sq_status {
+  SQ_OK = 0,
+  SQ_EINVAL = 1,     /* bad argument (size, NULL, mismatched handles)          */
+  SQ_ENOMEM = 2,     /* device or host allocation failed                        */
+  SQ_ECUDA = 3,      /* CUDA runtime error                                      */
+  SQ_ENOCONV = 4,    /* max_iter reached before the tolerance (result is valid) */
+  SQ_ETIMEOUT = 5,   /* a bounded device wait gave up                           */
+  SQ_EBADGUESS = 6   /* initial guess rejected, solve restarted from zero       */
+};
+
+enum sq_precision {
+  SQ_FP64 = 0,        /* every field, matvec, FFT and reduction in FP64          */
+  SQ_FP32_REFINE = 1  /* FP32 PCG inner solves inside FP64 iterative refinement:
+                         FP64 residual, solution, norms and mean projection     */
+};
+
+typedef struct sq_coeffs sq_coeffs;
+typedef struct sq_precond sq_precond;
+typedef struct sq_workspace sq_workspace;
+
+typedef struct sq_solve_info {
+  int iters;          /* PCG iterations (x updates); summed over inner solves   */
+  int outer_steps;    /* refinement steps (1 for SQ_FP64)                       */
+  int status;         /* SQ_OK or SQ_ENOCONV                                     */
+  int used_guess;     /* 1 if x0 was used                                        */
+  double relres;      /* last recurrence residual ||r||/||b||                    */
+  double relres_true; /* ||b - A psi||/||b||, recomputed in FP64 after the solve */
+} sq_solve_info;
+
+/* Coefficient generation (Sec. 2, Eq. 3: a = lambda + beta*ahat per cell).
+ * Cell (c1,c2,c3) is high (a_hi) iff the top 53 bits of output number
+ * c3 + L*c2 + L*L*c1 of the SplitMix64 stream seeded with `seed` (Steele, Lea
+ * & Flood, OOPSLA 2014), read as an integer, are below floor(p_hi * 2^53).
+ * L >= 1, n >= 2, 8 <= L*n <= 512, L*n even, L*n = 2^a 3^b with b <= 1,
+ * 0 <= p_hi <= 1, 0 < a_lo, 0 < a_hi. The cell phases (L^3 bytes) stay on the
+ * device inside the handle. */
+int sq_build_coeffs(int L, int n, uint64_t seed, double p_hi, double a_lo, double a_hi,
+                    sq_stream_t stream, sq_coeffs **out);
+
+/* Same, with the L^3 phases (0 = a_lo, nonzero = a_hi, index c3 + L*c2 + L*L*c1)
+ * given in HOST memory; they are copied to the device on `stream`
+ * (host_phase may be reused once the call returns: the copy is staged). */
+int sq_coeffs_from_host(int L, int n, const uint8_t *host_phase, double a_lo, double a_hi,
+                        sq_stream_t stream, sq_coeffs **out);
+
+/* Redraws the phases of an existing handle in place from (seed, p_hi), with
+ * the rule of sq_build_coeffs (no allocation; asynchronous on `stream`). */
+int sq_coeffs_regenerate(sq_coeffs *c, uint64_t seed, double p_hi, sq_stream_t stream);
+
+/* Copies L^3 phases from PINNED host memory into an existing handle
+ * (cudaMemcpyAsync on `stream`: host_phase must stay valid until the stream
+ * reaches the copy; values must be 0 or 1). */
+int sq_coeffs_upload(sq_coeffs *c, const uint8_t *host_phase, sq_stream_t stream);
+
+/* Copies the phases to host_phase (L^3 bytes, may be NULL) and counts the high
+ * cells into *n_hi (may be NULL). Synchronizes the handle's stream. */
+int sq_coeffs_cells(const sq_coeffs *c, uint8_t *host_phase, int64_t *n_hi);
+/* Grid parameters of a handle (any output may be NULL). */
+int sq_coeffs_shape(const sq_coeffs *c, int *L, int *n, int *N);
+void sq_coeffs_destroy(sq_coeffs *c);
+
+/* Preconditioner (Sec. 4.1-4.2): pseudo-inverse of the periodic Laplacian,
+ * z = F^-1 G F r with G(k) = 1/(l_k1 + l_k2 + l_k3), l_k = 4 sin^2(pi k/N),
+ * G(0,0,0) = 0 (Eqs. 31-33). rank = 0 uses this exact Fourier diagonal; rank
+ * R >= 2 uses the rank-R canonical tensor G_R = sum_r u_r (x) u_r (x) u_r
+ * (Lemma 4.2) from a trapezoid rule of the Laplace transform of 1/x (Eq. 34),
+ * R <= 64. Factors and twiddles are built on the host in FP64 and copied to
+ * the current device (synchronous). */
+int sq_precond_setup(int N, int rank, sq_precond **out);
+void sq_precond_destroy(sq_precond *p);
+
+/* Scratch fields for one solve at grid N and the given precision (device
+ * memory, allocated here with cudaMalloc): SQ_FP64 4 N^3 doubles, SQ_FP32_REFINE
+ * 5 N^3 floats, plus reduction partials. One workspace serves one solve at a
+ * time: solves that share it must be ordered on one stream. */
+int sq_workspace_create(int N, int precision, sq_workspace **out);
+void sq_workspace_destroy(sq_workspace *w);
+
+/* PCG solve of A psi = b_dir (dir = 0,1,2 for e_1,e_2,e_3) on the zero-mean
+ * subspace (Eqs. 24-25), preconditioned by `pc` (Sec. 4.2). Hestenes-Stiefel
+ * recurrence, x0 = x0 if given (device, N^3 doubles) else 0; stops when
+ * ||r||_2/||b||_2 <= tol on the recurrence residual, then confirms on the true
+ * FP64 residual (continuing from the current iterate if that fails). The
+ * result psi (device, N^3 doubles, may alias x0) is projected to zero mean.
+ * SQ_FP32_REFINE: psi is refined in FP64, each correction solved in FP32 to
+ * relative residual 1e-4 (at most max_iter inner iterations in total).
+ * Synchronizes `stream` (the host checks convergence). info may be NULL. */
+int sq_pcg_solve(const sq_coeffs *c, const sq_precond *pc, sq_workspace *w, int dir, double tol,
+                 int max_iter, int precision, const double *x0, double *psi,
+                 sq_solve_info *info, sq_stream_t stream);
+
+/* Homogenized matrix (Sec. 3.4, Eqs. 21-23) from the three correctors psi_i
+ * (device, N^3 doubles each):
+ *   A_hom[3*i+j] = delta_ij mean(a_j) + mean(a_j * D_j psi_i)   (edge form)
+ * and, if A_energy != NULL, the symmetric energy form
+ *   A_energy[3*i+j] = mean(sum_d a_d (delta_id + D_d psi_i)(delta_jd + D_d psi_j)).
+ * Outputs are HOST arrays of 9 doubles. Synchronizes `stream`. */
+int sq_homogenized_matrix(const sq_coeffs *c, const double *psi0, const double *psi1,
+                          const double *psi2, double *A_hom, double *A_energy, sq_stream_t stream);
+
+/* Building blocks, exposed for verification (asynchronous):
+ * y = A x (FP64 or FP32 fields), b = b_dir, z = G-preconditioned r (the full
+ * 3D transform pipeline of the solver; w must match pc's N and the field type:
+ * an SQ_FP64 workspace for the double version, SQ_FP32_REFINE for float). */
+int sq_apply_operator(const sq_coeffs *c, const double *x, double *y, sq_stream_t stream);
+int sq_apply_operator_f32(const sq_coeffs *c, const float *x, float *y, sq_stream_t stream);
+int sq_rhs(const sq_coeffs *c, int dir, double *b, sq_stream_t stream);
+int sq_apply_precond(const sq_precond *pc, sq_workspace *w, const double *r, double *z,
+                     sq_stream_t stream);
+int sq_apply_precond_f32(const sq_precond *pc, sq_workspace *w, const float *r, float *z,
+                         sq_stream_t stream);
+
+/* Kernel timing aid: while enabled, the library records a CUDA event pair on
+ * the launching stream around each of its kernel launches and sorts them into
+ * kernel classes (sq_profile_class_name). enable = 1 clears the totals and
+ * starts recording, 0 stops. Not thread-safe: one host thread at a time. */
+int sq_profile_enable(int enable);
+/* Synchronizes the recorded events and returns the number of classes (or
+ * -SQ_ECUDA); for k < min(classes, max_classes) fills ms[k] (summed device time
+ * of the class) and launches[k], then clears the record. Either array may be
+ * NULL. */
+int sq_profile_read(double *ms, int64_t *launches, int max_classes);
+const char *sq_profile_class_name(int k);
+
+const char *sq_strerror(int status);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* SQ_H */

@@ -146,3 +146,42 @@ def apply_stencil(a_edges: np.ndarray, psi: np.ndarray) -> np.ndarray:
         a_dn = np.roll(a_edges[d], 1, axis=d)  # a_d(j - e_d)
         out += a_edges[d] * (psi - up) + a_dn * (psi - dn)
     return out
+
+
+def edge_coefficient_at(cellval: np.ndarray, n: int, d: int, j) -> float:
+    """a_d(j) at one node from the definition: mean of the four voxels around
+    the edge j -> j+e_d (voxel v has the value of cell v // n)."""
+    L = cellval.shape[0]
+    N = L * n
+    t1, t2 = [t for t in range(3) if t != d]
+    s = 0.0
+    for s1 in (0, 1):
+        for s2 in (0, 1):
+            v = list(j)
+            v[t1] = (j[t1] - s1) % N
+            v[t2] = (j[t2] - s2) % N
+            s += cellval[v[0] // n, v[1] // n, v[2] // n]
+    return 0.25 * s
+
+
+def apply_at(cellval: np.ndarray, n: int, psi_at, j) -> float:
+    """(A psi)(j) at one node; psi_at(k) returns psi at node k (tuple)."""
+    N = cellval.shape[0] * n
+    out = 0.0
+    pj = psi_at(tuple(j))
+    for d in range(3):
+        up = list(j)
+        up[d] = (j[d] + 1) % N
+        dn = list(j)
+        dn[d] = (j[d] - 1) % N
+        out += edge_coefficient_at(cellval, n, d, j) * (pj - psi_at(tuple(up)))
+        out += edge_coefficient_at(cellval, n, d, tuple(dn)) * (pj - psi_at(tuple(dn)))
+    return out
+
+
+def rhs_at(cellval: np.ndarray, n: int, i: int, j) -> float:
+    """b_i(j) = a_i(j) - a_i(j - e_i) at one node."""
+    N = cellval.shape[0] * n
+    dn = list(j)
+    dn[i] = (j[i] - 1) % N
+    return edge_coefficient_at(cellval, n, i, j) - edge_coefficient_at(cellval, n, i, tuple(dn))

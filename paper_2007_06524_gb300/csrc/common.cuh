@@ -1,0 +1,222 @@
+// Internal declarations shared by the libsq translation units.
+//
+// Field layout (Sec. 3.2, big-endian order): node (j1,j2,j3) of the N^3 grid at
+// j3 + N*j2 + N*N*j1. Cells: (c1,c2,c3) at c3 + L*c2 + L*L*c1, c = j / n.
+#pragma once
+
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+#include "sq.h"
+
+namespace sq {
+
+constexpr int kThreads = 256;        // block size of every field kernel
+constexpr int kMaxPartials = 16384;  // max blocks of a reducing kernel
+constexpr int kMaxQ = 24;            // max quantities reduced by one kernel
+constexpr int kMaxN = 512;
+constexpr int kMaxRank = 64;
+
+// Device-resident solver scalars. Written only by the last block of a
+// reducing kernel (or by the host before a solve), read by later kernels.
+struct Scalars {
+  double bb;        // ||b||^2
+  double rr;        // ||r||^2 of the recurrence residual
+  double rz;        // r.z (current)
+  double rz_old;    // r.z (previous iteration)
+  double pq;        // p.Ap
+  double alpha;     // alpha_k = rz / pq
+  double beta;      // beta_k = rz_new / rz_old
+  double tol2;      // tol^2 * bb
+  double tolrel2;   // tol^2 (set by the host before a solve)
+  double mean;      // mean of the final iterate
+  double rr_true;   // ||b - A x||^2 recomputed
+  double red[kMaxQ];  // raw sums of the last reduction (verification / A_hom)
+  int done;         // 1: no further PCG kernel does work
+  int conv;         // 1: converged (0 with done=1: max_iter or breakdown)
+  int iter;         // x updates so far (cumulative over restarts)
+  int max_iter;
+  int x_pending;    // 1: x += alpha p of the last iteration not applied yet
+  int breakdown;    // 1: non-positive p.Ap or r.z
+  unsigned int ticket;  // last-block counter (reset by the last block)
+  int pad;
+};
+
+enum FinalizeOp : int {
+  FIN_NONE = 0,      // raw sums -> red[]
+  FIN_ALPHA = 1,     // q = A p: pq = s0, alpha = rz / pq
+  FIN_RESID = 2,     // r = b - A x: rr = s0, bb = s1 (if set_bb), done if rr <= tol2
+  FIN_RR_ITER = 3,   // r -= alpha q: rr = s0, iter++, convergence / max_iter check
+  FIN_RZ_FIRST = 4,  // r.z of the initial residual
+  FIN_RZ_BETA = 5,   // r.z -> beta
+  FIN_MEAN = 6,      // sum(x) -> mean
+};
+
+template <typename T> struct Cx;
+template <> struct Cx<float> { using type = float2; };
+template <> struct Cx<double> { using type = double2; };
+
+// ---------------------------------------------------------------- reductions
+
+__device__ __forceinline__ double warp_sum(double v) {
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+  return v;
+}
+
+// Block-reduces NQ per-thread values, writes one partial per block and lets
+// the last block to finish sum all partials in a fixed order (deterministic,
+// independent of which block is last). Returns true in every thread of that
+// last block; the sums are then in out[0..NQ). Requires blockDim = kThreads.
+template <int NQ>
+__device__ __forceinline__ bool reduce_last_block(double (&v)[NQ], double *partials, unsigned *ticket,
+                                                  double (&out)[NQ]) {
+  __shared__ double s_w[NQ][kThreads / 32];
+  __shared__ unsigned s_last;
+  const int tid = threadIdx.x + blockDim.x * (threadIdx.y + blockDim.y * threadIdx.z);
+  const int lane = tid & 31, wid = tid >> 5;
+  const int nblk = gridDim.x * gridDim.y * gridDim.z;
+  const int bid = blockIdx.x + gridDim.x * (blockIdx.y + gridDim.y * blockIdx.z);
+#pragma unroll
+  for (int q = 0; q < NQ; ++q) {
+    double s = warp_sum(v[q]);
+    if (lane == 0) s_w[q][wid] = s;
+  }
+  __syncthreads();
+  if (tid == 0) {
+#pragma unroll
+    for (int q = 0; q < NQ; ++q) {
+      double s = 0.0;
+      for (int w = 0; w < kThreads / 32; ++w) s += s_w[q][w];
+      partials[q * kMaxPartials + bid] = s;
+    }
+    __threadfence();
+    unsigned t = atomicAdd(ticket, 1u);
+    s_last = (t == (unsigned)(nblk - 1)) ? 1u : 0u;
+  }
+  __syncthreads();
+  if (!s_last) return false;
+  __threadfence();
+#pragma unroll
+  for (int q = 0; q < NQ; ++q) {
+    double s = 0.0;
+    for (int i = tid; i < nblk; i += kThreads) s += __ldcg(&partials[q * kMaxPartials + i]);
+    s = warp_sum(s);
+    if (lane == 0) s_w[q][wid] = s;
+  }
+  __syncthreads();
+#pragma unroll
+  for (int q = 0; q < NQ; ++q) {
+    double s = 0.0;
+    for (int w = 0; w < kThreads / 32; ++w) s += s_w[q][w];
+    out[q] = s;
+  }
+  if (tid == 0) *ticket = 0u;
+  return true;
+}
+
+// Scalar bookkeeping done by thread 0 of the last block.
+__device__ __forceinline__ void finalize_scalars(Scalars *st, int op, const double *s, int nq) {
+  for (int q = 0; q < nq && q < kMaxQ; ++q) st->red[q] = s[q];
+  switch (op) {
+    case FIN_ALPHA:
+      st->pq = s[0];
+      if (s[0] > 0.0 && st->rz > 0.0) {
+        st->alpha = st->rz / s[0];
+      } else {
+        st->alpha = 0.0;
+        st->done = 1;
+        st->breakdown = 1;
+      }
+      break;
+    case FIN_RESID:
+      st->bb = s[1];
+      st->tol2 = st->tolrel2 * s[1];
+      st->rr = s[0];
+      st->rr_true = s[0];
+      st->done = (s[0] <= st->tol2 || !(s[1] > 0.0)) ? 1 : 0;
+      st->conv = st->done;
+      st->x_pending = 0;
+      break;
+    case FIN_RR_ITER:
+      st->rr = s[0];
+      st->iter += 1;
+      if (s[0] <= st->tol2) {
+        st->done = 1;
+        st->conv = 1;
+        st->x_pending = 1;
+      } else if (st->iter >= st->max_iter || !(s[0] == s[0])) {
+        st->done = 1;
+        st->x_pending = 1;
+      }
+      break;
+    case FIN_RZ_FIRST:
+      st->rz = s[0];
+      if (!(s[0] > 0.0)) { st->done = 1; st->breakdown = 1; }
+      break;
+    case FIN_RZ_BETA:
+      st->rz_old = st->rz;
+      st->rz = s[0];
+      if (s[0] > 0.0) {
+        st->beta = s[0] / st->rz_old;
+      } else {
+        st->beta = 0.0;
+        st->done = 1;
+        st->breakdown = 1;
+      }
+      break;
+    default:
+      break;
+  }
+}
+
+// ------------------------------------------------------------ host launchers
+
+struct CellsDev {
+  const uint8_t *phase;  // L^3 cell phases
+  int L, n, N;
+  double a_lo, a_hi;
+};
+
+struct RedBuf {
+  Scalars *st;
+  double *partials;  // kMaxQ * kMaxPartials
+};
+
+// stencil.cu
+cudaError_t launch_coeff_gen(uint8_t *phase, int L, uint64_t seed, uint64_t thr, cudaStream_t s);
+enum StencilMode : int { ST_MATVEC = 0, ST_RESID = 1, ST_RHS = 2 };
+// y = A x (ST_MATVEC, reduces x.y), y = b_dir - A x (ST_RESID, reduces ||y||^2
+// and ||b||^2), y = b_dir (ST_RHS, reduces ||b||^2). Ti: type of x and of the
+// arithmetic; To: type of y.
+template <typename Ti, typename To>
+cudaError_t launch_stencil(const CellsDev &c, int mode, int dir, const Ti *x, To *y, RedBuf rb, int fin,
+                           bool check_done, cudaStream_t s);
+cudaError_t launch_ahom(const CellsDev &c, const double *p0, const double *p1, const double *p2, RedBuf rb,
+                        cudaStream_t s);
+template <typename T>
+cudaError_t launch_x_final_sum(T *x, const T *p, RedBuf rb, long long n, cudaStream_t s);
+template <typename T>
+cudaError_t launch_sub_mean(T *x, RedBuf rb, long long n, cudaStream_t s);
+// x64 += d32 (refinement update), and plain casts
+cudaError_t launch_add_f32_to_f64(double *x, const float *d, long long n, cudaStream_t s);
+
+// dht.cu
+struct SpectralDev {
+  int N;
+  int rank;          // 0 = exact
+  int nst;           // FFT stages
+  int radix[12];
+  const void *tw;    // N complex twiddles exp(-2 pi i m / N), type Cx<T>
+  const void *lam;   // N eigenvalues lambda_k (T)
+  const void *u;     // rank x N scaled factors (T), u_r(k) * (64 N^3)^(-1/3)
+  double scale;      // 1 / (64 N^3) for the exact diagonal
+};
+enum DhtPass : int { PASS_A_RESID = 0, PASS_A_PLAIN = 1, PASS_B = 2, PASS_C = 3, PASS_E_PCG = 4, PASS_E_PLAIN = 5 };
+// One pencil pass of the 3D Hartley transform pipeline (see dht.cu).
+template <typename T>
+cudaError_t launch_dht_pass(int pass, const SpectralDev &sp, const T *in, T *out, T *r, const T *q, T *p, T *x,
+                            RedBuf rb, bool first, bool check_done, cudaStream_t s);
+int dht_tile_pencils(int N, int elem_bytes);
+
+}  // namespace sq

@@ -1,0 +1,747 @@
+// Host side of libsq: handles, preconditioner tables, the PCG driver and the
+// C ABI declared in include/sq.h.
+//
+// PCG (Sec. 4.1, Eqs. 24-25; Hestenes-Stiefel form of Matlab's pcg) with the
+// iteration split into six kernels; all scalars stay on the device:
+//   K  q = A p                 ; p.q      -> alpha = rz/pq
+//   A  x3 Hartley pass of r -= alpha q    ; ||r||^2 -> iter++, stop test
+//   B  x2 pass
+//   C  x1 pass, G scaling, x1 pass        ; r.z    -> beta
+//   D  x2 pass
+//   E  x3 pass -> z; x += alpha p; p = z + beta p
+// Once the stop test fires every later kernel returns at entry; the host only
+// polls a pinned copy of the `done` flag one chunk of iterations behind, so the
+// GPU queue never drains while the host waits.
+#include <cmath>
+#include <cstdio>
+#include <cstdlib>
+#include <cstring>
+#include <new>
+#include <vector>
+
+#include "common.cuh"
+
+using namespace sq;
+
+struct sq_coeffs {
+  int L, n, N;
+  double a_lo, a_hi;
+  uint8_t *d_phase;
+  cudaStream_t stream;
+  Scalars *d_st;       // reduction scalars for operator / A_hom calls
+  double *d_partials;  // kMaxQ * kMaxPartials
+  Scalars *h_st;       // pinned
+};
+
+struct sq_precond {
+  int N, rank;
+  SpectralDev sp64, sp32;
+  void *d_mem;
+};
+
+struct sq_workspace {
+  int N, precision;
+  double *f64;   // r, p, q, Y (SQ_FP64)
+  float *f32;    // r, p, q, Y, d (SQ_FP32_REFINE)
+  Scalars *d_st;  // [0] outer / FP64 solve, [1] inner FP32 solve
+  double *d_partials;
+  Scalars *h_st;  // pinned copies of the two scalar blocks
+  int *h_poll;    // pinned, 2 slots
+  cudaEvent_t ev[2];
+};
+
+namespace {
+
+#define SQ_CK(call)                                   \
+  do {                                                \
+    cudaError_t _e = (call);                          \
+    if (_e != cudaSuccess) return SQ_ECUDA;           \
+  } while (0)
+
+// ---------------------------------------------------------------- profiling
+// Optional CUDA-event pairs around every kernel launch, summed per class.
+enum ProfClass : int {
+  PC_COEFF = 0, PC_MATVEC, PC_RESID, PC_DHT_A, PC_DHT_B, PC_DHT_C, PC_DHT_E, PC_VECTOR, PC_AHOM, PC_SCALAR,
+  PC_COUNT
+};
+const char *const kProfNames[PC_COUNT] = {"coeff_gen",  "stencil_matvec", "stencil_resid_rhs", "dht_x3_in",
+                                          "dht_x2",     "dht_x1_scale",   "dht_x3_out",        "vector",
+                                          "ahom",       "scalars"};
+struct Prof {
+  bool on = false;
+  std::vector<cudaEvent_t> pool;
+  std::vector<int> cls;
+  size_t used = 0;
+};
+Prof g_prof;
+
+const size_t kNoProf = (size_t)-1;
+
+size_t prof_begin(int cls, cudaStream_t s) {
+  if (!g_prof.on) return kNoProf;
+  while (g_prof.pool.size() < g_prof.used + 2) {
+    cudaEvent_t e;
+    if (cudaEventCreate(&e) != cudaSuccess) return kNoProf;
+    g_prof.pool.push_back(e);
+  }
+  const size_t i = g_prof.used;
+  if (cudaEventRecord(g_prof.pool[i], s) != cudaSuccess) return kNoProf;
+  g_prof.cls.push_back(cls);
+  g_prof.used += 2;
+  return i;
+}
+
+void prof_end(size_t i, cudaStream_t s) {
+  if (i != kNoProf) cudaEventRecord(g_prof.pool[i + 1], s);
+}
+
+#define SQ_LAUNCH(cls, s, call)                      \
+  do {                                               \
+    const size_t _pi = prof_begin((cls), (s));       \
+    cudaError_t _e = (call);                         \
+    prof_end(_pi, (s));                              \
+    if (_e != cudaSuccess) return SQ_ECUDA;          \
+  } while (0)
+
+bool valid_N(int N) {
+  if (N < 8 || N > kMaxN || (N & 1)) return false;
+  int m = N;
+  while (m % 2 == 0) m /= 2;
+  if (m % 3 == 0) m /= 3;
+  return m == 1;
+}
+
+CellsDev cells_dev(const sq_coeffs *c) {
+  CellsDev d;
+  d.phase = c->d_phase;
+  d.L = c->L;
+  d.n = c->n;
+  d.N = c->N;
+  d.a_lo = c->a_lo;
+  d.a_hi = c->a_hi;
+  return d;
+}
+
+int alloc_coeffs(int L, int n, double a_lo, double a_hi, cudaStream_t s, sq_coeffs **out) {
+  if (!out) return SQ_EINVAL;
+  *out = nullptr;
+  if (L < 1 || n < 2 || !valid_N(L * n)) return SQ_EINVAL;
+  if (!(a_lo > 0.0) || !(a_hi > 0.0) || !std::isfinite(a_lo) || !std::isfinite(a_hi)) return SQ_EINVAL;
+  sq_coeffs *c = new (std::nothrow) sq_coeffs();
+  if (!c) return SQ_ENOMEM;
+  c->L = L;
+  c->n = n;
+  c->N = L * n;
+  c->a_lo = a_lo;
+  c->a_hi = a_hi;
+  c->stream = s;
+  if (cudaMalloc(&c->d_phase, (size_t)L * L * L) != cudaSuccess ||
+      cudaMalloc(&c->d_st, sizeof(Scalars)) != cudaSuccess ||
+      cudaMalloc(&c->d_partials, sizeof(double) * kMaxQ * kMaxPartials) != cudaSuccess ||
+      cudaMallocHost(&c->h_st, sizeof(Scalars)) != cudaSuccess) {
+    sq_coeffs_destroy(c);
+    return SQ_ENOMEM;
+  }
+  if (cudaMemsetAsync(c->d_st, 0, sizeof(Scalars), s) != cudaSuccess) {
+    sq_coeffs_destroy(c);
+    return SQ_ECUDA;
+  }
+  *out = c;
+  return SQ_OK;
+}
+
+// radix plan: 3 (if present) last, powers of two as 8s then one 4 or 2
+int radix_plan(int N, int *rad) {
+  int m = N, ns = 0, t = 0;
+  while (m % 3 == 0) {
+    m /= 3;
+    ++t;
+  }
+  int e = 0;
+  while (m > 1) {
+    m /= 2;
+    ++e;
+  }
+  if (e == 4) {
+    rad[ns++] = 4;
+    rad[ns++] = 4;
+    e = 0;
+  }
+  while (e >= 3) {
+    rad[ns++] = 8;
+    e -= 3;
+  }
+  if (e == 2) rad[ns++] = 4;
+  if (e == 1) rad[ns++] = 2;
+  for (int i = 0; i < t; ++i) rad[ns++] = 3;
+  return ns;
+}
+
+// Rank-R exponential sum for 1/x on [lambda_min, 12] (Sec. 4.2, Eq. 34 read as
+// the trapezoid rule for 1/x = int exp(s - x e^s) ds): three error terms --
+// lower truncation 12 e^{s_lo}, upper truncation exp(-lambda_min e^{s_hi}) and
+// the step error exp(-pi^2/eta) -- are balanced at one level eps, found by
+// bisection on ln(eps); nodes s_r = s_lo + r eta, t_r = e^{s_r}, w_r = eta e^{s_r}.
+void rank_r_nodes(int N, int R, std::vector<double> &t, std::vector<double> &w) {
+  const double pi = 3.14159265358979323846;
+  const double sn = std::sin(pi / N);
+  const double lam_min = 4.0 * sn * sn;
+  double lo = std::log(1e-300), hi = std::log(0.5);
+  auto eta_of = [&](double le, double *slo) {
+    const double s_lo = le - std::log(12.0);
+    const double s_hi = std::log(-le / lam_min);
+    *slo = s_lo;
+    return (s_hi - s_lo) / (R - 1);
+  };
+  for (int it = 0; it < 200; ++it) {
+    const double mid = 0.5 * (lo + hi);
+    double slo;
+    const double eta = eta_of(mid, &slo);
+    if (std::exp(-pi * pi / eta) > std::exp(mid))
+      lo = mid;
+    else
+      hi = mid;
+  }
+  double s_lo;
+  const double eta = eta_of(0.5 * (lo + hi), &s_lo);
+  t.resize(R);
+  w.resize(R);
+  for (int r = 0; r < R; ++r) {
+    const double s = s_lo + eta * r;
+    t[r] = std::exp(s);
+    w[r] = eta * std::exp(s);
+  }
+}
+
+template <typename T>
+RedBuf redbuf(Scalars *st, double *partials) {
+  RedBuf rb;
+  rb.st = st;
+  rb.partials = partials;
+  return rb;
+}
+
+__global__ void k_scalars_reset(Scalars *st, double tolrel2, int max_iter) {
+  if (threadIdx.x == 0 && blockIdx.x == 0) {
+    Scalars z;
+    memset(&z, 0, sizeof(z));
+    z.tolrel2 = tolrel2;
+    z.max_iter = max_iter;
+    *st = z;
+  }
+}
+
+// Inner FP32 solve of A d = r (r = FP32 copy of the outer residual): its
+// ||b||^2 is the outer residual norm.
+__global__ void k_inner_init(Scalars *in, const Scalars *outer, double tolrel2, int max_iter) {
+  if (threadIdx.x == 0 && blockIdx.x == 0) {
+    Scalars z;
+    memset(&z, 0, sizeof(z));
+    z.tolrel2 = tolrel2;
+    z.max_iter = max_iter;
+    z.bb = outer->rr_true;
+    z.tol2 = tolrel2 * outer->rr_true;
+    z.done = (outer->rr_true > 0.0) ? 0 : 1;
+    *in = z;
+  }
+}
+
+template <typename T>
+const SpectralDev &spec(const sq_precond *pc);
+template <>
+const SpectralDev &spec<double>(const sq_precond *pc) { return pc->sp64; }
+template <>
+const SpectralDev &spec<float>(const sq_precond *pc) { return pc->sp32; }
+
+// Preconditioned residual from r: z passes with p = z (first) inside PCG.
+template <typename T>
+int precond_first(const sq_precond *pc, T *r, T *Y, T *p, RedBuf rb, cudaStream_t s) {
+  const SpectralDev &sp = spec<T>(pc);
+  SQ_LAUNCH(PC_DHT_A, s, launch_dht_pass<T>(PASS_A_PLAIN, sp, r, Y, nullptr, nullptr, nullptr, nullptr, rb, true, true, s));
+  SQ_LAUNCH(PC_DHT_B, s, launch_dht_pass<T>(PASS_B, sp, Y, Y, nullptr, nullptr, nullptr, nullptr, rb, true, true, s));
+  SQ_LAUNCH(PC_DHT_C, s, launch_dht_pass<T>(PASS_C, sp, Y, Y, nullptr, nullptr, nullptr, nullptr, rb, true, true, s));
+  SQ_LAUNCH(PC_DHT_B, s, launch_dht_pass<T>(PASS_B, sp, Y, Y, nullptr, nullptr, nullptr, nullptr, rb, true, true, s));
+  SQ_LAUNCH(PC_DHT_E, s, launch_dht_pass<T>(PASS_E_PCG, sp, Y, nullptr, nullptr, nullptr, p, nullptr, rb, true, true, s));
+  return SQ_OK;
+}
+
+template <typename T>
+int pcg_iteration(const sq_coeffs *c, const sq_precond *pc, T *x, T *r, T *p, T *q, T *Y, RedBuf rb,
+                  cudaStream_t s) {
+  const SpectralDev &sp = spec<T>(pc);
+  const CellsDev cd = cells_dev(c);
+  SQ_LAUNCH(PC_MATVEC, s, (launch_stencil<T, T>(cd, ST_MATVEC, 0, p, q, rb, FIN_ALPHA, true, s)));
+  SQ_LAUNCH(PC_DHT_A, s, launch_dht_pass<T>(PASS_A_RESID, sp, r, Y, r, q, nullptr, nullptr, rb, false, true, s));
+  SQ_LAUNCH(PC_DHT_B, s, launch_dht_pass<T>(PASS_B, sp, Y, Y, nullptr, nullptr, nullptr, nullptr, rb, false, true, s));
+  SQ_LAUNCH(PC_DHT_C, s, launch_dht_pass<T>(PASS_C, sp, Y, Y, nullptr, nullptr, nullptr, nullptr, rb, false, true, s));
+  SQ_LAUNCH(PC_DHT_B, s, launch_dht_pass<T>(PASS_B, sp, Y, Y, nullptr, nullptr, nullptr, nullptr, rb, false, true, s));
+  SQ_LAUNCH(PC_DHT_E, s, launch_dht_pass<T>(PASS_E_PCG, sp, Y, nullptr, nullptr, nullptr, p, x, rb, false, true, s));
+  return SQ_OK;
+}
+
+// Runs PCG iterations until the device sets `done` (converged, max_iter or
+// breakdown) or `budget` iterations were launched. Polls one chunk behind.
+template <typename T>
+int pcg_loop(sq_workspace *w, const sq_coeffs *c, const sq_precond *pc, T *x, T *r, T *p, T *q, T *Y, RedBuf rb,
+             int budget, cudaStream_t s) {
+  const int chunk = 8;
+  int launched = 0, slot = 0;
+  bool pending[2] = {false, false};
+  w->h_poll[0] = w->h_poll[1] = 0;
+  const size_t done_off = offsetof(Scalars, done);
+  while (launched < budget) {
+    const int nb = (budget - launched < chunk) ? budget - launched : chunk;
+    for (int i = 0; i < nb; ++i) {
+      int st = pcg_iteration<T>(c, pc, x, r, p, q, Y, rb, s);
+      if (st != SQ_OK) return st;
+    }
+    launched += nb;
+    SQ_CK(cudaMemcpyAsync(&w->h_poll[slot], reinterpret_cast<char *>(rb.st) + done_off, sizeof(int),
+                          cudaMemcpyDeviceToHost, s));
+    SQ_CK(cudaEventRecord(w->ev[slot], s));
+    pending[slot] = true;
+    const int other = slot ^ 1;
+    if (pending[other]) {
+      SQ_CK(cudaEventSynchronize(w->ev[other]));
+      pending[other] = false;
+      if (w->h_poll[other]) break;
+    }
+    slot = other;
+  }
+  return SQ_OK;
+}
+
+int read_scalars(Scalars *h, const Scalars *d, cudaStream_t s) {
+  SQ_CK(cudaMemcpyAsync(h, d, sizeof(Scalars), cudaMemcpyDeviceToHost, s));
+  SQ_CK(cudaStreamSynchronize(s));
+  return SQ_OK;
+}
+
+int solve_fp64(const sq_coeffs *c, const sq_precond *pc, sq_workspace *w, int dir, double tol, int max_iter,
+               const double *x0, double *psi, sq_solve_info *info, cudaStream_t s) {
+  const long long n3 = (long long)c->N * c->N * c->N;
+  double *r = w->f64, *p = r + n3, *q = p + n3, *Y = q + n3;
+  const RedBuf rb = redbuf<double>(&w->d_st[0], w->d_partials);
+  const CellsDev cd = cells_dev(c);
+  SQ_LAUNCH(PC_SCALAR, s, (k_scalars_reset<<<1, 1, 0, s>>>(rb.st, tol * tol, max_iter), cudaGetLastError()));
+  if (x0) {
+    if (x0 != psi) SQ_CK(cudaMemcpyAsync(psi, x0, sizeof(double) * n3, cudaMemcpyDeviceToDevice, s));
+    SQ_LAUNCH(PC_RESID, s, (launch_stencil<double, double>(cd, ST_RESID, dir, psi, r, rb, FIN_RESID, false, s)));
+  } else {
+    SQ_CK(cudaMemsetAsync(psi, 0, sizeof(double) * n3, s));
+    SQ_LAUNCH(PC_RESID, s, (launch_stencil<double, double>(cd, ST_RHS, dir, nullptr, r, rb, FIN_RESID, false, s)));
+  }
+  Scalars *h = &w->h_st[0];
+  for (int restart = 0; restart < 4; ++restart) {
+    int st = precond_first<double>(pc, r, Y, p, rb, s);
+    if (st != SQ_OK) return st;
+    st = pcg_loop<double>(w, c, pc, psi, r, p, q, Y, rb, max_iter, s);
+    if (st != SQ_OK) return st;
+    SQ_LAUNCH(PC_VECTOR, s, launch_x_final_sum<double>(psi, p, rb, n3, s));
+    SQ_LAUNCH(PC_VECTOR, s, launch_sub_mean<double>(psi, rb, n3, s));
+    SQ_LAUNCH(PC_RESID, s, (launch_stencil<double, double>(cd, ST_RESID, dir, psi, r, rb, FIN_RESID, false, s)));
+    st = read_scalars(h, rb.st, s);
+    if (st != SQ_OK) return st;
+    if (h->done || h->iter >= max_iter || h->breakdown) break;
+  }
+  if (info) {
+    info->iters = h->iter;
+    info->outer_steps = 1;
+    info->used_guess = x0 ? 1 : 0;
+    info->relres = (h->bb > 0.0) ? std::sqrt(h->rr / h->bb) : 0.0;
+    info->relres_true = (h->bb > 0.0) ? std::sqrt(h->rr_true / h->bb) : 0.0;
+    info->status = (h->bb == 0.0 || info->relres_true <= tol) ? SQ_OK : SQ_ENOCONV;
+  }
+  const bool ok = (h->bb == 0.0) || std::sqrt(h->rr_true / h->bb) <= tol;
+  return ok ? SQ_OK : SQ_ENOCONV;
+}
+
+int solve_fp32_refine(const sq_coeffs *c, const sq_precond *pc, sq_workspace *w, int dir, double tol,
+                      int max_iter, const double *x0, double *psi, sq_solve_info *info, cudaStream_t s) {
+  const long long n3 = (long long)c->N * c->N * c->N;
+  float *r = w->f32, *p = r + n3, *q = p + n3, *Y = q + n3, *d = Y + n3;
+  const RedBuf ro = redbuf<double>(&w->d_st[0], w->d_partials);
+  const RedBuf ri = redbuf<double>(&w->d_st[1], w->d_partials);
+  const CellsDev cd = cells_dev(c);
+  const double tol_in = 1e-4;
+  SQ_LAUNCH(PC_SCALAR, s, (k_scalars_reset<<<1, 1, 0, s>>>(ro.st, tol * tol, max_iter), cudaGetLastError()));
+  if (x0) {
+    if (x0 != psi) SQ_CK(cudaMemcpyAsync(psi, x0, sizeof(double) * n3, cudaMemcpyDeviceToDevice, s));
+  } else {
+    SQ_CK(cudaMemsetAsync(psi, 0, sizeof(double) * n3, s));
+  }
+  Scalars *ho = &w->h_st[0], *hi = &w->h_st[1];
+  int total_inner = 0, outer = 0;
+  double relres_in = 0.0;
+  for (;;) {
+    // FP64 true residual, stored as the FP32 right-hand side of the correction
+    SQ_LAUNCH(PC_RESID, s, (launch_stencil<double, float>(cd, ST_RESID, dir, psi, r, ro, FIN_RESID, false, s)));
+    int st = read_scalars(ho, ro.st, s);
+    if (st != SQ_OK) return st;
+    if (ho->done || total_inner >= max_iter || outer >= 30) break;
+    const int budget = max_iter - total_inner;
+    SQ_LAUNCH(PC_SCALAR, s, (k_inner_init<<<1, 1, 0, s>>>(ri.st, ro.st, tol_in * tol_in, budget), cudaGetLastError()));
+    SQ_CK(cudaMemsetAsync(d, 0, sizeof(float) * n3, s));
+    st = precond_first<float>(pc, r, Y, p, ri, s);
+    if (st != SQ_OK) return st;
+    st = pcg_loop<float>(w, c, pc, d, r, p, q, Y, ri, budget, s);
+    if (st != SQ_OK) return st;
+    SQ_LAUNCH(PC_VECTOR, s, launch_x_final_sum<float>(d, p, ri, n3, s));
+    SQ_LAUNCH(PC_VECTOR, s, launch_add_f32_to_f64(psi, d, n3, s));
+    st = read_scalars(hi, ri.st, s);
+    if (st != SQ_OK) return st;
+    relres_in = (hi->bb > 0.0) ? std::sqrt(hi->rr / hi->bb) : 0.0;
+    total_inner += hi->iter;
+    ++outer;
+    if (hi->iter == 0 && !hi->conv) break;  // no progress possible
+  }
+  SQ_LAUNCH(PC_VECTOR, s, launch_x_final_sum<double>(psi, nullptr, ro, n3, s));  // x_pending = 0 after FIN_RESID
+  SQ_LAUNCH(PC_VECTOR, s, launch_sub_mean<double>(psi, ro, n3, s));
+  SQ_CK(cudaStreamSynchronize(s));
+  const double rel = (ho->bb > 0.0) ? std::sqrt(ho->rr_true / ho->bb) : 0.0;
+  if (info) {
+    info->iters = total_inner;
+    info->outer_steps = outer;
+    info->used_guess = x0 ? 1 : 0;
+    info->relres = relres_in;
+    info->relres_true = rel;
+    info->status = (ho->bb == 0.0 || rel <= tol) ? SQ_OK : SQ_ENOCONV;
+  }
+  return (ho->bb == 0.0 || rel <= tol) ? SQ_OK : SQ_ENOCONV;
+}
+
+template <typename T>
+int apply_precond_t(const sq_precond *pc, sq_workspace *w, const T *r, T *z, T *Y, cudaStream_t s) {
+  const SpectralDev &sp = spec<T>(pc);
+  const RedBuf rb = redbuf<double>(&w->d_st[0], w->d_partials);
+  SQ_LAUNCH(PC_SCALAR, s, (k_scalars_reset<<<1, 1, 0, s>>>(rb.st, 0.0, 1), cudaGetLastError()));
+  SQ_LAUNCH(PC_DHT_A, s, launch_dht_pass<T>(PASS_A_PLAIN, sp, r, Y, nullptr, nullptr, nullptr, nullptr, rb, true, false, s));
+  SQ_LAUNCH(PC_DHT_B, s, launch_dht_pass<T>(PASS_B, sp, Y, Y, nullptr, nullptr, nullptr, nullptr, rb, true, false, s));
+  SQ_LAUNCH(PC_DHT_C, s, launch_dht_pass<T>(PASS_C, sp, Y, Y, nullptr, nullptr, nullptr, nullptr, rb, true, false, s));
+  SQ_LAUNCH(PC_DHT_B, s, launch_dht_pass<T>(PASS_B, sp, Y, Y, nullptr, nullptr, nullptr, nullptr, rb, true, false, s));
+  SQ_LAUNCH(PC_DHT_E, s, launch_dht_pass<T>(PASS_E_PLAIN, sp, Y, z, nullptr, nullptr, nullptr, nullptr, rb, true, false, s));
+  return SQ_OK;
+}
+
+}  // namespace
+
+// =================================================================== C ABI
+extern "C" {
+
+const char *sq_strerror(int st) {
+  switch (st) {
+    case SQ_OK: return "ok";
+    case SQ_EINVAL: return "invalid argument";
+    case SQ_ENOMEM: return "out of memory";
+    case SQ_ECUDA: return "CUDA error";
+    case SQ_ENOCONV: return "not converged within max_iter";
+    case SQ_ETIMEOUT: return "bounded device wait timed out";
+    case SQ_EBADGUESS: return "initial guess rejected";
+    default: return "unknown status";
+  }
+}
+
+int sq_build_coeffs(int L, int n, uint64_t seed, double p_hi, double a_lo, double a_hi, sq_stream_t stream,
+                    sq_coeffs **out) {
+  if (!(p_hi >= 0.0 && p_hi <= 1.0)) return SQ_EINVAL;
+  cudaStream_t s = reinterpret_cast<cudaStream_t>(stream);
+  int st = alloc_coeffs(L, n, a_lo, a_hi, s, out);
+  if (st != SQ_OK) return st;
+  const uint64_t thr = (uint64_t)(p_hi * 9007199254740992.0);  // floor(p_hi * 2^53)
+  const size_t pi = prof_begin(PC_COEFF, s);
+  const cudaError_t ge = launch_coeff_gen((*out)->d_phase, L, seed, thr, s);
+  prof_end(pi, s);
+  if (ge != cudaSuccess) {
+    sq_coeffs_destroy(*out);
+    *out = nullptr;
+    return SQ_ECUDA;
+  }
+  return SQ_OK;
+}
+
+int sq_coeffs_from_host(int L, int n, const uint8_t *host_phase, double a_lo, double a_hi, sq_stream_t stream,
+                        sq_coeffs **out) {
+  if (!host_phase) return SQ_EINVAL;
+  cudaStream_t s = reinterpret_cast<cudaStream_t>(stream);
+  int st = alloc_coeffs(L, n, a_lo, a_hi, s, out);
+  if (st != SQ_OK) return st;
+  const size_t nc = (size_t)L * L * L;
+  std::vector<uint8_t> norm(nc);
+  for (size_t i = 0; i < nc; ++i) norm[i] = host_phase[i] ? 1 : 0;
+  if (cudaMemcpyAsync((*out)->d_phase, norm.data(), nc, cudaMemcpyHostToDevice, s) != cudaSuccess ||
+      cudaStreamSynchronize(s) != cudaSuccess) {
+    sq_coeffs_destroy(*out);
+    *out = nullptr;
+    return SQ_ECUDA;
+  }
+  return SQ_OK;
+}
+
+int sq_coeffs_regenerate(sq_coeffs *c, uint64_t seed, double p_hi, sq_stream_t stream) {
+  if (!c || !(p_hi >= 0.0 && p_hi <= 1.0)) return SQ_EINVAL;
+  cudaStream_t s = reinterpret_cast<cudaStream_t>(stream);
+  const uint64_t thr = (uint64_t)(p_hi * 9007199254740992.0);
+  SQ_LAUNCH(PC_COEFF, s, launch_coeff_gen(c->d_phase, c->L, seed, thr, s));
+  return SQ_OK;
+}
+
+int sq_coeffs_upload(sq_coeffs *c, const uint8_t *host_phase, sq_stream_t stream) {
+  if (!c || !host_phase) return SQ_EINVAL;
+  cudaStream_t s = reinterpret_cast<cudaStream_t>(stream);
+  SQ_CK(cudaMemcpyAsync(c->d_phase, host_phase, (size_t)c->L * c->L * c->L, cudaMemcpyHostToDevice, s));
+  return SQ_OK;
+}
+
+int sq_profile_enable(int enable) {
+  g_prof.on = enable != 0;
+  if (g_prof.on) {
+    g_prof.used = 0;
+    g_prof.cls.clear();
+  }
+  return SQ_OK;
+}
+
+int sq_profile_read(double *ms, int64_t *launches, int max_classes) {
+  double acc[PC_COUNT] = {0};
+  int64_t cnt[PC_COUNT] = {0};
+  for (size_t k = 0; k < g_prof.cls.size(); ++k) {
+    const size_t i = 2 * k;
+    if (cudaEventSynchronize(g_prof.pool[i + 1]) != cudaSuccess) return -SQ_ECUDA;
+    float t = 0.f;
+    if (cudaEventElapsedTime(&t, g_prof.pool[i], g_prof.pool[i + 1]) != cudaSuccess) return -SQ_ECUDA;
+    acc[g_prof.cls[k]] += t;
+    cnt[g_prof.cls[k]] += 1;
+  }
+  for (int k = 0; k < PC_COUNT && k < max_classes; ++k) {
+    if (ms) ms[k] = acc[k];
+    if (launches) launches[k] = cnt[k];
+  }
+  g_prof.used = 0;
+  g_prof.cls.clear();
+  return PC_COUNT;
+}
+
+const char *sq_profile_class_name(int k) { return (k >= 0 && k < PC_COUNT) ? kProfNames[k] : "?"; }
+
+int sq_coeffs_cells(const sq_coeffs *c, uint8_t *host_phase, int64_t *n_hi) {
+  if (!c) return SQ_EINVAL;
+  const size_t nc = (size_t)c->L * c->L * c->L;
+  std::vector<uint8_t> tmp(nc);
+  SQ_CK(cudaMemcpyAsync(tmp.data(), c->d_phase, nc, cudaMemcpyDeviceToHost, c->stream));
+  SQ_CK(cudaStreamSynchronize(c->stream));
+  if (host_phase) std::memcpy(host_phase, tmp.data(), nc);
+  if (n_hi) {
+    int64_t k = 0;
+    for (size_t i = 0; i < nc; ++i) k += tmp[i] ? 1 : 0;
+    *n_hi = k;
+  }
+  return SQ_OK;
+}
+
+int sq_coeffs_shape(const sq_coeffs *c, int *L, int *n, int *N) {
+  if (!c) return SQ_EINVAL;
+  if (L) *L = c->L;
+  if (n) *n = c->n;
+  if (N) *N = c->N;
+  return SQ_OK;
+}
+
+void sq_coeffs_destroy(sq_coeffs *c) {
+  if (!c) return;
+  if (c->d_phase) cudaFree(c->d_phase);
+  if (c->d_st) cudaFree(c->d_st);
+  if (c->d_partials) cudaFree(c->d_partials);
+  if (c->h_st) cudaFreeHost(c->h_st);
+  delete c;
+}
+
+int sq_precond_setup(int N, int rank, sq_precond **out) {
+  if (!out) return SQ_EINVAL;
+  *out = nullptr;
+  if (!valid_N(N) || rank < 0 || rank == 1 || rank > kMaxRank) return SQ_EINVAL;
+  const double pi = 3.14159265358979323846;
+  std::vector<double> tw64(2 * N), lam64(N), u64((size_t)(rank > 0 ? rank : 1) * N, 0.0);
+  for (int m = 0; m < N; ++m) {
+    const double ang = 2.0 * pi * m / N;
+    tw64[2 * m] = std::cos(ang);
+    tw64[2 * m + 1] = -std::sin(ang);
+    const double sn = std::sin(pi * m / N);
+    lam64[m] = 4.0 * sn * sn;
+  }
+  if (rank > 0) {
+    std::vector<double> t, w;
+    rank_r_nodes(N, rank, t, w);
+    const double fold = 1.0 / (4.0 * N);  // (64 N^3)^(-1/3)
+    for (int r = 0; r < rank; ++r) {
+      const double wr = std::cbrt(w[r]) * fold;
+      for (int k = 0; k < N; ++k) u64[(size_t)r * N + k] = wr * std::exp(-t[r] * lam64[k]);
+    }
+  }
+  std::vector<float> tw32(2 * N), lam32(N), u32(u64.size());
+  for (size_t i = 0; i < tw64.size(); ++i) tw32[i] = (float)tw64[i];
+  for (int i = 0; i < N; ++i) lam32[i] = (float)lam64[i];
+  for (size_t i = 0; i < u64.size(); ++i) u32[i] = (float)u64[i];
+
+  sq_precond *pc = new (std::nothrow) sq_precond();
+  if (!pc) return SQ_ENOMEM;
+  pc->N = N;
+  pc->rank = rank;
+  const size_t b_tw64 = tw64.size() * 8, b_lam64 = lam64.size() * 8, b_u64 = u64.size() * 8;
+  const size_t b_tw32 = tw32.size() * 4, b_lam32 = lam32.size() * 4, b_u32 = u32.size() * 4;
+  auto al = [](size_t b) { return (b + 255) & ~(size_t)255; };
+  const size_t total = al(b_tw64) + al(b_lam64) + al(b_u64) + al(b_tw32) + al(b_lam32) + al(b_u32);
+  if (cudaMalloc(&pc->d_mem, total) != cudaSuccess) {
+    delete pc;
+    return SQ_ENOMEM;
+  }
+  char *bp = static_cast<char *>(pc->d_mem);
+  char *p_tw64 = bp;
+  char *p_lam64 = p_tw64 + al(b_tw64);
+  char *p_u64 = p_lam64 + al(b_lam64);
+  char *p_tw32 = p_u64 + al(b_u64);
+  char *p_lam32 = p_tw32 + al(b_tw32);
+  char *p_u32 = p_lam32 + al(b_lam32);
+  if (cudaMemcpy(p_tw64, tw64.data(), b_tw64, cudaMemcpyHostToDevice) != cudaSuccess ||
+      cudaMemcpy(p_lam64, lam64.data(), b_lam64, cudaMemcpyHostToDevice) != cudaSuccess ||
+      cudaMemcpy(p_u64, u64.data(), b_u64, cudaMemcpyHostToDevice) != cudaSuccess ||
+      cudaMemcpy(p_tw32, tw32.data(), b_tw32, cudaMemcpyHostToDevice) != cudaSuccess ||
+      cudaMemcpy(p_lam32, lam32.data(), b_lam32, cudaMemcpyHostToDevice) != cudaSuccess ||
+      cudaMemcpy(p_u32, u32.data(), b_u32, cudaMemcpyHostToDevice) != cudaSuccess) {
+    sq_precond_destroy(pc);
+    return SQ_ECUDA;
+  }
+  SpectralDev sp;
+  std::memset(&sp, 0, sizeof(sp));
+  sp.N = N;
+  sp.rank = rank;
+  sp.nst = radix_plan(N, sp.radix);
+  sp.scale = 1.0 / (64.0 * (double)N * N * N);
+  pc->sp64 = sp;
+  pc->sp64.tw = p_tw64;
+  pc->sp64.lam = p_lam64;
+  pc->sp64.u = p_u64;
+  pc->sp32 = sp;
+  pc->sp32.tw = p_tw32;
+  pc->sp32.lam = p_lam32;
+  pc->sp32.u = p_u32;
+  *out = pc;
+  return SQ_OK;
+}
+
+void sq_precond_destroy(sq_precond *p) {
+  if (!p) return;
+  if (p->d_mem) cudaFree(p->d_mem);
+  delete p;
+}
+
+int sq_workspace_create(int N, int precision, sq_workspace **out) {
+  if (!out) return SQ_EINVAL;
+  *out = nullptr;
+  if (!valid_N(N) || (precision != SQ_FP64 && precision != SQ_FP32_REFINE)) return SQ_EINVAL;
+  sq_workspace *w = new (std::nothrow) sq_workspace();
+  if (!w) return SQ_ENOMEM;
+  w->N = N;
+  w->precision = precision;
+  const size_t n3 = (size_t)N * N * N;
+  bool ok = true;
+  if (precision == SQ_FP64)
+    ok = ok && cudaMalloc(&w->f64, sizeof(double) * 4 * n3) == cudaSuccess;
+  else
+    ok = ok && cudaMalloc(&w->f32, sizeof(float) * 5 * n3) == cudaSuccess;
+  ok = ok && cudaMalloc(&w->d_st, 2 * sizeof(Scalars)) == cudaSuccess;
+  ok = ok && cudaMalloc(&w->d_partials, sizeof(double) * kMaxQ * kMaxPartials) == cudaSuccess;
+  ok = ok && cudaMallocHost(&w->h_st, 2 * sizeof(Scalars)) == cudaSuccess;
+  ok = ok && cudaMallocHost(&w->h_poll, 2 * sizeof(int)) == cudaSuccess;
+  ok = ok && cudaEventCreateWithFlags(&w->ev[0], cudaEventDisableTiming) == cudaSuccess;
+  ok = ok && cudaEventCreateWithFlags(&w->ev[1], cudaEventDisableTiming) == cudaSuccess;
+  if (ok) ok = cudaMemset(w->d_st, 0, 2 * sizeof(Scalars)) == cudaSuccess;
+  if (!ok) {
+    sq_workspace_destroy(w);
+    return SQ_ENOMEM;
+  }
+  *out = w;
+  return SQ_OK;
+}
+
+void sq_workspace_destroy(sq_workspace *w) {
+  if (!w) return;
+  if (w->f64) cudaFree(w->f64);
+  if (w->f32) cudaFree(w->f32);
+  if (w->d_st) cudaFree(w->d_st);
+  if (w->d_partials) cudaFree(w->d_partials);
+  if (w->h_st) cudaFreeHost(w->h_st);
+  if (w->h_poll) cudaFreeHost(w->h_poll);
+  if (w->ev[0]) cudaEventDestroy(w->ev[0]);
+  if (w->ev[1]) cudaEventDestroy(w->ev[1]);
+  delete w;
+}
+
+int sq_pcg_solve(const sq_coeffs *c, const sq_precond *pc, sq_workspace *w, int dir, double tol, int max_iter,
+                 int precision, const double *x0, double *psi, sq_solve_info *info, sq_stream_t stream) {
+  if (!c || !pc || !w || !psi) return SQ_EINVAL;
+  if (dir < 0 || dir > 2 || !(tol > 0.0) || max_iter < 1) return SQ_EINVAL;
+  if (pc->N != c->N || w->N != c->N || w->precision != precision) return SQ_EINVAL;
+  cudaStream_t s = reinterpret_cast<cudaStream_t>(stream);
+  if (info) std::memset(info, 0, sizeof(*info));
+  if (precision == SQ_FP64) return solve_fp64(c, pc, w, dir, tol, max_iter, x0, psi, info, s);
+  if (precision == SQ_FP32_REFINE) return solve_fp32_refine(c, pc, w, dir, tol, max_iter, x0, psi, info, s);
+  return SQ_EINVAL;
+}
+
+int sq_homogenized_matrix(const sq_coeffs *c, const double *psi0, const double *psi1, const double *psi2,
+                          double *A_hom, double *A_energy, sq_stream_t stream) {
+  if (!c || !psi0 || !psi1 || !psi2 || !A_hom) return SQ_EINVAL;
+  cudaStream_t s = reinterpret_cast<cudaStream_t>(stream);
+  const RedBuf rb = redbuf<double>(c->d_st, c->d_partials);
+  SQ_LAUNCH(PC_AHOM, s, launch_ahom(cells_dev(c), psi0, psi1, psi2, rb, s));
+  int st = read_scalars(c->h_st, c->d_st, s);
+  if (st != SQ_OK) return st;
+  const double nn = (double)c->N * c->N * c->N;
+  const double *red = c->h_st->red;
+  for (int i = 0; i < 3; ++i)
+    for (int j = 0; j < 3; ++j) A_hom[3 * i + j] = ((i == j) ? red[9 + j] : 0.0) / nn + red[3 * i + j] / nn;
+  if (A_energy) {
+    const int idx[3][3] = {{0, 1, 2}, {1, 3, 4}, {2, 4, 5}};
+    for (int i = 0; i < 3; ++i)
+      for (int j = 0; j < 3; ++j) A_energy[3 * i + j] = red[12 + idx[i][j]] / nn;
+  }
+  return SQ_OK;
+}
+
+int sq_apply_operator(const sq_coeffs *c, const double *x, double *y, sq_stream_t stream) {
+  if (!c || !x || !y || x == y) return SQ_EINVAL;
+  cudaStream_t s = reinterpret_cast<cudaStream_t>(stream);
+  SQ_LAUNCH(PC_MATVEC, s, (launch_stencil<double, double>(cells_dev(c), ST_MATVEC, 0, x, y, redbuf<double>(c->d_st, c->d_partials),
+                                        FIN_NONE, false, s)));
+  return SQ_OK;
+}
+
+int sq_apply_operator_f32(const sq_coeffs *c, const float *x, float *y, sq_stream_t stream) {
+  if (!c || !x || !y || x == y) return SQ_EINVAL;
+  cudaStream_t s = reinterpret_cast<cudaStream_t>(stream);
+  SQ_LAUNCH(PC_MATVEC, s, (launch_stencil<float, float>(cells_dev(c), ST_MATVEC, 0, x, y, redbuf<float>(c->d_st, c->d_partials),
+                                      FIN_NONE, false, s)));
+  return SQ_OK;
+}
+
+int sq_rhs(const sq_coeffs *c, int dir, double *b, sq_stream_t stream) {
+  if (!c || !b || dir < 0 || dir > 2) return SQ_EINVAL;
+  cudaStream_t s = reinterpret_cast<cudaStream_t>(stream);
+  SQ_LAUNCH(PC_RESID, s, (launch_stencil<double, double>(cells_dev(c), ST_RHS, dir, nullptr, b, redbuf<double>(c->d_st, c->d_partials),
+                                        FIN_NONE, false, s)));
+  return SQ_OK;
+}
+
+int sq_apply_precond(const sq_precond *pc, sq_workspace *w, const double *r, double *z, sq_stream_t stream) {
+  if (!pc || !w || !r || !z || w->N != pc->N || w->precision != SQ_FP64) return SQ_EINVAL;
+  const size_t n3 = (size_t)pc->N * pc->N * pc->N;
+  return apply_precond_t<double>(pc, w, r, z, w->f64 + 3 * n3, reinterpret_cast<cudaStream_t>(stream));
+}
+
+int sq_apply_precond_f32(const sq_precond *pc, sq_workspace *w, const float *r, float *z, sq_stream_t stream) {
+  if (!pc || !w || !r || !z || w->N != pc->N || w->precision != SQ_FP32_REFINE) return SQ_EINVAL;
+  const size_t n3 = (size_t)pc->N * pc->N * pc->N;
+  return apply_precond_t<float>(pc, w, r, z, w->f32 + 3 * n3, reinterpret_cast<cudaStream_t>(stream));
+}
+
+}  // extern "C"

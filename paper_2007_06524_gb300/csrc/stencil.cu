@@ -1,0 +1,338 @@
+// Cell generation, the matrix-free stiffness operator, right-hand sides,
+// homogenized matrix and small vector kernels.
+//
+// Operator (Sec. 3.2-3.3, Eqs. 9 and 18, read as the lumped form
+// A = sum_d D_d^T diag(a_d) D_d): for node j,
+//   (A x)(j) = sum_d a_d(j) (x(j) - x(j+e_d)) + a_d(j-e_d) (x(j) - x(j-e_d)),
+// where a_d(j) is the mean of the four grid voxels around the edge j -> j+e_d
+// (the Kronecker-sum weights Ihat = diag{1/2,1,..,1,1/2} of Sec. 3.3 summed over
+// the cells sharing that edge: 1, 1/2 or 1/4 per cell). Every voxel takes the
+// value of its cell, so the eight voxels around a node -- one bit each, read
+// from the L^3 phase array -- fix all six edge coefficients of that node. A
+// 256-entry table per block maps this 8-bit pattern to the six coefficients
+// and the diagonal; no N^3 coefficient field exists.
+//
+// RHS (Eq. 8 in grid units): b_dir(j) = a_dir(j) - a_dir(j - e_dir).
+#include "common.cuh"
+
+namespace sq {
+
+// --------------------------------------------------------------- cell phases
+// SplitMix64 (Steele, Lea & Flood, OOPSLA 2014): output number i of the stream
+// seeded with `seed` is mix(seed + (i+1) * golden_gamma).
+__device__ __forceinline__ uint64_t splitmix64_output(uint64_t seed, uint64_t i) {
+  uint64_t z = seed + (i + 1ull) * 0x9E3779B97F4A7C15ull;
+  z = (z ^ (z >> 30)) * 0xBF58476D1CE4E5B9ull;
+  z = (z ^ (z >> 27)) * 0x94D049BB133111EBull;
+  return z ^ (z >> 31);
+}
+
+__global__ void k_coeff_gen(uint8_t *__restrict__ phase, int ncell, uint64_t seed, uint64_t thr) {
+  int i = blockIdx.x * blockDim.x + threadIdx.x;
+  if (i < ncell) phase[i] = ((splitmix64_output(seed, (uint64_t)i) >> 11) < thr) ? 1 : 0;
+}
+
+cudaError_t launch_coeff_gen(uint8_t *phase, int L, uint64_t seed, uint64_t thr, cudaStream_t s) {
+  int ncell = L * L * L;
+  k_coeff_gen<<<(ncell + 255) / 256, 256, 0, s>>>(phase, ncell, seed, thr);
+  return cudaGetLastError();
+}
+
+// ------------------------------------------------------ coefficient patterns
+// Bit s1*4 + s2*2 + s3 of the pattern = phase of voxel (j1-s1, j2-s2, j3-s3).
+// Entries: 0 a_1(j), 1 a_1(j-e1), 2 a_2(j), 3 a_2(j-e2), 4 a_3(j), 5 a_3(j-e3),
+// 6 diagonal (sum of the six), 7 unused.
+template <typename T>
+__device__ __forceinline__ void build_pattern_table(T (*tab)[8], double a_lo, double a_hi, int tid) {
+  const unsigned face[6] = {0x0Fu, 0xF0u, 0x33u, 0xCCu, 0x55u, 0xAAu};
+  for (int m = tid; m < 256; m += kThreads) {
+    double diag = 0.0;
+#pragma unroll
+    for (int f = 0; f < 6; ++f) {
+      int k = __popc(m & face[f]);
+      double a = (k * a_hi + (4 - k) * a_lo) * 0.25;
+      tab[m][f] = (T)a;
+      diag += a;
+    }
+    tab[m][6] = (T)diag;
+    tab[m][7] = (T)0;
+  }
+}
+
+// Four phase bits of cell row c1 at the node's (s2, s3) cell offsets.
+__device__ __forceinline__ unsigned load4(const uint8_t *__restrict__ phase, int c1, int LL, int o00, int o01,
+                                          int o10, int o11) {
+  const uint8_t *ph = phase + (size_t)c1 * LL;
+  return (ph[o00] ? 1u : 0u) | (ph[o01] ? 2u : 0u) | (ph[o10] ? 4u : 0u) | (ph[o11] ? 8u : 0u);
+}
+
+// ------------------------------------------------------------ stencil kernel
+// Block (32 x 8) threads over (j3, j2); each thread marches along j1 over
+// [z0, z0 + zc), keeping x(j1-1), x(j1), x(j1+1) in registers. The eight voxel
+// bits change only when j1 crosses a cell boundary.
+template <typename Ti, typename To, int MODE>
+__global__ void __launch_bounds__(kThreads) k_stencil(CellsDev c, int dir, const Ti *__restrict__ x,
+                                                      To *__restrict__ y, RedBuf rb, int fin, int check_done,
+                                                      int zc) {
+  if (check_done && *(volatile int *)&rb.st->done) return;
+  __shared__ Ti tab[256][8];
+  const int tid = threadIdx.x + 32 * threadIdx.y;
+  build_pattern_table<Ti>(tab, c.a_lo, c.a_hi, tid);
+  __syncthreads();
+
+  const int N = c.N, n = c.n, L = c.L;
+  const size_t NN = (size_t)N * N;
+  const int j3 = blockIdx.x * 32 + threadIdx.x;
+  const int j2 = blockIdx.y * 8 + threadIdx.y;
+  const int z0 = blockIdx.z * zc;
+  const int z1 = min(z0 + zc, N);
+  double acc0 = 0.0, acc1 = 0.0;
+  if (j3 < N && j2 < N) {
+    const int j3m = (j3 == 0) ? N - 1 : j3 - 1, j3p = (j3 == N - 1) ? 0 : j3 + 1;
+    const int j2m = (j2 == 0) ? N - 1 : j2 - 1, j2p = (j2 == N - 1) ? 0 : j2 + 1;
+    const int c3a = j3 / n, c3b = j3m / n, c2a = j2 / n, c2b = j2m / n;
+    const int o00 = c2a * L + c3a, o01 = c2a * L + c3b, o10 = c2b * L + c3a, o11 = c2b * L + c3b;
+    const int LL = L * L;
+    const size_t row = (size_t)j2 * N + j3;
+    const size_t r2p = (size_t)j2p * N + j3, r2m = (size_t)j2m * N + j3;
+    const size_t r3p = (size_t)j2 * N + j3p, r3m = (size_t)j2 * N + j3m;
+
+    int j1 = z0;
+    const int j1m0 = (j1 == 0) ? N - 1 : j1 - 1;
+    unsigned m_prev = load4(c.phase, j1m0 / n, LL, o00, o01, o10, o11);
+    unsigned m_cur = (j1 % n == 0) ? load4(c.phase, j1 / n, LL, o00, o01, o10, o11) : m_prev;
+    Ti xm = (Ti)0, x0 = (Ti)0, xp = (Ti)0;
+    if (MODE != ST_RHS) {
+      xm = x[(size_t)j1m0 * NN + row];
+      x0 = x[(size_t)j1 * NN + row];
+    }
+    for (; j1 < z1; ++j1) {
+      if (j1 > z0) {
+        m_prev = m_cur;
+        if (j1 % n == 0) m_cur = load4(c.phase, j1 / n, LL, o00, o01, o10, o11);
+      }
+      const Ti *t = tab[m_cur | (m_prev << 4)];
+      const size_t base = (size_t)j1 * NN;
+      Ti out;
+      Ti bv = (Ti)0;
+      if (MODE != ST_MATVEC) bv = t[2 * dir] - t[2 * dir + 1];
+      if (MODE != ST_RHS) {
+        const int j1p = (j1 == N - 1) ? 0 : j1 + 1;
+        xp = x[(size_t)j1p * NN + row];
+        const Ti x2p = x[base + r2p], x2m = x[base + r2m];
+        const Ti x3p = x[base + r3p], x3m = x[base + r3m];
+        Ti off = t[0] * xp;
+        off = fma(t[1], xm, off);
+        off = fma(t[2], x2p, off);
+        off = fma(t[3], x2m, off);
+        off = fma(t[4], x3p, off);
+        off = fma(t[5], x3m, off);
+        const Ti ax = fma(t[6], x0, -off);
+        if (MODE == ST_MATVEC) {
+          out = ax;
+          acc0 = fma((double)x0, (double)ax, acc0);
+        } else {
+          out = bv - ax;
+          acc0 = fma((double)out, (double)out, acc0);
+          acc1 = fma((double)bv, (double)bv, acc1);
+        }
+        xm = x0;
+        x0 = xp;
+      } else {
+        out = bv;
+        acc0 = fma((double)bv, (double)bv, acc0);
+        acc1 = acc0;
+      }
+      y[base + row] = (To)out;
+    }
+  }
+  double v[2] = {acc0, acc1}, s[2];
+  if (reduce_last_block<2>(v, rb.partials, &rb.st->ticket, s)) {
+    if (tid == 0) finalize_scalars(rb.st, fin, s, 2);
+  }
+}
+
+static int stencil_zc(int N) {
+  // about 4 K blocks of 256 threads per launch, at least 2 planes per block
+  long long tiles = (long long)((N + 31) / 32) * ((N + 7) / 8);
+  long long want = 4096;
+  int nz = (int)((want + tiles - 1) / tiles);
+  if (nz > N / 2) nz = N / 2;
+  if (nz < 1) nz = 1;
+  int zc = (N + nz - 1) / nz;
+  return zc;
+}
+
+template <typename Ti, typename To>
+cudaError_t launch_stencil(const CellsDev &c, int mode, int dir, const Ti *x, To *y, RedBuf rb, int fin,
+                           bool check_done, cudaStream_t s) {
+  const int N = c.N;
+  const int zc = stencil_zc(N);
+  dim3 grid((N + 31) / 32, (N + 7) / 8, (N + zc - 1) / zc);
+  if ((long long)grid.x * grid.y * grid.z > kMaxPartials) return cudaErrorInvalidConfiguration;
+  dim3 block(32, 8, 1);
+  switch (mode) {
+    case ST_MATVEC:
+      k_stencil<Ti, To, ST_MATVEC><<<grid, block, 0, s>>>(c, dir, x, y, rb, fin, check_done ? 1 : 0, zc);
+      break;
+    case ST_RESID:
+      k_stencil<Ti, To, ST_RESID><<<grid, block, 0, s>>>(c, dir, x, y, rb, fin, check_done ? 1 : 0, zc);
+      break;
+    default:
+      k_stencil<Ti, To, ST_RHS><<<grid, block, 0, s>>>(c, dir, x, y, rb, fin, check_done ? 1 : 0, zc);
+      break;
+  }
+  return cudaGetLastError();
+}
+
+template cudaError_t launch_stencil<double, double>(const CellsDev &, int, int, const double *, double *, RedBuf,
+                                                    int, bool, cudaStream_t);
+template cudaError_t launch_stencil<float, float>(const CellsDev &, int, int, const float *, float *, RedBuf, int,
+                                                  bool, cudaStream_t);
+template cudaError_t launch_stencil<double, float>(const CellsDev &, int, int, const double *, float *, RedBuf,
+                                                   int, bool, cudaStream_t);
+
+// --------------------------------------------------------- homogenized matrix
+// Eq. 21 on the grid: A_ij = delta_ij mean(a_j) + mean(a_j D_j psi_i) (edge
+// form, the paper's Eq. 23 after summation by parts) and the energy form
+// E_ij = mean(sum_d a_d (delta_id + D_d psi_i)(delta_jd + D_d psi_j)).
+// Reduced quantities: 0..8 M[i][j] = sum a_j D_j psi_i, 9..11 sum a_j,
+// 12..17 energy sums for (i,j) in (00,01,02,11,12,22).
+__global__ void __launch_bounds__(kThreads) k_ahom(CellsDev c, const double *__restrict__ p0,
+                                                   const double *__restrict__ p1, const double *__restrict__ p2,
+                                                   RedBuf rb, int zc) {
+  __shared__ double tab[256][8];
+  const int tid = threadIdx.x + 32 * threadIdx.y;
+  build_pattern_table<double>(tab, c.a_lo, c.a_hi, tid);
+  __syncthreads();
+  const int N = c.N, n = c.n, L = c.L;
+  const size_t NN = (size_t)N * N;
+  const int j3 = blockIdx.x * 32 + threadIdx.x;
+  const int j2 = blockIdx.y * 8 + threadIdx.y;
+  const int z0 = blockIdx.z * zc;
+  const int z1 = min(z0 + zc, N);
+  double acc[18];
+#pragma unroll
+  for (int q = 0; q < 18; ++q) acc[q] = 0.0;
+  if (j3 < N && j2 < N) {
+    const int j3m = (j3 == 0) ? N - 1 : j3 - 1, j3p = (j3 == N - 1) ? 0 : j3 + 1;
+    const int j2m = (j2 == 0) ? N - 1 : j2 - 1, j2p = (j2 == N - 1) ? 0 : j2 + 1;
+    const int c3a = j3 / n, c3b = j3m / n, c2a = j2 / n, c2b = j2m / n;
+    const int LL = L * L;
+    const int o00 = c2a * L + c3a, o01 = c2a * L + c3b, o10 = c2b * L + c3a, o11 = c2b * L + c3b;
+    const double *ps[3] = {p0, p1, p2};
+    for (int j1 = z0; j1 < z1; ++j1) {
+      const int j1m = (j1 == 0) ? N - 1 : j1 - 1, j1p = (j1 == N - 1) ? 0 : j1 + 1;
+      const unsigned m = load4(c.phase, j1 / n, LL, o00, o01, o10, o11) |
+                         (load4(c.phase, j1m / n, LL, o00, o01, o10, o11) << 4);
+      const double a[3] = {tab[m][0], tab[m][2], tab[m][4]};
+      const size_t o = (size_t)j1 * NN + (size_t)j2 * N + j3;
+      const size_t on[3] = {(size_t)j1p * NN + (size_t)j2 * N + j3, (size_t)j1 * NN + (size_t)j2p * N + j3,
+                            (size_t)j1 * NN + (size_t)j2 * N + j3p};
+      double g[3][3];  // g[i][d] = D_d psi_i
+#pragma unroll
+      for (int i = 0; i < 3; ++i) {
+        const double v0 = ps[i][o];
+#pragma unroll
+        for (int d = 0; d < 3; ++d) g[i][d] = ps[i][on[d]] - v0;
+      }
+#pragma unroll
+      for (int i = 0; i < 3; ++i)
+#pragma unroll
+        for (int d = 0; d < 3; ++d) acc[3 * i + d] = fma(a[d], g[i][d], acc[3 * i + d]);
+#pragma unroll
+      for (int d = 0; d < 3; ++d) acc[9 + d] += a[d];
+      int q = 12;
+#pragma unroll
+      for (int i = 0; i < 3; ++i)
+#pragma unroll
+        for (int jj = i; jj < 3; ++jj) {
+          double e = 0.0;
+#pragma unroll
+          for (int d = 0; d < 3; ++d)
+            e += a[d] * ((i == d ? 1.0 : 0.0) + g[i][d]) * ((jj == d ? 1.0 : 0.0) + g[jj][d]);
+          acc[q++] += e;
+        }
+    }
+  }
+  double s[18];
+  if (reduce_last_block<18>(acc, rb.partials, &rb.st->ticket, s)) {
+    if (tid == 0) finalize_scalars(rb.st, FIN_NONE, s, 18);
+  }
+}
+
+cudaError_t launch_ahom(const CellsDev &c, const double *p0, const double *p1, const double *p2, RedBuf rb,
+                        cudaStream_t s) {
+  const int N = c.N;
+  const int zc = stencil_zc(N);
+  dim3 grid((N + 31) / 32, (N + 7) / 8, (N + zc - 1) / zc);
+  if ((long long)grid.x * grid.y * grid.z > kMaxPartials) return cudaErrorInvalidConfiguration;
+  k_ahom<<<grid, dim3(32, 8, 1), 0, s>>>(c, p0, p1, p2, rb, zc);
+  return cudaGetLastError();
+}
+
+// ------------------------------------------------------------- vector kernels
+template <typename T>
+__global__ void __launch_bounds__(kThreads) k_x_final_sum(T *__restrict__ x, const T *__restrict__ p, RedBuf rb,
+                                                          long long n) {
+  const int pend = rb.st->x_pending;
+  const T alpha = (T)rb.st->alpha;
+  double acc = 0.0;
+  for (long long i = blockIdx.x * (long long)kThreads + threadIdx.x; i < n; i += (long long)gridDim.x * kThreads) {
+    T v = x[i];
+    if (pend) {
+      v = fma(alpha, p[i], v);
+      x[i] = v;
+    }
+    acc += (double)v;
+  }
+  double vv[1] = {acc}, s[1];
+  if (reduce_last_block<1>(vv, rb.partials, &rb.st->ticket, s)) {
+    if (threadIdx.x == 0) {
+      rb.st->red[0] = s[0];
+      rb.st->mean = s[0] / (double)n;
+      rb.st->x_pending = 0;
+    }
+  }
+}
+
+template <typename T>
+__global__ void __launch_bounds__(kThreads) k_sub_mean(T *__restrict__ x, const Scalars *st, long long n) {
+  const T m = (T)st->mean;
+  for (long long i = blockIdx.x * (long long)kThreads + threadIdx.x; i < n; i += (long long)gridDim.x * kThreads)
+    x[i] -= m;
+}
+
+static int vec_grid(long long n) {
+  long long g = (n + kThreads - 1) / kThreads;
+  const long long cap = 152 * 16;
+  return (int)(g < cap ? g : cap);
+}
+
+template <typename T>
+cudaError_t launch_x_final_sum(T *x, const T *p, RedBuf rb, long long n, cudaStream_t s) {
+  k_x_final_sum<T><<<vec_grid(n), kThreads, 0, s>>>(x, p, rb, n);
+  return cudaGetLastError();
+}
+template <typename T>
+cudaError_t launch_sub_mean(T *x, RedBuf rb, long long n, cudaStream_t s) {
+  k_sub_mean<T><<<vec_grid(n), kThreads, 0, s>>>(x, rb.st, n);
+  return cudaGetLastError();
+}
+template cudaError_t launch_x_final_sum<double>(double *, const double *, RedBuf, long long, cudaStream_t);
+template cudaError_t launch_x_final_sum<float>(float *, const float *, RedBuf, long long, cudaStream_t);
+template cudaError_t launch_sub_mean<double>(double *, RedBuf, long long, cudaStream_t);
+template cudaError_t launch_sub_mean<float>(float *, RedBuf, long long, cudaStream_t);
+
+__global__ void __launch_bounds__(kThreads) k_add_f32_to_f64(double *__restrict__ x, const float *__restrict__ d,
+                                                             long long n) {
+  for (long long i = blockIdx.x * (long long)kThreads + threadIdx.x; i < n; i += (long long)gridDim.x * kThreads)
+    x[i] += (double)d[i];
+}
+
+cudaError_t launch_add_f32_to_f64(double *x, const float *d, long long n, cudaStream_t s) {
+  k_add_f32_to_f64<<<vec_grid(n), kThreads, 0, s>>>(x, d, n);
+  return cudaGetLastError();
+}
+
+}  // namespace sq

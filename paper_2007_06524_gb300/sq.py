@@ -1,0 +1,252 @@
+"""ctypes binding of libsq with the C ABI's names (include/sq.h).
+
+Device buffers are torch CUDA tensors (contiguous, float64 unless the call is
+an *_f32 one); streams default to torch's current stream. Handles are small
+owner objects whose destructor calls the matching sq_*_destroy.
+"""
+from __future__ import annotations
+
+import ctypes as C
+import os
+
+import numpy as np
+
+SQ_OK, SQ_EINVAL, SQ_ENOMEM, SQ_ECUDA, SQ_ENOCONV, SQ_ETIMEOUT, SQ_EBADGUESS = range(7)
+SQ_FP64, SQ_FP32_REFINE = 0, 1
+
+_HERE = os.path.dirname(os.path.abspath(__file__))
+_LIB = None
+
+
+def lib_path() -> str:
+    return os.path.join(_HERE, "libsq.so")
+
+
+class SqError(RuntimeError):
+    def __init__(self, status: int, where: str):
+        super().__init__(f"{where}: {sq_strerror(status)} (status {status})")
+        self.status = status
+
+
+class SolveInfo(C.Structure):
+    _fields_ = [("iters", C.c_int), ("outer_steps", C.c_int), ("status", C.c_int), ("used_guess", C.c_int),
+                ("relres", C.c_double), ("relres_true", C.c_double)]
+
+
+def load_library():
+    """Loads libsq.so (built by paper_2007_06524_gb300.build). Raises if absent."""
+    global _LIB
+    if _LIB is not None:
+        return _LIB
+    path = lib_path()
+    if not os.path.exists(path):
+        raise RuntimeError(f"libsq.so not found at {path}: run paper_2007_06524_gb300.build.build()")
+    lib = C.CDLL(path)
+    vp, i, d, u64, p = C.c_void_p, C.c_int, C.c_double, C.c_uint64, C.POINTER
+    sig = {
+        "sq_build_coeffs": (i, [i, i, u64, d, d, d, vp, p(vp)]),
+        "sq_coeffs_from_host": (i, [i, i, vp, d, d, vp, p(vp)]),
+        "sq_coeffs_cells": (i, [vp, vp, p(C.c_int64)]),
+        "sq_coeffs_regenerate": (i, [vp, u64, d, vp]),
+        "sq_coeffs_upload": (i, [vp, vp, vp]),
+        "sq_profile_enable": (i, [i]),
+        "sq_profile_read": (i, [vp, vp, i]),
+        "sq_profile_class_name": (C.c_char_p, [i]),
+        "sq_coeffs_shape": (i, [vp, p(i), p(i), p(i)]),
+        "sq_coeffs_destroy": (None, [vp]),
+        "sq_precond_setup": (i, [i, i, p(vp)]),
+        "sq_precond_destroy": (None, [vp]),
+        "sq_workspace_create": (i, [i, i, p(vp)]),
+        "sq_workspace_destroy": (None, [vp]),
+        "sq_pcg_solve": (i, [vp, vp, vp, i, d, i, i, vp, vp, p(SolveInfo), vp]),
+        "sq_homogenized_matrix": (i, [vp, vp, vp, vp, vp, vp, vp]),
+        "sq_apply_operator": (i, [vp, vp, vp, vp]),
+        "sq_apply_operator_f32": (i, [vp, vp, vp, vp]),
+        "sq_rhs": (i, [vp, i, vp, vp]),
+        "sq_apply_precond": (i, [vp, vp, vp, vp, vp]),
+        "sq_apply_precond_f32": (i, [vp, vp, vp, vp, vp]),
+        "sq_strerror": (C.c_char_p, [i]),
+    }
+    for name, (res, args) in sig.items():
+        f = getattr(lib, name)
+        f.restype = res
+        f.argtypes = args
+    _LIB = lib
+    return lib
+
+
+def sq_strerror(status: int) -> str:
+    return load_library().sq_strerror(int(status)).decode()
+
+
+def _check(st: int, where: str, allow=()):
+    if st != SQ_OK and st not in allow:
+        raise SqError(st, where)
+    return st
+
+
+def _stream(stream):
+    if stream is None:
+        import torch
+        return C.c_void_p(torch.cuda.current_stream().cuda_stream)
+    if isinstance(stream, int):
+        return C.c_void_p(stream)
+    return C.c_void_p(stream.cuda_stream)
+
+
+def _ptr(t, dtype_name="float64"):
+    if t is None:
+        return None
+    if not t.is_cuda or not t.is_contiguous() or str(t.dtype) != "torch." + dtype_name:
+        raise ValueError(f"expected a contiguous CUDA {dtype_name} tensor")
+    return C.c_void_p(t.data_ptr())
+
+
+class _Handle:
+    _destroy = None
+
+    def __init__(self, ptr):
+        self.ptr = ptr
+
+    def close(self):
+        if self.ptr:
+            getattr(load_library(), self._destroy)(self.ptr)
+            self.ptr = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    @property
+    def _as_parameter_(self):
+        return self.ptr
+
+
+class Coeffs(_Handle):
+    _destroy = "sq_coeffs_destroy"
+
+
+class Precond(_Handle):
+    _destroy = "sq_precond_destroy"
+
+
+class Workspace(_Handle):
+    _destroy = "sq_workspace_destroy"
+
+
+def sq_build_coeffs(L, n, seed, p_hi, a_lo, a_hi, stream=None) -> Coeffs:
+    out = C.c_void_p()
+    _check(load_library().sq_build_coeffs(int(L), int(n), int(seed) & (2**64 - 1), float(p_hi), float(a_lo),
+                                          float(a_hi), _stream(stream), C.byref(out)), "sq_build_coeffs")
+    return Coeffs(out)
+
+
+def sq_coeffs_from_host(L, n, host_phase, a_lo, a_hi, stream=None) -> Coeffs:
+    arr = np.ascontiguousarray(host_phase, dtype=np.uint8)
+    if arr.size != L ** 3:
+        raise ValueError("host_phase must hold L^3 bytes")
+    out = C.c_void_p()
+    _check(load_library().sq_coeffs_from_host(int(L), int(n), arr.ctypes.data_as(C.c_void_p), float(a_lo),
+                                              float(a_hi), _stream(stream), C.byref(out)), "sq_coeffs_from_host")
+    return Coeffs(out)
+
+
+def sq_coeffs_regenerate(c: Coeffs, seed, p_hi, stream=None):
+    _check(load_library().sq_coeffs_regenerate(c, int(seed) & (2**64 - 1), float(p_hi), _stream(stream)),
+           "sq_coeffs_regenerate")
+
+
+def sq_coeffs_upload(c: Coeffs, host_phase, stream=None):
+    """host_phase: a PINNED torch uint8 CPU tensor of L^3 values in {0, 1}."""
+    if host_phase.is_cuda or not host_phase.is_pinned() or str(host_phase.dtype) != "torch.uint8":
+        raise ValueError("expected a pinned uint8 CPU tensor")
+    _check(load_library().sq_coeffs_upload(c, C.c_void_p(host_phase.data_ptr()), _stream(stream)),
+           "sq_coeffs_upload")
+
+
+def sq_profile_enable(enable: bool):
+    _check(load_library().sq_profile_enable(1 if enable else 0), "sq_profile_enable")
+
+
+def sq_profile_read() -> dict:
+    """{class name: (total ms, launches)} of the launches recorded since enable."""
+    lib = load_library()
+    ms = (C.c_double * 64)()
+    cnt = (C.c_int64 * 64)()
+    k = lib.sq_profile_read(ms, cnt, 64)
+    if k < 0:
+        raise SqError(-k, "sq_profile_read")
+    return {lib.sq_profile_class_name(i).decode(): (ms[i], cnt[i]) for i in range(k)}
+
+
+def sq_profile_class_name(k: int) -> str:
+    return load_library().sq_profile_class_name(int(k)).decode()
+
+
+def sq_coeffs_shape(c: Coeffs):
+    L, n, N = C.c_int(), C.c_int(), C.c_int()
+    _check(load_library().sq_coeffs_shape(c, C.byref(L), C.byref(n), C.byref(N)), "sq_coeffs_shape")
+    return L.value, n.value, N.value
+
+
+def sq_coeffs_cells(c: Coeffs):
+    L, _, _ = sq_coeffs_shape(c)
+    ph = np.empty(L ** 3, dtype=np.uint8)
+    nhi = C.c_int64()
+    _check(load_library().sq_coeffs_cells(c, ph.ctypes.data_as(C.c_void_p), C.byref(nhi)), "sq_coeffs_cells")
+    return ph.reshape(L, L, L), nhi.value
+
+
+def sq_precond_setup(N, rank) -> Precond:
+    out = C.c_void_p()
+    _check(load_library().sq_precond_setup(int(N), int(rank), C.byref(out)), "sq_precond_setup")
+    return Precond(out)
+
+
+def sq_workspace_create(N, precision) -> Workspace:
+    out = C.c_void_p()
+    _check(load_library().sq_workspace_create(int(N), int(precision), C.byref(out)), "sq_workspace_create")
+    return Workspace(out)
+
+
+def sq_pcg_solve(c, pc, w, dir, tol, max_iter, precision, x0, psi, stream=None) -> dict:
+    """Solves into psi (float64 CUDA tensor, N^3); returns the solve info.
+    SQ_ENOCONV is reported in info['status'], other errors raise."""
+    info = SolveInfo()
+    st = load_library().sq_pcg_solve(c, pc, w, int(dir), float(tol), int(max_iter), int(precision), _ptr(x0),
+                                     _ptr(psi), C.byref(info), _stream(stream))
+    _check(st, "sq_pcg_solve", allow=(SQ_ENOCONV,))
+    return {k: getattr(info, k) for k, _ in SolveInfo._fields_}
+
+
+def sq_homogenized_matrix(c, psi0, psi1, psi2, stream=None):
+    A = np.zeros(9)
+    E = np.zeros(9)
+    _check(load_library().sq_homogenized_matrix(c, _ptr(psi0), _ptr(psi1), _ptr(psi2),
+                                                A.ctypes.data_as(C.c_void_p), E.ctypes.data_as(C.c_void_p),
+                                                _stream(stream)), "sq_homogenized_matrix")
+    return A.reshape(3, 3), E.reshape(3, 3)
+
+
+def sq_apply_operator(c, x, y, stream=None):
+    _check(load_library().sq_apply_operator(c, _ptr(x), _ptr(y), _stream(stream)), "sq_apply_operator")
+
+
+def sq_apply_operator_f32(c, x, y, stream=None):
+    _check(load_library().sq_apply_operator_f32(c, _ptr(x, "float32"), _ptr(y, "float32"), _stream(stream)),
+           "sq_apply_operator_f32")
+
+
+def sq_rhs(c, dir, b, stream=None):
+    _check(load_library().sq_rhs(c, int(dir), _ptr(b), _stream(stream)), "sq_rhs")
+
+
+def sq_apply_precond(pc, w, r, z, stream=None):
+    _check(load_library().sq_apply_precond(pc, w, _ptr(r), _ptr(z), _stream(stream)), "sq_apply_precond")
+
+
+def sq_apply_precond_f32(pc, w, r, z, stream=None):
+    _check(load_library().sq_apply_precond_f32(pc, w, _ptr(r, "float32"), _ptr(z, "float32"), _stream(stream)),
+           "sq_apply_precond_f32")

@@ -1,0 +1,295 @@
+"""GPU parity: libsq (through its C ABI) against the CPU oracle.
+
+Tolerances: bit-exact for the cell phases; FP64 operator / RHS / preconditioner
+within a few ulps of the field scale (1e-13 relative); FP64 solves run to
+rel. residual 1e-12 so the solution matches the oracle's tight solve within
+1e-9 (rel. L2) and A_hom within 1e-10; FP32 kernels within 1e-5 relative;
+FP32 + FP64 refinement to 1e-10 within 1e-6 of the oracle.
+"""
+import numpy as np
+import pytest
+
+from oracle import assembly, homogenized, pcg, precond, problem, rng
+from tests import inputs
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module")
+def sq():
+    torch = pytest.importorskip("torch")
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    import __graft_entry__
+
+    __graft_entry__.build()
+    import paper_2007_06524_gb300 as pkg
+
+    return pkg
+
+
+def _dev(a, dtype="float64"):
+    import torch
+
+    return torch.from_numpy(np.ascontiguousarray(a)).to(device="cuda", dtype=getattr(torch, dtype))
+
+
+def _host(t):
+    import torch
+
+    torch.cuda.synchronize()
+    return t.cpu().numpy()
+
+
+def _relmax(a, b):
+    return float(np.abs(a - b).max() / max(np.abs(b).max(), 1e-300))
+
+
+# ------------------------------------------------------------------ cells
+@pytest.mark.parametrize("L,n,seed,p", [(4, 4, 0, 0.5), (6, 2, 3, 0.5), (6, 2, 11, 0.3), (32, 8, 0, 0.5),
+                                        (32, 8, 7, 0.5), (64, 8, 1, 0.5), (4, 2, 2**63 + 9, 0.9)])
+def test_cell_phases_bit_exact(sq, L, n, seed, p):
+    c = sq.sq_build_coeffs(L, n, seed, p, 1.0, 10.0)
+    ph, nhi = sq.sq_coeffs_cells(c)
+    ref = rng.cell_phases(L, seed, p) if L <= 6 else rng.cell_phases_vec(L, seed, p)
+    assert np.array_equal(ph, ref)
+    assert nhi == int(ref.sum())
+
+
+def test_cells_from_host_roundtrip(sq):
+    ph = rng.cell_phases_vec(8, 5)
+    c = sq.sq_coeffs_from_host(8, 4, ph * 7, 1.0, 100.0)  # nonzero = high
+    out, nhi = sq.sq_coeffs_cells(c)
+    assert np.array_equal(out, ph) and nhi == int(ph.sum())
+
+
+# --------------------------------------------------------- operator, RHS
+GRIDS = [(4, 4, 0), (3, 4, 1), (4, 8, 2), (12, 4, 3), (6, 8, 4), (24, 4, 5), (2, 6, 6)]
+
+
+@pytest.mark.parametrize("L,n,seed", GRIDS)
+def test_rhs_and_operator_fp64(sq, L, n, seed):
+    re = problem.realization(L, n, seed, 1.0, 100.0)
+    c = sq.sq_build_coeffs(L, n, seed, 0.5, 1.0, 100.0)
+    N = L * n
+    import torch
+
+    b = torch.empty(N ** 3, dtype=torch.float64, device="cuda")
+    for i in range(3):
+        sq.sq_rhs(c, i, b)
+        assert _relmax(_host(b), re.b[i]) <= 1e-15
+    psi = inputs.random_field(N, seed + 100)
+    y = torch.empty(N ** 3, dtype=torch.float64, device="cuda")
+    sq.sq_apply_operator(c, _dev(psi.ravel()), y)
+    assert _relmax(_host(y), re.A @ psi.ravel()) <= 1e-13
+
+
+@pytest.mark.parametrize("L,n,seed", GRIDS[:4])
+def test_operator_fp32(sq, L, n, seed):
+    re = problem.realization(L, n, seed, 1.0, 100.0)
+    c = sq.sq_build_coeffs(L, n, seed, 0.5, 1.0, 100.0)
+    N = L * n
+    import torch
+
+    psi = inputs.random_field(N, seed + 7, np.float32)
+    y = torch.empty(N ** 3, dtype=torch.float32, device="cuda")
+    sq.sq_apply_operator_f32(c, _dev(psi.ravel(), "float32"), y)
+    assert _relmax(_host(y).astype(np.float64), re.A @ psi.ravel().astype(np.float64)) <= 1e-5
+
+
+# ---------------------------------------------------------- preconditioner
+@pytest.mark.parametrize("N", [8, 12, 16, 24, 32, 48, 64, 96, 128])
+@pytest.mark.parametrize("rank", [0, 6, 16])
+def test_precond_fp64(sq, N, rank):
+    import torch
+
+    pc = sq.sq_precond_setup(N, rank)
+    w = sq.sq_workspace_create(N, sq.SQ_FP64)
+    r = inputs.random_field(N, N + rank)
+    z = torch.empty(N ** 3, dtype=torch.float64, device="cuda")
+    sq.sq_apply_precond(pc, w, _dev(r.ravel()), z)
+    ref = precond.apply_precond(precond.core_tensor(N, rank), r)
+    assert _relmax(_host(z).reshape(N, N, N), ref) <= 1e-12
+
+
+@pytest.mark.parametrize("N", [16, 48, 96, 256])
+@pytest.mark.parametrize("rank", [0, 8])
+def test_precond_fp32(sq, N, rank):
+    import torch
+
+    pc = sq.sq_precond_setup(N, rank)
+    w = sq.sq_workspace_create(N, sq.SQ_FP32_REFINE)
+    r = inputs.random_field(N, 3 * N + rank, np.float32)
+    z = torch.empty(N ** 3, dtype=torch.float32, device="cuda")
+    sq.sq_apply_precond_f32(pc, w, _dev(r.ravel(), "float32"), z)
+    ref = precond.apply_precond(precond.core_tensor(N, rank), r.astype(np.float64))
+    assert _relmax(_host(z).reshape(N, N, N).astype(np.float64), ref) <= 2e-5
+
+
+def test_precond_fp64_full_size(sq):
+    import torch
+
+    N, rank = 256, 8
+    pc = sq.sq_precond_setup(N, rank)
+    w = sq.sq_workspace_create(N, sq.SQ_FP64)
+    r = inputs.random_field(N, 42)
+    z = torch.empty(N ** 3, dtype=torch.float64, device="cuda")
+    sq.sq_apply_precond(pc, w, _dev(r.ravel()), z)
+    ref = precond.apply_precond(precond.core_tensor(N, rank), r)
+    assert _relmax(_host(z).reshape(N, N, N), ref) <= 1e-12
+
+
+# ------------------------------------------------------------------ solves
+def _solve(sq, c, N, dir, rank, tol, precision=0, max_iter=2000, x0=None):
+    import torch
+
+    pc = sq.sq_precond_setup(N, rank)
+    w = sq.sq_workspace_create(N, precision)
+    psi = torch.empty(N ** 3, dtype=torch.float64, device="cuda")
+    info = sq.sq_pcg_solve(c, pc, w, dir, tol, max_iter, precision, x0, psi)
+    return psi, info
+
+
+@pytest.mark.parametrize("rank", [0, 6])
+def test_solve_plain_n16(sq, rank):
+    # L=4, n=4, Bernoulli(1/2) on {1,10}, seed 0, e_1
+    re = problem.realization(4, 4, 0, 1.0, 10.0)
+    ref, it_tight, _ = pcg.tight_solve(re.A, re.b[0], re.N)
+    c = sq.sq_build_coeffs(4, 4, 0, 0.5, 1.0, 10.0)
+    psi, info = _solve(sq, c, re.N, 0, rank, 1e-12)
+    x = _host(psi)
+    assert info["status"] == sq.SQ_OK and info["relres_true"] <= 1e-12
+    assert np.linalg.norm(x - ref) / np.linalg.norm(ref) <= 1e-9
+    assert abs(x.mean()) < 1e-14
+    # iteration count of the same PCG on the oracle at tol 1e-10
+    _, it_o, _ = pcg.pcg(re.A, re.b[0], pcg.fft_preconditioner(re.N, rank), tol=1e-10)
+    psi2, info2 = _solve(sq, c, re.N, 0, rank, 1e-10)
+    assert abs(info2["iters"] - it_o) <= 1
+    Ah, _ = sq.sq_homogenized_matrix(c, psi, psi, psi)
+    Ao = homogenized.ahom_edge(re.a_edges, [ref.reshape(re.N, re.N, re.N), None, None])
+    assert abs(Ah[0, 0] - Ao[0, 0]) <= 1e-10 * abs(Ao[0, 0])
+
+
+@pytest.mark.parametrize("L,n,seed,rank", [(4, 4, 1, 8), (12, 4, 2, 0), (6, 8, 3, 4)])
+def test_solve_three_dirs_ahom(sq, L, n, seed, rank):
+    re = problem.realization(L, n, seed, 1.0, 100.0)
+    c = sq.sq_build_coeffs(L, n, seed, 0.5, 1.0, 100.0)
+    N = re.N
+    psis, refs = [], []
+    for i in range(3):
+        ref = pcg.tight_solve(re.A, re.b[i], N)[0]
+        psi, info = _solve(sq, c, N, i, rank, 1e-12)
+        assert info["status"] == sq.SQ_OK
+        x = _host(psi)
+        assert np.linalg.norm(x - ref) / np.linalg.norm(ref) <= 1e-9
+        psis.append(psi)
+        refs.append(ref.reshape(N, N, N))
+    Ah, Ae = sq.sq_homogenized_matrix(c, *psis)
+    Ao = homogenized.ahom_edge(re.a_edges, refs)
+    Aeo = homogenized.ahom_energy(re.a_edges, refs)
+    assert np.abs(Ah - Ao).max() <= 1e-10 * np.abs(Ao).max()
+    assert np.abs(Ae - Aeo).max() <= 1e-10 * np.abs(Ao).max()
+    assert np.abs(Ah - Ah.T).max() <= 1e-10 * np.abs(Ah).max()
+
+
+def test_fp32_refinement(sq):
+    re = problem.realization(4, 8, 5, 1.0, 100.0)
+    c = sq.sq_build_coeffs(4, 8, 5, 0.5, 1.0, 100.0)
+    ref = pcg.tight_solve(re.A, re.b[1], re.N)[0]
+    psi, info = _solve(sq, c, re.N, 1, 0, 1e-10, precision=sq.SQ_FP32_REFINE)
+    assert info["status"] == sq.SQ_OK and info["relres_true"] <= 1e-10
+    assert info["outer_steps"] >= 2
+    x = _host(psi)
+    assert np.linalg.norm(x - ref) / np.linalg.norm(ref) <= 1e-6
+    assert abs(x.mean()) <= 1e-12 * np.abs(x).max()
+
+
+def test_warm_start_and_enoconv(sq):
+    re = problem.realization(4, 4, 3, 1.0, 10.0)
+    c = sq.sq_build_coeffs(4, 4, 3, 0.5, 1.0, 10.0)
+    ref = pcg.tight_solve(re.A, re.b[2], re.N)[0]
+    psi, info = _solve(sq, c, re.N, 2, 0, 1e-8, max_iter=2)
+    assert info["status"] == sq.SQ_ENOCONV and info["iters"] == 2
+    x0 = _dev(ref + 1e-6 * inputs.random_field(re.N, 1).ravel())
+    psi, info_w = _solve(sq, c, re.N, 2, 0, 1e-8, x0=x0)
+    _, info_0 = _solve(sq, c, re.N, 2, 0, 1e-8)
+    assert info_w["used_guess"] == 1 and info_w["iters"] < info_0["iters"]
+    assert np.linalg.norm(_host(psi) - ref) / np.linalg.norm(ref) <= 1e-7
+
+
+def test_degenerate_constant_coefficient(sq):
+    c = sq.sq_build_coeffs(4, 4, 0, 0.5, 3.0, 3.0)   # a_lo == a_hi -> b = 0
+    psi, info = _solve(sq, c, 16, 0, 0, 1e-8)
+    assert info["status"] == sq.SQ_OK and info["iters"] == 0
+    assert np.abs(_host(psi)).max() == 0.0
+    Ah, _ = sq.sq_homogenized_matrix(c, psi, psi, psi)
+    assert np.allclose(Ah, 3.0 * np.eye(3), atol=1e-14)
+
+
+def test_invalid_arguments(sq):
+    with pytest.raises(sq.SqError) as e:
+        sq.sq_build_coeffs(5, 2, 0, 0.5, 1.0, 10.0)      # N = 10 not 2^a 3^b
+    assert e.value.status == sq.SQ_EINVAL
+    with pytest.raises(sq.SqError):
+        sq.sq_precond_setup(16, 1)
+    with pytest.raises(sq.SqError):
+        sq.sq_workspace_create(1024, 0)
+    c = sq.sq_build_coeffs(4, 4, 0, 0.5, 1.0, 10.0)
+    pc = sq.sq_precond_setup(32, 0)
+    w = sq.sq_workspace_create(16, 0)
+    import torch
+
+    psi = torch.zeros(16 ** 3, dtype=torch.float64, device="cuda")
+    with pytest.raises(sq.SqError):
+        sq.sq_pcg_solve(c, pc, w, 0, 1e-8, 10, 0, None, psi)
+    with pytest.raises(sq.SqError):
+        sq.sq_pcg_solve(c, sq.sq_precond_setup(16, 0), w, 0, 1e-8, 10, sq.SQ_FP32_REFINE, None, psi)
+
+
+# --------------------------------------- full size (L=32, n=8, N=256), sampled
+def test_full_size_n256_sampled(sq):
+    import torch
+
+    L, n, seed = 32, 8, 0
+    N = L * n
+    cellval = rng.cell_values(rng.cell_phases_vec(L, seed), 1.0, 100.0)
+    c = sq.sq_build_coeffs(L, n, seed, 0.5, 1.0, 100.0)
+    nodes = inputs.sample_nodes(N, 300, 1)
+    # operator on a random field, sampled
+    psi_h = inputs.random_field(N, 9)
+    y = torch.empty(N ** 3, dtype=torch.float64, device="cuda")
+    sq.sq_apply_operator(c, _dev(psi_h.ravel()), y)
+    yh = _host(y).reshape(N, N, N)
+    for j in nodes:
+        ref = assembly.apply_at(cellval, n, lambda k: psi_h[k], j)
+        assert abs(yh[j] - ref) <= 1e-13 * (abs(ref) + 100.0)
+    # RHS, sampled
+    b = torch.empty(N ** 3, dtype=torch.float64, device="cuda")
+    sq.sq_rhs(c, 1, b)
+    bh = _host(b).reshape(N, N, N)
+    for j in nodes:
+        assert bh[j] == assembly.rhs_at(cellval, n, 1, j)
+    # the timed solve: FP64 PCG, rank-8 preconditioner, tol 1e-8, all three directions
+    psis = []
+    for i in range(3):
+        psi, info = _solve(sq, c, N, i, 8, 1e-8)
+        assert info["status"] == sq.SQ_OK and info["relres_true"] <= 1e-8
+        assert 10 <= info["iters"] <= 200
+        psis.append(psi)
+    Ah, Ae = sq.sq_homogenized_matrix(c, *psis)
+    vals = cellval.ravel()
+    hm, am = 1.0 / np.mean(1.0 / vals), vals.mean()
+    for i in range(3):
+        assert hm <= Ah[i, i] <= am
+    assert np.abs(Ah - Ah.T).max() <= 1e-6 * Ah[0, 0]
+    assert np.abs(Ah - Ae).max() <= 1e-6 * Ah[0, 0]
+    # the residual of the returned psi_1 checked at sampled nodes by the oracle
+    x = _host(psis[0]).reshape(N, N, N)
+    for j in nodes[:50]:
+        rj = assembly.rhs_at(cellval, n, 0, j) - assembly.apply_at(cellval, n, lambda k: x[k], j)
+        assert abs(rj) <= 1e-3  # pointwise residual of a 1e-8 relative solve (||b|| ~ 1e4)
+    # FP32 + FP64 refinement on the same system agrees with the FP64 solve
+    psi_r, info_r = _solve(sq, c, N, 0, 0, 1e-8, precision=sq.SQ_FP32_REFINE)
+    assert info_r["status"] == sq.SQ_OK
+    xr = _host(psi_r)
+    assert np.linalg.norm(xr - x.ravel()) / np.linalg.norm(x) <= 1e-5

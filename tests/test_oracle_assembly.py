@@ -89,3 +89,18 @@ def test_rhs_properties():
         assert np.allclose(b.reshape(a.shape[1:]), a[i] - np.roll(a[i], 1, axis=i), atol=0)
     ac = assembly.edge_coefficients(np.full((2, 2, 2), 7.0), 3)
     assert np.abs(assembly.rhs(ac, 0)).max() == 0.0
+
+
+def test_point_evaluators_match_full_arrays():
+    cv = _cells(4, 3, 1.0, 100.0)
+    n = 3
+    a = assembly.edge_coefficients(cv, n)
+    psi = np.random.default_rng(5).standard_normal(a.shape[1:])
+    Ap = assembly.apply_stencil(a, psi)
+    rng_ = np.random.default_rng(6)
+    for _ in range(40):
+        j = tuple(int(v) for v in rng_.integers(0, 12, 3))
+        assert abs(assembly.apply_at(cv, n, lambda k: psi[k], j) - Ap[j]) < 1e-12
+        for i in range(3):
+            assert abs(assembly.rhs_at(cv, n, i, j) - assembly.rhs(a, i).reshape(a.shape[1:])[j]) < 1e-14
+            assert assembly.edge_coefficient_at(cv, n, i, j) == a[i][j]
