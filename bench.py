@@ -241,15 +241,16 @@ def run_native(args):
 
     # --- end to end through the C ABI with pinned host inputs
     rng = np.random.default_rng(12345 + rank)
-    host = [torch.from_numpy(rng.integers(0, 2, L ** 3, dtype=np.uint8)).pin_memory() for _ in range(args.steps)]
-    torch.cuda.synchronize()
-    t0 = time.perf_counter()
-    for k in range(args.steps):
-        step(None, upload=host[k])
-    torch.cuda.synchronize()
-    t_e2e = time.perf_counter() - t0
-    out["e2e"] = {"value": round(3 * args.steps / t_e2e, 4), "unit": UNIT, "h2d_bytes_per_step": L ** 3,
-                  "d2h_bytes_per_step": 2 * 9 * 8}
+    if not args.no_e2e:
+        host = [torch.from_numpy(rng.integers(0, 2, L ** 3, dtype=np.uint8)).pin_memory() for _ in range(args.steps)]
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        for k in range(args.steps):
+            step(None, upload=host[k])
+        torch.cuda.synchronize()
+        t_e2e = time.perf_counter() - t0
+        out["e2e"] = {"value": round(3 * args.steps / t_e2e, 4), "unit": UNIT, "h2d_bytes_per_step": L ** 3,
+                      "d2h_bytes_per_step": 2 * 9 * 8}
 
     # --- variants on the same workload (2 steps each)
     if not args.no_variants and rank == 0:
@@ -363,6 +364,7 @@ def main():
     ap.add_argument("--precision", choices=["fp64", "fp32_refine"], default="fp64")
     ap.add_argument("--no-variants", action="store_true")
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--no-e2e", action="store_true")
     args = ap.parse_args()
     if args.warmup < 3 and args.impl == "native":
         args.warmup = 3
