@@ -146,6 +146,24 @@ int sq_pcg_solve(const sq_coeffs *c, const sq_precond *pc, sq_workspace *w, int 
 int sq_homogenized_matrix(const sq_coeffs *c, const double *psi0, const double *psi1,
                           const double *psi2, double *A_hom, double *A_energy, sq_stream_t stream);
 
+/* A_hom without allocating: for callers that may not allocate device memory
+ * when they need the result (code running under CUDA stream capture, or a
+ * framework that hands out all device memory from its own pool). The paper has
+ * no counterpart; the arithmetic is that of sq_homogenized_matrix. Inputs are
+ * device pointers the caller owns: `phase` (L^3 bytes, nonzero = a_hi, index
+ * c3 + L*c2 + L*L*c1) and the three correctors psi_i (N^3 doubles, N = L*n).
+ * Output: `out` (device, 18 doubles) = A_hom[9] (edge form, row-major) then
+ * the energy form[9]. Sizes as for sq_build_coeffs (N <= 512), else SQ_EINVAL.
+ * Asynchronous on `stream`; calls no allocator. Its reduction scratch is one
+ * fixed 2.36 MB __device__ array per GPU, held until the process exits and
+ * shared by every call: calls that overlap on the GPU race, so order them on
+ * one stream. The first call on a device looks up the array's address
+ * (cudaGetSymbolAddress) with that device current: make it before any stream
+ * capture. */
+int sq_homogenized_matrix_noalloc(int L, int n, const uint8_t *phase, double a_lo, double a_hi,
+                                  const double *psi0, const double *psi1, const double *psi2,
+                                  double *out, sq_stream_t stream);
+
 /* Building blocks, exposed for verification (asynchronous):
  * y = A x (FP64 or FP32 fields), b = b_dir, z = G-preconditioned r (the full
  * 3D transform pipeline of the solver; w must match pc's N and the field type:

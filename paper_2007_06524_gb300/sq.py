@@ -60,6 +60,7 @@ def load_library():
         "sq_workspace_destroy": (None, [vp]),
         "sq_pcg_solve": (i, [vp, vp, vp, i, d, i, i, vp, vp, p(SolveInfo), vp]),
         "sq_homogenized_matrix": (i, [vp, vp, vp, vp, vp, vp, vp]),
+        "sq_homogenized_matrix_noalloc": (i, [i, i, vp, d, d, vp, vp, vp, vp, vp]),
         "sq_apply_operator": (i, [vp, vp, vp, vp]),
         "sq_apply_operator_f32": (i, [vp, vp, vp, vp]),
         "sq_rhs": (i, [vp, i, vp, vp]),
@@ -228,6 +229,15 @@ def sq_homogenized_matrix(c, psi0, psi1, psi2, stream=None):
                                                 A.ctypes.data_as(C.c_void_p), E.ctypes.data_as(C.c_void_p),
                                                 _stream(stream)), "sq_homogenized_matrix")
     return A.reshape(3, 3), E.reshape(3, 3)
+
+
+def sq_homogenized_matrix_noalloc(L, n, phase, a_lo, a_hi, psi0, psi1, psi2, out, stream=None):
+    """A_hom with no allocation inside the library: phase is a CUDA uint8 tensor
+    (L^3), psi_i CUDA float64 tensors (N^3), out a CUDA float64 tensor of 18
+    (edge form then energy form). Asynchronous on the stream."""
+    _check(load_library().sq_homogenized_matrix_noalloc(int(L), int(n), _ptr(phase, "uint8"), float(a_lo), float(a_hi),
+                                                        _ptr(psi0), _ptr(psi1), _ptr(psi2), _ptr(out),
+                                                        _stream(stream)), "sq_homogenized_matrix_noalloc")
 
 
 def sq_apply_operator(c, x, y, stream=None):
