@@ -137,6 +137,41 @@ int sq_pcg_solve(const sq_coeffs *c, const sq_precond *pc, sq_workspace *w, int 
                  int max_iter, int precision, const double *x0, double *psi,
                  sq_solve_info *info, sq_stream_t stream);
 
+/* Batched solves: many independent corrector problems (realizations x
+ * right-hand sides, any mix of grid sizes) advanced together, each kernel
+ * launch covering every solve. Precision as SQ_FP32_REFINE. */
+typedef struct sq_batch sq_batch;
+
+typedef struct sq_solve_desc {
+  const sq_coeffs *coeffs; /* realization; must outlive the batch              */
+  int dir;                 /* right-hand side e_{dir+1}, 0..2                   */
+  double *psi;             /* device, N^3 doubles: the solution (zero mean)     */
+} sq_solve_desc;
+
+/* Tile shape per grid size (0 = default): Hartley-pass tile of `dht_pencils`
+ * complex pencils (a power of two, 2*dht_pencils dividing N), operator blocks of
+ * `stencil_planes` x1-planes. */
+typedef struct sq_tile_config {
+  int N;
+  int dht_pencils;
+  int stencil_planes;
+} sq_tile_config;
+
+/* Plans a batch of `count` solves; precs[k] is the preconditioner (same N) of
+ * descs[k]. Allocates 5 N^3 floats per solve plus scalars and partials, and
+ * captures the batched inner PCG iteration into a CUDA graph on first solve.
+ * tiles (ntiles entries, may be NULL) overrides the default tile per N.
+ * Synchronous. */
+int sq_batch_create(int count, const sq_solve_desc *descs, const sq_precond *const *precs,
+                    const sq_tile_config *tiles, int ntiles, sq_batch **out);
+void sq_batch_destroy(sq_batch *b);
+
+/* Solves every problem of the batch to ||b - A psi||/||b|| <= tol (FP64 true
+ * residual), x0 = 0, at most max_iter inner iterations per solve. infos (host,
+ * `count` entries, may be NULL) receives per-solve iterations and residuals.
+ * Returns SQ_ENOCONV if any solve missed the tolerance. Synchronizes `stream`. */
+int sq_pcg_solve_batched(sq_batch *b, double tol, int max_iter, sq_solve_info *infos, sq_stream_t stream);
+
 /* Homogenized matrix (Sec. 3.4, Eqs. 21-23) from the three correctors psi_i
  * (device, N^3 doubles each):
  *   A_hom[3*i+j] = delta_ij mean(a_j) + mean(a_j * D_j psi_i)   (edge form)

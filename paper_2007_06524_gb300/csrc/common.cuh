@@ -58,6 +58,32 @@ template <> struct Cx<double> { using type = double2; };
 
 // ---------------------------------------------------------------- reductions
 
+// Per-thread partial sums. FP64 kernels accumulate in FP64. FP32 kernels use
+// compensated (Kahan) FP32 sums and convert to FP64 once per thread: GB300's
+// FP64 pipe is ~1/58 of its FP32 rate, and one FP64 FMA plus two conversions
+// per point saturate it. Block and global sums are FP64 in both cases.
+template <typename T>
+struct Accum;
+template <>
+struct Accum<double> {
+  double s = 0.0;
+  __device__ __forceinline__ void add(double v) { s += v; }
+  __device__ __forceinline__ void add_prod(double a, double b) { s = fma(a, b, s); }
+  __device__ __forceinline__ double get() const { return s; }
+};
+template <>
+struct Accum<float> {
+  float s = 0.f, c = 0.f;  // running sum and its compensation (sum = s - c)
+  __device__ __forceinline__ void add(float v) {
+    const float y = v - c;
+    const float t = s + y;
+    c = (t - s) - y;
+    s = t;
+  }
+  __device__ __forceinline__ void add_prod(float a, float b) { add(a * b); }
+  __device__ __forceinline__ double get() const { return (double)s - (double)c; }
+};
+
 __device__ __forceinline__ double warp_sum(double v) {
 #pragma unroll
   for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
@@ -68,15 +94,16 @@ __device__ __forceinline__ double warp_sum(double v) {
 // the last block to finish sum all partials in a fixed order (deterministic,
 // independent of which block is last). Returns true in every thread of that
 // last block; the sums are then in out[0..NQ). Requires blockDim = kThreads.
+// The explicit form takes the block's index `bid` among the `nblk` blocks that
+// share one ticket, and the partials row stride `pstride` (batched kernels
+// reduce per solve); reduce_last_block uses the whole grid.
 template <int NQ>
-__device__ __forceinline__ bool reduce_last_block(double (&v)[NQ], double *partials, unsigned *ticket,
-                                                  double (&out)[NQ]) {
+__device__ __forceinline__ bool reduce_last_block_ex(double (&v)[NQ], double *partials, int pstride,
+                                                     unsigned *ticket, int nblk, int bid, double (&out)[NQ]) {
   __shared__ double s_w[NQ][kThreads / 32];
   __shared__ unsigned s_last;
   const int tid = threadIdx.x + blockDim.x * (threadIdx.y + blockDim.y * threadIdx.z);
   const int lane = tid & 31, wid = tid >> 5;
-  const int nblk = gridDim.x * gridDim.y * gridDim.z;
-  const int bid = blockIdx.x + gridDim.x * (blockIdx.y + gridDim.y * blockIdx.z);
 #pragma unroll
   for (int q = 0; q < NQ; ++q) {
     double s = warp_sum(v[q]);
@@ -88,7 +115,7 @@ __device__ __forceinline__ bool reduce_last_block(double (&v)[NQ], double *parti
     for (int q = 0; q < NQ; ++q) {
       double s = 0.0;
       for (int w = 0; w < kThreads / 32; ++w) s += s_w[q][w];
-      partials[q * kMaxPartials + bid] = s;
+      partials[q * pstride + bid] = s;
     }
     __threadfence();
     unsigned t = atomicAdd(ticket, 1u);
@@ -100,7 +127,7 @@ __device__ __forceinline__ bool reduce_last_block(double (&v)[NQ], double *parti
 #pragma unroll
   for (int q = 0; q < NQ; ++q) {
     double s = 0.0;
-    for (int i = tid; i < nblk; i += kThreads) s += __ldcg(&partials[q * kMaxPartials + i]);
+    for (int i = tid; i < nblk; i += kThreads) s += __ldcg(&partials[q * pstride + i]);
     s = warp_sum(s);
     if (lane == 0) s_w[q][wid] = s;
   }
@@ -113,6 +140,14 @@ __device__ __forceinline__ bool reduce_last_block(double (&v)[NQ], double *parti
   }
   if (tid == 0) *ticket = 0u;
   return true;
+}
+
+template <int NQ>
+__device__ __forceinline__ bool reduce_last_block(double (&v)[NQ], double *partials, unsigned *ticket,
+                                                  double (&out)[NQ]) {
+  const int nblk = gridDim.x * gridDim.y * gridDim.z;
+  const int bid = blockIdx.x + gridDim.x * (blockIdx.y + gridDim.y * blockIdx.z);
+  return reduce_last_block_ex<NQ>(v, partials, kMaxPartials, ticket, nblk, bid, out);
 }
 
 // Scalar bookkeeping done by thread 0 of the last block.
@@ -176,7 +211,36 @@ struct CellsDev {
   const uint8_t *phase;  // L^3 cell phases
   int L, n, N;
   double a_lo, a_hi;
+  // An edge touches 4 voxels, k of them high: a_edge = (k a_hi + (4-k) a_lo)/4.
+  // A node's six edges touch 24 voxel slots, K of them high: the diagonal is
+  // (K a_hi + (24-K) a_lo)/4. Both tables are filled on the host (fill_tables).
+  double edge_d[5], diag_d[25];
+  float edge_f[5], diag_f[25];
 };
+
+inline void fill_tables(CellsDev &c) {
+  for (int k = 0; k <= 4; ++k) {
+    c.edge_d[k] = (k * c.a_hi + (4 - k) * c.a_lo) * 0.25;
+    c.edge_f[k] = (float)c.edge_d[k];
+  }
+  for (int k = 0; k <= 24; ++k) {
+    c.diag_d[k] = (k * c.a_hi + (24 - k) * c.a_lo) * 0.25;
+    c.diag_f[k] = (float)c.diag_d[k];
+  }
+}
+
+template <typename T>
+__device__ __forceinline__ const T *edge_table(const CellsDev &c);
+template <>
+__device__ __forceinline__ const double *edge_table<double>(const CellsDev &c) { return c.edge_d; }
+template <>
+__device__ __forceinline__ const float *edge_table<float>(const CellsDev &c) { return c.edge_f; }
+template <typename T>
+__device__ __forceinline__ const T *diag_table(const CellsDev &c);
+template <>
+__device__ __forceinline__ const double *diag_table<double>(const CellsDev &c) { return c.diag_d; }
+template <>
+__device__ __forceinline__ const float *diag_table<float>(const CellsDev &c) { return c.diag_f; }
 
 struct RedBuf {
   Scalars *st;
@@ -218,5 +282,9 @@ template <typename T>
 cudaError_t launch_dht_pass(int pass, const SpectralDev &sp, const T *in, T *out, T *r, const T *q, T *p, T *x,
                             RedBuf rb, bool first, bool check_done, cudaStream_t s);
 int dht_tile_pencils(int N, int elem_bytes);
+
+// solver.cu: read-only views of the opaque handles (used by batch.cu)
+int coeffs_view(const sq_coeffs *c, CellsDev *out);
+int precond_spec32(const sq_precond *p, SpectralDev *out, int *N);
 
 }  // namespace sq

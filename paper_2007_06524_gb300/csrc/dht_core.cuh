@@ -1,0 +1,303 @@
+// Device core of the Hartley-transform pencil passes, shared by the
+// single-solve and the batched kernels. See dht.cu for the method.
+#pragma once
+
+#include "common.cuh"
+
+namespace sq {
+
+template <typename C>
+__device__ __forceinline__ C cadd(C a, C b) { return C{a.x + b.x, a.y + b.y}; }
+template <typename C>
+__device__ __forceinline__ C csub(C a, C b) { return C{a.x - b.x, a.y - b.y}; }
+template <typename C>
+__device__ __forceinline__ C cmul(C a, C w) {
+  return C{fma(a.x, w.x, -a.y * w.y), fma(a.x, w.y, a.y * w.x)};
+}
+template <typename C>
+__device__ __forceinline__ C mul_mi(C a) { return C{a.y, -a.x}; }  // (-i) a
+
+template <typename T, typename C>
+__device__ __forceinline__ void dft4(C &u0, C &u1, C &u2, C &u3) {
+  const C t0 = cadd(u0, u2), t1 = csub(u0, u2), t2 = cadd(u1, u3), t3 = mul_mi(csub(u1, u3));
+  u0 = cadd(t0, t2);
+  u2 = csub(t0, t2);
+  u1 = cadd(t1, t3);
+  u3 = csub(t1, t3);
+}
+
+template <typename T, typename C, int R>
+__device__ __forceinline__ void dft(C (&u)[R]) {
+  if (R == 2) {
+    const C t = u[0];
+    u[0] = cadd(t, u[1]);
+    u[1] = csub(t, u[1]);
+  } else if (R == 3) {
+    const T c = (T)0.86602540378443864676;  // sqrt(3)/2
+    const C s = cadd(u[1], u[2]), d = csub(u[1], u[2]);
+    const C m = C{fma((T)-0.5, s.x, u[0].x), fma((T)-0.5, s.y, u[0].y)};
+    u[0] = cadd(u[0], s);
+    u[1] = C{fma(c, d.y, m.x), fma(-c, d.x, m.y)};
+    u[2] = C{fma(-c, d.y, m.x), fma(c, d.x, m.y)};
+  } else if (R == 4) {
+    dft4<T, C>(u[0], u[1], u[2], u[3]);
+  } else if (R == 8) {
+    const T h = (T)0.70710678118654752440;  // sqrt(2)/2
+    C e0 = u[0], e1 = u[2], e2 = u[4], e3 = u[6];
+    C o0 = u[1], o1 = u[3], o2 = u[5], o3 = u[7];
+    dft4<T, C>(e0, e1, e2, e3);
+    dft4<T, C>(o0, o1, o2, o3);
+    const C w1 = C{h * (o1.x + o1.y), h * (o1.y - o1.x)};
+    const C w2 = mul_mi(o2);
+    const C w3 = C{h * (o3.y - o3.x), -h * (o3.x + o3.y)};
+    u[0] = cadd(e0, o0);
+    u[4] = csub(e0, o0);
+    u[1] = cadd(e1, w1);
+    u[5] = csub(e1, w1);
+    u[2] = cadd(e2, w2);
+    u[6] = csub(e2, w2);
+    u[3] = cadd(e3, w3);
+    u[7] = csub(e3, w3);
+  }
+}
+
+// One radix-R Stockham stage over P pencils stored [j][p] with row stride SP.
+// ps = product of the radices of the previous stages.
+template <typename T, typename C, int R>
+__device__ __forceinline__ void fft_stage(const C *__restrict__ in, C *__restrict__ out, const C *__restrict__ tw,
+                                          int N, int ps, int SP, int logP) {
+  const int P = 1 << logP;
+  const int NR = N / R;
+  const int nb = NR << logP;
+  const int tstride = N / (ps * R);
+  for (int t = threadIdx.x; t < nb; t += kThreads) {
+    const int p = t & (P - 1);
+    const int b = t >> logP;
+    const int k = b % ps;
+    C u[R];
+#pragma unroll
+    for (int q = 0; q < R; ++q) u[q] = in[(b + q * NR) * SP + p];
+    if (ps > 1) {
+      const int step = k * tstride;
+#pragma unroll
+      for (int q = 1; q < R; ++q) u[q] = cmul(u[q], tw[q * step]);
+    }
+    dft<T, C, R>(u);
+    const int j = (b - k) * R + k;
+#pragma unroll
+    for (int q = 0; q < R; ++q) out[(j + q * ps) * SP + p] = u[q];
+  }
+}
+
+template <typename T, typename C>
+__device__ __forceinline__ C *fft_all(C *b0, C *b1, const C *tw, const SpectralDev &sp, int SP, int logP) {
+  C *src = b0, *dst = b1;
+  int ps = 1;
+  for (int s = 0; s < sp.nst; ++s) {
+    const int r = sp.radix[s];
+    switch (r) {
+      case 2: fft_stage<T, C, 2>(src, dst, tw, sp.N, ps, SP, logP); break;
+      case 3: fft_stage<T, C, 3>(src, dst, tw, sp.N, ps, SP, logP); break;
+      case 4: fft_stage<T, C, 4>(src, dst, tw, sp.N, ps, SP, logP); break;
+      default: fft_stage<T, C, 8>(src, dst, tw, sp.N, ps, SP, logP); break;
+    }
+    __syncthreads();
+    C *t = src;
+    src = dst;
+    dst = t;
+    ps *= r;
+  }
+  return src;
+}
+
+enum LoadMode { LD_PLAIN = 0, LD_RESID = 1 };
+enum StoreMode { SO_PLAIN = 0, SO_PCG = 1 };
+
+// Operands of one tile: fields, PCG scalars and tile shape.
+template <typename T>
+struct DhtTile {
+  const T *in;
+  T *out;
+  T *r;
+  const T *q;
+  T *p;
+  T *x;
+  T alpha, beta;
+  int first;
+  int logP;
+};
+
+// Shared-memory layout: two ping-pong buffers of N (P+1) complex values, N
+// twiddles, then rank x 2P column factors (pass C with a rank-R tensor).
+template <typename T>
+__host__ __device__ inline size_t dht_smem_bytes_t(int N, int P, int rank) {
+  const size_t c = 2 * sizeof(T);
+  return 2 * (size_t)N * (P + 1) * c + (size_t)N * c + (size_t)rank * 2 * P * sizeof(T);
+}
+
+// One tile: load (with the fused residual update), transform(s), store (with
+// the fused PCG update). Per-thread sums of ||r||^2 (LD_RESID) or r.z (SCALE)
+// go to acc. Starts with a barrier so consecutive tiles may reuse the buffers.
+template <typename T, int AXIS, int LOADM, int STOREM, bool SCALE>
+__device__ __forceinline__ void dht_tile(const SpectralDev &sp, const DhtTile<T> &a, int tile,
+                                         typename Cx<T>::type *buf0, typename Cx<T>::type *buf1,
+                                         const typename Cx<T>::type *tw, T *vtab, Accum<T> &acc) {
+  using C = typename Cx<T>::type;
+  const int N = sp.N;
+  const int logP = a.logP;
+  const int P = 1 << logP;
+  const int SP = P + 1;
+  const int tid = threadIdx.x;
+  const size_t NN = (size_t)N * N;
+  const int nb2 = N / (2 * P);  // tiles per line for x1 / x2 passes
+  const T alpha = a.alpha, beta = a.beta;
+  const T *lam = reinterpret_cast<const T *>(sp.lam);
+  const T *uf = reinterpret_cast<const T *>(sp.u);
+  const int R = sp.rank;
+  const T gscale = (T)sp.scale;
+
+  __syncthreads();
+  // ------------------------------------------------------------------ load
+  size_t base = 0, stride = 0;
+  int k2 = 0, c0 = 0;
+  if (AXIS == 3) {
+    const size_t row0 = (size_t)tile * 2 * P;
+    const int halfN = N >> 1;
+    for (int e = tid; e < P * N; e += kThreads) {
+      const int q = e / halfN;
+      const int jj = 2 * (e - q * halfN);
+      const size_t g = (row0 + q) * N + jj;
+      C v = reinterpret_cast<const C *>(a.in)[g >> 1];
+      if (LOADM == LD_RESID && !a.first) {
+        const C qq = reinterpret_cast<const C *>(a.q)[g >> 1];
+        v.x = fma(-alpha, qq.x, v.x);
+        v.y = fma(-alpha, qq.y, v.y);
+        reinterpret_cast<C *>(a.r)[g >> 1] = v;
+        acc.add(fma(v.x, v.x, v.y * v.y));
+      }
+      T *bs = reinterpret_cast<T *>(buf0);
+      bs[(jj * SP + (q >> 1)) * 2 + (q & 1)] = v.x;
+      bs[((jj + 1) * SP + (q >> 1)) * 2 + (q & 1)] = v.y;
+    }
+  } else {
+    const int line = tile / nb2;
+    const int cb = tile - line * nb2;
+    c0 = cb * 2 * P;
+    if (AXIS == 2) {
+      base = (size_t)line * NN + c0;
+      stride = N;
+    } else {
+      base = (size_t)line * N + c0;
+      stride = NN;
+      k2 = line;
+    }
+    for (int e = tid; e < P * N; e += kThreads) {
+      const int p = e & (P - 1);
+      const int j = e >> logP;
+      const size_t g = base + (size_t)j * stride + 2 * p;
+      buf0[j * SP + p] = reinterpret_cast<const C *>(a.in)[g >> 1];
+    }
+    if (SCALE && R > 0) {
+      for (int e = tid; e < R * 2 * P; e += kThreads) {
+        const int rr = e / (2 * P), w = e - rr * 2 * P;
+        vtab[e] = uf[rr * N + k2] * uf[rr * N + c0 + w];
+      }
+    }
+  }
+  __syncthreads();
+  // --------------------------------------------------------- transform(s)
+  C *res = fft_all<T, C>(buf0, buf1, tw, sp, SP, logP);
+  {
+    const int halfN = N >> 1;
+    for (int t = tid; t < ((halfN + 1) << logP); t += kThreads) {
+      const int p = t & (P - 1);
+      const int k = t >> logP;
+      const int km = (k == 0) ? 0 : N - k;
+      const C X = res[k * SP + p], Y = res[km * SP + p];
+      T ak = X.x - X.y + Y.x + Y.y, bk = X.x + X.y - Y.x + Y.y;
+      T akm = Y.x - Y.y + X.x + X.y, bkm = Y.x + Y.y - X.x + X.y;
+      if (SCALE) {
+        const int k3a = c0 + 2 * p, k3b = k3a + 1;
+        T ga, gb;
+        if (R == 0) {
+          const T l12 = lam[k] + lam[k2];
+          const T g1 = l12 + lam[k3a], g2 = l12 + lam[k3b];
+          ga = (g1 > (T)0) ? gscale / g1 : (T)0;
+          gb = (g2 > (T)0) ? gscale / g2 : (T)0;
+        } else {
+          T sa = (T)0, sb = (T)0;
+          for (int rr = 0; rr < R; ++rr) {
+            const T uk = uf[rr * N + k];
+            sa = fma(uk, vtab[rr * 2 * P + 2 * p], sa);
+            sb = fma(uk, vtab[rr * 2 * P + 2 * p + 1], sb);
+          }
+          ga = (k == 0 && k2 == 0 && k3a == 0) ? (T)0 : sa;
+          gb = sb;  // k3b >= 1
+        }
+        T e2 = fma(ga * ak, ak, gb * bk * bk);
+        if (km != k) e2 += fma(ga * akm, akm, gb * bkm * bkm);
+        acc.add(e2);
+        ak *= ga;
+        akm *= ga;
+        bk *= gb;
+        bkm *= gb;
+      }
+      res[k * SP + p] = C{ak, bk};
+      if (km != k) res[km * SP + p] = C{akm, bkm};
+    }
+    __syncthreads();
+  }
+  if (SCALE) {
+    C *other = (res == buf0) ? buf1 : buf0;
+    res = fft_all<T, C>(res, other, tw, sp, SP, logP);
+    const int halfN = N >> 1;
+    for (int t = tid; t < ((halfN + 1) << logP); t += kThreads) {
+      const int p = t & (P - 1);
+      const int k = t >> logP;
+      const int km = (k == 0) ? 0 : N - k;
+      const C X = res[k * SP + p], Y = res[km * SP + p];
+      res[k * SP + p] = C{X.x - X.y + Y.x + Y.y, X.x + X.y - Y.x + Y.y};
+      if (km != k) res[km * SP + p] = C{Y.x - Y.y + X.x + X.y, Y.x + Y.y - X.x + X.y};
+    }
+    __syncthreads();
+  }
+  // ----------------------------------------------------------------- store
+  if (AXIS == 3) {
+    const size_t row0 = (size_t)tile * 2 * P;
+    const int halfN = N >> 1;
+    const T *bs = reinterpret_cast<const T *>(res);
+    for (int e = tid; e < P * N; e += kThreads) {
+      const int q = e / halfN;
+      const int jj = 2 * (e - q * halfN);
+      const size_t g = (row0 + q) * N + jj;
+      C z;
+      z.x = bs[(jj * SP + (q >> 1)) * 2 + (q & 1)];
+      z.y = bs[((jj + 1) * SP + (q >> 1)) * 2 + (q & 1)];
+      if (STOREM == SO_PCG) {
+        C *pp = reinterpret_cast<C *>(a.p) + (g >> 1);
+        if (a.first) {
+          *pp = z;
+        } else {
+          C *xx = reinterpret_cast<C *>(a.x) + (g >> 1);
+          const C po = *pp;
+          C xo = *xx;
+          xo.x = fma(alpha, po.x, xo.x);
+          xo.y = fma(alpha, po.y, xo.y);
+          *xx = xo;
+          *pp = C{fma(beta, po.x, z.x), fma(beta, po.y, z.y)};
+        }
+      } else {
+        reinterpret_cast<C *>(a.out)[g >> 1] = z;
+      }
+    }
+  } else {
+    for (int e = tid; e < P * N; e += kThreads) {
+      const int p = e & (P - 1);
+      const int j = e >> logP;
+      const size_t g = base + (size_t)j * stride + 2 * p;
+      reinterpret_cast<C *>(a.out)[g >> 1] = res[j * SP + p];
+    }
+  }
+}
+
+}  // namespace sq

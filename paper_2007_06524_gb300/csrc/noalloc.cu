@@ -108,6 +108,7 @@ extern "C" int sq_homogenized_matrix_noalloc(int L, int n, const uint8_t *phase,
   c.N = L * n;
   c.a_lo = a_lo;
   c.a_hi = a_hi;
+  fill_tables(c);
   RedBuf rb;
   rb.st = sc;
   rb.partials = scratch + kScalarsDoubles;

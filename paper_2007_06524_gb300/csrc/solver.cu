@@ -119,6 +119,7 @@ CellsDev cells_dev(const sq_coeffs *c) {
   d.N = c->N;
   d.a_lo = c->a_lo;
   d.a_hi = c->a_hi;
+  fill_tables(d);
   return d;
 }
 
@@ -424,6 +425,20 @@ int apply_precond_t(const sq_precond *pc, sq_workspace *w, const T *r, T *z, T *
 }
 
 }  // namespace
+
+namespace sq {
+int coeffs_view(const sq_coeffs *c, CellsDev *out) {
+  if (!c || !out) return SQ_EINVAL;
+  *out = cells_dev(c);
+  return SQ_OK;
+}
+int precond_spec32(const sq_precond *p, SpectralDev *out, int *N) {
+  if (!p || !out || !N) return SQ_EINVAL;
+  *out = p->sp32;
+  *N = p->N;
+  return SQ_OK;
+}
+}  // namespace sq
 
 // =================================================================== C ABI
 extern "C" {

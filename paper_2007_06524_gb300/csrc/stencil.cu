@@ -13,7 +13,7 @@
 // and the diagonal; no N^3 coefficient field exists.
 //
 // RHS (Eq. 8 in grid units): b_dir(j) = a_dir(j) - a_dir(j - e_dir).
-#include "common.cuh"
+#include "stencil_core.cuh"
 
 namespace sq {
 
@@ -38,115 +38,23 @@ cudaError_t launch_coeff_gen(uint8_t *phase, int L, uint64_t seed, uint64_t thr,
   return cudaGetLastError();
 }
 
-// ------------------------------------------------------ coefficient patterns
-// Bit s1*4 + s2*2 + s3 of the pattern = phase of voxel (j1-s1, j2-s2, j3-s3).
-// Entries: 0 a_1(j), 1 a_1(j-e1), 2 a_2(j), 3 a_2(j-e2), 4 a_3(j), 5 a_3(j-e3),
-// 6 diagonal (sum of the six), 7 unused.
-template <typename T>
-__device__ __forceinline__ void build_pattern_table(T (*tab)[8], double a_lo, double a_hi, int tid) {
-  const unsigned face[6] = {0x0Fu, 0xF0u, 0x33u, 0xCCu, 0x55u, 0xAAu};
-  for (int m = tid; m < 256; m += kThreads) {
-    double diag = 0.0;
-#pragma unroll
-    for (int f = 0; f < 6; ++f) {
-      int k = __popc(m & face[f]);
-      double a = (k * a_hi + (4 - k) * a_lo) * 0.25;
-      tab[m][f] = (T)a;
-      diag += a;
-    }
-    tab[m][6] = (T)diag;
-    tab[m][7] = (T)0;
-  }
-}
-
-// Four phase bits of cell row c1 at the node's (s2, s3) cell offsets.
-__device__ __forceinline__ unsigned load4(const uint8_t *__restrict__ phase, int c1, int LL, int o00, int o01,
-                                          int o10, int o11) {
-  const uint8_t *ph = phase + (size_t)c1 * LL;
-  return (ph[o00] ? 1u : 0u) | (ph[o01] ? 2u : 0u) | (ph[o10] ? 4u : 0u) | (ph[o11] ? 8u : 0u);
-}
-
-// ------------------------------------------------------------ stencil kernel
-// Block (32 x 8) threads over (j3, j2); each thread marches along j1 over
-// [z0, z0 + zc), keeping x(j1-1), x(j1), x(j1+1) in registers. The eight voxel
-// bits change only when j1 crosses a cell boundary.
+// Block (32 x 8) threads over (j3, j2), blockIdx.z over j1 chunks of zc planes.
 template <typename Ti, typename To, int MODE>
 __global__ void __launch_bounds__(kThreads) k_stencil(CellsDev c, int dir, const Ti *__restrict__ x,
                                                       To *__restrict__ y, RedBuf rb, int fin, int check_done,
                                                       int zc) {
   if (check_done && *(volatile int *)&rb.st->done) return;
-  __shared__ Ti tab[256][8];
+  __shared__ Ti tab[256][kTabStride];
   const int tid = threadIdx.x + 32 * threadIdx.y;
-  build_pattern_table<Ti>(tab, c.a_lo, c.a_hi, tid);
+  build_pattern_table<Ti>(tab, c, tid);
   __syncthreads();
-
-  const int N = c.N, n = c.n, L = c.L;
-  const size_t NN = (size_t)N * N;
   const int j3 = blockIdx.x * 32 + threadIdx.x;
   const int j2 = blockIdx.y * 8 + threadIdx.y;
   const int z0 = blockIdx.z * zc;
-  const int z1 = min(z0 + zc, N);
-  double acc0 = 0.0, acc1 = 0.0;
-  if (j3 < N && j2 < N) {
-    const int j3m = (j3 == 0) ? N - 1 : j3 - 1, j3p = (j3 == N - 1) ? 0 : j3 + 1;
-    const int j2m = (j2 == 0) ? N - 1 : j2 - 1, j2p = (j2 == N - 1) ? 0 : j2 + 1;
-    const int c3a = j3 / n, c3b = j3m / n, c2a = j2 / n, c2b = j2m / n;
-    const int o00 = c2a * L + c3a, o01 = c2a * L + c3b, o10 = c2b * L + c3a, o11 = c2b * L + c3b;
-    const int LL = L * L;
-    const size_t row = (size_t)j2 * N + j3;
-    const size_t r2p = (size_t)j2p * N + j3, r2m = (size_t)j2m * N + j3;
-    const size_t r3p = (size_t)j2 * N + j3p, r3m = (size_t)j2 * N + j3m;
-
-    int j1 = z0;
-    const int j1m0 = (j1 == 0) ? N - 1 : j1 - 1;
-    unsigned m_prev = load4(c.phase, j1m0 / n, LL, o00, o01, o10, o11);
-    unsigned m_cur = (j1 % n == 0) ? load4(c.phase, j1 / n, LL, o00, o01, o10, o11) : m_prev;
-    Ti xm = (Ti)0, x0 = (Ti)0, xp = (Ti)0;
-    if (MODE != ST_RHS) {
-      xm = x[(size_t)j1m0 * NN + row];
-      x0 = x[(size_t)j1 * NN + row];
-    }
-    for (; j1 < z1; ++j1) {
-      if (j1 > z0) {
-        m_prev = m_cur;
-        if (j1 % n == 0) m_cur = load4(c.phase, j1 / n, LL, o00, o01, o10, o11);
-      }
-      const Ti *t = tab[m_cur | (m_prev << 4)];
-      const size_t base = (size_t)j1 * NN;
-      Ti out;
-      Ti bv = (Ti)0;
-      if (MODE != ST_MATVEC) bv = t[2 * dir] - t[2 * dir + 1];
-      if (MODE != ST_RHS) {
-        const int j1p = (j1 == N - 1) ? 0 : j1 + 1;
-        xp = x[(size_t)j1p * NN + row];
-        const Ti x2p = x[base + r2p], x2m = x[base + r2m];
-        const Ti x3p = x[base + r3p], x3m = x[base + r3m];
-        Ti off = t[0] * xp;
-        off = fma(t[1], xm, off);
-        off = fma(t[2], x2p, off);
-        off = fma(t[3], x2m, off);
-        off = fma(t[4], x3p, off);
-        off = fma(t[5], x3m, off);
-        const Ti ax = fma(t[6], x0, -off);
-        if (MODE == ST_MATVEC) {
-          out = ax;
-          acc0 = fma((double)x0, (double)ax, acc0);
-        } else {
-          out = bv - ax;
-          acc0 = fma((double)out, (double)out, acc0);
-          acc1 = fma((double)bv, (double)bv, acc1);
-        }
-        xm = x0;
-        x0 = xp;
-      } else {
-        out = bv;
-        acc0 = fma((double)bv, (double)bv, acc0);
-        acc1 = acc0;
-      }
-      y[base + row] = (To)out;
-    }
-  }
-  double v[2] = {acc0, acc1}, s[2];
+  const int z1 = min(z0 + zc, c.N);
+  Accum<Ti> acc0, acc1;
+  if (j3 < c.N && j2 < c.N) stencil_column<Ti, To, MODE>(c, dir, x, y, tab, j3, j2, z0, z1, acc0, acc1);
+  double v[2] = {acc0.get(), acc1.get()}, s[2];
   if (reduce_last_block<2>(v, rb.partials, &rb.st->ticket, s)) {
     if (tid == 0) finalize_scalars(rb.st, fin, s, 2);
   }
@@ -201,9 +109,9 @@ template cudaError_t launch_stencil<double, float>(const CellsDev &, int, int, c
 __global__ void __launch_bounds__(kThreads) k_ahom(CellsDev c, const double *__restrict__ p0,
                                                    const double *__restrict__ p1, const double *__restrict__ p2,
                                                    RedBuf rb, int zc) {
-  __shared__ double tab[256][8];
+  __shared__ double tab[256][kTabStride];
   const int tid = threadIdx.x + 32 * threadIdx.y;
-  build_pattern_table<double>(tab, c.a_lo, c.a_hi, tid);
+  build_pattern_table<double>(tab, c, tid);
   __syncthreads();
   const int N = c.N, n = c.n, L = c.L;
   const size_t NN = (size_t)N * N;
@@ -277,16 +185,16 @@ __global__ void __launch_bounds__(kThreads) k_x_final_sum(T *__restrict__ x, con
                                                           long long n) {
   const int pend = rb.st->x_pending;
   const T alpha = (T)rb.st->alpha;
-  double acc = 0.0;
+  Accum<T> acc;
   for (long long i = blockIdx.x * (long long)kThreads + threadIdx.x; i < n; i += (long long)gridDim.x * kThreads) {
     T v = x[i];
     if (pend) {
       v = fma(alpha, p[i], v);
       x[i] = v;
     }
-    acc += (double)v;
+    acc.add(v);
   }
-  double vv[1] = {acc}, s[1];
+  double vv[1] = {acc.get()}, s[1];
   if (reduce_last_block<1>(vv, rb.partials, &rb.st->ticket, s)) {
     if (threadIdx.x == 0) {
       rb.st->red[0] = s[0];

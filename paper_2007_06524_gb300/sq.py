@@ -33,6 +33,14 @@ class SolveInfo(C.Structure):
                 ("relres", C.c_double), ("relres_true", C.c_double)]
 
 
+class SolveDesc(C.Structure):
+    _fields_ = [("coeffs", C.c_void_p), ("dir", C.c_int), ("psi", C.c_void_p)]
+
+
+class TileConfig(C.Structure):
+    _fields_ = [("N", C.c_int), ("dht_pencils", C.c_int), ("stencil_planes", C.c_int)]
+
+
 def load_library():
     """Loads libsq.so (built by paper_2007_06524_gb300.build). Raises if absent."""
     global _LIB
@@ -67,6 +75,9 @@ def load_library():
         "sq_apply_precond": (i, [vp, vp, vp, vp, vp]),
         "sq_apply_precond_f32": (i, [vp, vp, vp, vp, vp]),
         "sq_strerror": (C.c_char_p, [i]),
+        "sq_batch_create": (i, [i, p(SolveDesc), p(vp), p(TileConfig), i, p(vp)]),
+        "sq_batch_destroy": (None, [vp]),
+        "sq_pcg_solve_batched": (i, [vp, d, i, p(SolveInfo), vp]),
     }
     for name, (res, args) in sig.items():
         f = getattr(lib, name)
@@ -135,6 +146,15 @@ class Precond(_Handle):
 
 class Workspace(_Handle):
     _destroy = "sq_workspace_destroy"
+
+
+class Batch(_Handle):
+    _destroy = "sq_batch_destroy"
+
+    def __init__(self, ptr, count, keep):
+        super().__init__(ptr)
+        self.count = count
+        self._keep = keep  # coefficient handles, solution tensors and preconditioners stay alive
 
 
 def sq_build_coeffs(L, n, seed, p_hi, a_lo, a_hi, stream=None) -> Coeffs:
@@ -260,3 +280,32 @@ def sq_apply_precond(pc, w, r, z, stream=None):
 def sq_apply_precond_f32(pc, w, r, z, stream=None):
     _check(load_library().sq_apply_precond_f32(pc, w, _ptr(r, "float32"), _ptr(z, "float32"), _stream(stream)),
            "sq_apply_precond_f32")
+
+
+def sq_batch_create(descs, precs, tiles=None) -> Batch:
+    """descs: list of (Coeffs, dir, psi) with psi a float64 CUDA tensor of N^3;
+    precs: one Precond per solve (same N); tiles: optional list of
+    (N, dht_pencils, stencil_planes)."""
+    n = len(descs)
+    arr = (SolveDesc * n)()
+    for k, (c, d, psi) in enumerate(descs):
+        arr[k].coeffs = c.ptr
+        arr[k].dir = int(d)
+        arr[k].psi = _ptr(psi).value
+    parr = (C.c_void_p * n)(*[p.ptr.value if isinstance(p.ptr, C.c_void_p) else p.ptr for p in precs])
+    tl = list(tiles or [])
+    tarr = (TileConfig * max(1, len(tl)))()
+    for k, (N, dp, sp) in enumerate(tl):
+        tarr[k].N, tarr[k].dht_pencils, tarr[k].stencil_planes = int(N), int(dp), int(sp)
+    out = C.c_void_p()
+    _check(load_library().sq_batch_create(n, arr, parr, tarr if tl else None, len(tl), C.byref(out)), "sq_batch_create")
+    return Batch(out, n, (list(descs), list(precs)))
+
+
+def sq_pcg_solve_batched(b: Batch, tol, max_iter, stream=None) -> list:
+    """Solves the batch; returns one info dict per solve (SQ_ENOCONV is reported
+    per solve, other errors raise)."""
+    infos = (SolveInfo * b.count)()
+    st = load_library().sq_pcg_solve_batched(b, float(tol), int(max_iter), infos, _stream(stream))
+    _check(st, "sq_pcg_solve_batched", allow=(SQ_ENOCONV,))
+    return [{k: getattr(inf, k) for k, _ in SolveInfo._fields_} for inf in infos]

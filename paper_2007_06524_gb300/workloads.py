@@ -29,3 +29,10 @@ WARM_N64 = dict(
     name="learned warm start: L=16 n=4 (N=64), Bernoulli(1/2) on {1,10}, tol 1e-8",
     L=16, n=4, p_hi=0.5, a_lo=1.0, a_hi=10.0, train_seeds=list(range(1000, 5096)),
     eval_seeds=list(range(6000, 6512)), dirs=[0, 1, 2], ranks=[0], tol=1e-8)
+
+
+def batch_L_index(seed: int) -> int:
+    """Which of BATCH_MIXED['Ls'] realization `seed` uses: a seeded uniform draw."""
+    import numpy as np
+
+    return int(np.random.default_rng(seed).integers(4))
