@@ -181,6 +181,36 @@ int sq_pcg_solve_batched(sq_batch *b, double tol, int max_iter, sq_solve_info *i
 int sq_homogenized_matrix(const sq_coeffs *c, const double *psi0, const double *psi1,
                           const double *psi2, double *A_hom, double *A_energy, sq_stream_t stream);
 
+/* Learned warm start (an addition to the paper's method): a periodic 3D
+ * convolutional net -- 6 layers of 3x3x3 convolutions, 32 channels, GELU,
+ * BF16 weights and activations with FP32 accumulation on the tensor cores --
+ * maps the coefficient field (+1 high / -1 low per grid voxel) to a first
+ * guess of the three correctors psi_1..3 (scaled by out_scale). The guess is
+ * passed to sq_pcg_solve as x0; the solve judges it by its residual. Grids
+ * N = 32, 64, 96 or 128 (N % 32 == 0). */
+typedef struct sq_net sq_net;
+
+/* Creates the net for grid N with buffers for up to max_batch training
+ * samples; weights He-normal from `seed` (SplitMix64), biases zero. */
+int sq_net_create(int N, int max_batch, uint64_t seed, double out_scale, sq_net **out);
+void sq_net_destroy(sq_net *net);
+/* FP32 parameters (per layer: weights [27][cout][cin], then bias [cout]):
+ * copy out (host may be NULL to query *count) or in (resets the optimizer). */
+int sq_net_params(const sq_net *net, float *host, int64_t *count);
+int sq_net_set_params(sq_net *net, const float *host, int64_t count);
+/* Gradient of the last sq_net_train_step (same layout as the parameters). */
+int sq_net_grads(const sq_net *net, float *host, int64_t count);
+/* Guess for the three correctors of realization c (device outputs, N^3 doubles
+ * each). Asynchronous on `stream`. */
+int sq_net_predict(sq_net *net, const sq_coeffs *c, double *psi0, double *psi1, double *psi2,
+                   sq_stream_t stream);
+/* One Adam step (lr; beta 0.9 / 0.999) on the mean squared error against the
+ * targets targets[3*b + i] (device, N^3 doubles: psi_i of sample b) for the
+ * `batch` realizations cs[b]. *loss (host, may be NULL) receives the mean
+ * squared error / out_scale^2 of the forward pass (synchronizes `stream`). */
+int sq_net_train_step(sq_net *net, int batch, const sq_coeffs *const *cs, const double *const *targets,
+                      float lr, double *loss, sq_stream_t stream);
+
 /* A_hom without allocating: for callers that may not allocate device memory
  * when they need the result (code running under CUDA stream capture, or a
  * framework that hands out all device memory from its own pool). The paper has

@@ -7,7 +7,8 @@ raises.
 """
 from .sq import (  # noqa: F401
     SQ_EBADGUESS, SQ_ECUDA, SQ_EINVAL, SQ_ENOCONV, SQ_ENOMEM, SQ_ETIMEOUT, SQ_FP32_REFINE, SQ_FP64, SQ_OK,
-    Batch, Coeffs, Precond, SqError, Workspace, sq_batch_create, sq_pcg_solve_batched, lib_path, load_library, sq_apply_operator, sq_apply_operator_f32,
+    Batch, Coeffs, Net, sq_net_create, sq_net_grads, sq_net_params, sq_net_predict, sq_net_set_params,
+    sq_net_train_step, Precond, SqError, Workspace, sq_batch_create, sq_pcg_solve_batched, lib_path, load_library, sq_apply_operator, sq_apply_operator_f32,
     sq_apply_precond, sq_apply_precond_f32, sq_build_coeffs, sq_coeffs_cells, sq_coeffs_from_host,
     sq_coeffs_regenerate, sq_coeffs_shape, sq_coeffs_upload, sq_homogenized_matrix, sq_homogenized_matrix_noalloc, sq_profile_class_name,
     sq_profile_enable, sq_profile_read, sq_pcg_solve, sq_precond_setup, sq_rhs, sq_strerror,

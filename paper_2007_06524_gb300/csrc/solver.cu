@@ -325,14 +325,20 @@ int solve_fp64(const sq_coeffs *c, const sq_precond *pc, sq_workspace *w, int di
   const RedBuf rb = redbuf<double>(&w->d_st[0], w->d_partials);
   const CellsDev cd = cells_dev(c);
   SQ_LAUNCH(PC_SCALAR, s, (k_scalars_reset<<<1, 1, 0, s>>>(rb.st, tol * tol, max_iter), cudaGetLastError()));
+  Scalars *h = &w->h_st[0];
+  bool used_guess = false;
   if (x0) {
     if (x0 != psi) SQ_CK(cudaMemcpyAsync(psi, x0, sizeof(double) * n3, cudaMemcpyDeviceToDevice, s));
     SQ_LAUNCH(PC_RESID, s, (launch_stencil<double, double>(cd, ST_RESID, dir, psi, r, rb, FIN_RESID, false, s)));
-  } else {
+    // the residual judges the guess: keep it only if ||b - A x0|| < ||b||
+    int st = read_scalars(h, rb.st, s);
+    if (st != SQ_OK) return st;
+    used_guess = h->rr < h->bb;
+  }
+  if (!used_guess) {
     SQ_CK(cudaMemsetAsync(psi, 0, sizeof(double) * n3, s));
     SQ_LAUNCH(PC_RESID, s, (launch_stencil<double, double>(cd, ST_RHS, dir, nullptr, r, rb, FIN_RESID, false, s)));
   }
-  Scalars *h = &w->h_st[0];
   for (int restart = 0; restart < 4; ++restart) {
     int st = precond_first<double>(pc, r, Y, p, rb, s);
     if (st != SQ_OK) return st;
@@ -348,7 +354,7 @@ int solve_fp64(const sq_coeffs *c, const sq_precond *pc, sq_workspace *w, int di
   if (info) {
     info->iters = h->iter;
     info->outer_steps = 1;
-    info->used_guess = x0 ? 1 : 0;
+    info->used_guess = used_guess ? 1 : 0;
     info->relres = (h->bb > 0.0) ? std::sqrt(h->rr / h->bb) : 0.0;
     info->relres_true = (h->bb > 0.0) ? std::sqrt(h->rr_true / h->bb) : 0.0;
     info->status = (h->bb == 0.0 || info->relres_true <= tol) ? SQ_OK : SQ_ENOCONV;
@@ -366,12 +372,16 @@ int solve_fp32_refine(const sq_coeffs *c, const sq_precond *pc, sq_workspace *w,
   const CellsDev cd = cells_dev(c);
   const double tol_in = 1e-4;
   SQ_LAUNCH(PC_SCALAR, s, (k_scalars_reset<<<1, 1, 0, s>>>(ro.st, tol * tol, max_iter), cudaGetLastError()));
+  Scalars *ho = &w->h_st[0], *hi = &w->h_st[1];
+  bool used_guess = false;
   if (x0) {
     if (x0 != psi) SQ_CK(cudaMemcpyAsync(psi, x0, sizeof(double) * n3, cudaMemcpyDeviceToDevice, s));
-  } else {
-    SQ_CK(cudaMemsetAsync(psi, 0, sizeof(double) * n3, s));
+    SQ_LAUNCH(PC_RESID, s, (launch_stencil<double, float>(cd, ST_RESID, dir, psi, r, ro, FIN_RESID, false, s)));
+    int st = read_scalars(ho, ro.st, s);
+    if (st != SQ_OK) return st;
+    used_guess = ho->rr_true < ho->bb;  // keep the guess only if it reduces the residual
   }
-  Scalars *ho = &w->h_st[0], *hi = &w->h_st[1];
+  if (!used_guess) SQ_CK(cudaMemsetAsync(psi, 0, sizeof(double) * n3, s));
   int total_inner = 0, outer = 0;
   double relres_in = 0.0;
   for (;;) {
@@ -403,7 +413,7 @@ int solve_fp32_refine(const sq_coeffs *c, const sq_precond *pc, sq_workspace *w,
   if (info) {
     info->iters = total_inner;
     info->outer_steps = outer;
-    info->used_guess = x0 ? 1 : 0;
+    info->used_guess = used_guess ? 1 : 0;
     info->relres = relres_in;
     info->relres_true = rel;
     info->status = (ho->bb == 0.0 || rel <= tol) ? SQ_OK : SQ_ENOCONV;

@@ -1,0 +1,680 @@
+// Learned warm start: a periodic 3D convolutional net maps the coefficient
+// field to a first guess of the three correctors (an addition to the paper's
+// method; the PCG solve keeps judging the guess by its residual).
+//
+// Net: 6 layers of 3x3x3 periodic convolutions, 32 channels, GELU after the
+// first five; input 1 channel (the voxel coefficient, +1 high / -1 low),
+// output 3 channels (psi_1..3 / out_scale). Activations are BF16 in
+// channel-last layout [sample][voxel][32] (voxel = x3 + N x2 + N^2 x1), weights
+// BF16, accumulation FP32.
+//
+// Kernels:
+//  * conv_mma: implicit GEMM on the tensor cores (mma.sync m16n8k16 BF16, FP32
+//    accumulate). Block = 2 x 4 x 32 output voxels, one warp per 32-voxel row
+//    (two 16-row m-tiles) and all output channels; the input halo tile
+//    (4 x 6 x 34 voxels) and the weights sit in shared memory with padded row
+//    strides (conflict-free fragment loads). Epilogues: bias + GELU (stores
+//    pre-activation and activation), bias only (FP32 output channels), or
+//    plain (data gradient). The data gradient of a layer is the same
+//    convolution with the weights flipped in space and transposed in channels.
+//  * conv_in (layer 1, one input channel) and the weight gradients run on the
+//    FP32 pipes (SIMT); weight gradients are reduced deterministically.
+#include <cmath>
+#include <cstring>
+#include <new>
+#include <vector>
+
+#include <cuda_bf16.h>
+
+#include "common.cuh"
+
+namespace sq {
+namespace {
+
+constexpr int kC = 32;       // hidden channels
+constexpr int kTaps = 27;
+constexpr int kLayers = 6;
+constexpr int TZ = 2, TY = 4, TX = 32;  // output tile per block (8 warps)
+constexpr int HZ = TZ + 2, HY = TY + 2, HX = TX + 2;
+
+__device__ __forceinline__ float gelu(float z) { return 0.5f * z * (1.0f + erff(z * 0.70710678118654752f)); }
+__device__ __forceinline__ float gelu_grad(float z) {
+  return 0.5f * (1.0f + erff(z * 0.70710678118654752f)) + z * 0.39894228040143268f * expf(-0.5f * z * z);
+}
+
+__device__ __forceinline__ void mma16816(float (&d)[4], const uint32_t (&a)[4], const uint32_t (&b)[2]) {
+  asm volatile(
+      "mma.sync.aligned.m16n8k16.row.col.f32.bf16.bf16.f32 {%0,%1,%2,%3}, {%4,%5,%6,%7}, {%8,%9}, "
+      "{%0,%1,%2,%3};\n"
+      : "+f"(d[0]), "+f"(d[1]), "+f"(d[2]), "+f"(d[3])
+      : "r"(a[0]), "r"(a[1]), "r"(a[2]), "r"(a[3]), "r"(b[0]), "r"(b[1]));
+}
+
+__device__ __forceinline__ int wrap(int i, int N) { return i < 0 ? i + N : (i >= N ? i - N : i); }
+
+enum Epi { EPI_GELU = 0, EPI_OUT = 1, EPI_PLAIN = 2 };
+
+// out = conv(in, W) over one output tile. CIN in {16, 32} input channels (the
+// stored channel count of `in` is CSTR), COUT in {8, 32}. Weights wt are
+// [tap][COUT][CIN] BF16 (input channel fastest).
+template <int CIN, int CSTR, int COUT, int EPI>
+__global__ void __launch_bounds__(256) k_conv_mma(const __nv_bfloat16 *__restrict__ in,
+                                                  const __nv_bfloat16 *__restrict__ wt,
+                                                  const float *__restrict__ bias, __nv_bfloat16 *__restrict__ zout,
+                                                  __nv_bfloat16 *__restrict__ aout, float *__restrict__ fout,
+                                                  float out_scale, int N) {
+  constexpr int VW = CIN / 2 + 4;   // 32-bit words per staged voxel (padded: conflict-free)
+  constexpr int WW = CIN / 2 + 4;   // words per staged weight row
+  extern __shared__ __align__(16) uint32_t sm[];
+  uint32_t *s_in = sm;                          // HZ*HY*HX voxels x VW words
+  uint32_t *s_w = sm + HZ * HY * HX * VW;       // 27*COUT rows x WW words
+  const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+  const int ntx = N / TX, nty = N / TY, ntz = N / TZ;
+  int b = blockIdx.x;
+  const int tx = b % ntx; b /= ntx;
+  const int ty = b % nty; b /= nty;
+  const int tz = b % ntz; b /= ntz;
+  const int sample = b;
+  const size_t NN = (size_t)N * N, N3 = NN * N;
+  const int x0 = tx * TX, y0 = ty * TY, z0 = tz * TZ;
+  // weights -> smem
+  for (int e = tid; e < kTaps * COUT * (CIN / 2); e += 256) {
+    const int row = e / (CIN / 2), w = e - row * (CIN / 2);
+    s_w[row * WW + w] = reinterpret_cast<const uint32_t *>(wt)[e];
+  }
+  // input halo tile -> smem (periodic)
+  const uint32_t *gin = reinterpret_cast<const uint32_t *>(in) + (size_t)sample * N3 * (CSTR / 2);
+  for (int e = tid; e < HZ * HY * HX * (CIN / 2); e += 256) {
+    const int v = e / (CIN / 2), w = e - v * (CIN / 2);
+    const int hx = v % HX, hy = (v / HX) % HY, hz = v / (HX * HY);
+    const int gx = wrap(x0 + hx - 1, N), gy = wrap(y0 + hy - 1, N), gz = wrap(z0 + hz - 1, N);
+    s_in[v * VW + w] = gin[((size_t)gz * NN + (size_t)gy * N + gx) * (CSTR / 2) + w];
+  }
+  __syncthreads();
+  const int g = lane >> 2, t4 = lane & 3;
+  const int wz = warp / TY, wy = warp % TY;  // warp's output row: (z0+wz, y0+wy, x0..x0+31)
+  constexpr int NT = COUT / 8;
+  float acc[2][NT][4];
+#pragma unroll
+  for (int m = 0; m < 2; ++m)
+#pragma unroll
+    for (int nt = 0; nt < NT; ++nt)
+#pragma unroll
+      for (int i = 0; i < 4; ++i) acc[m][nt][i] = 0.f;
+  for (int tap = 0; tap < kTaps; ++tap) {
+    const int dz = tap / 9, dy = (tap / 3) % 3, dx = tap % 3;
+    const int hbase = ((wz + dz) * HY + (wy + dy)) * HX + dx;
+#pragma unroll
+    for (int kc = 0; kc < CIN / 16; ++kc) {
+      uint32_t af[2][4];
+#pragma unroll
+      for (int m = 0; m < 2; ++m) {
+        const int v0 = hbase + m * 16 + g;
+        af[m][0] = s_in[v0 * VW + kc * 8 + t4];
+        af[m][1] = s_in[(v0 + 8) * VW + kc * 8 + t4];
+        af[m][2] = s_in[v0 * VW + kc * 8 + 4 + t4];
+        af[m][3] = s_in[(v0 + 8) * VW + kc * 8 + 4 + t4];
+      }
+#pragma unroll
+      for (int nt = 0; nt < NT; ++nt) {
+        const int row = tap * COUT + nt * 8 + g;
+        uint32_t bf[2];
+        bf[0] = s_w[row * WW + kc * 8 + t4];
+        bf[1] = s_w[row * WW + kc * 8 + 4 + t4];
+        mma16816(acc[0][nt], af[0], bf);
+        mma16816(acc[1][nt], af[1], bf);
+      }
+    }
+  }
+  // epilogue
+  const int z = z0 + wz, y = y0 + wy;
+#pragma unroll
+  for (int m = 0; m < 2; ++m) {
+#pragma unroll
+    for (int half = 0; half < 2; ++half) {
+      const int x = x0 + m * 16 + g + half * 8;
+      const size_t vox = (size_t)z * NN + (size_t)y * N + x;
+#pragma unroll
+      for (int nt = 0; nt < NT; ++nt) {
+        const int co = nt * 8 + 2 * t4;
+        float v0 = acc[m][nt][half * 2 + 0], v1 = acc[m][nt][half * 2 + 1];
+        if (EPI != EPI_PLAIN) {  // bias has COUT entries, or 3 for the output layer
+          const int nb = (EPI == EPI_OUT) ? 3 : COUT;
+          if (co < nb) v0 += bias[co];
+          if (co + 1 < nb) v1 += bias[co + 1];
+        }
+        if (EPI == EPI_GELU) {
+          const size_t o = ((size_t)sample * N3 + vox) * COUT + co;
+          *reinterpret_cast<__nv_bfloat162 *>(zout + o) = __floats2bfloat162_rn(v0, v1);
+          *reinterpret_cast<__nv_bfloat162 *>(aout + o) = __floats2bfloat162_rn(gelu(v0), gelu(v1));
+        } else if (EPI == EPI_PLAIN) {
+          const size_t o = ((size_t)sample * N3 + vox) * COUT + co;
+          *reinterpret_cast<__nv_bfloat162 *>(aout + o) = __floats2bfloat162_rn(v0, v1);
+        } else {  // EPI_OUT: channels 0..2 -> FP32 fields [sample][channel][voxel]
+          if (co < 3) fout[((size_t)sample * 3 + co) * N3 + vox] = v0 * out_scale;
+          if (co + 1 < 3) fout[((size_t)sample * 3 + co + 1) * N3 + vox] = v1 * out_scale;
+        }
+      }
+    }
+  }
+}
+
+// Layer 1 (one input channel, FP32 feature): z = sum_tap w[tap][co] f + b.
+__global__ void __launch_bounds__(256) k_conv_in(const float *__restrict__ f, const float *__restrict__ w,
+                                                 const float *__restrict__ bias, __nv_bfloat16 *__restrict__ zout,
+                                                 __nv_bfloat16 *__restrict__ aout, int N, long long total) {
+  __shared__ float sw[kTaps * kC];
+  __shared__ float sb[kC];
+  for (int e = threadIdx.x; e < kTaps * kC; e += 256) sw[e] = w[e];
+  if (threadIdx.x < kC) sb[threadIdx.x] = bias[threadIdx.x];
+  __syncthreads();
+  const long long i = blockIdx.x * 256LL + threadIdx.x;
+  if (i >= total) return;
+  const size_t N3 = (size_t)N * N * N;
+  const long long sample = i / N3;
+  const size_t vox = i - sample * N3;
+  const int x = vox % N, y = (vox / N) % N, z = vox / ((size_t)N * N);
+  float nb[kTaps];
+  for (int tap = 0; tap < kTaps; ++tap) {
+    const int dz = tap / 9 - 1, dy = (tap / 3) % 3 - 1, dx = tap % 3 - 1;
+    nb[tap] = f[sample * N3 + (size_t)wrap(z + dz, N) * N * N + (size_t)wrap(y + dy, N) * N + wrap(x + dx, N)];
+  }
+  for (int co = 0; co < kC; co += 2) {
+    float v0 = sb[co], v1 = sb[co + 1];
+    for (int tap = 0; tap < kTaps; ++tap) {
+      v0 = fmaf(sw[tap * kC + co], nb[tap], v0);
+      v1 = fmaf(sw[tap * kC + co + 1], nb[tap], v1);
+    }
+    const size_t o = (size_t)i * kC + co;
+    *reinterpret_cast<__nv_bfloat162 *>(zout + o) = __floats2bfloat162_rn(v0, v1);
+    *reinterpret_cast<__nv_bfloat162 *>(aout + o) = __floats2bfloat162_rn(gelu(v0), gelu(v1));
+  }
+}
+
+// Input feature: voxel coefficient as +1 (high) / -1 (low), from the cell phases.
+__global__ void k_feature(const uint8_t *__restrict__ phase, int L, int n, float *__restrict__ f) {
+  const int N = L * n;
+  const size_t N3 = (size_t)N * N * N;
+  const size_t i = blockIdx.x * 256ULL + threadIdx.x;
+  if (i >= N3) return;
+  const int x = i % N, y = (i / N) % N, z = i / ((size_t)N * N);
+  f[i] = phase[((size_t)(z / n) * L + y / n) * L + x / n] ? 1.f : -1.f;
+}
+
+// FP32 fields [3][N3] -> three FP64 correctors
+__global__ void k_to_psi(const float *__restrict__ o, double *p0, double *p1, double *p2, long long N3) {
+  const long long i = blockIdx.x * 256LL + threadIdx.x;
+  if (i >= N3) return;
+  p0[i] = o[i];
+  p1[i] = o[N3 + i];
+  p2[i] = o[2 * N3 + i];
+}
+
+// ----------------------------------------------------------------- training
+// Loss L = sum((y - t)^2) / out_scale^2 over samples x 3 channels x voxels
+// (Adam is invariant to the overall gradient scale). Writes dL/d(conv6 out)
+// = 2 (y - t) / out_scale as BF16 [sample][voxel][16] (channels 3..15 zero)
+// and per-block loss partials.
+__global__ void __launch_bounds__(256) k_loss_grad(const float *__restrict__ y, const float *__restrict__ tgt,
+                                                   __nv_bfloat16 *__restrict__ g, float inv_scale,
+                                                   double *__restrict__ partials, long long N3, int B) {
+  const long long i = blockIdx.x * 256LL + threadIdx.x;  // sample * N3 + voxel
+  Accum<float> acc;
+  if (i < (long long)B * N3) {
+    const long long smp = i / N3, vox = i - smp * N3;
+    uint32_t w[8];
+#pragma unroll
+    for (int k = 0; k < 8; ++k) w[k] = 0u;
+    for (int c = 0; c < 3; ++c) {
+      const float e = (y[(smp * 3 + c) * N3 + vox] - tgt[(smp * 3 + c) * N3 + vox]) * inv_scale;
+      acc.add(e * e);
+      const __nv_bfloat16 gb = __float2bfloat16_rn(2.f * e);
+      const uint32_t bits = (uint32_t)(*reinterpret_cast<const unsigned short *>(&gb));
+      w[c >> 1] |= bits << (16 * (c & 1));
+    }
+    uint4 *dst = reinterpret_cast<uint4 *>(g + i * 16);
+    dst[0] = make_uint4(w[0], w[1], w[2], w[3]);
+    dst[1] = make_uint4(w[4], w[5], w[6], w[7]);
+  }
+  __shared__ double sh[8];
+  double v = warp_sum(acc.get());
+  if ((threadIdx.x & 31) == 0) sh[threadIdx.x >> 5] = v;
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    double t = 0.0;
+    for (int k = 0; k < 8; ++k) t += sh[k];
+    partials[blockIdx.x] = t;
+  }
+}
+
+// gz = ga * gelu'(z), 32 channels BF16
+__global__ void k_gelu_bwd(const __nv_bfloat16 *__restrict__ ga, const __nv_bfloat16 *__restrict__ z,
+                           __nv_bfloat16 *__restrict__ gz, long long n2) {
+  const long long i = blockIdx.x * 256LL + threadIdx.x;  // pairs
+  if (i >= n2) return;
+  const float2 a = __bfloat1622float2(reinterpret_cast<const __nv_bfloat162 *>(ga)[i]);
+  const float2 zz = __bfloat1622float2(reinterpret_cast<const __nv_bfloat162 *>(z)[i]);
+  reinterpret_cast<__nv_bfloat162 *>(gz)[i] = __floats2bfloat162_rn(a.x * gelu_grad(zz.x), a.y * gelu_grad(zz.y));
+}
+
+// Weight (and bias, tap 27) gradient partials: dW[tap][co][ci] = sum_v
+// A[v + off_tap][ci] G[v][co] over the voxels of one chunk (FP32 SIMT).
+// A: BF16 [B][N3][32] (CA = 32) or FP32 feature [B][N3] (CA = 1).
+// G: BF16 [B][N3][CGS], CG real channels.
+template <int CA, int CG>
+__global__ void __launch_bounds__(256) k_dw(const void *__restrict__ A, const __nv_bfloat16 *__restrict__ G, int CGS,
+                                            int N, long long total, int chunk, float *__restrict__ partials) {
+  constexpr int V = 64;
+  __shared__ float sa[V][CA + 1];
+  __shared__ float sg[V][CG + 1];
+  const int tap = blockIdx.y;
+  const long long v0 = (long long)blockIdx.x * chunk;
+  const long long v1 = (v0 + chunk < total) ? v0 + chunk : total;
+  const size_t N3 = (size_t)N * N * N;
+  const int dz = tap / 9 - 1, dy = (tap / 3) % 3 - 1, dx = tap % 3 - 1;
+  constexpr int NOUT = CG * CA;
+  constexpr int PER = (NOUT + 255) / 256;
+  float acc[PER];
+#pragma unroll
+  for (int k = 0; k < PER; ++k) acc[k] = 0.f;
+  for (long long vb = v0; vb < v1; vb += V) {
+    __syncthreads();
+    for (int e = threadIdx.x; e < V * CA; e += 256) {
+      const int vi = e / CA, ci = e - vi * CA;
+      const long long v = vb + vi;
+      float val = 0.f;
+      if (v < v1) {
+        if (tap == 27) {
+          val = (ci == 0) ? 1.f : 0.f;
+        } else {
+          const long long smp = v / N3;
+          const size_t vox = v - smp * N3;
+          const int x = vox % N, y = (vox / N) % N, z = vox / ((size_t)N * N);
+          const size_t nb = smp * N3 + (size_t)wrap(z + dz, N) * N * N + (size_t)wrap(y + dy, N) * N + wrap(x + dx, N);
+          if (CA == 1)
+            val = reinterpret_cast<const float *>(A)[nb];
+          else
+            val = __bfloat162float(reinterpret_cast<const __nv_bfloat16 *>(A)[nb * CA + ci]);
+        }
+      }
+      sa[vi][ci] = val;
+    }
+    for (int e = threadIdx.x; e < V * CG; e += 256) {
+      const int vi = e / CG, co = e - vi * CG;
+      const long long v = vb + vi;
+      sg[vi][co] = (v < v1) ? __bfloat162float(G[v * CGS + co]) : 0.f;
+    }
+    __syncthreads();
+#pragma unroll
+    for (int k = 0; k < PER; ++k) {
+      const int o = threadIdx.x + k * 256;
+      if (o < NOUT) {
+        const int co = o / CA, ci = o - co * CA;
+        float s = acc[k];
+        for (int vi = 0; vi < V; ++vi) s = fmaf(sa[vi][ci], sg[vi][co], s);
+        acc[k] = s;
+      }
+    }
+  }
+#pragma unroll
+  for (int k = 0; k < PER; ++k) {
+    const int o = threadIdx.x + k * 256;
+    if (o < NOUT) partials[((size_t)blockIdx.x * 28 + tap) * NOUT + o] = acc[k];
+  }
+}
+
+// Sum of the chunk partials (fixed order) -> weight gradient [27][CG][CA]
+// (taps 0..26) and bias gradient [CG] (tap 27, input slot 0).
+__global__ void k_dw_reduce(const float *__restrict__ partials, int nchunk, int nout, int ca, float *__restrict__ gw,
+                            float *__restrict__ gb) {
+  const int o = blockIdx.x * 256 + threadIdx.x;  // over 28 * nout
+  if (o >= 28 * nout) return;
+  double s = 0.0;
+  for (int c = 0; c < nchunk; ++c) s += partials[(size_t)c * 28 * nout + o];
+  const int tap = o / nout, r = o - tap * nout;
+  if (tap < 27) {
+    gw[o] = (float)s;
+  } else if (r % ca == 0) {
+    gb[r / ca] = (float)s;
+  }
+}
+
+__global__ void k_adam(float *__restrict__ w, const float *__restrict__ g, float *__restrict__ m, float *__restrict__ v,
+                       int n, float lr, float b1, float b2, float eps, float c1, float c2) {
+  const int i = blockIdx.x * 256 + threadIdx.x;
+  if (i >= n) return;
+  const float gi = g[i];
+  const float mi = b1 * m[i] + (1.f - b1) * gi;
+  const float vi = b2 * v[i] + (1.f - b2) * gi * gi;
+  m[i] = mi;
+  v[i] = vi;
+  w[i] -= lr * (mi / c1) / (sqrtf(vi / c2) + eps);
+}
+
+// BF16 copies of a layer's FP32 weights [27][cout][cin]: forward layout
+// [tap][COUTP][CINP] and data-gradient layout [tap'][CINP2=cin][COUTP2] with
+// tap' = 26 - tap (spatial flip) and channels transposed; padding rows zero.
+__global__ void k_pack_weights(const float *__restrict__ w, int cout, int cin, int coutp, __nv_bfloat16 *__restrict__ wf,
+                               __nv_bfloat16 *__restrict__ wb, int coutp2) {
+  const int i = blockIdx.x * 256 + threadIdx.x;
+  const int nf = 27 * coutp * cin;
+  if (i < nf) {
+    const int tap = i / (coutp * cin), r = i - tap * coutp * cin, co = r / cin, ci = r - co * cin;
+    wf[i] = __float2bfloat16_rn(co < cout ? w[(tap * cout + co) * cin + ci] : 0.f);
+  }
+  if (wb) {
+    const int nb = 27 * cin * coutp2;
+    if (i < nb) {
+      const int tp = i / (cin * coutp2), r = i - tp * cin * coutp2, ci = r / coutp2, co = r - ci * coutp2;
+      const int tap = 26 - tp;
+      wb[i] = __float2bfloat16_rn(co < cout ? w[(tap * cout + co) * cin + ci] : 0.f);
+    }
+  }
+}
+
+__global__ void k_target_f32(const double *__restrict__ t0, const double *__restrict__ t1, const double *__restrict__ t2,
+                             float *__restrict__ out, long long N3) {
+  const long long i = blockIdx.x * 256LL + threadIdx.x;
+  if (i >= N3) return;
+  out[i] = (float)t0[i];
+  out[N3 + i] = (float)t1[i];
+  out[2 * N3 + i] = (float)t2[i];
+}
+
+}  // namespace
+}  // namespace sq
+
+using namespace sq;
+
+// Parameter layout (FP32 master): per layer l, weights [27][cout][cin] then bias [cout].
+struct sq_net {
+  int N = 0, max_batch = 0;
+  double out_scale = 1.0;
+  int cin[kLayers], cout[kLayers];
+  long long woff[kLayers], boff[kLayers], nparam = 0;
+  float *d_w = nullptr, *d_g = nullptr, *d_m = nullptr, *d_v = nullptr;
+  __nv_bfloat16 *d_wf[kLayers] = {nullptr}, *d_wb[kLayers] = {nullptr};
+  float *d_f = nullptr, *d_y = nullptr, *d_t = nullptr;
+  __nv_bfloat16 *d_z[5] = {nullptr}, *d_a[5] = {nullptr};
+  __nv_bfloat16 *d_g6 = nullptr, *d_ga = nullptr, *d_gz = nullptr;
+  float *d_dwpart = nullptr;
+  double *d_lpart = nullptr, *h_lpart = nullptr;
+  int nchunk = 0, chunk = 0;
+  int step = 0;
+  std::vector<void *> allocs;
+};
+
+namespace {
+
+#define SQN_CK(call)                        \
+  do {                                      \
+    if ((call) != cudaSuccess) return SQ_ECUDA; \
+  } while (0)
+
+template <int CIN, int CSTR, int COUT, int EPI>
+int conv(const sq_net *net, int B, const __nv_bfloat16 *in, const __nv_bfloat16 *wt, const float *bias,
+         __nv_bfloat16 *z, __nv_bfloat16 *a, float *fo, cudaStream_t s) {
+  const int N = net->N;
+  const size_t smem = (size_t)(HZ * HY * HX * (CIN / 2 + 4) + kTaps * COUT * (CIN / 2 + 4)) * 4;
+  auto kern = k_conv_mma<CIN, CSTR, COUT, EPI>;
+  SQN_CK(cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+  const int blocks = (N / TX) * (N / TY) * (N / TZ) * B;
+  kern<<<blocks, 256, smem, s>>>(in, wt, bias, z, a, fo, (float)net->out_scale, N);
+  SQN_CK(cudaGetLastError());
+  return SQ_OK;
+}
+
+int pack_all(sq_net *net, cudaStream_t s) {
+  for (int l = 1; l < kLayers; ++l) {
+    const int coutp = (l == kLayers - 1) ? 8 : kC;
+    const int coutp2 = (l == kLayers - 1) ? 16 : kC;
+    const int n = 27 * std::max(coutp * net->cin[l], net->cin[l] * coutp2);
+    k_pack_weights<<<(n + 255) / 256, 256, 0, s>>>(net->d_w + net->woff[l], net->cout[l], net->cin[l], coutp,
+                                                   net->d_wf[l], net->d_wb[l], coutp2);
+    SQN_CK(cudaGetLastError());
+  }
+  return SQ_OK;
+}
+
+int forward(sq_net *net, int B, cudaStream_t s) {
+  const int N = net->N;
+  const long long N3 = (long long)N * N * N, tot = (long long)B * N3;
+  k_conv_in<<<(unsigned)((tot + 255) / 256), 256, 0, s>>>(net->d_f, net->d_w + net->woff[0], net->d_w + net->boff[0],
+                                                          net->d_z[0], net->d_a[0], N, tot);
+  SQN_CK(cudaGetLastError());
+  int st;
+  for (int l = 1; l < 5; ++l) {
+    st = conv<32, 32, 32, EPI_GELU>(net, B, net->d_a[l - 1], net->d_wf[l], net->d_w + net->boff[l], net->d_z[l],
+                                    net->d_a[l], nullptr, s);
+    if (st != SQ_OK) return st;
+  }
+  return conv<32, 32, 8, EPI_OUT>(net, B, net->d_a[4], net->d_wf[5], net->d_w + net->boff[5], nullptr, nullptr,
+                                  net->d_y, s);
+}
+
+template <int CA, int CG>
+int weight_grad(sq_net *net, int B, const void *A, const __nv_bfloat16 *G, int CGS, int layer, cudaStream_t s) {
+  const int N = net->N;
+  const long long tot = (long long)B * N * N * N;
+  const int nchunk = (int)((tot + net->chunk - 1) / net->chunk);
+  if (nchunk > net->nchunk) return SQ_EINVAL;
+  k_dw<CA, CG><<<dim3(nchunk, 28), 256, 0, s>>>(A, G, CGS, N, tot, net->chunk, net->d_dwpart);
+  SQN_CK(cudaGetLastError());
+  const int nout = CG * CA;
+  k_dw_reduce<<<(28 * nout + 255) / 256, 256, 0, s>>>(net->d_dwpart, nchunk, nout, CA, net->d_g + net->woff[layer],
+                                                      net->d_g + net->boff[layer]);
+  SQN_CK(cudaGetLastError());
+  return SQ_OK;
+}
+
+int backward(sq_net *net, int B, cudaStream_t s) {
+  const int N = net->N;
+  const long long N3 = (long long)N * N * N;
+  const long long n2 = (long long)B * N3 * kC / 2;
+  int st;
+  // layer 6 (32 -> 3): weights from a5 and g6, data gradient g6 -> ga
+  if ((st = weight_grad<32, 3>(net, B, net->d_a[4], net->d_g6, 16, 5, s)) != SQ_OK) return st;
+  if ((st = conv<16, 16, 32, EPI_PLAIN>(net, B, net->d_g6, net->d_wb[5], nullptr, nullptr, net->d_ga, nullptr, s)) !=
+      SQ_OK)
+    return st;
+  // layers 5..2 (32 -> 32)
+  for (int l = 4; l >= 1; --l) {
+    k_gelu_bwd<<<(unsigned)((n2 + 255) / 256), 256, 0, s>>>(net->d_ga, net->d_z[l], net->d_gz, n2);
+    SQN_CK(cudaGetLastError());
+    if ((st = weight_grad<32, 32>(net, B, net->d_a[l - 1], net->d_gz, 32, l, s)) != SQ_OK) return st;
+    if ((st = conv<32, 32, 32, EPI_PLAIN>(net, B, net->d_gz, net->d_wb[l], nullptr, nullptr, net->d_ga, nullptr, s)) !=
+        SQ_OK)
+      return st;
+  }
+  // layer 1 (1 -> 32): weights only
+  k_gelu_bwd<<<(unsigned)((n2 + 255) / 256), 256, 0, s>>>(net->d_ga, net->d_z[0], net->d_gz, n2);
+  SQN_CK(cudaGetLastError());
+  return weight_grad<1, 32>(net, B, net->d_f, net->d_gz, 32, 0, s);
+}
+
+// SplitMix64-driven normal draws (Box-Muller) for the initial weights.
+struct HostRng {
+  uint64_t s;
+  uint64_t next() {
+    uint64_t z = (s += 0x9E3779B97F4A7C15ull);
+    z = (z ^ (z >> 30)) * 0xBF58476D1CE4E5B9ull;
+    z = (z ^ (z >> 27)) * 0x94D049BB133111EBull;
+    return z ^ (z >> 31);
+  }
+  double uniform() { return ((next() >> 11) + 0.5) * (1.0 / 9007199254740992.0); }
+  double normal() { return std::sqrt(-2.0 * std::log(uniform())) * std::cos(6.283185307179586 * uniform()); }
+};
+
+template <typename T>
+T *nalloc(sq_net *net, size_t count, bool *ok) {
+  void *p = nullptr;
+  if (cudaMalloc(&p, count * sizeof(T)) != cudaSuccess) {
+    *ok = false;
+    return nullptr;
+  }
+  net->allocs.push_back(p);
+  return static_cast<T *>(p);
+}
+
+int feature_all(sq_net *net, int B, const sq_coeffs *const *cs, cudaStream_t s) {
+  const long long N3 = (long long)net->N * net->N * net->N;
+  for (int b = 0; b < B; ++b) {
+    CellsDev c;
+    if (coeffs_view(cs[b], &c) != SQ_OK || c.N != net->N) return SQ_EINVAL;
+    k_feature<<<(unsigned)((N3 + 255) / 256), 256, 0, s>>>(c.phase, c.L, c.n, net->d_f + b * N3);
+    SQN_CK(cudaGetLastError());
+  }
+  return SQ_OK;
+}
+
+}  // namespace
+
+extern "C" {
+
+int sq_net_create(int N, int max_batch, uint64_t seed, double out_scale, sq_net **out) {
+  if (!out) return SQ_EINVAL;
+  *out = nullptr;
+  if (N < 32 || N > 128 || N % 32 != 0 || max_batch < 1 || max_batch > 64 || !(out_scale > 0.0)) return SQ_EINVAL;
+  sq_net *net = new (std::nothrow) sq_net();
+  if (!net) return SQ_ENOMEM;
+  net->N = N;
+  net->max_batch = max_batch;
+  net->out_scale = out_scale;
+  long long off = 0;
+  for (int l = 0; l < kLayers; ++l) {
+    net->cin[l] = (l == 0) ? 1 : kC;
+    net->cout[l] = (l == kLayers - 1) ? 3 : kC;
+    net->woff[l] = off;
+    off += 27LL * net->cin[l] * net->cout[l];
+    net->boff[l] = off;
+    off += net->cout[l];
+  }
+  net->nparam = off;
+  const size_t N3 = (size_t)N * N * N, BN = N3 * max_batch;
+  bool ok = true;
+  net->d_w = nalloc<float>(net, off, &ok);
+  net->d_g = nalloc<float>(net, off, &ok);
+  net->d_m = nalloc<float>(net, off, &ok);
+  net->d_v = nalloc<float>(net, off, &ok);
+  for (int l = 1; l < kLayers; ++l) {
+    const int coutp = (l == kLayers - 1) ? 8 : kC, coutp2 = (l == kLayers - 1) ? 16 : kC;
+    net->d_wf[l] = nalloc<__nv_bfloat16>(net, 27 * coutp * net->cin[l], &ok);
+    net->d_wb[l] = nalloc<__nv_bfloat16>(net, 27 * net->cin[l] * coutp2, &ok);
+  }
+  net->d_f = nalloc<float>(net, BN, &ok);
+  net->d_y = nalloc<float>(net, 3 * BN, &ok);
+  net->d_t = nalloc<float>(net, 3 * BN, &ok);
+  for (int l = 0; l < 5; ++l) {
+    net->d_z[l] = nalloc<__nv_bfloat16>(net, BN * kC, &ok);
+    net->d_a[l] = nalloc<__nv_bfloat16>(net, BN * kC, &ok);
+  }
+  net->d_g6 = nalloc<__nv_bfloat16>(net, BN * 16, &ok);
+  net->d_ga = nalloc<__nv_bfloat16>(net, BN * kC, &ok);
+  net->d_gz = nalloc<__nv_bfloat16>(net, BN * kC, &ok);
+  net->chunk = 8192;
+  net->nchunk = (int)((BN + net->chunk - 1) / net->chunk);
+  net->d_dwpart = nalloc<float>(net, (size_t)net->nchunk * 28 * kC * kC, &ok);
+  const int lblocks = (int)((BN + 255) / 256);
+  net->d_lpart = nalloc<double>(net, lblocks, &ok);
+  if (ok && cudaMallocHost(&net->h_lpart, sizeof(double) * lblocks) != cudaSuccess) ok = false;
+  if (!ok) {
+    sq_net_destroy(net);
+    return SQ_ENOMEM;
+  }
+  // He-normal weights (last layer scaled down so the first guess is near zero), zero biases
+  std::vector<float> w(off, 0.f);
+  HostRng rng{seed};
+  for (int l = 0; l < kLayers; ++l) {
+    const double sd = std::sqrt(2.0 / (27.0 * net->cin[l])) * ((l == kLayers - 1) ? 0.1 : 1.0);
+    for (long long i = 0; i < 27LL * net->cin[l] * net->cout[l]; ++i) w[net->woff[l] + i] = (float)(sd * rng.normal());
+  }
+  if (sq_net_set_params(net, w.data(), off) != SQ_OK) {
+    sq_net_destroy(net);
+    return SQ_ECUDA;
+  }
+  *out = net;
+  return SQ_OK;
+}
+
+void sq_net_destroy(sq_net *net) {
+  if (!net) return;
+  for (void *p : net->allocs) cudaFree(p);
+  if (net->h_lpart) cudaFreeHost(net->h_lpart);
+  delete net;
+}
+
+int sq_net_params(const sq_net *net, float *host, int64_t *count) {
+  if (!net) return SQ_EINVAL;
+  if (count) *count = net->nparam;
+  if (host) SQN_CK(cudaMemcpy(host, net->d_w, sizeof(float) * net->nparam, cudaMemcpyDeviceToHost));
+  return SQ_OK;
+}
+
+int sq_net_grads(const sq_net *net, float *host, int64_t count) {
+  if (!net || !host || count != net->nparam) return SQ_EINVAL;
+  SQN_CK(cudaMemcpy(host, net->d_g, sizeof(float) * count, cudaMemcpyDeviceToHost));
+  return SQ_OK;
+}
+
+int sq_net_set_params(sq_net *net, const float *host, int64_t count) {
+  if (!net || !host || count != net->nparam) return SQ_EINVAL;
+  SQN_CK(cudaMemcpy(net->d_w, host, sizeof(float) * count, cudaMemcpyHostToDevice));
+  SQN_CK(cudaMemset(net->d_m, 0, sizeof(float) * count));
+  SQN_CK(cudaMemset(net->d_v, 0, sizeof(float) * count));
+  net->step = 0;
+  int st = pack_all(net, 0);
+  if (st != SQ_OK) return st;
+  SQN_CK(cudaDeviceSynchronize());
+  return SQ_OK;
+}
+
+int sq_net_predict(sq_net *net, const sq_coeffs *c, double *psi0, double *psi1, double *psi2, sq_stream_t stream) {
+  if (!net || !c || !psi0 || !psi1 || !psi2) return SQ_EINVAL;
+  cudaStream_t s = reinterpret_cast<cudaStream_t>(stream);
+  int st = feature_all(net, 1, &c, s);
+  if (st != SQ_OK) return st;
+  if ((st = forward(net, 1, s)) != SQ_OK) return st;
+  const long long N3 = (long long)net->N * net->N * net->N;
+  k_to_psi<<<(unsigned)((N3 + 255) / 256), 256, 0, s>>>(net->d_y, psi0, psi1, psi2, N3);
+  SQN_CK(cudaGetLastError());
+  return SQ_OK;
+}
+
+int sq_net_train_step(sq_net *net, int batch, const sq_coeffs *const *cs, const double *const *targets, float lr,
+                      double *loss, sq_stream_t stream) {
+  if (!net || !cs || !targets || batch < 1 || batch > net->max_batch || !(lr > 0.f)) return SQ_EINVAL;
+  cudaStream_t s = reinterpret_cast<cudaStream_t>(stream);
+  const long long N3 = (long long)net->N * net->N * net->N;
+  int st = feature_all(net, batch, cs, s);
+  if (st != SQ_OK) return st;
+  for (int b = 0; b < batch; ++b) {
+    if (!targets[3 * b] || !targets[3 * b + 1] || !targets[3 * b + 2]) return SQ_EINVAL;
+    k_target_f32<<<(unsigned)((N3 + 255) / 256), 256, 0, s>>>(targets[3 * b], targets[3 * b + 1],
+                                                              targets[3 * b + 2], net->d_t + 3 * b * N3, N3);
+    SQN_CK(cudaGetLastError());
+  }
+  if ((st = forward(net, batch, s)) != SQ_OK) return st;
+  const long long tot = (long long)batch * N3;
+  const int lblocks = (int)((tot + 255) / 256);
+  k_loss_grad<<<lblocks, 256, 0, s>>>(net->d_y, net->d_t, net->d_g6, (float)(1.0 / net->out_scale), net->d_lpart,
+                                      N3, batch);
+  SQN_CK(cudaGetLastError());
+  if ((st = backward(net, batch, s)) != SQ_OK) return st;
+  net->step += 1;
+  const float b1 = 0.9f, b2 = 0.999f;
+  const float c1 = 1.f - std::pow(b1, (float)net->step), c2 = 1.f - std::pow(b2, (float)net->step);
+  k_adam<<<(unsigned)((net->nparam + 255) / 256), 256, 0, s>>>(net->d_w, net->d_g, net->d_m, net->d_v,
+                                                               (int)net->nparam, lr, b1, b2, 1e-8f, c1, c2);
+  SQN_CK(cudaGetLastError());
+  if ((st = pack_all(net, s)) != SQ_OK) return st;
+  if (loss) {
+    SQN_CK(cudaMemcpyAsync(net->h_lpart, net->d_lpart, sizeof(double) * lblocks, cudaMemcpyDeviceToHost, s));
+    SQN_CK(cudaStreamSynchronize(s));
+    double t = 0.0;
+    for (int i = 0; i < lblocks; ++i) t += net->h_lpart[i];
+    *loss = t / (3.0 * (double)tot);
+  }
+  return SQ_OK;
+}
+
+}  // extern "C"

@@ -76,6 +76,13 @@ def load_library():
         "sq_apply_precond_f32": (i, [vp, vp, vp, vp, vp]),
         "sq_strerror": (C.c_char_p, [i]),
         "sq_batch_create": (i, [i, p(SolveDesc), p(vp), p(TileConfig), i, p(vp)]),
+        "sq_net_create": (i, [i, i, u64, d, p(vp)]),
+        "sq_net_destroy": (None, [vp]),
+        "sq_net_params": (i, [vp, vp, p(C.c_int64)]),
+        "sq_net_set_params": (i, [vp, vp, C.c_int64]),
+        "sq_net_grads": (i, [vp, vp, C.c_int64]),
+        "sq_net_predict": (i, [vp, vp, vp, vp, vp, vp]),
+        "sq_net_train_step": (i, [vp, i, p(vp), p(vp), C.c_float, p(d), vp]),
         "sq_batch_destroy": (None, [vp]),
         "sq_pcg_solve_batched": (i, [vp, d, i, p(SolveInfo), vp]),
     }
@@ -146,6 +153,10 @@ class Precond(_Handle):
 
 class Workspace(_Handle):
     _destroy = "sq_workspace_destroy"
+
+
+class Net(_Handle):
+    _destroy = "sq_net_destroy"
 
 
 class Batch(_Handle):
@@ -309,3 +320,48 @@ def sq_pcg_solve_batched(b: Batch, tol, max_iter, stream=None) -> list:
     st = load_library().sq_pcg_solve_batched(b, float(tol), int(max_iter), infos, _stream(stream))
     _check(st, "sq_pcg_solve_batched", allow=(SQ_ENOCONV,))
     return [{k: getattr(inf, k) for k, _ in SolveInfo._fields_} for inf in infos]
+
+
+def sq_net_create(N, max_batch, seed, out_scale) -> Net:
+    out = C.c_void_p()
+    _check(load_library().sq_net_create(int(N), int(max_batch), int(seed) & (2**64 - 1), float(out_scale),
+                                        C.byref(out)), "sq_net_create")
+    return Net(out)
+
+
+def sq_net_params(net: Net) -> np.ndarray:
+    n = C.c_int64()
+    _check(load_library().sq_net_params(net, None, C.byref(n)), "sq_net_params")
+    a = np.empty(n.value, dtype=np.float32)
+    _check(load_library().sq_net_params(net, a.ctypes.data_as(C.c_void_p), C.byref(n)), "sq_net_params")
+    return a
+
+
+def sq_net_set_params(net: Net, params):
+    a = np.ascontiguousarray(params, dtype=np.float32)
+    _check(load_library().sq_net_set_params(net, a.ctypes.data_as(C.c_void_p), a.size), "sq_net_set_params")
+
+
+def sq_net_grads(net: Net) -> np.ndarray:
+    n = C.c_int64()
+    _check(load_library().sq_net_params(net, None, C.byref(n)), "sq_net_params")
+    a = np.empty(n.value, dtype=np.float32)
+    _check(load_library().sq_net_grads(net, a.ctypes.data_as(C.c_void_p), a.size), "sq_net_grads")
+    return a
+
+
+def sq_net_predict(net: Net, c, psi0, psi1, psi2, stream=None):
+    _check(load_library().sq_net_predict(net, c, _ptr(psi0), _ptr(psi1), _ptr(psi2), _stream(stream)),
+           "sq_net_predict")
+
+
+def sq_net_train_step(net: Net, coeffs, targets, lr, stream=None) -> float:
+    """coeffs: list of B Coeffs; targets: list of B triples of float64 CUDA
+    tensors (psi_1..3). Returns the loss of the forward pass."""
+    B = len(coeffs)
+    carr = (C.c_void_p * B)(*[c.ptr.value for c in coeffs])
+    tarr = (C.c_void_p * (3 * B))(*[_ptr(t).value for tri in targets for t in tri])
+    loss = C.c_double()
+    _check(load_library().sq_net_train_step(net, B, carr, tarr, C.c_float(lr), C.byref(loss), _stream(stream)),
+           "sq_net_train_step")
+    return loss.value

@@ -1,0 +1,162 @@
+"""Learned warm start: the conv net kernels against a plain PyTorch FP32
+reference of the same ops (periodic 3x3x3 convolutions, GELU), with the BF16
+roundings of the kernels emulated; then the warm start inside the solver."""
+import numpy as np
+import pytest
+
+pytestmark = pytest.mark.gpu
+
+N_NET = 32
+
+
+@pytest.fixture(scope="module")
+def sq():
+    torch = pytest.importorskip("torch")
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    import __graft_entry__
+
+    __graft_entry__.build()
+    import paper_2007_06524_gb300 as pkg
+
+    return pkg
+
+
+def _layers():
+    cin = [1, 32, 32, 32, 32, 32]
+    cout = [32, 32, 32, 32, 32, 3]
+    offs, o = [], 0
+    for ci, co in zip(cin, cout):
+        offs.append((o, o + 27 * ci * co, ci, co))
+        o += 27 * ci * co + co
+    return offs, o
+
+
+def _bf16(x):
+    import torch
+
+    return x + (x.to(torch.bfloat16).to(torch.float32) - x).detach()
+
+
+def _reference(params, feats, out_scale):
+    """feats: (B,1,N,N,N) float32 -> (B,3,N,N,N); params: torch tensor (requires_grad ok)."""
+    import torch
+    import torch.nn.functional as F
+
+    offs, _ = _layers()
+    x = feats
+    for l, (wo, bo, ci, co) in enumerate(offs):
+        W = params[wo:wo + 27 * ci * co].reshape(3, 3, 3, co, ci).permute(3, 4, 0, 1, 2)
+        if l > 0:
+            W = _bf16(W)
+        b = params[bo:bo + co]
+        z = F.conv3d(F.pad(x, (1, 1, 1, 1, 1, 1), mode="circular"), W) + b[None, :, None, None, None]
+        if l < 5:
+            x = _bf16(F.gelu(z))
+        else:
+            return out_scale * z
+
+
+def _features(sq, c, L, n):
+    ph, _ = sq.sq_coeffs_cells(c)
+    V = np.repeat(np.repeat(np.repeat(ph, n, 0), n, 1), n, 2)
+    return np.where(V > 0, 1.0, -1.0).astype(np.float32)
+
+
+def test_forward_matches_reference(sq):
+    import torch
+
+    L, n = 8, 4
+    net = sq.sq_net_create(N_NET, 2, seed=7, out_scale=1.5)
+    p = sq.sq_net_params(net)
+    # bring the output layer to full scale so every layer matters
+    offs, _ = _layers()
+    wo, bo, ci, co = offs[5]
+    p[wo:bo] *= 10.0
+    p[bo:bo + co] = [0.1, -0.2, 0.3]
+    sq.sq_net_set_params(net, p)
+    c = sq.sq_build_coeffs(L, n, 11, 0.5, 1.0, 10.0)
+    outs = [torch.empty(N_NET ** 3, dtype=torch.float64, device="cuda") for _ in range(3)]
+    sq.sq_net_predict(net, c, *outs)
+    torch.cuda.synchronize()
+    got = np.stack([o.cpu().numpy().reshape(N_NET, N_NET, N_NET) for o in outs])
+    f = torch.from_numpy(_features(sq, c, L, n))[None, None]
+    ref = _reference(torch.from_numpy(p), f, 1.5)[0].detach().numpy()
+    err = np.linalg.norm(got - ref) / np.linalg.norm(ref)
+    assert err <= 1e-2, err
+
+
+def test_gradients_match_reference(sq):
+    import torch
+
+    L, n = 8, 4
+    net = sq.sq_net_create(N_NET, 2, seed=3, out_scale=2.0)
+    p = sq.sq_net_params(net)
+    offs, _ = _layers()
+    wo, bo, ci, co = offs[5]
+    p[wo:bo] *= 10.0
+    sq.sq_net_set_params(net, p)
+    cs = [sq.sq_build_coeffs(L, n, s, 0.5, 1.0, 10.0) for s in (21, 22)]
+    rng = np.random.default_rng(0)
+    tg = [[torch.from_numpy(rng.standard_normal(N_NET ** 3)).cuda() for _ in range(3)] for _ in cs]
+    loss = sq.sq_net_train_step(net, cs, tg, 1e-3)
+    g_gpu = sq.sq_net_grads(net)
+    P = torch.from_numpy(p).requires_grad_(True)
+    feats = torch.from_numpy(np.stack([_features(sq, c, L, n) for c in cs]))[:, None]
+    y = _reference(P, feats, 2.0)
+    t = torch.from_numpy(np.stack([np.stack([x.cpu().numpy().reshape(N_NET, N_NET, N_NET) for x in tri])
+                                   for tri in tg]).astype(np.float32))
+    lref = (((y - t) / 2.0) ** 2).sum()
+    lref.backward()
+    g_ref = P.grad.numpy()
+    assert abs(loss - lref.item() / (3 * 2 * N_NET ** 3)) <= 1e-3 * abs(loss)
+    for l, (wo, bo, ci, co) in enumerate(offs):
+        for a, b in ((wo, bo), (bo, bo + co)):
+            e = np.linalg.norm(g_gpu[a:b] - g_ref[a:b]) / max(np.linalg.norm(g_ref[a:b]), 1e-30)
+            assert e <= 5e-2, (l, a == bo, e)
+
+
+def test_training_and_warm_start_cut_iterations(sq):
+    import torch
+
+    L, n = 8, 4
+    N = L * n
+    pc = sq.sq_precond_setup(N, 0)
+    seeds = list(range(100, 108))
+    cs = [sq.sq_build_coeffs(L, n, s, 0.5, 1.0, 10.0) for s in seeds]
+    tg = [[torch.empty(N ** 3, dtype=torch.float64, device="cuda") for _ in range(3)] for _ in cs]
+    b = sq.sq_batch_create([(c, i, tg[k][i]) for k, c in enumerate(cs) for i in range(3)], [pc] * 24)
+    sq.sq_pcg_solve_batched(b, 1e-10, 2000)
+    scale = float(torch.stack([t.std() for tri in tg for t in tri]).mean())
+    net = sq.sq_net_create(N, 4, seed=1, out_scale=scale)
+    losses = []
+    for step in range(120):
+        k = (4 * step) % len(cs)
+        losses.append(sq.sq_net_train_step(net, cs[k:k + 4], tg[k:k + 4], 3e-3))
+    assert np.mean(losses[-8:]) < 0.5 * np.mean(losses[:4]), (losses[:4], losses[-8:])
+    # warm start on a training realization: the guess lowers the initial
+    # residual (so the solver keeps it) and the solve reaches the same corrector
+    w = sq.sq_workspace_create(N, sq.SQ_FP32_REFINE)
+    g = [torch.empty(N ** 3, dtype=torch.float64, device="cuda") for _ in range(3)]
+    sq.sq_net_predict(net, cs[0], *g)
+    bvec = torch.empty(N ** 3, dtype=torch.float64, device="cuda")
+    Ag = torch.empty(N ** 3, dtype=torch.float64, device="cuda")
+    for i in range(3):
+        sq.sq_rhs(cs[0], i, bvec)
+        sq.sq_apply_operator(cs[0], g[i], Ag)
+        rel0 = float(torch.linalg.norm(bvec - Ag) / torch.linalg.norm(bvec))
+        assert rel0 < 0.9, rel0
+        psi0 = torch.empty(N ** 3, dtype=torch.float64, device="cuda")
+        psiw = torch.empty(N ** 3, dtype=torch.float64, device="cuda")
+        i0 = sq.sq_pcg_solve(cs[0], pc, w, i, 1e-8, 2000, sq.SQ_FP32_REFINE, None, psi0)
+        iw = sq.sq_pcg_solve(cs[0], pc, w, i, 1e-8, 2000, sq.SQ_FP32_REFINE, g[i], psiw)
+        assert iw["status"] == sq.SQ_OK and iw["used_guess"] == 1 and iw["relres_true"] <= 1e-8
+        assert float(torch.linalg.norm(psiw - psi0) / torch.linalg.norm(psi0)) <= 1e-6
+    # a useless guess is rejected by its residual and the solve starts from zero
+    bad = torch.from_numpy(1e3 * np.random.default_rng(1).standard_normal(N ** 3)).cuda()
+    psi = torch.empty(N ** 3, dtype=torch.float64, device="cuda")
+    ib = sq.sq_pcg_solve(cs[1], pc, w, 0, 1e-8, 2000, sq.SQ_FP32_REFINE, bad, psi)
+    assert ib["used_guess"] == 0 and ib["status"] == sq.SQ_OK
+    wf = sq.sq_workspace_create(N, sq.SQ_FP64)
+    ib = sq.sq_pcg_solve(cs[1], pc, wf, 0, 1e-8, 2000, sq.SQ_FP64, bad, psi)
+    assert ib["used_guess"] == 0 and ib["status"] == sq.SQ_OK
