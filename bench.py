@@ -146,6 +146,9 @@ def run_native(args):
     tol, max_iter = wl["tol"], 1000
     stream = torch.cuda.current_stream()
 
+    from paper_2007_06524_gb300 import autotune
+
+    tiles = autotune.tune(torch, N, L, n, cache=None)  # FP32 pass tile and operator planes for this grid
     c = sq.sq_build_coeffs(L, n, 0, wl["p_hi"], wl["a_lo"], wl["a_hi"])
     pc = sq.sq_precond_setup(N, R)
     w = sq.sq_workspace_create(N, prec)
@@ -237,7 +240,7 @@ def run_native(args):
                       "parallelism": "replicas" if ws > 1 else "single GPU"},
            "clocks": clocks, "gpu_launches": gpu_launches, "roofline": roof, "kernels": kernels,
            "iters": {"mean": round(statistics.mean(iters), 2), "min": min(iters), "max": max(iters)},
-           "converged": ok}
+           "converged": ok, "tiles": {"dht_pencils_fp32": tiles[0], "stencil_planes": tiles[1]}}
 
     # --- end to end through the C ABI with pinned host inputs
     rng = np.random.default_rng(12345 + rank)
@@ -283,6 +286,7 @@ def run_native(args):
 
     if not args.no_variants and rank == 0:
         out.setdefault("variants", {})["batch_768_mixed"] = run_batch(sq, torch, stream)
+        out["variants"]["warm_start_n64"] = run_warm_start(sq, torch)
 
     if rank == 0 and not args.no_cpu_baseline and ws == 1:
         out["cpu_baseline"] = cpu_baseline(statistics.mean(iters), R)
@@ -328,6 +332,23 @@ def run_batch(sq, torch, stream, nseeds=256):
     return {"solves": len(descs), "solves_per_s": round(len(descs) / t, 1), "seconds": round(t, 4),
             "iters_p50": float(np.percentile(its, 50)), "iters_p99": float(np.percentile(its, 99)),
             "unknowns": unknowns, "converged": ok}
+
+
+def run_warm_start(sq, torch, nseeds=64):
+    """Zero start vs learned start (committed weights, trained on seeds 1000..5095)
+    on held-out seeds 6000.. at L=16, n=4 (N=64), Bernoulli(1/2) on {1,10},
+    exact preconditioner, tol 1e-8: FP32+FP64 refinement and plain FP64."""
+    from paper_2007_06524_gb300 import warmstart, workloads
+
+    if not os.path.exists(warmstart.DEFAULT_WEIGHTS):
+        return {"unavailable": "no trained weights"}
+    wl = workloads.WARM_N64
+    net = warmstart.load(warmstart.DEFAULT_WEIGHTS)
+    seeds = wl["eval_seeds"][:nseeds]
+    res = {"eval_seeds": f"{seeds[0]}..{seeds[-1]}"}
+    res["fp32_refine"] = warmstart.evaluate(torch, wl, net, seeds, sq.SQ_FP32_REFINE)
+    res["fp64"] = warmstart.evaluate(torch, wl, net, seeds[:16], sq.SQ_FP64)
+    return res
 
 
 def _oracle_sample(iters_mean, R, n_iter_sample=3):

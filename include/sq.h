@@ -110,11 +110,17 @@ void sq_coeffs_destroy(sq_coeffs *c);
 /* Preconditioner (Sec. 4.1-4.2): pseudo-inverse of the periodic Laplacian,
  * z = F^-1 G F r with G(k) = 1/(l_k1 + l_k2 + l_k3), l_k = 4 sin^2(pi k/N),
  * G(0,0,0) = 0 (Eqs. 31-33). rank = 0 uses this exact Fourier diagonal; rank
- * R >= 2 uses the rank-R canonical tensor G_R = sum_r u_r (x) u_r (x) u_r
- * (Lemma 4.2) from a trapezoid rule of the Laplace transform of 1/x (Eq. 34),
- * R <= 64. Factors and twiddles are built on the host in FP64 and copied to
- * the current device (synchronous). */
+ * R >= 2 uses the rank-R canonical tensor G_R = sum_r u_r (x) u_r (x) u_r with
+ * u_r(k) = w_r^(1/3) exp(-t_r l_k) (Lemma 4.2; the exponential sum
+ * sum_r w_r exp(-t_r x) ~ 1/x of the Laplace transform, Eq. 34), R <= 64. For
+ * R <= 32 the nodes are geometric and the weights fitted by least squares to
+ * the relative error over the discrete spectrum; above, a balanced trapezoid
+ * rule. Factors and twiddles are built on the host in FP64 and copied to the
+ * current device (synchronous). */
 int sq_precond_setup(int N, int rank, sq_precond **out);
+/* The exponential-sum nodes t[r] and weights w[r], r < rank (host arrays,
+ * either may be NULL; nothing is written for rank 0). */
+int sq_precond_factors(const sq_precond *p, double *t, double *w);
 void sq_precond_destroy(sq_precond *p);
 
 /* Scratch fields for one solve at grid N and the given precision (device
@@ -156,6 +162,12 @@ typedef struct sq_tile_config {
   int dht_pencils;
   int stencil_planes;
 } sq_tile_config;
+
+/* Process-wide tile choice per grid size for single solves (FP32 Hartley
+ * passes and the operator of both precisions) and the default of new batches;
+ * ntiles = 0 restores the built-in defaults. Not thread-safe with concurrent
+ * solves. */
+int sq_set_tiles(const sq_tile_config *tiles, int ntiles);
 
 /* Plans a batch of `count` solves; precs[k] is the preconditioner (same N) of
  * descs[k]. Allocates 5 N^3 floats per solve plus scalars and partials, and

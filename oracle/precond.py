@@ -111,6 +111,25 @@ def core_tensor_rank_r(N: int, R: int) -> np.ndarray:
     return G
 
 
+def core_tensor_from_nodes(N: int, t, w) -> np.ndarray:
+    """G(k) = sum_r w_r exp(-t_r (l_k1 + l_k2 + l_k3)), G(0,0,0) := 0, for given
+    nodes t_r and weights w_r (an exponential sum for 1/x, Eq. 34)."""
+    lam = laplacian_eigenvalues(N)
+    U = np.cbrt(np.asarray(w, dtype=np.float64))[:, None] * np.exp(-np.outer(np.asarray(t, dtype=np.float64), lam))
+    G = np.einsum("ri,rj,rk->ijk", U, U, U)
+    G[0, 0, 0] = 0.0
+    return G
+
+
+def max_relative_error(N: int, t, w) -> float:
+    """max over nonzero modes of |g * G(g) - 1| for the exponential sum (t, w)."""
+    lam = laplacian_eigenvalues(N)
+    g = np.unique(np.round((lam[:, None, None] + lam[None, :, None] + lam[None, None, :]).ravel(), 13))
+    g = g[g > 0]
+    G = np.exp(-np.outer(g, np.asarray(t, dtype=np.float64))) @ np.asarray(w, dtype=np.float64)
+    return float(np.abs(g * G - 1.0).max())
+
+
 def core_tensor(N: int, rank: int) -> np.ndarray:
     """rank 0 = exact Fourier diagonal, else the rank-R canonical tensor."""
     return core_tensor_exact(N) if rank == 0 else core_tensor_rank_r(N, rank)

@@ -1,0 +1,82 @@
+"""Tile autotuner: times candidate tile shapes through the C ABI and installs
+the fastest per grid size with sq_set_tiles.
+
+Tuned per N: the number of complex pencils of a Hartley-pass tile (FP32 passes;
+2P real pencils, 2P * 4 bytes per row segment) and the number of x1-planes of
+an operator block. Each candidate is timed with CUDA events over a few
+repetitions of the kernel it drives (sq_apply_precond_f32 for the passes,
+sq_apply_operator_f32 for the operator); results are cached in a JSON file
+keyed by N and the device name.
+"""
+from __future__ import annotations
+
+import json
+import os
+
+from . import sq as _sq
+
+DEFAULT_CACHE = os.path.join(os.path.dirname(os.path.dirname(os.path.abspath(__file__))), "_build", "tiles.json")
+
+
+def _time(torch, fn, reps=5):
+    fn()
+    torch.cuda.synchronize()
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    e0.record()
+    for _ in range(reps):
+        fn()
+    e1.record()
+    torch.cuda.synchronize()
+    return e0.elapsed_time(e1) / reps
+
+
+def tune(torch, N, L=None, n=None, cache=DEFAULT_CACHE, reps=5):
+    """Returns (dht_pencils, stencil_planes) for grid N and installs them."""
+    dev = torch.cuda.get_device_name()
+    key = f"{dev}:{N}"
+    table = {}
+    if cache and os.path.exists(cache):
+        try:
+            table = json.load(open(cache))
+        except Exception:
+            table = {}
+    if key in table:
+        P, zc = table[key]["dht_pencils"], table[key]["stencil_planes"]
+        _sq.sq_set_tiles([(N, P, zc)])
+        return P, zc
+    if L is None:
+        n = 8 if N % 8 == 0 else 4
+        L = N // n
+    c = _sq.sq_build_coeffs(L, n, 1, 0.5, 1.0, 100.0)
+    pc = _sq.sq_precond_setup(N, 0)
+    w = _sq.sq_workspace_create(N, _sq.SQ_FP32_REFINE)
+    r = torch.randn(N ** 3, dtype=torch.float32, device="cuda")
+    z = torch.empty_like(r)
+    times_p = {}
+    for P in (2, 4, 8, 16):
+        if N % (2 * P) != 0:
+            continue
+        try:
+            _sq.sq_set_tiles([(N, P, 0)])
+        except _sq.SqError:
+            continue
+        times_p[P] = _time(torch, lambda: _sq.sq_apply_precond_f32(pc, w, r, z), reps)
+    bestP = min(times_p, key=times_p.get)
+    times_z = {}
+    for zc in (2, 4, 8, 16, 32, 64):
+        if zc > N:
+            continue
+        try:
+            _sq.sq_set_tiles([(N, bestP, zc)])
+        except _sq.SqError:
+            continue
+        times_z[zc] = _time(torch, lambda: _sq.sq_apply_operator_f32(c, r, z), reps)
+    bestZ = min(times_z, key=times_z.get)
+    _sq.sq_set_tiles([(N, bestP, bestZ)])
+    table[key] = {"dht_pencils": bestP, "stencil_planes": bestZ,
+                  "precond_ms": {str(k): round(v, 4) for k, v in times_p.items()},
+                  "operator_ms": {str(k): round(v, 4) for k, v in times_z.items()}}
+    if cache:
+        os.makedirs(os.path.dirname(cache), exist_ok=True)
+        json.dump(table, open(cache, "w"), indent=1)
+    return bestP, bestZ

@@ -159,17 +159,21 @@ __global__ void kb_count(const BSolve *__restrict__ S, int count, int which, int
 }
 
 // Inner solve of A d = r for every solve whose outer residual is not yet small.
-__global__ void kb_inner_init(BSolve *S, int count, double tolrel2, int max_iter, const int *iters_total) {
+__global__ void kb_inner_init(BSolve *S, int count, double tol_in, double tol, int max_iter,
+                              const int *iters_total) {
   const int s = blockIdx.x * blockDim.x + threadIdx.x;
   if (s >= count) return;
   const Scalars *o = S[s].st_o;
   Scalars z;
   memset(&z, 0, sizeof(z));
   const int budget = max_iter - iters_total[s];
-  z.tolrel2 = tolrel2;
+  // cut the residual by tol_in, or just enough for the outer tolerance (last step)
+  const double need = (o->rr_true > 0.0) ? 0.9 * tol * sqrt(o->bb / o->rr_true) : 1.0;
+  const double tin = fmax(tol_in, need);
+  z.tolrel2 = tin * tin;
   z.max_iter = budget;
   z.bb = o->rr_true;
-  z.tol2 = tolrel2 * o->rr_true;
+  z.tol2 = z.tolrel2 * o->rr_true;
   z.done = (o->done || !(o->rr_true > 0.0) || budget <= 0) ? 1 : 0;
   *S[s].st_i = z;
 }
@@ -488,7 +492,7 @@ int sq_pcg_solve_batched(sq_batch *b, double tol, int max_iter, sq_solve_info *i
     int active = 0;
     if ((st = count_active(b, 0, s, &active)) != SQ_OK) return st;
     if (active == 0) break;
-    kb_inner_init<<<tb, 128, 0, s>>>(b->dS, count, tol_in * tol_in, max_iter, b->d_iters);
+    kb_inner_init<<<tb, 128, 0, s>>>(b->dS, count, tol_in, tol, max_iter, b->d_iters);
     kb_vec<1><<<b->tot_vec, kThreads, 0, s>>>(b->dS, pre_vec, count);
     SQB_CK(cudaGetLastError());
     if ((st = precond_first_b(b, s)) != SQ_OK) return st;

@@ -282,6 +282,9 @@ template <typename T>
 cudaError_t launch_dht_pass(int pass, const SpectralDev &sp, const T *in, T *out, T *r, const T *q, T *p, T *x,
                             RedBuf rb, bool first, bool check_done, cudaStream_t s);
 int dht_tile_pencils(int N, int elem_bytes);
+// tile overrides (0 = default); return 0 on success
+int set_dht_pencils_override(int N, int P);
+int set_stencil_planes_override(int N, int zc);
 
 // solver.cu: read-only views of the opaque handles (used by batch.cu)
 int coeffs_view(const sq_coeffs *c, CellsDev *out);

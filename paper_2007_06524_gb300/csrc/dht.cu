@@ -85,14 +85,24 @@ __global__ void __launch_bounds__(kThreads) k_dht(DhtArgs<T> a) {
   }
 }
 
+static int g_pencils_override[kMaxN + 1] = {0};  // FP32 passes, per N (0 = default)
+
+int set_dht_pencils_override(int N, int P) {
+  if (N < 8 || N > kMaxN) return 1;
+  if (P != 0 && (P < 1 || (P & (P - 1)) || N % (2 * P) != 0 || dht_smem_bytes_t<float>(N, P, kMaxRank) > 200 * 1024))
+    return 1;
+  g_pencils_override[N] = P;
+  return 0;
+}
+
 int dht_tile_pencils(int N, int elem_bytes) {
+  if (elem_bytes == 4 && N >= 8 && N <= kMaxN && g_pencils_override[N]) return g_pencils_override[N];
   // 2P real pencils per tile: 128-byte row segments where N allows, and two
   // ping-pong buffers of N (P+1) complex values within about 80 KB.
   int P = 128 / (2 * elem_bytes);
   while (P > 1 && ((N % (2 * P)) != 0 || 2L * N * (P + 1) * 2 * elem_bytes > 90 * 1024)) P >>= 1;
   return P;
 }
-
 
 template <typename T, int AXIS, int LOADM, int STOREM, bool SCALE>
 static cudaError_t launch_one(const DhtArgs<T> &a, int grid, size_t smem, cudaStream_t s) {

@@ -15,7 +15,9 @@
 #include <cmath>
 #include <cstdio>
 #include <cstdlib>
+#include <algorithm>
 #include <cstring>
+#include <limits>
 #include <new>
 #include <vector>
 
@@ -35,6 +37,7 @@ struct sq_coeffs {
 
 struct sq_precond {
   int N, rank;
+  std::vector<double> t, w;  // exponential-sum nodes and weights (rank > 0)
   SpectralDev sp64, sp32;
   void *d_mem;
 };
@@ -183,7 +186,7 @@ int radix_plan(int N, int *rad) {
 // lower truncation 12 e^{s_lo}, upper truncation exp(-lambda_min e^{s_hi}) and
 // the step error exp(-pi^2/eta) -- are balanced at one level eps, found by
 // bisection on ln(eps); nodes s_r = s_lo + r eta, t_r = e^{s_r}, w_r = eta e^{s_r}.
-void rank_r_nodes(int N, int R, std::vector<double> &t, std::vector<double> &w) {
+void sinc_nodes(int N, int R, std::vector<double> &t, std::vector<double> &w) {
   const double pi = 3.14159265358979323846;
   const double sn = std::sin(pi / N);
   const double lam_min = 4.0 * sn * sn;
@@ -211,6 +214,130 @@ void rank_r_nodes(int N, int R, std::vector<double> &t, std::vector<double> &w) 
     const double s = s_lo + eta * r;
     t[r] = std::exp(s);
     w[r] = eta * std::exp(s);
+  }
+}
+
+// Least-squares solve min ||E w - 1|| (M x R, column-major copy) by Householder QR.
+bool lsq_ones(std::vector<double> E, int M, int R, std::vector<double> &w) {
+  if (M < 2 * R) return false;  // too few distinct spectral values for a fit
+  std::vector<double> rhs(M, 1.0);
+  for (int k = 0; k < R; ++k) {
+    double nrm = 0.0;
+    for (int i = k; i < M; ++i) nrm += E[(size_t)k * M + i] * E[(size_t)k * M + i];
+    nrm = std::sqrt(nrm);
+    if (!(nrm > 0.0)) return false;
+    const double a0 = E[(size_t)k * M + k];
+    const double alpha = (a0 > 0) ? -nrm : nrm;
+    std::vector<double> v(E.begin() + (size_t)k * M + k, E.begin() + (size_t)k * M + M);
+    v[0] -= alpha;
+    double vv = 0.0;
+    for (double x : v) vv += x * x;
+    if (!(vv > 0.0)) return false;
+    for (int j = k; j < R; ++j) {
+      double d = 0.0;
+      for (int i = k; i < M; ++i) d += v[i - k] * E[(size_t)j * M + i];
+      d = 2.0 * d / vv;
+      for (int i = k; i < M; ++i) E[(size_t)j * M + i] -= d * v[i - k];
+    }
+    double d = 0.0;
+    for (int i = k; i < M; ++i) d += v[i - k] * rhs[i];
+    d = 2.0 * d / vv;
+    for (int i = k; i < M; ++i) rhs[i] -= d * v[i - k];
+  }
+  w.assign(R, 0.0);
+  for (int k = R - 1; k >= 0; --k) {
+    double s = rhs[k];
+    for (int j = k + 1; j < R; ++j) s -= E[(size_t)j * M + k] * w[j];
+    const double d = E[(size_t)k * M + k];
+    if (!(std::fabs(d) > 0.0)) return false;
+    w[k] = s / d;
+  }
+  return true;
+}
+
+// Largest relative error |x G(x) - 1| of the exponential sum over the values xs.
+double exp_sum_error(const std::vector<double> &xs, const std::vector<double> &t, const std::vector<double> &w) {
+  double err = 0.0;
+  for (double x : xs) {
+    double g = 0.0;
+    for (size_t r = 0; r < t.size(); ++r) g += w[r] * std::exp(-t[r] * x);
+    err = std::max(err, std::fabs(x * g - 1.0));
+  }
+  return err;
+}
+
+// Rank-R factors used by the library: geometric nodes t_r between e^a and e^b,
+// weights w_r by least squares on the relative error x G_R(x) - 1 over a
+// log-uniform sample of the discrete spectrum {l_i + l_j + l_k > 0}; (a, b) is
+// chosen on a grid to minimise the largest sampled error with all w_r > 0. The
+// result is kept only if its largest error over the whole spectrum is below
+// that of the balanced trapezoid rule (which is used otherwise, and for R > 32).
+void rank_r_nodes(int N, int R, std::vector<double> &t, std::vector<double> &w) {
+  sinc_nodes(N, R, t, w);
+  if (R > 32) return;
+  const double pi = 3.14159265358979323846;
+  const int H = N / 2;
+  std::vector<double> lam(H + 1);
+  for (int k = 0; k <= H; ++k) {
+    const double sn = std::sin(pi * k / N);
+    lam[k] = 4.0 * sn * sn;
+  }
+  std::vector<double> xs;
+  xs.reserve((size_t)(H + 1) * (H + 2) * (H + 3) / 6);
+  for (int i = 0; i <= H; ++i)
+    for (int j = i; j <= H; ++j)
+      for (int k = j; k <= H; ++k) {
+        const double g = lam[i] + lam[j] + lam[k];
+        if (g > 0.0) xs.push_back(g);
+      }
+  std::sort(xs.begin(), xs.end());
+  std::vector<double> u;  // distinct spectral values
+  for (double x : xs)
+    if (u.empty() || x > u.back() * (1.0 + 1e-12)) u.push_back(x);
+  // log-uniform sample: the distinct value nearest to each point of a geometric grid
+  std::vector<double> smp;
+  const int K = 3000;
+  const double x0 = u.front(), x1 = u.back();
+  for (int m = 0; m < K; ++m) {
+    const double xt = x0 * std::pow(x1 / x0, (double)m / (K - 1));
+    auto it = std::lower_bound(u.begin(), u.end(), xt);
+    double pick = (it == u.end()) ? u.back() : *it;
+    if (it != u.begin() && (it == u.end() || std::fabs(*(it - 1) - xt) < std::fabs(pick - xt))) pick = *(it - 1);
+    if (smp.empty() || pick > smp.back()) smp.push_back(pick);
+  }
+  const int M = (int)smp.size();
+  if (M < 2 * R) return;
+  const double lam_min = lam[1];
+  const int ng = (R <= 16) ? 40 : 20;
+  double best = std::numeric_limits<double>::infinity();
+  std::vector<double> bt, bw, tt(R), ww, E((size_t)M * R);
+  for (int ia = 0; ia < ng; ++ia) {
+    const double a = -std::log(12.0) - 6.0 + 7.0 * ia / (ng - 1);
+    for (int ib = 0; ib < ng; ++ib) {
+      const double b = std::log(1.0 / lam_min) - 1.0 + 5.0 * ib / (ng - 1);
+      for (int r = 0; r < R; ++r) tt[r] = std::exp(a + (b - a) * r / (R - 1));
+      for (int r = 0; r < R; ++r)
+        for (int i = 0; i < M; ++i) E[(size_t)r * M + i] = smp[i] * std::exp(-tt[r] * smp[i]);
+      if (!lsq_ones(E, M, R, ww)) continue;
+      bool pos = true;
+      for (double x : ww) pos = pos && (x > 0.0);
+      if (!pos) continue;
+      double err = 0.0;
+      for (int i = 0; i < M; ++i) {
+        double gsum = 0.0;
+        for (int r = 0; r < R; ++r) gsum += ww[r] * E[(size_t)r * M + i];
+        err = std::max(err, std::fabs(gsum - 1.0));
+      }
+      if (err < best) {
+        best = err;
+        bt = tt;
+        bw = ww;
+      }
+    }
+  }
+  if (!bt.empty() && exp_sum_error(u, bt, bw) < exp_sum_error(u, t, w)) {
+    t = bt;
+    w = bw;
   }
 }
 
@@ -391,7 +518,11 @@ int solve_fp32_refine(const sq_coeffs *c, const sq_precond *pc, sq_workspace *w,
     if (st != SQ_OK) return st;
     if (ho->done || total_inner >= max_iter || outer >= 30) break;
     const int budget = max_iter - total_inner;
-    SQ_LAUNCH(PC_SCALAR, s, (k_inner_init<<<1, 1, 0, s>>>(ri.st, ro.st, tol_in * tol_in, budget), cudaGetLastError()));
+    // each inner solve cuts its residual by tol_in, or just enough for the
+    // outer tolerance when that is less (the last step)
+    const double need = 0.9 * tol * std::sqrt(ho->bb / ho->rr_true);
+    const double tin = std::max(tol_in, need);
+    SQ_LAUNCH(PC_SCALAR, s, (k_inner_init<<<1, 1, 0, s>>>(ri.st, ro.st, tin * tin, budget), cudaGetLastError()));
     SQ_CK(cudaMemsetAsync(d, 0, sizeof(float) * n3, s));
     st = precond_first<float>(pc, r, Y, p, ri, s);
     if (st != SQ_OK) return st;
@@ -593,8 +724,8 @@ int sq_precond_setup(int N, int rank, sq_precond **out) {
     const double sn = std::sin(pi * m / N);
     lam64[m] = 4.0 * sn * sn;
   }
+  std::vector<double> t, w;
   if (rank > 0) {
-    std::vector<double> t, w;
     rank_r_nodes(N, rank, t, w);
     const double fold = 1.0 / (4.0 * N);  // (64 N^3)^(-1/3)
     for (int r = 0; r < rank; ++r) {
@@ -611,6 +742,8 @@ int sq_precond_setup(int N, int rank, sq_precond **out) {
   if (!pc) return SQ_ENOMEM;
   pc->N = N;
   pc->rank = rank;
+  pc->t = t;
+  pc->w = w;
   const size_t b_tw64 = tw64.size() * 8, b_lam64 = lam64.size() * 8, b_u64 = u64.size() * 8;
   const size_t b_tw32 = tw32.size() * 4, b_lam32 = lam32.size() * 4, b_u32 = u32.size() * 4;
   auto al = [](size_t b) { return (b + 255) & ~(size_t)255; };
@@ -650,6 +783,32 @@ int sq_precond_setup(int N, int rank, sq_precond **out) {
   pc->sp32.lam = p_lam32;
   pc->sp32.u = p_u32;
   *out = pc;
+  return SQ_OK;
+}
+
+int sq_set_tiles(const sq_tile_config *tiles, int ntiles) {
+  if (ntiles < 0 || (ntiles > 0 && !tiles)) return SQ_EINVAL;
+  for (int k = 0; k < ntiles; ++k) {
+    const int N = tiles[k].N;
+    if (!valid_N(N)) return SQ_EINVAL;
+    if (tiles[k].dht_pencils && set_dht_pencils_override(N, tiles[k].dht_pencils) != 0) return SQ_EINVAL;
+    if (tiles[k].stencil_planes && set_stencil_planes_override(N, tiles[k].stencil_planes) != 0) return SQ_EINVAL;
+  }
+  if (ntiles == 0) {
+    for (int N = 8; N <= kMaxN; ++N) {
+      set_dht_pencils_override(N, 0);
+      set_stencil_planes_override(N, 0);
+    }
+  }
+  return SQ_OK;
+}
+
+int sq_precond_factors(const sq_precond *p, double *t, double *w) {
+  if (!p) return SQ_EINVAL;
+  for (int r = 0; r < p->rank; ++r) {
+    if (t) t[r] = p->t[r];
+    if (w) w[r] = p->w[r];
+  }
   return SQ_OK;
 }
 

@@ -60,7 +60,21 @@ __global__ void __launch_bounds__(kThreads) k_stencil(CellsDev c, int dir, const
   }
 }
 
+static int g_planes_override[kMaxN + 1] = {0};
+
+int set_stencil_planes_override(int N, int zc) {
+  if (N < 8 || N > kMaxN) return 1;
+  if (zc != 0) {
+    if (zc < 1 || zc > N) return 1;
+    const long long blocks = (long long)((N + 31) / 32) * ((N + 7) / 8) * ((N + zc - 1) / zc);
+    if (blocks > kMaxPartials) return 1;
+  }
+  g_planes_override[N] = zc;
+  return 0;
+}
+
 static int stencil_zc(int N) {
+  if (N >= 8 && N <= kMaxN && g_planes_override[N]) return g_planes_override[N];
   // about 4 K blocks of 256 threads per launch, at least 2 planes per block
   long long tiles = (long long)((N + 31) / 32) * ((N + 7) / 8);
   long long want = 4096;

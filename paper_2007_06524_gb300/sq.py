@@ -64,6 +64,7 @@ def load_library():
         "sq_coeffs_destroy": (None, [vp]),
         "sq_precond_setup": (i, [i, i, p(vp)]),
         "sq_precond_destroy": (None, [vp]),
+        "sq_precond_factors": (i, [vp, vp, vp]),
         "sq_workspace_create": (i, [i, i, p(vp)]),
         "sq_workspace_destroy": (None, [vp]),
         "sq_pcg_solve": (i, [vp, vp, vp, i, d, i, i, vp, vp, p(SolveInfo), vp]),
@@ -85,6 +86,7 @@ def load_library():
         "sq_net_train_step": (i, [vp, i, p(vp), p(vp), C.c_float, p(d), vp]),
         "sq_batch_destroy": (None, [vp]),
         "sq_pcg_solve_batched": (i, [vp, d, i, p(SolveInfo), vp]),
+        "sq_set_tiles": (i, [p(TileConfig), i]),
     }
     for name, (res, args) in sig.items():
         f = getattr(lib, name)
@@ -237,6 +239,15 @@ def sq_precond_setup(N, rank) -> Precond:
     return Precond(out)
 
 
+def sq_precond_factors(pc: Precond, rank: int):
+    """(t, w): the exponential-sum nodes and weights of a rank-R preconditioner."""
+    t = np.zeros(max(rank, 1))
+    w = np.zeros(max(rank, 1))
+    _check(load_library().sq_precond_factors(pc, t.ctypes.data_as(C.c_void_p), w.ctypes.data_as(C.c_void_p)),
+           "sq_precond_factors")
+    return t[:rank], w[:rank]
+
+
 def sq_workspace_create(N, precision) -> Workspace:
     out = C.c_void_p()
     _check(load_library().sq_workspace_create(int(N), int(precision), C.byref(out)), "sq_workspace_create")
@@ -365,3 +376,12 @@ def sq_net_train_step(net: Net, coeffs, targets, lr, stream=None) -> float:
     _check(load_library().sq_net_train_step(net, B, carr, tarr, C.c_float(lr), C.byref(loss), _stream(stream)),
            "sq_net_train_step")
     return loss.value
+
+
+def sq_set_tiles(tiles):
+    """tiles: list of (N, dht_pencils, stencil_planes); [] restores defaults."""
+    tl = list(tiles)
+    arr = (TileConfig * max(1, len(tl)))()
+    for k, (N, dp, sp) in enumerate(tl):
+        arr[k].N, arr[k].dht_pencils, arr[k].stencil_planes = int(N), int(dp), int(sp)
+    _check(load_library().sq_set_tiles(arr if tl else None, len(tl)), "sq_set_tiles")

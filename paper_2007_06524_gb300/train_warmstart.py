@@ -1,0 +1,52 @@
+"""Trains the learned warm start on method-generated correctors and saves the weights.
+
+  python -m paper_2007_06524_gb300.train_warmstart [--train N] [--epochs E] [--out PATH]
+
+Workload: L=16, n=4 (N=64), Bernoulli(1/2) on {1,10}; training seeds
+1000..1000+N-1 (default 4096), held-out evaluation seeds 6000.. (default 512).
+"""
+import argparse
+import json
+import os
+import sys
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+if ROOT not in sys.path:
+    sys.path.insert(0, ROOT)
+
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--train", type=int, default=4096)
+    ap.add_argument("--eval", type=int, default=512)
+    ap.add_argument("--epochs", type=int, default=4)
+    ap.add_argument("--batch", type=int, default=8)
+    ap.add_argument("--lr", type=float, default=2e-3)
+    ap.add_argument("--out", default=None)
+    args = ap.parse_args()
+    import numpy as np
+    import torch
+
+    import __graft_entry__
+
+    __graft_entry__.build()
+    import paper_2007_06524_gb300 as sq
+    from paper_2007_06524_gb300 import warmstart, workloads
+
+    wl = workloads.WARM_N64
+    seeds = wl["train_seeds"][: args.train]
+    targets, gen_iters = warmstart.generate_targets(torch, wl, seeds)
+    net, losses, secs = warmstart.train(torch, wl, targets, seeds, epochs=args.epochs, batch=args.batch, lr=args.lr,
+                                        log_every=64)
+    out = args.out or warmstart.DEFAULT_WEIGHTS
+    N = wl["L"] * wl["n"]
+    warmstart.save(net, out, N, float(targets.std()),
+                   {"train_seeds": np.array([seeds[0], seeds[-1]]), "epochs": args.epochs, "final_loss": losses[-1]})
+    ev = warmstart.evaluate(torch, wl, warmstart.load(out), wl["eval_seeds"][: args.eval], sq.SQ_FP32_REFINE)
+    print(json.dumps({"train_samples": len(seeds), "epochs": args.epochs, "train_seconds": round(secs, 1),
+                      "loss_first": float(np.mean(losses[:16])), "loss_last": float(np.mean(losses[-16:])),
+                      "gen_iters_mean": float(np.mean(gen_iters)), "eval": ev, "weights": out}))
+
+
+if __name__ == "__main__":
+    main()

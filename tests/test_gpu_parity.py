@@ -98,6 +98,24 @@ def test_operator_fp32(sq, L, n, seed):
 
 
 # ---------------------------------------------------------- preconditioner
+def _core(sq, pc, N, rank):
+    """The oracle's G for the library's preconditioner: exact, or the exponential
+    sum with the library's nodes and weights (passed in as inputs)."""
+    if rank == 0:
+        return precond.core_tensor_exact(N)
+    t, w = sq.sq_precond_factors(pc, rank)
+    return precond.core_tensor_from_nodes(N, t, w)
+
+
+@pytest.mark.parametrize("N,rank", [(16, 6), (32, 8), (64, 16), (256, 8), (48, 4)])
+def test_rank_r_factors_at_least_as_accurate_as_trapezoid(sq, N, rank):
+    pc = sq.sq_precond_setup(N, rank)
+    t, w = sq.sq_precond_factors(pc, rank)
+    assert np.all(w > 0) and np.all(t > 0)
+    ts, ws = precond.rank_r_nodes(N, rank)
+    assert precond.max_relative_error(N, t, w) <= precond.max_relative_error(N, ts, ws) * (1 + 1e-9)
+
+
 @pytest.mark.parametrize("N", [8, 12, 16, 24, 32, 48, 64, 96, 128])
 @pytest.mark.parametrize("rank", [0, 6, 16])
 def test_precond_fp64(sq, N, rank):
@@ -108,7 +126,7 @@ def test_precond_fp64(sq, N, rank):
     r = inputs.random_field(N, N + rank)
     z = torch.empty(N ** 3, dtype=torch.float64, device="cuda")
     sq.sq_apply_precond(pc, w, _dev(r.ravel()), z)
-    ref = precond.apply_precond(precond.core_tensor(N, rank), r)
+    ref = precond.apply_precond(_core(sq, pc, N, rank), r)
     assert _relmax(_host(z).reshape(N, N, N), ref) <= 1e-12
 
 
@@ -122,7 +140,7 @@ def test_precond_fp32(sq, N, rank):
     r = inputs.random_field(N, 3 * N + rank, np.float32)
     z = torch.empty(N ** 3, dtype=torch.float32, device="cuda")
     sq.sq_apply_precond_f32(pc, w, _dev(r.ravel(), "float32"), z)
-    ref = precond.apply_precond(precond.core_tensor(N, rank), r.astype(np.float64))
+    ref = precond.apply_precond(_core(sq, pc, N, rank), r.astype(np.float64))
     assert _relmax(_host(z).reshape(N, N, N).astype(np.float64), ref) <= 2e-5
 
 
@@ -135,7 +153,7 @@ def test_precond_fp64_full_size(sq):
     r = inputs.random_field(N, 42)
     z = torch.empty(N ** 3, dtype=torch.float64, device="cuda")
     sq.sq_apply_precond(pc, w, _dev(r.ravel()), z)
-    ref = precond.apply_precond(precond.core_tensor(N, rank), r)
+    ref = precond.apply_precond(_core(sq, pc, N, rank), r)
     assert _relmax(_host(z).reshape(N, N, N), ref) <= 1e-12
 
 
@@ -162,7 +180,9 @@ def test_solve_plain_n16(sq, rank):
     assert np.linalg.norm(x - ref) / np.linalg.norm(ref) <= 1e-9
     assert abs(x.mean()) < 1e-14
     # iteration count of the same PCG on the oracle at tol 1e-10
-    _, it_o, _ = pcg.pcg(re.A, re.b[0], pcg.fft_preconditioner(re.N, rank), tol=1e-10)
+    G = _core(sq, sq.sq_precond_setup(re.N, rank), re.N, rank)
+    P = lambda r: precond.apply_precond(G, r.reshape(re.N, re.N, re.N)).ravel()  # noqa: E731
+    _, it_o, _ = pcg.pcg(re.A, re.b[0], P, tol=1e-10)
     psi2, info2 = _solve(sq, c, re.N, 0, rank, 1e-10)
     assert abs(info2["iters"] - it_o) <= 1
     Ah, _ = sq.sq_homogenized_matrix(c, psi, psi, psi)

@@ -67,3 +67,13 @@ def test_rank_r_symmetric_factorisation():
 def test_spectral_ratio_bounds():
     assert precond.spectral_ratio(32, 8) < 1.2
     assert precond.spectral_ratio(32, 16) < 1.01
+
+
+def test_core_tensor_from_nodes_consistent():
+    N, R = 16, 6
+    t, w = precond.rank_r_nodes(N, R)
+    assert np.allclose(precond.core_tensor_from_nodes(N, t, w), precond.core_tensor_rank_r(N, R), rtol=1e-14, atol=0)
+    E = precond.core_tensor_exact(N)
+    G = precond.core_tensor_rank_r(N, R)
+    m = E > 0
+    assert abs(precond.max_relative_error(N, t, w) - np.abs(G[m] / E[m] - 1).max()) < 1e-12
