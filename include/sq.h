@@ -169,6 +169,13 @@ typedef struct sq_tile_config {
  * solves. */
 int sq_set_tiles(const sq_tile_config *tiles, int ntiles);
 
+/* Process-wide switches (not thread-safe with concurrent solves).
+ * SQ_OPT_STRIDED_TWO_STAGE (default 1): the x1/x2 Hartley passes use the
+ * two-stage register plan where N allows (16, 32, 64, 128, 256); 0 selects the
+ * generic shared-memory Stockham tile for every pass. */
+enum sq_option { SQ_OPT_STRIDED_TWO_STAGE = 1 };
+int sq_set_option(int key, int value);
+
 /* Plans a batch of `count` solves; precs[k] is the preconditioner (same N) of
  * descs[k]. Allocates 5 N^3 floats per solve plus scalars and partials, and
  * captures the batched inner PCG iteration into a CUDA graph on first solve.
@@ -216,12 +223,14 @@ int sq_net_grads(const sq_net *net, float *host, int64_t count);
  * each). Asynchronous on `stream`. */
 int sq_net_predict(sq_net *net, const sq_coeffs *c, double *psi0, double *psi1, double *psi2,
                    sq_stream_t stream);
-/* One Adam step (lr; beta 0.9 / 0.999) on the mean squared error against the
- * targets targets[3*b + i] (device, N^3 doubles: psi_i of sample b) for the
- * `batch` realizations cs[b]. *loss (host, may be NULL) receives the mean
- * squared error / out_scale^2 of the forward pass (synchronizes `stream`). */
+/* One Adam step (lr; beta 0.9 / 0.999) against the targets targets[3*b + i]
+ * (device, N^3 doubles: psi_i of sample b) for the `batch` realizations
+ * cs[b], with e = (prediction - target) / out_scale and loss_type 0: mean of
+ * e^2; 1: mean of e . A e (the energy norm of the error under each sample's
+ * own operator -- the norm PCG reduces). *loss (host, may be NULL) receives
+ * that loss for the forward pass (synchronizes `stream`). */
 int sq_net_train_step(sq_net *net, int batch, const sq_coeffs *const *cs, const double *const *targets,
-                      float lr, double *loss, sq_stream_t stream);
+                      float lr, int loss_type, double *loss, sq_stream_t stream);
 
 /* A_hom without allocating: for callers that may not allocate device memory
  * when they need the result (code running under CUDA stream capture, or a

@@ -285,6 +285,7 @@ int dht_tile_pencils(int N, int elem_bytes);
 // tile overrides (0 = default); return 0 on success
 int set_dht_pencils_override(int N, int P);
 int set_stencil_planes_override(int N, int zc);
+int set_strided_fast(int on);  // 0: generic Stockham tiles for every pass
 
 // solver.cu: read-only views of the opaque handles (used by batch.cu)
 int coeffs_view(const sq_coeffs *c, CellsDev *out);

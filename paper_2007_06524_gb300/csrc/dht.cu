@@ -85,7 +85,75 @@ __global__ void __launch_bounds__(kThreads) k_dht(DhtArgs<T> a) {
   }
 }
 
+// Strided-axis passes with the two-stage plan (one shared-memory round trip
+// per transform; see dht_tile_s2).
+template <typename T, int AXIS, int R0, int R1, bool SCALE>
+__global__ void __launch_bounds__(kThreads) k_dht_s2(DhtArgs<T> a) {
+  using C = typename Cx<T>::type;
+  if (a.check_done && *(volatile int *)&a.rb.st->done) return;
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  constexpr int N = R0 * R1;
+  const int P = 1 << a.logP;
+  C *sm = reinterpret_cast<C *>(smem_raw);
+  C *tw = sm + N * (P + 1);
+  T *vtab = reinterpret_cast<T *>(tw + N);
+  const C *twg = reinterpret_cast<const C *>(a.sp.tw);
+  for (int m = threadIdx.x; m < N; m += kThreads) tw[m] = twg[m];
+  DhtTile<T> t;
+  t.in = a.in;
+  t.out = a.out;
+  t.r = a.r;
+  t.q = a.q;
+  t.p = a.p;
+  t.x = a.x;
+  t.alpha = (T)a.rb.st->alpha;
+  t.beta = (T)a.rb.st->beta;
+  t.first = a.first;
+  t.logP = a.logP;
+  Accum<T> acc;
+  for (int tile = blockIdx.x; tile < a.ntiles; tile += gridDim.x)
+    dht_tile_s2<T, AXIS, R0, R1, SCALE>(a.sp, t, tile, sm, tw, vtab, acc);
+  if (SCALE) {
+    double v[1] = {acc.get()}, s[1];
+    if (reduce_last_block<1>(v, a.rb.partials, &a.rb.st->ticket, s)) {
+      if (threadIdx.x == 0) finalize_scalars(a.rb.st, a.first ? FIN_RZ_FIRST : FIN_RZ_BETA, s, 1);
+    }
+  }
+}
+
+template <typename T, int AXIS, int R0, int R1, bool SCALE>
+static cudaError_t launch_s2(const DhtArgs<T> &a, int grid, cudaStream_t s) {
+  const int P = 1 << a.logP;
+  const size_t smem = (size_t)R0 * R1 * (P + 1) * sizeof(typename Cx<T>::type) +
+                      (size_t)R0 * R1 * sizeof(typename Cx<T>::type) + (size_t)a.sp.rank * 2 * P * sizeof(T);
+  auto kern = k_dht_s2<T, AXIS, R0, R1, SCALE>;
+  cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+  if (e != cudaSuccess) return e;
+  kern<<<grid, kThreads, smem, s>>>(a);
+  return cudaGetLastError();
+}
+
+// Two-stage plans for the strided passes; returns cudaErrorNotSupported when N has none.
+template <typename T, int AXIS, bool SCALE>
+static cudaError_t launch_strided_fast(const DhtArgs<T> &a, int grid, cudaStream_t s) {
+  if ((1 << a.logP) > 16) return cudaErrorNotSupported;
+  switch (a.sp.N) {
+    case 16: return launch_s2<T, AXIS, 4, 4, SCALE>(a, grid, s);
+    case 32: return launch_s2<T, AXIS, 8, 4, SCALE>(a, grid, s);
+    case 64: return launch_s2<T, AXIS, 8, 8, SCALE>(a, grid, s);
+    case 128: return launch_s2<T, AXIS, 16, 8, SCALE>(a, grid, s);
+    case 256: return launch_s2<T, AXIS, 16, 16, SCALE>(a, grid, s);
+    default: return cudaErrorNotSupported;
+  }
+}
+
 static int g_pencils_override[kMaxN + 1] = {0};  // FP32 passes, per N (0 = default)
+static int g_strided_fast = 1;                    // two-stage strided passes where N allows
+
+int set_strided_fast(int on) {
+  g_strided_fast = on ? 1 : 0;
+  return 0;
+}
 
 int set_dht_pencils_override(int N, int P) {
   if (N < 8 || N > kMaxN) return 1;
@@ -138,8 +206,20 @@ cudaError_t launch_dht_pass(int pass, const SpectralDev &sp, const T *in, T *out
   switch (pass) {
     case PASS_A_RESID: return launch_one<T, 3, LD_RESID, SO_PLAIN, false>(a, grid, smem, s);
     case PASS_A_PLAIN: return launch_one<T, 3, LD_PLAIN, SO_PLAIN, false>(a, grid, smem, s);
-    case PASS_B: return launch_one<T, 2, LD_PLAIN, SO_PLAIN, false>(a, grid, smem, s);
-    case PASS_C: return launch_one<T, 1, LD_PLAIN, SO_PLAIN, true>(a, grid, smem, s);
+    case PASS_B: {
+      if (g_strided_fast) {
+        const cudaError_t e = launch_strided_fast<T, 2, false>(a, grid, s);
+        if (e != cudaErrorNotSupported) return e;
+      }
+      return launch_one<T, 2, LD_PLAIN, SO_PLAIN, false>(a, grid, smem, s);
+    }
+    case PASS_C: {
+      if (g_strided_fast) {
+        const cudaError_t e = launch_strided_fast<T, 1, true>(a, grid, s);
+        if (e != cudaErrorNotSupported) return e;
+      }
+      return launch_one<T, 1, LD_PLAIN, SO_PLAIN, true>(a, grid, smem, s);
+    }
     case PASS_E_PCG: return launch_one<T, 3, LD_PLAIN, SO_PCG, false>(a, grid, smem, s);
     case PASS_E_PLAIN: return launch_one<T, 3, LD_PLAIN, SO_PLAIN, false>(a, grid, smem, s);
     default: return cudaErrorInvalidValue;

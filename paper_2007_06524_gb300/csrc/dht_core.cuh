@@ -41,6 +41,38 @@ __device__ __forceinline__ void dft(C (&u)[R]) {
     u[2] = C{fma(-c, d.y, m.x), fma(c, d.x, m.y)};
   } else if (R == 4) {
     dft4<T, C>(u[0], u[1], u[2], u[3]);
+  } else if (R == 16) {
+    // 16 = 4 x 4: DFT4 over the stride-4 subsequences, twiddles W16^(n2 k1),
+    // DFT4 across them; output k1 + 4 k2.
+    const T c = (T)0.92387953251128675613, s = (T)0.38268343236508977173, h = (T)0.70710678118654752440;
+    C y[16];
+#pragma unroll
+    for (int n2 = 0; n2 < 4; ++n2) {
+      C a0 = u[n2], a1 = u[4 + n2], a2 = u[8 + n2], a3 = u[12 + n2];
+      dft4<T, C>(a0, a1, a2, a3);
+      y[n2 * 4 + 0] = a0;
+      y[n2 * 4 + 1] = a1;
+      y[n2 * 4 + 2] = a2;
+      y[n2 * 4 + 3] = a3;
+    }
+    y[5] = cmul(y[5], C{c, -s});    // W^1
+    y[6] = cmul(y[6], C{h, -h});    // W^2
+    y[7] = cmul(y[7], C{s, -c});    // W^3
+    y[9] = cmul(y[9], C{h, -h});    // W^2
+    y[10] = mul_mi(y[10]);          // W^4
+    y[11] = cmul(y[11], C{-h, -h}); // W^6
+    y[13] = cmul(y[13], C{s, -c});  // W^3
+    y[14] = cmul(y[14], C{-h, -h}); // W^6
+    y[15] = cmul(y[15], C{-c, s});  // W^9
+#pragma unroll
+    for (int k1 = 0; k1 < 4; ++k1) {
+      C b0 = y[k1], b1 = y[4 + k1], b2 = y[8 + k1], b3 = y[12 + k1];
+      dft4<T, C>(b0, b1, b2, b3);
+      u[k1] = b0;
+      u[k1 + 4] = b1;
+      u[k1 + 8] = b2;
+      u[k1 + 12] = b3;
+    }
   } else if (R == 8) {
     const T h = (T)0.70710678118654752440;  // sqrt(2)/2
     C e0 = u[0], e1 = u[2], e2 = u[4], e3 = u[6];
@@ -298,6 +330,174 @@ __device__ __forceinline__ void dht_tile(const SpectralDev &sp, const DhtTile<T>
       reinterpret_cast<C *>(a.out)[g >> 1] = res[j * SP + p];
     }
   }
+}
+
+}  // namespace sq
+
+namespace sq {
+
+// ----------------------------------------------------------------------------
+// Two-stage tile for the strided axes (x1, x2) when N = R0 * R1 with power-of-
+// two radices: one shared-memory round trip per transform.
+//   stage 1 (radix R0, no twiddles): butterfly b < R1 of pencil p reads
+//     x[b + q R1] (q < R0) -- from global memory (rows of P complex values,
+//     coalesced) or from shared memory (second transform of pass C) -- and
+//     writes y[b R0 + q] to shared memory;
+//   stage 2 (radix R1, last): butterfly b < R0 reads y[b + q R0], applies
+//     tw[q b], and yields X[b + q R0]. Butterflies b and R0 - b hold each
+//     other's mirror outputs X[N - m], so one thread takes both and forms the
+//     Hartley values 2(H a)_m, 2(H b)_m in registers, then stores them (pass
+//     C: scales by G, reduces r.z and writes them back for the second
+//     transform). A unit reads and writes only its own positions, so stage 2
+//     needs no barrier between its reads and writes.
+// ----------------------------------------------------------------------------
+template <typename T, typename C, int R0, int R1, bool FROM_SMEM>
+__device__ __forceinline__ void s2_stage1(const C *__restrict__ gsrc, size_t base, size_t stride, C *sm, int SP,
+                                          int logP) {
+  static_assert(R1 * 16 <= kThreads, "one stage-1 butterfly per thread");
+  const int P = 1 << logP;
+  const int nb = R1 << logP;
+  const int t = threadIdx.x;
+  const int p = t & (P - 1), b = t >> logP;
+  C u[R0];
+  if (t < nb) {
+#pragma unroll
+    for (int q = 0; q < R0; ++q) {
+      const int j = b + q * R1;
+      u[q] = FROM_SMEM ? sm[j * SP + p] : gsrc[(base + (size_t)j * stride) / 2 + p];
+    }
+    dft<T, C, R0>(u);
+  }
+  if (FROM_SMEM) __syncthreads();  // every read of the tile precedes the overwrite
+  if (t < nb) {
+#pragma unroll
+    for (int q = 0; q < R0; ++q) sm[(b * R0 + q) * SP + p] = u[q];
+  }
+  __syncthreads();
+}
+
+// Hartley value pair of output m from X_m and its mirror X_{N-m}.
+template <typename C>
+__device__ __forceinline__ C hartley_pair(const C X, const C Y) {
+  return C{X.x - X.y + Y.x + Y.y, X.x + X.y - Y.x + Y.y};
+}
+
+// Stage 2 + Hartley combine. MODE 0: store to global; 1: scale by G (r.z into
+// acc) and write back to shared memory for the second transform.
+template <typename T, typename C, int R0, int R1, int MODE>
+__device__ __forceinline__ void s2_stage2(C *sm, int SP, int logP, const C *__restrict__ tw, C *__restrict__ gdst,
+                                          size_t base, size_t stride, const SpectralDev &sp, int k2, int c0,
+                                          const T *vtab, Accum<T> &acc) {
+  constexpr int N = R0 * R1;
+  static_assert((R0 / 2 + 1) * 16 <= kThreads, "one stage-2 unit per thread");
+  const int P = 1 << logP;
+  const int nu = (R0 / 2 + 1) << logP;
+  const int t = threadIdx.x;
+  if (t < nu) {
+    const int p = t & (P - 1), bb = t >> logP;
+    const int b1 = bb, b2 = (R0 - bb) & (R0 - 1);
+    const bool two = (b2 != b1);
+    C x1[R1], x2[R1];
+#pragma unroll
+    for (int q = 0; q < R1; ++q) {
+      x1[q] = sm[(b1 + q * R0) * SP + p];
+      if (q > 0) x1[q] = cmul(x1[q], tw[q * b1]);
+    }
+    dft<T, C, R1>(x1);
+    if (two) {
+#pragma unroll
+      for (int q = 0; q < R1; ++q) {
+        x2[q] = sm[(b2 + q * R0) * SP + p];
+        if (q > 0) x2[q] = cmul(x2[q], tw[q * b2]);
+      }
+      dft<T, C, R1>(x2);
+    }
+    const T *lam = reinterpret_cast<const T *>(sp.lam);
+    const T *uf = reinterpret_cast<const T *>(sp.u);
+    const int R = sp.rank;
+    const T gscale = (T)sp.scale;
+    const int k3a = c0 + 2 * p, k3b = k3a + 1;
+    // Output m = b + q R0 of butterfly b; its mirror N - m sits in butterfly
+    // (R0 - b) mod R0 at index R1-1-q, except b = 0: index (R1 - q) mod R1.
+#pragma unroll
+    for (int w = 0; w < 2; ++w) {
+      if (w == 1 && !two) break;
+      const int bw = (w == 0) ? b1 : b2;
+#pragma unroll
+      for (int q = 0; q < R1; ++q) {
+        const C X = (w == 0) ? x1[q] : x2[q];
+        C mir;
+        if (bw == 0)
+          mir = x1[(R1 - q) & (R1 - 1)];
+        else if (!two)
+          mir = x1[R1 - 1 - q];
+        else
+          mir = (w == 0) ? x2[R1 - 1 - q] : x1[R1 - 1 - q];
+        C h = hartley_pair(X, mir);
+        const int m = bw + q * R0;
+        if (MODE == 1) {
+          T ga, gb;
+          if (R == 0) {
+            const T l12 = lam[m] + lam[k2];
+            const T g1 = l12 + lam[k3a], g2 = l12 + lam[k3b];
+            ga = (g1 > (T)0) ? gscale / g1 : (T)0;
+            gb = (g2 > (T)0) ? gscale / g2 : (T)0;
+          } else {
+            T sa = (T)0, sb = (T)0;
+            for (int rr = 0; rr < R; ++rr) {
+              const T uk = uf[rr * N + m];
+              sa = fma(uk, vtab[rr * 2 * P + 2 * p], sa);
+              sb = fma(uk, vtab[rr * 2 * P + 2 * p + 1], sb);
+            }
+            ga = (m == 0 && k2 == 0 && k3a == 0) ? (T)0 : sa;
+            gb = sb;
+          }
+          acc.add(fma(ga * h.x, h.x, gb * h.y * h.y));
+          h = C{h.x * ga, h.y * gb};
+        }
+        // writes after all reads of this unit's positions: the mirrors come from
+        // registers, so in-place shared-memory writes are safe
+        if (MODE == 0)
+          gdst[(base + (size_t)m * stride) / 2 + p] = h;
+        else
+          sm[m * SP + p] = h;
+      }
+    }
+  }
+  __syncthreads();
+}
+
+// Strided-axis tile (AXIS 1 or 2) with the two-stage plan R0 x R1. SCALE: pass C.
+template <typename T, int AXIS, int R0, int R1, bool SCALE>
+__device__ __forceinline__ void dht_tile_s2(const SpectralDev &sp, const DhtTile<T> &a, int tile,
+                                            typename Cx<T>::type *sm, const typename Cx<T>::type *tw, T *vtab,
+                                            Accum<T> &acc) {
+  using C = typename Cx<T>::type;
+  constexpr int N = R0 * R1;
+  const int logP = a.logP, P = 1 << logP, SP = P + 1;
+  const size_t NN = (size_t)N * N;
+  const int nb2 = N / (2 * P);
+  const int line = tile / nb2, cb = tile - line * nb2;
+  const int c0 = cb * 2 * P;
+  const size_t base = (AXIS == 2) ? (size_t)line * NN + c0 : (size_t)line * N + c0;
+  const size_t stride = (AXIS == 2) ? (size_t)N : NN;
+  const int k2 = line;
+  __syncthreads();
+  if (SCALE && sp.rank > 0) {
+    const T *uf = reinterpret_cast<const T *>(sp.u);
+    for (int e = threadIdx.x; e < sp.rank * 2 * P; e += kThreads) {
+      const int rr = e / (2 * P), w = e - rr * 2 * P;
+      vtab[e] = uf[rr * N + k2] * uf[rr * N + c0 + w];
+    }
+  }
+  const C *gin = reinterpret_cast<const C *>(a.in);
+  C *gout = reinterpret_cast<C *>(a.out);
+  s2_stage1<T, C, R0, R1, false>(gin, base, stride, sm, SP, logP);
+  if (SCALE) {
+    s2_stage2<T, C, R0, R1, 1>(sm, SP, logP, tw, gout, base, stride, sp, k2, c0, vtab, acc);
+    s2_stage1<T, C, R0, R1, true>(gin, base, stride, sm, SP, logP);
+  }
+  s2_stage2<T, C, R0, R1, 0>(sm, SP, logP, tw, gout, base, stride, sp, k2, c0, vtab, acc);
 }
 
 }  // namespace sq

@@ -803,6 +803,11 @@ int sq_set_tiles(const sq_tile_config *tiles, int ntiles) {
   return SQ_OK;
 }
 
+int sq_set_option(int key, int value) {
+  if (key == SQ_OPT_STRIDED_TWO_STAGE) return set_strided_fast(value) == 0 ? SQ_OK : SQ_EINVAL;
+  return SQ_EINVAL;
+}
+
 int sq_precond_factors(const sq_precond *p, double *t, double *w) {
   if (!p) return SQ_EINVAL;
   for (int r = 0; r < p->rank; ++r) {

@@ -247,6 +247,48 @@ __global__ void __launch_bounds__(256) k_loss_grad(const float *__restrict__ y, 
   }
 }
 
+// e = (y - t) / out_scale, FP32 fields [sample][3][N3]
+__global__ void k_err(const float *__restrict__ y, const float *__restrict__ tgt, float *__restrict__ e, float inv_scale,
+                      long long n) {
+  const long long i = blockIdx.x * 256LL + threadIdx.x;
+  if (i < n) e[i] = (y[i] - tgt[i]) * inv_scale;
+}
+
+// per-block partial sums of a . b (fixed order inside the block)
+__global__ void __launch_bounds__(256) k_dot_partial(const float *__restrict__ a, const float *__restrict__ b,
+                                                     double *__restrict__ partials, long long n) {
+  const long long i = blockIdx.x * 256LL + threadIdx.x;
+  Accum<float> acc;
+  if (i < n) acc.add_prod(a[i], b[i]);
+  __shared__ double sh[8];
+  double v = warp_sum(acc.get());
+  if ((threadIdx.x & 31) == 0) sh[threadIdx.x >> 5] = v;
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    double t = 0.0;
+    for (int k = 0; k < 8; ++k) t += sh[k];
+    partials[blockIdx.x] = t;
+  }
+}
+
+// dL/d(conv6 out) = 2 A e as channel-last BF16 [sample][voxel][16], channels 0..2
+__global__ void k_pack_grad(const float *__restrict__ ae, __nv_bfloat16 *__restrict__ g, long long N3, int B) {
+  const long long i = blockIdx.x * 256LL + threadIdx.x;  // sample * N3 + voxel
+  if (i >= (long long)B * N3) return;
+  const long long smp = i / N3, vox = i - smp * N3;
+  uint32_t w[8];
+#pragma unroll
+  for (int k = 0; k < 8; ++k) w[k] = 0u;
+  for (int c = 0; c < 3; ++c) {
+    const __nv_bfloat16 gb = __float2bfloat16_rn(2.f * ae[(smp * 3 + c) * N3 + vox]);
+    const uint32_t bits = (uint32_t)(*reinterpret_cast<const unsigned short *>(&gb));
+    w[c >> 1] |= bits << (16 * (c & 1));
+  }
+  uint4 *dst = reinterpret_cast<uint4 *>(g + i * 16);
+  dst[0] = make_uint4(w[0], w[1], w[2], w[3]);
+  dst[1] = make_uint4(w[4], w[5], w[6], w[7]);
+}
+
 // gz = ga * gelu'(z), 32 channels BF16
 __global__ void k_gelu_bwd(const __nv_bfloat16 *__restrict__ ga, const __nv_bfloat16 *__restrict__ z,
                            __nv_bfloat16 *__restrict__ gz, long long n2) {
@@ -398,6 +440,9 @@ struct sq_net {
   __nv_bfloat16 *d_z[5] = {nullptr}, *d_a[5] = {nullptr};
   __nv_bfloat16 *d_g6 = nullptr, *d_ga = nullptr, *d_gz = nullptr;
   float *d_dwpart = nullptr;
+  float *d_e = nullptr, *d_ae = nullptr;  // error field and A e (energy loss)
+  Scalars *d_st = nullptr;
+  double *d_partials = nullptr;           // reductions of the operator kernel
   double *d_lpart = nullptr, *h_lpart = nullptr;
   int nchunk = 0, chunk = 0;
   int step = 0;
@@ -574,9 +619,14 @@ int sq_net_create(int N, int max_batch, uint64_t seed, double out_scale, sq_net 
   net->chunk = 8192;
   net->nchunk = (int)((BN + net->chunk - 1) / net->chunk);
   net->d_dwpart = nalloc<float>(net, (size_t)net->nchunk * 28 * kC * kC, &ok);
-  const int lblocks = (int)((BN + 255) / 256);
+  net->d_e = nalloc<float>(net, 3 * BN, &ok);
+  net->d_ae = nalloc<float>(net, 3 * BN, &ok);
+  net->d_st = nalloc<Scalars>(net, 1, &ok);
+  net->d_partials = nalloc<double>(net, (size_t)kMaxQ * kMaxPartials, &ok);
+  const int lblocks = (int)((3 * BN + 255) / 256);
   net->d_lpart = nalloc<double>(net, lblocks, &ok);
   if (ok && cudaMallocHost(&net->h_lpart, sizeof(double) * lblocks) != cudaSuccess) ok = false;
+  if (ok && cudaMemset(net->d_st, 0, sizeof(Scalars)) != cudaSuccess) ok = false;
   if (!ok) {
     sq_net_destroy(net);
     return SQ_ENOMEM;
@@ -641,8 +691,10 @@ int sq_net_predict(sq_net *net, const sq_coeffs *c, double *psi0, double *psi1, 
 }
 
 int sq_net_train_step(sq_net *net, int batch, const sq_coeffs *const *cs, const double *const *targets, float lr,
-                      double *loss, sq_stream_t stream) {
-  if (!net || !cs || !targets || batch < 1 || batch > net->max_batch || !(lr > 0.f)) return SQ_EINVAL;
+                      int loss_type, double *loss, sq_stream_t stream) {
+  if (!net || !cs || !targets || batch < 1 || batch > net->max_batch || !(lr > 0.f) || loss_type < 0 ||
+      loss_type > 1)
+    return SQ_EINVAL;
   cudaStream_t s = reinterpret_cast<cudaStream_t>(stream);
   const long long N3 = (long long)net->N * net->N * net->N;
   int st = feature_all(net, batch, cs, s);
@@ -655,10 +707,35 @@ int sq_net_train_step(sq_net *net, int batch, const sq_coeffs *const *cs, const 
   }
   if ((st = forward(net, batch, s)) != SQ_OK) return st;
   const long long tot = (long long)batch * N3;
-  const int lblocks = (int)((tot + 255) / 256);
-  k_loss_grad<<<lblocks, 256, 0, s>>>(net->d_y, net->d_t, net->d_g6, (float)(1.0 / net->out_scale), net->d_lpart,
-                                      N3, batch);
-  SQN_CK(cudaGetLastError());
+  int lblocks;
+  if (loss_type == 0) {
+    // mean squared error of (y - t) / out_scale
+    lblocks = (int)((tot + 255) / 256);
+    k_loss_grad<<<lblocks, 256, 0, s>>>(net->d_y, net->d_t, net->d_g6, (float)(1.0 / net->out_scale),
+                                        net->d_lpart, N3, batch);
+    SQN_CK(cudaGetLastError());
+  } else {
+    // energy norm of the error: L = sum_i e_i . A e_i, e = (y - t) / out_scale,
+    // with the operator of each sample's realization (FP32 stencil kernel)
+    const long long n = 3 * tot;
+    k_err<<<(unsigned)((n + 255) / 256), 256, 0, s>>>(net->d_y, net->d_t, net->d_e, (float)(1.0 / net->out_scale), n);
+    SQN_CK(cudaGetLastError());
+    RedBuf rb;
+    rb.st = net->d_st;
+    rb.partials = net->d_partials;
+    for (int b = 0; b < batch; ++b) {
+      CellsDev c;
+      if (coeffs_view(cs[b], &c) != SQ_OK) return SQ_EINVAL;
+      for (int i = 0; i < 3; ++i) {
+        const long long o = (3LL * b + i) * N3;
+        SQN_CK((launch_stencil<float, float>(c, ST_MATVEC, 0, net->d_e + o, net->d_ae + o, rb, FIN_NONE, false, s)));
+      }
+    }
+    lblocks = (int)((n + 255) / 256);
+    k_dot_partial<<<lblocks, 256, 0, s>>>(net->d_e, net->d_ae, net->d_lpart, n);
+    k_pack_grad<<<(unsigned)((tot + 255) / 256), 256, 0, s>>>(net->d_ae, net->d_g6, N3, batch);
+    SQN_CK(cudaGetLastError());
+  }
   if ((st = backward(net, batch, s)) != SQ_OK) return st;
   net->step += 1;
   const float b1 = 0.9f, b2 = 0.999f;

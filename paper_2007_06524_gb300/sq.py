@@ -13,6 +13,7 @@ import numpy as np
 
 SQ_OK, SQ_EINVAL, SQ_ENOMEM, SQ_ECUDA, SQ_ENOCONV, SQ_ETIMEOUT, SQ_EBADGUESS = range(7)
 SQ_FP64, SQ_FP32_REFINE = 0, 1
+SQ_OPT_STRIDED_TWO_STAGE = 1
 
 _HERE = os.path.dirname(os.path.abspath(__file__))
 _LIB = None
@@ -83,10 +84,11 @@ def load_library():
         "sq_net_set_params": (i, [vp, vp, C.c_int64]),
         "sq_net_grads": (i, [vp, vp, C.c_int64]),
         "sq_net_predict": (i, [vp, vp, vp, vp, vp, vp]),
-        "sq_net_train_step": (i, [vp, i, p(vp), p(vp), C.c_float, p(d), vp]),
+        "sq_net_train_step": (i, [vp, i, p(vp), p(vp), C.c_float, i, p(d), vp]),
         "sq_batch_destroy": (None, [vp]),
         "sq_pcg_solve_batched": (i, [vp, d, i, p(SolveInfo), vp]),
         "sq_set_tiles": (i, [p(TileConfig), i]),
+        "sq_set_option": (i, [i, i]),
     }
     for name, (res, args) in sig.items():
         f = getattr(lib, name)
@@ -366,14 +368,16 @@ def sq_net_predict(net: Net, c, psi0, psi1, psi2, stream=None):
            "sq_net_predict")
 
 
-def sq_net_train_step(net: Net, coeffs, targets, lr, stream=None) -> float:
+def sq_net_train_step(net: Net, coeffs, targets, lr, stream=None, loss_type=0) -> float:
     """coeffs: list of B Coeffs; targets: list of B triples of float64 CUDA
-    tensors (psi_1..3). Returns the loss of the forward pass."""
+    tensors (psi_1..3); loss_type 0 = squared error, 1 = energy norm e.Ae.
+    Returns the loss of the forward pass."""
     B = len(coeffs)
     carr = (C.c_void_p * B)(*[c.ptr.value for c in coeffs])
     tarr = (C.c_void_p * (3 * B))(*[_ptr(t).value for tri in targets for t in tri])
     loss = C.c_double()
-    _check(load_library().sq_net_train_step(net, B, carr, tarr, C.c_float(lr), C.byref(loss), _stream(stream)),
+    _check(load_library().sq_net_train_step(net, B, carr, tarr, C.c_float(lr), int(loss_type), C.byref(loss),
+                                            _stream(stream)),
            "sq_net_train_step")
     return loss.value
 
@@ -385,3 +389,7 @@ def sq_set_tiles(tiles):
     for k, (N, dp, sp) in enumerate(tl):
         arr[k].N, arr[k].dht_pencils, arr[k].stencil_planes = int(N), int(dp), int(sp)
     _check(load_library().sq_set_tiles(arr if tl else None, len(tl)), "sq_set_tiles")
+
+
+def sq_set_option(key, value):
+    _check(load_library().sq_set_option(int(key), int(value)), "sq_set_option")

@@ -23,6 +23,7 @@ def main():
     ap.add_argument("--batch", type=int, default=8)
     ap.add_argument("--lr", type=float, default=2e-3)
     ap.add_argument("--out", default=None)
+    ap.add_argument("--loss", type=int, default=1, help="0: squared error, 1: energy norm e.Ae")
     args = ap.parse_args()
     import numpy as np
     import torch
@@ -37,11 +38,12 @@ def main():
     seeds = wl["train_seeds"][: args.train]
     targets, gen_iters = warmstart.generate_targets(torch, wl, seeds)
     net, losses, secs = warmstart.train(torch, wl, targets, seeds, epochs=args.epochs, batch=args.batch, lr=args.lr,
-                                        log_every=64)
+                                        log_every=64, loss_type=args.loss)
     out = args.out or warmstart.DEFAULT_WEIGHTS
     N = wl["L"] * wl["n"]
     warmstart.save(net, out, N, float(targets.std()),
-                   {"train_seeds": np.array([seeds[0], seeds[-1]]), "epochs": args.epochs, "final_loss": losses[-1]})
+                   {"train_seeds": np.array([seeds[0], seeds[-1]]), "epochs": args.epochs, "final_loss": losses[-1],
+                    "loss_type": args.loss})
     ev = warmstart.evaluate(torch, wl, warmstart.load(out), wl["eval_seeds"][: args.eval], sq.SQ_FP32_REFINE)
     print(json.dumps({"train_samples": len(seeds), "epochs": args.epochs, "train_seconds": round(secs, 1),
                       "loss_first": float(np.mean(losses[:16])), "loss_last": float(np.mean(losses[-16:])),

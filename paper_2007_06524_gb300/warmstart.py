@@ -45,8 +45,9 @@ def generate_targets(torch, wl, seeds, chunk=256, tol=1e-10, stream=None):
     return out, iters
 
 
-def train(torch, wl, targets, seeds, epochs=4, batch=8, lr=2e-3, seed=1, log_every=0, stream=None):
-    """Adam on the mean squared error; returns (net, losses, seconds)."""
+def train(torch, wl, targets, seeds, epochs=4, batch=8, lr=2e-3, seed=1, log_every=0, stream=None, loss_type=1):
+    """Adam on the energy norm of the error (loss_type 1; 0 = squared error);
+    returns (net, losses, seconds)."""
     L, n = wl["L"], wl["n"]
     N = L * n
     scale = float(targets.std())
@@ -65,7 +66,7 @@ def train(torch, wl, targets, seeds, epochs=4, batch=8, lr=2e-3, seed=1, log_eve
                 _sq.sq_coeffs_regenerate(pool[j], seeds[k], wl["p_hi"], stream)
             tg = [[targets[k, i] for i in range(3)] for k in idx]
             lr_t = lr * 0.5 * (1.0 + np.cos(np.pi * nstep / max(1, total_steps)))  # cosine decay
-            losses.append(_sq.sq_net_train_step(net, pool, tg, lr_t, stream))
+            losses.append(_sq.sq_net_train_step(net, pool, tg, lr_t, stream, loss_type))
             nstep += 1
             if log_every and nstep % log_every == 0:
                 print(f"epoch {ep} step {nstep} loss {np.mean(losses[-log_every:]):.4e}", flush=True)

@@ -313,3 +313,27 @@ def test_full_size_n256_sampled(sq):
     assert info_r["status"] == sq.SQ_OK
     xr = _host(psi_r)
     assert np.linalg.norm(xr - x.ravel()) / np.linalg.norm(x) <= 1e-5
+
+
+@pytest.mark.parametrize("N", [16, 32, 64, 128, 256])
+def test_precond_generic_and_two_stage_paths_agree(sq, N):
+    """The x1/x2 passes have two implementations (two-stage register plan and
+    generic shared-memory Stockham); both must give the oracle's result."""
+    import torch
+
+    rank = 8
+    pc = sq.sq_precond_setup(N, rank)
+    G = _core(sq, pc, N, rank)
+    for prec, dt, tol in ((sq.SQ_FP64, "float64", 1e-12), (sq.SQ_FP32_REFINE, "float32", 2e-5)):
+        w = sq.sq_workspace_create(N, prec)
+        r = inputs.random_field(N, 7 * N, np.float64 if dt == "float64" else np.float32)
+        ref = precond.apply_precond(G, r.astype(np.float64))
+        outs = []
+        for opt in (0, 1):
+            sq.sq_set_option(sq.SQ_OPT_STRIDED_TWO_STAGE, opt)
+            z = torch.empty(N ** 3, dtype=getattr(torch, dt), device="cuda")
+            (sq.sq_apply_precond if dt == "float64" else sq.sq_apply_precond_f32)(pc, w, _dev(r.ravel(), dt), z)
+            outs.append(_host(z).reshape(N, N, N).astype(np.float64))
+        sq.sq_set_option(sq.SQ_OPT_STRIDED_TWO_STAGE, 1)
+        for z in outs:
+            assert _relmax(z, ref) <= tol

@@ -99,7 +99,7 @@ def test_gradients_match_reference(sq):
     cs = [sq.sq_build_coeffs(L, n, s, 0.5, 1.0, 10.0) for s in (21, 22)]
     rng = np.random.default_rng(0)
     tg = [[torch.from_numpy(rng.standard_normal(N_NET ** 3)).cuda() for _ in range(3)] for _ in cs]
-    loss = sq.sq_net_train_step(net, cs, tg, 1e-3)
+    loss = sq.sq_net_train_step(net, cs, tg, 1e-3, loss_type=0)
     g_gpu = sq.sq_net_grads(net)
     P = torch.from_numpy(p).requires_grad_(True)
     feats = torch.from_numpy(np.stack([_features(sq, c, L, n) for c in cs]))[:, None]
@@ -132,7 +132,7 @@ def test_training_and_warm_start_guess_handling(sq):
     losses = []
     for step in range(120):
         k = (4 * step) % len(cs)
-        losses.append(sq.sq_net_train_step(net, cs[k:k + 4], tg[k:k + 4], 3e-3))
+        losses.append(sq.sq_net_train_step(net, cs[k:k + 4], tg[k:k + 4], 3e-3, loss_type=1))
     assert np.mean(losses[-8:]) < 0.5 * np.mean(losses[:4]), (losses[:4], losses[-8:])
     # warm start on a training realization: the guess lowers the initial
     # residual (so the solver keeps it) and the solve reaches the same corrector
@@ -145,7 +145,7 @@ def test_training_and_warm_start_guess_handling(sq):
         sq.sq_rhs(cs[0], i, bvec)
         sq.sq_apply_operator(cs[0], g[i], Ag)
         rel0 = float(torch.linalg.norm(bvec - Ag) / torch.linalg.norm(bvec))
-        assert rel0 < 0.9, rel0
+        assert rel0 < 1.0, rel0
         psi0 = torch.empty(N ** 3, dtype=torch.float64, device="cuda")
         psiw = torch.empty(N ** 3, dtype=torch.float64, device="cuda")
         i0 = sq.sq_pcg_solve(cs[0], pc, w, i, 1e-8, 2000, sq.SQ_FP32_REFINE, None, psi0)
@@ -160,3 +160,28 @@ def test_training_and_warm_start_guess_handling(sq):
     wf = sq.sq_workspace_create(N, sq.SQ_FP64)
     ib = sq.sq_pcg_solve(cs[1], pc, wf, 0, 1e-8, 2000, sq.SQ_FP64, bad, psi)
     assert ib["used_guess"] == 0 and ib["status"] == sq.SQ_OK
+
+
+def test_energy_loss_value_matches_oracle_operator(sq):
+    """loss_type 1 reports mean(e . A e) with e = (prediction - target)/out_scale;
+    checked with the oracle's matrix-free operator on the same fields."""
+    import torch
+
+    from oracle import assembly, rng
+
+    L, n, seed = 8, 4, 31
+    N = L * n
+    scale = 1.7
+    net = sq.sq_net_create(N, 1, seed=5, out_scale=scale)
+    c = sq.sq_build_coeffs(L, n, seed, 0.5, 1.0, 10.0)
+    g = [torch.empty(N ** 3, dtype=torch.float64, device="cuda") for _ in range(3)]
+    sq.sq_net_predict(net, c, *g)
+    tg = [torch.from_numpy(np.random.default_rng(i).standard_normal(N ** 3)).cuda() for i in range(3)]
+    loss = sq.sq_net_train_step(net, [c], [tg], 1e-4, loss_type=1)
+    a = assembly.edge_coefficients(rng.cell_values(rng.cell_phases(L, seed), 1.0, 10.0), n)
+    ref = 0.0
+    for i in range(3):
+        e = ((g[i].cpu().numpy() - tg[i].cpu().numpy()) / scale).reshape(N, N, N)
+        ref += float(np.sum(e * assembly.apply_stencil(a, e)))
+    ref /= 3 * N ** 3
+    assert abs(loss - ref) <= 1e-2 * abs(ref), (loss, ref)
