@@ -287,6 +287,7 @@ def run_native(args):
     if not args.no_variants and rank == 0:
         out.setdefault("variants", {})["batch_768_mixed"] = run_batch(sq, torch, stream)
         out["variants"]["warm_start_n64"] = run_warm_start(sq, torch)
+        out["variants"]["refine_n512"] = run_refine_n512(sq, torch, stream)
 
     if rank == 0 and not args.no_cpu_baseline and ws == 1:
         out["cpu_baseline"] = cpu_baseline(statistics.mean(iters), R)
@@ -348,6 +349,38 @@ def run_warm_start(sq, torch, nseeds=64):
     res = {"eval_seeds": f"{seeds[0]}..{seeds[-1]}"}
     res["fp32_refine"] = warmstart.evaluate(torch, wl, net, seeds, sq.SQ_FP32_REFINE)
     res["fp64"] = warmstart.evaluate(torch, wl, net, seeds[:16], sq.SQ_FP64)
+    return res
+
+
+def run_refine_n512(sq, torch, stream):
+    """L=64, n=8 (N=512, 134 M unknowns), Bernoulli(1/2) on {1,100}, three
+    correctors: FP32 PCG inside FP64 refinement to rel. residual 1e-10, exact
+    and rank-8 preconditioners (one realization, seed 0)."""
+    from paper_2007_06524_gb300 import autotune, workloads
+
+    wl = workloads.REFINE_N512
+    L, n = wl["L"], wl["n"]
+    N = L * n
+    autotune.tune(torch, N, L, n, cache=None)
+    c = sq.sq_build_coeffs(L, n, 0, wl["p_hi"], wl["a_lo"], wl["a_hi"])
+    w = sq.sq_workspace_create(N, sq.SQ_FP32_REFINE)
+    psi = torch.empty(N ** 3, dtype=torch.float64, device="cuda")
+    res = {}
+    for rank in wl["ranks"]:
+        pc = sq.sq_precond_setup(N, rank)
+        sq.sq_pcg_solve(c, pc, w, 0, wl["tol"], 4000, sq.SQ_FP32_REFINE, None, psi)  # warm-up
+        torch.cuda.synchronize()
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        infos = [sq.sq_pcg_solve(c, pc, w, i, wl["tol"], 4000, sq.SQ_FP32_REFINE, None, psi) for i in range(3)]
+        e1.record(stream)
+        torch.cuda.synchronize()
+        t = e0.elapsed_time(e1) / 1e3
+        res[f"rank{rank}"] = {"solves_per_s": round(3 / t, 3), "iters_mean": round(statistics.mean(i["iters"] for i in infos), 1),
+                              "outer_steps": [i["outer_steps"] for i in infos],
+                              "relres_true_max": max(i["relres_true"] for i in infos),
+                              "converged": all(i["status"] == sq.SQ_OK for i in infos)}
+        del pc
     return res
 
 

@@ -170,9 +170,11 @@ typedef struct sq_tile_config {
 int sq_set_tiles(const sq_tile_config *tiles, int ntiles);
 
 /* Process-wide switches (not thread-safe with concurrent solves).
- * SQ_OPT_STRIDED_TWO_STAGE (default 1): the x1/x2 Hartley passes use the
- * two-stage register plan where N allows (16, 32, 64, 128, 256); 0 selects the
- * generic shared-memory Stockham tile for every pass. */
+ * SQ_OPT_STRIDED_TWO_STAGE (default 1): the FP32 x2 Hartley passes use the
+ * two-stage register plan where N allows (16, 32, 64, 128, 256); 2 also uses it
+ * for FP64 and for the x1 scaling pass (slower on GB300, kept for
+ * verification); 0 selects the generic shared-memory Stockham tile
+ * everywhere. */
 enum sq_option { SQ_OPT_STRIDED_TWO_STAGE = 1 };
 int sq_set_option(int key, int value);
 

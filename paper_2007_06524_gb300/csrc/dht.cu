@@ -151,7 +151,8 @@ static int g_pencils_override[kMaxN + 1] = {0};  // FP32 passes, per N (0 = defa
 static int g_strided_fast = 1;                    // two-stage strided passes where N allows
 
 int set_strided_fast(int on) {
-  g_strided_fast = on ? 1 : 0;
+  if (on < 0 || on > 2) return 1;
+  g_strided_fast = on;
   return 0;
 }
 
@@ -207,19 +208,21 @@ cudaError_t launch_dht_pass(int pass, const SpectralDev &sp, const T *in, T *out
     case PASS_A_RESID: return launch_one<T, 3, LD_RESID, SO_PLAIN, false>(a, grid, smem, s);
     case PASS_A_PLAIN: return launch_one<T, 3, LD_PLAIN, SO_PLAIN, false>(a, grid, smem, s);
     case PASS_B: {
-      if (g_strided_fast) {
+      // FP32 only: in FP64 the ALU-bound pass prefers the generic tile
+      if (g_strided_fast && (sizeof(T) == 4 || g_strided_fast > 1)) {
         const cudaError_t e = launch_strided_fast<T, 2, false>(a, grid, s);
         if (e != cudaErrorNotSupported) return e;
       }
       return launch_one<T, 2, LD_PLAIN, SO_PLAIN, false>(a, grid, smem, s);
     }
-    case PASS_C: {
-      if (g_strided_fast) {
+    case PASS_C:
+      // measured on GB300: the two-stage plan loses here (register pressure,
+      // 9 of 16 stage-2 units per pencil), so pass C keeps the generic tile
+      if (g_strided_fast > 1) {
         const cudaError_t e = launch_strided_fast<T, 1, true>(a, grid, s);
         if (e != cudaErrorNotSupported) return e;
       }
       return launch_one<T, 1, LD_PLAIN, SO_PLAIN, true>(a, grid, smem, s);
-    }
     case PASS_E_PCG: return launch_one<T, 3, LD_PLAIN, SO_PCG, false>(a, grid, smem, s);
     case PASS_E_PLAIN: return launch_one<T, 3, LD_PLAIN, SO_PLAIN, false>(a, grid, smem, s);
     default: return cudaErrorInvalidValue;

@@ -219,7 +219,7 @@ void sinc_nodes(int N, int R, std::vector<double> &t, std::vector<double> &w) {
 
 // Least-squares solve min ||E w - 1|| (M x R, column-major copy) by Householder QR.
 bool lsq_ones(std::vector<double> E, int M, int R, std::vector<double> &w) {
-  if (M < 2 * R) return false;  // too few distinct spectral values for a fit
+  if (R < 1 || M < 2 * R) return false;  // too few distinct spectral values for a fit
   std::vector<double> rhs(M, 1.0);
   for (int k = 0; k < R; ++k) {
     double nrm = 0.0;

@@ -329,7 +329,7 @@ def test_precond_generic_and_two_stage_paths_agree(sq, N):
         r = inputs.random_field(N, 7 * N, np.float64 if dt == "float64" else np.float32)
         ref = precond.apply_precond(G, r.astype(np.float64))
         outs = []
-        for opt in (0, 1):
+        for opt in (0, 1, 2):
             sq.sq_set_option(sq.SQ_OPT_STRIDED_TWO_STAGE, opt)
             z = torch.empty(N ** 3, dtype=getattr(torch, dt), device="cuda")
             (sq.sq_apply_precond if dt == "float64" else sq.sq_apply_precond_f32)(pc, w, _dev(r.ravel(), dt), z)
@@ -337,3 +337,17 @@ def test_precond_generic_and_two_stage_paths_agree(sq, N):
         sq.sq_set_option(sq.SQ_OPT_STRIDED_TWO_STAGE, 1)
         for z in outs:
             assert _relmax(z, ref) <= tol
+
+
+def test_refinement_n128_against_oracle(sq):
+    """The precision configuration's oracle subsample: L=16, n=8 (N=128),
+    Bernoulli(1/2) on {1,100}, FP32 PCG inside FP64 refinement to 1e-10: error
+    against the FP64 oracle's tight solve <= 1e-6 (stated per result)."""
+    re = problem.realization(16, 8, 0, 1.0, 100.0)
+    ref = pcg.tight_solve(re.A, re.b[0], re.N)[0]
+    c = sq.sq_build_coeffs(16, 8, 0, 0.5, 1.0, 100.0)
+    for rank in (0, 8):
+        psi, info = _solve(sq, c, re.N, 0, rank, 1e-10, precision=sq.SQ_FP32_REFINE, max_iter=4000)
+        assert info["status"] == sq.SQ_OK and info["relres_true"] <= 1e-10
+        err = np.linalg.norm(_host(psi) - ref) / np.linalg.norm(ref)
+        assert err <= 1e-6, (rank, err)
