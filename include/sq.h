@@ -170,11 +170,11 @@ typedef struct sq_tile_config {
 int sq_set_tiles(const sq_tile_config *tiles, int ntiles);
 
 /* Process-wide switches (not thread-safe with concurrent solves).
- * SQ_OPT_STRIDED_TWO_STAGE (default 1): the FP32 x2 Hartley passes use the
- * two-stage register plan where N allows (16, 32, 64, 128, 256); 2 also uses it
- * for FP64 and for the x1 scaling pass (slower on GB300, kept for
- * verification); 0 selects the generic shared-memory Stockham tile
- * everywhere. */
+ * SQ_OPT_STRIDED_TWO_STAGE (default 1): the FP32 x1/x2 Hartley passes use the
+ * two-stage plan (one register stage from global memory, one in-place shared
+ * memory stage, an all-thread combine) where N allows (16, 32, 64, 128, 256);
+ * 2 also uses it for FP64 (ALU-bound: the generic tile is faster there); 0
+ * selects the generic shared-memory Stockham tile everywhere. */
 enum sq_option { SQ_OPT_STRIDED_TWO_STAGE = 1 };
 int sq_set_option(int key, int value);
 

@@ -216,9 +216,8 @@ cudaError_t launch_dht_pass(int pass, const SpectralDev &sp, const T *in, T *out
       return launch_one<T, 2, LD_PLAIN, SO_PLAIN, false>(a, grid, smem, s);
     }
     case PASS_C:
-      // measured on GB300: the two-stage plan loses here (register pressure,
-      // 9 of 16 stage-2 units per pencil), so pass C keeps the generic tile
-      if (g_strided_fast > 1) {
+      // FP32 only by default: in FP64 the ALU-bound pass prefers the generic tile
+      if (g_strided_fast && (sizeof(T) == 4 || g_strided_fast > 1)) {
         const cudaError_t e = launch_strided_fast<T, 1, true>(a, grid, s);
         if (e != cudaErrorNotSupported) return e;
       }

@@ -382,86 +382,75 @@ __device__ __forceinline__ C hartley_pair(const C X, const C Y) {
   return C{X.x - X.y + Y.x + Y.y, X.x + X.y - Y.x + Y.y};
 }
 
-// Stage 2 + Hartley combine. MODE 0: store to global; 1: scale by G (r.z into
-// acc) and write back to shared memory for the second transform.
-template <typename T, typename C, int R0, int R1, int MODE>
-__device__ __forceinline__ void s2_stage2(C *sm, int SP, int logP, const C *__restrict__ tw, C *__restrict__ gdst,
-                                          size_t base, size_t stride, const SpectralDev &sp, int k2, int c0,
-                                          const T *vtab, Accum<T> &acc) {
-  constexpr int N = R0 * R1;
-  static_assert((R0 / 2 + 1) * 16 <= kThreads, "one stage-2 unit per thread");
+// Stage 2 (radix R1, twiddles tw[q b]) in place: butterfly b of pencil p reads
+// and writes exactly the positions b + q R0, so threads never touch each
+// other's data and no barrier is needed between reads and writes.
+template <typename T, typename C, int R0, int R1>
+__device__ __forceinline__ void s2_stage2(C *sm, int SP, int logP, const C *__restrict__ tw) {
+  static_assert(R0 * 16 <= kThreads, "one stage-2 butterfly per thread");
   const int P = 1 << logP;
-  const int nu = (R0 / 2 + 1) << logP;
+  const int nb = R0 << logP;
   const int t = threadIdx.x;
-  if (t < nu) {
-    const int p = t & (P - 1), bb = t >> logP;
-    const int b1 = bb, b2 = (R0 - bb) & (R0 - 1);
-    const bool two = (b2 != b1);
-    C x1[R1], x2[R1];
+  if (t < nb) {
+    const int p = t & (P - 1), b = t >> logP;
+    C x[R1];
 #pragma unroll
     for (int q = 0; q < R1; ++q) {
-      x1[q] = sm[(b1 + q * R0) * SP + p];
-      if (q > 0) x1[q] = cmul(x1[q], tw[q * b1]);
+      x[q] = sm[(b + q * R0) * SP + p];
+      if (q > 0) x[q] = cmul(x[q], tw[q * b]);
     }
-    dft<T, C, R1>(x1);
-    if (two) {
+    dft<T, C, R1>(x);
 #pragma unroll
-      for (int q = 0; q < R1; ++q) {
-        x2[q] = sm[(b2 + q * R0) * SP + p];
-        if (q > 0) x2[q] = cmul(x2[q], tw[q * b2]);
-      }
-      dft<T, C, R1>(x2);
-    }
-    const T *lam = reinterpret_cast<const T *>(sp.lam);
-    const T *uf = reinterpret_cast<const T *>(sp.u);
-    const int R = sp.rank;
-    const T gscale = (T)sp.scale;
-    const int k3a = c0 + 2 * p, k3b = k3a + 1;
-    // Output m = b + q R0 of butterfly b; its mirror N - m sits in butterfly
-    // (R0 - b) mod R0 at index R1-1-q, except b = 0: index (R1 - q) mod R1.
-#pragma unroll
-    for (int w = 0; w < 2; ++w) {
-      if (w == 1 && !two) break;
-      const int bw = (w == 0) ? b1 : b2;
-#pragma unroll
-      for (int q = 0; q < R1; ++q) {
-        const C X = (w == 0) ? x1[q] : x2[q];
-        C mir;
-        if (bw == 0)
-          mir = x1[(R1 - q) & (R1 - 1)];
-        else if (!two)
-          mir = x1[R1 - 1 - q];
-        else
-          mir = (w == 0) ? x2[R1 - 1 - q] : x1[R1 - 1 - q];
-        C h = hartley_pair(X, mir);
-        const int m = bw + q * R0;
-        if (MODE == 1) {
-          T ga, gb;
-          if (R == 0) {
-            const T l12 = lam[m] + lam[k2];
-            const T g1 = l12 + lam[k3a], g2 = l12 + lam[k3b];
-            ga = (g1 > (T)0) ? gscale / g1 : (T)0;
-            gb = (g2 > (T)0) ? gscale / g2 : (T)0;
-          } else {
-            T sa = (T)0, sb = (T)0;
-            for (int rr = 0; rr < R; ++rr) {
-              const T uk = uf[rr * N + m];
-              sa = fma(uk, vtab[rr * 2 * P + 2 * p], sa);
-              sb = fma(uk, vtab[rr * 2 * P + 2 * p + 1], sb);
-            }
-            ga = (m == 0 && k2 == 0 && k3a == 0) ? (T)0 : sa;
-            gb = sb;
-          }
-          acc.add(fma(ga * h.x, h.x, gb * h.y * h.y));
-          h = C{h.x * ga, h.y * gb};
+    for (int q = 0; q < R1; ++q) sm[(b + q * R0) * SP + p] = x[q];
+  }
+  __syncthreads();
+}
+
+// Hartley combine of the spectrum X in shared memory: thread (p, k), k <= N/2,
+// forms 2(H a), 2(H b) at k and N - k. MODE 0: store to global (rows of P
+// complex values, coalesced); 1: scale by G, reduce r.z into acc, write back in
+// place for the second transform.
+template <typename T, typename C, int N, int MODE>
+__device__ __forceinline__ void s2_combine(C *sm, int SP, int logP, C *__restrict__ gdst, size_t base, size_t stride,
+                                           const SpectralDev &sp, int k2, int c0, const T *vtab, Accum<T> &acc) {
+  const int P = 1 << logP;
+  const T *lam = reinterpret_cast<const T *>(sp.lam);
+  const T *uf = reinterpret_cast<const T *>(sp.u);
+  const int R = sp.rank;
+  const T gscale = (T)sp.scale;
+  for (int t = threadIdx.x; t < ((N / 2 + 1) << logP); t += kThreads) {
+    const int p = t & (P - 1), k = t >> logP;
+    const int km = (k == 0) ? 0 : N - k;
+    const C X = sm[k * SP + p], Y = sm[km * SP + p];
+    C hk = hartley_pair(X, Y), hm = hartley_pair(Y, X);
+    if (MODE == 1) {
+      const int k3a = c0 + 2 * p, k3b = k3a + 1;
+      T ga, gb;
+      if (R == 0) {
+        const T l12 = lam[k] + lam[k2];
+        const T g1 = l12 + lam[k3a], g2 = l12 + lam[k3b];
+        ga = (g1 > (T)0) ? gscale / g1 : (T)0;
+        gb = (g2 > (T)0) ? gscale / g2 : (T)0;
+      } else {
+        T sa = (T)0, sb = (T)0;
+        for (int rr = 0; rr < R; ++rr) {
+          const T uk = uf[rr * N + k];
+          sa = fma(uk, vtab[rr * 2 * P + 2 * p], sa);
+          sb = fma(uk, vtab[rr * 2 * P + 2 * p + 1], sb);
         }
-        // writes after all reads of this unit's positions: the mirrors come from
-        // registers, so in-place shared-memory writes are safe
-        if (MODE == 0)
-          gdst[(base + (size_t)m * stride) / 2 + p] = h;
-        else
-          sm[m * SP + p] = h;
+        ga = (k == 0 && k2 == 0 && k3a == 0) ? (T)0 : sa;
+        gb = sb;
       }
+      T e2 = fma(ga * hk.x, hk.x, gb * hk.y * hk.y);
+      if (km != k) e2 += fma(ga * hm.x, hm.x, gb * hm.y * hm.y);
+      acc.add(e2);
+      hk = C{hk.x * ga, hk.y * gb};
+      hm = C{hm.x * ga, hm.y * gb};  // G(N - k) = G(k)
+      sm[k * SP + p] = hk;
+      if (km != k) sm[km * SP + p] = hm;
+    } else {
+      gdst[(base + (size_t)k * stride) / 2 + p] = hk;
+      if (km != k) gdst[(base + (size_t)km * stride) / 2 + p] = hm;
     }
   }
   __syncthreads();
@@ -493,11 +482,13 @@ __device__ __forceinline__ void dht_tile_s2(const SpectralDev &sp, const DhtTile
   const C *gin = reinterpret_cast<const C *>(a.in);
   C *gout = reinterpret_cast<C *>(a.out);
   s2_stage1<T, C, R0, R1, false>(gin, base, stride, sm, SP, logP);
+  s2_stage2<T, C, R0, R1>(sm, SP, logP, tw);
   if (SCALE) {
-    s2_stage2<T, C, R0, R1, 1>(sm, SP, logP, tw, gout, base, stride, sp, k2, c0, vtab, acc);
+    s2_combine<T, C, N, 1>(sm, SP, logP, gout, base, stride, sp, k2, c0, vtab, acc);
     s2_stage1<T, C, R0, R1, true>(gin, base, stride, sm, SP, logP);
+    s2_stage2<T, C, R0, R1>(sm, SP, logP, tw);
   }
-  s2_stage2<T, C, R0, R1, 0>(sm, SP, logP, tw, gout, base, stride, sp, k2, c0, vtab, acc);
+  s2_combine<T, C, N, 0>(sm, SP, logP, gout, base, stride, sp, k2, c0, vtab, acc);
 }
 
 }  // namespace sq
