@@ -2,8 +2,8 @@
 the fastest per grid size with sq_set_tiles.
 
 Tuned per N: the number of complex pencils of a Hartley-pass tile (FP32 passes;
-2P real pencils, 2P * 4 bytes per row segment) and the number of x1-planes of
-an operator block. Each candidate is timed with CUDA events over a few
+2P real pencils, 2P * 4 bytes per row segment), and jointly the node rows per
+thread and the x1-planes per work item of the FP32 operator. Each candidate is timed with CUDA events over a few
 repetitions of the kernel it drives (sq_apply_precond_f32 for the passes,
 sq_apply_operator_f32 for the operator); results are cached in a JSON file
 keyed by N and the device name.
@@ -31,7 +31,8 @@ def _time(torch, fn, reps=5):
 
 
 def tune(torch, N, L=None, n=None, cache=DEFAULT_CACHE, reps=5):
-    """Returns (dht_pencils, stencil_planes) for grid N and installs them."""
+    """Returns (dht_pencils, stencil_planes) for grid N and installs them,
+    together with the operator's rows per thread, with sq_set_tiles."""
     dev = torch.cuda.get_device_name()
     key = f"{dev}:{N}"
     table = {}
@@ -40,9 +41,9 @@ def tune(torch, N, L=None, n=None, cache=DEFAULT_CACHE, reps=5):
             table = json.load(open(cache))
         except Exception:
             table = {}
-    if key in table:
-        P, zc = table[key]["dht_pencils"], table[key]["stencil_planes"]
-        _sq.sq_set_tiles([(N, P, zc)])
+    if key in table and "stencil_rows" in table[key]:
+        P, zc, rows = table[key]["dht_pencils"], table[key]["stencil_planes"], table[key]["stencil_rows"]
+        _sq.sq_set_tiles([(N, P, zc, rows)])
         return P, zc
     if L is None:
         n = 8 if N % 8 == 0 else 4
@@ -63,19 +64,22 @@ def tune(torch, N, L=None, n=None, cache=DEFAULT_CACHE, reps=5):
         times_p[P] = _time(torch, lambda: _sq.sq_apply_precond_f32(pc, w, r, z), reps)
     bestP = min(times_p, key=times_p.get)
     times_z = {}
-    for zc in (2, 4, 8, 16, 32, 64):
-        if zc > N:
+    for rows in (1, 2, 4):
+        if N % rows != 0:
             continue
-        try:
-            _sq.sq_set_tiles([(N, bestP, zc)])
-        except _sq.SqError:
-            continue
-        times_z[zc] = _time(torch, lambda: _sq.sq_apply_operator_f32(c, r, z), reps)
-    bestZ = min(times_z, key=times_z.get)
-    _sq.sq_set_tiles([(N, bestP, bestZ)])
-    table[key] = {"dht_pencils": bestP, "stencil_planes": bestZ,
+        for zc in (4, 8, 16, 32):
+            if zc > N:
+                continue
+            try:
+                _sq.sq_set_tiles([(N, bestP, zc, rows)])
+            except _sq.SqError:
+                continue
+            times_z[(rows, zc)] = _time(torch, lambda: _sq.sq_apply_operator_f32(c, r, z), reps)
+    bestR, bestZ = min(times_z, key=times_z.get)
+    _sq.sq_set_tiles([(N, bestP, bestZ, bestR)])
+    table[key] = {"dht_pencils": bestP, "stencil_planes": bestZ, "stencil_rows": bestR,
                   "precond_ms": {str(k): round(v, 4) for k, v in times_p.items()},
-                  "operator_ms": {str(k): round(v, 4) for k, v in times_z.items()}}
+                  "operator_ms": {f"{k[0]}x{k[1]}": round(v, 4) for k, v in times_z.items()}}
     if cache:
         os.makedirs(os.path.dirname(cache), exist_ok=True)
         json.dump(table, open(cache, "w"), indent=1)

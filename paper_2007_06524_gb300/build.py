@@ -21,7 +21,7 @@ SOURCES = ["stencil.cu", "dht.cu", "solver.cu", "noalloc.cu", "batch.cu", "warms
 
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 FLAGS = ["-O3", "-lineinfo", "-std=c++17", "-Xcompiler", "-fPIC", "-Xcompiler", "-O2",
-         "--expt-relaxed-constexpr", "-I", INCLUDE, "-I", CSRC]
+         "--expt-relaxed-constexpr", "--Werror", "cross-execution-space-call", "-I", INCLUDE, "-I", CSRC]
 
 
 def _nvcc() -> str:

@@ -70,8 +70,10 @@ __global__ void __launch_bounds__(kThreads) kb_stencil(const BSolve *__restrict_
   Scalars *st = (WHICH == 0) ? B.st_o : B.st_i;
   if (*(volatile int *)&st->done) return;
   __shared__ Ti tab[256][kTabStride];
+  __shared__ short cellof[kMaxN];
   const int tid = threadIdx.x + 32 * threadIdx.y;
   build_pattern_table<Ti>(tab, B.c, tid);
+  build_cellof(cellof, B.c.N, B.c.n, tid);
   __syncthreads();
   const int N = B.c.N;
   const int lb = blockIdx.x - pre[s];
@@ -82,11 +84,12 @@ __global__ void __launch_bounds__(kThreads) kb_stencil(const BSolve *__restrict_
   Accum<Ti> acc0, acc1;
   if (j3 < N && j2 < N) {
     if constexpr (WHICH == 0)
-      stencil_column<double, float, ST_RESID>(B.c, B.dir, B.x, B.r, tab, j3, j2, z0, z1, acc0, acc1);
+      stencil_rows<double, float, ST_RESID, 1>(B.c, B.dir, B.x, B.r, tab, cellof, j3, j2, z0, z1, acc0, acc1);
     else
-      stencil_column<float, float, ST_MATVEC>(B.c, 0, B.p, B.q, tab, j3, j2, z0, z1, acc0, acc1);
+      stencil_rows<float, float, ST_MATVEC, 1>(B.c, 0, B.p, B.q, tab, cellof, j3, j2, z0, z1, acc0, acc1);
   }
-  double v[2] = {acc0.get(), acc1.get()}, out[2];
+  typename Accum<Ti>::Part v[2] = {acc0.part(), acc1.part()};
+  double out[2];
   if (reduce_last_block_ex<2>(v, B.partials, B.pstride, &st->ticket, B.nb_st, lb, out)) {
     if (tid == 0) finalize_scalars(st, WHICH == 0 ? FIN_RESID : FIN_ALPHA, out, 2);
   }
@@ -127,7 +130,8 @@ __global__ void __launch_bounds__(kThreads) kb_dht(const BSolve *__restrict__ S,
   Accum<float> acc;
   dht_tile<float, AXIS, LOADM, STOREM, SCALE>(B.sp, t, tile, buf0, buf1, tw, vtab, acc);
   if (LOADM == LD_RESID || SCALE) {
-    double v[1] = {acc.get()}, out[1];
+    FF v[1] = {acc.part()};
+    double out[1];
     if (reduce_last_block_ex<1>(v, B.partials, B.pstride, &st->ticket, B.nb_dht, tile, out)) {
       if (threadIdx.x == 0) {
         int op = FIN_NONE;

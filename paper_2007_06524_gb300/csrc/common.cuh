@@ -59,20 +59,45 @@ template <> struct Cx<double> { using type = double2; };
 // ---------------------------------------------------------------- reductions
 
 // Per-thread partial sums. FP64 kernels accumulate in FP64. FP32 kernels use
-// compensated (Kahan) FP32 sums and convert to FP64 once per thread: GB300's
-// FP64 pipe is ~1/58 of its FP32 rate, and one FP64 FMA plus two conversions
-// per point saturate it. Block and global sums are FP64 in both cases.
+// compensated (Kahan) FP32 sums per thread and carry them on as float-float
+// numbers (below) through the warp, block and last-block sums, converting to
+// FP64 once, for the final scalar: GB300's FP64 pipe runs at ~1/58 of its FP32
+// rate, and even a handful of FP64 adds per warp in every block of an FP32
+// pass costs more pipe time than the pass's own arithmetic.
 template <typename T>
 struct Accum;
+
+// Float-float (double-word) value hi + lo, |lo| <= ulp(hi)/2. The sum of two
+// is Knuth's TwoSum of the high parts (exact error term), plus the low parts,
+// renormalised by Dekker's Fast2Sum (Dekker 1971; the "sloppy" double-word
+// addition). Relative error ~2^-44 per addition, with FP32 instructions only.
+struct FF {
+  float hi, lo;
+};
+__device__ __forceinline__ FF ff_renorm(float s, float e) {
+  const float h = s + e;
+  return FF{h, e - (h - s)};
+}
+__device__ __forceinline__ FF ff_add(FF a, FF b) {
+  const float s = a.hi + b.hi;
+  const float bv = s - a.hi;
+  float e = (a.hi - (s - bv)) + (b.hi - bv);
+  e += a.lo + b.lo;
+  return ff_renorm(s, e);
+}
+
 template <>
 struct Accum<double> {
+  using Part = double;
   double s = 0.0;
   __device__ __forceinline__ void add(double v) { s += v; }
   __device__ __forceinline__ void add_prod(double a, double b) { s = fma(a, b, s); }
   __device__ __forceinline__ double get() const { return s; }
+  __device__ __forceinline__ double part() const { return s; }
 };
 template <>
 struct Accum<float> {
+  using Part = FF;
   float s = 0.f, c = 0.f;  // running sum and its compensation (sum = s - c)
   __device__ __forceinline__ void add(float v) {
     const float y = v - c;
@@ -82,11 +107,41 @@ struct Accum<float> {
   }
   __device__ __forceinline__ void add_prod(float a, float b) { add(a * b); }
   __device__ __forceinline__ double get() const { return (double)s - (double)c; }
+  // |c| <= ulp(s) after every step, so Fast2Sum's precondition holds
+  __device__ __forceinline__ FF part() const { return ff_renorm(s, -c); }
 };
+
+// Operations on a partial sum (double or FF) used by the block reductions.
+__device__ __forceinline__ double part_zero(double) { return 0.0; }
+__device__ __forceinline__ FF part_zero(FF) { return FF{0.f, 0.f}; }
+__device__ __forceinline__ double part_add(double a, double b) { return a + b; }
+__device__ __forceinline__ FF part_add(FF a, FF b) { return ff_add(a, b); }
+__device__ __forceinline__ double part_shfl(double v, int o) { return __shfl_xor_sync(0xffffffffu, v, o); }
+__device__ __forceinline__ FF part_shfl(FF v, int o) {
+  return FF{__shfl_xor_sync(0xffffffffu, v.hi, o), __shfl_xor_sync(0xffffffffu, v.lo, o)};
+}
+__device__ __forceinline__ double part_value(double v) { return v; }
+__device__ __forceinline__ double part_value(FF v) { return (double)v.hi + (double)v.lo; }
+// A partial occupies one 8-byte slot of the partials buffer either way.
+__device__ __forceinline__ void part_store(double *p, double v) { *p = v; }
+__device__ __forceinline__ void part_store(double *p, FF v) {
+  *reinterpret_cast<float2 *>(p) = make_float2(v.hi, v.lo);
+}
+__device__ __forceinline__ double part_load(const double *p, double) { return __ldcg(p); }
+__device__ __forceinline__ FF part_load(const double *p, FF) {
+  const float2 f = __ldcg(reinterpret_cast<const float2 *>(p));
+  return FF{f.x, f.y};
+}
 
 __device__ __forceinline__ double warp_sum(double v) {
 #pragma unroll
   for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+  return v;
+}
+template <typename P>
+__device__ __forceinline__ P warp_sum_part(P v) {
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) v = part_add(v, part_shfl(v, o));
   return v;
 }
 
@@ -94,28 +149,30 @@ __device__ __forceinline__ double warp_sum(double v) {
 // the last block to finish sum all partials in a fixed order (deterministic,
 // independent of which block is last). Returns true in every thread of that
 // last block; the sums are then in out[0..NQ). Requires blockDim = kThreads.
+// P is double or FF; the sums stay in P until the final conversion.
 // The explicit form takes the block's index `bid` among the `nblk` blocks that
 // share one ticket, and the partials row stride `pstride` (batched kernels
 // reduce per solve); reduce_last_block uses the whole grid.
-template <int NQ>
-__device__ __forceinline__ bool reduce_last_block_ex(double (&v)[NQ], double *partials, int pstride,
-                                                     unsigned *ticket, int nblk, int bid, double (&out)[NQ]) {
-  __shared__ double s_w[NQ][kThreads / 32];
+template <int NQ, typename P>
+__device__ __forceinline__ bool reduce_last_block_ex(P (&v)[NQ], double *partials, int pstride, unsigned *ticket,
+                                                     int nblk, int bid, double (&out)[NQ]) {
+  __shared__ P s_w[NQ][kThreads / 32];
   __shared__ unsigned s_last;
   const int tid = threadIdx.x + blockDim.x * (threadIdx.y + blockDim.y * threadIdx.z);
   const int lane = tid & 31, wid = tid >> 5;
+  const P z = part_zero(v[0]);
 #pragma unroll
   for (int q = 0; q < NQ; ++q) {
-    double s = warp_sum(v[q]);
+    P s = warp_sum_part(v[q]);
     if (lane == 0) s_w[q][wid] = s;
   }
   __syncthreads();
   if (tid == 0) {
 #pragma unroll
     for (int q = 0; q < NQ; ++q) {
-      double s = 0.0;
-      for (int w = 0; w < kThreads / 32; ++w) s += s_w[q][w];
-      partials[q * pstride + bid] = s;
+      P s = z;
+      for (int w = 0; w < kThreads / 32; ++w) s = part_add(s, s_w[q][w]);
+      part_store(&partials[q * pstride + bid], s);
     }
     __threadfence();
     unsigned t = atomicAdd(ticket, 1u);
@@ -126,24 +183,24 @@ __device__ __forceinline__ bool reduce_last_block_ex(double (&v)[NQ], double *pa
   __threadfence();
 #pragma unroll
   for (int q = 0; q < NQ; ++q) {
-    double s = 0.0;
-    for (int i = tid; i < nblk; i += kThreads) s += __ldcg(&partials[q * pstride + i]);
-    s = warp_sum(s);
+    P s = z;
+    for (int i = tid; i < nblk; i += kThreads) s = part_add(s, part_load(&partials[q * pstride + i], z));
+    s = warp_sum_part(s);
     if (lane == 0) s_w[q][wid] = s;
   }
   __syncthreads();
 #pragma unroll
   for (int q = 0; q < NQ; ++q) {
-    double s = 0.0;
-    for (int w = 0; w < kThreads / 32; ++w) s += s_w[q][w];
-    out[q] = s;
+    P s = z;
+    for (int w = 0; w < kThreads / 32; ++w) s = part_add(s, s_w[q][w]);
+    out[q] = part_value(s);
   }
   if (tid == 0) *ticket = 0u;
   return true;
 }
 
-template <int NQ>
-__device__ __forceinline__ bool reduce_last_block(double (&v)[NQ], double *partials, unsigned *ticket,
+template <int NQ, typename P>
+__device__ __forceinline__ bool reduce_last_block(P (&v)[NQ], double *partials, unsigned *ticket,
                                                   double (&out)[NQ]) {
   const int nblk = gridDim.x * gridDim.y * gridDim.z;
   const int bid = blockIdx.x + gridDim.x * (blockIdx.y + gridDim.y * blockIdx.z);
@@ -285,6 +342,8 @@ int dht_tile_pencils(int N, int elem_bytes);
 // tile overrides (0 = default); return 0 on success
 int set_dht_pencils_override(int N, int P);
 int set_stencil_planes_override(int N, int zc);
+int set_stencil_rows(int rpt);  // FP32 operator rows per thread: 0 auto, 1, 2, 4
+int set_stencil_rows_override(int N, int rpt);  // per grid size; 0 = the process-wide choice
 int set_strided_fast(int on);  // 0: generic Stockham tiles for every pass
 
 // solver.cu: read-only views of the opaque handles (used by batch.cu)

@@ -491,4 +491,134 @@ __device__ __forceinline__ void dht_tile_s2(const SpectralDev &sp, const DhtTile
   s2_combine<T, C, N, 0>(sm, SP, logP, gout, base, stride, sp, k2, c0, vtab, acc);
 }
 
+// ----------------------------------------------------------------------------
+// Two-stage tile for the contiguous axis (x3), N = R0 * R1: 2P consecutive rows
+// of N reals, rows 2p and 2p+1 forming complex pencil p. Shared memory holds
+// pencil p at p * SJ + x3pos(j) with one pad entry per 16 (SJ = x3pos(N)), so
+// that the stage-1 writes (stride R0 = 16 along j across lanes) and the
+// stage-2 / combine accesses (consecutive j across lanes) are conflict-free.
+//   stage 1: butterfly (p, b), b < R1, b fastest so that lanes read
+//     consecutive row entries: x[b + q R1] of rows 2p, 2p+1 for q < R0 (pass
+//     A fuses r -= alpha q and ||r||^2 here), radix R0, y -> x3pos(b R0 + q);
+//   stage 2: butterfly (p, b), b < R0, in place on x3pos(b + q R0): twiddles
+//     tw[q b], radix R1, giving X[b + q R0];
+//   combine: (p, k), 0 < k < N/2, forms the Hartley values of both rows at k
+//     and N - k (k = 0 also takes the self-paired 0 and N/2) and stores them
+//     along the rows (pass E fuses x += alpha p, p = z + beta p).
+// ----------------------------------------------------------------------------
+__host__ __device__ constexpr int x3pos(int j) { return j + (j >> 4); }
+
+// The fields a kernel reads and writes may alias (pass A reads r through
+// `in` and writes it through `r`), so the compiler keeps every load behind
+// the stores before it; each butterfly therefore issues its loads in chunks
+// of HC pairs ahead of the chunk's stores, one memory latency per chunk.
+template <typename T, typename C, int R0, int R1, int LOADM>
+__device__ __forceinline__ void x3_stage1(const DhtTile<T> &a, size_t row0, C *sm, int SJ, int P, Accum<T> &acc) {
+  constexpr int N = R0 * R1;
+  constexpr int HC = R0 > 8 ? 8 : R0;
+  const T alpha = a.alpha;
+  for (int t = threadIdx.x; t < R1 * P; t += kThreads) {
+    const int p = t / R1, b = t - p * R1;
+    const size_t ga = (row0 + 2 * p) * N + b, gb = ga + N;
+    C u[R0];
+#pragma unroll
+    for (int h = 0; h < R0; h += HC) {
+      T va[HC], vb[HC];
+#pragma unroll
+      for (int q = 0; q < HC; ++q) {
+        va[q] = a.in[ga + (h + q) * R1];
+        vb[q] = a.in[gb + (h + q) * R1];
+      }
+      if (LOADM == LD_RESID && !a.first) {
+        T qa[HC], qb[HC];
+#pragma unroll
+        for (int q = 0; q < HC; ++q) {
+          qa[q] = a.q[ga + (h + q) * R1];
+          qb[q] = a.q[gb + (h + q) * R1];
+        }
+#pragma unroll
+        for (int q = 0; q < HC; ++q) {
+          va[q] = fma(-alpha, qa[q], va[q]);
+          vb[q] = fma(-alpha, qb[q], vb[q]);
+          acc.add(fma(va[q], va[q], vb[q] * vb[q]));
+        }
+#pragma unroll
+        for (int q = 0; q < HC; ++q) {
+          a.r[ga + (h + q) * R1] = va[q];
+          a.r[gb + (h + q) * R1] = vb[q];
+        }
+      }
+#pragma unroll
+      for (int q = 0; q < HC; ++q) u[h + q] = C{va[q], vb[q]};
+    }
+    dft<T, C, R0>(u);
+    C *sp = sm + p * SJ;
+#pragma unroll
+    for (int q = 0; q < R0; ++q) sp[x3pos(b * R0 + q)] = u[q];
+  }
+  __syncthreads();
+}
+
+template <typename T, typename C, int R0, int R1>
+__device__ __forceinline__ void x3_stage2(C *sm, int SJ, int P, const C *__restrict__ tw) {
+  for (int t = threadIdx.x; t < R0 * P; t += kThreads) {
+    const int p = t / R0, b = t - p * R0;
+    C *sp = sm + p * SJ;
+    C x[R1];
+#pragma unroll
+    for (int q = 0; q < R1; ++q) {
+      x[q] = sp[x3pos(b + q * R0)];
+      if (q > 0) x[q] = cmul(x[q], tw[q * b]);
+    }
+    dft<T, C, R1>(x);
+#pragma unroll
+    for (int q = 0; q < R1; ++q) sp[x3pos(b + q * R0)] = x[q];
+  }
+  __syncthreads();
+}
+
+// Stores the values v[0..3] of row positions g[0..3]: plain, or the fused PCG
+// update (all loads of the four positions before any store; see x3_stage1).
+template <typename T, int STOREM>
+__device__ __forceinline__ void x3_put4(const DhtTile<T> &a, const size_t (&g)[4], const T (&v)[4]) {
+  if (STOREM == SO_PCG) {
+    if (a.first) {
+#pragma unroll
+      for (int i = 0; i < 4; ++i) a.p[g[i]] = v[i];
+    } else {
+      T po[4], xo[4];
+#pragma unroll
+      for (int i = 0; i < 4; ++i) {
+        po[i] = a.p[g[i]];
+        xo[i] = a.x[g[i]];
+      }
+#pragma unroll
+      for (int i = 0; i < 4; ++i) {
+        a.x[g[i]] = fma(a.alpha, po[i], xo[i]);
+        a.p[g[i]] = fma(a.beta, po[i], v[i]);
+      }
+    }
+  } else {
+#pragma unroll
+    for (int i = 0; i < 4; ++i) a.out[g[i]] = v[i];
+  }
+}
+
+template <typename T, typename C, int N, int STOREM>
+__device__ __forceinline__ void x3_combine(const DhtTile<T> &a, size_t row0, const C *sm, int SJ, int P) {
+  constexpr int H = N / 2;
+  for (int t = threadIdx.x; t < H * P; t += kThreads) {
+    const int p = t / H, k = t - p * H;
+    const C *sp = sm + p * SJ;
+    const size_t ga = (row0 + 2 * p) * N, gb = ga + N;
+    const int km = (k == 0) ? H : N - k;  // k = 0: the second self-paired output is N/2
+    const C X = sp[x3pos(k)], Y = sp[x3pos(km)];
+    // k = 0: outputs 0 and N/2 are their own mirrors
+    const C hk = hartley_pair(X, k == 0 ? X : Y), hm = hartley_pair(Y, k == 0 ? Y : X);
+    const size_t g[4] = {ga + k, gb + k, ga + km, gb + km};
+    const T v[4] = {hk.x, hk.y, hm.x, hm.y};
+    x3_put4<T, STOREM>(a, g, v);
+  }
+}
+
 }  // namespace sq

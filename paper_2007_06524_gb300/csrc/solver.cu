@@ -793,11 +793,13 @@ int sq_set_tiles(const sq_tile_config *tiles, int ntiles) {
     if (!valid_N(N)) return SQ_EINVAL;
     if (tiles[k].dht_pencils && set_dht_pencils_override(N, tiles[k].dht_pencils) != 0) return SQ_EINVAL;
     if (tiles[k].stencil_planes && set_stencil_planes_override(N, tiles[k].stencil_planes) != 0) return SQ_EINVAL;
+    if (tiles[k].stencil_rows && set_stencil_rows_override(N, tiles[k].stencil_rows) != 0) return SQ_EINVAL;
   }
   if (ntiles == 0) {
     for (int N = 8; N <= kMaxN; ++N) {
       set_dht_pencils_override(N, 0);
       set_stencil_planes_override(N, 0);
+      set_stencil_rows_override(N, 0);
     }
   }
   return SQ_OK;
@@ -805,6 +807,7 @@ int sq_set_tiles(const sq_tile_config *tiles, int ntiles) {
 
 int sq_set_option(int key, int value) {
   if (key == SQ_OPT_STRIDED_TWO_STAGE) return set_strided_fast(value) == 0 ? SQ_OK : SQ_EINVAL;
+  if (key == SQ_OPT_STENCIL_ROWS) return set_stencil_rows(value) == 0 ? SQ_OK : SQ_EINVAL;
   return SQ_EINVAL;
 }
 

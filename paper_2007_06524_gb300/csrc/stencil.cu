@@ -38,73 +38,139 @@ cudaError_t launch_coeff_gen(uint8_t *phase, int L, uint64_t seed, uint64_t thr,
   return cudaGetLastError();
 }
 
-// Block (32 x 8) threads over (j3, j2), blockIdx.z over j1 chunks of zc planes.
-template <typename Ti, typename To, int MODE>
+// Work item = a tile of 32 node columns (j3) x 8 RPT node rows (j2) times a
+// chunk of zc planes along j1; items are numbered with j3 tiles fastest, then
+// j2 tiles, then chunks, so concurrently running blocks share their halo rows
+// in L2. The grid holds as many blocks as fit on the GPU at once and each
+// block loops over items: the tables are built and the block's partial sums
+// reduced once per block, not once per item. RPT > 1 (FP32, N divisible by
+// RPT) amortises the per-plane index and coefficient work over RPT rows at
+// the cost of registers (RPT 4: ~114, two blocks per SM; RPT 2: ~64, four);
+// FP64 (ALU-bound) keeps one row per thread.
+template <typename Ti, typename To, int MODE, int RPT>
 __global__ void __launch_bounds__(kThreads) k_stencil(CellsDev c, int dir, const Ti *__restrict__ x,
                                                       To *__restrict__ y, RedBuf rb, int fin, int check_done,
-                                                      int zc) {
+                                                      int zc, int nitems) {
   if (check_done && *(volatile int *)&rb.st->done) return;
   __shared__ Ti tab[256][kTabStride];
+  __shared__ short cellof[kMaxN];
   const int tid = threadIdx.x + 32 * threadIdx.y;
   build_pattern_table<Ti>(tab, c, tid);
+  build_cellof(cellof, c.N, c.n, tid);
   __syncthreads();
-  const int j3 = blockIdx.x * 32 + threadIdx.x;
-  const int j2 = blockIdx.y * 8 + threadIdx.y;
-  const int z0 = blockIdx.z * zc;
-  const int z1 = min(z0 + zc, c.N);
+  const int N = c.N;
+  const int nbx = (N + 31) / 32, nby = (N + 8 * RPT - 1) / (8 * RPT);
   Accum<Ti> acc0, acc1;
-  if (j3 < c.N && j2 < c.N) stencil_column<Ti, To, MODE>(c, dir, x, y, tab, j3, j2, z0, z1, acc0, acc1);
-  double v[2] = {acc0.get(), acc1.get()}, s[2];
+  for (int it = blockIdx.x; it < nitems; it += gridDim.x) {
+    const int bx = it % nbx, rest = it / nbx;
+    const int by = rest % nby, bz = rest / nby;
+    const int j3 = bx * 32 + threadIdx.x;
+    const int j2b = (by * 8 + threadIdx.y) * RPT;
+    const int z0 = bz * zc;
+    const int z1 = min(z0 + zc, N);
+    if (j3 < N && j2b < N)
+      stencil_rows<Ti, To, MODE, RPT>(c, dir, x, y, tab, cellof, j3, j2b, z0, z1, acc0, acc1);
+  }
+  typename Accum<Ti>::Part v[2] = {acc0.part(), acc1.part()};
+  double s[2];
   if (reduce_last_block<2>(v, rb.partials, &rb.st->ticket, s)) {
     if (tid == 0) finalize_scalars(rb.st, fin, s, 2);
   }
 }
 
 static int g_planes_override[kMaxN + 1] = {0};
+static int g_stencil_rows = 0;  // rows per thread of the FP32 operator; 0 = automatic
+
+static int g_rows_override[kMaxN + 1] = {0};
+
+int set_stencil_rows(int rpt) {
+  if (rpt != 0 && rpt != 1 && rpt != 2 && rpt != 4) return 1;
+  g_stencil_rows = rpt;
+  return 0;
+}
+
+int set_stencil_rows_override(int N, int rpt) {
+  if (N < 8 || N > kMaxN || (rpt != 0 && rpt != 1 && rpt != 2 && rpt != 4)) return 1;
+  g_rows_override[N] = rpt;
+  return 0;
+}
 
 int set_stencil_planes_override(int N, int zc) {
   if (N < 8 || N > kMaxN) return 1;
-  if (zc != 0) {
-    if (zc < 1 || zc > N) return 1;
-    const long long blocks = (long long)((N + 31) / 32) * ((N + 7) / 8) * ((N + zc - 1) / zc);
-    if (blocks > kMaxPartials) return 1;
-  }
+  if (zc != 0 && (zc < 1 || zc > N)) return 1;
   g_planes_override[N] = zc;
   return 0;
 }
 
-static int stencil_zc(int N) {
+static int stencil_zc(int N, int rpt) {
   if (N >= 8 && N <= kMaxN && g_planes_override[N]) return g_planes_override[N];
-  // about 4 K blocks of 256 threads per launch, at least 2 planes per block
-  long long tiles = (long long)((N + 31) / 32) * ((N + 7) / 8);
-  long long want = 4096;
-  int nz = (int)((want + tiles - 1) / tiles);
-  if (nz > N / 2) nz = N / 2;
-  if (nz < 1) nz = 1;
-  int zc = (N + nz - 1) / nz;
+  // about 4 K items of 4 to 16 planes
+  const long long tiles = (long long)((N + 31) / 32) * ((N + 8 * rpt - 1) / (8 * rpt));
+  int zc = (int)((tiles * N + 4095) / 4096);
+  if (zc < 4) zc = 4;
+  if (zc > 16) zc = 16;
+  if (zc > N) zc = N;
   return zc;
+}
+
+// Blocks that fit on the device at once for one kernel (cached per kernel and
+// device); 0 on error.
+static int resident_blocks(const void *kern, int threads, size_t smem) {
+  int dev = 0;
+  if (cudaGetDevice(&dev) != cudaSuccess) return 0;
+  struct Entry {
+    const void *k;
+    int dev;
+    int blocks;
+  };
+  static Entry cache[64];
+  static int used = 0;
+  for (int i = 0; i < used; ++i)
+    if (cache[i].k == kern && cache[i].dev == dev) return cache[i].blocks;
+  int per_sm = 0, sms = 0;
+  if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kern, threads, smem) != cudaSuccess) return 0;
+  if (cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess) return 0;
+  const int blocks = per_sm * sms;
+  if (used < 64) cache[used++] = Entry{kern, dev, blocks};
+  return blocks;
+}
+
+template <typename Ti, typename To, int MODE, int RPT>
+static cudaError_t launch_stencil_mode(const CellsDev &c, int dir, const Ti *x, To *y, RedBuf rb, int fin,
+                                       bool check_done, cudaStream_t s) {
+  const int N = c.N;
+  const int zc = stencil_zc(N, RPT);
+  const long long items =
+      (long long)((N + 31) / 32) * ((N + 8 * RPT - 1) / (8 * RPT)) * ((N + zc - 1) / zc);
+  auto kern = k_stencil<Ti, To, MODE, RPT>;
+  long long grid = resident_blocks((const void *)kern, kThreads, 0);
+  if (grid <= 0) return cudaErrorInvalidConfiguration;
+  if (grid > items) grid = items;
+  if (grid > kMaxPartials) grid = kMaxPartials;
+  kern<<<(int)grid, dim3(32, 8, 1), 0, s>>>(c, dir, x, y, rb, fin, check_done ? 1 : 0, zc, (int)items);
+  return cudaGetLastError();
+}
+
+template <typename Ti, typename To, int MODE>
+static cudaError_t launch_stencil_rows(const CellsDev &c, int dir, const Ti *x, To *y, RedBuf rb, int fin,
+                                       bool check_done, cudaStream_t s) {
+  if constexpr (sizeof(Ti) == 4) {
+    const int per_n = (c.N >= 8 && c.N <= kMaxN) ? g_rows_override[c.N] : 0;
+    const int want = per_n ? per_n : (g_stencil_rows ? g_stencil_rows : 4);
+    if (want >= 4 && c.N % 4 == 0) return launch_stencil_mode<Ti, To, MODE, 4>(c, dir, x, y, rb, fin, check_done, s);
+    if (want >= 2 && c.N % 2 == 0) return launch_stencil_mode<Ti, To, MODE, 2>(c, dir, x, y, rb, fin, check_done, s);
+  }
+  return launch_stencil_mode<Ti, To, MODE, 1>(c, dir, x, y, rb, fin, check_done, s);
 }
 
 template <typename Ti, typename To>
 cudaError_t launch_stencil(const CellsDev &c, int mode, int dir, const Ti *x, To *y, RedBuf rb, int fin,
                            bool check_done, cudaStream_t s) {
-  const int N = c.N;
-  const int zc = stencil_zc(N);
-  dim3 grid((N + 31) / 32, (N + 7) / 8, (N + zc - 1) / zc);
-  if ((long long)grid.x * grid.y * grid.z > kMaxPartials) return cudaErrorInvalidConfiguration;
-  dim3 block(32, 8, 1);
   switch (mode) {
-    case ST_MATVEC:
-      k_stencil<Ti, To, ST_MATVEC><<<grid, block, 0, s>>>(c, dir, x, y, rb, fin, check_done ? 1 : 0, zc);
-      break;
-    case ST_RESID:
-      k_stencil<Ti, To, ST_RESID><<<grid, block, 0, s>>>(c, dir, x, y, rb, fin, check_done ? 1 : 0, zc);
-      break;
-    default:
-      k_stencil<Ti, To, ST_RHS><<<grid, block, 0, s>>>(c, dir, x, y, rb, fin, check_done ? 1 : 0, zc);
-      break;
+    case ST_MATVEC: return launch_stencil_rows<Ti, To, ST_MATVEC>(c, dir, x, y, rb, fin, check_done, s);
+    case ST_RESID: return launch_stencil_rows<Ti, To, ST_RESID>(c, dir, x, y, rb, fin, check_done, s);
+    default: return launch_stencil_rows<Ti, To, ST_RHS>(c, dir, x, y, rb, fin, check_done, s);
   }
-  return cudaGetLastError();
 }
 
 template cudaError_t launch_stencil<double, double>(const CellsDev &, int, int, const double *, double *, RedBuf,
@@ -183,10 +249,20 @@ __global__ void __launch_bounds__(kThreads) k_ahom(CellsDev c, const double *__r
   }
 }
 
+// A_hom sweep: one block per (32 x 8) tile and chunk of planes, about 4 K
+// blocks (at most kMaxPartials).
+static int ahom_zc(int N) {
+  const long long tiles = (long long)((N + 31) / 32) * ((N + 7) / 8);
+  int nz = (int)((4096 + tiles - 1) / tiles);
+  if (nz > N / 2) nz = N / 2;
+  if (nz < 1) nz = 1;
+  return (N + nz - 1) / nz;
+}
+
 cudaError_t launch_ahom(const CellsDev &c, const double *p0, const double *p1, const double *p2, RedBuf rb,
                         cudaStream_t s) {
   const int N = c.N;
-  const int zc = stencil_zc(N);
+  const int zc = ahom_zc(N);
   dim3 grid((N + 31) / 32, (N + 7) / 8, (N + zc - 1) / zc);
   if ((long long)grid.x * grid.y * grid.z > kMaxPartials) return cudaErrorInvalidConfiguration;
   k_ahom<<<grid, dim3(32, 8, 1), 0, s>>>(c, p0, p1, p2, rb, zc);
@@ -208,7 +284,8 @@ __global__ void __launch_bounds__(kThreads) k_x_final_sum(T *__restrict__ x, con
     }
     acc.add(v);
   }
-  double vv[1] = {acc.get()}, s[1];
+  typename Accum<T>::Part vv[1] = {acc.part()};
+  double s[1];
   if (reduce_last_block<1>(vv, rb.partials, &rb.st->ticket, s)) {
     if (threadIdx.x == 0) {
       rb.st->red[0] = s[0];

@@ -14,6 +14,7 @@ import numpy as np
 SQ_OK, SQ_EINVAL, SQ_ENOMEM, SQ_ECUDA, SQ_ENOCONV, SQ_ETIMEOUT, SQ_EBADGUESS = range(7)
 SQ_FP64, SQ_FP32_REFINE = 0, 1
 SQ_OPT_STRIDED_TWO_STAGE = 1
+SQ_OPT_STENCIL_ROWS = 2
 
 _HERE = os.path.dirname(os.path.abspath(__file__))
 _LIB = None
@@ -39,7 +40,18 @@ class SolveDesc(C.Structure):
 
 
 class TileConfig(C.Structure):
-    _fields_ = [("N", C.c_int), ("dht_pencils", C.c_int), ("stencil_planes", C.c_int)]
+    _fields_ = [("N", C.c_int), ("dht_pencils", C.c_int), ("stencil_planes", C.c_int), ("stencil_rows", C.c_int)]
+
+
+def _tile_array(tl):
+    """(N, dht_pencils, stencil_planes[, stencil_rows]) tuples -> TileConfig array."""
+    arr = (TileConfig * max(1, len(tl)))()
+    for k, t in enumerate(tl):
+        if len(t) not in (3, 4):
+            raise ValueError("tile entries are (N, dht_pencils, stencil_planes[, stencil_rows])")
+        arr[k].N, arr[k].dht_pencils, arr[k].stencil_planes = int(t[0]), int(t[1]), int(t[2])
+        arr[k].stencil_rows = int(t[3]) if len(t) == 4 else 0
+    return arr
 
 
 def load_library():
@@ -318,9 +330,7 @@ def sq_batch_create(descs, precs, tiles=None) -> Batch:
         arr[k].psi = _ptr(psi).value
     parr = (C.c_void_p * n)(*[p.ptr.value if isinstance(p.ptr, C.c_void_p) else p.ptr for p in precs])
     tl = list(tiles or [])
-    tarr = (TileConfig * max(1, len(tl)))()
-    for k, (N, dp, sp) in enumerate(tl):
-        tarr[k].N, tarr[k].dht_pencils, tarr[k].stencil_planes = int(N), int(dp), int(sp)
+    tarr = _tile_array(tl)
     out = C.c_void_p()
     _check(load_library().sq_batch_create(n, arr, parr, tarr if tl else None, len(tl), C.byref(out)), "sq_batch_create")
     return Batch(out, n, (list(descs), list(precs)))
@@ -383,11 +393,10 @@ def sq_net_train_step(net: Net, coeffs, targets, lr, stream=None, loss_type=0) -
 
 
 def sq_set_tiles(tiles):
-    """tiles: list of (N, dht_pencils, stencil_planes); [] restores defaults."""
+    """tiles: list of (N, dht_pencils, stencil_planes[, stencil_rows]); 0 = default;
+    [] restores every default."""
     tl = list(tiles)
-    arr = (TileConfig * max(1, len(tl)))()
-    for k, (N, dp, sp) in enumerate(tl):
-        arr[k].N, arr[k].dht_pencils, arr[k].stencil_planes = int(N), int(dp), int(sp)
+    arr = _tile_array(tl)
     _check(load_library().sq_set_tiles(arr if tl else None, len(tl)), "sq_set_tiles")
 
 

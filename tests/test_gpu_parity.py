@@ -97,6 +97,52 @@ def test_operator_fp32(sq, L, n, seed):
     assert _relmax(_host(y).astype(np.float64), re.A @ psi.ravel().astype(np.float64)) <= 1e-5
 
 
+# FP32 operator with 1, 2 and 4 node rows per thread (every valid N, 2^a 3^b
+# with b <= 1 and N >= 8, is divisible by 4): grids ragged against the
+# 32-wide j3 tiles and the 8*rows-high j2 tiles, and exact multiples.
+ROW_GRIDS = [(3, 4, 8), (3, 8, 9), (4, 8, 11), (12, 4, 12), (12, 8, 13), (6, 32, 14)]
+
+
+@pytest.mark.parametrize("rows", [1, 2, 4])
+@pytest.mark.parametrize("L,n,seed", ROW_GRIDS)
+def test_operator_fp32_rows_per_thread(sq, rows, L, n, seed):
+    re = problem.realization(L, n, seed, 1.0, 100.0)
+    c = sq.sq_build_coeffs(L, n, seed, 0.5, 1.0, 100.0)
+    N = L * n
+    import torch
+
+    psi = inputs.random_field(N, seed + 17, np.float32)
+    y = torch.empty(N ** 3, dtype=torch.float32, device="cuda")
+    try:
+        sq.sq_set_option(sq.SQ_OPT_STENCIL_ROWS, rows)
+        sq.sq_apply_operator_f32(c, _dev(psi.ravel(), "float32"), y)
+    finally:
+        sq.sq_set_option(sq.SQ_OPT_STENCIL_ROWS, 0)
+    assert _relmax(_host(y).astype(np.float64), re.A @ psi.ravel().astype(np.float64)) <= 1e-5
+
+
+@pytest.mark.parametrize("rows", [1, 2, 4])
+def test_fp32_refinement_rows_per_thread(sq, rows):
+    # p.Ap of the inner FP32 iteration comes from the operator's reduction
+    re = problem.realization(6, 4, 21, 1.0, 100.0)
+    c = sq.sq_build_coeffs(6, 4, 21, 0.5, 1.0, 100.0)
+    ref = pcg.tight_solve(re.A, re.b[0], re.N)[0]
+    try:
+        sq.sq_set_option(sq.SQ_OPT_STENCIL_ROWS, rows)
+        psi, info = _solve(sq, c, re.N, 0, 0, 1e-10, precision=sq.SQ_FP32_REFINE)
+    finally:
+        sq.sq_set_option(sq.SQ_OPT_STENCIL_ROWS, 0)
+    assert info["status"] == sq.SQ_OK and info["relres_true"] <= 1e-10
+    x = _host(psi)
+    assert np.linalg.norm(x - ref) / np.linalg.norm(ref) <= 1e-6
+
+
+def test_stencil_rows_option_rejects_bad_values(sq):
+    for bad in (3, 5, -1, 8):
+        with pytest.raises(sq.SqError):
+            sq.sq_set_option(sq.SQ_OPT_STENCIL_ROWS, bad)
+
+
 # ---------------------------------------------------------- preconditioner
 def _core(sq, pc, N, rank):
     """The oracle's G for the library's preconditioner: exact, or the exponential
@@ -317,8 +363,9 @@ def test_full_size_n256_sampled(sq):
 
 @pytest.mark.parametrize("N", [16, 32, 64, 128, 256])
 def test_precond_generic_and_two_stage_paths_agree(sq, N):
-    """The x1/x2 passes have two implementations (two-stage register plan and
-    generic shared-memory Stockham); both must give the oracle's result."""
+    """The Hartley passes have two implementations (two-stage register plans
+    for x1/x2 and for the contiguous x3, and the generic shared-memory
+    Stockham tile); both must give the oracle's result."""
     import torch
 
     rank = 8
@@ -351,3 +398,23 @@ def test_refinement_n128_against_oracle(sq):
         assert info["status"] == sq.SQ_OK and info["relres_true"] <= 1e-10
         err = np.linalg.norm(_host(psi) - ref) / np.linalg.norm(ref)
         assert err <= 1e-6, (rank, err)
+
+
+@pytest.mark.parametrize("opt", [0, 1, 2])
+def test_solves_with_each_pass_implementation(sq, opt):
+    """The fused PCG forms of the x3 passes (r -= alpha q with ||r||^2 on
+    load, x += alpha p and p = z + beta p on store) in both implementations:
+    FP32 refinement and FP64 solves reach the oracle's corrector."""
+    re = problem.realization(8, 8, 33, 1.0, 100.0)
+    c = sq.sq_build_coeffs(8, 8, 33, 0.5, 1.0, 100.0)
+    ref = pcg.tight_solve(re.A, re.b[2], re.N)[0]
+    try:
+        sq.sq_set_option(sq.SQ_OPT_STRIDED_TWO_STAGE, opt)
+        psi32, i32 = _solve(sq, c, re.N, 2, 8, 1e-10, precision=sq.SQ_FP32_REFINE)
+        psi64, i64 = _solve(sq, c, re.N, 2, 8, 1e-12)
+    finally:
+        sq.sq_set_option(sq.SQ_OPT_STRIDED_TWO_STAGE, 1)
+    assert i32["status"] == sq.SQ_OK and i32["relres_true"] <= 1e-10
+    assert i64["status"] == sq.SQ_OK and i64["relres_true"] <= 1e-12
+    assert np.linalg.norm(_host(psi32) - ref) / np.linalg.norm(ref) <= 1e-6
+    assert np.linalg.norm(_host(psi64) - ref) / np.linalg.norm(ref) <= 1e-9
