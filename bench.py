@@ -148,7 +148,12 @@ def run_native(args):
 
     from paper_2007_06524_gb300 import autotune
 
-    tiles = autotune.tune(torch, N, L, n, cache=None)  # FP32 pass tile and operator planes for this grid
+    if args.tiles:
+        tP, tZ, tR = (int(v) for v in args.tiles.split(","))
+        sq.sq_set_tiles([(N, tP, tZ, tR)])
+        tiles = (tP, tZ, tR)
+    else:
+        tiles = autotune.tune(torch, N, L, n, cache=None)  # FP32 pass tile and operator planes for this grid
     c = sq.sq_build_coeffs(L, n, 0, wl["p_hi"], wl["a_lo"], wl["a_hi"])
     pc = sq.sq_precond_setup(N, R)
     w = sq.sq_workspace_create(N, prec)
@@ -240,7 +245,8 @@ def run_native(args):
                       "parallelism": "replicas" if ws > 1 else "single GPU"},
            "clocks": clocks, "gpu_launches": gpu_launches, "roofline": roof, "kernels": kernels,
            "iters": {"mean": round(statistics.mean(iters), 2), "min": min(iters), "max": max(iters)},
-           "converged": ok, "tiles": {"dht_pencils_fp32": tiles[0], "stencil_planes": tiles[1]}}
+           "converged": ok, "tiles": {"dht_pencils_fp32": tiles[0], "stencil_planes": tiles[1],
+                                                "stencil_rows_fp32": tiles[2]}}
 
     # --- end to end through the C ABI with pinned host inputs
     rng = np.random.default_rng(12345 + rank)
@@ -459,6 +465,9 @@ def main():
     ap.add_argument("--no-variants", action="store_true")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-e2e", action="store_true")
+    ap.add_argument("--tiles", default=None,
+                    help="fixed FP32 tile shape 'P,planes,rows' (Hartley pencils, operator planes per item, operator "
+                         "rows per thread) instead of the autotuner")
     args = ap.parse_args()
     if args.warmup < 3 and args.impl == "native":
         args.warmup = 3

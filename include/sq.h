@@ -156,9 +156,10 @@ typedef struct sq_solve_desc {
 
 /* Tile shape per grid size (0 = default): Hartley-pass tile of `dht_pencils`
  * complex pencils (a power of two, 2*dht_pencils dividing N), operator work
- * items of `stencil_planes` x1-planes, and `stencil_rows` node rows per thread
- * of the FP32 operator of single solves (1, 2 or 4; used where N is divisible
- * by it, else the next smaller; batches use 1). */
+ * items of `stencil_planes` x1-planes (register kernels), and the FP32
+ * operator variant of single solves `stencil_rows` (1, 2, 4 node rows per
+ * thread, or 8 for the shared-memory-staged kernel; see SQ_OPT_STENCIL_ROWS;
+ * batches use 1). */
 typedef struct sq_tile_config {
   int N;
   int dht_pencils;
@@ -176,15 +177,17 @@ int sq_set_tiles(const sq_tile_config *tiles, int ntiles);
  * SQ_OPT_STRIDED_TWO_STAGE (default 1): the FP32 Hartley passes (x1/x2 and the
  * contiguous x3) use the two-stage plans (one register stage from global
  * memory, one in-place shared-memory stage, an all-thread combine) where N
- * allows (16, 32, 64, 128, 256); 2 also uses them for FP64 (ALU-bound: the
- * generic tile is faster there); 0 selects the generic shared-memory Stockham
- * tile everywhere.
- * SQ_OPT_STENCIL_ROWS (default 0 = automatic, i.e. 4): node rows per thread of
- * the FP32 operator of single solves for grid sizes without a per-N choice
- * (sq_tile_config.stencil_rows), 1, 2 or 4 (used where N is divisible by it,
- * else the next smaller); more rows share the per-plane index and coefficient
- * work but take more registers. Results are identical up to the order of the
- * p.Ap summation. */
+ * allows (16, 32, 64, 128, 256) and the tile has 8 or 16 pencils; 0 selects
+ * the generic shared-memory Stockham tile everywhere. 2 is accepted and acts
+ * as 1. FP64 passes (ALU-bound; the two-stage plans measured slower there)
+ * always use the generic tile.
+ * SQ_OPT_STENCIL_ROWS (default 0 = automatic, i.e. 8): the FP32 operator of
+ * single solves for grid sizes without a per-N choice
+ * (sq_tile_config.stencil_rows): 1, 2 or 4 node rows per thread with a
+ * register plane queue (used where N is divisible by it, else the next
+ * smaller), or 8: planes staged through shared memory with asynchronous
+ * copies (where N is a multiple of 32 and p is 16-byte aligned, else 4).
+ * Results are identical up to the order of the p.Ap summation. */
 enum sq_option { SQ_OPT_STRIDED_TWO_STAGE = 1, SQ_OPT_STENCIL_ROWS = 2 };
 int sq_set_option(int key, int value);
 

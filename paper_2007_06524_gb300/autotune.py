@@ -5,7 +5,7 @@ Tuned per N: the number of complex pencils of a Hartley-pass tile (FP32 passes;
 2P real pencils, 2P * 4 bytes per row segment), and jointly the node rows per
 thread and the x1-planes per work item of the FP32 operator. Each candidate is timed with CUDA events over a few
 repetitions of the kernel it drives (sq_apply_precond_f32 for the passes,
-sq_apply_operator_f32 for the operator); results are cached in a JSON file
+sq_apply_operator_f32 for the operator), each after an L2 flush; results are cached in a JSON file
 keyed by N and the device name.
 """
 from __future__ import annotations
@@ -18,21 +18,34 @@ from . import sq as _sq
 DEFAULT_CACHE = os.path.join(os.path.dirname(os.path.dirname(os.path.abspath(__file__))), "_build", "tiles.json")
 
 
+_FLUSH = {}
+
+
 def _time(torch, fn, reps=5):
+    """Median time of fn over reps runs, each after writing 256 MB (twice the
+    L2 size) so that the inputs come from HBM, as they do inside a solve."""
+    dev = torch.cuda.current_device()
+    if dev not in _FLUSH:
+        _FLUSH[dev] = torch.empty(256 * 2 ** 20, dtype=torch.uint8, device="cuda")
+    flush = _FLUSH[dev]
     fn()
     torch.cuda.synchronize()
-    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
-    e0.record()
+    ts = []
     for _ in range(reps):
+        flush.zero_()
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record()
         fn()
-    e1.record()
-    torch.cuda.synchronize()
-    return e0.elapsed_time(e1) / reps
+        e1.record()
+        torch.cuda.synchronize()
+        ts.append(e0.elapsed_time(e1))
+    ts.sort()
+    return ts[len(ts) // 2]
 
 
 def tune(torch, N, L=None, n=None, cache=DEFAULT_CACHE, reps=5):
-    """Returns (dht_pencils, stencil_planes) for grid N and installs them,
-    together with the operator's rows per thread, with sq_set_tiles."""
+    """Returns (dht_pencils, stencil_planes, stencil_rows) for grid N and
+    installs them with sq_set_tiles."""
     dev = torch.cuda.get_device_name()
     key = f"{dev}:{N}"
     table = {}
@@ -44,7 +57,7 @@ def tune(torch, N, L=None, n=None, cache=DEFAULT_CACHE, reps=5):
     if key in table and "stencil_rows" in table[key]:
         P, zc, rows = table[key]["dht_pencils"], table[key]["stencil_planes"], table[key]["stencil_rows"]
         _sq.sq_set_tiles([(N, P, zc, rows)])
-        return P, zc
+        return P, zc, rows
     if L is None:
         n = 8 if N % 8 == 0 else 4
         L = N // n
@@ -64,10 +77,10 @@ def tune(torch, N, L=None, n=None, cache=DEFAULT_CACHE, reps=5):
         times_p[P] = _time(torch, lambda: _sq.sq_apply_precond_f32(pc, w, r, z), reps)
     bestP = min(times_p, key=times_p.get)
     times_z = {}
-    for rows in (1, 2, 4):
-        if N % rows != 0:
+    for rows in (1, 2, 4, 8):
+        if N % (32 if rows == 8 else rows) != 0:
             continue
-        for zc in (4, 8, 16, 32):
+        for zc in ((0,) if rows == 8 else (4, 8, 16, 32)):  # the staged kernel sizes its own plane runs
             if zc > N:
                 continue
             try:
@@ -83,4 +96,4 @@ def tune(torch, N, L=None, n=None, cache=DEFAULT_CACHE, reps=5):
     if cache:
         os.makedirs(os.path.dirname(cache), exist_ok=True)
         json.dump(table, open(cache, "w"), indent=1)
-    return bestP, bestZ
+    return bestP, bestZ, bestR

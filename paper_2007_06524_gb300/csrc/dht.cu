@@ -86,41 +86,37 @@ __global__ void __launch_bounds__(kThreads) k_dht(DhtArgs<T> a) {
   }
 }
 
-// Strided-axis passes with the two-stage plan (one shared-memory round trip
-// per transform; see dht_tile_s2). FP32 tiles hold ~38 KB of shared memory at
-// N = 256, room for 5 blocks per SM; the register cap keeps at least 3 of
-// them resident (uncapped, pass C takes 128 registers: 2 blocks).
-template <typename T>
-constexpr int s2_min_blocks() { return sizeof(T) == 4 ? 3 : 1; }
-
-template <typename T, int AXIS, int R0, int R1, bool SCALE>
-__global__ void __launch_bounds__(kThreads, s2_min_blocks<T>()) k_dht_s2(DhtArgs<T> a) {
-  using C = typename Cx<T>::type;
+// Two-stage passes (FP32; see dht_tile_s2 and x3_stage1). A tile holds ~38 KB
+// of shared memory at N = 256, P = 16: room for 5 blocks per SM; the register
+// cap keeps 3 of them resident (uncapped, pass C takes 128 registers).
+// Strided axes x1 (pass C, SCALE) and x2 (passes B, D).
+template <int AXIS, int R0, int R1, int P, bool SCALE, int RR>
+__global__ void __launch_bounds__(kThreads, 3) k_dht_s2(DhtArgs<float> a) {
+  using C = float2;
   if (a.check_done && *(volatile int *)&a.rb.st->done) return;
   extern __shared__ __align__(16) unsigned char smem_raw[];
   constexpr int N = R0 * R1;
-  const int P = 1 << a.logP;
   C *sm = reinterpret_cast<C *>(smem_raw);
   C *tw = sm + N * (P + 1);
-  T *vtab = reinterpret_cast<T *>(tw + N);
+  float *vtab = reinterpret_cast<float *>(tw + N);
   const C *twg = reinterpret_cast<const C *>(a.sp.tw);
   for (int m = threadIdx.x; m < N; m += kThreads) tw[m] = twg[m];
-  DhtTile<T> t;
+  DhtTile<float> t;
   t.in = a.in;
   t.out = a.out;
   t.r = a.r;
   t.q = a.q;
   t.p = a.p;
   t.x = a.x;
-  t.alpha = (T)a.rb.st->alpha;
-  t.beta = (T)a.rb.st->beta;
+  t.alpha = (float)a.rb.st->alpha;
+  t.beta = (float)a.rb.st->beta;
   t.first = a.first;
   t.logP = a.logP;
-  Accum<T> acc;
+  Accum<float> acc;
   for (int tile = blockIdx.x; tile < a.ntiles; tile += gridDim.x)
-    dht_tile_s2<T, AXIS, R0, R1, SCALE>(a.sp, t, tile, sm, tw, vtab, acc);
+    dht_tile_s2<float, AXIS, R0, R1, P, SCALE, RR>(a.sp, t, tile, sm, tw, vtab, acc);
   if (SCALE) {
-    typename Accum<T>::Part v[1] = {acc.part()};
+    FF v[1] = {acc.part()};
     double s[1];
     if (reduce_last_block<1>(v, a.rb.partials, &a.rb.st->ticket, s)) {
       if (threadIdx.x == 0) finalize_scalars(a.rb.st, a.first ? FIN_RZ_FIRST : FIN_RZ_BETA, s, 1);
@@ -128,66 +124,85 @@ __global__ void __launch_bounds__(kThreads, s2_min_blocks<T>()) k_dht_s2(DhtArgs
   }
 }
 
-template <typename T, int AXIS, int R0, int R1, bool SCALE>
-static cudaError_t launch_s2(const DhtArgs<T> &a, int grid, cudaStream_t s) {
-  const int P = 1 << a.logP;
-  const size_t smem = (size_t)R0 * R1 * (P + 1) * sizeof(typename Cx<T>::type) +
-                      (size_t)R0 * R1 * sizeof(typename Cx<T>::type) + (size_t)a.sp.rank * 2 * P * sizeof(T);
-  auto kern = k_dht_s2<T, AXIS, R0, R1, SCALE>;
+template <int AXIS, int R0, int R1, int P, bool SCALE, int RR>
+static cudaError_t launch_s2(const DhtArgs<float> &a, int grid, cudaStream_t s) {
+  const size_t smem = (size_t)R0 * R1 * (P + 1) * sizeof(float2) + (size_t)R0 * R1 * sizeof(float2) +
+                      (size_t)a.sp.rank * 2 * P * sizeof(float);
+  auto kern = k_dht_s2<AXIS, R0, R1, P, SCALE, RR>;
   cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
   if (e != cudaSuccess) return e;
   kern<<<grid, kThreads, smem, s>>>(a);
   return cudaGetLastError();
 }
 
-// Two-stage plans for the strided passes; returns cudaErrorNotSupported when N has none.
-template <typename T, int AXIS, bool SCALE>
-static cudaError_t launch_strided_fast(const DhtArgs<T> &a, int grid, cudaStream_t s) {
-  if ((1 << a.logP) > 16) return cudaErrorNotSupported;
+// Rank specialisations of pass C: exact (0), rank 8 in registers, else runtime.
+template <int AXIS, int R0, int R1, int P, bool SCALE>
+static cudaError_t launch_s2_rank(const DhtArgs<float> &a, int grid, cudaStream_t s) {
+  if constexpr (!SCALE) {
+    return launch_s2<AXIS, R0, R1, P, SCALE, -1>(a, grid, s);
+  } else {
+    if (a.sp.rank == 0) return launch_s2<AXIS, R0, R1, P, SCALE, 0>(a, grid, s);
+    if (a.sp.rank == 8) return launch_s2<AXIS, R0, R1, P, SCALE, 8>(a, grid, s);
+    return launch_s2<AXIS, R0, R1, P, SCALE, -1>(a, grid, s);
+  }
+}
+
+// P = 8 or 16 pencils where the tile fits the grid (2P <= N).
+template <int AXIS, int R0, int R1, bool SCALE>
+static cudaError_t launch_s2_p(const DhtArgs<float> &a, int grid, cudaStream_t s) {
+  if (a.logP == 3) return launch_s2_rank<AXIS, R0, R1, 8, SCALE>(a, grid, s);
+  if constexpr (R0 * R1 >= 32) {
+    if (a.logP == 4) return launch_s2_rank<AXIS, R0, R1, 16, SCALE>(a, grid, s);
+  }
+  return cudaErrorNotSupported;
+}
+
+// Two-stage plans for the strided passes; cudaErrorNotSupported when N or P has none.
+template <int AXIS, bool SCALE>
+static cudaError_t launch_strided_fast(const DhtArgs<float> &a, int grid, cudaStream_t s) {
   switch (a.sp.N) {
-    case 16: return launch_s2<T, AXIS, 4, 4, SCALE>(a, grid, s);
-    case 32: return launch_s2<T, AXIS, 8, 4, SCALE>(a, grid, s);
-    case 64: return launch_s2<T, AXIS, 8, 8, SCALE>(a, grid, s);
-    case 128: return launch_s2<T, AXIS, 16, 8, SCALE>(a, grid, s);
-    case 256: return launch_s2<T, AXIS, 16, 16, SCALE>(a, grid, s);
+    case 16: return launch_s2_p<AXIS, 4, 4, SCALE>(a, grid, s);
+    case 32: return launch_s2_p<AXIS, 8, 4, SCALE>(a, grid, s);
+    case 64: return launch_s2_p<AXIS, 8, 8, SCALE>(a, grid, s);
+    case 128: return launch_s2_p<AXIS, 16, 8, SCALE>(a, grid, s);
+    case 256: return launch_s2_p<AXIS, 16, 16, SCALE>(a, grid, s);
     default: return cudaErrorNotSupported;
   }
 }
 
-// Contiguous-axis passes (A, E) with the two-stage plan; see x3_stage1.
-template <typename T, int R0, int R1, int LOADM, int STOREM>
-__global__ void __launch_bounds__(kThreads, s2_min_blocks<T>()) k_dht_s3(DhtArgs<T> a) {
-  using C = typename Cx<T>::type;
+// Contiguous axis x3 (passes A and E).
+template <int R0, int R1, int P, int LOADM, int STOREM>
+__global__ void __launch_bounds__(kThreads, 3) k_dht_s3(DhtArgs<float> a) {
+  using C = float2;
   if (a.check_done && *(volatile int *)&a.rb.st->done) return;
   extern __shared__ __align__(16) unsigned char smem_raw[];
   constexpr int N = R0 * R1;
-  const int P = 1 << a.logP;
-  const int SJ = x3pos(N);
+  constexpr int SJ = x3pos(N);
   C *sm = reinterpret_cast<C *>(smem_raw);
   C *tw = sm + (size_t)P * SJ;
   const C *twg = reinterpret_cast<const C *>(a.sp.tw);
   for (int m = threadIdx.x; m < N; m += kThreads) tw[m] = twg[m];
-  DhtTile<T> t;
+  DhtTile<float> t;
   t.in = a.in;
   t.out = a.out;
   t.r = a.r;
   t.q = a.q;
   t.p = a.p;
   t.x = a.x;
-  t.alpha = (T)a.rb.st->alpha;
-  t.beta = (T)a.rb.st->beta;
+  t.alpha = (float)a.rb.st->alpha;
+  t.beta = (float)a.rb.st->beta;
   t.first = a.first;
   t.logP = a.logP;
-  Accum<T> acc;
+  Accum<float> acc;
   for (int tile = blockIdx.x; tile < a.ntiles; tile += gridDim.x) {
     __syncthreads();  // twiddles loaded; the previous tile's combine is done with sm
     const size_t row0 = (size_t)tile * 2 * P;
-    x3_stage1<T, C, R0, R1, LOADM>(t, row0, sm, SJ, P, acc);
-    x3_stage2<T, C, R0, R1>(sm, SJ, P, tw);
-    x3_combine<T, C, N, STOREM>(t, row0, sm, SJ, P);
+    x3_stage1<float, C, R0, R1, P, LOADM>(t, row0, sm, acc);
+    x3_stage2<float, C, R0, R1, P>(sm, tw);
+    x3_combine<float, C, N, P, STOREM>(t, row0, sm);
   }
   if (LOADM == LD_RESID) {
-    typename Accum<T>::Part v[1] = {acc.part()};
+    FF v[1] = {acc.part()};
     double s[1];
     if (reduce_last_block<1>(v, a.rb.partials, &a.rb.st->ticket, s)) {
       if (threadIdx.x == 0) finalize_scalars(a.rb.st, a.first ? FIN_NONE : FIN_RR_ITER, s, 1);
@@ -195,28 +210,54 @@ __global__ void __launch_bounds__(kThreads, s2_min_blocks<T>()) k_dht_s3(DhtArgs
   }
 }
 
-template <typename T, int R0, int R1, int LOADM, int STOREM>
-static cudaError_t launch_s3(const DhtArgs<T> &a, int grid, cudaStream_t s) {
-  const int P = 1 << a.logP;
-  const size_t smem = ((size_t)P * x3pos(R0 * R1) + (size_t)R0 * R1) * sizeof(typename Cx<T>::type);
-  auto kern = k_dht_s3<T, R0, R1, LOADM, STOREM>;
+template <int R0, int R1, int P, int LOADM, int STOREM>
+static cudaError_t launch_s3(const DhtArgs<float> &a, int grid, cudaStream_t s) {
+  const size_t smem = ((size_t)P * x3pos(R0 * R1) + (size_t)R0 * R1) * sizeof(float2);
+  auto kern = k_dht_s3<R0, R1, P, LOADM, STOREM>;
   cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
   if (e != cudaSuccess) return e;
   kern<<<grid, kThreads, smem, s>>>(a);
   return cudaGetLastError();
 }
 
-// Two-stage plans for the contiguous passes; cudaErrorNotSupported when N has none.
-template <typename T, int LOADM, int STOREM>
-static cudaError_t launch_contig_fast(const DhtArgs<T> &a, int grid, cudaStream_t s) {
-  if ((1 << a.logP) > 32) return cudaErrorNotSupported;
+template <int R0, int R1, int LOADM, int STOREM>
+static cudaError_t launch_s3_p(const DhtArgs<float> &a, int grid, cudaStream_t s) {
+  if (a.logP == 3) return launch_s3<R0, R1, 8, LOADM, STOREM>(a, grid, s);
+  if constexpr (R0 * R1 >= 32) {
+    if (a.logP == 4) return launch_s3<R0, R1, 16, LOADM, STOREM>(a, grid, s);
+  }
+  return cudaErrorNotSupported;
+}
+
+// Two-stage plans for the contiguous passes; cudaErrorNotSupported when N or P has none.
+template <int LOADM, int STOREM>
+static cudaError_t launch_contig_fast(const DhtArgs<float> &a, int grid, cudaStream_t s) {
   switch (a.sp.N) {
-    case 16: return launch_s3<T, 4, 4, LOADM, STOREM>(a, grid, s);
-    case 32: return launch_s3<T, 8, 4, LOADM, STOREM>(a, grid, s);
-    case 64: return launch_s3<T, 8, 8, LOADM, STOREM>(a, grid, s);
-    case 128: return launch_s3<T, 16, 8, LOADM, STOREM>(a, grid, s);
-    case 256: return launch_s3<T, 16, 16, LOADM, STOREM>(a, grid, s);
+    case 16: return launch_s3_p<4, 4, LOADM, STOREM>(a, grid, s);
+    case 32: return launch_s3_p<8, 4, LOADM, STOREM>(a, grid, s);
+    case 64: return launch_s3_p<8, 8, LOADM, STOREM>(a, grid, s);
+    case 128: return launch_s3_p<16, 8, LOADM, STOREM>(a, grid, s);
+    case 256: return launch_s3_p<16, 16, LOADM, STOREM>(a, grid, s);
     default: return cudaErrorNotSupported;
+  }
+}
+
+// FP32 passes through the two-stage tiles where N and P allow; FP64 (ALU-bound,
+// where the two-stage tiles measured slower) always takes the generic tile.
+template <typename T>
+static cudaError_t launch_fast(int pass, const DhtArgs<T> &a, int grid, cudaStream_t s) {
+  if constexpr (sizeof(T) != 4) {
+    return cudaErrorNotSupported;
+  } else {
+    switch (pass) {
+      case PASS_A_RESID: return launch_contig_fast<LD_RESID, SO_PLAIN>(a, grid, s);
+      case PASS_A_PLAIN: return launch_contig_fast<LD_PLAIN, SO_PLAIN>(a, grid, s);
+      case PASS_E_PCG: return launch_contig_fast<LD_PLAIN, SO_PCG>(a, grid, s);
+      case PASS_E_PLAIN: return launch_contig_fast<LD_PLAIN, SO_PLAIN>(a, grid, s);
+      case PASS_B: return launch_strided_fast<2, false>(a, grid, s);
+      case PASS_C: return launch_strided_fast<1, true>(a, grid, s);
+      default: return cudaErrorNotSupported;
+    }
   }
 }
 
@@ -277,34 +318,15 @@ cudaError_t launch_dht_pass(int pass, const SpectralDev &sp, const T *in, T *out
   a.ntiles = (int)(((long long)N * N) / (2 * P));
   const int grid = a.ntiles < 8192 ? a.ntiles : 8192;
   const size_t smem = dht_smem_bytes_t<T>(N, P, pass == PASS_C ? sp.rank : 0);
-  // FP32 by default: in FP64 the ALU-bound passes prefer the generic tile
-  const bool fast = g_strided_fast && (sizeof(T) == 4 || g_strided_fast > 1);
-  if (fast && (pass == PASS_A_RESID || pass == PASS_A_PLAIN || pass == PASS_E_PCG || pass == PASS_E_PLAIN)) {
-    cudaError_t e = cudaErrorNotSupported;
-    switch (pass) {
-      case PASS_A_RESID: e = launch_contig_fast<T, LD_RESID, SO_PLAIN>(a, grid, s); break;
-      case PASS_A_PLAIN: e = launch_contig_fast<T, LD_PLAIN, SO_PLAIN>(a, grid, s); break;
-      case PASS_E_PCG: e = launch_contig_fast<T, LD_PLAIN, SO_PCG>(a, grid, s); break;
-      default: e = launch_contig_fast<T, LD_PLAIN, SO_PLAIN>(a, grid, s); break;
-    }
+  if (g_strided_fast) {
+    const cudaError_t e = launch_fast<T>(pass, a, grid, s);
     if (e != cudaErrorNotSupported) return e;
   }
   switch (pass) {
     case PASS_A_RESID: return launch_one<T, 3, LD_RESID, SO_PLAIN, false>(a, grid, smem, s);
     case PASS_A_PLAIN: return launch_one<T, 3, LD_PLAIN, SO_PLAIN, false>(a, grid, smem, s);
-    case PASS_B: {
-      if (fast) {
-        const cudaError_t e = launch_strided_fast<T, 2, false>(a, grid, s);
-        if (e != cudaErrorNotSupported) return e;
-      }
-      return launch_one<T, 2, LD_PLAIN, SO_PLAIN, false>(a, grid, smem, s);
-    }
-    case PASS_C:
-      if (fast) {
-        const cudaError_t e = launch_strided_fast<T, 1, true>(a, grid, s);
-        if (e != cudaErrorNotSupported) return e;
-      }
-      return launch_one<T, 1, LD_PLAIN, SO_PLAIN, true>(a, grid, smem, s);
+    case PASS_B: return launch_one<T, 2, LD_PLAIN, SO_PLAIN, false>(a, grid, smem, s);
+    case PASS_C: return launch_one<T, 1, LD_PLAIN, SO_PLAIN, true>(a, grid, smem, s);
     case PASS_E_PCG: return launch_one<T, 3, LD_PLAIN, SO_PCG, false>(a, grid, smem, s);
     case PASS_E_PLAIN: return launch_one<T, 3, LD_PLAIN, SO_PLAIN, false>(a, grid, smem, s);
     default: return cudaErrorInvalidValue;

@@ -337,39 +337,42 @@ __device__ __forceinline__ void dht_tile(const SpectralDev &sp, const DhtTile<T>
 namespace sq {
 
 // ----------------------------------------------------------------------------
-// Two-stage tile for the strided axes (x1, x2) when N = R0 * R1 with power-of-
-// two radices: one shared-memory round trip per transform.
+// Two-stage tiles (FP32): N = R0 * R1 with power-of-two radices, P complex
+// pencils per tile, all shape parameters compile-time so that the index
+// arithmetic folds to shifts and constants. One shared-memory round trip per
+// transform.
+//
+// Strided axes (x1, x2): pencil p of a tile is the complex column 2P-wide row
+// segment element p; shared memory holds position j of pencil p at j SP + p,
+// SP = P + 1.
 //   stage 1 (radix R0, no twiddles): butterfly b < R1 of pencil p reads
 //     x[b + q R1] (q < R0) -- from global memory (rows of P complex values,
 //     coalesced) or from shared memory (second transform of pass C) -- and
 //     writes y[b R0 + q] to shared memory;
 //   stage 2 (radix R1, last): butterfly b < R0 reads y[b + q R0], applies
-//     tw[q b], and yields X[b + q R0]. Butterflies b and R0 - b hold each
-//     other's mirror outputs X[N - m], so one thread takes both and forms the
-//     Hartley values 2(H a)_m, 2(H b)_m in registers, then stores them (pass
-//     C: scales by G, reduces r.z and writes them back for the second
-//     transform). A unit reads and writes only its own positions, so stage 2
-//     needs no barrier between its reads and writes.
+//     tw[q b], and yields X[b + q R0] in place (a butterfly reads and writes
+//     only its own positions, so no barrier is needed inside the stage);
+//   combine: thread (p, k), k <= N/2, forms the Hartley values 2(H a), 2(H b)
+//     at k and N - k and stores them (pass C: scales by G, reduces r.z and
+//     writes them back for the second transform).
 // ----------------------------------------------------------------------------
-template <typename T, typename C, int R0, int R1, bool FROM_SMEM>
-__device__ __forceinline__ void s2_stage1(const C *__restrict__ gsrc, size_t base, size_t stride, C *sm, int SP,
-                                          int logP) {
-  static_assert(R1 * 16 <= kThreads, "one stage-1 butterfly per thread");
-  const int P = 1 << logP;
-  const int nb = R1 << logP;
+constexpr int ilog2c(int v) { return v <= 1 ? 0 : 1 + ilog2c(v / 2); }
+
+template <typename T, typename C, int R0, int R1, int P, bool FROM_SMEM, long long STRIDE>
+__device__ __forceinline__ void s2_stage1(const C *__restrict__ gsrc, size_t base, C *sm) {
+  constexpr int SP = P + 1, LP = ilog2c(P);
+  static_assert(R1 * P <= kThreads, "one stage-1 butterfly per thread");
   const int t = threadIdx.x;
-  const int p = t & (P - 1), b = t >> logP;
+  const int p = t & (P - 1), b = t >> LP;
   C u[R0];
-  if (t < nb) {
+  if (t < R1 * P) {
+    const C *g = gsrc + (base >> 1) + (size_t)b * (STRIDE >> 1) + p;
 #pragma unroll
-    for (int q = 0; q < R0; ++q) {
-      const int j = b + q * R1;
-      u[q] = FROM_SMEM ? sm[j * SP + p] : gsrc[(base + (size_t)j * stride) / 2 + p];
-    }
+    for (int q = 0; q < R0; ++q) u[q] = FROM_SMEM ? sm[(b + q * R1) * SP + p] : g[(size_t)q * R1 * (STRIDE >> 1)];
     dft<T, C, R0>(u);
   }
   if (FROM_SMEM) __syncthreads();  // every read of the tile precedes the overwrite
-  if (t < nb) {
+  if (t < R1 * P) {
 #pragma unroll
     for (int q = 0; q < R0; ++q) sm[(b * R0 + q) * SP + p] = u[q];
   }
@@ -382,17 +385,13 @@ __device__ __forceinline__ C hartley_pair(const C X, const C Y) {
   return C{X.x - X.y + Y.x + Y.y, X.x + X.y - Y.x + Y.y};
 }
 
-// Stage 2 (radix R1, twiddles tw[q b]) in place: butterfly b of pencil p reads
-// and writes exactly the positions b + q R0, so threads never touch each
-// other's data and no barrier is needed between reads and writes.
-template <typename T, typename C, int R0, int R1>
-__device__ __forceinline__ void s2_stage2(C *sm, int SP, int logP, const C *__restrict__ tw) {
-  static_assert(R0 * 16 <= kThreads, "one stage-2 butterfly per thread");
-  const int P = 1 << logP;
-  const int nb = R0 << logP;
+template <typename T, typename C, int R0, int R1, int P>
+__device__ __forceinline__ void s2_stage2(C *sm, const C *__restrict__ tw) {
+  constexpr int SP = P + 1, LP = ilog2c(P);
+  static_assert(R0 * P <= kThreads, "one stage-2 butterfly per thread");
   const int t = threadIdx.x;
-  if (t < nb) {
-    const int p = t & (P - 1), b = t >> logP;
+  if (t < R0 * P) {
+    const int p = t & (P - 1), b = t >> LP;
     C x[R1];
 #pragma unroll
     for (int q = 0; q < R1; ++q) {
@@ -406,41 +405,67 @@ __device__ __forceinline__ void s2_stage2(C *sm, int SP, int logP, const C *__re
   __syncthreads();
 }
 
-// Hartley combine of the spectrum X in shared memory: thread (p, k), k <= N/2,
-// forms 2(H a), 2(H b) at k and N - k. MODE 0: store to global (rows of P
-// complex values, coalesced); 1: scale by G, reduce r.z into acc, write back in
-// place for the second transform.
-template <typename T, typename C, int N, int MODE>
-__device__ __forceinline__ void s2_combine(C *sm, int SP, int logP, C *__restrict__ gdst, size_t base, size_t stride,
-                                           const SpectralDev &sp, int k2, int c0, const T *vtab, Accum<T> &acc) {
-  const int P = 1 << logP;
+// Multiplier G at (k, k2, k3a) and (k, k2, k3a + 1), k3a = c0 + 2p: exact
+// (RR = 0), rank RR with the column factors va/vb of this thread's pencil in
+// registers (RR > 0), or a runtime rank (RR < 0, factors read from vtab).
+template <typename T, int N, int P, int RR>
+__device__ __forceinline__ void s2_multiplier(const SpectralDev &sp, int k, int k2, int c0, int p, const T *vtab,
+                                              const T (&va)[RR > 0 ? RR : 1], const T (&vb)[RR > 0 ? RR : 1],
+                                              T &ga, T &gb) {
   const T *lam = reinterpret_cast<const T *>(sp.lam);
   const T *uf = reinterpret_cast<const T *>(sp.u);
-  const int R = sp.rank;
-  const T gscale = (T)sp.scale;
-  for (int t = threadIdx.x; t < ((N / 2 + 1) << logP); t += kThreads) {
-    const int p = t & (P - 1), k = t >> logP;
+  const int k3a = c0 + 2 * p;
+  if constexpr (RR == 0) {
+    const T gscale = (T)sp.scale;
+    const T l12 = lam[k] + lam[k2];
+    const T g1 = l12 + lam[k3a], g2 = l12 + lam[k3a + 1];
+    ga = (g1 > (T)0) ? gscale / g1 : (T)0;
+    gb = (g2 > (T)0) ? gscale / g2 : (T)0;
+  } else {
+    T sa = (T)0, sb = (T)0;
+    if constexpr (RR > 0) {
+#pragma unroll
+      for (int rr = 0; rr < RR; ++rr) {
+        const T uk = uf[rr * N + k];
+        sa = fma(uk, va[rr], sa);
+        sb = fma(uk, vb[rr], sb);
+      }
+    } else {
+      for (int rr = 0; rr < sp.rank; ++rr) {
+        const T uk = uf[rr * N + k];
+        sa = fma(uk, vtab[rr * 2 * P + 2 * p], sa);
+        sb = fma(uk, vtab[rr * 2 * P + 2 * p + 1], sb);
+      }
+    }
+    ga = (k == 0 && k2 == 0 && k3a == 0) ? (T)0 : sa;
+    gb = sb;  // k3a + 1 >= 1
+  }
+}
+
+// MODE 0: store to global (rows of P complex values, coalesced); 1: scale by
+// G, reduce r.z into acc, write back in place for the second transform.
+template <typename T, typename C, int N, int P, int MODE, int RR, long long STRIDE>
+__device__ __forceinline__ void s2_combine(C *sm, C *__restrict__ gdst, size_t base, const SpectralDev &sp, int k2,
+                                           int c0, const T *vtab, Accum<T> &acc) {
+  constexpr int SP = P + 1, LP = ilog2c(P);
+  const int p = threadIdx.x & (P - 1);  // the same pencil for all of this thread's outputs
+  T va[RR > 0 ? RR : 1], vb[RR > 0 ? RR : 1];
+  if constexpr (MODE == 1 && RR > 0) {
+#pragma unroll
+    for (int rr = 0; rr < RR; ++rr) {
+      va[rr] = vtab[rr * 2 * P + 2 * p];
+      vb[rr] = vtab[rr * 2 * P + 2 * p + 1];
+    }
+  }
+  C *g = gdst + (base >> 1) + p;
+  for (int t = threadIdx.x; t < ((N / 2 + 1) << LP); t += kThreads) {
+    const int k = t >> LP;
     const int km = (k == 0) ? 0 : N - k;
     const C X = sm[k * SP + p], Y = sm[km * SP + p];
     C hk = hartley_pair(X, Y), hm = hartley_pair(Y, X);
     if (MODE == 1) {
-      const int k3a = c0 + 2 * p, k3b = k3a + 1;
       T ga, gb;
-      if (R == 0) {
-        const T l12 = lam[k] + lam[k2];
-        const T g1 = l12 + lam[k3a], g2 = l12 + lam[k3b];
-        ga = (g1 > (T)0) ? gscale / g1 : (T)0;
-        gb = (g2 > (T)0) ? gscale / g2 : (T)0;
-      } else {
-        T sa = (T)0, sb = (T)0;
-        for (int rr = 0; rr < R; ++rr) {
-          const T uk = uf[rr * N + k];
-          sa = fma(uk, vtab[rr * 2 * P + 2 * p], sa);
-          sb = fma(uk, vtab[rr * 2 * P + 2 * p + 1], sb);
-        }
-        ga = (k == 0 && k2 == 0 && k3a == 0) ? (T)0 : sa;
-        gb = sb;
-      }
+      s2_multiplier<T, N, P, RR>(sp, k, k2, c0, p, vtab, va, vb, ga, gb);
       T e2 = fma(ga * hk.x, hk.x, gb * hk.y * hk.y);
       if (km != k) e2 += fma(ga * hm.x, hm.x, gb * hm.y * hm.y);
       acc.add(e2);
@@ -449,30 +474,30 @@ __device__ __forceinline__ void s2_combine(C *sm, int SP, int logP, C *__restric
       sm[k * SP + p] = hk;
       if (km != k) sm[km * SP + p] = hm;
     } else {
-      gdst[(base + (size_t)k * stride) / 2 + p] = hk;
-      if (km != k) gdst[(base + (size_t)km * stride) / 2 + p] = hm;
+      g[(size_t)k * (STRIDE >> 1)] = hk;
+      if (km != k) g[(size_t)km * (STRIDE >> 1)] = hm;
     }
   }
   __syncthreads();
 }
 
 // Strided-axis tile (AXIS 1 or 2) with the two-stage plan R0 x R1. SCALE: pass C.
-template <typename T, int AXIS, int R0, int R1, bool SCALE>
+template <typename T, int AXIS, int R0, int R1, int P, bool SCALE, int RR>
 __device__ __forceinline__ void dht_tile_s2(const SpectralDev &sp, const DhtTile<T> &a, int tile,
                                             typename Cx<T>::type *sm, const typename Cx<T>::type *tw, T *vtab,
                                             Accum<T> &acc) {
   using C = typename Cx<T>::type;
   constexpr int N = R0 * R1;
-  const int logP = a.logP, P = 1 << logP, SP = P + 1;
-  const size_t NN = (size_t)N * N;
-  const int nb2 = N / (2 * P);
+  constexpr long long NN = (long long)N * N;
+  constexpr long long STRIDE = (AXIS == 2) ? N : NN;
+  constexpr int nb2 = N / (2 * P);
+  static_assert(nb2 >= 1, "a tile of 2P pencils must fit the grid");
   const int line = tile / nb2, cb = tile - line * nb2;
   const int c0 = cb * 2 * P;
   const size_t base = (AXIS == 2) ? (size_t)line * NN + c0 : (size_t)line * N + c0;
-  const size_t stride = (AXIS == 2) ? (size_t)N : NN;
   const int k2 = line;
   __syncthreads();
-  if (SCALE && sp.rank > 0) {
+  if (SCALE && RR != 0) {
     const T *uf = reinterpret_cast<const T *>(sp.u);
     for (int e = threadIdx.x; e < sp.rank * 2 * P; e += kThreads) {
       const int rr = e / (2 * P), w = e - rr * 2 * P;
@@ -481,22 +506,22 @@ __device__ __forceinline__ void dht_tile_s2(const SpectralDev &sp, const DhtTile
   }
   const C *gin = reinterpret_cast<const C *>(a.in);
   C *gout = reinterpret_cast<C *>(a.out);
-  s2_stage1<T, C, R0, R1, false>(gin, base, stride, sm, SP, logP);
-  s2_stage2<T, C, R0, R1>(sm, SP, logP, tw);
+  s2_stage1<T, C, R0, R1, P, false, STRIDE>(gin, base, sm);
+  s2_stage2<T, C, R0, R1, P>(sm, tw);
   if (SCALE) {
-    s2_combine<T, C, N, 1>(sm, SP, logP, gout, base, stride, sp, k2, c0, vtab, acc);
-    s2_stage1<T, C, R0, R1, true>(gin, base, stride, sm, SP, logP);
-    s2_stage2<T, C, R0, R1>(sm, SP, logP, tw);
+    s2_combine<T, C, N, P, 1, RR, STRIDE>(sm, gout, base, sp, k2, c0, vtab, acc);
+    s2_stage1<T, C, R0, R1, P, true, STRIDE>(gin, base, sm);
+    s2_stage2<T, C, R0, R1, P>(sm, tw);
   }
-  s2_combine<T, C, N, 0>(sm, SP, logP, gout, base, stride, sp, k2, c0, vtab, acc);
+  s2_combine<T, C, N, P, 0, RR, STRIDE>(sm, gout, base, sp, k2, c0, vtab, acc);
 }
 
 // ----------------------------------------------------------------------------
-// Two-stage tile for the contiguous axis (x3), N = R0 * R1: 2P consecutive rows
-// of N reals, rows 2p and 2p+1 forming complex pencil p. Shared memory holds
-// pencil p at p * SJ + x3pos(j) with one pad entry per 16 (SJ = x3pos(N)), so
-// that the stage-1 writes (stride R0 = 16 along j across lanes) and the
-// stage-2 / combine accesses (consecutive j across lanes) are conflict-free.
+// Two-stage tile for the contiguous axis (x3): 2P consecutive rows of N reals,
+// rows 2p and 2p+1 forming complex pencil p. Shared memory holds pencil p at
+// p * SJ + x3pos(j) with one pad entry per 16 (SJ = x3pos(N)), so that the
+// stage-1 writes (stride R0 = 16 along j across lanes) and the stage-2 /
+// combine accesses (consecutive j across lanes) are conflict-free.
 //   stage 1: butterfly (p, b), b < R1, b fastest so that lanes read
 //     consecutive row entries: x[b + q R1] of rows 2p, 2p+1 for q < R0 (pass
 //     A fuses r -= alpha q and ||r||^2 here), radix R0, y -> x3pos(b R0 + q);
@@ -512,9 +537,10 @@ __host__ __device__ constexpr int x3pos(int j) { return j + (j >> 4); }
 // `in` and writes it through `r`), so the compiler keeps every load behind
 // the stores before it; each butterfly therefore issues its loads in chunks
 // of HC pairs ahead of the chunk's stores, one memory latency per chunk.
-template <typename T, typename C, int R0, int R1, int LOADM>
-__device__ __forceinline__ void x3_stage1(const DhtTile<T> &a, size_t row0, C *sm, int SJ, int P, Accum<T> &acc) {
+template <typename T, typename C, int R0, int R1, int P, int LOADM>
+__device__ __forceinline__ void x3_stage1(const DhtTile<T> &a, size_t row0, C *sm, Accum<T> &acc) {
   constexpr int N = R0 * R1;
+  constexpr int SJ = x3pos(N);
   constexpr int HC = R0 > 8 ? 8 : R0;
   const T alpha = a.alpha;
   for (int t = threadIdx.x; t < R1 * P; t += kThreads) {
@@ -559,8 +585,9 @@ __device__ __forceinline__ void x3_stage1(const DhtTile<T> &a, size_t row0, C *s
   __syncthreads();
 }
 
-template <typename T, typename C, int R0, int R1>
-__device__ __forceinline__ void x3_stage2(C *sm, int SJ, int P, const C *__restrict__ tw) {
+template <typename T, typename C, int R0, int R1, int P>
+__device__ __forceinline__ void x3_stage2(C *sm, const C *__restrict__ tw) {
+  constexpr int SJ = x3pos(R0 * R1);
   for (int t = threadIdx.x; t < R0 * P; t += kThreads) {
     const int p = t / R0, b = t - p * R0;
     C *sp = sm + p * SJ;
@@ -604,9 +631,10 @@ __device__ __forceinline__ void x3_put4(const DhtTile<T> &a, const size_t (&g)[4
   }
 }
 
-template <typename T, typename C, int N, int STOREM>
-__device__ __forceinline__ void x3_combine(const DhtTile<T> &a, size_t row0, const C *sm, int SJ, int P) {
+template <typename T, typename C, int N, int P, int STOREM>
+__device__ __forceinline__ void x3_combine(const DhtTile<T> &a, size_t row0, const C *sm) {
   constexpr int H = N / 2;
+  constexpr int SJ = x3pos(N);
   for (int t = threadIdx.x; t < H * P; t += kThreads) {
     const int p = t / H, k = t - p * H;
     const C *sp = sm + p * SJ;

@@ -97,13 +97,14 @@ def test_operator_fp32(sq, L, n, seed):
     assert _relmax(_host(y).astype(np.float64), re.A @ psi.ravel().astype(np.float64)) <= 1e-5
 
 
-# FP32 operator with 1, 2 and 4 node rows per thread (every valid N, 2^a 3^b
-# with b <= 1 and N >= 8, is divisible by 4): grids ragged against the
-# 32-wide j3 tiles and the 8*rows-high j2 tiles, and exact multiples.
+# FP32 operator with 1, 2 and 4 node rows per thread and the shared-memory-
+# staged kernel (8; used where N is a multiple of 32, else 4 rows): grids
+# ragged against the 32-wide j3 tiles and the 8*rows-high j2 tiles, and exact
+# multiples (every valid N, 2^a 3^b with b <= 1 and N >= 8, is divisible by 4).
 ROW_GRIDS = [(3, 4, 8), (3, 8, 9), (4, 8, 11), (12, 4, 12), (12, 8, 13), (6, 32, 14)]
 
 
-@pytest.mark.parametrize("rows", [1, 2, 4])
+@pytest.mark.parametrize("rows", [1, 2, 4, 8])
 @pytest.mark.parametrize("L,n,seed", ROW_GRIDS)
 def test_operator_fp32_rows_per_thread(sq, rows, L, n, seed):
     re = problem.realization(L, n, seed, 1.0, 100.0)
@@ -121,7 +122,7 @@ def test_operator_fp32_rows_per_thread(sq, rows, L, n, seed):
     assert _relmax(_host(y).astype(np.float64), re.A @ psi.ravel().astype(np.float64)) <= 1e-5
 
 
-@pytest.mark.parametrize("rows", [1, 2, 4])
+@pytest.mark.parametrize("rows", [1, 2, 4, 8])
 def test_fp32_refinement_rows_per_thread(sq, rows):
     # p.Ap of the inner FP32 iteration comes from the operator's reduction
     re = problem.realization(6, 4, 21, 1.0, 100.0)
@@ -138,7 +139,7 @@ def test_fp32_refinement_rows_per_thread(sq, rows):
 
 
 def test_stencil_rows_option_rejects_bad_values(sq):
-    for bad in (3, 5, -1, 8):
+    for bad in (3, 5, -1, 16):
         with pytest.raises(sq.SqError):
             sq.sq_set_option(sq.SQ_OPT_STENCIL_ROWS, bad)
 
