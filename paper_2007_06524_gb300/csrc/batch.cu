@@ -26,8 +26,12 @@ struct BSolve {
   int dir;
   int logP;        // Hartley tile: P = 2^logP complex pencils
   int zc;          // stencil planes per block
-  int nb_st;       // stencil blocks of this solve
-  int nb_dht;      // Hartley tiles of this solve (same for every axis)
+  int nb_st;       // stencil blocks of this solve (one node row per thread)
+  int in_staged;   // inner FP32 operator: 1 = staged 32 x 32 tiles (N % 32 == 0), 0 = one row per thread
+  int zc_in;       // planes per block of the inner operator
+  int nb_in;       // inner FP32 operator blocks of this solve
+  int ntiles;      // Hartley tiles of this solve (same for every axis)
+  int nb_dht;      // Hartley blocks of this solve: kTilesPerBlock tiles each
   int nb_vec;      // vector-kernel blocks of this solve
   int pstride;     // partials row stride
   double *x;       // caller's psi (FP64 iterate)
@@ -59,10 +63,13 @@ __global__ void kb_scalars_reset(BSolve *S, int count, double tolrel2, int max_i
   iters_total[s] = 0;
 }
 
-// WHICH 0: outer FP64 residual r32 = b - A x (FIN_RESID on st_o);
-// WHICH 1: inner FP32 q = A p (FIN_ALPHA on st_i).
+// WHICH 0: outer FP64 residual r32 = b - A x (FIN_RESID on st_o), one node
+// row per thread (FP64-ALU-bound);
+// WHICH 1: inner FP32 q = A p (FIN_ALPHA on st_i): the shared-memory-staged
+// operator (stencil_staged_run) on 32 x 32 tiles where N % 32 == 0, else one
+// row per thread.
 template <int WHICH>
-__global__ void __launch_bounds__(kThreads) kb_stencil(const BSolve *__restrict__ S, const int *__restrict__ pre,
+__global__ void __launch_bounds__(kThreads, WHICH == 1 ? 3 : 1) kb_stencil(const BSolve *__restrict__ S, const int *__restrict__ pre,
                                                        int count) {
   using Ti = typename std::conditional<WHICH == 0, double, float>::type;
   const int s = find_solve(pre, count, blockIdx.x);
@@ -72,6 +79,23 @@ __global__ void __launch_bounds__(kThreads) kb_stencil(const BSolve *__restrict_
   __shared__ Ti tab[256][kTabStride];
   __shared__ short cellof[kMaxN];
   const int tid = threadIdx.x + 32 * threadIdx.y;
+  if constexpr (WHICH == 1) {
+    if (B.in_staged) {
+      extern __shared__ __align__(16) float ring[];  // kStages * kSlot floats
+      const int N = B.c.N, nbx = N / 32, ntl = nbx * nbx;
+      const int lb = blockIdx.x - pre[s];
+      const int tile = lb % ntl, zb = lb / ntl;
+      const int z0 = zb * B.zc_in, z1 = min(z0 + B.zc_in, N);
+      Accum<float> acc;
+      stencil_staged_run(B.c, B.p, B.q, tab, cellof, ring, (tile / nbx) * 32, (tile % nbx) * 32, z0, z1, acc);
+      FF v[2] = {acc.part(), FF{0.f, 0.f}};
+      double out[2];
+      if (reduce_last_block_ex<2>(v, B.partials, B.pstride, &st->ticket, B.nb_in, lb, out)) {
+        if (tid == 0) finalize_scalars(st, FIN_ALPHA, out, 2);
+      }
+      return;
+    }
+  }
   build_pattern_table<Ti>(tab, B.c, tid);
   build_cellof(cellof, B.c.N, B.c.n, tid);
   __syncthreads();
@@ -90,15 +114,74 @@ __global__ void __launch_bounds__(kThreads) kb_stencil(const BSolve *__restrict_
   }
   typename Accum<Ti>::Part v[2] = {acc0.part(), acc1.part()};
   double out[2];
-  if (reduce_last_block_ex<2>(v, B.partials, B.pstride, &st->ticket, B.nb_st, lb, out)) {
+  if (reduce_last_block_ex<2>(v, B.partials, B.pstride, &st->ticket, WHICH == 1 ? B.nb_in : B.nb_st, lb, out)) {
     if (tid == 0) finalize_scalars(st, WHICH == 0 ? FIN_RESID : FIN_ALPHA, out, 2);
   }
 }
 
-// Inner passes on the FP32 fields of every active solve.
+// Two-stage tile (see dht_core.cuh) of plan R0 x R1 with P pencils for this
+// block's solve.
+template <int R0, int R1, int P, int AXIS, int LOADM, int STOREM, bool SCALE>
+__device__ __forceinline__ void kb_tile(const BSolve &B, const DhtTile<float> &t, int tile, float2 *sm,
+                                        const float2 *tw, float *vtab, Accum<float> &acc) {
+  if constexpr (AXIS == 3) {
+    __syncthreads();  // twiddles loaded; the previous tile's combine is done with sm
+    const size_t row0 = (size_t)tile * 2 * P;
+    x3_stage1<float, float2, R0, R1, P, LOADM>(t, row0, sm, acc);
+    x3_stage2<float, float2, R0, R1, P>(sm, tw);
+    x3_combine<float, float2, R0 * R1, P, STOREM>(t, row0, sm);
+  } else if constexpr (SCALE) {
+    if (B.sp.rank == 0)
+      dht_tile_s2<float, AXIS, R0, R1, P, true, 0>(B.sp, t, tile, sm, tw, vtab, acc);
+    else
+      dht_tile_s2<float, AXIS, R0, R1, P, true, -1>(B.sp, t, tile, sm, tw, vtab, acc);
+  } else {
+    dht_tile_s2<float, AXIS, R0, R1, P, false, -1>(B.sp, t, tile, sm, tw, vtab, acc);
+  }
+}
+
+template <int R0, int R1, int AXIS, int LOADM, int STOREM, bool SCALE>
+__device__ __forceinline__ bool kb_tile_p(const BSolve &B, const DhtTile<float> &t, int tile, float2 *sm,
+                                          const float2 *tw, float *vtab, Accum<float> &acc) {
+  if constexpr ((R0 * R1) % 16 == 0) {
+    if (B.logP == 3) {
+      kb_tile<R0, R1, 8, AXIS, LOADM, STOREM, SCALE>(B, t, tile, sm, tw, vtab, acc);
+      return true;
+    }
+  }
+  if constexpr ((R0 * R1) % 32 == 0) {
+    if (B.logP == 4) {
+      kb_tile<R0, R1, 16, AXIS, LOADM, STOREM, SCALE>(B, t, tile, sm, tw, vtab, acc);
+      return true;
+    }
+  }
+  return false;
+}
+
+// The two-stage tile where the solve's N and P have a plan; false otherwise
+// (the caller then takes the generic tile). Block-uniform branch.
 template <int AXIS, int LOADM, int STOREM, bool SCALE>
-__global__ void __launch_bounds__(kThreads) kb_dht(const BSolve *__restrict__ S, const int *__restrict__ pre,
-                                                   int count, int first) {
+__device__ __forceinline__ bool kb_fast_tile(const BSolve &B, const DhtTile<float> &t, int tile, float2 *sm,
+                                             const float2 *tw, float *vtab, Accum<float> &acc) {
+  switch (B.c.N) {
+    case 32: return kb_tile_p<8, 4, AXIS, LOADM, STOREM, SCALE>(B, t, tile, sm, tw, vtab, acc);
+    case 48: return kb_tile_p<16, 3, AXIS, LOADM, STOREM, SCALE>(B, t, tile, sm, tw, vtab, acc);
+    case 64: return kb_tile_p<8, 8, AXIS, LOADM, STOREM, SCALE>(B, t, tile, sm, tw, vtab, acc);
+    case 96: return kb_tile_p<16, 6, AXIS, LOADM, STOREM, SCALE>(B, t, tile, sm, tw, vtab, acc);
+    case 128: return kb_tile_p<16, 8, AXIS, LOADM, STOREM, SCALE>(B, t, tile, sm, tw, vtab, acc);
+    default: return false;
+  }
+}
+
+// Inner passes on the FP32 fields of every active solve. A block takes
+// kTilesPerBlock consecutive tiles of its solve, so that its fixed start-up
+// (finding the solve, its descriptor and stop flag, the twiddles) is paid
+// once per several tiles.
+constexpr int kTilesPerBlock = 4;
+
+template <int AXIS, int LOADM, int STOREM, bool SCALE>
+__global__ void __launch_bounds__(kThreads, 3) kb_dht(const BSolve *__restrict__ S, const int *__restrict__ pre,
+                                                      int count, int first) {
   using C = float2;
   const int s = find_solve(pre, count, blockIdx.x);
   const BSolve &B = S[s];
@@ -126,13 +209,20 @@ __global__ void __launch_bounds__(kThreads) kb_dht(const BSolve *__restrict__ S,
   t.beta = (float)st->beta;
   t.first = first;
   t.logP = B.logP;
-  const int tile = blockIdx.x - pre[s];
+  const int lb = blockIdx.x - pre[s];
+  const int t1 = min(B.ntiles, (lb + 1) * kTilesPerBlock);
   Accum<float> acc;
-  dht_tile<float, AXIS, LOADM, STOREM, SCALE>(B.sp, t, tile, buf0, buf1, tw, vtab, acc);
+  // the two-stage tiles use buf0 (and, for x3, part of buf1) as their shared
+  // tile; the twiddles and column factors stay where they were loaded; every
+  // tile starts with a barrier, so consecutive tiles may reuse the buffers
+  for (int tile = lb * kTilesPerBlock; tile < t1; ++tile) {
+    if (!kb_fast_tile<AXIS, LOADM, STOREM, SCALE>(B, t, tile, buf0, tw, vtab, acc))
+      dht_tile<float, AXIS, LOADM, STOREM, SCALE>(B.sp, t, tile, buf0, buf1, tw, vtab, acc);
+  }
   if (LOADM == LD_RESID || SCALE) {
     FF v[1] = {acc.part()};
     double out[1];
-    if (reduce_last_block_ex<1>(v, B.partials, B.pstride, &st->ticket, B.nb_dht, tile, out)) {
+    if (reduce_last_block_ex<1>(v, B.partials, B.pstride, &st->ticket, B.nb_dht, lb, out)) {
       if (threadIdx.x == 0) {
         int op = FIN_NONE;
         if (LOADM == LD_RESID) op = first ? FIN_NONE : FIN_RR_ITER;
@@ -235,8 +325,8 @@ struct sq_batch {
   int count;
   std::vector<BSolve> hS;
   BSolve *dS = nullptr;
-  int *d_pre = nullptr;  // [0..count] stencil, [count+1..] dht, [2count+2..] vec
-  int tot_st = 0, tot_dht = 0, tot_vec = 0;
+  int *d_pre = nullptr;  // [0..count] stencil, [count+1..] dht, [2count+2..] vec, [3count+3..] inner stencil
+  int tot_st = 0, tot_dht = 0, tot_vec = 0, tot_in = 0;
   size_t dht_smem[2] = {0, 0};  // plain passes, pass C
   void *d_mem = nullptr;        // fields, scalars, partials
   int *d_iters = nullptr;
@@ -253,6 +343,7 @@ struct sq_batch {
 namespace {
 
 constexpr int kChunk = 8;
+constexpr size_t kStagedSmem = (size_t)kStages * kSlot * sizeof(float);  // ring of the staged inner operator
 
 #define SQB_CK(call)                        \
   do {                                      \
@@ -285,7 +376,7 @@ int precond_first_b(sq_batch *b, cudaStream_t s) {
 }
 
 int iteration_b(sq_batch *b, cudaStream_t s) {
-  kb_stencil<1><<<b->tot_st, dim3(32, 8, 1), 0, s>>>(b->dS, b->d_pre, b->count);
+  kb_stencil<1><<<b->tot_in, dim3(32, 8, 1), kStagedSmem, s>>>(b->dS, b->d_pre + 3 * (b->count + 1), b->count);
   if (cudaGetLastError() != cudaSuccess) return SQ_ECUDA;
   int st;
   if ((st = launch_kb_dht<3, LD_RESID, SO_PLAIN, false>(b, 0, s)) != SQ_OK) return st;
@@ -349,7 +440,7 @@ int sq_batch_create(int count, const sq_solve_desc *descs, const sq_precond *con
   if (!b) return SQ_ENOMEM;
   b->count = count;
   b->hS.resize(count);
-  std::vector<int> pre((size_t)3 * (count + 1), 0);
+  std::vector<int> pre((size_t)4 * (count + 1), 0);
   size_t field_floats = 0;
   int maxN = 0, maxR = 0, maxP = 1;
   for (int k = 0; k < count; ++k) {
@@ -386,13 +477,23 @@ int sq_batch_create(int count, const sq_solve_desc *descs, const sq_precond *con
     B.logP = logP;
     B.zc = zc;
     B.nb_st = ((N + 31) / 32) * ((N + 7) / 8) * ((N + zc - 1) / zc);
-    B.nb_dht = N * N / (2 * P);
+    B.in_staged = (N % 32 == 0) ? 1 : 0;
+    if (B.in_staged) {
+      B.zc_in = std::min(N, 16);
+      B.nb_in = (N / 32) * (N / 32) * ((N + B.zc_in - 1) / B.zc_in);
+    } else {
+      B.zc_in = zc;
+      B.nb_in = B.nb_st;
+    }
+    B.ntiles = N * N / (2 * P);
+    B.nb_dht = (B.ntiles + kTilesPerBlock - 1) / kTilesPerBlock;
     const long long n3 = (long long)N * N * N;
     B.nb_vec = (int)std::max(1LL, std::min(4096LL, n3 / (kThreads * 8)));
-    B.pstride = std::max(B.nb_st, std::max(B.nb_dht, B.nb_vec));
+    B.pstride = std::max(std::max(B.nb_st, B.nb_in), std::max(B.nb_dht, B.nb_vec));
     pre[k + 1] = pre[k] + B.nb_st;
     pre[(count + 1) + k + 1] = pre[(count + 1) + k] + B.nb_dht;
     pre[2 * (count + 1) + k + 1] = pre[2 * (count + 1) + k] + B.nb_vec;
+    pre[3 * (count + 1) + k + 1] = pre[3 * (count + 1) + k] + B.nb_in;
     field_floats += 5 * (size_t)n3;
     maxN = std::max(maxN, N);
     maxR = std::max(maxR, sp.rank);
@@ -403,6 +504,7 @@ int sq_batch_create(int count, const sq_solve_desc *descs, const sq_precond *con
   b->tot_st = pre[count];
   b->tot_dht = pre[(count + 1) + count];
   b->tot_vec = pre[2 * (count + 1) + count];
+  b->tot_in = pre[3 * (count + 1) + count];
   // one allocation: FP32 fields, scalars (2 per solve), partials
   size_t partials = 0;
   for (auto &B : b->hS) partials += (size_t)2 * B.pstride;
@@ -445,6 +547,8 @@ int sq_batch_create(int count, const sq_solve_desc *descs, const sq_precond *con
   ok = cudaMemcpy(b->dS, b->hS.data(), sizeof(BSolve) * count, cudaMemcpyHostToDevice) == cudaSuccess;
   ok = ok && cudaMemcpy(b->d_pre, pre.data(), sizeof(int) * pre.size(), cudaMemcpyHostToDevice) == cudaSuccess;
   ok = ok && cudaMemset(sc, 0, bytes_scal) == cudaSuccess;
+  ok = ok && cudaFuncSetAttribute(kb_stencil<1>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kStagedSmem) ==
+                 cudaSuccess;
   ok = ok && set_kb_dht_smem<3, LD_PLAIN, SO_PLAIN, false>(b->dht_smem[0]) == SQ_OK;
   ok = ok && set_kb_dht_smem<3, LD_RESID, SO_PLAIN, false>(b->dht_smem[0]) == SQ_OK;
   ok = ok && set_kb_dht_smem<2, LD_PLAIN, SO_PLAIN, false>(b->dht_smem[0]) == SQ_OK;

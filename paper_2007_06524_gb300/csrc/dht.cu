@@ -147,11 +147,13 @@ static cudaError_t launch_s2_rank(const DhtArgs<float> &a, int grid, cudaStream_
   }
 }
 
-// P = 8 or 16 pencils where the tile fits the grid (2P <= N).
+// P = 8 or 16 pencils where tiles of 2P pencils cover the grid (2P | N).
 template <int AXIS, int R0, int R1, bool SCALE>
 static cudaError_t launch_s2_p(const DhtArgs<float> &a, int grid, cudaStream_t s) {
-  if (a.logP == 3) return launch_s2_rank<AXIS, R0, R1, 8, SCALE>(a, grid, s);
-  if constexpr (R0 * R1 >= 32) {
+  if constexpr ((R0 * R1) % 16 == 0) {
+    if (a.logP == 3) return launch_s2_rank<AXIS, R0, R1, 8, SCALE>(a, grid, s);
+  }
+  if constexpr ((R0 * R1) % 32 == 0) {
     if (a.logP == 4) return launch_s2_rank<AXIS, R0, R1, 16, SCALE>(a, grid, s);
   }
   return cudaErrorNotSupported;
@@ -163,7 +165,9 @@ static cudaError_t launch_strided_fast(const DhtArgs<float> &a, int grid, cudaSt
   switch (a.sp.N) {
     case 16: return launch_s2_p<AXIS, 4, 4, SCALE>(a, grid, s);
     case 32: return launch_s2_p<AXIS, 8, 4, SCALE>(a, grid, s);
+    case 48: return launch_s2_p<AXIS, 16, 3, SCALE>(a, grid, s);
     case 64: return launch_s2_p<AXIS, 8, 8, SCALE>(a, grid, s);
+    case 96: return launch_s2_p<AXIS, 16, 6, SCALE>(a, grid, s);
     case 128: return launch_s2_p<AXIS, 16, 8, SCALE>(a, grid, s);
     case 256: return launch_s2_p<AXIS, 16, 16, SCALE>(a, grid, s);
     default: return cudaErrorNotSupported;
@@ -222,8 +226,10 @@ static cudaError_t launch_s3(const DhtArgs<float> &a, int grid, cudaStream_t s) 
 
 template <int R0, int R1, int LOADM, int STOREM>
 static cudaError_t launch_s3_p(const DhtArgs<float> &a, int grid, cudaStream_t s) {
-  if (a.logP == 3) return launch_s3<R0, R1, 8, LOADM, STOREM>(a, grid, s);
-  if constexpr (R0 * R1 >= 32) {
+  if constexpr ((R0 * R1) % 16 == 0) {
+    if (a.logP == 3) return launch_s3<R0, R1, 8, LOADM, STOREM>(a, grid, s);
+  }
+  if constexpr ((R0 * R1) % 32 == 0) {
     if (a.logP == 4) return launch_s3<R0, R1, 16, LOADM, STOREM>(a, grid, s);
   }
   return cudaErrorNotSupported;
@@ -235,7 +241,9 @@ static cudaError_t launch_contig_fast(const DhtArgs<float> &a, int grid, cudaStr
   switch (a.sp.N) {
     case 16: return launch_s3_p<4, 4, LOADM, STOREM>(a, grid, s);
     case 32: return launch_s3_p<8, 4, LOADM, STOREM>(a, grid, s);
+    case 48: return launch_s3_p<16, 3, LOADM, STOREM>(a, grid, s);
     case 64: return launch_s3_p<8, 8, LOADM, STOREM>(a, grid, s);
+    case 96: return launch_s3_p<16, 6, LOADM, STOREM>(a, grid, s);
     case 128: return launch_s3_p<16, 8, LOADM, STOREM>(a, grid, s);
     case 256: return launch_s3_p<16, 16, LOADM, STOREM>(a, grid, s);
     default: return cudaErrorNotSupported;

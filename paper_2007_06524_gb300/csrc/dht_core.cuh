@@ -73,6 +73,19 @@ __device__ __forceinline__ void dft(C (&u)[R]) {
       u[k1 + 8] = b2;
       u[k1 + 12] = b3;
     }
+  } else if (R == 6) {
+    // 6 = 2 x 3: DFT3 of the even and odd samples, twiddles W6^k, radix-2 combine
+    const T h = (T)0.5, c = (T)0.86602540378443864676;  // cos, sin of pi/3
+    C e[3] = {u[0], u[2], u[4]}, o[3] = {u[1], u[3], u[5]};
+    dft<T, C, 3>(e);
+    dft<T, C, 3>(o);
+    const C w1 = cmul(o[1], C{h, -c}), w2 = cmul(o[2], C{-h, -c});
+    u[0] = cadd(e[0], o[0]);
+    u[3] = csub(e[0], o[0]);
+    u[1] = cadd(e[1], w1);
+    u[4] = csub(e[1], w1);
+    u[2] = cadd(e[2], w2);
+    u[5] = csub(e[2], w2);
   } else if (R == 8) {
     const T h = (T)0.70710678118654752440;  // sqrt(2)/2
     C e0 = u[0], e1 = u[2], e2 = u[4], e3 = u[6];
@@ -337,7 +350,7 @@ __device__ __forceinline__ void dht_tile(const SpectralDev &sp, const DhtTile<T>
 namespace sq {
 
 // ----------------------------------------------------------------------------
-// Two-stage tiles (FP32): N = R0 * R1 with power-of-two radices, P complex
+// Two-stage tiles (FP32): N = R0 * R1 with radices 3, 4, 6, 8, 16, P complex
 // pencils per tile, all shape parameters compile-time so that the index
 // arithmetic folds to shifts and constants. One shared-memory round trip per
 // transform.

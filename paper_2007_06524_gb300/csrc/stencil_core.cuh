@@ -213,4 +213,156 @@ __device__ __forceinline__ void stencil_rows(const CellsDev &c, int dir, const T
   }
 }
 
+// ------------------------------------------------- staged FP32 operator
+// q = A p with p.q for FP32 single solves where N is a multiple of 32 and x is
+// 16-byte aligned. A block owns one tile of 32 node columns (j3) x 32 node
+// rows (j2) and a run of zc consecutive planes j1 (grid = tiles x plane runs,
+// sized to one wave of resident blocks, so the copy pipeline is filled once
+// per block). Each plane of the tile with its one-node halo (rows j2-1 and
+// j2+32, columns j3-1 and j3+32, periodic) is copied into a ring of kStages
+// shared-memory slots with cp.async, kStages - 2 planes ahead of its use: no
+// thread waits on HBM latency, and every neighbour is a conflict-free shared-
+// memory read at a fixed offset. A thread owns column j3 of four consecutive
+// rows; x(j1-1) and x(j1) stay in registers, and so do the four rows'
+// coefficients between cell boundaries.
+constexpr int kStages = 6;
+constexpr int kSW = 40;             // slot row stride (floats): left halo at 3, body 4..35, right halo 36
+constexpr int kSRows = 34;          // rows j2-1 .. j2+32
+constexpr int kSlot = kSRows * kSW;  // floats per slot
+
+__device__ __forceinline__ void cp_async16(float *dst, const float *src) {
+  const unsigned d = (unsigned)__cvta_generic_to_shared(dst);
+  asm volatile("cp.async.cg.shared.global [%0], [%1], 16;\n" ::"r"(d), "l"(src) : "memory");
+}
+__device__ __forceinline__ void cp_async4(float *dst, const float *src) {
+  const unsigned d = (unsigned)__cvta_generic_to_shared(dst);
+  asm volatile("cp.async.ca.shared.global [%0], [%1], 4;\n" ::"r"(d), "l"(src) : "memory");
+}
+__device__ __forceinline__ void cp_async_commit() { asm volatile("cp.async.commit_group;\n" ::: "memory"); }
+template <int PENDING>
+__device__ __forceinline__ void cp_async_wait() {
+  asm volatile("cp.async.wait_group %0;\n" ::"n"(PENDING) : "memory");
+}
+
+// Issues the copies of plane j1 (< N) of tile (j2_0, j3_0) with its halo into slot s.
+__device__ __forceinline__ void stage_plane(float *s, const float *__restrict__ x, int N, int j1, int j2_0, int j3_0,
+                                            int tid) {
+  const float *pl = x + (size_t)j1 * N * N;
+  {  // body: 32 rows x 8 chunks of 4 floats, one chunk per thread
+    const int row = tid >> 3, ch = tid & 7;
+    cp_async16(s + (1 + row) * kSW + 4 + 4 * ch, pl + (size_t)(j2_0 + row) * N + j3_0 + 4 * ch);
+  }
+  if (tid < 16) {  // halo rows j2_0 - 1 and j2_0 + 32
+    const int hr = tid >> 3, ch = tid & 7;
+    const int gr = hr ? (j2_0 + 32 == N ? 0 : j2_0 + 32) : (j2_0 == 0 ? N - 1 : j2_0 - 1);
+    cp_async16(s + (hr ? kSRows - 1 : 0) * kSW + 4 + 4 * ch, pl + (size_t)gr * N + j3_0 + 4 * ch);
+  } else if (tid < 80) {  // halo columns j3_0 - 1 and j3_0 + 32
+    const int e = tid - 16, side = e >> 5, row = e & 31;
+    const int gc = side ? (j3_0 + 32 == N ? 0 : j3_0 + 32) : (j3_0 == 0 ? N - 1 : j3_0 - 1);
+    cp_async4(s + (1 + row) * kSW + (side ? 36 : 3), pl + (size_t)(j2_0 + row) * N + gc);
+  }
+}
+
+
+// Runs the staged FP32 operator y = A x (MATVEC) over planes [z0, z1) of the
+// 32 x 32 tile (j2_0, j3_0) and adds p.Ap to acc. Builds the block's pattern
+// and cell tables itself; `ring` is kStages * kSlot floats of 16-byte aligned
+// shared memory. All threads of the block (32 x 8) must call it.
+__device__ __forceinline__ void stencil_staged_run(const CellsDev &c, const float *__restrict__ x,
+                                                   float *__restrict__ y, float (*tab)[kTabStride], short *cellof,
+                                                   float *ring, int j2_0, int j3_0, int z0, int z1,
+                                                   Accum<float> &acc) {
+  const int tid = threadIdx.x + 32 * threadIdx.y;
+  const int N = c.N, n = c.n, L = c.L, LL = L * L;
+  const int NN = N * N;
+  // prologue: planes z0 .. z0 + kStages - 2 (one commit group each, empty past z1)
+#pragma unroll
+  for (int st = 0; st < kStages - 1; ++st) {
+    const int j = z0 + st;
+    if (j <= z1) stage_plane(ring + st * kSlot, x, N, j == N ? 0 : j, j2_0, j3_0, tid);
+    cp_async_commit();
+  }
+  __syncthreads();  // the caller's previous use of the tables is over
+  build_pattern_table<float>(tab, c, tid);
+  build_cellof(cellof, N, n, tid);
+  __syncthreads();
+
+  const int tx = threadIdx.x, ty = threadIdx.y;
+  const int j3 = j3_0 + tx, j2b = j2_0 + 4 * ty;
+  const int j3m = (j3 == 0) ? N - 1 : j3 - 1;
+  const int c3a = cellof[j3], c3b = cellof[j3m];
+  int crow[5];
+#pragma unroll
+  for (int q = 0; q <= 4; ++q) crow[q] = cellof[(j2b - 1 + q < 0) ? N - 1 : j2b - 1 + q] * L;
+  const int j1m0 = (z0 == 0) ? N - 1 : z0 - 1;
+  int cpos = z0 - cellof[z0] * n;
+  unsigned np[4], nc[4];
+  row_nibbles<4>(c.phase, cellof[j1m0], LL, crow, c3a, c3b, np);
+  if (cpos == 0) {
+    row_nibbles<4>(c.phase, cellof[z0], LL, crow, c3a, c3b, nc);
+  } else {
+#pragma unroll
+    for (int r = 0; r < 4; ++r) nc[r] = np[r];
+  }
+  float t[4][7];
+  row_coeffs<float, 4>(tab, nc, np, t);
+  const int row0 = j2b * N + j3;
+  float xm[4], x0[4];
+#pragma unroll
+  for (int r = 0; r < 4; ++r) xm[r] = x[(size_t)j1m0 * NN + row0 + r * N];
+
+  for (int k = 0; z0 + k < z1; ++k) {
+    const int j1 = z0 + k;
+    cp_async_wait<kStages - 3>();  // this thread's copies of planes j1, j1 + 1 have landed
+    __syncthreads();               // ... everyone's; and everyone is done with plane j1 - 1's slot
+    {
+      const int j = j1 + kStages - 1;
+      if (j <= z1) stage_plane(ring + ((k + kStages - 1) % kStages) * kSlot, x, N, j == N ? 0 : j, j2_0, j3_0, tid);
+      cp_async_commit();
+    }
+    if (k > 0) {
+      cpos = (cpos + 1 == n) ? 0 : cpos + 1;
+      if (cpos <= 1) {
+#pragma unroll
+        for (int r = 0; r < 4; ++r) np[r] = nc[r];
+        if (cpos == 0) row_nibbles<4>(c.phase, cellof[j1], LL, crow, c3a, c3b, nc);
+        row_coeffs<float, 4>(tab, nc, np, t);
+      }
+    }
+    const float *S0 = ring + (k % kStages) * kSlot + (1 + 4 * ty) * kSW + 4 + tx;
+    const float *S1 = ring + ((k + 1) % kStages) * kSlot + (1 + 4 * ty) * kSW + 4 + tx;
+    if (k == 0) {
+#pragma unroll
+      for (int r = 0; r < 4; ++r) x0[r] = S0[r * kSW];
+    }
+    float xp[4];
+#pragma unroll
+    for (int r = 0; r < 4; ++r) xp[r] = S1[r * kSW];
+    float *yp = y + (size_t)j1 * NN + row0;
+    float psum = 0.f;
+#pragma unroll
+    for (int r = 0; r < 4; ++r) {
+      const float *cr = S0 + r * kSW;
+      const float x2m = (r == 0) ? cr[-kSW] : x0[r > 0 ? r - 1 : 0];
+      const float x2p = (r == 3) ? cr[kSW] : x0[r < 3 ? r + 1 : 3];
+      float off = t[r][0] * xp[r];
+      off = fmaf(t[r][1], xm[r], off);
+      off = fmaf(t[r][2], x2p, off);
+      off = fmaf(t[r][3], x2m, off);
+      off = fmaf(t[r][4], cr[1], off);
+      off = fmaf(t[r][5], cr[-1], off);
+      const float ax = fmaf(t[r][6], x0[r], -off);
+      yp[r * N] = ax;
+      psum = fmaf(x0[r], ax, psum);
+    }
+    acc.add(psum);
+#pragma unroll
+    for (int r = 0; r < 4; ++r) {
+      xm[r] = x0[r];
+      x0[r] = xp[r];
+    }
+  }
+  cp_async_wait<0>();
+}
+
 }  // namespace sq

@@ -89,3 +89,36 @@ def test_batch_degenerate_and_invalid(sq):
         sq.sq_batch_create([(c1, 0, _empty(16))], [sq.sq_precond_setup(32, 0)])   # N mismatch
     with pytest.raises(sq.SqError):
         sq.sq_batch_create([(c1, 0, _empty(16))], [pc], tiles=[(16, 3, 4)])       # P not a power of two
+
+
+def test_batch_two_stage_tiles_mixed_sizes(sq):
+    """Default tiles (P = 16, 8, 16, 16 for N = 32, 48, 64, 96) take the two-stage
+    Hartley tiles inside the batched kernels, radix-3 and radix-6 plans included:
+    the batch matches the oracle (N = 32, 48) and single solves (all sizes)."""
+    import torch
+
+    cases = [(8, 4, 41), (12, 4, 42), (16, 4, 43), (24, 4, 44)]
+    descs, pl, singles, refs = [], [], [], []
+    for L, n, seed in cases:
+        N = L * n
+        c = sq.sq_build_coeffs(L, n, seed, 0.5, 1.0, 10.0)
+        pc = sq.sq_precond_setup(N, 0)
+        w = sq.sq_workspace_create(N, sq.SQ_FP32_REFINE)
+        ps = _empty(N)
+        sq.sq_pcg_solve(c, pc, w, 1, 1e-9, 2000, sq.SQ_FP32_REFINE, None, ps)
+        singles.append(ps.cpu().numpy())
+        descs.append((c, 1, _empty(N)))
+        pl.append(pc)
+        if N <= 48:
+            re = problem.realization(L, n, seed, 1.0, 10.0)
+            refs.append(pcg.tight_solve(re.A, re.b[1], N)[0])
+        else:
+            refs.append(None)
+    infos = sq.sq_pcg_solve_batched(sq.sq_batch_create(descs, pl), 1e-9, 2000)
+    torch.cuda.synchronize()
+    for (c, i, psi), xs, ref, inf in zip(descs, singles, refs, infos):
+        assert inf["status"] == sq.SQ_OK and inf["relres_true"] <= 1e-9
+        x = psi.cpu().numpy()
+        assert np.linalg.norm(x - xs) / np.linalg.norm(xs) <= 1e-6
+        if ref is not None:
+            assert np.linalg.norm(x - ref) / np.linalg.norm(ref) <= 1e-6

@@ -362,7 +362,7 @@ def test_full_size_n256_sampled(sq):
     assert np.linalg.norm(xr - x.ravel()) / np.linalg.norm(x) <= 1e-5
 
 
-@pytest.mark.parametrize("N", [16, 32, 64, 128, 256])
+@pytest.mark.parametrize("N", [16, 32, 48, 64, 96, 128, 256])
 def test_precond_generic_and_two_stage_paths_agree(sq, N):
     """The Hartley passes have two implementations (two-stage register plans
     for x1/x2 and for the contiguous x3, and the generic shared-memory
