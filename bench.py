@@ -122,6 +122,41 @@ def _algorithmic(N, elem, rank_r):
     }
 
 
+def kernel_table(work, prof, N, elem, R, t_ms):
+    """Per-class table and the dominant class's roofline from the library's
+    event profile: achieved = algorithmic bytes (flops) per launch x launches
+    that did work / their summed duration (launches that returned at entry,
+    their solve having stopped, excluded by sq_profile_work)."""
+    alg = _algorithmic(N, elem, R)
+    peaks = _peaks()
+    kernels = {}
+    for name, (ms, cnt) in prof.items():
+        if ms <= 0:
+            continue
+        k = {"ms": round(ms, 3), "launches": cnt, "share": round(ms / t_ms, 4)}
+        wms, wn = work.get(name, (0.0, 0))
+        if name in alg and wn > 0 and wms > 0:
+            b, f = alg[name]
+            k.update({"work_launches": wn, "us_per_work_launch": round(wms / wn * 1e3, 1),
+                      "GBps": round(b * wn / (wms / 1e3) / 1e9, 1), "GFLOPps": round(f * wn / (wms / 1e3) / 1e9, 1)})
+        kernels[name] = k
+    dom = max((k for k in kernels if "GBps" in kernels[k]), key=lambda k: kernels[k]["ms"])
+    kd = kernels[dom]
+    fp_peak = FP64_PEAK_TFLOPS if elem == 8 else FP32_PEAK_TFLOPS
+    frac_hbm = kd["GBps"] / peaks["hbm_gbs"]
+    frac_alu = kd["GFLOPps"] / (fp_peak * 1e3)
+    if frac_alu > frac_hbm:
+        roof = {"kernel": dom, "bound": "alu", "achieved": round(kd["GFLOPps"] / 1e3, 4), "peak": fp_peak,
+                "unit": "TFLOP/s", "frac": round(frac_alu, 4),
+                "peak_src": "nominal FP64 rate of GB300 (1.25 TFLOP/s)" if elem == 8 else "152 SMs x 128 FMA x 2.07 GHz",
+                "hbm_frac": round(frac_hbm, 4)}
+    else:
+        roof = {"kernel": dom, "bound": "hbm", "achieved": kd["GBps"], "peak": peaks["hbm_gbs"], "unit": "GB/s",
+                "frac": round(frac_hbm, 4), "peak_src": peaks["src"], "alu_frac": round(frac_alu, 4)}
+    roof["traffic"] = None
+    return kernels, roof
+
+
 def run_native(args):
     import numpy as np
     import torch
@@ -202,35 +237,7 @@ def run_native(args):
 
     # --- roofline of the dominant kernel class
     elem = 8 if prec == sq.SQ_FP64 else 4
-    alg = _algorithmic(N, elem, R)
-    n_iter = sum(iters)
-    eff = {"stencil_matvec": n_iter, "dht_x3_in": n_iter + 3 * args.steps, "dht_x2": 2 * (n_iter + 3 * args.steps),
-           "dht_x1_scale": n_iter + 3 * args.steps, "dht_x3_out": n_iter + 3 * args.steps}
-    peaks = _peaks()
-    kernels = {}
-    for name, (ms, cnt) in prof.items():
-        if name in alg and ms > 0:
-            b, f = alg[name]
-            ne = eff[name]
-            kernels[name] = {"ms": round(ms, 3), "launches": cnt, "share": round(ms / t_ms, 4),
-                             "GBps": round(b * ne / (ms / 1e3) / 1e9, 1),
-                             "GFLOPps": round(f * ne / (ms / 1e3) / 1e9, 1)}
-        elif ms > 0:
-            kernels[name] = {"ms": round(ms, 3), "launches": cnt, "share": round(ms / t_ms, 4)}
-    dom = max((k for k in kernels if k in alg), key=lambda k: kernels[k]["ms"])
-    kd = kernels[dom]
-    fp_peak = FP64_PEAK_TFLOPS if elem == 8 else FP32_PEAK_TFLOPS
-    frac_hbm = kd["GBps"] / peaks["hbm_gbs"]
-    frac_alu = kd["GFLOPps"] / (fp_peak * 1e3)
-    if frac_alu > frac_hbm:
-        roof = {"kernel": dom, "bound": "alu", "achieved": round(kd["GFLOPps"] / 1e3, 4), "peak": fp_peak,
-                "unit": "TFLOP/s", "frac": round(frac_alu, 4),
-                "peak_src": "nominal FP64 rate of GB300 (1.25 TFLOP/s)" if elem == 8 else "152 SMs x 128 FMA x 2.07 GHz",
-                "hbm_frac": round(frac_hbm, 4)}
-    else:
-        roof = {"kernel": dom, "bound": "hbm", "achieved": kd["GBps"], "peak": peaks["hbm_gbs"], "unit": "GB/s",
-                "frac": round(frac_hbm, 4), "peak_src": peaks["src"], "alu_frac": round(frac_alu, 4)}
-    roof["traffic"] = None
+    kernels, roof = kernel_table(sq.sq_profile_work(), prof, N, elem, R, t_ms)
     gpu_launches = int(sum(cnt for _, cnt in prof.values()))
 
     out = {"metric": METRIC, "value": round(value, 4), "unit": UNIT, "n_gpus": ws, "steps": args.steps,
@@ -274,6 +281,9 @@ def run_native(args):
                 sq.sq_pcg_solve(c, pcv, wv, i, tol, max_iter, pp, None, psis[i])
             torch.cuda.synchronize()
             ev0, ev1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            profile = label == "fp32_refine_rank8"
+            if profile:
+                sq.sq_profile_enable(True)
             ev0.record(stream)
             its = []
             nst = 2
@@ -287,6 +297,12 @@ def run_native(args):
             torch.cuda.synchronize()
             tv = ev0.elapsed_time(ev1)
             variants[label] = {"solves_per_s": round(3 * nst / (tv / 1e3), 3), "iters_mean": round(statistics.mean(its), 1)}
+            if profile:
+                pv = sq.sq_profile_read()
+                sq.sq_profile_enable(False)
+                kv, rv = kernel_table(sq.sq_profile_work(), pv, N, 4, rr, tv)
+                variants[label]["kernels"] = kv
+                out["roofline_fp32_refine"] = rv
             del pcv
         out["variants"] = variants
 

@@ -287,6 +287,12 @@ int sq_profile_enable(int enable);
  * of the class) and launches[k], then clears the record. Either array may be
  * NULL. */
 int sq_profile_read(double *ms, int64_t *launches, int max_classes);
+/* The launches of the last sq_profile_read that did work: per class, those
+ * lasting at least half of the class median (the others returned at
+ * entry because their solve had already stopped, e.g. the iterations queued
+ * behind the host's convergence check). Fills ms[k] and launches[k] as
+ * sq_profile_read does; returns the number of classes. */
+int sq_profile_work(double *ms, int64_t *launches, int max_classes);
 const char *sq_profile_class_name(int k);
 
 const char *sq_strerror(int status);

@@ -77,6 +77,8 @@ struct Prof {
   size_t used = 0;
 };
 Prof g_prof;
+double g_prof_work_ms[PC_COUNT] = {0};  // of the last sq_profile_read
+int64_t g_prof_work_n[PC_COUNT] = {0};
 
 const size_t kNoProf = (size_t)-1;
 
@@ -660,6 +662,7 @@ int sq_profile_enable(int enable) {
 int sq_profile_read(double *ms, int64_t *launches, int max_classes) {
   double acc[PC_COUNT] = {0};
   int64_t cnt[PC_COUNT] = {0};
+  std::vector<float> times[PC_COUNT];
   for (size_t k = 0; k < g_prof.cls.size(); ++k) {
     const size_t i = 2 * k;
     if (cudaEventSynchronize(g_prof.pool[i + 1]) != cudaSuccess) return -SQ_ECUDA;
@@ -667,6 +670,22 @@ int sq_profile_read(double *ms, int64_t *launches, int max_classes) {
     if (cudaEventElapsedTime(&t, g_prof.pool[i], g_prof.pool[i + 1]) != cudaSuccess) return -SQ_ECUDA;
     acc[g_prof.cls[k]] += t;
     cnt[g_prof.cls[k]] += 1;
+    times[g_prof.cls[k]].push_back(t);
+  }
+  // launches that did work: at least half of the class median (the
+  // others returned at entry because the solve had already stopped)
+  for (int k = 0; k < PC_COUNT; ++k) {
+    g_prof_work_ms[k] = 0.0;
+    g_prof_work_n[k] = 0;
+    if (times[k].empty()) continue;
+    std::vector<float> v = times[k];
+    std::nth_element(v.begin(), v.begin() + v.size() / 2, v.end());
+    const float thr = 0.5f * v[v.size() / 2];
+    for (float t : times[k])
+      if (t >= thr) {
+        g_prof_work_ms[k] += t;
+        g_prof_work_n[k] += 1;
+      }
   }
   for (int k = 0; k < PC_COUNT && k < max_classes; ++k) {
     if (ms) ms[k] = acc[k];
@@ -674,6 +693,14 @@ int sq_profile_read(double *ms, int64_t *launches, int max_classes) {
   }
   g_prof.used = 0;
   g_prof.cls.clear();
+  return PC_COUNT;
+}
+
+int sq_profile_work(double *ms, int64_t *launches, int max_classes) {
+  for (int k = 0; k < PC_COUNT && k < max_classes; ++k) {
+    if (ms) ms[k] = g_prof_work_ms[k];
+    if (launches) launches[k] = g_prof_work_n[k];
+  }
   return PC_COUNT;
 }
 

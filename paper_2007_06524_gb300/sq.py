@@ -72,6 +72,7 @@ def load_library():
         "sq_coeffs_upload": (i, [vp, vp, vp]),
         "sq_profile_enable": (i, [i]),
         "sq_profile_read": (i, [vp, vp, i]),
+        "sq_profile_work": (i, [vp, vp, i]),
         "sq_profile_class_name": (C.c_char_p, [i]),
         "sq_coeffs_shape": (i, [vp, p(i), p(i), p(i)]),
         "sq_coeffs_destroy": (None, [vp]),
@@ -226,6 +227,16 @@ def sq_profile_read() -> dict:
     k = lib.sq_profile_read(ms, cnt, 64)
     if k < 0:
         raise SqError(-k, "sq_profile_read")
+    return {lib.sq_profile_class_name(i).decode(): (ms[i], cnt[i]) for i in range(k)}
+
+
+def sq_profile_work() -> dict:
+    """{class name: (ms, launches)} of the launches that did work, from the last
+    sq_profile_read (launches of at least half of the class median)."""
+    lib = load_library()
+    ms = (C.c_double * 64)()
+    cnt = (C.c_int64 * 64)()
+    k = lib.sq_profile_work(ms, cnt, 64)
     return {lib.sq_profile_class_name(i).decode(): (ms[i], cnt[i]) for i in range(k)}
 
 
