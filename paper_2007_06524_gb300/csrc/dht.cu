@@ -90,8 +90,12 @@ __global__ void __launch_bounds__(kThreads) k_dht(DhtArgs<T> a) {
 // of shared memory at N = 256, P = 16: room for 5 blocks per SM; the register
 // cap keeps 3 of them resident (uncapped, pass C takes 128 registers).
 // Strided axes x1 (pass C, SCALE) and x2 (passes B, D).
+// Blocks per SM the register cap aims at: 3 (80 registers), 2 for the
+// radix-32 stages of N = 512 (up to 128 registers).
+constexpr int s2_min_blocks(int n) { return n > 256 ? 2 : 3; }
+
 template <int AXIS, int R0, int R1, int P, bool SCALE, int RR>
-__global__ void __launch_bounds__(kThreads, 3) k_dht_s2(DhtArgs<float> a) {
+__global__ void __launch_bounds__(kThreads, s2_min_blocks(R0 * R1)) k_dht_s2(DhtArgs<float> a) {
   using C = float2;
   if (a.check_done && *(volatile int *)&a.rb.st->done) return;
   extern __shared__ __align__(16) unsigned char smem_raw[];
@@ -153,7 +157,7 @@ static cudaError_t launch_s2_p(const DhtArgs<float> &a, int grid, cudaStream_t s
   if constexpr ((R0 * R1) % 16 == 0) {
     if (a.logP == 3) return launch_s2_rank<AXIS, R0, R1, 8, SCALE>(a, grid, s);
   }
-  if constexpr ((R0 * R1) % 32 == 0) {
+  if constexpr ((R0 * R1) % 32 == 0 && R0 * 16 <= kThreads) {
     if (a.logP == 4) return launch_s2_rank<AXIS, R0, R1, 16, SCALE>(a, grid, s);
   }
   return cudaErrorNotSupported;
@@ -170,13 +174,14 @@ static cudaError_t launch_strided_fast(const DhtArgs<float> &a, int grid, cudaSt
     case 96: return launch_s2_p<AXIS, 16, 6, SCALE>(a, grid, s);
     case 128: return launch_s2_p<AXIS, 16, 8, SCALE>(a, grid, s);
     case 256: return launch_s2_p<AXIS, 16, 16, SCALE>(a, grid, s);
+    case 512: return launch_s2_p<AXIS, 32, 16, SCALE>(a, grid, s);
     default: return cudaErrorNotSupported;
   }
 }
 
 // Contiguous axis x3 (passes A and E).
 template <int R0, int R1, int P, int LOADM, int STOREM>
-__global__ void __launch_bounds__(kThreads, 3) k_dht_s3(DhtArgs<float> a) {
+__global__ void __launch_bounds__(kThreads, s2_min_blocks(R0 * R1)) k_dht_s3(DhtArgs<float> a) {
   using C = float2;
   if (a.check_done && *(volatile int *)&a.rb.st->done) return;
   extern __shared__ __align__(16) unsigned char smem_raw[];
@@ -246,6 +251,7 @@ static cudaError_t launch_contig_fast(const DhtArgs<float> &a, int grid, cudaStr
     case 96: return launch_s3_p<16, 6, LOADM, STOREM>(a, grid, s);
     case 128: return launch_s3_p<16, 8, LOADM, STOREM>(a, grid, s);
     case 256: return launch_s3_p<16, 16, LOADM, STOREM>(a, grid, s);
+    case 512: return launch_s3_p<32, 16, LOADM, STOREM>(a, grid, s);
     default: return cudaErrorNotSupported;
   }
 }

@@ -86,6 +86,38 @@ __device__ __forceinline__ void dft(C (&u)[R]) {
     u[4] = csub(e[1], w1);
     u[2] = cadd(e[2], w2);
     u[5] = csub(e[2], w2);
+  } else if (R == 32) {
+    // 32 = 4 x 8: DFT8 over the stride-4 subsequences, twiddles W32^(n2 k1),
+    // DFT4 across them; output k1 + 8 k2. W32^j = (cos, -sin)(2 pi j / 32).
+    const T c1 = (T)0.98078528040323044913, s1 = (T)0.19509032201612826785;
+    const T c2 = (T)0.92387953251128675613, s2 = (T)0.38268343236508977173;
+    const T c3 = (T)0.83146961230254523708, s3 = (T)0.55557023301960222474;
+    const T h = (T)0.70710678118654752440;
+    // cos and sin of 2 pi j / 32 for j = 0..21 (the twiddle exponents n2 k1 < 22)
+    const T cs[22] = {(T)1, c1, c2, c3, h, s3, s2, s1, (T)0, -s1, -s2, -s3, -h, -c3, -c2, -c1, (T)-1, -c1, -c2, -c3, -h, -s3};
+    const T sn[22] = {(T)0, s1, s2, s3, h, c3, c2, c1, (T)1, c1, c2, c3, h, s3, s2, s1, (T)0, -s1, -s2, -s3, -h, -c3};
+    C y[4][8];
+#pragma unroll
+    for (int n2 = 0; n2 < 4; ++n2) {
+      C a[8];
+#pragma unroll
+      for (int m = 0; m < 8; ++m) a[m] = u[n2 + 4 * m];
+      dft<T, C, 8>(a);
+#pragma unroll
+      for (int k1 = 0; k1 < 8; ++k1) {
+        const int j = n2 * k1;
+        y[n2][k1] = (j == 0) ? a[k1] : cmul(a[k1], C{cs[j], -sn[j]});
+      }
+    }
+#pragma unroll
+    for (int k1 = 0; k1 < 8; ++k1) {
+      C b0 = y[0][k1], b1 = y[1][k1], b2 = y[2][k1], b3 = y[3][k1];
+      dft4<T, C>(b0, b1, b2, b3);
+      u[k1] = b0;
+      u[k1 + 8] = b1;
+      u[k1 + 16] = b2;
+      u[k1 + 24] = b3;
+    }
   } else if (R == 8) {
     const T h = (T)0.70710678118654752440;  // sqrt(2)/2
     C e0 = u[0], e1 = u[2], e2 = u[4], e3 = u[6];
@@ -350,7 +382,7 @@ __device__ __forceinline__ void dht_tile(const SpectralDev &sp, const DhtTile<T>
 namespace sq {
 
 // ----------------------------------------------------------------------------
-// Two-stage tiles (FP32): N = R0 * R1 with radices 3, 4, 6, 8, 16, P complex
+// Two-stage tiles (FP32): N = R0 * R1 with radices 3, 4, 6, 8, 16, 32, P complex
 // pencils per tile, all shape parameters compile-time so that the index
 // arithmetic folds to shifts and constants. One shared-memory round trip per
 // transform.

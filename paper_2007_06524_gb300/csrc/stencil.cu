@@ -101,7 +101,7 @@ static int resident_blocks(const void *kern, int threads, size_t smem) {
 }
 
 // Staged FP32 operator over one (tile, plane run) per block; see stencil_staged_run.
-__global__ void __launch_bounds__(kThreads) k_stencil_staged(CellsDev c, const float *__restrict__ x,
+__global__ void __launch_bounds__(kThreads, 3) k_stencil_staged(CellsDev c, const float *__restrict__ x,
                                                              float *__restrict__ y, RedBuf rb, int fin,
                                                              int check_done, int zc, int ntiles) {
   if (check_done && *(volatile int *)&rb.st->done) return;

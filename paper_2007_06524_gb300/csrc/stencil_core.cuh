@@ -230,13 +230,11 @@ constexpr int kSW = 40;             // slot row stride (floats): left halo at 3,
 constexpr int kSRows = 34;          // rows j2-1 .. j2+32
 constexpr int kSlot = kSRows * kSW;  // floats per slot
 
-__device__ __forceinline__ void cp_async16(float *dst, const float *src) {
-  const unsigned d = (unsigned)__cvta_generic_to_shared(dst);
-  asm volatile("cp.async.cg.shared.global [%0], [%1], 16;\n" ::"r"(d), "l"(src) : "memory");
+__device__ __forceinline__ void cp_async16(unsigned dst, const float *src) {
+  asm volatile("cp.async.cg.shared.global [%0], [%1], 16;\n" ::"r"(dst), "l"(src) : "memory");
 }
-__device__ __forceinline__ void cp_async4(float *dst, const float *src) {
-  const unsigned d = (unsigned)__cvta_generic_to_shared(dst);
-  asm volatile("cp.async.ca.shared.global [%0], [%1], 4;\n" ::"r"(d), "l"(src) : "memory");
+__device__ __forceinline__ void cp_async4(unsigned dst, const float *src) {
+  asm volatile("cp.async.ca.shared.global [%0], [%1], 4;\n" ::"r"(dst), "l"(src) : "memory");
 }
 __device__ __forceinline__ void cp_async_commit() { asm volatile("cp.async.commit_group;\n" ::: "memory"); }
 template <int PENDING>
@@ -244,25 +242,46 @@ __device__ __forceinline__ void cp_async_wait() {
   asm volatile("cp.async.wait_group %0;\n" ::"n"(PENDING) : "memory");
 }
 
-// Issues the copies of plane j1 (< N) of tile (j2_0, j3_0) with its halo into slot s.
-__device__ __forceinline__ void stage_plane(float *s, const float *__restrict__ x, int N, int j1, int j2_0, int j3_0,
-                                            int tid) {
-  const float *pl = x + (size_t)j1 * N * N;
-  {  // body: 32 rows x 8 chunks of 4 floats, one chunk per thread
+// A thread's share of copying one plane of the tile (j2_0, j3_0) with its
+// halo: a 16-byte body chunk, and for threads 0..15 a 16-byte halo-row chunk
+// or for threads 16..79 one halo-column float. The in-plane source offsets and
+// the slot offsets are fixed per thread and computed once.
+struct PlaneCopy {
+  int src0, dst0;  // body chunk: element offset in a plane, byte offset in a slot
+  int src1, dst1;  // halo element, or -1
+  int wide1;       // halo is a 16-byte chunk (1) or one float (0)
+  __device__ __forceinline__ void init(int N, int j2_0, int j3_0, int tid) {
     const int row = tid >> 3, ch = tid & 7;
-    cp_async16(s + (1 + row) * kSW + 4 + 4 * ch, pl + (size_t)(j2_0 + row) * N + j3_0 + 4 * ch);
+    src0 = (j2_0 + row) * N + j3_0 + 4 * ch;
+    dst0 = ((1 + row) * kSW + 4 + 4 * ch) * 4;
+    src1 = -1;
+    dst1 = 0;
+    wide1 = 0;
+    if (tid < 16) {  // halo rows j2_0 - 1 and j2_0 + 32
+      const int hr = tid >> 3;
+      const int gr = hr ? (j2_0 + 32 == N ? 0 : j2_0 + 32) : (j2_0 == 0 ? N - 1 : j2_0 - 1);
+      src1 = gr * N + j3_0 + 4 * ch;
+      dst1 = ((hr ? kSRows - 1 : 0) * kSW + 4 + 4 * ch) * 4;
+      wide1 = 1;
+    } else if (tid < 80) {  // halo columns j3_0 - 1 and j3_0 + 32
+      const int e = tid - 16, side = e >> 5, hrow = e & 31;
+      const int gc = side ? (j3_0 + 32 == N ? 0 : j3_0 + 32) : (j3_0 == 0 ? N - 1 : j3_0 - 1);
+      src1 = (j2_0 + hrow) * N + gc;
+      dst1 = ((1 + hrow) * kSW + (side ? 36 : 3)) * 4;
+    }
   }
-  if (tid < 16) {  // halo rows j2_0 - 1 and j2_0 + 32
-    const int hr = tid >> 3, ch = tid & 7;
-    const int gr = hr ? (j2_0 + 32 == N ? 0 : j2_0 + 32) : (j2_0 == 0 ? N - 1 : j2_0 - 1);
-    cp_async16(s + (hr ? kSRows - 1 : 0) * kSW + 4 + 4 * ch, pl + (size_t)gr * N + j3_0 + 4 * ch);
-  } else if (tid < 80) {  // halo columns j3_0 - 1 and j3_0 + 32
-    const int e = tid - 16, side = e >> 5, row = e & 31;
-    const int gc = side ? (j3_0 + 32 == N ? 0 : j3_0 + 32) : (j3_0 == 0 ? N - 1 : j3_0 - 1);
-    cp_async4(s + (1 + row) * kSW + (side ? 36 : 3), pl + (size_t)(j2_0 + row) * N + gc);
+  // Issues the copies of plane `pl` (the plane's first element) into the slot
+  // at shared address `slot`.
+  __device__ __forceinline__ void issue(const float *pl, unsigned slot) const {
+    cp_async16(slot + dst0, pl + src0);
+    if (src1 >= 0) {
+      if (wide1)
+        cp_async16(slot + dst1, pl + src1);
+      else
+        cp_async4(slot + dst1, pl + src1);
+    }
   }
-}
-
+};
 
 // Runs the staged FP32 operator y = A x (MATVEC) over planes [z0, z1) of the
 // 32 x 32 tile (j2_0, j3_0) and adds p.Ap to acc. Builds the block's pattern
@@ -275,11 +294,15 @@ __device__ __forceinline__ void stencil_staged_run(const CellsDev &c, const floa
   const int tid = threadIdx.x + 32 * threadIdx.y;
   const int N = c.N, n = c.n, L = c.L, LL = L * L;
   const int NN = N * N;
+  PlaneCopy cp;
+  cp.init(N, j2_0, j3_0, tid);
+  const unsigned ring_s = (unsigned)__cvta_generic_to_shared(ring);
+  const size_t plane = (size_t)NN;
   // prologue: planes z0 .. z0 + kStages - 2 (one commit group each, empty past z1)
 #pragma unroll
   for (int st = 0; st < kStages - 1; ++st) {
     const int j = z0 + st;
-    if (j <= z1) stage_plane(ring + st * kSlot, x, N, j == N ? 0 : j, j2_0, j3_0, tid);
+    if (j <= z1) cp.issue(x + (j == N ? 0 : (size_t)j * plane), ring_s + st * kSlot * 4);
     cp_async_commit();
   }
   __syncthreads();  // the caller's previous use of the tables is over
@@ -311,13 +334,15 @@ __device__ __forceinline__ void stencil_staged_run(const CellsDev &c, const floa
 #pragma unroll
   for (int r = 0; r < 4; ++r) xm[r] = x[(size_t)j1m0 * NN + row0 + r * N];
 
+  // ring slots of planes j1 (s0), j1 + 1 (s1) and j1 + kStages - 1 (sr, the slot of j1 - 1)
+  int s0 = 0, s1 = 1, sr = kStages - 1;
   for (int k = 0; z0 + k < z1; ++k) {
     const int j1 = z0 + k;
     cp_async_wait<kStages - 3>();  // this thread's copies of planes j1, j1 + 1 have landed
     __syncthreads();               // ... everyone's; and everyone is done with plane j1 - 1's slot
     {
       const int j = j1 + kStages - 1;
-      if (j <= z1) stage_plane(ring + ((k + kStages - 1) % kStages) * kSlot, x, N, j == N ? 0 : j, j2_0, j3_0, tid);
+      if (j <= z1) cp.issue(x + (size_t)(j == N ? 0 : j) * plane, ring_s + sr * kSlot * 4);
       cp_async_commit();
     }
     if (k > 0) {
@@ -329,8 +354,8 @@ __device__ __forceinline__ void stencil_staged_run(const CellsDev &c, const floa
         row_coeffs<float, 4>(tab, nc, np, t);
       }
     }
-    const float *S0 = ring + (k % kStages) * kSlot + (1 + 4 * ty) * kSW + 4 + tx;
-    const float *S1 = ring + ((k + 1) % kStages) * kSlot + (1 + 4 * ty) * kSW + 4 + tx;
+    const float *S0 = ring + s0 * kSlot + (1 + 4 * ty) * kSW + 4 + tx;
+    const float *S1 = ring + s1 * kSlot + (1 + 4 * ty) * kSW + 4 + tx;
     if (k == 0) {
 #pragma unroll
       for (int r = 0; r < 4; ++r) x0[r] = S0[r * kSW];
@@ -361,6 +386,9 @@ __device__ __forceinline__ void stencil_staged_run(const CellsDev &c, const floa
       xm[r] = x0[r];
       x0[r] = xp[r];
     }
+    s0 = s1;
+    s1 = (s1 + 1 == kStages) ? 0 : s1 + 1;
+    sr = (sr + 1 == kStages) ? 0 : sr + 1;
   }
   cp_async_wait<0>();
 }

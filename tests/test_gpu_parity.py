@@ -419,3 +419,45 @@ def test_solves_with_each_pass_implementation(sq, opt):
     assert i64["status"] == sq.SQ_OK and i64["relres_true"] <= 1e-12
     assert np.linalg.norm(_host(psi32) - ref) / np.linalg.norm(ref) <= 1e-6
     assert np.linalg.norm(_host(psi64) - ref) / np.linalg.norm(ref) <= 1e-9
+
+
+@pytest.mark.parametrize("N", [256, 512])
+@pytest.mark.parametrize("rank", [0, 8])
+def test_precond_cosine_modes_full_size(sq, N, rank):
+    """Closed form at full size: a cosine mode cos(2 pi k.j / N) is an
+    eigenvector of the preconditioner with eigenvalue G(k) (G is even in each
+    index), so a sum of modes comes back scaled mode by mode. FP32 and FP64,
+    both Hartley implementations (two-stage plans incl. radix 32 at N = 512)."""
+    import torch
+
+    ks = [(1, 0, 0), (3, 5, 7), (N // 2, N // 4, 1)]
+    amps = [1.0, -0.5, 0.25]
+    j = np.arange(N)
+    lam = 4 * np.sin(np.pi * j / N) ** 2
+    if rank:
+        t, w = sq.sq_precond_factors(sq.sq_precond_setup(N, rank), rank)
+    pc = sq.sq_precond_setup(N, rank)
+    r = torch.zeros((N, N, N), dtype=torch.float64, device="cuda")
+    zexp = torch.zeros_like(r)
+    jj = torch.arange(N, dtype=torch.float64, device="cuda")
+    for k, a in zip(ks, amps):
+        th = 2 * np.pi * (k[0] * jj[:, None, None] + k[1] * jj[None, :, None] + k[2] * jj[None, None, :]) / N
+        mode = a * torch.cos(th)
+        g = lam[k[0]] + lam[k[1]] + lam[k[2]]
+        G = 1.0 / g if rank == 0 else float(np.sum(np.asarray(w) * np.exp(-np.asarray(t) * g)))
+        r += mode
+        zexp += G * mode
+    for prec, dt, tol in ((sq.SQ_FP64, torch.float64, 1e-12), (sq.SQ_FP32_REFINE, torch.float32, 1e-5)):
+        w_ = sq.sq_workspace_create(N, prec)
+        for opt in (0, 1):
+            try:
+                sq.sq_set_option(sq.SQ_OPT_STRIDED_TWO_STAGE, opt)
+                z = torch.empty(N ** 3, dtype=dt, device="cuda")
+                (sq.sq_apply_precond if dt == torch.float64 else sq.sq_apply_precond_f32)(
+                    pc, w_, r.reshape(-1).to(dt).contiguous(), z)
+                torch.cuda.synchronize()
+            finally:
+                sq.sq_set_option(sq.SQ_OPT_STRIDED_TWO_STAGE, 1)
+            err = float((z.double().reshape(N, N, N) - zexp).abs().max() / zexp.abs().max())
+            assert err <= tol, (prec, opt, err)
+        del w_
