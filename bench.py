@@ -122,6 +122,13 @@ def _algorithmic(N, elem, rank_r):
     }
 
 
+# dram__bytes_read.sum + dram__bytes_write.sum of one launch (ncu --set full,
+# N = 256, rank 8): profiles/dht_x1_scale_fp64_n256.md and
+# profiles/dht_x3_pass_e_fp32_n256.md. Part of each kernel's writes is still in
+# L2 when it ends, so traffic can read below the algorithmic bytes.
+PROFILED_TRAFFIC = {("dht_x1_scale", 8): 134.34e6 + 72.89e6, ("dht_x3_out", 4): 201.37e6 + 76.47e6}
+
+
 def kernel_table(work, prof, N, elem, R, t_ms):
     """Per-class table and the dominant class's roofline from the library's
     event profile: achieved = algorithmic bytes (flops) per launch x launches
@@ -153,7 +160,12 @@ def kernel_table(work, prof, N, elem, R, t_ms):
     else:
         roof = {"kernel": dom, "bound": "hbm", "achieved": kd["GBps"], "peak": peaks["hbm_gbs"], "unit": "GB/s",
                 "frac": round(frac_hbm, 4), "peak_src": peaks["src"], "alu_frac": round(frac_alu, 4)}
-    roof["traffic"] = None
+    # DRAM bytes per launch (read + write) from the ncu capture of this kernel
+    # at N = 256 (profiles/); None where no capture of the current kernel exists
+    tr = PROFILED_TRAFFIC.get((dom, elem)) if N == 256 else None
+    roof["traffic"] = tr
+    if tr is not None:
+        roof["traffic_alg"] = alg[dom][0]
     return kernels, roof
 
 
