@@ -101,7 +101,8 @@ def test_operator_fp32(sq, L, n, seed):
 # staged kernel (8; used where N is a multiple of 32, else 4 rows): grids
 # ragged against the 32-wide j3 tiles and the 8*rows-high j2 tiles, and exact
 # multiples (every valid N, 2^a 3^b with b <= 1 and N >= 8, is divisible by 4).
-ROW_GRIDS = [(3, 4, 8), (3, 8, 9), (4, 8, 11), (12, 4, 12), (12, 8, 13), (6, 32, 14)]
+ROW_GRIDS = [(3, 4, 8), (3, 8, 9), (4, 8, 11), (12, 4, 12), (12, 8, 13), (6, 32, 14), (16, 2, 15), (8, 4, 16),
+             (4, 16, 17)]
 
 
 @pytest.mark.parametrize("rows", [1, 2, 4, 8])
