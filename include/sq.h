@@ -220,8 +220,8 @@ int sq_homogenized_matrix(const sq_coeffs *c, const double *psi0, const double *
  * BF16 weights and activations with FP32 accumulation on the tensor cores --
  * maps the coefficient field (+1 high / -1 low per grid voxel) to a first
  * guess of the three correctors psi_1..3 (scaled by out_scale). The guess is
- * passed to sq_pcg_solve as x0; the solve judges it by its residual. Grids
- * N = 32, 64, 96 or 128 (N % 32 == 0). */
+ * passed to sq_pcg_solve as x0; the solve keeps it only if it lowers the
+ * residual. Grids N = 32, 64, 96 or 128 (N % 32 == 0). */
 typedef struct sq_net sq_net;
 
 /* Creates the net for grid N with buffers for up to max_batch training

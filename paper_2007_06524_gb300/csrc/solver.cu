@@ -459,7 +459,7 @@ int solve_fp64(const sq_coeffs *c, const sq_precond *pc, sq_workspace *w, int di
   if (x0) {
     if (x0 != psi) SQ_CK(cudaMemcpyAsync(psi, x0, sizeof(double) * n3, cudaMemcpyDeviceToDevice, s));
     SQ_LAUNCH(PC_RESID, s, (launch_stencil<double, double>(cd, ST_RESID, dir, psi, r, rb, FIN_RESID, false, s)));
-    // the residual judges the guess: keep it only if ||b - A x0|| < ||b||
+    // the residual decides on the guess: keep it only if ||b - A x0|| < ||b||
     int st = read_scalars(h, rb.st, s);
     if (st != SQ_OK) return st;
     used_guess = h->rr < h->bb;
