@@ -97,6 +97,26 @@ class ClockSampler:
                 "samples": len(sm), "reasons": sorted(reasons)}
 
 
+def replica_seeds(rank, ws, count, offset=0):
+    """Realization seeds of one rank, disjoint across ranks for any count:
+    offset + rank + ws * k, k < count."""
+    return [offset + rank + ws * k for k in range(count)]
+
+
+def aggregate(t_ms, steps, ws, device):
+    """The slowest rank's timed region (max over ranks) and the whole-job
+    corrector solves/s: 3 solves per realization, `steps` realizations per
+    rank. Needs an initialised process group when ws > 1."""
+    if ws > 1:
+        import torch
+        import torch.distributed as dist
+
+        tt = torch.tensor([float(t_ms)], dtype=torch.float64, device=device)
+        dist.all_reduce(tt, op=dist.ReduceOp.MAX)
+        t_ms = float(tt.item())
+    return t_ms, 3 * steps * ws / (t_ms / 1e3)
+
+
 def _dist():
     ws = int(os.environ.get("WORLD_SIZE", "1"))
     rank = int(os.environ.get("RANK", "0"))
@@ -215,9 +235,9 @@ def run_native(args):
         A, E = sq.sq_homogenized_matrix(c, *psis)
         return infos, A
 
-    seed_base = 1000 * rank
-    for k in range(args.warmup):
-        step(10 ** 6 + seed_base + k)
+    seeds = replica_seeds(rank, ws, args.steps)
+    for sd in replica_seeds(rank, ws, args.warmup, offset=10 ** 6):
+        step(sd)
     torch.cuda.synchronize()
     if ws > 1:
         torch.distributed.barrier()
@@ -228,8 +248,8 @@ def run_native(args):
     torch.cuda.synchronize()
     e0.record(stream)
     all_infos, As = [], []
-    for k in range(args.steps):
-        infos, A = step(seed_base + k)
+    for sd in seeds:
+        infos, A = step(sd)
         all_infos += infos
         As.append(A)
     e1.record(stream)
@@ -237,13 +257,7 @@ def run_native(args):
     prof = sq.sq_profile_read()
     sq.sq_profile_enable(False)
     clocks = sampler.stop()
-    t_ms = e0.elapsed_time(e1)
-    if ws > 1:
-        tt = torch.tensor([t_ms], device="cuda")
-        torch.distributed.all_reduce(tt, op=torch.distributed.ReduceOp.MAX)
-        t_ms = float(tt.item())
-    solves = 3 * args.steps * ws
-    value = solves / (t_ms / 1e3)
+    t_ms, value = aggregate(e0.elapsed_time(e1), args.steps, ws, "cuda")
     iters = [i["iters"] for i in all_infos]
     ok = all(i["status"] == sq.SQ_OK and i["relres_true"] <= tol for i in all_infos)
 
@@ -259,7 +273,7 @@ def run_native(args):
            "config": {"workload": f"plain L={L} n={n} N={N}, Bernoulli(1/2) on {{1,100}}, 3 correctors + A_hom, "
                                   f"rank-{R} preconditioner, tol {tol:g}, {args.precision}",
                       "L": L, "n": n, "N": N, "rank": R, "tol": tol, "precision": args.precision,
-                      "seeds": f"{seed_base}..{seed_base + args.steps - 1} per rank",
+                      "seeds": f"rank + {ws} k, k < {args.steps}",
                       "l2": "inputs larger than L2 (4 working fields of %d MB each)" % (N ** 3 * elem // 2 ** 20),
                       "parallelism": "replicas" if ws > 1 else "single GPU"},
            "clocks": clocks, "gpu_launches": gpu_launches, "roofline": roof, "kernels": kernels,
@@ -293,14 +307,11 @@ def run_native(args):
                 sq.sq_pcg_solve(c, pcv, wv, i, tol, max_iter, pp, None, psis[i])
             torch.cuda.synchronize()
             ev0, ev1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
-            profile = label == "fp32_refine_rank8"
-            if profile:
-                sq.sq_profile_enable(True)
             ev0.record(stream)
             its = []
             nst = 2
             for k in range(nst):
-                sq.sq_coeffs_regenerate(c, seed_base + k, wl["p_hi"])
+                sq.sq_coeffs_regenerate(c, replica_seeds(rank, ws, nst)[k], wl["p_hi"])
                 for i in range(3):
                     inf = sq.sq_pcg_solve(c, pcv, wv, i, tol, max_iter, pp, None, psis[i])
                     its.append(inf["iters"])
@@ -309,10 +320,20 @@ def run_native(args):
             torch.cuda.synchronize()
             tv = ev0.elapsed_time(ev1)
             variants[label] = {"solves_per_s": round(3 * nst / (tv / 1e3), 3), "iters_mean": round(statistics.mean(its), 1)}
-            if profile:
+            if label == "fp32_refine_rank8":
+                # per-kernel table from one more, profiled realization (the
+                # event pairs around every launch would slow the timed steps)
+                sq.sq_coeffs_regenerate(c, replica_seeds(rank, ws, 1, offset=10 ** 7)[0], wl["p_hi"])
+                sq.sq_profile_enable(True)
+                evp0, evp1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+                evp0.record(stream)
+                for i in range(3):
+                    sq.sq_pcg_solve(c, pcv, wv, i, tol, max_iter, pp, None, psis[i])
+                evp1.record(stream)
+                torch.cuda.synchronize()
                 pv = sq.sq_profile_read()
                 sq.sq_profile_enable(False)
-                kv, rv = kernel_table(sq.sq_profile_work(), pv, N, 4, rr, tv)
+                kv, rv = kernel_table(sq.sq_profile_work(), pv, N, 4, rr, evp0.elapsed_time(evp1))
                 variants[label]["kernels"] = kv
                 out["roofline_fp32_refine"] = rv
             del pcv
