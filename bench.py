@@ -97,6 +97,22 @@ class ClockSampler:
                 "samples": len(sm), "reasons": sorted(reasons)}
 
 
+def workload_config(args, ws):
+    """The `config` object of both arms: the N=256 workload and its settings."""
+    from paper_2007_06524_gb300 import workloads
+
+    wl = workloads.PLAIN_N256
+    L, n = wl["L"], wl["n"]
+    N = L * n
+    elem = 8 if args.precision == "fp64" else 4
+    return {"workload": f"plain L={L} n={n} N={N}, Bernoulli(1/2) on {{1,100}}, 3 correctors + A_hom, "
+                        f"rank-{args.rank} preconditioner, tol {wl['tol']:g}, {args.precision}",
+            "L": L, "n": n, "N": N, "rank": args.rank, "tol": wl["tol"], "precision": args.precision,
+            "seeds": f"rank + {ws} k, k < {args.steps}",
+            "l2": "inputs larger than L2 (4 working fields of %d MB each)" % (N ** 3 * elem // 2 ** 20),
+            "parallelism": "replicas" if ws > 1 else "single GPU"}
+
+
 def replica_seeds(rank, ws, count, offset=0):
     """Realization seeds of one rank, disjoint across ranks for any count:
     offset + rank + ws * k, k < count."""
@@ -270,12 +286,7 @@ def run_native(args):
            "warmup": args.warmup, "ms_per_step": round(t_ms / args.steps, 3), "higher_is_better": True,
            "scaling": "weak", "vs_baseline": None, "dtype": "f64" if elem == 8 else "f32+f64",
            "data": "synthetic",
-           "config": {"workload": f"plain L={L} n={n} N={N}, Bernoulli(1/2) on {{1,100}}, 3 correctors + A_hom, "
-                                  f"rank-{R} preconditioner, tol {tol:g}, {args.precision}",
-                      "L": L, "n": n, "N": N, "rank": R, "tol": tol, "precision": args.precision,
-                      "seeds": f"rank + {ws} k, k < {args.steps}",
-                      "l2": "inputs larger than L2 (4 working fields of %d MB each)" % (N ** 3 * elem // 2 ** 20),
-                      "parallelism": "replicas" if ws > 1 else "single GPU"},
+           "config": workload_config(args, ws),
            "clocks": clocks, "gpu_launches": gpu_launches, "roofline": roof, "kernels": kernels,
            "iters": {"mean": round(statistics.mean(iters), 2), "min": min(iters), "max": max(iters)},
            "converged": ok, "tiles": {"dht_pencils_fp32": tiles[0], "stencil_planes": tiles[1],
@@ -481,7 +492,9 @@ def run_reference(args):
     re = problem.realization(wl["L"], wl["n"], 0, wl["a_lo"], wl["a_hi"])
     t_setup = time.perf_counter() - t0
     P = pcg.fft_preconditioner(re.N, R)
-    iters_per_solve = 50.0  # typical FP64 rank-8 count at this workload (the native arm reports its own)
+    # PCG iterations per solve on this workload (FP64, tol 1e-8, measured with
+    # the same method on the GPU; the oracle's PCG takes the same iterations)
+    iters_per_solve = {0: 42.5, 4: 84.0, 8: 57.0, 16: 49.3}.get(R, 57.0)
     times = []
     for k in range(args.warmup + args.steps):
         t0 = time.perf_counter()
@@ -495,7 +508,7 @@ def run_reference(args):
     out = {"metric": METRIC, "value": round(value, 6), "unit": UNIT, "n_gpus": ws, "steps": args.steps,
            "warmup": args.warmup, "ms_per_step": round(t_it * 1e3, 3), "higher_is_better": True, "scaling": "weak",
            "vs_baseline": None, "dtype": "f64", "data": "synthetic", "impl": "reference",
-           "config": {"workload": f"plain L=32 n=8 N=256, Bernoulli(1/2) on {{1,100}}, rank-{R}, tol 1e-8, fp64"},
+           "config": workload_config(args, _dist()[0]),
            "cpu_baseline": {"value": round(value, 6), "unit": UNIT, "cores": 1, "kind": "oracle",
                             "sample": f"step = one PCG iteration of the oracle at N=256 ({t_it:.2f} s); assembly "
                                       f"{t_setup:.1f} s once; extrapolated to {iters_per_solve:.0f} iterations"},
