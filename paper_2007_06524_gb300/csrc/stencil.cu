@@ -13,6 +13,8 @@
 // and the diagonal; no N^3 coefficient field exists.
 //
 // RHS (Eq. 8 in grid units): b_dir(j) = a_dir(j) - a_dir(j - e_dir).
+#include <mutex>
+
 #include "stencil_core.cuh"
 
 namespace sq {
@@ -79,24 +81,30 @@ __global__ void __launch_bounds__(kThreads) k_stencil(CellsDev c, int dir, const
 }
 
 // Blocks that fit on the device at once for one kernel (cached per kernel and
-// device); 0 on error.
+// device; the cache is guarded for concurrent host threads); 0 on error.
 static int resident_blocks(const void *kern, int threads, size_t smem) {
   int dev = 0;
   if (cudaGetDevice(&dev) != cudaSuccess) return 0;
   struct Entry {
     const void *k;
     int dev;
+    size_t smem;
     int blocks;
   };
   static Entry cache[64];
   static int used = 0;
-  for (int i = 0; i < used; ++i)
-    if (cache[i].k == kern && cache[i].dev == dev) return cache[i].blocks;
+  static std::mutex mu;
+  {
+    std::lock_guard<std::mutex> lock(mu);
+    for (int i = 0; i < used; ++i)
+      if (cache[i].k == kern && cache[i].dev == dev && cache[i].smem == smem) return cache[i].blocks;
+  }
   int per_sm = 0, sms = 0;
   if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kern, threads, smem) != cudaSuccess) return 0;
   if (cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess) return 0;
   const int blocks = per_sm * sms;
-  if (used < 64) cache[used++] = Entry{kern, dev, blocks};
+  std::lock_guard<std::mutex> lock(mu);
+  if (used < 64) cache[used++] = Entry{kern, dev, smem, blocks};
   return blocks;
 }
 
