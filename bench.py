@@ -354,6 +354,7 @@ def run_native(args):
         out.setdefault("variants", {})["batch_768_mixed"] = run_batch(sq, torch, stream)
         out["variants"]["warm_start_n64"] = run_warm_start(sq, torch)
         out["variants"]["refine_n512"] = run_refine_n512(sq, torch, stream)
+        out["variants"]["ensemble"] = run_ensemble(sq, torch)
 
     if rank == 0 and not args.no_cpu_baseline and ws == 1:
         out["cpu_baseline"] = cpu_baseline(statistics.mean(iters), R)
@@ -415,6 +416,31 @@ def run_warm_start(sq, torch, nseeds=64):
     res = {"eval_seeds": f"{seeds[0]}..{seeds[-1]}"}
     res["fp32_refine"] = warmstart.evaluate(torch, wl, net, seeds, sq.SQ_FP32_REFINE)
     res["fp64"] = warmstart.evaluate(torch, wl, net, seeds[:16], sq.SQ_FP64)
+    return res
+
+
+def run_ensemble(sq, torch, M=32):
+    """Ensemble statistics of A_hom (Sec. 5): M realizations at each period
+    L in {8, 16, 32} (n = 4, N = 32..128), Bernoulli(1/2) on {1,10}, exact
+    preconditioner, FP32 + FP64 refinement to 1e-8; the diagonal spread
+    sigma^M_L and its fitted exponent in L (theory: -3/2, Eq. var)."""
+    import numpy as np
+
+    res, Ls, sig = {}, [8, 16, 32], []
+    for L in Ls:
+        seeds = list(range(5000, 5000 + M))
+        sq.sq_ensemble_ahom(L, 4, seeds[:2], 0.5, 1.0, 10.0)  # warm-up (graph capture, first touch)
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        r = sq.sq_ensemble_ahom(L, 4, seeds, 0.5, 1.0, 10.0, tol=1e-8)
+        dt = time.perf_counter() - t0
+        s = float(np.mean(np.diag(r["sigma"])))
+        sig.append(s)
+        res[f"L{L}"] = {"realizations_per_s": round(M / dt, 2), "seconds": round(dt, 3),
+                        "mean_diag": round(float(np.mean(np.diag(r["mean"]))), 6), "sigma_diag": round(s, 6),
+                        "converged": r["status"] == sq.SQ_OK}
+    res["sigma_exponent"] = round(float(np.polyfit(np.log(Ls), np.log(sig), 1)[0]), 3)
+    res["M"] = M
     return res
 
 

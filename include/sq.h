@@ -215,6 +215,24 @@ int sq_pcg_solve_batched(sq_batch *b, double tol, int max_iter, sq_solve_info *i
 int sq_homogenized_matrix(const sq_coeffs *c, const double *psi0, const double *psi1,
                           const double *psi2, double *A_hom, double *A_energy, sq_stream_t stream);
 
+/* Ensemble statistics of the homogenized matrix (Sec. 5, Eq. A_hom_Empir and
+ * the sample standard deviation sigma^M_L estimating Eq. var): for the M >= 2
+ * realizations seeds[0..M) of the L^3 checkerboard (cells as sq_build_coeffs
+ * with p_hi, a_lo, a_hi), solves the three correctors of each with the batched
+ * solver (FP32 PCG in FP64 refinement to `tol`, preconditioner `rank`, at most
+ * max_iter inner iterations), takes the edge-form A_hom of each, and returns
+ * on the host, entry-wise (row-major 3 x 3):
+ *   mean[9]  = (1/M) sum_m A^(m),
+ *   sigma[9] = sqrt( sum_m (A^(m) - mean)^2 / (M - 1) ),
+ * and, where not NULL, per_real[9 M] (realization m at 9 m) and iters[3 M]
+ * (inner iterations of corrector i of realization m at 3 m + i).
+ * Realizations are solved `chunk` at a time (0 = all at once; device memory
+ * about 84 N^3 bytes per realization of a chunk). Returns SQ_ENOCONV (with
+ * all outputs filled) if a solve missed the tolerance. Synchronous. */
+int sq_ensemble_ahom(int L, int n, const uint64_t *seeds, int M, double p_hi, double a_lo, double a_hi,
+                     int rank, double tol, int max_iter, int chunk, double *mean, double *sigma,
+                     double *per_real, int *iters, sq_stream_t stream);
+
 /* Learned warm start (an addition to the paper's method): a periodic 3D
  * convolutional net -- 6 layers of 3x3x3 convolutions, 32 channels, GELU,
  * BF16 weights and activations with FP32 accumulation on the tensor cores --

@@ -101,6 +101,7 @@ def load_library():
         "sq_batch_destroy": (None, [vp]),
         "sq_pcg_solve_batched": (i, [vp, d, i, p(SolveInfo), vp]),
         "sq_set_tiles": (i, [p(TileConfig), i]),
+        "sq_ensemble_ahom": (i, [i, i, vp, i, d, d, d, i, d, i, i, vp, vp, vp, vp, vp]),
         "sq_set_option": (i, [i, i]),
     }
     for name, (res, args) in sig.items():
@@ -409,6 +410,26 @@ def sq_set_tiles(tiles):
     tl = list(tiles)
     arr = _tile_array(tl)
     _check(load_library().sq_set_tiles(arr if tl else None, len(tl)), "sq_set_tiles")
+
+
+def sq_ensemble_ahom(L, n, seeds, p_hi, a_lo, a_hi, rank=0, tol=1e-8, max_iter=2000, chunk=0, stream=None):
+    """Empirical average and sample standard deviation of the edge-form A_hom
+    over the realizations `seeds` (M >= 2). Returns a dict with mean (3x3),
+    sigma (3x3), per_realization (M x 3 x 3), iters (M x 3) and status
+    (SQ_OK or SQ_ENOCONV; other errors raise)."""
+    sd = np.ascontiguousarray([int(x) & (2 ** 64 - 1) for x in seeds], dtype=np.uint64)
+    M = sd.size
+    mean, sigma = np.zeros(9), np.zeros(9)
+    per = np.zeros(9 * max(M, 1))
+    its = np.zeros(3 * max(M, 1), dtype=np.int32)
+    st = load_library().sq_ensemble_ahom(int(L), int(n), sd.ctypes.data_as(C.c_void_p), int(M), float(p_hi),
+                                         float(a_lo), float(a_hi), int(rank), float(tol), int(max_iter), int(chunk),
+                                         mean.ctypes.data_as(C.c_void_p), sigma.ctypes.data_as(C.c_void_p),
+                                         per.ctypes.data_as(C.c_void_p), its.ctypes.data_as(C.c_void_p),
+                                         _stream(stream))
+    _check(st, "sq_ensemble_ahom", allow=(SQ_ENOCONV,))
+    return {"mean": mean.reshape(3, 3), "sigma": sigma.reshape(3, 3), "per_realization": per[:9 * M].reshape(M, 3, 3),
+            "iters": its[:3 * M].reshape(M, 3), "status": st}
 
 
 def sq_set_option(key, value):
