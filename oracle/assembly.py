@@ -44,14 +44,36 @@ def voxel_field(cellval: np.ndarray, n: int) -> np.ndarray:
     return np.repeat(np.repeat(np.repeat(cellval, n, axis=0), n, axis=1), n, axis=2)
 
 
+def inclusion_field(phase: np.ndarray, n: int, sub: int, a_lo: float, a_hi: float) -> np.ndarray:
+    """Voxel coefficients with sub-cell inclusions (Sec. 3.1): every unit cell
+    holds a centred cube S_s of side sub grid intervals (sub = 2 alpha n); a
+    voxel is a_hi when its cell is high and it lies in that cube, else a_lo
+    (a = lambda + beta * indicator, lambda = a_lo). sub = n is the checkerboard."""
+    if sub < 1 or sub > n or (n - sub) % 2:
+        raise ValueError("sub must be in [1, n] with n - sub even (a centred cube)")
+    lo = (n - sub) // 2
+    u = np.arange(n)
+    inside1 = (u >= lo) & (u < lo + sub)
+    inside = inside1[:, None, None] & inside1[None, :, None] & inside1[None, None, :]
+    hi_cell = np.repeat(np.repeat(np.repeat(phase.astype(bool), n, 0), n, 1), n, 2)
+    L = phase.shape[0]
+    inside_all = np.tile(inside, (L, L, L))
+    return np.where(hi_cell & inside_all, float(a_hi), float(a_lo))
+
+
 def edge_coefficients(cellval: np.ndarray, n: int) -> np.ndarray:
-    """a_d(j) for d = 0, 1, 2 (axes x1, x2, x3), shape (3, N, N, N).
+    """a_d(j) for d = 0, 1, 2 (axes x1, x2, x3), shape (3, N, N, N), of the
+    checkerboard with cell values cellval; see edge_coefficients_voxels."""
+    return edge_coefficients_voxels(voxel_field(cellval, n))
+
+
+def edge_coefficients_voxels(V: np.ndarray) -> np.ndarray:
+    """a_d(j) for d = 0, 1, 2 (axes x1, x2, x3) of the voxel field V, shape (3, N, N, N).
 
     a_d(j) is the mean of the four voxels that share the edge j -> j + e_d:
     voxel index j along d, and j_t - 1 or j_t along each transverse axis t.
     np.roll(V, 1, axis=t)[j] == V[j - e_t] (periodic).
     """
-    V = voxel_field(cellval, n)
     out = np.empty((3,) + V.shape)
     for d in range(3):
         t1, t2 = [t for t in range(3) if t != d]

@@ -27,11 +27,16 @@ class Realization:
 
 
 def realization(L: int, n: int, seed: int, a_lo: float, a_hi: float, p_hi: float = 0.5,
-                phase: np.ndarray | None = None) -> Realization:
+                phase: np.ndarray | None = None, sub: int | None = None) -> Realization:
+    """sub: side of the centred inclusion cube per cell in grid intervals
+    (sub-cell inclusions, Sec. 3.1); None or n = the full-cell checkerboard."""
     if phase is None:
         phase = rng.cell_phases_vec(L, seed, p_hi) if L > 16 else rng.cell_phases(L, seed, p_hi)
     cellval = rng.cell_values(phase, a_lo, a_hi)
-    a_edges = assembly.edge_coefficients(cellval, n)
+    if sub is None or sub == n:
+        a_edges = assembly.edge_coefficients(cellval, n)
+    else:
+        a_edges = assembly.edge_coefficients_voxels(assembly.inclusion_field(phase, n, sub, a_lo, a_hi))
     A = assembly.stiffness_edges(a_edges)
     b = [assembly.rhs(a_edges, i) for i in range(3)]
     return Realization(L, n, L * n, phase, cellval, a_edges, A, b)
