@@ -105,6 +105,14 @@ int sq_coeffs_upload(sq_coeffs *c, const uint8_t *host_phase, sq_stream_t stream
 int sq_coeffs_cells(const sq_coeffs *c, uint8_t *host_phase, int64_t *n_hi);
 /* Grid parameters of a handle (any output may be NULL). */
 int sq_coeffs_shape(const sq_coeffs *c, int *L, int *n, int *N);
+/* Sub-cell inclusions (Sec. 3.1): every unit cell holds a centred cube of
+ * side `sub` grid intervals (sub = 2 alpha n, alpha the paper's overlap
+ * factor); a voxel takes a_hi only if its cell is high and it lies in that
+ * cube, a_lo everywhere else. sub = n (the default) is the full-cell
+ * checkerboard. Requires 1 <= sub <= n with n - sub even; SQ_EINVAL otherwise.
+ * Applies to every later use of c (solves, batches created afterwards,
+ * A_hom, the warm-start features). */
+int sq_coeffs_set_subcell(sq_coeffs *c, int sub);
 void sq_coeffs_destroy(sq_coeffs *c);
 
 /* Preconditioner (Sec. 4.1-4.2): pseudo-inverse of the periodic Laplacian,

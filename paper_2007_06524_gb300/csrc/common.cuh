@@ -268,6 +268,10 @@ struct CellsDev {
   const uint8_t *phase;  // L^3 cell phases
   int L, n, N;
   double a_lo, a_hi;
+  // Sub-cell inclusions (Sec. 3.1): a voxel at cell-local index u (per axis)
+  // takes its cell's value only if sub_lo <= u < sub_hi on every axis, else
+  // a_lo. The default is the whole cell (the checkerboard).
+  int sub_lo = 0, sub_hi = 1 << 30;
   // An edge touches 4 voxels, k of them high: a_edge = (k a_hi + (4-k) a_lo)/4.
   // A node's six edges touch 24 voxel slots, K of them high: the diagonal is
   // (K a_hi + (24-K) a_lo)/4. Both tables are filled on the host (fill_tables).

@@ -28,6 +28,7 @@ using namespace sq;
 struct sq_coeffs {
   int L, n, N;
   double a_lo, a_hi;
+  int sub_lo = 0, sub_hi = 1 << 30;  // inclusion cube of every cell (default: the whole cell)
   uint8_t *d_phase;
   cudaStream_t stream;
   Scalars *d_st;       // reduction scalars for operator / A_hom calls
@@ -124,6 +125,8 @@ CellsDev cells_dev(const sq_coeffs *c) {
   d.N = c->N;
   d.a_lo = c->a_lo;
   d.a_hi = c->a_hi;
+  d.sub_lo = c->sub_lo;
+  d.sub_hi = c->sub_hi;
   fill_tables(d);
   return d;
 }
@@ -705,6 +708,18 @@ int sq_profile_work(double *ms, int64_t *launches, int max_classes) {
 }
 
 const char *sq_profile_class_name(int k) { return (k >= 0 && k < PC_COUNT) ? kProfNames[k] : "?"; }
+
+int sq_coeffs_set_subcell(sq_coeffs *c, int sub) {
+  if (!c || sub < 1 || sub > c->n || (c->n - sub) % 2 != 0) return SQ_EINVAL;
+  if (sub == c->n) {
+    c->sub_lo = 0;
+    c->sub_hi = 1 << 30;
+  } else {
+    c->sub_lo = (c->n - sub) / 2;
+    c->sub_hi = c->sub_lo + sub;
+  }
+  return SQ_OK;
+}
 
 int sq_coeffs_cells(const sq_coeffs *c, uint8_t *host_phase, int64_t *n_hi) {
   if (!c) return SQ_EINVAL;

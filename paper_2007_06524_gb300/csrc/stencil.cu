@@ -263,11 +263,16 @@ __global__ void __launch_bounds__(kThreads) k_ahom(CellsDev c, const double *__r
     const int c3a = j3 / n, c3b = j3m / n, c2a = j2 / n, c2b = j2m / n;
     const int LL = L * L;
     const int o00 = c2a * L + c3a, o01 = c2a * L + c3b, o10 = c2b * L + c3a, o11 = c2b * L + c3b;
+    // sub-cell inclusions: which of the four in-plane voxels may be high (load4's bit order)
+    const bool i2a = in_sub(c, j2 - c2a * n), i2b = in_sub(c, j2m - c2b * n);
+    const bool i3a = in_sub(c, j3 - c3a * n), i3b = in_sub(c, j3m - c3b * n);
+    const unsigned m23 = (i2a && i3a ? 1u : 0u) | (i2a && i3b ? 2u : 0u) | (i2b && i3a ? 4u : 0u) | (i2b && i3b ? 8u : 0u);
     const double *ps[3] = {p0, p1, p2};
     for (int j1 = z0; j1 < z1; ++j1) {
       const int j1m = (j1 == 0) ? N - 1 : j1 - 1, j1p = (j1 == N - 1) ? 0 : j1 + 1;
-      const unsigned m = load4(c.phase, j1 / n, LL, o00, o01, o10, o11) |
-                         (load4(c.phase, j1m / n, LL, o00, o01, o10, o11) << 4);
+      const unsigned pm0 = in_sub(c, j1 - (j1 / n) * n) ? m23 : 0u, pm1 = in_sub(c, j1m - (j1m / n) * n) ? m23 : 0u;
+      const unsigned m = (load4(c.phase, j1 / n, LL, o00, o01, o10, o11) & pm0) |
+                         ((load4(c.phase, j1m / n, LL, o00, o01, o10, o11) & pm1) << 4);
       const double a[3] = {tab[m][0], tab[m][2], tab[m][4]};
       const size_t o = (size_t)j1 * NN + (size_t)j2 * N + j3;
       const size_t on[3] = {(size_t)j1p * NN + (size_t)j2 * N + j3, (size_t)j1 * NN + (size_t)j2p * N + j3,

@@ -37,6 +37,21 @@ __device__ __forceinline__ unsigned load4(const uint8_t *__restrict__ phase, int
   return (ph[o00] ? 1u : 0u) | (ph[o01] ? 2u : 0u) | (ph[o10] ? 4u : 0u) | (ph[o11] ? 8u : 0u);
 }
 
+// Sub-cell inclusions: can the voxel at cell-local index u (one axis) be high?
+__device__ __forceinline__ bool in_sub(const CellsDev &c, int u) { return u >= c.sub_lo && u < c.sub_hi; }
+// Node patterns change between planes j1 - 1 and j1 where a voxel plane
+// crosses a cell face (cell position 0, 1) or a sub-cell face (sub_lo,
+// sub_lo + 1, sub_hi, sub_hi + 1); for whole cells only at 0 and 1.
+__device__ __forceinline__ bool pattern_changes(const CellsDev &c, int cpos) {
+  return cpos <= 1 || cpos == c.sub_lo || cpos == c.sub_lo + 1 || cpos == c.sub_hi || cpos == c.sub_hi + 1;
+}
+// Plane masks of a node at cell position cpos: the voxels of plane j1 (low
+// nibble) and of plane j1 - 1 (high nibble) may be high.
+__device__ __forceinline__ void plane_masks(const CellsDev &c, int cpos, unsigned &pm0, unsigned &pm1) {
+  pm0 = in_sub(c, cpos) ? 0xFu : 0u;
+  pm1 = in_sub(c, cpos == 0 ? c.n - 1 : cpos - 1) ? 0xFu : 0u;
+}
+
 // ------------------------------------------------------------ stencil kernel
 // A thread owns RPT consecutive node rows j2b .. j2b+RPT-1 of column j3 and
 // marches along j1 over [z0, z1). Per row it keeps x(j1-1), x(j1) in
@@ -55,23 +70,25 @@ __device__ __forceinline__ unsigned load4(const uint8_t *__restrict__ phase, int
 // Pattern nibbles of the RPT rows for cell plane c1: bit 0 / 1 = the row's
 // own cell at j3 / j3-1, bit 2 / 3 = the cell of row j2-1 at j3 / j3-1.
 // crow[q] = (cell of row j2b-1+q) * L.
+// mq[q]: in-plane inclusion mask of row q (bits 0 / 1: the voxel at j3 / j3-1
+// of that row may be high).
 template <int RPT>
 __device__ __forceinline__ void row_nibbles(const uint8_t *__restrict__ phase, int c1, int LL, const int (&crow)[RPT + 1],
-                                            int c3a, int c3b, unsigned (&nb)[RPT]) {
+                                            int c3a, int c3b, const unsigned (&mq)[RPT + 1], unsigned (&nb)[RPT]) {
   const uint8_t *ph = phase + (size_t)c1 * LL;
   unsigned b[RPT + 1];
 #pragma unroll
-  for (int q = 0; q <= RPT; ++q) b[q] = (ph[crow[q] + c3a] ? 1u : 0u) | (ph[crow[q] + c3b] ? 2u : 0u);
+  for (int q = 0; q <= RPT; ++q) b[q] = ((ph[crow[q] + c3a] ? 1u : 0u) | (ph[crow[q] + c3b] ? 2u : 0u)) & mq[q];
 #pragma unroll
   for (int r = 0; r < RPT; ++r) nb[r] = b[r + 1] | (b[r] << 2);
 }
 
 template <typename Ti, int RPT>
 __device__ __forceinline__ void row_coeffs(const Ti (*tab)[kTabStride], const unsigned (&nc)[RPT],
-                                           const unsigned (&np)[RPT], Ti (&t)[RPT][7]) {
+                                           const unsigned (&np)[RPT], unsigned pm0, unsigned pm1, Ti (&t)[RPT][7]) {
 #pragma unroll
   for (int r = 0; r < RPT; ++r) {
-    const Ti *tr = tab[nc[r] | (np[r] << 4)];
+    const Ti *tr = tab[(nc[r] & pm0) | ((np[r] & pm1) << 4)];
 #pragma unroll
     for (int k = 0; k < 7; ++k) t[r][k] = tr[k];
   }
@@ -93,10 +110,13 @@ __device__ __forceinline__ void stencil_rows(const CellsDev &c, int dir, const T
   const int c3a = cellof[j3], c3b = cellof[j3m];
   const int d3p = j3p - j3, d3m = j3m - j3;
   int crow[RPT + 1];
+  unsigned mq[RPT + 1];  // in-plane inclusion masks (see row_nibbles)
+  const unsigned m3 = (in_sub(c, j3 - c3a * n) ? 1u : 0u) | (in_sub(c, j3m - c3b * n) ? 2u : 0u);
 #pragma unroll
   for (int q = 0; q <= RPT; ++q) {
     const int j2 = (j2b - 1 + q < 0) ? N - 1 : j2b - 1 + q;  // rows j2b .. j2b+RPT-1 are < N
     crow[q] = cellof[j2] * L;
+    mq[q] = in_sub(c, j2 - cellof[j2] * n) ? m3 : 0u;
   }
   const int row0 = j2b * N + j3;
   const int up = ((j2b == 0) ? N - 1 : j2b - 1) * N + j3 - row0;          // row j2b - 1
@@ -104,16 +124,17 @@ __device__ __forceinline__ void stencil_rows(const CellsDev &c, int dir, const T
 
   const int j1m0 = (z0 == 0) ? N - 1 : z0 - 1;
   int cpos = z0 - cellof[z0] * n;  // position of plane z0 within its cell
-  unsigned np[RPT], nc[RPT];
-  row_nibbles<RPT>(c.phase, cellof[j1m0], LL, crow, c3a, c3b, np);
+  unsigned np[RPT], nc[RPT], pm0, pm1;
+  row_nibbles<RPT>(c.phase, cellof[j1m0], LL, crow, c3a, c3b, mq, np);
   if (cpos == 0) {
-    row_nibbles<RPT>(c.phase, cellof[z0], LL, crow, c3a, c3b, nc);
+    row_nibbles<RPT>(c.phase, cellof[z0], LL, crow, c3a, c3b, mq, nc);
   } else {
 #pragma unroll
     for (int r = 0; r < RPT; ++r) nc[r] = np[r];
   }
+  plane_masks(c, cpos, pm0, pm1);
   Ti t[RPT][7];
-  row_coeffs<Ti, RPT>(tab, nc, np, t);
+  row_coeffs<Ti, RPT>(tab, nc, np, pm0, pm1, t);
 
   Ti xm[RPT], x0[RPT], ahead[RPT][kAhead];  // ahead[r][u] = x(jb + 1 + u) of row r
 #pragma unroll
@@ -145,11 +166,14 @@ __device__ __forceinline__ void stencil_rows(const CellsDev &c, int dir, const T
       if (j1 < z1) {
         if (j1 > z0) {
           cpos = (cpos + 1 == n) ? 0 : cpos + 1;
-          if (cpos <= 1) {
+          if (pattern_changes(c, cpos)) {
+            if (cpos <= 1) {
 #pragma unroll
-            for (int r = 0; r < RPT; ++r) np[r] = nc[r];
-            if (cpos == 0) row_nibbles<RPT>(c.phase, cellof[j1], LL, crow, c3a, c3b, nc);
-            row_coeffs<Ti, RPT>(tab, nc, np, t);
+              for (int r = 0; r < RPT; ++r) np[r] = nc[r];
+            }
+            if (cpos == 0) row_nibbles<RPT>(c.phase, cellof[j1], LL, crow, c3a, c3b, mq, nc);
+            plane_masks(c, cpos, pm0, pm1);
+            row_coeffs<Ti, RPT>(tab, nc, np, pm0, pm1, t);
           }
         }
         const int b0 = j1 * NN + row0;
@@ -315,20 +339,27 @@ __device__ __forceinline__ void stencil_staged_run(const CellsDev &c, const floa
   const int j3m = (j3 == 0) ? N - 1 : j3 - 1;
   const int c3a = cellof[j3], c3b = cellof[j3m];
   int crow[5];
+  unsigned mq[5];  // in-plane inclusion masks (see row_nibbles)
+  const unsigned m3 = (in_sub(c, j3 - c3a * n) ? 1u : 0u) | (in_sub(c, j3m - c3b * n) ? 2u : 0u);
 #pragma unroll
-  for (int q = 0; q <= 4; ++q) crow[q] = cellof[(j2b - 1 + q < 0) ? N - 1 : j2b - 1 + q] * L;
+  for (int q = 0; q <= 4; ++q) {
+    const int j2 = (j2b - 1 + q < 0) ? N - 1 : j2b - 1 + q;
+    crow[q] = cellof[j2] * L;
+    mq[q] = in_sub(c, j2 - cellof[j2] * n) ? m3 : 0u;
+  }
   const int j1m0 = (z0 == 0) ? N - 1 : z0 - 1;
   int cpos = z0 - cellof[z0] * n;
-  unsigned np[4], nc[4];
-  row_nibbles<4>(c.phase, cellof[j1m0], LL, crow, c3a, c3b, np);
+  unsigned np[4], nc[4], pm0, pm1;
+  row_nibbles<4>(c.phase, cellof[j1m0], LL, crow, c3a, c3b, mq, np);
   if (cpos == 0) {
-    row_nibbles<4>(c.phase, cellof[z0], LL, crow, c3a, c3b, nc);
+    row_nibbles<4>(c.phase, cellof[z0], LL, crow, c3a, c3b, mq, nc);
   } else {
 #pragma unroll
     for (int r = 0; r < 4; ++r) nc[r] = np[r];
   }
+  plane_masks(c, cpos, pm0, pm1);
   float t[4][7];
-  row_coeffs<float, 4>(tab, nc, np, t);
+  row_coeffs<float, 4>(tab, nc, np, pm0, pm1, t);
   const int row0 = j2b * N + j3;
   float xm[4], x0[4];
 #pragma unroll
@@ -347,11 +378,14 @@ __device__ __forceinline__ void stencil_staged_run(const CellsDev &c, const floa
     }
     if (k > 0) {
       cpos = (cpos + 1 == n) ? 0 : cpos + 1;
-      if (cpos <= 1) {
+      if (pattern_changes(c, cpos)) {
+        if (cpos <= 1) {
 #pragma unroll
-        for (int r = 0; r < 4; ++r) np[r] = nc[r];
-        if (cpos == 0) row_nibbles<4>(c.phase, cellof[j1], LL, crow, c3a, c3b, nc);
-        row_coeffs<float, 4>(tab, nc, np, t);
+          for (int r = 0; r < 4; ++r) np[r] = nc[r];
+        }
+        if (cpos == 0) row_nibbles<4>(c.phase, cellof[j1], LL, crow, c3a, c3b, mq, nc);
+        plane_masks(c, cpos, pm0, pm1);
+        row_coeffs<float, 4>(tab, nc, np, pm0, pm1, t);
       }
     }
     const float *S0 = ring + s0 * kSlot + (1 + 4 * ty) * kSW + 4 + tx;

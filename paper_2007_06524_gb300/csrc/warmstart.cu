@@ -192,13 +192,18 @@ __global__ void __launch_bounds__(256) k_conv_in(const float *__restrict__ f, co
 }
 
 // Input feature: voxel coefficient as +1 (high) / -1 (low), from the cell phases.
-__global__ void k_feature(const uint8_t *__restrict__ phase, int L, int n, float *__restrict__ f) {
+// +1 where the voxel is high (its cell is high and, with sub-cell inclusions,
+// it lies in the cell's inclusion cube [sub_lo, sub_hi)^3), else -1.
+__global__ void k_feature(const uint8_t *__restrict__ phase, int L, int n, int sub_lo, int sub_hi,
+                          float *__restrict__ f) {
   const int N = L * n;
   const size_t N3 = (size_t)N * N * N;
   const size_t i = blockIdx.x * 256ULL + threadIdx.x;
   if (i >= N3) return;
   const int x = i % N, y = (i / N) % N, z = i / ((size_t)N * N);
-  f[i] = phase[((size_t)(z / n) * L + y / n) * L + x / n] ? 1.f : -1.f;
+  const int ux = x % n, uy = y % n, uz = z % n;
+  const bool inside = ux >= sub_lo && ux < sub_hi && uy >= sub_lo && uy < sub_hi && uz >= sub_lo && uz < sub_hi;
+  f[i] = (inside && phase[((size_t)(z / n) * L + y / n) * L + x / n]) ? 1.f : -1.f;
 }
 
 // FP32 fields [3][N3] -> three FP64 correctors
@@ -566,7 +571,8 @@ int feature_all(sq_net *net, int B, const sq_coeffs *const *cs, cudaStream_t s) 
   for (int b = 0; b < B; ++b) {
     CellsDev c;
     if (coeffs_view(cs[b], &c) != SQ_OK || c.N != net->N) return SQ_EINVAL;
-    k_feature<<<(unsigned)((N3 + 255) / 256), 256, 0, s>>>(c.phase, c.L, c.n, net->d_f + b * N3);
+    k_feature<<<(unsigned)((N3 + 255) / 256), 256, 0, s>>>(c.phase, c.L, c.n, c.sub_lo, c.sub_hi,
+                                                            net->d_f + b * N3);
     SQN_CK(cudaGetLastError());
   }
   return SQ_OK;

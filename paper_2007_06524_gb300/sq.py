@@ -76,6 +76,7 @@ def load_library():
         "sq_profile_class_name": (C.c_char_p, [i]),
         "sq_coeffs_shape": (i, [vp, p(i), p(i), p(i)]),
         "sq_coeffs_destroy": (None, [vp]),
+        "sq_coeffs_set_subcell": (i, [vp, i]),
         "sq_precond_setup": (i, [i, i, p(vp)]),
         "sq_precond_destroy": (None, [vp]),
         "sq_precond_factors": (i, [vp, vp, vp]),
@@ -201,6 +202,12 @@ def sq_coeffs_from_host(L, n, host_phase, a_lo, a_hi, stream=None) -> Coeffs:
     _check(load_library().sq_coeffs_from_host(int(L), int(n), arr.ctypes.data_as(C.c_void_p), float(a_lo),
                                               float(a_hi), _stream(stream), C.byref(out)), "sq_coeffs_from_host")
     return Coeffs(out)
+
+
+def sq_coeffs_set_subcell(c: Coeffs, sub: int):
+    """Sub-cell inclusions: a centred cube of side `sub` grid intervals per cell
+    carries the cell's value (sub = n: the checkerboard)."""
+    _check(load_library().sq_coeffs_set_subcell(c, int(sub)), "sq_coeffs_set_subcell")
 
 
 def sq_coeffs_regenerate(c: Coeffs, seed, p_hi, stream=None):
