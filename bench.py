@@ -355,6 +355,7 @@ def run_native(args):
         out["variants"]["warm_start_n64"] = run_warm_start(sq, torch)
         out["variants"]["refine_n512"] = run_refine_n512(sq, torch, stream)
         out["variants"]["ensemble"] = run_ensemble(sq, torch)
+        out["variants"]["inclusions_alpha_quarter"] = run_inclusions(sq, torch, stream)
 
     if rank == 0 and not args.no_cpu_baseline and ws == 1:
         out["cpu_baseline"] = cpu_baseline(statistics.mean(iters), R)
@@ -441,6 +442,43 @@ def run_ensemble(sq, torch, M=32):
                         "converged": r["status"] == sq.SQ_OK}
     res["sigma_exponent"] = round(float(np.polyfit(np.log(Ls), np.log(sig), 1)[0]), 3)
     res["M"] = M
+    return res
+
+
+def run_inclusions(sq, torch, stream):
+    """The paper's experiment setting (Sec. 5): sub-cell inclusions with
+    alpha = 1/4 (a centred cube of n/2 grid intervals per cell), lambda = 0.4
+    (a in {0.4, 1.0}), Bernoulli(1/2) cells, L = 32, n = 8 (N = 256), three
+    correctors + A_hom per realization, tol 1e-8: FP64 PCG (rank 8) and FP32
+    + FP64 refinement (exact)."""
+    import numpy as np
+
+    L, n, sub, N = 32, 8, 4, 256
+    c = sq.sq_build_coeffs(L, n, 0, 0.5, 0.4, 1.0)
+    sq.sq_coeffs_set_subcell(c, sub)
+    psis = [torch.empty(N ** 3, dtype=torch.float64, device="cuda") for _ in range(3)]
+    res = {}
+    for label, rank, prec in (("fp64_rank8", 8, sq.SQ_FP64), ("fp32_refine_exact", 0, sq.SQ_FP32_REFINE)):
+        pc = sq.sq_precond_setup(N, rank)
+        w = sq.sq_workspace_create(N, prec)
+        for i in range(3):
+            sq.sq_pcg_solve(c, pc, w, i, 1e-8, 1000, prec, None, psis[i])
+        torch.cuda.synchronize()
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        its, ok, As = [], True, []
+        for sd in (11, 12):
+            sq.sq_coeffs_regenerate(c, sd, 0.5)
+            for i in range(3):
+                inf = sq.sq_pcg_solve(c, pc, w, i, 1e-8, 1000, prec, None, psis[i])
+                its.append(inf["iters"])
+                ok = ok and inf["status"] == sq.SQ_OK
+            As.append(sq.sq_homogenized_matrix(c, *psis)[0])
+        e1.record(stream)
+        torch.cuda.synchronize()
+        t = e0.elapsed_time(e1) / 1e3
+        res[label] = {"solves_per_s": round(6 / t, 3), "iters_mean": round(float(np.mean(its)), 1), "converged": ok,
+                      "A_hom_diag_mean": round(float(np.mean([np.diag(A) for A in As])), 6)}
     return res
 
 
