@@ -61,6 +61,26 @@ def inclusion_field(phase: np.ndarray, n: int, sub: int, a_lo: float, a_hi: floa
     return np.where(hi_cell & inside_all, float(a_hi), float(a_lo))
 
 
+def level_field(level: np.ndarray, n: int, values, sub: int | None = None) -> np.ndarray:
+    """Voxel coefficients of a multi-level medium (varying contrast, Sec. 2):
+    cell level l carries the value values[min(l, K-1)] on its centred
+    inclusion cube of side sub (Sec. 3.1; None or n = the whole cell) and
+    values[0] everywhere else. K = 2 is :func:`inclusion_field`."""
+    if sub is None:
+        sub = n
+    if sub < 1 or sub > n or (n - sub) % 2:
+        raise ValueError("sub must be in [1, n] with n - sub even (a centred cube)")
+    v = np.asarray(values, dtype=np.float64)
+    lv = np.minimum(level.astype(np.int64), len(v) - 1)
+    lo = (n - sub) // 2
+    u = np.arange(n)
+    inside1 = (u >= lo) & (u < lo + sub)
+    inside = inside1[:, None, None] & inside1[None, :, None] & inside1[None, None, :]
+    L = level.shape[0]
+    cell_v = np.repeat(np.repeat(np.repeat(v[lv], n, 0), n, 1), n, 2)
+    return np.where(np.tile(inside, (L, L, L)), cell_v, v[0])
+
+
 def edge_coefficients(cellval: np.ndarray, n: int) -> np.ndarray:
     """a_d(j) for d = 0, 1, 2 (axes x1, x2, x3), shape (3, N, N, N), of the
     checkerboard with cell values cellval; see edge_coefficients_voxels."""

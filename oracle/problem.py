@@ -42,6 +42,21 @@ def realization(L: int, n: int, seed: int, a_lo: float, a_hi: float, p_hi: float
     return Realization(L, n, L * n, phase, cellval, a_edges, A, b)
 
 
+def realization_levels(L: int, n: int, seed: int, values, probs=None, level: np.ndarray | None = None,
+                       sub: int | None = None) -> Realization:
+    """Multi-level realization (varying contrast, Sec. 2): cell levels drawn
+    with probabilities probs (rng.cell_levels) or given as `level`; voxel
+    values from assembly.level_field. `phase` holds the levels and `cellval`
+    the cell values."""
+    if level is None:
+        level = rng.cell_levels_vec(L, seed, probs) if L > 16 else rng.cell_levels(L, seed, probs)
+    cellval = rng.level_values(level, values)
+    a_edges = assembly.edge_coefficients_voxels(assembly.level_field(level, n, values, sub))
+    A = assembly.stiffness_edges(a_edges)
+    b = [assembly.rhs(a_edges, i) for i in range(3)]
+    return Realization(L, n, L * n, level, cellval, a_edges, A, b)
+
+
 def solve_correctors(re: Realization, dirs=(0, 1, 2), rank: int = 0, tol: float = 1e-13):
     """PCG-solve A psi_i = b_i for the requested directions; returns
     (psis list (None where not solved), iterations list, A_hom)."""
@@ -54,4 +69,4 @@ def solve_correctors(re: Realization, dirs=(0, 1, 2), rank: int = 0, tol: float 
     return psis, its, homogenized.ahom_edge(re.a_edges, psis)
 
 
-__all__ = ["Realization", "realization", "solve_correctors", "precond"]
+__all__ = ["Realization", "realization", "realization_levels", "solve_correctors", "precond"]

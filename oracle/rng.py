@@ -97,3 +97,61 @@ def cell_values(phase: np.ndarray, a_lo: float, a_hi: float) -> np.ndarray:
     """Cell coefficient a = a_lo on low cells, a_hi on high cells (Eq. 3 with
     a_lo = lambda, a_hi = lambda + beta)."""
     return np.where(phase.astype(bool), float(a_hi), float(a_lo))
+
+
+# ---------------------------------------------------------------- contrast levels
+# Varying contrast (Sec. 2, the two-contrast and layer-type realizations): a
+# cell takes one of K levels 0 .. K-1 with the coefficient values[level]. The
+# draw uses the same output u (top 53 bits) as the two-level rule: with the
+# tail probabilities P_m = probs[m] + probs[m+1] + ... + probs[K-1], summed in
+# FP64 from the top level down, and T_m = floor(P_m * 2^53), the level is the
+# number of m in 1 .. K-1 with u < T_m. For K = 2 (probs = (1 - p_hi, p_hi))
+# T_1 = floor(p_hi * 2^53): the two-level rule above.
+
+
+def level_thresholds(probs) -> list[int]:
+    """Integer thresholds T_1 >= ... >= T_{K-1} of the level draw."""
+    K = len(probs)
+    if K < 2 or any(not (0.0 <= float(p) <= 1.0) for p in probs):
+        raise ValueError("need K >= 2 probabilities in [0, 1]")
+    tail = 0.0
+    T = [0] * K
+    for m in range(K - 1, 0, -1):
+        tail = float(probs[m]) + tail
+        T[m] = int(min(tail, 1.0) * 9007199254740992.0)
+    return T[1:]
+
+
+def cell_levels(L: int, seed: int, probs) -> np.ndarray:
+    """Level (0 .. K-1) of every cell, shape (L, L, L); pure-Python loop."""
+    T = level_thresholds(probs)
+    lv = np.zeros((L, L, L), dtype=np.uint8)
+    for c1 in range(L):
+        for c2 in range(L):
+            for c3 in range(L):
+                u = splitmix64_at(seed, c3 + L * c2 + L * L * c1) >> 11
+                lv[c1, c2, c3] = sum(1 for t in T if u < t)
+    return lv
+
+
+def cell_levels_vec(L: int, seed: int, probs) -> np.ndarray:
+    """Same as :func:`cell_levels`, vectorised (checked against it in the tests)."""
+    T = level_thresholds(probs)
+    idx = np.arange(L * L * L, dtype=np.uint64)
+    with np.errstate(over="ignore"):
+        z = np.uint64(seed & MASK64) + (idx + np.uint64(1)) * np.uint64(GAMMA)
+        z = (z ^ (z >> np.uint64(30))) * np.uint64(MIX_M1)
+        z = (z ^ (z >> np.uint64(27))) * np.uint64(MIX_M2)
+        z = z ^ (z >> np.uint64(31))
+    u = z >> np.uint64(11)
+    lv = np.zeros(L * L * L, dtype=np.uint8)
+    for t in T:
+        lv += (u < np.uint64(t)).astype(np.uint8)
+    return lv.reshape(L, L, L)
+
+
+def level_values(level: np.ndarray, values) -> np.ndarray:
+    """Cell coefficient values[min(level, K-1)] (a level byte past the top
+    level reads as the top level)."""
+    v = np.asarray(values, dtype=np.float64)
+    return v[np.minimum(level.astype(np.int64), len(v) - 1)]
