@@ -356,6 +356,7 @@ def run_native(args):
         out["variants"]["refine_n512"] = run_refine_n512(sq, torch, stream)
         out["variants"]["ensemble"] = run_ensemble(sq, torch)
         out["variants"]["inclusions_alpha_quarter"] = run_inclusions(sq, torch, stream)
+        out["variants"]["two_contrasts_alpha_quarter"] = run_two_contrasts(sq, torch, stream)
 
     if rank == 0 and not args.no_cpu_baseline and ws == 1:
         out["cpu_baseline"] = cpu_baseline(statistics.mean(iters), R)
@@ -479,6 +480,56 @@ def run_inclusions(sq, torch, stream):
         t = e0.elapsed_time(e1) / 1e3
         res[label] = {"solves_per_s": round(6 / t, 3), "iters_mean": round(float(np.mean(its)), 1), "converged": ok,
                       "A_hom_diag_mean": round(float(np.mean([np.diag(A) for A in As])), 6)}
+    return res
+
+
+def run_two_contrasts(sq, torch, stream):
+    """Varying contrast (Sec. 2): alpha = 1/4 inclusions on half of the cells,
+    lambda = 0.4, each inclusion with contrast beta = 0.3 or 0.6 (levels
+    {0.4, 0.7, 1.0}), L = 32, n = 8 (N = 256), three correctors + A_hom per
+    realization, tol 1e-8. "random": the contrast drawn per cell (probabilities
+    1/2, 1/4, 1/4); "layers": the contrast set per layer of four cell planes
+    along x1 (alternating), inclusion cells drawn with probability 1/2."""
+    import numpy as np
+
+    L, n, sub, N = 32, 8, 4, 256
+    vals, probs = (0.4, 0.7, 1.0), (0.5, 0.25, 0.25)
+    layer = (1 + (np.arange(L) // 4) % 2).astype(np.uint8)[:, None, None]
+
+    def layered(seed):
+        ph, _ = sq.sq_coeffs_cells(sq.sq_build_coeffs(L, n, seed, 0.5, 1.0, 2.0))
+        return ph * layer
+
+    psis = [torch.empty(N ** 3, dtype=torch.float64, device="cuda") for _ in range(3)]
+    res = {}
+    for kind in ("random", "layers"):
+        if kind == "random":
+            cs = [sq.sq_build_coeffs_levels(L, n, sd, probs, vals) for sd in (11, 12)]
+        else:
+            cs = [sq.sq_coeffs_from_host_levels(L, n, layered(sd).ravel(), vals) for sd in (11, 12)]
+        for c in cs:
+            sq.sq_coeffs_set_subcell(c, sub)
+        for label, rank, prec in (("fp64_rank8", 8, sq.SQ_FP64), ("fp32_refine_exact", 0, sq.SQ_FP32_REFINE)):
+            pc = sq.sq_precond_setup(N, rank)
+            w = sq.sq_workspace_create(N, prec)
+            for i in range(3):
+                sq.sq_pcg_solve(cs[0], pc, w, i, 1e-8, 1000, prec, None, psis[i])
+            torch.cuda.synchronize()
+            e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            e0.record(stream)
+            its, ok, As = [], True, []
+            for c in cs:
+                for i in range(3):
+                    inf = sq.sq_pcg_solve(c, pc, w, i, 1e-8, 1000, prec, None, psis[i])
+                    its.append(inf["iters"])
+                    ok = ok and inf["status"] == sq.SQ_OK
+                As.append(sq.sq_homogenized_matrix(c, *psis)[0])
+            e1.record(stream)
+            torch.cuda.synchronize()
+            t = e0.elapsed_time(e1) / 1e3
+            res[f"{kind}_{label}"] = {"solves_per_s": round(6 / t, 3), "iters_mean": round(float(np.mean(its)), 1),
+                                      "converged": ok,
+                                      "A_hom_diag": [round(float(v), 6) for v in np.mean([np.diag(A) for A in As], 0)]}
     return res
 
 

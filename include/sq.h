@@ -87,7 +87,8 @@ int sq_build_coeffs(int L, int n, uint64_t seed, double p_hi, double a_lo, doubl
 
 /* Same, with the L^3 phases (0 = a_lo, nonzero = a_hi, index c3 + L*c2 + L*L*c1)
  * given in HOST memory; they are copied to the device on `stream`
- * (host_phase may be reused once the call returns: the copy is staged). */
+ * (host_phase may be reused once the call returns: the copy is staged).
+ * Nonzero bytes are stored as 1. */
 int sq_coeffs_from_host(int L, int n, const uint8_t *host_phase, double a_lo, double a_hi,
                         sq_stream_t stream, sq_coeffs **out);
 
@@ -97,7 +98,8 @@ int sq_coeffs_regenerate(sq_coeffs *c, uint64_t seed, double p_hi, sq_stream_t s
 
 /* Copies L^3 phases from PINNED host memory into an existing handle
  * (cudaMemcpyAsync on `stream`: host_phase must stay valid until the stream
- * reaches the copy; values must be 0 or 1). */
+ * reaches the copy; values 0 or 1, or the cell levels of a multi-level
+ * handle, at most 3). */
 int sq_coeffs_upload(sq_coeffs *c, const uint8_t *host_phase, sq_stream_t stream);
 
 /* Copies the phases to host_phase (L^3 bytes, may be NULL) and counts the high
@@ -113,6 +115,36 @@ int sq_coeffs_shape(const sq_coeffs *c, int *L, int *n, int *N);
  * Applies to every later use of c (solves, batches created afterwards,
  * A_hom, the warm-start features). */
 int sq_coeffs_set_subcell(sq_coeffs *c, int sub);
+
+/* Multi-level media (varying contrast, Sec. 2: inclusion cells carry
+ * lambda + beta_c with a contrast beta_c that differs between cells, drawn
+ * at random or set per layer of cells). A cell's phase byte v selects level
+ * min(v, K - 1) with coefficient values[level]; voxels outside the cell's
+ * inclusion cube (sq_coeffs_set_subcell) take values[0]. The lumped edge
+ * coefficient stays the mean of the four voxels around the edge.
+ * sq_coeffs_set_levels: 2 <= K <= 4 values, each finite and > 0 (HOST
+ * array, read during the call); K = 2 is the two-level medium
+ * {a_lo, a_hi} = {values[0], values[1]}. Applies to every later use of c,
+ * as sq_coeffs_set_subcell does. SQ_EINVAL on a bad argument. */
+int sq_coeffs_set_levels(sq_coeffs *c, int K, const double *values);
+
+/* A new K-level handle with cell levels drawn from the SplitMix64 stream of
+ * sq_build_coeffs: with the top 53 bits u of the cell's output and the tail
+ * probabilities P_m = probs[m] + ... + probs[K-1] (summed in FP64 from the
+ * top level down), the level is the number of m in 1..K-1 with
+ * u < floor(min(P_m, 1) * 2^53). K = 2 with probs = {1 - p_hi, p_hi} draws
+ * the same cells as sq_build_coeffs. probs: K HOST values in [0, 1] summing
+ * to 1 (within 1e-9); values as for sq_coeffs_set_levels. */
+int sq_build_coeffs_levels(int L, int n, uint64_t seed, int K, const double *probs, const double *values,
+                           sq_stream_t stream, sq_coeffs **out);
+/* A new K-level handle with the L^3 cell levels given in HOST memory (index
+ * as in sq_coeffs_from_host; bytes >= K are stored as K - 1; the copy is
+ * staged, host_level may be reused once the call returns). */
+int sq_coeffs_from_host_levels(int L, int n, const uint8_t *host_level, int K, const double *values,
+                               sq_stream_t stream, sq_coeffs **out);
+/* Redraws the levels of a K-level handle in place (K must equal the
+ * handle's level count; asynchronous on `stream`, no allocation). */
+int sq_coeffs_regenerate_levels(sq_coeffs *c, uint64_t seed, int K, const double *probs, sq_stream_t stream);
 void sq_coeffs_destroy(sq_coeffs *c);
 
 /* Preconditioner (Sec. 4.1-4.2): pseudo-inverse of the periodic Laplacian,

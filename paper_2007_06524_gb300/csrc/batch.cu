@@ -76,12 +76,16 @@ __global__ void __launch_bounds__(kThreads, WHICH == 1 ? 3 : 1) kb_stencil(const
   const BSolve &B = S[s];
   Scalars *st = (WHICH == 0) ? B.st_o : B.st_i;
   if (*(volatile int *)&st->done) return;
-  __shared__ Ti tab[256][kTabStride];
+  // dynamic shared memory: WHICH 1: the staged ring (kStages * kSlot floats),
+  // then the pattern tables; WHICH 0: the tables (tab_bytes of the batch's
+  // largest layer count)
+  extern __shared__ __align__(16) float dsm_b[];
+  float *ring = dsm_b;
+  Ti(*tab)[kTabStride] = reinterpret_cast<Ti(*)[kTabStride]>(dsm_b + (WHICH == 1 ? kStages * kSlot : 0));
   __shared__ short cellof[kMaxN];
   const int tid = threadIdx.x + 32 * threadIdx.y;
   if constexpr (WHICH == 1) {
     if (B.in_staged) {
-      extern __shared__ __align__(16) float ring[];  // kStages * kSlot floats
       const int N = B.c.N, nbx = N / 32, ntl = nbx * nbx;
       const int lb = blockIdx.x - pre[s];
       const int tile = lb % ntl, zb = lb / ntl;
@@ -328,6 +332,7 @@ struct sq_batch {
   int *d_pre = nullptr;  // [0..count] stencil, [count+1..] dht, [2count+2..] vec, [3count+3..] inner stencil
   int tot_st = 0, tot_dht = 0, tot_vec = 0, tot_in = 0;
   size_t dht_smem[2] = {0, 0};  // plain passes, pass C
+  int layers = 1;               // most threshold layers of the batch's media (pattern tables)
   void *d_mem = nullptr;        // fields, scalars, partials
   int *d_iters = nullptr;
   int *d_count = nullptr;
@@ -376,7 +381,8 @@ int precond_first_b(sq_batch *b, cudaStream_t s) {
 }
 
 int iteration_b(sq_batch *b, cudaStream_t s) {
-  kb_stencil<1><<<b->tot_in, dim3(32, 8, 1), kStagedSmem, s>>>(b->dS, b->d_pre + 3 * (b->count + 1), b->count);
+  kb_stencil<1><<<b->tot_in, dim3(32, 8, 1), kStagedSmem + tab_bytes<float>(b->layers), s>>>(
+      b->dS, b->d_pre + 3 * (b->count + 1), b->count);
   if (cudaGetLastError() != cudaSuccess) return SQ_ECUDA;
   int st;
   if ((st = launch_kb_dht<3, LD_RESID, SO_PLAIN, false>(b, 0, s)) != SQ_OK) return st;
@@ -496,6 +502,7 @@ int sq_batch_create(int count, const sq_solve_desc *descs, const sq_precond *con
     pre[3 * (count + 1) + k + 1] = pre[3 * (count + 1) + k] + B.nb_in;
     field_floats += 5 * (size_t)n3;
     maxN = std::max(maxN, N);
+    b->layers = std::max(b->layers, B.c.layers);
     maxR = std::max(maxR, sp.rank);
     maxP = std::max(maxP, P);
     b->dht_smem[0] = std::max(b->dht_smem[0], dht_smem_bytes_t<float>(N, P, 0));
@@ -547,8 +554,8 @@ int sq_batch_create(int count, const sq_solve_desc *descs, const sq_precond *con
   ok = cudaMemcpy(b->dS, b->hS.data(), sizeof(BSolve) * count, cudaMemcpyHostToDevice) == cudaSuccess;
   ok = ok && cudaMemcpy(b->d_pre, pre.data(), sizeof(int) * pre.size(), cudaMemcpyHostToDevice) == cudaSuccess;
   ok = ok && cudaMemset(sc, 0, bytes_scal) == cudaSuccess;
-  ok = ok && cudaFuncSetAttribute(kb_stencil<1>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kStagedSmem) ==
-                 cudaSuccess;
+  ok = ok && allow_dynamic_smem((const void *)kb_stencil<1>, kStagedSmem + tab_bytes<float>(b->layers)) == cudaSuccess;
+  ok = ok && allow_dynamic_smem((const void *)kb_stencil<0>, tab_bytes<double>(b->layers)) == cudaSuccess;
   ok = ok && set_kb_dht_smem<3, LD_PLAIN, SO_PLAIN, false>(b->dht_smem[0]) == SQ_OK;
   ok = ok && set_kb_dht_smem<3, LD_RESID, SO_PLAIN, false>(b->dht_smem[0]) == SQ_OK;
   ok = ok && set_kb_dht_smem<2, LD_PLAIN, SO_PLAIN, false>(b->dht_smem[0]) == SQ_OK;
@@ -595,7 +602,7 @@ int sq_pcg_solve_batched(sq_batch *b, double tol, int max_iter, sq_solve_info *i
   SQB_CK(cudaGetLastError());
   int outer = 0;
   for (; outer < 30; ++outer) {
-    kb_stencil<0><<<b->tot_st, dim3(32, 8, 1), 0, s>>>(b->dS, b->d_pre, count);
+    kb_stencil<0><<<b->tot_st, dim3(32, 8, 1), tab_bytes<double>(b->layers), s>>>(b->dS, b->d_pre, count);
     SQB_CK(cudaGetLastError());
     int active = 0;
     if ((st = count_active(b, 0, s, &active)) != SQ_OK) return st;

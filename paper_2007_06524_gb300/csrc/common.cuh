@@ -264,44 +264,70 @@ __device__ __forceinline__ void finalize_scalars(Scalars *st, int op, const doub
 
 // ------------------------------------------------------------ host launchers
 
+// Multi-level media (varying contrast): a cell's phase byte v selects level
+// min(v, K - 1) of K <= kMaxLevels coefficient values.
+constexpr int kMaxLevels = 4;
+constexpr int kMaxLayers = kMaxLevels - 1;
+
 struct CellsDev {
-  const uint8_t *phase;  // L^3 cell phases
+  const uint8_t *phase;  // L^3 cell phases (levels)
   int L, n, N;
-  double a_lo, a_hi;
+  double a_lo, a_hi;  // values of levels 0 and 1
   // Sub-cell inclusions (Sec. 3.1): a voxel at cell-local index u (per axis)
   // takes its cell's value only if sub_lo <= u < sub_hi on every axis, else
   // a_lo. The default is the whole cell (the checkerboard).
   int sub_lo = 0, sub_hi = 1 << 30;
-  // An edge touches 4 voxels, k of them high: a_edge = (k a_hi + (4-k) a_lo)/4.
-  // A node's six edges touch 24 voxel slots, K of them high: the diagonal is
-  // (K a_hi + (24-K) a_lo)/4. Both tables are filled on the host (fill_tables).
-  double edge_d[5], diag_d[25];
-  float edge_f[5], diag_f[25];
+  // Levels above 1 (host side; K = 2 + the count set): a_up[l - 2] = value of level l.
+  double a_up[kMaxLevels - 2] = {0.0, 0.0};
+  // Threshold layers: the value of a voxel at level v is
+  //   a_lo + sum_{l = 1 .. K-1} [v >= l] (value(l) - value(l - 1)),
+  // and an edge coefficient is the mean of its four voxels, so it is the sum
+  // over layers l of the layer's table at k_l = the number of the four voxels
+  // with level >= l. Layer 0 (l = 1): a_edge = (k a_hi + (4-k) a_lo)/4; a
+  // higher layer adds k (value(l) - value(l - 1))/4. A node's six edges touch
+  // 24 voxel slots, K_l of them at level >= l: the diagonal is the same sum
+  // with 24 in place of 4. The tables are filled on the host (fill_tables);
+  // two-level media use layer 0 only.
+  int layers = 1;  // K - 1
+  double edge_d[kMaxLayers][5], diag_d[kMaxLayers][25];
+  float edge_f[kMaxLayers][5], diag_f[kMaxLayers][25];
 };
 
+inline double level_value(const CellsDev &c, int l) { return l == 0 ? c.a_lo : l == 1 ? c.a_hi : c.a_up[l - 2]; }
+
 inline void fill_tables(CellsDev &c) {
-  for (int k = 0; k <= 4; ++k) {
-    c.edge_d[k] = (k * c.a_hi + (4 - k) * c.a_lo) * 0.25;
-    c.edge_f[k] = (float)c.edge_d[k];
-  }
-  for (int k = 0; k <= 24; ++k) {
-    c.diag_d[k] = (k * c.a_hi + (24 - k) * c.a_lo) * 0.25;
-    c.diag_f[k] = (float)c.diag_d[k];
+  for (int l = 0; l < kMaxLayers; ++l) {
+    const double lo = (l == 0) ? c.a_lo : 0.0;
+    const double step = (l < c.layers) ? level_value(c, l + 1) - level_value(c, l) : 0.0;
+    for (int k = 0; k <= 4; ++k) {
+      c.edge_d[l][k] = (l == 0) ? (k * c.a_hi + (4 - k) * lo) * 0.25 : k * step * 0.25;
+      c.edge_f[l][k] = (float)c.edge_d[l][k];
+    }
+    for (int k = 0; k <= 24; ++k) {
+      c.diag_d[l][k] = (l == 0) ? (k * c.a_hi + (24 - k) * lo) * 0.25 : k * step * 0.25;
+      c.diag_f[l][k] = (float)c.diag_d[l][k];
+    }
   }
 }
 
+// Shared-memory bytes of the pattern tables of `layers` layers.
 template <typename T>
-__device__ __forceinline__ const T *edge_table(const CellsDev &c);
-template <>
-__device__ __forceinline__ const double *edge_table<double>(const CellsDev &c) { return c.edge_d; }
-template <>
-__device__ __forceinline__ const float *edge_table<float>(const CellsDev &c) { return c.edge_f; }
+constexpr size_t tab_bytes(int layers) {
+  return (size_t)layers * 256 * 9 * sizeof(T);
+}
+
 template <typename T>
-__device__ __forceinline__ const T *diag_table(const CellsDev &c);
+__device__ __forceinline__ const T *edge_table(const CellsDev &c, int l);
 template <>
-__device__ __forceinline__ const double *diag_table<double>(const CellsDev &c) { return c.diag_d; }
+__device__ __forceinline__ const double *edge_table<double>(const CellsDev &c, int l) { return c.edge_d[l]; }
 template <>
-__device__ __forceinline__ const float *diag_table<float>(const CellsDev &c) { return c.diag_f; }
+__device__ __forceinline__ const float *edge_table<float>(const CellsDev &c, int l) { return c.edge_f[l]; }
+template <typename T>
+__device__ __forceinline__ const T *diag_table(const CellsDev &c, int l);
+template <>
+__device__ __forceinline__ const double *diag_table<double>(const CellsDev &c, int l) { return c.diag_d[l]; }
+template <>
+__device__ __forceinline__ const float *diag_table<float>(const CellsDev &c, int l) { return c.diag_f[l]; }
 
 struct RedBuf {
   Scalars *st;
@@ -309,7 +335,9 @@ struct RedBuf {
 };
 
 // stencil.cu
-cudaError_t launch_coeff_gen(uint8_t *phase, int L, uint64_t seed, uint64_t thr, cudaStream_t s);
+// thr[0..2]: level thresholds on the top 53 bits (see k_coeff_gen).
+cudaError_t launch_coeff_gen(uint8_t *phase, int L, uint64_t seed, const uint64_t *thr, cudaStream_t s);
+cudaError_t allow_dynamic_smem(const void *kern, size_t smem);
 enum StencilMode : int { ST_MATVEC = 0, ST_RESID = 1, ST_RHS = 2 };
 // y = A x (ST_MATVEC, reduces x.y), y = b_dir - A x (ST_RESID, reduces ||y||^2
 // and ||b||^2), y = b_dir (ST_RHS, reduces ||b||^2). Ti: type of x and of the

@@ -29,6 +29,8 @@ struct sq_coeffs {
   int L, n, N;
   double a_lo, a_hi;
   int sub_lo = 0, sub_hi = 1 << 30;  // inclusion cube of every cell (default: the whole cell)
+  int levels = 2;                    // K: phase byte v reads level min(v, K - 1)
+  double a_up[kMaxLevels - 2] = {0.0, 0.0};  // values of levels 2 .. K-1
   uint8_t *d_phase;
   cudaStream_t stream;
   Scalars *d_st;       // reduction scalars for operator / A_hom calls
@@ -127,6 +129,8 @@ CellsDev cells_dev(const sq_coeffs *c) {
   d.a_hi = c->a_hi;
   d.sub_lo = c->sub_lo;
   d.sub_hi = c->sub_hi;
+  d.layers = c->levels - 1;
+  for (int l = 0; l < kMaxLevels - 2; ++l) d.a_up[l] = c->a_up[l];
   fill_tables(d);
   return d;
 }
@@ -608,7 +612,7 @@ int sq_build_coeffs(int L, int n, uint64_t seed, double p_hi, double a_lo, doubl
   cudaStream_t s = reinterpret_cast<cudaStream_t>(stream);
   int st = alloc_coeffs(L, n, a_lo, a_hi, s, out);
   if (st != SQ_OK) return st;
-  const uint64_t thr = (uint64_t)(p_hi * 9007199254740992.0);  // floor(p_hi * 2^53)
+  const uint64_t thr[3] = {(uint64_t)(p_hi * 9007199254740992.0), 0, 0};  // floor(p_hi * 2^53)
   const size_t pi = prof_begin(PC_COEFF, s);
   const cudaError_t ge = launch_coeff_gen((*out)->d_phase, L, seed, thr, s);
   prof_end(pi, s);
@@ -641,7 +645,91 @@ int sq_coeffs_from_host(int L, int n, const uint8_t *host_phase, double a_lo, do
 int sq_coeffs_regenerate(sq_coeffs *c, uint64_t seed, double p_hi, sq_stream_t stream) {
   if (!c || !(p_hi >= 0.0 && p_hi <= 1.0)) return SQ_EINVAL;
   cudaStream_t s = reinterpret_cast<cudaStream_t>(stream);
-  const uint64_t thr = (uint64_t)(p_hi * 9007199254740992.0);
+  const uint64_t thr[3] = {(uint64_t)(p_hi * 9007199254740992.0), 0, 0};
+  SQ_LAUNCH(PC_COEFF, s, launch_coeff_gen(c->d_phase, c->L, seed, thr, s));
+  return SQ_OK;
+}
+
+// Level thresholds: tail probabilities P_m = probs[m] + ... + probs[K-1],
+// summed in FP64 from the top level down, T_m = floor(min(P_m, 1) * 2^53).
+static int level_thresholds(int K, const double *probs, uint64_t *thr) {
+  if (K < 2 || K > kMaxLevels || !probs) return SQ_EINVAL;
+  double total = 0.0;
+  for (int m = 0; m < K; ++m) {
+    if (!(probs[m] >= 0.0 && probs[m] <= 1.0)) return SQ_EINVAL;
+    total += probs[m];
+  }
+  if (std::fabs(total - 1.0) > 1e-9) return SQ_EINVAL;
+  thr[0] = thr[1] = thr[2] = 0;
+  double tail = 0.0;
+  for (int m = K - 1; m >= 1; --m) {
+    tail = probs[m] + tail;
+    thr[m - 1] = (uint64_t)((tail < 1.0 ? tail : 1.0) * 9007199254740992.0);
+  }
+  return SQ_OK;
+}
+
+int sq_coeffs_set_levels(sq_coeffs *c, int K, const double *values) {
+  if (!c || K < 2 || K > kMaxLevels || !values) return SQ_EINVAL;
+  for (int l = 0; l < K; ++l)
+    if (!(values[l] > 0.0) || !std::isfinite(values[l])) return SQ_EINVAL;
+  c->levels = K;
+  c->a_lo = values[0];
+  c->a_hi = values[1];
+  for (int l = 0; l < kMaxLevels - 2; ++l) c->a_up[l] = (l + 2 < K) ? values[l + 2] : 0.0;
+  return SQ_OK;
+}
+
+int sq_build_coeffs_levels(int L, int n, uint64_t seed, int K, const double *probs, const double *values,
+                           sq_stream_t stream, sq_coeffs **out) {
+  if (!out) return SQ_EINVAL;
+  *out = nullptr;
+  uint64_t thr[3];
+  if (level_thresholds(K, probs, thr) != SQ_OK || !values) return SQ_EINVAL;
+  cudaStream_t s = reinterpret_cast<cudaStream_t>(stream);
+  int st = alloc_coeffs(L, n, values[0], values[1], s, out);
+  if (st != SQ_OK) return st;
+  st = sq_coeffs_set_levels(*out, K, values);
+  if (st == SQ_OK) {
+    const size_t pi = prof_begin(PC_COEFF, s);
+    if (launch_coeff_gen((*out)->d_phase, L, seed, thr, s) != cudaSuccess) st = SQ_ECUDA;
+    prof_end(pi, s);
+  }
+  if (st != SQ_OK) {
+    sq_coeffs_destroy(*out);
+    *out = nullptr;
+  }
+  return st;
+}
+
+int sq_coeffs_from_host_levels(int L, int n, const uint8_t *host_level, int K, const double *values,
+                               sq_stream_t stream, sq_coeffs **out) {
+  if (!out) return SQ_EINVAL;
+  *out = nullptr;
+  if (!host_level || !values || K < 2 || K > kMaxLevels) return SQ_EINVAL;
+  cudaStream_t s = reinterpret_cast<cudaStream_t>(stream);
+  int st = alloc_coeffs(L, n, values[0], values[1], s, out);
+  if (st != SQ_OK) return st;
+  st = sq_coeffs_set_levels(*out, K, values);
+  if (st == SQ_OK) {
+    const size_t nc = (size_t)L * L * L;
+    std::vector<uint8_t> lv(nc);  // levels past the top one read as the top level
+    for (size_t i = 0; i < nc; ++i) lv[i] = host_level[i] < K ? host_level[i] : (uint8_t)(K - 1);
+    if (cudaMemcpyAsync((*out)->d_phase, lv.data(), nc, cudaMemcpyHostToDevice, s) != cudaSuccess ||
+        cudaStreamSynchronize(s) != cudaSuccess)
+      st = SQ_ECUDA;
+  }
+  if (st != SQ_OK) {
+    sq_coeffs_destroy(*out);
+    *out = nullptr;
+  }
+  return st;
+}
+
+int sq_coeffs_regenerate_levels(sq_coeffs *c, uint64_t seed, int K, const double *probs, sq_stream_t stream) {
+  uint64_t thr[3];
+  if (!c || K != c->levels || level_thresholds(K, probs, thr) != SQ_OK) return SQ_EINVAL;
+  cudaStream_t s = reinterpret_cast<cudaStream_t>(stream);
   SQ_LAUNCH(PC_COEFF, s, launch_coeff_gen(c->d_phase, c->L, seed, thr, s));
   return SQ_OK;
 }

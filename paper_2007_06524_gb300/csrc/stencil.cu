@@ -29,14 +29,20 @@ __device__ __forceinline__ uint64_t splitmix64_output(uint64_t seed, uint64_t i)
   return z ^ (z >> 31);
 }
 
-__global__ void k_coeff_gen(uint8_t *__restrict__ phase, int ncell, uint64_t seed, uint64_t thr) {
+// Level of cell i = the number of thresholds t1 >= t2 >= t3 above the top 53
+// bits u of its output (two-level media: t2 = t3 = 0, level = [u < t1]).
+__global__ void k_coeff_gen(uint8_t *__restrict__ phase, int ncell, uint64_t seed, uint64_t t1, uint64_t t2,
+                            uint64_t t3) {
   int i = blockIdx.x * blockDim.x + threadIdx.x;
-  if (i < ncell) phase[i] = ((splitmix64_output(seed, (uint64_t)i) >> 11) < thr) ? 1 : 0;
+  if (i < ncell) {
+    const uint64_t u = splitmix64_output(seed, (uint64_t)i) >> 11;
+    phase[i] = (uint8_t)((u < t1 ? 1 : 0) + (u < t2 ? 1 : 0) + (u < t3 ? 1 : 0));
+  }
 }
 
-cudaError_t launch_coeff_gen(uint8_t *phase, int L, uint64_t seed, uint64_t thr, cudaStream_t s) {
+cudaError_t launch_coeff_gen(uint8_t *phase, int L, uint64_t seed, const uint64_t *thr, cudaStream_t s) {
   int ncell = L * L * L;
-  k_coeff_gen<<<(ncell + 255) / 256, 256, 0, s>>>(phase, ncell, seed, thr);
+  k_coeff_gen<<<(ncell + 255) / 256, 256, 0, s>>>(phase, ncell, seed, thr[0], thr[1], thr[2]);
   return cudaGetLastError();
 }
 
@@ -54,7 +60,8 @@ __global__ void __launch_bounds__(kThreads) k_stencil(CellsDev c, int dir, const
                                                       To *__restrict__ y, RedBuf rb, int fin, int check_done,
                                                       int zc, int nitems) {
   if (check_done && *(volatile int *)&rb.st->done) return;
-  __shared__ Ti tab[256][kTabStride];
+  extern __shared__ __align__(16) unsigned char dsm[];  // pattern tables, tab_bytes<Ti>(c.layers)
+  Ti(*tab)[kTabStride] = reinterpret_cast<Ti(*)[kTabStride]>(dsm);
   __shared__ short cellof[kMaxN];
   const int tid = threadIdx.x + 32 * threadIdx.y;
   build_pattern_table<Ti>(tab, c, tid);
@@ -78,6 +85,30 @@ __global__ void __launch_bounds__(kThreads) k_stencil(CellsDev c, int dir, const
   if (reduce_last_block<2>(v, rb.partials, &rb.st->ticket, s)) {
     if (tid == 0) finalize_scalars(rb.st, fin, s, 2);
   }
+}
+
+// Raises a kernel's dynamic shared-memory limit to `smem` bytes where that is
+// above the default 48 KB (once per kernel and device; guarded for
+// concurrent host threads).
+cudaError_t allow_dynamic_smem(const void *kern, size_t smem) {
+  if (smem <= 48 * 1024) return cudaSuccess;
+  int dev = 0;
+  cudaError_t e = cudaGetDevice(&dev);
+  if (e != cudaSuccess) return e;
+  struct Entry {
+    const void *k;
+    int dev;
+    size_t smem;
+  };
+  static Entry done[64];
+  static int used = 0;
+  static std::mutex mu;
+  std::lock_guard<std::mutex> lock(mu);
+  for (int i = 0; i < used; ++i)
+    if (done[i].k == kern && done[i].dev == dev && done[i].smem >= smem) return cudaSuccess;
+  e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+  if (e == cudaSuccess && used < 64) done[used++] = Entry{kern, dev, smem};
+  return e;
 }
 
 // Blocks that fit on the device at once for one kernel (cached per kernel and
@@ -113,8 +144,8 @@ __global__ void __launch_bounds__(kThreads, 3) k_stencil_staged(CellsDev c, cons
                                                              float *__restrict__ y, RedBuf rb, int fin,
                                                              int check_done, int zc, int ntiles) {
   if (check_done && *(volatile int *)&rb.st->done) return;
-  extern __shared__ __align__(16) float ring[];  // kStages slots of kSlot floats
-  __shared__ float tab[256][kTabStride];
+  extern __shared__ __align__(16) float ring[];  // kStages slots of kSlot floats, then the pattern tables
+  float(*tab)[kTabStride] = reinterpret_cast<float(*)[kTabStride]>(ring + kStages * kSlot);
   __shared__ short cellof[kMaxN];
   const int N = c.N;
   const int nbx = N / 32;
@@ -132,8 +163,8 @@ __global__ void __launch_bounds__(kThreads, 3) k_stencil_staged(CellsDev c, cons
 static cudaError_t launch_stencil_staged(const CellsDev &c, const float *x, float *y, RedBuf rb, int fin,
                                          bool check_done, cudaStream_t s) {
   const int N = c.N;
-  const size_t smem = (size_t)kStages * kSlot * sizeof(float);
-  const cudaError_t e = cudaFuncSetAttribute(k_stencil_staged, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+  const size_t smem = (size_t)kStages * kSlot * sizeof(float) + tab_bytes<float>(c.layers);
+  const cudaError_t e = allow_dynamic_smem((const void *)k_stencil_staged, smem);
   if (e != cudaSuccess) return e;
   const int ntiles = (N / 32) * (N / 32);
   const int resident = resident_blocks((const void *)k_stencil_staged, kThreads, smem);
@@ -194,11 +225,14 @@ static cudaError_t launch_stencil_mode(const CellsDev &c, int dir, const Ti *x, 
   const long long items =
       (long long)((N + 31) / 32) * ((N + 8 * RPT - 1) / (8 * RPT)) * ((N + zc - 1) / zc);
   auto kern = k_stencil<Ti, To, MODE, RPT>;
-  long long grid = resident_blocks((const void *)kern, kThreads, 0);
+  const size_t smem = tab_bytes<Ti>(c.layers);
+  const cudaError_t e = allow_dynamic_smem((const void *)kern, smem);
+  if (e != cudaSuccess) return e;
+  long long grid = resident_blocks((const void *)kern, kThreads, smem);
   if (grid <= 0) return cudaErrorInvalidConfiguration;
   if (grid > items) grid = items;
   if (grid > kMaxPartials) grid = kMaxPartials;
-  kern<<<(int)grid, dim3(32, 8, 1), 0, s>>>(c, dir, x, y, rb, fin, check_done ? 1 : 0, zc, (int)items);
+  kern<<<(int)grid, dim3(32, 8, 1), smem, s>>>(c, dir, x, y, rb, fin, check_done ? 1 : 0, zc, (int)items);
   return cudaGetLastError();
 }
 
@@ -244,7 +278,8 @@ template cudaError_t launch_stencil<double, float>(const CellsDev &, int, int, c
 __global__ void __launch_bounds__(kThreads) k_ahom(CellsDev c, const double *__restrict__ p0,
                                                    const double *__restrict__ p1, const double *__restrict__ p2,
                                                    RedBuf rb, int zc) {
-  __shared__ double tab[256][kTabStride];
+  extern __shared__ __align__(16) unsigned char dsm[];  // pattern tables, tab_bytes<double>(c.layers)
+  double(*tab)[kTabStride] = reinterpret_cast<double(*)[kTabStride]>(dsm);
   const int tid = threadIdx.x + 32 * threadIdx.y;
   build_pattern_table<double>(tab, c, tid);
   __syncthreads();
@@ -266,14 +301,20 @@ __global__ void __launch_bounds__(kThreads) k_ahom(CellsDev c, const double *__r
     // sub-cell inclusions: which of the four in-plane voxels may be high (load4's bit order)
     const bool i2a = in_sub(c, j2 - c2a * n), i2b = in_sub(c, j2m - c2b * n);
     const bool i3a = in_sub(c, j3 - c3a * n), i3b = in_sub(c, j3m - c3b * n);
-    const unsigned m23 = (i2a && i3a ? 1u : 0u) | (i2a && i3b ? 2u : 0u) | (i2b && i3a ? 4u : 0u) | (i2b && i3b ? 8u : 0u);
+    const unsigned m23 =
+        all_layers((i2a && i3a ? 1u : 0u) | (i2a && i3b ? 2u : 0u) | (i2b && i3a ? 4u : 0u) | (i2b && i3b ? 8u : 0u));
     const double *ps[3] = {p0, p1, p2};
     for (int j1 = z0; j1 < z1; ++j1) {
       const int j1m = (j1 == 0) ? N - 1 : j1 - 1, j1p = (j1 == N - 1) ? 0 : j1 + 1;
       const unsigned pm0 = in_sub(c, j1 - (j1 / n) * n) ? m23 : 0u, pm1 = in_sub(c, j1m - (j1m / n) * n) ? m23 : 0u;
-      const unsigned m = (load4(c.phase, j1 / n, LL, o00, o01, o10, o11) & pm0) |
-                         ((load4(c.phase, j1m / n, LL, o00, o01, o10, o11) & pm1) << 4);
-      const double a[3] = {tab[m][0], tab[m][2], tab[m][4]};
+      const unsigned b0 = load4(c.phase, j1 / n, LL, o00, o01, o10, o11) & pm0;
+      const unsigned b1 = load4(c.phase, j1m / n, LL, o00, o01, o10, o11) & pm1;
+      double a[3] = {0.0, 0.0, 0.0};
+      for (int l = 0; l < c.layers; ++l) {
+        const unsigned m = ((b0 >> (8 * l)) & 15u) | (((b1 >> (8 * l)) & 15u) << 4);
+#pragma unroll
+        for (int d = 0; d < 3; ++d) a[d] += tab[256 * l + m][2 * d];
+      }
       const size_t o = (size_t)j1 * NN + (size_t)j2 * N + j3;
       const size_t on[3] = {(size_t)j1p * NN + (size_t)j2 * N + j3, (size_t)j1 * NN + (size_t)j2p * N + j3,
                             (size_t)j1 * NN + (size_t)j2 * N + j3p};
@@ -325,7 +366,10 @@ cudaError_t launch_ahom(const CellsDev &c, const double *p0, const double *p1, c
   const int zc = ahom_zc(N);
   dim3 grid((N + 31) / 32, (N + 7) / 8, (N + zc - 1) / zc);
   if ((long long)grid.x * grid.y * grid.z > kMaxPartials) return cudaErrorInvalidConfiguration;
-  k_ahom<<<grid, dim3(32, 8, 1), 0, s>>>(c, p0, p1, p2, rb, zc);
+  const size_t smem = tab_bytes<double>(c.layers);
+  const cudaError_t e = allow_dynamic_smem((const void *)k_ahom, smem);
+  if (e != cudaSuccess) return e;
+  k_ahom<<<grid, dim3(32, 8, 1), smem, s>>>(c, p0, p1, p2, rb, zc);
   return cudaGetLastError();
 }
 

@@ -10,31 +10,44 @@ namespace sq {
 // Bit s1*4 + s2*2 + s3 of the pattern = phase of voxel (j1-s1, j2-s2, j3-s3).
 // Entries: 0 a_1(j), 1 a_1(j-e1), 2 a_2(j), 3 a_2(j-e2), 4 a_3(j), 5 a_3(j-e3),
 // 6 diagonal (sum of the six), 7.. unused (odd row stride: no bank conflicts
-// between nodes that see different patterns).
+// between nodes that see different patterns). Multi-level media keep one
+// 256-row table per threshold layer (rows l*256 + pattern; see CellsDev): the
+// pattern of layer l has the bit "voxel level >= l + 1" and the node's
+// coefficients are the sum of its layers' rows.
 constexpr int kTabStride = 9;
 template <typename T>
 __device__ __forceinline__ void build_pattern_table(T (*tab)[kTabStride], const CellsDev &c, int tid) {
   const unsigned face[6] = {0x0Fu, 0xF0u, 0x33u, 0xCCu, 0x55u, 0xAAu};
-  const T *ev = edge_table<T>(c);
-  const T *dv = diag_table<T>(c);
-  for (int m = tid; m < 256; m += kThreads) {
+  for (int row = tid; row < 256 * c.layers; row += kThreads) {
+    const int l = row >> 8, m = row & 255;
+    const T *ev = edge_table<T>(c, l);
+    const T *dv = diag_table<T>(c, l);
     int kk = 0;
 #pragma unroll
     for (int f = 0; f < 6; ++f) {
       const int k = __popc(m & face[f]);
-      tab[m][f] = ev[k];
+      tab[row][f] = ev[k];
       kk += k;
     }
-    tab[m][6] = dv[kk];
-    for (int f = 7; f < kTabStride; ++f) tab[m][f] = (T)0;
+    tab[row][6] = dv[kk];
+    for (int f = 7; f < kTabStride; ++f) tab[row][f] = (T)0;
   }
 }
 
-// Four phase bits of cell row c1 at the node's (s2, s3) cell offsets.
+// Layer bits of one phase byte v: bit 8l set iff v >= l + 1 (layers 0..2).
+// Two-level media read only bit 0, i.e. any nonzero phase is high.
+__device__ __forceinline__ unsigned level_bits(unsigned v) {
+  return (v != 0u ? 1u : 0u) | (v >= 2u ? 0x100u : 0u) | (v >= 3u ? 0x10000u : 0u);
+}
+// Replicates a mask of layer-0 bits into every layer's byte.
+__device__ __forceinline__ unsigned all_layers(unsigned m) { return m * 0x10101u; }
+
+// Four phase bits of cell row c1 at the node's (s2, s3) cell offsets, one
+// nibble per layer (bits 8l .. 8l+3).
 __device__ __forceinline__ unsigned load4(const uint8_t *__restrict__ phase, int c1, int LL, int o00, int o01,
                                           int o10, int o11) {
   const uint8_t *ph = phase + (size_t)c1 * LL;
-  return (ph[o00] ? 1u : 0u) | (ph[o01] ? 2u : 0u) | (ph[o10] ? 4u : 0u) | (ph[o11] ? 8u : 0u);
+  return level_bits(ph[o00]) | (level_bits(ph[o01]) << 1) | (level_bits(ph[o10]) << 2) | (level_bits(ph[o11]) << 3);
 }
 
 // Sub-cell inclusions: can the voxel at cell-local index u (one axis) be high?
@@ -71,26 +84,40 @@ __device__ __forceinline__ void plane_masks(const CellsDev &c, int cpos, unsigne
 // own cell at j3 / j3-1, bit 2 / 3 = the cell of row j2-1 at j3 / j3-1.
 // crow[q] = (cell of row j2b-1+q) * L.
 // mq[q]: in-plane inclusion mask of row q (bits 0 / 1: the voxel at j3 / j3-1
-// of that row may be high).
+// of that row may be high; the same bits in every layer's byte).
 template <int RPT>
 __device__ __forceinline__ void row_nibbles(const uint8_t *__restrict__ phase, int c1, int LL, const int (&crow)[RPT + 1],
                                             int c3a, int c3b, const unsigned (&mq)[RPT + 1], unsigned (&nb)[RPT]) {
   const uint8_t *ph = phase + (size_t)c1 * LL;
   unsigned b[RPT + 1];
 #pragma unroll
-  for (int q = 0; q <= RPT; ++q) b[q] = ((ph[crow[q] + c3a] ? 1u : 0u) | (ph[crow[q] + c3b] ? 2u : 0u)) & mq[q];
+  for (int q = 0; q <= RPT; ++q) b[q] = (level_bits(ph[crow[q] + c3a]) | (level_bits(ph[crow[q] + c3b]) << 1)) & mq[q];
 #pragma unroll
   for (int r = 0; r < RPT; ++r) nb[r] = b[r + 1] | (b[r] << 2);
 }
 
+// Coefficients of the RPT rows from their current (nc) and previous-plane
+// (np) nibbles: layer 0's table row, plus the higher layers' rows for
+// multi-level media (block-uniform branch on c.layers).
 template <typename Ti, int RPT>
-__device__ __forceinline__ void row_coeffs(const Ti (*tab)[kTabStride], const unsigned (&nc)[RPT],
+__device__ __forceinline__ void row_coeffs(const Ti (*tab)[kTabStride], int layers, const unsigned (&nc)[RPT],
                                            const unsigned (&np)[RPT], unsigned pm0, unsigned pm1, Ti (&t)[RPT][7]) {
 #pragma unroll
   for (int r = 0; r < RPT; ++r) {
     const Ti *tr = tab[(nc[r] & pm0) | ((np[r] & pm1) << 4)];
 #pragma unroll
     for (int k = 0; k < 7; ++k) t[r][k] = tr[k];
+  }
+#pragma unroll
+  for (int l = 1; l < kMaxLayers; ++l) {
+    if (l < layers) {
+#pragma unroll
+      for (int r = 0; r < RPT; ++r) {
+        const Ti *tr = tab[256 * l + ((((nc[r] >> (8 * l)) & pm0)) | (((np[r] >> (8 * l)) & pm1) << 4))];
+#pragma unroll
+        for (int k = 0; k < 7; ++k) t[r][k] += tr[k];
+      }
+    }
   }
 }
 
@@ -111,7 +138,7 @@ __device__ __forceinline__ void stencil_rows(const CellsDev &c, int dir, const T
   const int d3p = j3p - j3, d3m = j3m - j3;
   int crow[RPT + 1];
   unsigned mq[RPT + 1];  // in-plane inclusion masks (see row_nibbles)
-  const unsigned m3 = (in_sub(c, j3 - c3a * n) ? 1u : 0u) | (in_sub(c, j3m - c3b * n) ? 2u : 0u);
+  const unsigned m3 = all_layers((in_sub(c, j3 - c3a * n) ? 1u : 0u) | (in_sub(c, j3m - c3b * n) ? 2u : 0u));
 #pragma unroll
   for (int q = 0; q <= RPT; ++q) {
     const int j2 = (j2b - 1 + q < 0) ? N - 1 : j2b - 1 + q;  // rows j2b .. j2b+RPT-1 are < N
@@ -134,7 +161,7 @@ __device__ __forceinline__ void stencil_rows(const CellsDev &c, int dir, const T
   }
   plane_masks(c, cpos, pm0, pm1);
   Ti t[RPT][7];
-  row_coeffs<Ti, RPT>(tab, nc, np, pm0, pm1, t);
+  row_coeffs<Ti, RPT>(tab, c.layers, nc, np, pm0, pm1, t);
 
   Ti xm[RPT], x0[RPT], ahead[RPT][kAhead];  // ahead[r][u] = x(jb + 1 + u) of row r
 #pragma unroll
@@ -173,7 +200,7 @@ __device__ __forceinline__ void stencil_rows(const CellsDev &c, int dir, const T
             }
             if (cpos == 0) row_nibbles<RPT>(c.phase, cellof[j1], LL, crow, c3a, c3b, mq, nc);
             plane_masks(c, cpos, pm0, pm1);
-            row_coeffs<Ti, RPT>(tab, nc, np, pm0, pm1, t);
+            row_coeffs<Ti, RPT>(tab, c.layers, nc, np, pm0, pm1, t);
           }
         }
         const int b0 = j1 * NN + row0;
@@ -340,7 +367,7 @@ __device__ __forceinline__ void stencil_staged_run(const CellsDev &c, const floa
   const int c3a = cellof[j3], c3b = cellof[j3m];
   int crow[5];
   unsigned mq[5];  // in-plane inclusion masks (see row_nibbles)
-  const unsigned m3 = (in_sub(c, j3 - c3a * n) ? 1u : 0u) | (in_sub(c, j3m - c3b * n) ? 2u : 0u);
+  const unsigned m3 = all_layers((in_sub(c, j3 - c3a * n) ? 1u : 0u) | (in_sub(c, j3m - c3b * n) ? 2u : 0u));
 #pragma unroll
   for (int q = 0; q <= 4; ++q) {
     const int j2 = (j2b - 1 + q < 0) ? N - 1 : j2b - 1 + q;
@@ -359,7 +386,7 @@ __device__ __forceinline__ void stencil_staged_run(const CellsDev &c, const floa
   }
   plane_masks(c, cpos, pm0, pm1);
   float t[4][7];
-  row_coeffs<float, 4>(tab, nc, np, pm0, pm1, t);
+  row_coeffs<float, 4>(tab, c.layers, nc, np, pm0, pm1, t);
   const int row0 = j2b * N + j3;
   float xm[4], x0[4];
 #pragma unroll
@@ -385,7 +412,7 @@ __device__ __forceinline__ void stencil_staged_run(const CellsDev &c, const floa
         }
         if (cpos == 0) row_nibbles<4>(c.phase, cellof[j1], LL, crow, c3a, c3b, mq, nc);
         plane_masks(c, cpos, pm0, pm1);
-        row_coeffs<float, 4>(tab, nc, np, pm0, pm1, t);
+        row_coeffs<float, 4>(tab, c.layers, nc, np, pm0, pm1, t);
       }
     }
     const float *S0 = ring + s0 * kSlot + (1 + 4 * ty) * kSW + 4 + tx;

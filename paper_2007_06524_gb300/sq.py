@@ -77,6 +77,10 @@ def load_library():
         "sq_coeffs_shape": (i, [vp, p(i), p(i), p(i)]),
         "sq_coeffs_destroy": (None, [vp]),
         "sq_coeffs_set_subcell": (i, [vp, i]),
+        "sq_coeffs_set_levels": (i, [vp, i, vp]),
+        "sq_build_coeffs_levels": (i, [i, i, u64, i, vp, vp, vp, p(vp)]),
+        "sq_coeffs_regenerate_levels": (i, [vp, u64, i, vp, vp]),
+        "sq_coeffs_from_host_levels": (i, [i, i, vp, i, vp, vp, p(vp)]),
         "sq_precond_setup": (i, [i, i, p(vp)]),
         "sq_precond_destroy": (None, [vp]),
         "sq_precond_factors": (i, [vp, vp, vp]),
@@ -210,13 +214,63 @@ def sq_coeffs_set_subcell(c: Coeffs, sub: int):
     _check(load_library().sq_coeffs_set_subcell(c, int(sub)), "sq_coeffs_set_subcell")
 
 
+def _f64_array(vals, name):
+    arr = np.ascontiguousarray(np.asarray(vals, dtype=np.float64).ravel())
+    if arr.size < 2 or arr.size > 4:
+        raise ValueError(f"{name}: 2 to 4 levels")
+    return arr
+
+
+def sq_coeffs_set_levels(c: Coeffs, values):
+    """Multi-level medium: phase byte v reads level min(v, K-1) with value
+    values[level] (K = len(values), 2..4); voxels outside the inclusion cube
+    take values[0]."""
+    arr = _f64_array(values, "values")
+    _check(load_library().sq_coeffs_set_levels(c, int(arr.size), arr.ctypes.data_as(C.c_void_p)),
+           "sq_coeffs_set_levels")
+
+
+def sq_build_coeffs_levels(L, n, seed, probs, values, stream=None) -> Coeffs:
+    """K-level cells drawn with probabilities probs (nested thresholds on the
+    SplitMix64 stream of sq_build_coeffs) and coefficient values `values`."""
+    pa, va = _f64_array(probs, "probs"), _f64_array(values, "values")
+    if pa.size != va.size:
+        raise ValueError("probs and values must have the same length")
+    out = C.c_void_p()
+    _check(load_library().sq_build_coeffs_levels(int(L), int(n), int(seed) & (2**64 - 1), int(pa.size),
+                                                 pa.ctypes.data_as(C.c_void_p), va.ctypes.data_as(C.c_void_p),
+                                                 _stream(stream), C.byref(out)), "sq_build_coeffs_levels")
+    return Coeffs(out)
+
+
+def sq_coeffs_from_host_levels(L, n, host_level, values, stream=None) -> Coeffs:
+    """K-level handle from L^3 host cell levels (bytes >= K read as K - 1)."""
+    arr = np.ascontiguousarray(host_level, dtype=np.uint8)
+    if arr.size != L ** 3:
+        raise ValueError("host_level must hold L^3 bytes")
+    va = _f64_array(values, "values")
+    out = C.c_void_p()
+    _check(load_library().sq_coeffs_from_host_levels(int(L), int(n), arr.ctypes.data_as(C.c_void_p), int(va.size),
+                                                     va.ctypes.data_as(C.c_void_p), _stream(stream), C.byref(out)),
+           "sq_coeffs_from_host_levels")
+    return Coeffs(out)
+
+
+def sq_coeffs_regenerate_levels(c: Coeffs, seed, probs, stream=None):
+    pa = _f64_array(probs, "probs")
+    _check(load_library().sq_coeffs_regenerate_levels(c, int(seed) & (2**64 - 1), int(pa.size),
+                                                      pa.ctypes.data_as(C.c_void_p), _stream(stream)),
+           "sq_coeffs_regenerate_levels")
+
+
 def sq_coeffs_regenerate(c: Coeffs, seed, p_hi, stream=None):
     _check(load_library().sq_coeffs_regenerate(c, int(seed) & (2**64 - 1), float(p_hi), _stream(stream)),
            "sq_coeffs_regenerate")
 
 
 def sq_coeffs_upload(c: Coeffs, host_phase, stream=None):
-    """host_phase: a PINNED torch uint8 CPU tensor of L^3 values in {0, 1}."""
+    """host_phase: a PINNED torch uint8 CPU tensor of L^3 phases (0 / 1, or the
+    cell levels of a multi-level handle)."""
     if host_phase.is_cuda or not host_phase.is_pinned() or str(host_phase.dtype) != "torch.uint8":
         raise ValueError("expected a pinned uint8 CPU tensor")
     _check(load_library().sq_coeffs_upload(c, C.c_void_p(host_phase.data_ptr()), _stream(stream)),
