@@ -10,7 +10,9 @@
 // value of its cell, so the eight voxels around a node -- one bit each, read
 // from the L^3 phase array -- fix all six edge coefficients of that node. A
 // 256-entry table per block maps this 8-bit pattern to the six coefficients
-// and the diagonal; no N^3 coefficient field exists.
+// and the diagonal; no N^3 coefficient field exists. Multi-level media (K
+// coefficient levels) add one table per extra threshold layer; the node's
+// coefficients are the sum of its layers' rows (see CellsDev).
 //
 // RHS (Eq. 8 in grid units): b_dir(j) = a_dir(j) - a_dir(j - e_dir).
 #include <mutex>
