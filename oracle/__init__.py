@@ -19,6 +19,9 @@ coefficients", arXiv 2007.06524) by eye:
                       core tensor G^+ (Eqs. 32-33), its rank-R canonical
                       approximation (Eq. 34, Lemma 4.2) and the FFT apply
                       (Eq. 31).
+* ``tucker``       -- the paper's Tucker route to the canonical factors
+                      (HOSVD of G^+, Tucker-to-canonical, Sec. 4.2) and the
+                      2R+1 split of Lemma 4.2.
 * ``pcg``          -- CG / PCG on the zero-mean subspace (Eqs. 24-25) and the
                       tight / dense reference solves.
 * ``homogenized``  -- the homogenized matrix (Eqs. 21-23).
