@@ -357,6 +357,7 @@ def run_native(args):
         out["variants"]["ensemble"] = run_ensemble(sq, torch)
         out["variants"]["inclusions_alpha_quarter"] = run_inclusions(sq, torch, stream)
         out["variants"]["two_contrasts_alpha_quarter"] = run_two_contrasts(sq, torch, stream)
+        out["variants"]["precond_routes_n256"] = run_precond_routes(sq, torch, stream)
 
     if rank == 0 and not args.no_cpu_baseline and ws == 1:
         out["cpu_baseline"] = cpu_baseline(statistics.mean(iters), R)
@@ -530,6 +531,58 @@ def run_two_contrasts(sq, torch, stream):
             res[f"{kind}_{label}"] = {"solves_per_s": round(6 / t, 3), "iters_mean": round(float(np.mean(its)), 1),
                                       "converged": ok,
                                       "A_hom_diag": [round(float(v), 6) for v in np.mean([np.diag(A) for A in As], 0)]}
+    return res
+
+
+def run_precond_routes(sq, torch, stream):
+    """Canonical preconditioners on the headline workload (L = 32, n = 8,
+    N = 256, Bernoulli(1/2) on {1, 100}, FP64 PCG to 1e-8, three correctors):
+    the exponential sum (rank 8), the same sum written as the 2R + 1 terms of
+    Lemma 4.2 (without the mean projection's shortcut), and the paper's route
+    (Sec. 4.2): HOSVD of G+ with Tucker rank r, then Tucker-to-canonical with
+    core-slice eigenvalues below tol * max dropped. Per route: canonical
+    rank, max relative error of the preconditioner over the nonzero modes,
+    host setup time, iterations, solves/s."""
+    import numpy as np
+
+    L, n, N = 32, 8, 256
+    c = sq.sq_build_coeffs(L, n, 0, 0.5, 1.0, 100.0)
+    w = sq.sq_workspace_create(N, sq.SQ_FP64)
+    psi = torch.empty(N ** 3, dtype=torch.float64, device="cuda")
+
+    def split_factors(pc, R):
+        t, wts = sq.sq_precond_factors(pc, R)
+        lam = 4.0 * np.sin(np.pi * np.arange(N) / N) ** 2
+        E = np.exp(-np.outer(t, lam))
+        d0 = np.zeros(N)
+        d0[0] = 1.0
+        F1 = np.vstack([wts[:, None] * E, wts[:, None] * d0, [-wts.sum() * d0]])
+        F1[:R, 0] = 0.0
+        F23 = np.vstack([E, E, [d0]])
+        return F1, F23, F23
+
+    routes = [("expsum_r8", lambda: sq.sq_precond_setup(N, 8)),
+              ("lemma_split_r8", lambda: sq.sq_precond_setup_canonical(N, *split_factors(sq.sq_precond_setup(N, 8), 8))),
+              ("tucker_r8", lambda: sq.sq_precond_setup_tucker(N, 8, 0.0)),
+              ("tucker_r10_tol1e-4", lambda: sq.sq_precond_setup_tucker(N, 10, 1e-4)),
+              ("tucker_r12", lambda: sq.sq_precond_setup_tucker(N, 12, 0.0))]
+    res = {}
+    for name, make in routes:
+        t0 = time.perf_counter()
+        pc = make()
+        setup_s = time.perf_counter() - t0
+        R, err = sq.sq_precond_info(pc)
+        sq.sq_pcg_solve(c, pc, w, 0, 1e-8, 2000, sq.SQ_FP64, None, psi)  # warm-up
+        torch.cuda.synchronize()
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        infos = [sq.sq_pcg_solve(c, pc, w, i, 1e-8, 2000, sq.SQ_FP64, None, psi) for i in range(3)]
+        e1.record(stream)
+        torch.cuda.synchronize()
+        t = e0.elapsed_time(e1) / 1e3
+        res[name] = {"rank": R, "max_rel_err": float(f"{err:.4g}"), "setup_s": round(setup_s, 3),
+                     "iters_mean": round(float(np.mean([i["iters"] for i in infos])), 1),
+                     "solves_per_s": round(3 / t, 3), "converged": all(i["status"] == sq.SQ_OK for i in infos)}
     return res
 
 

@@ -159,8 +159,40 @@ void sq_coeffs_destroy(sq_coeffs *c);
  * current device (synchronous). */
 int sq_precond_setup(int N, int rank, sq_precond **out);
 /* The exponential-sum nodes t[r] and weights w[r], r < rank (host arrays,
- * either may be NULL; nothing is written for rank 0). */
+ * either may be NULL; nothing is written for rank 0). SQ_EINVAL for a
+ * preconditioner that is not an exponential sum. */
 int sq_precond_factors(const sq_precond *p, double *t, double *w);
+
+/* A rank-R canonical preconditioner from given factors (Sec. 4.2, Eq. 34 in
+ * general form): G(k1,k2,k3) = sum_r f1[r N + k1] f2[r N + k2] f3[r N + k3]
+ * on every nonzero mode (k1 on the slowest grid axis x1), G(0,0,0) = 0. f1,
+ * f2, f3: HOST arrays of R x N doubles, read during the call; f2 or f3 NULL
+ * repeats f1. Every factor row must be even, f[r N + k] = f[r N + N - k]
+ * (within 1e-12 of the row's largest entry): G is then a function of the
+ * per-axis eigenvalues l_k, the class the separable Hartley transform
+ * diagonalises. 1 <= R <= 256; SQ_EINVAL otherwise (N as for
+ * sq_precond_setup). Synchronous, like sq_precond_setup. */
+int sq_precond_setup_canonical(int N, int R, const double *f1, const double *f2, const double *f3,
+                               sq_precond **out);
+
+/* The paper's construction of the canonical factors (Sec. 4.2): a Tucker
+ * decomposition of G+ with multilinear rank (r, r, r) -- the higher-order
+ * SVD (De Lathauwer, De Moor & Vandewalle 2000; the paper computes it with a
+ * multigrid acceleration), which for the symmetric G+ uses one even factor
+ * for all modes -- then Tucker-to-canonical: each mode-3 slice of the r^3
+ * core is eigen-decomposed, giving up to r^2 terms sigma (U e) (x) (U e) (x)
+ * U[:, c]; terms with |sigma| <= tol * max|sigma| are dropped (tol = 0 keeps
+ * all r^2 and reproduces the Tucker tensor). 1 <= r <= min(N/2 + 1, 64),
+ * 0 <= tol < 1, and the resulting rank must be <= 256; SQ_EINVAL otherwise.
+ * Host-side FP64 setup (O(N^4 / 16) flops for the Gram matrix), then
+ * synchronous upload. */
+int sq_precond_setup_tucker(int N, int r, double tol, sq_precond **out);
+
+/* Canonical rank of p (0 for the exact diagonal) and max over the nonzero
+ * modes of |(l_k1 + l_k2 + l_k3) G(k) - 1| (the preconditioner's relative
+ * error; 0 for the exact diagonal). Either output may be NULL; the error is
+ * evaluated on the host in O(R N^3 / 8). */
+int sq_precond_info(const sq_precond *p, int *rank, double *max_rel_err);
 void sq_precond_destroy(sq_precond *p);
 
 /* Scratch fields for one solve at grid N and the given precision (device

@@ -7,6 +7,8 @@
 #include <cuda_runtime.h>
 #include <stdint.h>
 
+#include <vector>
+
 #include "sq.h"
 
 namespace sq {
@@ -15,7 +17,8 @@ constexpr int kThreads = 256;        // block size of every field kernel
 constexpr int kMaxPartials = 16384;  // max blocks of a reducing kernel
 constexpr int kMaxQ = 24;            // max quantities reduced by one kernel
 constexpr int kMaxN = 512;
-constexpr int kMaxRank = 64;
+constexpr int kMaxRank = 256;    // canonical terms of a preconditioner from given factors
+constexpr int kMaxExpRank = 64;  // terms of the exponential-sum preconditioner
 
 // Device-resident solver scalars. Written only by the last block of a
 // reducing kernel (or by the host before a solve), read by later kernels.
@@ -362,7 +365,11 @@ struct SpectralDev {
   int radix[12];
   const void *tw;    // N complex twiddles exp(-2 pi i m / N), type Cx<T>
   const void *lam;   // N eigenvalues lambda_k (T)
-  const void *u;     // rank x N scaled factors (T), u_r(k) * (64 N^3)^(-1/3)
+  // canonical factors (T), 3 x rank x N: the x1, x2 and x3 factors of term r
+  // at u + (a rank + r) N, a = 0, 1, 2, each scaled by (64 N^3)^(-1/3), so
+  // that G(k1,k2,k3) = sum_r u1_r(k1) u2_r(k2) u3_r(k3). Every factor is even
+  // (u(k) = u(N - k)): G is then diagonal in the separable Hartley basis.
+  const void *u;
   double scale;      // 1 / (64 N^3) for the exact diagonal
 };
 enum DhtPass : int { PASS_A_RESID = 0, PASS_A_PLAIN = 1, PASS_B = 2, PASS_C = 3, PASS_E_PCG = 4, PASS_E_PLAIN = 5 };
@@ -381,5 +388,11 @@ int set_strided_fast(int on);  // 0: generic Stockham tiles for every pass
 // solver.cu: read-only views of the opaque handles (used by batch.cu)
 int coeffs_view(const sq_coeffs *c, CellsDev *out);
 int precond_spec32(const sq_precond *p, SpectralDev *out, int *N);
+// Grid sizes the solver supports: 8 <= N <= 512, N even, N = 2^a 3^b, b <= 1.
+bool grid_size_ok(int N);
+// solver.cu: a preconditioner from host factors f (3 x R x N, unscaled; R = 0:
+// the exact diagonal) and, for an exponential sum, its nodes and weights.
+int precond_create(int N, int R, const double *f, const std::vector<double> &t, const std::vector<double> &w,
+                   sq_precond **out);
 
 }  // namespace sq

@@ -275,9 +275,11 @@ __device__ __forceinline__ void dht_tile(const SpectralDev &sp, const DhtTile<T>
       buf0[j * SP + p] = reinterpret_cast<const C *>(a.in)[g >> 1];
     }
     if (SCALE && R > 0) {
+      // x2 factors at uf + R N, x3 factors at uf + 2 R N (see SpectralDev)
+      const T *u2 = uf + (size_t)R * N, *u3 = uf + 2 * (size_t)R * N;
       for (int e = tid; e < R * 2 * P; e += kThreads) {
         const int rr = e / (2 * P), w = e - rr * 2 * P;
-        vtab[e] = uf[rr * N + k2] * uf[rr * N + c0 + w];
+        vtab[e] = u2[rr * N + k2] * u3[rr * N + c0 + w];
       }
     }
   }
@@ -544,9 +546,10 @@ __device__ __forceinline__ void dht_tile_s2(const SpectralDev &sp, const DhtTile
   __syncthreads();
   if (SCALE && RR != 0) {
     const T *uf = reinterpret_cast<const T *>(sp.u);
+    const T *u2 = uf + (size_t)sp.rank * N, *u3 = uf + 2 * (size_t)sp.rank * N;  // x2, x3 factors
     for (int e = threadIdx.x; e < sp.rank * 2 * P; e += kThreads) {
       const int rr = e / (2 * P), w = e - rr * 2 * P;
-      vtab[e] = uf[rr * N + k2] * uf[rr * N + c0 + w];
+      vtab[e] = u2[rr * N + k2] * u3[rr * N + c0 + w];
     }
   }
   const C *gin = reinterpret_cast<const C *>(a.in);

@@ -40,7 +40,8 @@ struct sq_coeffs {
 
 struct sq_precond {
   int N, rank;
-  std::vector<double> t, w;  // exponential-sum nodes and weights (rank > 0)
+  std::vector<double> t, w;  // exponential-sum nodes and weights (empty for other factors)
+  std::vector<double> f;     // host factors, 3 x rank x N (unscaled; see precond_create)
   SpectralDev sp64, sp32;
   void *d_mem;
 };
@@ -577,6 +578,7 @@ int apply_precond_t(const sq_precond *pc, sq_workspace *w, const T *r, T *z, T *
 }  // namespace
 
 namespace sq {
+bool grid_size_ok(int N) { return valid_N(N); }
 int coeffs_view(const sq_coeffs *c, CellsDev *out) {
   if (!c || !out) return SQ_EINVAL;
   *out = cells_dev(c);
@@ -841,12 +843,21 @@ void sq_coeffs_destroy(sq_coeffs *c) {
   delete c;
 }
 
-int sq_precond_setup(int N, int rank, sq_precond **out) {
+}  // extern "C"
+
+namespace sq {
+
+// Uploads a preconditioner: rank R >= 0 canonical terms with the host
+// factors f (3 x R x N, axis a of term r at f + (a R + r) N; unscaled, so
+// that G(k) = sum_r f1_r(k1) f2_r(k2) f3_r(k3)); R = 0 is the exact diagonal.
+// t, w: the exponential-sum nodes and weights when the factors come from one.
+int precond_create(int N, int R, const double *f, const std::vector<double> &t, const std::vector<double> &w,
+                   sq_precond **out) {
   if (!out) return SQ_EINVAL;
   *out = nullptr;
-  if (!valid_N(N) || rank < 0 || rank == 1 || rank > kMaxRank) return SQ_EINVAL;
+  if (!valid_N(N) || R < 0 || R > kMaxRank || (R > 0 && !f)) return SQ_EINVAL;
   const double pi = 3.14159265358979323846;
-  std::vector<double> tw64(2 * N), lam64(N), u64((size_t)(rank > 0 ? rank : 1) * N, 0.0);
+  std::vector<double> tw64(2 * N), lam64(N), u64((size_t)3 * (R > 0 ? R : 1) * N, 0.0);
   for (int m = 0; m < N; ++m) {
     const double ang = 2.0 * pi * m / N;
     tw64[2 * m] = std::cos(ang);
@@ -854,15 +865,8 @@ int sq_precond_setup(int N, int rank, sq_precond **out) {
     const double sn = std::sin(pi * m / N);
     lam64[m] = 4.0 * sn * sn;
   }
-  std::vector<double> t, w;
-  if (rank > 0) {
-    rank_r_nodes(N, rank, t, w);
-    const double fold = 1.0 / (4.0 * N);  // (64 N^3)^(-1/3)
-    for (int r = 0; r < rank; ++r) {
-      const double wr = std::cbrt(w[r]) * fold;
-      for (int k = 0; k < N; ++k) u64[(size_t)r * N + k] = wr * std::exp(-t[r] * lam64[k]);
-    }
-  }
+  const double fold = 1.0 / (4.0 * N);  // (64 N^3)^(-1/3)
+  for (size_t i = 0; i < (size_t)3 * R * N; ++i) u64[i] = f[i] * fold;
   std::vector<float> tw32(2 * N), lam32(N), u32(u64.size());
   for (size_t i = 0; i < tw64.size(); ++i) tw32[i] = (float)tw64[i];
   for (int i = 0; i < N; ++i) lam32[i] = (float)lam64[i];
@@ -871,9 +875,10 @@ int sq_precond_setup(int N, int rank, sq_precond **out) {
   sq_precond *pc = new (std::nothrow) sq_precond();
   if (!pc) return SQ_ENOMEM;
   pc->N = N;
-  pc->rank = rank;
+  pc->rank = R;
   pc->t = t;
   pc->w = w;
+  if (R > 0) pc->f.assign(f, f + (size_t)3 * R * N);
   const size_t b_tw64 = tw64.size() * 8, b_lam64 = lam64.size() * 8, b_u64 = u64.size() * 8;
   const size_t b_tw32 = tw32.size() * 4, b_lam32 = lam32.size() * 4, b_u32 = u32.size() * 4;
   auto al = [](size_t b) { return (b + 255) & ~(size_t)255; };
@@ -901,7 +906,7 @@ int sq_precond_setup(int N, int rank, sq_precond **out) {
   SpectralDev sp;
   std::memset(&sp, 0, sizeof(sp));
   sp.N = N;
-  sp.rank = rank;
+  sp.rank = R;
   sp.nst = radix_plan(N, sp.radix);
   sp.scale = 1.0 / (64.0 * (double)N * N * N);
   pc->sp64 = sp;
@@ -913,6 +918,68 @@ int sq_precond_setup(int N, int rank, sq_precond **out) {
   pc->sp32.lam = p_lam32;
   pc->sp32.u = p_u32;
   *out = pc;
+  return SQ_OK;
+}
+
+}  // namespace sq
+
+extern "C" {
+
+int sq_precond_setup(int N, int rank, sq_precond **out) {
+  if (!out) return SQ_EINVAL;
+  *out = nullptr;
+  if (!valid_N(N) || rank < 0 || rank == 1 || rank > kMaxExpRank) return SQ_EINVAL;
+  std::vector<double> t, w, f;
+  if (rank > 0) {
+    // the same exponential-sum factor u_r(k) = w_r^(1/3) exp(-t_r lambda_k) on every axis
+    rank_r_nodes(N, rank, t, w);
+    f.resize((size_t)3 * rank * N);
+    for (int r = 0; r < rank; ++r) {
+      const double wr = std::cbrt(w[r]);
+      for (int k = 0; k < N; ++k) {
+        const double sn = std::sin(3.14159265358979323846 * k / N);
+        const double v = wr * std::exp(-t[r] * 4.0 * sn * sn);
+        for (int a = 0; a < 3; ++a) f[((size_t)a * rank + r) * N + k] = v;
+      }
+    }
+  }
+  return precond_create(N, rank, f.data(), t, w, out);
+}
+
+// max over nonzero modes of |g G(k) - 1|, g = lambda_k1 + lambda_k2 +
+// lambda_k3, over k in [0, N/2]^3 (every factor is even).
+static double precond_max_rel_err(const sq_precond *p) {
+  const int N = p->N, M = N / 2 + 1, R = p->rank;
+  std::vector<double> lam(M);
+  for (int m = 0; m < M; ++m) {
+    const double sn = std::sin(3.14159265358979323846 * m / N);
+    lam[m] = 4.0 * sn * sn;
+  }
+  double worst = 0.0;
+  std::vector<double> v23((size_t)R);
+  for (int k2 = 0; k2 < M; ++k2)
+    for (int k3 = 0; k3 < M; ++k3) {
+      for (int r = 0; r < R; ++r)
+        v23[r] = p->f[((size_t)1 * R + r) * N + k2] * p->f[((size_t)2 * R + r) * N + k3];
+      for (int k1 = 0; k1 < M; ++k1) {
+        const double g = lam[k1] + lam[k2] + lam[k3];
+        if (!(g > 0.0)) continue;
+        double G = 0.0;
+        if (R == 0) {
+          G = 1.0 / g;
+        } else {
+          for (int r = 0; r < R; ++r) G += p->f[(size_t)r * N + k1] * v23[r];
+        }
+        worst = std::max(worst, std::fabs(g * G - 1.0));
+      }
+    }
+  return worst;
+}
+
+int sq_precond_info(const sq_precond *p, int *rank, double *max_rel_err) {
+  if (!p) return SQ_EINVAL;
+  if (rank) *rank = p->rank;
+  if (max_rel_err) *max_rel_err = precond_max_rel_err(p);
   return SQ_OK;
 }
 
@@ -942,7 +1009,7 @@ int sq_set_option(int key, int value) {
 }
 
 int sq_precond_factors(const sq_precond *p, double *t, double *w) {
-  if (!p) return SQ_EINVAL;
+  if (!p || (int)p->t.size() != p->rank) return SQ_EINVAL;  // not an exponential sum
   for (int r = 0; r < p->rank; ++r) {
     if (t) t[r] = p->t[r];
     if (w) w[r] = p->w[r];

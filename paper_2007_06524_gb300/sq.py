@@ -84,6 +84,9 @@ def load_library():
         "sq_precond_setup": (i, [i, i, p(vp)]),
         "sq_precond_destroy": (None, [vp]),
         "sq_precond_factors": (i, [vp, vp, vp]),
+        "sq_precond_setup_canonical": (i, [i, i, vp, vp, vp, p(vp)]),
+        "sq_precond_setup_tucker": (i, [i, i, d, p(vp)]),
+        "sq_precond_info": (i, [vp, p(i), p(d)]),
         "sq_workspace_create": (i, [i, i, p(vp)]),
         "sq_workspace_destroy": (None, [vp]),
         "sq_pcg_solve": (i, [vp, vp, vp, i, d, i, i, vp, vp, p(SolveInfo), vp]),
@@ -324,6 +327,37 @@ def sq_precond_setup(N, rank) -> Precond:
     out = C.c_void_p()
     _check(load_library().sq_precond_setup(int(N), int(rank), C.byref(out)), "sq_precond_setup")
     return Precond(out)
+
+
+def sq_precond_setup_canonical(N, f1, f2=None, f3=None) -> Precond:
+    """Canonical preconditioner from host factors, each (R, N) FP64 with even
+    rows; f2 / f3 None repeat f1."""
+    arrs = [None if f is None else np.ascontiguousarray(np.asarray(f, dtype=np.float64)) for f in (f1, f2, f3)]
+    R = arrs[0].shape[0]
+    for a in arrs:
+        if a is not None and a.shape != (R, N):
+            raise ValueError("factors must have shape (R, N)")
+    ptrs = [None if a is None else a.ctypes.data_as(C.c_void_p) for a in arrs]
+    out = C.c_void_p()
+    _check(load_library().sq_precond_setup_canonical(int(N), int(R), ptrs[0], ptrs[1], ptrs[2], C.byref(out)),
+           "sq_precond_setup_canonical")
+    return Precond(out)
+
+
+def sq_precond_setup_tucker(N, r, tol=0.0) -> Precond:
+    """The paper's route: HOSVD of G+ with rank r, then Tucker-to-canonical
+    dropping core-slice eigenvalues at or below tol * max."""
+    out = C.c_void_p()
+    _check(load_library().sq_precond_setup_tucker(int(N), int(r), float(tol), C.byref(out)),
+           "sq_precond_setup_tucker")
+    return Precond(out)
+
+
+def sq_precond_info(pc: Precond):
+    """(canonical rank, max relative error over the nonzero modes)."""
+    R, e = C.c_int(), C.c_double()
+    _check(load_library().sq_precond_info(pc, C.byref(R), C.byref(e)), "sq_precond_info")
+    return R.value, e.value
 
 
 def sq_precond_factors(pc: Precond, rank: int):
