@@ -25,6 +25,8 @@ coefficients", arXiv 2007.06524) by eye:
 * ``pcg``          -- CG / PCG on the zero-mean subspace (Eqs. 24-25) and the
                       tight / dense reference solves.
 * ``homogenized``  -- the homogenized matrix (Eqs. 21-23).
+* ``solver2d``     -- the 2D corrector problem of the paper's 2D experiments
+                      (node scheme, 2D preconditioner, PCG, 2 x 2 A_hom).
 * ``dual2d``       -- an independent 2D cell-centred scheme used only to pin the
                       node scheme through discrete Keller duality.
 
