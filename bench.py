@@ -358,6 +358,7 @@ def run_native(args):
         out["variants"]["inclusions_alpha_quarter"] = run_inclusions(sq, torch, stream)
         out["variants"]["two_contrasts_alpha_quarter"] = run_two_contrasts(sq, torch, stream)
         out["variants"]["precond_routes_n256"] = run_precond_routes(sq, torch, stream)
+        out["variants"]["table_2d_alpha_quarter"] = run_2d_table(sq, torch, stream)
 
     if rank == 0 and not args.no_cpu_baseline and ws == 1:
         out["cpu_baseline"] = cpu_baseline(statistics.mean(iters), R)
@@ -583,6 +584,42 @@ def run_precond_routes(sq, torch, stream):
         res[name] = {"rank": R, "max_rel_err": float(f"{err:.4g}"), "setup_s": round(setup_s, 3),
                      "iters_mean": round(float(np.mean([i["iters"] for i in infos])), 1),
                      "solves_per_s": round(3 / t, 3), "converged": all(i["status"] == sq.SQ_OK for i in infos)}
+    return res
+
+
+def run_2d_table(sq, torch, stream):
+    """The paper's 2D experiment (Sec. 5, its tables of 2D solve times): n0 = 4
+    grid intervals per cell, alpha = 1/4 inclusions (a centred 2 x 2 voxel
+    square per cell), lambda = 0.4 (a in {0.4, 1.0}), Bernoulli(1/2) cells,
+    L = 64 .. 512 (N = 256 .. 2048), FP64 PCG to 1e-8 with the exact and the
+    rank-8 preconditioner, both correctors + A_hom of one realization (seed
+    0). Per L: ms per corrector solve, iterations, and A_hom[0, 0]."""
+    import numpy as np
+
+    res = {}
+    for L in (64, 128, 256, 512):
+        n = 4
+        N = L * n
+        c = sq.sq2d_build_coeffs(L, n, 0, 0.5, 0.4, 1.0)
+        sq.sq2d_coeffs_set_subcell(c, 2)
+        w = sq.sq2d_workspace_create(N)
+        psis = [torch.empty(N * N, dtype=torch.float64, device="cuda") for _ in range(2)]
+        row = {}
+        for rank in (0, 8):
+            pc = sq.sq2d_precond_setup(N, rank)
+            sq.sq2d_pcg_solve(c, pc, w, 0, 1e-8, 3000, psis[0])  # warm-up
+            torch.cuda.synchronize()
+            e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            e0.record(stream)
+            infos = [sq.sq2d_pcg_solve(c, pc, w, i, 1e-8, 3000, psis[i]) for i in range(2)]
+            H, _ = sq.sq2d_homogenized_matrix(c, *psis)
+            e1.record(stream)
+            torch.cuda.synchronize()
+            ms = e0.elapsed_time(e1)
+            row[f"rank{rank}"] = {"ms_per_solve": round(ms / 2, 3), "iters": [i["iters"] for i in infos],
+                                  "converged": all(i["status"] == sq.SQ_OK for i in infos),
+                                  "A_hom_00": round(float(H[0, 0]), 6)}
+        res[f"L{L}_N{N}"] = row
     return res
 
 

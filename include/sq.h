@@ -387,6 +387,61 @@ const char *sq_profile_class_name(int k);
 
 const char *sq_strerror(int status);
 
+/* ------------------------------------------------------------------ 2D
+ * The 2D corrector problem of the paper's 2D experiments (Sec. 5): the same
+ * method on an N x N periodic grid, N = L n with 8 <= N <= 2048, N even,
+ * N = 2^a 3^b with b <= 1 (x2 contiguous, index j2 + N j1), two correctors
+ * psi_1, psi_2 and the 2 x 2 A_hom; FP64 throughout.
+ * - Cells: cell (c1, c2) of the L x L lattice is high iff the top 53 bits of
+ *   SplitMix64 output number c2 + L c1 (the rule of sq_build_coeffs on its
+ *   slab c1 = 0) are below floor(p_hi 2^53). Sub-cell inclusions: a centred
+ *   square of side `sub` grid intervals per cell (sq2d_coeffs_set_subcell).
+ * - Operator: sum_d D_d^T diag(a_d) D_d with a_d(j) the mean of the two
+ *   voxels beside the edge j -> j + e_d; RHS b_i(j) = a_i(j) - a_i(j - e_i).
+ * - Preconditioner: G(k1, k2) = 1/(l_k1 + l_k2), G(0, 0) = 0 (rank 0), or
+ *   the rank-R exponential sum sum_r w_r exp(-t_r (l_k1 + l_k2)), 2 <= R <= 64,
+ *   fitted on the 2D spectrum; applied as a 2D Hartley transform.
+ * Handles, ownership, streams and errors as for the 3D calls. */
+typedef struct sq2d_coeffs sq2d_coeffs;
+typedef struct sq2d_precond sq2d_precond;
+typedef struct sq2d_workspace sq2d_workspace;
+
+int sq2d_build_coeffs(int L, int n, uint64_t seed, double p_hi, double a_lo, double a_hi, sq_stream_t stream,
+                      sq2d_coeffs **out);
+/* L^2 phases in HOST memory (0 = a_lo, nonzero = a_hi, index c2 + L c1). */
+int sq2d_coeffs_from_host(int L, int n, const uint8_t *host_phase, double a_lo, double a_hi, sq_stream_t stream,
+                          sq2d_coeffs **out);
+/* 1 <= sub <= n with n - sub even (sub = n: whole cells). */
+int sq2d_coeffs_set_subcell(sq2d_coeffs *c, int sub);
+/* Copies the L^2 phases to host_phase (synchronous). */
+int sq2d_coeffs_cells(const sq2d_coeffs *c, uint8_t *host_phase);
+void sq2d_coeffs_destroy(sq2d_coeffs *c);
+
+int sq2d_precond_setup(int N, int rank, sq2d_precond **out);
+/* Exponential-sum nodes and weights (rank entries each; NULL allowed). */
+int sq2d_precond_factors(const sq2d_precond *p, double *t, double *w);
+void sq2d_precond_destroy(sq2d_precond *p);
+
+/* 4 N^2 doubles of scratch plus reduction buffers (device). */
+int sq2d_workspace_create(int N, sq2d_workspace **out);
+void sq2d_workspace_destroy(sq2d_workspace *w);
+
+/* PCG for corrector dir (0 or 1) to ||b - A psi|| <= tol ||b|| from psi = 0;
+ * psi: DEVICE array of N^2 doubles, zero-mean on return. SQ_ENOCONV if the
+ * tolerance is not met within max_iter. */
+int sq2d_pcg_solve(const sq2d_coeffs *c, const sq2d_precond *pc, sq2d_workspace *w, int dir, double tol,
+                   int max_iter, double *psi, sq_solve_info *info, sq_stream_t stream);
+/* A_hom (edge form, row-major 2 x 2) and, if A_energy is not NULL, the
+ * energy form, from the two correctors (DEVICE arrays; synchronous on the
+ * handle's stream). */
+int sq2d_homogenized_matrix(const sq2d_coeffs *c, const double *psi0, const double *psi1, double *A_hom,
+                            double *A_energy);
+/* Verification blocks (DEVICE arrays of N^2 doubles): y = A x; b = b_dir;
+ * z = G-preconditioned r (zero mean). */
+int sq2d_apply_operator(const sq2d_coeffs *c, const double *x, double *y, sq_stream_t stream);
+int sq2d_rhs(const sq2d_coeffs *c, int dir, double *b, sq_stream_t stream);
+int sq2d_apply_precond(const sq2d_precond *pc, sq2d_workspace *w, const double *r, double *z, sq_stream_t stream);
+
 #ifdef __cplusplus
 }
 #endif

@@ -340,6 +340,8 @@ struct RedBuf {
 // stencil.cu
 // thr[0..2]: level thresholds on the top 53 bits (see k_coeff_gen).
 cudaError_t launch_coeff_gen(uint8_t *phase, int L, uint64_t seed, const uint64_t *thr, cudaStream_t s);
+// The same draw for cells 0 .. ncell-1 (a 2D lattice: ncell = L^2).
+cudaError_t launch_coeff_gen_cells(uint8_t *phase, int ncell, uint64_t seed, const uint64_t *thr, cudaStream_t s);
 cudaError_t allow_dynamic_smem(const void *kern, size_t smem);
 enum StencilMode : int { ST_MATVEC = 0, ST_RESID = 1, ST_RHS = 2 };
 // y = A x (ST_MATVEC, reduces x.y), y = b_dir - A x (ST_RESID, reduces ||y||^2
@@ -378,6 +380,10 @@ template <typename T>
 cudaError_t launch_dht_pass(int pass, const SpectralDev &sp, const T *in, T *out, T *r, const T *q, T *p, T *x,
                             RedBuf rb, bool first, bool check_done, cudaStream_t s);
 int dht_tile_pencils(int N, int elem_bytes);
+// The same passes on an N x N field (see dht.cu): PASS_A_*, PASS_C, PASS_E_*.
+template <typename T>
+cudaError_t launch_dht_pass_2d(int pass, const SpectralDev &sp, const T *in, T *out, T *r, const T *q, T *p, T *x,
+                               RedBuf rb, bool first, bool check_done, cudaStream_t s);
 // tile overrides (0 = default); return 0 on success
 int set_dht_pencils_override(int N, int P);
 int set_stencil_planes_override(int N, int zc);
@@ -390,6 +396,11 @@ int coeffs_view(const sq_coeffs *c, CellsDev *out);
 int precond_spec32(const sq_precond *p, SpectralDev *out, int *N);
 // Grid sizes the solver supports: 8 <= N <= 512, N even, N = 2^a 3^b, b <= 1.
 bool grid_size_ok(int N);
+// Exponential sum sum_r w_r exp(-t_r x) ~ 1/x over the dim-D spectrum of the
+// periodic Laplacian on N points per axis (dim = 2 or 3).
+void exp_sum_nodes(int N, int R, int dim, std::vector<double> &t, std::vector<double> &w);
+// Mixed-radix plan of the Stockham FFT of length N (returns the stage count).
+int radix_plan_of(int N, int *rad);
 // solver.cu: a preconditioner from host factors f (3 x R x N, unscaled; R = 0:
 // the exact diagonal) and, for an exponential sum, its nodes and weights.
 int precond_create(int N, int R, const double *f, const std::vector<double> &t, const std::vector<double> &w,

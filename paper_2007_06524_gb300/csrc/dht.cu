@@ -347,6 +347,46 @@ cudaError_t launch_dht_pass(int pass, const SpectralDev &sp, const T *in, T *out
   }
 }
 
+// 2D passes on an N x N field (x2 contiguous): the same tiles with N rows in
+// place of N^2. PASS_A_* / PASS_E_*: row transforms (the x3 tile); PASS_C: the
+// column transform (the x2 tile of the single line 0), scaled by G(k, 0, k2)
+// = G2(k, k2) and transformed again. Scale and factors are set up for 2D.
+template <typename T>
+cudaError_t launch_dht_pass_2d(int pass, const SpectralDev &sp, const T *in, T *out, T *r, const T *q, T *p, T *x,
+                               RedBuf rb, bool first, bool check_done, cudaStream_t s) {
+  const int N = sp.N;
+  const int P = dht_tile_pencils(N, (int)sizeof(T));
+  int logP = 0;
+  while ((1 << logP) < P) ++logP;
+  DhtArgs<T> a;
+  a.sp = sp;
+  a.in = in;
+  a.out = out;
+  a.r = r;
+  a.q = q;
+  a.p = p;
+  a.x = x;
+  a.rb = rb;
+  a.first = first ? 1 : 0;
+  a.check_done = check_done ? 1 : 0;
+  a.logP = logP;
+  a.ntiles = N / (2 * P);
+  const int grid = a.ntiles;
+  const size_t smem = dht_smem_bytes_t<T>(N, P, pass == PASS_C ? sp.rank : 0);
+  switch (pass) {
+    case PASS_A_RESID: return launch_one<T, 3, LD_RESID, SO_PLAIN, false>(a, grid, smem, s);
+    case PASS_A_PLAIN: return launch_one<T, 3, LD_PLAIN, SO_PLAIN, false>(a, grid, smem, s);
+    case PASS_C: return launch_one<T, 2, LD_PLAIN, SO_PLAIN, true>(a, grid, smem, s);
+    case PASS_E_PCG: return launch_one<T, 3, LD_PLAIN, SO_PCG, false>(a, grid, smem, s);
+    case PASS_E_PLAIN: return launch_one<T, 3, LD_PLAIN, SO_PLAIN, false>(a, grid, smem, s);
+    default: return cudaErrorInvalidValue;
+  }
+}
+
+template cudaError_t launch_dht_pass_2d<double>(int, const SpectralDev &, const double *, double *, double *,
+                                                const double *, double *, double *, RedBuf, bool, bool,
+                                                cudaStream_t);
+
 template cudaError_t launch_dht_pass<double>(int, const SpectralDev &, const double *, double *, double *,
                                              const double *, double *, double *, RedBuf, bool, bool, cudaStream_t);
 template cudaError_t launch_dht_pass<float>(int, const SpectralDev &, const float *, float *, float *, const float *,

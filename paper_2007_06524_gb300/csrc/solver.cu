@@ -196,13 +196,15 @@ int radix_plan(int N, int *rad) {
 // lower truncation 12 e^{s_lo}, upper truncation exp(-lambda_min e^{s_hi}) and
 // the step error exp(-pi^2/eta) -- are balanced at one level eps, found by
 // bisection on ln(eps); nodes s_r = s_lo + r eta, t_r = e^{s_r}, w_r = eta e^{s_r}.
-void sinc_nodes(int N, int R, std::vector<double> &t, std::vector<double> &w) {
+// dim = 2 or 3: the spectrum lies in [lambda_min, 4 dim].
+void sinc_nodes(int N, int R, std::vector<double> &t, std::vector<double> &w, int dim = 3) {
   const double pi = 3.14159265358979323846;
   const double sn = std::sin(pi / N);
   const double lam_min = 4.0 * sn * sn;
+  const double xmax = 4.0 * dim;
   double lo = std::log(1e-300), hi = std::log(0.5);
   auto eta_of = [&](double le, double *slo) {
-    const double s_lo = le - std::log(12.0);
+    const double s_lo = le - std::log(xmax);
     const double s_hi = std::log(-le / lam_min);
     *slo = s_lo;
     return (s_hi - s_lo) / (R - 1);
@@ -278,12 +280,13 @@ double exp_sum_error(const std::vector<double> &xs, const std::vector<double> &t
 
 // Rank-R factors used by the library: geometric nodes t_r between e^a and e^b,
 // weights w_r by least squares on the relative error x G_R(x) - 1 over a
-// log-uniform sample of the discrete spectrum {l_i + l_j + l_k > 0}; (a, b) is
-// chosen on a grid to minimise the largest sampled error with all w_r > 0. The
-// result is kept only if its largest error over the whole spectrum is below
-// that of the balanced trapezoid rule (which is used otherwise, and for R > 32).
-void rank_r_nodes(int N, int R, std::vector<double> &t, std::vector<double> &w) {
-  sinc_nodes(N, R, t, w);
+// log-uniform sample of the discrete spectrum {l_i + l_j + l_k > 0} (dim 3;
+// {l_i + l_j > 0} for dim 2); (a, b) is chosen on a grid to minimise the
+// largest sampled error with all w_r > 0. The result is kept only if its
+// largest error over the whole spectrum is below that of the balanced
+// trapezoid rule (which is used otherwise, and for R > 32).
+void rank_r_nodes(int N, int R, std::vector<double> &t, std::vector<double> &w, int dim = 3) {
+  sinc_nodes(N, R, t, w, dim);
   if (R > 32) return;
   const double pi = 3.14159265358979323846;
   const int H = N / 2;
@@ -293,13 +296,20 @@ void rank_r_nodes(int N, int R, std::vector<double> &t, std::vector<double> &w) 
     lam[k] = 4.0 * sn * sn;
   }
   std::vector<double> xs;
-  xs.reserve((size_t)(H + 1) * (H + 2) * (H + 3) / 6);
-  for (int i = 0; i <= H; ++i)
-    for (int j = i; j <= H; ++j)
-      for (int k = j; k <= H; ++k) {
-        const double g = lam[i] + lam[j] + lam[k];
-        if (g > 0.0) xs.push_back(g);
-      }
+  if (dim == 2) {
+    xs.reserve((size_t)(H + 1) * (H + 2) / 2);
+    for (int i = 0; i <= H; ++i)
+      for (int j = i; j <= H; ++j)
+        if (lam[i] + lam[j] > 0.0) xs.push_back(lam[i] + lam[j]);
+  } else {
+    xs.reserve((size_t)(H + 1) * (H + 2) * (H + 3) / 6);
+    for (int i = 0; i <= H; ++i)
+      for (int j = i; j <= H; ++j)
+        for (int k = j; k <= H; ++k) {
+          const double g = lam[i] + lam[j] + lam[k];
+          if (g > 0.0) xs.push_back(g);
+        }
+  }
   std::sort(xs.begin(), xs.end());
   std::vector<double> u;  // distinct spectral values
   for (double x : xs)
@@ -322,7 +332,7 @@ void rank_r_nodes(int N, int R, std::vector<double> &t, std::vector<double> &w) 
   double best = std::numeric_limits<double>::infinity();
   std::vector<double> bt, bw, tt(R), ww, E((size_t)M * R);
   for (int ia = 0; ia < ng; ++ia) {
-    const double a = -std::log(12.0) - 6.0 + 7.0 * ia / (ng - 1);
+    const double a = -std::log(4.0 * dim) - 6.0 + 7.0 * ia / (ng - 1);
     for (int ib = 0; ib < ng; ++ib) {
       const double b = std::log(1.0 / lam_min) - 1.0 + 5.0 * ib / (ng - 1);
       for (int r = 0; r < R; ++r) tt[r] = std::exp(a + (b - a) * r / (R - 1));
@@ -579,6 +589,10 @@ int apply_precond_t(const sq_precond *pc, sq_workspace *w, const T *r, T *z, T *
 
 namespace sq {
 bool grid_size_ok(int N) { return valid_N(N); }
+void exp_sum_nodes(int N, int R, int dim, std::vector<double> &t, std::vector<double> &w) {
+  rank_r_nodes(N, R, t, w, dim);
+}
+int radix_plan_of(int N, int *rad) { return radix_plan(N, rad); }
 int coeffs_view(const sq_coeffs *c, CellsDev *out) {
   if (!c || !out) return SQ_EINVAL;
   *out = cells_dev(c);

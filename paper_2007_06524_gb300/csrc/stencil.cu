@@ -42,10 +42,13 @@ __global__ void k_coeff_gen(uint8_t *__restrict__ phase, int ncell, uint64_t see
   }
 }
 
-cudaError_t launch_coeff_gen(uint8_t *phase, int L, uint64_t seed, const uint64_t *thr, cudaStream_t s) {
-  int ncell = L * L * L;
+cudaError_t launch_coeff_gen_cells(uint8_t *phase, int ncell, uint64_t seed, const uint64_t *thr, cudaStream_t s) {
   k_coeff_gen<<<(ncell + 255) / 256, 256, 0, s>>>(phase, ncell, seed, thr[0], thr[1], thr[2]);
   return cudaGetLastError();
+}
+
+cudaError_t launch_coeff_gen(uint8_t *phase, int L, uint64_t seed, const uint64_t *thr, cudaStream_t s) {
+  return launch_coeff_gen_cells(phase, L * L * L, seed, thr, s);
 }
 
 // Work item = a tile of 32 node columns (j3) x 8 RPT node rows (j2) times a

@@ -111,6 +111,21 @@ def load_library():
         "sq_set_tiles": (i, [p(TileConfig), i]),
         "sq_ensemble_ahom": (i, [i, i, vp, i, d, d, d, i, d, i, i, vp, vp, vp, vp, vp]),
         "sq_set_option": (i, [i, i]),
+        "sq2d_build_coeffs": (i, [i, i, u64, d, d, d, vp, p(vp)]),
+        "sq2d_coeffs_from_host": (i, [i, i, vp, d, d, vp, p(vp)]),
+        "sq2d_coeffs_set_subcell": (i, [vp, i]),
+        "sq2d_coeffs_cells": (i, [vp, vp]),
+        "sq2d_coeffs_destroy": (None, [vp]),
+        "sq2d_precond_setup": (i, [i, i, p(vp)]),
+        "sq2d_precond_factors": (i, [vp, vp, vp]),
+        "sq2d_precond_destroy": (None, [vp]),
+        "sq2d_workspace_create": (i, [i, p(vp)]),
+        "sq2d_workspace_destroy": (None, [vp]),
+        "sq2d_pcg_solve": (i, [vp, vp, vp, i, d, i, vp, p(SolveInfo), vp]),
+        "sq2d_homogenized_matrix": (i, [vp, vp, vp, vp, vp]),
+        "sq2d_apply_operator": (i, [vp, vp, vp, vp]),
+        "sq2d_rhs": (i, [vp, i, vp, vp]),
+        "sq2d_apply_precond": (i, [vp, vp, vp, vp, vp]),
     }
     for name, (res, args) in sig.items():
         f = getattr(lib, name)
@@ -183,6 +198,22 @@ class Workspace(_Handle):
 
 class Net(_Handle):
     _destroy = "sq_net_destroy"
+
+
+class Coeffs2D(_Handle):
+    _destroy = "sq2d_coeffs_destroy"
+
+    def __init__(self, ptr, L):
+        super().__init__(ptr)
+        self.L = L
+
+
+class Precond2D(_Handle):
+    _destroy = "sq2d_precond_destroy"
+
+
+class Workspace2D(_Handle):
+    _destroy = "sq2d_workspace_destroy"
 
 
 class Batch(_Handle):
@@ -529,3 +560,80 @@ def sq_ensemble_ahom(L, n, seeds, p_hi, a_lo, a_hi, rank=0, tol=1e-8, max_iter=2
 
 def sq_set_option(key, value):
     _check(load_library().sq_set_option(int(key), int(value)), "sq_set_option")
+
+
+# ----------------------------------------------------------------------- 2D
+def sq2d_build_coeffs(L, n, seed, p_hi, a_lo, a_hi, stream=None) -> Coeffs2D:
+    out = C.c_void_p()
+    _check(load_library().sq2d_build_coeffs(int(L), int(n), int(seed) & (2**64 - 1), float(p_hi), float(a_lo),
+                                            float(a_hi), _stream(stream), C.byref(out)), "sq2d_build_coeffs")
+    return Coeffs2D(out, int(L))
+
+
+def sq2d_coeffs_from_host(L, n, host_phase, a_lo, a_hi, stream=None) -> Coeffs2D:
+    arr = np.ascontiguousarray(host_phase, dtype=np.uint8)
+    if arr.size != L * L:
+        raise ValueError("host_phase must hold L^2 bytes")
+    out = C.c_void_p()
+    _check(load_library().sq2d_coeffs_from_host(int(L), int(n), arr.ctypes.data_as(C.c_void_p), float(a_lo),
+                                                float(a_hi), _stream(stream), C.byref(out)), "sq2d_coeffs_from_host")
+    return Coeffs2D(out, int(L))
+
+
+def sq2d_coeffs_set_subcell(c: Coeffs2D, sub: int):
+    _check(load_library().sq2d_coeffs_set_subcell(c, int(sub)), "sq2d_coeffs_set_subcell")
+
+
+def sq2d_coeffs_cells(c: Coeffs2D) -> np.ndarray:
+    ph = np.empty(c.L * c.L, dtype=np.uint8)
+    _check(load_library().sq2d_coeffs_cells(c, ph.ctypes.data_as(C.c_void_p)), "sq2d_coeffs_cells")
+    return ph.reshape(c.L, c.L)
+
+
+def sq2d_precond_setup(N, rank) -> Precond2D:
+    out = C.c_void_p()
+    _check(load_library().sq2d_precond_setup(int(N), int(rank), C.byref(out)), "sq2d_precond_setup")
+    return Precond2D(out)
+
+
+def sq2d_precond_factors(pc: Precond2D, rank: int):
+    t = np.zeros(max(rank, 1))
+    w = np.zeros(max(rank, 1))
+    _check(load_library().sq2d_precond_factors(pc, t.ctypes.data_as(C.c_void_p), w.ctypes.data_as(C.c_void_p)),
+           "sq2d_precond_factors")
+    return t[:rank], w[:rank]
+
+
+def sq2d_workspace_create(N) -> Workspace2D:
+    out = C.c_void_p()
+    _check(load_library().sq2d_workspace_create(int(N), C.byref(out)), "sq2d_workspace_create")
+    return Workspace2D(out)
+
+
+def sq2d_pcg_solve(c, pc, w, dir, tol, max_iter, psi, stream=None) -> dict:
+    """Solves corrector dir (0, 1) into psi (float64 CUDA tensor, N^2)."""
+    info = SolveInfo()
+    st = load_library().sq2d_pcg_solve(c, pc, w, int(dir), float(tol), int(max_iter), _ptr(psi), C.byref(info),
+                                       _stream(stream))
+    _check(st, "sq2d_pcg_solve", allow=(SQ_ENOCONV,))
+    return {k: getattr(info, k) for k, _ in SolveInfo._fields_}
+
+
+def sq2d_homogenized_matrix(c, psi0, psi1):
+    A = np.zeros(4)
+    E = np.zeros(4)
+    _check(load_library().sq2d_homogenized_matrix(c, _ptr(psi0), _ptr(psi1), A.ctypes.data_as(C.c_void_p),
+                                                  E.ctypes.data_as(C.c_void_p)), "sq2d_homogenized_matrix")
+    return A.reshape(2, 2), E.reshape(2, 2)
+
+
+def sq2d_apply_operator(c, x, y, stream=None):
+    _check(load_library().sq2d_apply_operator(c, _ptr(x), _ptr(y), _stream(stream)), "sq2d_apply_operator")
+
+
+def sq2d_rhs(c, dir, b, stream=None):
+    _check(load_library().sq2d_rhs(c, int(dir), _ptr(b), _stream(stream)), "sq2d_rhs")
+
+
+def sq2d_apply_precond(pc, w, r, z, stream=None):
+    _check(load_library().sq2d_apply_precond(pc, w, _ptr(r), _ptr(z), _stream(stream)), "sq2d_apply_precond")

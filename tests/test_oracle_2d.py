@@ -11,6 +11,8 @@ from oracle import assembly, dual2d, homogenized, pcg, precond, rng, solver2d
 def test_2d_draw_is_the_first_slab_of_the_3d_draw():
     for L, seed, p in ((4, 0, 0.5), (6, 11, 0.3), (5, 2**63 + 1, 0.8)):
         assert np.array_equal(solver2d.cell_phases_2d(L, seed, p), rng.cell_phases(L, seed, p)[0])
+        assert np.array_equal(solver2d.cell_phases_2d_vec(L, seed, p), solver2d.cell_phases_2d(L, seed, p))
+    assert np.array_equal(solver2d.cell_phases_2d_vec(40, 9, 0.5), rng.cell_phases_vec(40, 9, 0.5)[0])
 
 
 @pytest.mark.parametrize("sub", [None, 2])
