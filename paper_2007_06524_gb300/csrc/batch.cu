@@ -68,7 +68,7 @@ __global__ void kb_scalars_reset(BSolve *S, int count, double tolrel2, int max_i
 // WHICH 1: inner FP32 q = A p (FIN_ALPHA on st_i): the shared-memory-staged
 // operator (stencil_staged_run) on 32 x 32 tiles where N % 32 == 0, else one
 // row per thread.
-template <int WHICH>
+template <int WHICH, bool GEN>
 __global__ void __launch_bounds__(kThreads, WHICH == 1 ? 3 : 1) kb_stencil(const BSolve *__restrict__ S, const int *__restrict__ pre,
                                                        int count) {
   using Ti = typename std::conditional<WHICH == 0, double, float>::type;
@@ -91,7 +91,7 @@ __global__ void __launch_bounds__(kThreads, WHICH == 1 ? 3 : 1) kb_stencil(const
       const int tile = lb % ntl, zb = lb / ntl;
       const int z0 = zb * B.zc_in, z1 = min(z0 + B.zc_in, N);
       Accum<float> acc;
-      stencil_staged_run(B.c, B.p, B.q, tab, cellof, ring, (tile / nbx) * 32, (tile % nbx) * 32, z0, z1, acc);
+      stencil_staged_run<GEN>(B.c, B.p, B.q, tab, cellof, ring, (tile / nbx) * 32, (tile % nbx) * 32, z0, z1, acc);
       FF v[2] = {acc.part(), FF{0.f, 0.f}};
       double out[2];
       if (reduce_last_block_ex<2>(v, B.partials, B.pstride, &st->ticket, B.nb_in, lb, out)) {
@@ -112,9 +112,9 @@ __global__ void __launch_bounds__(kThreads, WHICH == 1 ? 3 : 1) kb_stencil(const
   Accum<Ti> acc0, acc1;
   if (j3 < N && j2 < N) {
     if constexpr (WHICH == 0)
-      stencil_rows<double, float, ST_RESID, 1>(B.c, B.dir, B.x, B.r, tab, cellof, j3, j2, z0, z1, acc0, acc1);
+      stencil_rows<double, float, ST_RESID, 1, GEN>(B.c, B.dir, B.x, B.r, tab, cellof, j3, j2, z0, z1, acc0, acc1);
     else
-      stencil_rows<float, float, ST_MATVEC, 1>(B.c, 0, B.p, B.q, tab, cellof, j3, j2, z0, z1, acc0, acc1);
+      stencil_rows<float, float, ST_MATVEC, 1, GEN>(B.c, 0, B.p, B.q, tab, cellof, j3, j2, z0, z1, acc0, acc1);
   }
   typename Accum<Ti>::Part v[2] = {acc0.part(), acc1.part()};
   double out[2];
@@ -333,6 +333,7 @@ struct sq_batch {
   int tot_st = 0, tot_dht = 0, tot_vec = 0, tot_in = 0;
   size_t dht_smem[2] = {0, 0};  // plain passes, pass C
   int layers = 1;               // most threshold layers of the batch's media (pattern tables)
+  bool general = false;         // some medium is not the plain checkerboard (see general_media)
   void *d_mem = nullptr;        // fields, scalars, partials
   int *d_iters = nullptr;
   int *d_count = nullptr;
@@ -381,8 +382,12 @@ int precond_first_b(sq_batch *b, cudaStream_t s) {
 }
 
 int iteration_b(sq_batch *b, cudaStream_t s) {
-  kb_stencil<1><<<b->tot_in, dim3(32, 8, 1), kStagedSmem + tab_bytes<float>(b->layers), s>>>(
-      b->dS, b->d_pre + 3 * (b->count + 1), b->count);
+  if (b->general)
+    kb_stencil<1, true><<<b->tot_in, dim3(32, 8, 1), kStagedSmem + tab_bytes<float>(b->layers), s>>>(
+        b->dS, b->d_pre + 3 * (b->count + 1), b->count);
+  else
+    kb_stencil<1, false><<<b->tot_in, dim3(32, 8, 1), kStagedSmem + tab_bytes<float>(1), s>>>(
+        b->dS, b->d_pre + 3 * (b->count + 1), b->count);
   if (cudaGetLastError() != cudaSuccess) return SQ_ECUDA;
   int st;
   if ((st = launch_kb_dht<3, LD_RESID, SO_PLAIN, false>(b, 0, s)) != SQ_OK) return st;
@@ -503,6 +508,7 @@ int sq_batch_create(int count, const sq_solve_desc *descs, const sq_precond *con
     field_floats += 5 * (size_t)n3;
     maxN = std::max(maxN, N);
     b->layers = std::max(b->layers, B.c.layers);
+    b->general = b->general || general_media(B.c);
     maxR = std::max(maxR, sp.rank);
     maxP = std::max(maxP, P);
     b->dht_smem[0] = std::max(b->dht_smem[0], dht_smem_bytes_t<float>(N, P, 0));
@@ -554,8 +560,10 @@ int sq_batch_create(int count, const sq_solve_desc *descs, const sq_precond *con
   ok = cudaMemcpy(b->dS, b->hS.data(), sizeof(BSolve) * count, cudaMemcpyHostToDevice) == cudaSuccess;
   ok = ok && cudaMemcpy(b->d_pre, pre.data(), sizeof(int) * pre.size(), cudaMemcpyHostToDevice) == cudaSuccess;
   ok = ok && cudaMemset(sc, 0, bytes_scal) == cudaSuccess;
-  ok = ok && allow_dynamic_smem((const void *)kb_stencil<1>, kStagedSmem + tab_bytes<float>(b->layers)) == cudaSuccess;
-  ok = ok && allow_dynamic_smem((const void *)kb_stencil<0>, tab_bytes<double>(b->layers)) == cudaSuccess;
+  ok = ok && allow_dynamic_smem(b->general ? (const void *)kb_stencil<1, true> : (const void *)kb_stencil<1, false>,
+                                kStagedSmem + tab_bytes<float>(b->layers)) == cudaSuccess;
+  ok = ok && allow_dynamic_smem(b->general ? (const void *)kb_stencil<0, true> : (const void *)kb_stencil<0, false>,
+                                tab_bytes<double>(b->layers)) == cudaSuccess;
   ok = ok && set_kb_dht_smem<3, LD_PLAIN, SO_PLAIN, false>(b->dht_smem[0]) == SQ_OK;
   ok = ok && set_kb_dht_smem<3, LD_RESID, SO_PLAIN, false>(b->dht_smem[0]) == SQ_OK;
   ok = ok && set_kb_dht_smem<2, LD_PLAIN, SO_PLAIN, false>(b->dht_smem[0]) == SQ_OK;
@@ -602,7 +610,10 @@ int sq_pcg_solve_batched(sq_batch *b, double tol, int max_iter, sq_solve_info *i
   SQB_CK(cudaGetLastError());
   int outer = 0;
   for (; outer < 30; ++outer) {
-    kb_stencil<0><<<b->tot_st, dim3(32, 8, 1), tab_bytes<double>(b->layers), s>>>(b->dS, b->d_pre, count);
+    if (b->general)
+      kb_stencil<0, true><<<b->tot_st, dim3(32, 8, 1), tab_bytes<double>(b->layers), s>>>(b->dS, b->d_pre, count);
+    else
+      kb_stencil<0, false><<<b->tot_st, dim3(32, 8, 1), tab_bytes<double>(1), s>>>(b->dS, b->d_pre, count);
     SQB_CK(cudaGetLastError());
     int active = 0;
     if ((st = count_active(b, 0, s, &active)) != SQ_OK) return st;

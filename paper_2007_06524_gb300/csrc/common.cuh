@@ -296,6 +296,9 @@ struct CellsDev {
   float edge_f[kMaxLayers][5], diag_f[kMaxLayers][25];
 };
 
+// Anything but the plain two-level checkerboard of whole cells.
+inline bool general_media(const CellsDev &c) { return c.layers > 1 || c.sub_lo != 0 || c.sub_hi < (1 << 30); }
+
 inline double level_value(const CellsDev &c, int l) { return l == 0 ? c.a_lo : l == 1 ? c.a_hi : c.a_up[l - 2]; }
 
 inline void fill_tables(CellsDev &c) {

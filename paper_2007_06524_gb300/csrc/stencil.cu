@@ -60,7 +60,7 @@ cudaError_t launch_coeff_gen(uint8_t *phase, int L, uint64_t seed, const uint64_
 // RPT) amortises the per-plane index and coefficient work over RPT rows at
 // the cost of registers (RPT 4: ~114, two blocks per SM; RPT 2: ~64, four);
 // FP64 (ALU-bound) keeps one row per thread.
-template <typename Ti, typename To, int MODE, int RPT>
+template <typename Ti, typename To, int MODE, int RPT, bool GEN>
 __global__ void __launch_bounds__(kThreads) k_stencil(CellsDev c, int dir, const Ti *__restrict__ x,
                                                       To *__restrict__ y, RedBuf rb, int fin, int check_done,
                                                       int zc, int nitems) {
@@ -83,7 +83,7 @@ __global__ void __launch_bounds__(kThreads) k_stencil(CellsDev c, int dir, const
     const int z0 = bz * zc;
     const int z1 = min(z0 + zc, N);
     if (j3 < N && j2b < N)
-      stencil_rows<Ti, To, MODE, RPT>(c, dir, x, y, tab, cellof, j3, j2b, z0, z1, acc0, acc1);
+      stencil_rows<Ti, To, MODE, RPT, GEN>(c, dir, x, y, tab, cellof, j3, j2b, z0, z1, acc0, acc1);
   }
   typename Accum<Ti>::Part v[2] = {acc0.part(), acc1.part()};
   double s[2];
@@ -145,6 +145,7 @@ static int resident_blocks(const void *kern, int threads, size_t smem) {
 }
 
 // Staged FP32 operator over one (tile, plane run) per block; see stencil_staged_run.
+template <bool GEN>
 __global__ void __launch_bounds__(kThreads, 3) k_stencil_staged(CellsDev c, const float *__restrict__ x,
                                                              float *__restrict__ y, RedBuf rb, int fin,
                                                              int check_done, int zc, int ntiles) {
@@ -157,7 +158,7 @@ __global__ void __launch_bounds__(kThreads, 3) k_stencil_staged(CellsDev c, cons
   const int tile = blockIdx.x % ntiles, zb = blockIdx.x / ntiles;
   const int z0 = zb * zc, z1 = min(z0 + zc, N);
   Accum<float> acc;
-  stencil_staged_run(c, x, y, tab, cellof, ring, (tile / nbx) * 32, (tile % nbx) * 32, z0, z1, acc);
+  stencil_staged_run<GEN>(c, x, y, tab, cellof, ring, (tile / nbx) * 32, (tile % nbx) * 32, z0, z1, acc);
   FF v[2] = {acc.part(), FF{0.f, 0.f}};
   double sres[2];
   if (reduce_last_block<2>(v, rb.partials, &rb.st->ticket, sres)) {
@@ -165,14 +166,16 @@ __global__ void __launch_bounds__(kThreads, 3) k_stencil_staged(CellsDev c, cons
   }
 }
 
+template <bool GEN>
 static cudaError_t launch_stencil_staged(const CellsDev &c, const float *x, float *y, RedBuf rb, int fin,
                                          bool check_done, cudaStream_t s) {
   const int N = c.N;
   const size_t smem = (size_t)kStages * kSlot * sizeof(float) + tab_bytes<float>(c.layers);
-  const cudaError_t e = allow_dynamic_smem((const void *)k_stencil_staged, smem);
+  auto kern = k_stencil_staged<GEN>;
+  const cudaError_t e = allow_dynamic_smem((const void *)kern, smem);
   if (e != cudaSuccess) return e;
   const int ntiles = (N / 32) * (N / 32);
-  const int resident = resident_blocks((const void *)k_stencil_staged, kThreads, smem);
+  const int resident = resident_blocks((const void *)kern, kThreads, smem);
   if (resident <= 0) return cudaErrorInvalidConfiguration;
   int nz = resident / ntiles;
   if (nz > N / 4) nz = N / 4;  // at least 4 planes per block
@@ -181,7 +184,7 @@ static cudaError_t launch_stencil_staged(const CellsDev &c, const float *x, floa
   nz = (N + zc - 1) / zc;
   const long long grid = (long long)ntiles * nz;
   if (grid > kMaxPartials) return cudaErrorInvalidConfiguration;
-  k_stencil_staged<<<(int)grid, dim3(32, 8, 1), smem, s>>>(c, x, y, rb, fin, check_done ? 1 : 0, zc, ntiles);
+  kern<<<(int)grid, dim3(32, 8, 1), smem, s>>>(c, x, y, rb, fin, check_done ? 1 : 0, zc, ntiles);
   return cudaGetLastError();
 }
 
@@ -222,14 +225,14 @@ static int stencil_zc(int N, int rpt) {
   return zc;
 }
 
-template <typename Ti, typename To, int MODE, int RPT>
+template <typename Ti, typename To, int MODE, int RPT, bool GEN = false>
 static cudaError_t launch_stencil_mode(const CellsDev &c, int dir, const Ti *x, To *y, RedBuf rb, int fin,
                                        bool check_done, cudaStream_t s) {
   const int N = c.N;
   const int zc = stencil_zc(N, RPT);
   const long long items =
       (long long)((N + 31) / 32) * ((N + 8 * RPT - 1) / (8 * RPT)) * ((N + zc - 1) / zc);
-  auto kern = k_stencil<Ti, To, MODE, RPT>;
+  auto kern = k_stencil<Ti, To, MODE, RPT, GEN>;
   const size_t smem = tab_bytes<Ti>(c.layers);
   const cudaError_t e = allow_dynamic_smem((const void *)kern, smem);
   if (e != cudaSuccess) return e;
@@ -241,15 +244,24 @@ static cudaError_t launch_stencil_mode(const CellsDev &c, int dir, const Ti *x, 
   return cudaGetLastError();
 }
 
+// Media other than the plain checkerboard (several levels or sub-cell
+// inclusions) take the kernels compiled for them: the staged FP32 operator
+// where it applies, else one row per thread.
 template <typename Ti, typename To, int MODE>
 static cudaError_t launch_stencil_rows(const CellsDev &c, int dir, const Ti *x, To *y, RedBuf rb, int fin,
                                        bool check_done, cudaStream_t s) {
+  if (general_media(c)) {
+    if constexpr (sizeof(Ti) == 4 && MODE == ST_MATVEC && sizeof(To) == 4) {
+      if (c.N % 32 == 0 && ((uintptr_t)x & 15) == 0) return launch_stencil_staged<true>(c, x, y, rb, fin, check_done, s);
+    }
+    return launch_stencil_mode<Ti, To, MODE, 1, true>(c, dir, x, y, rb, fin, check_done, s);
+  }
   if constexpr (sizeof(Ti) == 4) {
     const int per_n = (c.N >= 8 && c.N <= kMaxN) ? g_rows_override[c.N] : 0;
     const int want = per_n ? per_n : (g_stencil_rows ? g_stencil_rows : 8);
     if constexpr (MODE == ST_MATVEC && sizeof(To) == 4) {
       if (want == 8 && c.N % 32 == 0 && ((uintptr_t)x & 15) == 0)
-        return launch_stencil_staged(c, x, y, rb, fin, check_done, s);
+        return launch_stencil_staged<false>(c, x, y, rb, fin, check_done, s);
     }
     if (want >= 4 && c.N % 4 == 0) return launch_stencil_mode<Ti, To, MODE, 4>(c, dir, x, y, rb, fin, check_done, s);
     if (want >= 2 && c.N % 2 == 0) return launch_stencil_mode<Ti, To, MODE, 2>(c, dir, x, y, rb, fin, check_done, s);

@@ -35,9 +35,14 @@ __device__ __forceinline__ void build_pattern_table(T (*tab)[kTabStride], const 
 }
 
 // Layer bits of one phase byte v: bit 8l set iff v >= l + 1 (layers 0..2).
-// Two-level media read only bit 0, i.e. any nonzero phase is high.
+// The plain checkerboard kernels (ML = false, compiled without the extra
+// layers) read only bit 0, i.e. any nonzero phase is high.
+template <bool ML = true>
 __device__ __forceinline__ unsigned level_bits(unsigned v) {
-  return (v != 0u ? 1u : 0u) | (v >= 2u ? 0x100u : 0u) | (v >= 3u ? 0x10000u : 0u);
+  if constexpr (ML)
+    return (v != 0u ? 1u : 0u) | (v >= 2u ? 0x100u : 0u) | (v >= 3u ? 0x10000u : 0u);
+  else
+    return v != 0u ? 1u : 0u;
 }
 // Replicates a mask of layer-0 bits into every layer's byte.
 __device__ __forceinline__ unsigned all_layers(unsigned m) { return m * 0x10101u; }
@@ -55,14 +60,28 @@ __device__ __forceinline__ bool in_sub(const CellsDev &c, int u) { return u >= c
 // Node patterns change between planes j1 - 1 and j1 where a voxel plane
 // crosses a cell face (cell position 0, 1) or a sub-cell face (sub_lo,
 // sub_lo + 1, sub_hi, sub_hi + 1); for whole cells only at 0 and 1.
+// GEN = false compiles the plain checkerboard (two levels, whole cells).
+template <bool GEN>
 __device__ __forceinline__ bool pattern_changes(const CellsDev &c, int cpos) {
+  if constexpr (!GEN) return cpos <= 1;
   return cpos <= 1 || cpos == c.sub_lo || cpos == c.sub_lo + 1 || cpos == c.sub_hi || cpos == c.sub_hi + 1;
 }
 // Plane masks of a node at cell position cpos: the voxels of plane j1 (low
 // nibble) and of plane j1 - 1 (high nibble) may be high.
+template <bool GEN>
 __device__ __forceinline__ void plane_masks(const CellsDev &c, int cpos, unsigned &pm0, unsigned &pm1) {
+  if constexpr (!GEN) {
+    pm0 = pm1 = 0xFu;
+    return;
+  }
   pm0 = in_sub(c, cpos) ? 0xFu : 0u;
   pm1 = in_sub(c, cpos == 0 ? c.n - 1 : cpos - 1) ? 0xFu : 0u;
+}
+// In-plane inclusion mask of a node row (see row_nibbles).
+template <bool GEN>
+__device__ __forceinline__ unsigned row_mask(const CellsDev &c, int u2, unsigned m3) {
+  if constexpr (!GEN) return 0x3u;
+  return in_sub(c, u2) ? m3 : 0u;
 }
 
 // ------------------------------------------------------------ stencil kernel
@@ -85,13 +104,14 @@ __device__ __forceinline__ void plane_masks(const CellsDev &c, int cpos, unsigne
 // crow[q] = (cell of row j2b-1+q) * L.
 // mq[q]: in-plane inclusion mask of row q (bits 0 / 1: the voxel at j3 / j3-1
 // of that row may be high; the same bits in every layer's byte).
-template <int RPT>
+template <int RPT, bool ML>
 __device__ __forceinline__ void row_nibbles(const uint8_t *__restrict__ phase, int c1, int LL, const int (&crow)[RPT + 1],
                                             int c3a, int c3b, const unsigned (&mq)[RPT + 1], unsigned (&nb)[RPT]) {
   const uint8_t *ph = phase + (size_t)c1 * LL;
   unsigned b[RPT + 1];
 #pragma unroll
-  for (int q = 0; q <= RPT; ++q) b[q] = (level_bits(ph[crow[q] + c3a]) | (level_bits(ph[crow[q] + c3b]) << 1)) & mq[q];
+  for (int q = 0; q <= RPT; ++q)
+    b[q] = (level_bits<ML>(ph[crow[q] + c3a]) | (level_bits<ML>(ph[crow[q] + c3b]) << 1)) & mq[q];
 #pragma unroll
   for (int r = 0; r < RPT; ++r) nb[r] = b[r + 1] | (b[r] << 2);
 }
@@ -99,7 +119,7 @@ __device__ __forceinline__ void row_nibbles(const uint8_t *__restrict__ phase, i
 // Coefficients of the RPT rows from their current (nc) and previous-plane
 // (np) nibbles: layer 0's table row, plus the higher layers' rows for
 // multi-level media (block-uniform branch on c.layers).
-template <typename Ti, int RPT>
+template <typename Ti, int RPT, bool ML>
 __device__ __forceinline__ void row_coeffs(const Ti (*tab)[kTabStride], int layers, const unsigned (&nc)[RPT],
                                            const unsigned (&np)[RPT], unsigned pm0, unsigned pm1, Ti (&t)[RPT][7]) {
 #pragma unroll
@@ -108,6 +128,7 @@ __device__ __forceinline__ void row_coeffs(const Ti (*tab)[kTabStride], int laye
 #pragma unroll
     for (int k = 0; k < 7; ++k) t[r][k] = tr[k];
   }
+  if constexpr (!ML) return;
 #pragma unroll
   for (int l = 1; l < kMaxLayers; ++l) {
     if (l < layers) {
@@ -126,7 +147,7 @@ __device__ __forceinline__ void build_cellof(short *cellof, int N, int n, int ti
   for (int j = tid; j < N; j += kThreads) cellof[j] = (short)(j / n);
 }
 
-template <typename Ti, typename To, int MODE, int RPT, int kAhead = 4>
+template <typename Ti, typename To, int MODE, int RPT, bool GEN, int kAhead = 4>
 __device__ __forceinline__ void stencil_rows(const CellsDev &c, int dir, const Ti *__restrict__ x, To *__restrict__ y,
                                              const Ti (*tab)[kTabStride], const short *__restrict__ cellof, int j3,
                                              int j2b, int z0, int z1, Accum<Ti> &acc0, Accum<Ti> &acc1) {
@@ -143,7 +164,7 @@ __device__ __forceinline__ void stencil_rows(const CellsDev &c, int dir, const T
   for (int q = 0; q <= RPT; ++q) {
     const int j2 = (j2b - 1 + q < 0) ? N - 1 : j2b - 1 + q;  // rows j2b .. j2b+RPT-1 are < N
     crow[q] = cellof[j2] * L;
-    mq[q] = in_sub(c, j2 - cellof[j2] * n) ? m3 : 0u;
+    mq[q] = row_mask<GEN>(c, j2 - cellof[j2] * n, m3);
   }
   const int row0 = j2b * N + j3;
   const int up = ((j2b == 0) ? N - 1 : j2b - 1) * N + j3 - row0;          // row j2b - 1
@@ -152,16 +173,16 @@ __device__ __forceinline__ void stencil_rows(const CellsDev &c, int dir, const T
   const int j1m0 = (z0 == 0) ? N - 1 : z0 - 1;
   int cpos = z0 - cellof[z0] * n;  // position of plane z0 within its cell
   unsigned np[RPT], nc[RPT], pm0, pm1;
-  row_nibbles<RPT>(c.phase, cellof[j1m0], LL, crow, c3a, c3b, mq, np);
+  row_nibbles<RPT, GEN>(c.phase, cellof[j1m0], LL, crow, c3a, c3b, mq, np);
   if (cpos == 0) {
-    row_nibbles<RPT>(c.phase, cellof[z0], LL, crow, c3a, c3b, mq, nc);
+    row_nibbles<RPT, GEN>(c.phase, cellof[z0], LL, crow, c3a, c3b, mq, nc);
   } else {
 #pragma unroll
     for (int r = 0; r < RPT; ++r) nc[r] = np[r];
   }
-  plane_masks(c, cpos, pm0, pm1);
+  plane_masks<GEN>(c, cpos, pm0, pm1);
   Ti t[RPT][7];
-  row_coeffs<Ti, RPT>(tab, c.layers, nc, np, pm0, pm1, t);
+  row_coeffs<Ti, RPT, GEN>(tab, c.layers, nc, np, pm0, pm1, t);
 
   Ti xm[RPT], x0[RPT], ahead[RPT][kAhead];  // ahead[r][u] = x(jb + 1 + u) of row r
 #pragma unroll
@@ -193,14 +214,14 @@ __device__ __forceinline__ void stencil_rows(const CellsDev &c, int dir, const T
       if (j1 < z1) {
         if (j1 > z0) {
           cpos = (cpos + 1 == n) ? 0 : cpos + 1;
-          if (pattern_changes(c, cpos)) {
+          if (pattern_changes<GEN>(c, cpos)) {
             if (cpos <= 1) {
 #pragma unroll
               for (int r = 0; r < RPT; ++r) np[r] = nc[r];
             }
-            if (cpos == 0) row_nibbles<RPT>(c.phase, cellof[j1], LL, crow, c3a, c3b, mq, nc);
-            plane_masks(c, cpos, pm0, pm1);
-            row_coeffs<Ti, RPT>(tab, c.layers, nc, np, pm0, pm1, t);
+            if (cpos == 0) row_nibbles<RPT, GEN>(c.phase, cellof[j1], LL, crow, c3a, c3b, mq, nc);
+            plane_masks<GEN>(c, cpos, pm0, pm1);
+            row_coeffs<Ti, RPT, GEN>(tab, c.layers, nc, np, pm0, pm1, t);
           }
         }
         const int b0 = j1 * NN + row0;
@@ -338,6 +359,7 @@ struct PlaneCopy {
 // 32 x 32 tile (j2_0, j3_0) and adds p.Ap to acc. Builds the block's pattern
 // and cell tables itself; `ring` is kStages * kSlot floats of 16-byte aligned
 // shared memory. All threads of the block (32 x 8) must call it.
+template <bool GEN>
 __device__ __forceinline__ void stencil_staged_run(const CellsDev &c, const float *__restrict__ x,
                                                    float *__restrict__ y, float (*tab)[kTabStride], short *cellof,
                                                    float *ring, int j2_0, int j3_0, int z0, int z1,
@@ -372,21 +394,21 @@ __device__ __forceinline__ void stencil_staged_run(const CellsDev &c, const floa
   for (int q = 0; q <= 4; ++q) {
     const int j2 = (j2b - 1 + q < 0) ? N - 1 : j2b - 1 + q;
     crow[q] = cellof[j2] * L;
-    mq[q] = in_sub(c, j2 - cellof[j2] * n) ? m3 : 0u;
+    mq[q] = row_mask<GEN>(c, j2 - cellof[j2] * n, m3);
   }
   const int j1m0 = (z0 == 0) ? N - 1 : z0 - 1;
   int cpos = z0 - cellof[z0] * n;
   unsigned np[4], nc[4], pm0, pm1;
-  row_nibbles<4>(c.phase, cellof[j1m0], LL, crow, c3a, c3b, mq, np);
+  row_nibbles<4, GEN>(c.phase, cellof[j1m0], LL, crow, c3a, c3b, mq, np);
   if (cpos == 0) {
-    row_nibbles<4>(c.phase, cellof[z0], LL, crow, c3a, c3b, mq, nc);
+    row_nibbles<4, GEN>(c.phase, cellof[z0], LL, crow, c3a, c3b, mq, nc);
   } else {
 #pragma unroll
     for (int r = 0; r < 4; ++r) nc[r] = np[r];
   }
-  plane_masks(c, cpos, pm0, pm1);
+  plane_masks<GEN>(c, cpos, pm0, pm1);
   float t[4][7];
-  row_coeffs<float, 4>(tab, c.layers, nc, np, pm0, pm1, t);
+  row_coeffs<float, 4, GEN>(tab, c.layers, nc, np, pm0, pm1, t);
   const int row0 = j2b * N + j3;
   float xm[4], x0[4];
 #pragma unroll
@@ -405,14 +427,14 @@ __device__ __forceinline__ void stencil_staged_run(const CellsDev &c, const floa
     }
     if (k > 0) {
       cpos = (cpos + 1 == n) ? 0 : cpos + 1;
-      if (pattern_changes(c, cpos)) {
+      if (pattern_changes<GEN>(c, cpos)) {
         if (cpos <= 1) {
 #pragma unroll
           for (int r = 0; r < 4; ++r) np[r] = nc[r];
         }
-        if (cpos == 0) row_nibbles<4>(c.phase, cellof[j1], LL, crow, c3a, c3b, mq, nc);
-        plane_masks(c, cpos, pm0, pm1);
-        row_coeffs<float, 4>(tab, c.layers, nc, np, pm0, pm1, t);
+        if (cpos == 0) row_nibbles<4, GEN>(c.phase, cellof[j1], LL, crow, c3a, c3b, mq, nc);
+        plane_masks<GEN>(c, cpos, pm0, pm1);
+        row_coeffs<float, 4, GEN>(tab, c.layers, nc, np, pm0, pm1, t);
       }
     }
     const float *S0 = ring + s0 * kSlot + (1 + 4 * ty) * kSW + 4 + tx;
