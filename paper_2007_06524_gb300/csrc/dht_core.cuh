@@ -17,6 +17,33 @@ __device__ __forceinline__ C cmul(C a, C w) {
 template <typename C>
 __device__ __forceinline__ C mul_mi(C a) { return C{a.y, -a.x}; }  // (-i) a
 
+// FP32 complex sums and differences as one packed two-lane instruction
+// (add / sub .f32x2, sm_100 and later): fewer issued instructions in every
+// butterfly of the FP32 passes. A complex product would need both operands
+// broadcast into lane pairs first, so it stays scalar.
+__device__ __forceinline__ unsigned long long f2_bits(float2 a) {
+  unsigned long long r;
+  asm("mov.b64 %0, {%1, %2};" : "=l"(r) : "f"(a.x), "f"(a.y));
+  return r;
+}
+__device__ __forceinline__ float2 bits_f2(unsigned long long r) {
+  float2 a;
+  asm("mov.b64 {%0, %1}, %2;" : "=f"(a.x), "=f"(a.y) : "l"(r));
+  return a;
+}
+template <>
+__device__ __forceinline__ float2 cadd<float2>(float2 a, float2 b) {
+  unsigned long long r;
+  asm("add.rn.f32x2 %0, %1, %2;" : "=l"(r) : "l"(f2_bits(a)), "l"(f2_bits(b)));
+  return bits_f2(r);
+}
+template <>
+__device__ __forceinline__ float2 csub<float2>(float2 a, float2 b) {
+  unsigned long long r;
+  asm("sub.rn.f32x2 %0, %1, %2;" : "=l"(r) : "l"(f2_bits(a)), "l"(f2_bits(b)));
+  return bits_f2(r);
+}
+
 template <typename T, typename C>
 __device__ __forceinline__ void dft4(C &u0, C &u1, C &u2, C &u3) {
   const C t0 = cadd(u0, u2), t1 = csub(u0, u2), t2 = cadd(u1, u3), t3 = mul_mi(csub(u1, u3));
