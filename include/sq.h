@@ -259,8 +259,12 @@ int sq_set_tiles(const sq_tile_config *tiles, int ntiles);
  * register plane queue (used where N is divisible by it, else the next
  * smaller), or 8: planes staged through shared memory with asynchronous
  * copies (where N is a multiple of 32 and p is 16-byte aligned, else 4).
- * Results are identical up to the order of the p.Ap summation. */
-enum sq_option { SQ_OPT_STRIDED_TWO_STAGE = 1, SQ_OPT_STENCIL_ROWS = 2 };
+ * Results are identical up to the order of the p.Ap summation.
+ * SQ_OPT_INNER_TOL_EXP (default 5): each inner FP32 solve of SQ_FP32_REFINE
+ * (single and batched) cuts its residual by 10^-value, or just enough for the
+ * outer tolerance when that is less; 2 <= value <= 7.
+ */
+enum sq_option { SQ_OPT_STRIDED_TWO_STAGE = 1, SQ_OPT_STENCIL_ROWS = 2, SQ_OPT_INNER_TOL_EXP = 3 };
 int sq_set_option(int key, int value);
 
 /* Plans a batch of `count` solves; precs[k] is the preconditioner (same N) of

@@ -601,7 +601,7 @@ int sq_pcg_solve_batched(sq_batch *b, double tol, int max_iter, sq_solve_info *i
   cudaStream_t s = reinterpret_cast<cudaStream_t>(stream);
   const int count = b->count;
   const int *pre_vec = b->d_pre + 2 * (count + 1);
-  const double tol_in = 1e-4;
+  const double tol_in = inner_tol();
   int st = capture_graph(b, s);
   if (st != SQ_OK) return st;
   const int tb = (count + 127) / 128;

@@ -399,6 +399,9 @@ int coeffs_view(const sq_coeffs *c, CellsDev *out);
 int precond_spec32(const sq_precond *p, SpectralDev *out, int *N);
 // Grid sizes the solver supports: 8 <= N <= 512, N even, N = 2^a 3^b, b <= 1.
 bool grid_size_ok(int N);
+// Residual reduction asked of each inner FP32 solve of the refinement (10^-e).
+int set_inner_tol_exp(int e);
+double inner_tol();
 // Exponential sum sum_r w_r exp(-t_r x) ~ 1/x over the dim-D spectrum of the
 // periodic Laplacian on N points per axis (dim = 2 or 3).
 void exp_sum_nodes(int N, int R, int dim, std::vector<double> &t, std::vector<double> &w);

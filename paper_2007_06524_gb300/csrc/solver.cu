@@ -517,7 +517,7 @@ int solve_fp32_refine(const sq_coeffs *c, const sq_precond *pc, sq_workspace *w,
   const RedBuf ro = redbuf<double>(&w->d_st[0], w->d_partials);
   const RedBuf ri = redbuf<double>(&w->d_st[1], w->d_partials);
   const CellsDev cd = cells_dev(c);
-  const double tol_in = 1e-4;
+  const double tol_in = inner_tol();
   SQ_LAUNCH(PC_SCALAR, s, (k_scalars_reset<<<1, 1, 0, s>>>(ro.st, tol * tol, max_iter), cudaGetLastError()));
   Scalars *ho = &w->h_st[0], *hi = &w->h_st[1];
   bool used_guess = false;
@@ -588,6 +588,13 @@ int apply_precond_t(const sq_precond *pc, sq_workspace *w, const T *r, T *z, T *
 }  // namespace
 
 namespace sq {
+static int g_inner_tol_exp = 5;
+int set_inner_tol_exp(int e) {
+  if (e < 2 || e > 7) return 1;
+  g_inner_tol_exp = e;
+  return 0;
+}
+double inner_tol() { return std::pow(10.0, -(double)g_inner_tol_exp); }
 bool grid_size_ok(int N) { return valid_N(N); }
 void exp_sum_nodes(int N, int R, int dim, std::vector<double> &t, std::vector<double> &w) {
   rank_r_nodes(N, R, t, w, dim);
@@ -1019,6 +1026,7 @@ int sq_set_tiles(const sq_tile_config *tiles, int ntiles) {
 int sq_set_option(int key, int value) {
   if (key == SQ_OPT_STRIDED_TWO_STAGE) return set_strided_fast(value) == 0 ? SQ_OK : SQ_EINVAL;
   if (key == SQ_OPT_STENCIL_ROWS) return set_stencil_rows(value) == 0 ? SQ_OK : SQ_EINVAL;
+  if (key == SQ_OPT_INNER_TOL_EXP) return set_inner_tol_exp(value) == 0 ? SQ_OK : SQ_EINVAL;
   return SQ_EINVAL;
 }
 

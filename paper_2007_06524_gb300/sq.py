@@ -15,6 +15,7 @@ SQ_OK, SQ_EINVAL, SQ_ENOMEM, SQ_ECUDA, SQ_ENOCONV, SQ_ETIMEOUT, SQ_EBADGUESS = r
 SQ_FP64, SQ_FP32_REFINE = 0, 1
 SQ_OPT_STRIDED_TWO_STAGE = 1
 SQ_OPT_STENCIL_ROWS = 2
+SQ_OPT_INNER_TOL_EXP = 3
 
 _HERE = os.path.dirname(os.path.abspath(__file__))
 _LIB = None
