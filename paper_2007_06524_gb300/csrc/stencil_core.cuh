@@ -414,64 +414,69 @@ __device__ __forceinline__ void stencil_staged_run(const CellsDev &c, const floa
 #pragma unroll
   for (int r = 0; r < 4; ++r) xm[r] = x[(size_t)j1m0 * NN + row0 + r * N];
 
-  // ring slots of planes j1 (s0), j1 + 1 (s1) and j1 + kStages - 1 (sr, the slot of j1 - 1)
-  int s0 = 0, s1 = 1, sr = kStages - 1;
-  for (int k = 0; z0 + k < z1; ++k) {
-    const int j1 = z0 + k;
-    cp_async_wait<kStages - 3>();  // this thread's copies of planes j1, j1 + 1 have landed
-    __syncthreads();               // ... everyone's; and everyone is done with plane j1 - 1's slot
-    {
-      const int j = j1 + kStages - 1;
-      if (j <= z1) cp.issue(x + (size_t)(j == N ? 0 : j) * plane, ring_s + sr * kSlot * 4);
-      cp_async_commit();
-    }
-    if (k > 0) {
-      cpos = (cpos + 1 == n) ? 0 : cpos + 1;
-      if (pattern_changes<GEN>(c, cpos)) {
-        if (cpos <= 1) {
+  // The march is unrolled by the ring depth: plane j1 = z0 + k sits in slot
+  // u = k mod kStages, so the slots of planes j1 (s0), j1 + 1 (s1) and
+  // j1 + kStages - 1 (sr, the slot of j1 - 1) are compile-time constants.
+  const int toff = (1 + 4 * ty) * kSW + 4 + tx;
+  for (int kb = 0; z0 + kb < z1; kb += kStages) {
 #pragma unroll
-          for (int r = 0; r < 4; ++r) np[r] = nc[r];
+    for (int u = 0; u < kStages; ++u) {
+      const int k = kb + u;
+      const int j1 = z0 + k;
+      if (j1 >= z1) break;
+      const int s0 = u, s1 = (u + 1) % kStages, sr = (u + kStages - 1) % kStages;
+      cp_async_wait<kStages - 3>();  // this thread's copies of planes j1, j1 + 1 have landed
+      __syncthreads();               // ... everyone's; and everyone is done with plane j1 - 1's slot
+      {
+        const int j = j1 + kStages - 1;
+        if (j <= z1) cp.issue(x + (size_t)(j == N ? 0 : j) * plane, ring_s + sr * kSlot * 4);
+        cp_async_commit();
+      }
+      if (k > 0) {
+        cpos = (cpos + 1 == n) ? 0 : cpos + 1;
+        if (pattern_changes<GEN>(c, cpos)) {
+          if (cpos <= 1) {
+#pragma unroll
+            for (int r = 0; r < 4; ++r) np[r] = nc[r];
+          }
+          if (cpos == 0) row_nibbles<4, GEN>(c.phase, cellof[j1], LL, crow, c3a, c3b, mq, nc);
+          plane_masks<GEN>(c, cpos, pm0, pm1);
+          row_coeffs<float, 4, GEN>(tab, c.layers, nc, np, pm0, pm1, t);
         }
-        if (cpos == 0) row_nibbles<4, GEN>(c.phase, cellof[j1], LL, crow, c3a, c3b, mq, nc);
-        plane_masks<GEN>(c, cpos, pm0, pm1);
-        row_coeffs<float, 4, GEN>(tab, c.layers, nc, np, pm0, pm1, t);
+      }
+      const float *S0 = ring + s0 * kSlot + toff;
+      const float *S1 = ring + s1 * kSlot + toff;
+      if (k == 0) {
+#pragma unroll
+        for (int r = 0; r < 4; ++r) x0[r] = S0[r * kSW];
+      }
+      float xp[4];
+#pragma unroll
+      for (int r = 0; r < 4; ++r) xp[r] = S1[r * kSW];
+      float *yp = y + (size_t)j1 * NN + row0;
+      float psum = 0.f;
+#pragma unroll
+      for (int r = 0; r < 4; ++r) {
+        const float *cr = S0 + r * kSW;
+        const float x2m = (r == 0) ? cr[-kSW] : x0[r > 0 ? r - 1 : 0];
+        const float x2p = (r == 3) ? cr[kSW] : x0[r < 3 ? r + 1 : 3];
+        float off = t[r][0] * xp[r];
+        off = fmaf(t[r][1], xm[r], off);
+        off = fmaf(t[r][2], x2p, off);
+        off = fmaf(t[r][3], x2m, off);
+        off = fmaf(t[r][4], cr[1], off);
+        off = fmaf(t[r][5], cr[-1], off);
+        const float ax = fmaf(t[r][6], x0[r], -off);
+        yp[r * N] = ax;
+        psum = fmaf(x0[r], ax, psum);
+      }
+      acc.add(psum);
+#pragma unroll
+      for (int r = 0; r < 4; ++r) {
+        xm[r] = x0[r];
+        x0[r] = xp[r];
       }
     }
-    const float *S0 = ring + s0 * kSlot + (1 + 4 * ty) * kSW + 4 + tx;
-    const float *S1 = ring + s1 * kSlot + (1 + 4 * ty) * kSW + 4 + tx;
-    if (k == 0) {
-#pragma unroll
-      for (int r = 0; r < 4; ++r) x0[r] = S0[r * kSW];
-    }
-    float xp[4];
-#pragma unroll
-    for (int r = 0; r < 4; ++r) xp[r] = S1[r * kSW];
-    float *yp = y + (size_t)j1 * NN + row0;
-    float psum = 0.f;
-#pragma unroll
-    for (int r = 0; r < 4; ++r) {
-      const float *cr = S0 + r * kSW;
-      const float x2m = (r == 0) ? cr[-kSW] : x0[r > 0 ? r - 1 : 0];
-      const float x2p = (r == 3) ? cr[kSW] : x0[r < 3 ? r + 1 : 3];
-      float off = t[r][0] * xp[r];
-      off = fmaf(t[r][1], xm[r], off);
-      off = fmaf(t[r][2], x2p, off);
-      off = fmaf(t[r][3], x2m, off);
-      off = fmaf(t[r][4], cr[1], off);
-      off = fmaf(t[r][5], cr[-1], off);
-      const float ax = fmaf(t[r][6], x0[r], -off);
-      yp[r * N] = ax;
-      psum = fmaf(x0[r], ax, psum);
-    }
-    acc.add(psum);
-#pragma unroll
-    for (int r = 0; r < 4; ++r) {
-      xm[r] = x0[r];
-      x0[r] = xp[r];
-    }
-    s0 = s1;
-    s1 = (s1 + 1 == kStages) ? 0 : s1 + 1;
-    sr = (sr + 1 == kStages) ? 0 : sr + 1;
   }
   cp_async_wait<0>();
 }
