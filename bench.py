@@ -282,6 +282,16 @@ def run_native(args):
     kernels, roof = kernel_table(sq.sq_profile_work(), prof, N, elem, R, t_ms)
     gpu_launches = int(sum(cnt for _, cnt in prof.values()))
 
+    # whole-solve HBM fraction: the fused iteration's 17 field passes (operator
+    # 2, x3 in 4, x2 2 + 2, x1 2, x3 out 5) of s-byte words per PCG iteration,
+    # against the solve's wall time (setup passes, residual recomputations
+    # and A_hom are not counted: a lower bound on the bytes moved)
+    def solve_hbm(its_mean, solves_per_s, s_bytes):
+        gbs = 17 * s_bytes * N ** 3 * its_mean * solves_per_s / 1e9
+        pk = _peaks()
+        return {"algorithmic_GBps": round(gbs, 1), "peak": pk["hbm_gbs"], "peak_src": pk["src"],
+                "frac": round(gbs / pk["hbm_gbs"], 4), "bytes_per_iteration": 17 * s_bytes * N ** 3}
+
     out = {"metric": METRIC, "value": round(value, 4), "unit": UNIT, "n_gpus": ws, "steps": args.steps,
            "warmup": args.warmup, "ms_per_step": round(t_ms / args.steps, 3), "higher_is_better": True,
            "scaling": "weak", "vs_baseline": None, "dtype": "f64" if elem == 8 else "f32+f64",
@@ -289,6 +299,7 @@ def run_native(args):
            "config": workload_config(args, ws),
            "clocks": clocks, "gpu_launches": gpu_launches, "roofline": roof, "kernels": kernels,
            "iters": {"mean": round(statistics.mean(iters), 2), "min": min(iters), "max": max(iters)},
+           "solve_hbm": solve_hbm(statistics.mean(iters), value / max(ws, 1), elem),
            "converged": ok, "tiles": {"dht_pencils_fp32": tiles[0], "stencil_planes": tiles[1],
                                                 "stencil_rows_fp32": tiles[2]}}
 
@@ -330,7 +341,9 @@ def run_native(args):
             ev1.record(stream)
             torch.cuda.synchronize()
             tv = ev0.elapsed_time(ev1)
-            variants[label] = {"solves_per_s": round(3 * nst / (tv / 1e3), 3), "iters_mean": round(statistics.mean(its), 1)}
+            variants[label] = {"solves_per_s": round(3 * nst / (tv / 1e3), 3), "iters_mean": round(statistics.mean(its), 1),
+                               "solve_hbm": solve_hbm(statistics.mean(its), 3 * nst / (tv / 1e3),
+                                                      4 if pp == sq.SQ_FP32_REFINE else 8)}
             if label == "fp32_refine_rank8":
                 # per-kernel table from one more, profiled realization (the
                 # event pairs around every launch would slow the timed steps)
