@@ -42,7 +42,7 @@ struct Scalars {
   int x_pending;    // 1: x += alpha p of the last iteration not applied yet
   int breakdown;    // 1: non-positive p.Ap or r.z
   unsigned int ticket;  // last-block counter (reset by the last block)
-  int pad;
+  int fault;            // 1: a bounded device wait gave up (the kernel fell back; reported as SQ_ETIMEOUT)
 };
 
 enum FinalizeOp : int {

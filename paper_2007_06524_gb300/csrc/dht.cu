@@ -43,6 +43,7 @@ struct DhtArgs {
   int check_done;
   int logP;
   int ntiles;
+  int stage;  // pass E with the PCG update: stage the tile's p and x rows (set by the launcher)
 };
 
 template <typename T, int AXIS, int LOADM, int STOREM, bool SCALE>
@@ -203,13 +204,53 @@ __global__ void __launch_bounds__(kThreads, s2_min_blocks(R0 * R1)) k_dht_s3(Dht
   t.first = a.first;
   t.logP = a.logP;
   Accum<float> acc;
+  // Pass E with the PCG update: the tile's p and x rows (2P N contiguous
+  // floats each) are fetched into shared memory by two bulk copies issued at
+  // the start of the tile, so they land while the tile is transformed.
+  // Every wait is bounded; a thread whose wait gives up reads global memory
+  // and flags the fault, and the block stops staging (that barrier phase
+  // never completed and must not be armed again).
+  __shared__ __align__(8) unsigned long long mbar;
+  __shared__ int s_stage_off;
+  float *pl = nullptr, *xl = nullptr;
+  bool staged = (STOREM == SO_PCG) && !a.first && a.stage;
+  unsigned phase = 0;
+  bool late = false;  // a wait gave up: that phase's copies may still be in flight
+  if (staged) {
+    pl = reinterpret_cast<float *>(tw + N);
+    xl = pl + 2 * P * N;
+    if (threadIdx.x == 0) {
+      mbar_init(&mbar, 1);
+      s_stage_off = 0;
+    }
+  }
+  constexpr unsigned kRowBytes = 2u * P * N * sizeof(float);
   for (int tile = blockIdx.x; tile < a.ntiles; tile += gridDim.x) {
-    __syncthreads();  // twiddles loaded; the previous tile's combine is done with sm
+    __syncthreads();  // twiddles loaded; the previous tile's combine is done with sm, pl, xl
+    if (staged && s_stage_off) staged = false;
     const size_t row0 = (size_t)tile * 2 * P;
+    if (staged && threadIdx.x == 0) {
+      asm volatile("fence.proxy.async.shared::cta;\n" ::: "memory");
+      mbar_expect_tx(&mbar, 2 * kRowBytes);
+      bulk_g2s(pl, a.p + row0 * N, kRowBytes, &mbar);
+      bulk_g2s(xl, a.x + row0 * N, kRowBytes, &mbar);
+    }
     x3_stage1<float, C, R0, R1, P, LOADM>(t, row0, sm, acc);
     x3_stage2<float, C, R0, R1, P>(sm, tw);
-    x3_combine<float, C, N, P, STOREM>(t, row0, sm);
+    if (staged) {
+      const bool ok = mbar_wait(&mbar, phase, 1 << 22);
+      phase ^= 1u;
+      if (!ok) {
+        a.rb.st->fault = 1;
+        s_stage_off = 1;
+        late = true;
+      }
+      x3_combine<float, C, N, P, STOREM>(t, row0, sm, ok ? pl : nullptr, ok ? xl : nullptr);
+    } else {
+      x3_combine<float, C, N, P, STOREM>(t, row0, sm);
+    }
   }
+  if (late) mbar_wait(&mbar, phase ^ 1u, 1 << 24);  // do not leave with a copy into this block in flight
   if (LOADM == LD_RESID) {
     FF v[1] = {acc.part()};
     double s[1];
@@ -219,13 +260,20 @@ __global__ void __launch_bounds__(kThreads, s2_min_blocks(R0 * R1)) k_dht_s3(Dht
   }
 }
 
+
 template <int R0, int R1, int P, int LOADM, int STOREM>
 static cudaError_t launch_s3(const DhtArgs<float> &a, int grid, cudaStream_t s) {
-  const size_t smem = ((size_t)P * x3pos(R0 * R1) + (size_t)R0 * R1) * sizeof(float2);
+  // pass E with the PCG update also stages the tile's p and x rows, where the
+  // block still fits twice on an SM
+  const size_t base = ((size_t)P * x3pos(R0 * R1) + (size_t)R0 * R1) * sizeof(float2);
+  const size_t rows = 2 * (size_t)(2 * P * R0 * R1) * sizeof(float);
+  DhtArgs<float> b = a;
+  b.stage = (STOREM == SO_PCG && !a.first && base + rows <= 110 * 1024) ? 1 : 0;
+  const size_t smem = base + (b.stage ? rows : 0);
   auto kern = k_dht_s3<R0, R1, P, LOADM, STOREM>;
   cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
   if (e != cudaSuccess) return e;
-  kern<<<grid, kThreads, smem, s>>>(a);
+  kern<<<grid, kThreads, smem, s>>>(b);
   return cudaGetLastError();
 }
 
@@ -329,6 +377,7 @@ cudaError_t launch_dht_pass(int pass, const SpectralDev &sp, const T *in, T *out
   a.first = first ? 1 : 0;
   a.check_done = check_done ? 1 : 0;
   a.logP = logP;
+  a.stage = 0;
   a.ntiles = (int)(((long long)N * N) / (2 * P));
   const int grid = a.ntiles < 8192 ? a.ntiles : 8192;
   const size_t smem = dht_smem_bytes_t<T>(N, P, pass == PASS_C ? sp.rank : 0);
@@ -370,6 +419,7 @@ cudaError_t launch_dht_pass_2d(int pass, const SpectralDev &sp, const T *in, T *
   a.first = first ? 1 : 0;
   a.check_done = check_done ? 1 : 0;
   a.logP = logP;
+  a.stage = 0;
   a.ntiles = N / (2 * P);
   const int grid = a.ntiles;
   const size_t smem = dht_smem_bytes_t<T>(N, P, pass == PASS_C ? sp.rank : 0);

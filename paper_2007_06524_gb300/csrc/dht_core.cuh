@@ -618,6 +618,8 @@ __device__ __forceinline__ void x3_stage1(const DhtTile<T> &a, size_t row0, C *s
   constexpr int SJ = x3pos(N);
   constexpr int HC = R0 > 8 ? 8 : R0;
   const T alpha = a.alpha;
+  const T *inp = a.in;
+  const T *qp = a.q;
   for (int t = threadIdx.x; t < R1 * P; t += kThreads) {
     const int p = t / R1, b = t - p * R1;
     const size_t ga = (row0 + 2 * p) * N + b, gb = ga + N;
@@ -627,15 +629,15 @@ __device__ __forceinline__ void x3_stage1(const DhtTile<T> &a, size_t row0, C *s
       T va[HC], vb[HC];
 #pragma unroll
       for (int q = 0; q < HC; ++q) {
-        va[q] = a.in[ga + (h + q) * R1];
-        vb[q] = a.in[gb + (h + q) * R1];
+        va[q] = inp[ga + (h + q) * R1];
+        vb[q] = inp[gb + (h + q) * R1];
       }
       if (LOADM == LD_RESID && !a.first) {
         T qa[HC], qb[HC];
 #pragma unroll
         for (int q = 0; q < HC; ++q) {
-          qa[q] = a.q[ga + (h + q) * R1];
-          qb[q] = a.q[gb + (h + q) * R1];
+          qa[q] = qp[ga + (h + q) * R1];
+          qb[q] = qp[gb + (h + q) * R1];
         }
 #pragma unroll
         for (int q = 0; q < HC; ++q) {
@@ -679,20 +681,66 @@ __device__ __forceinline__ void x3_stage2(C *sm, const C *__restrict__ tw) {
   __syncthreads();
 }
 
+// ------------------------------------------------- bulk copies (sm_90+)
+// One-dimensional global -> shared copies by the asynchronous copy engine,
+// completing on a shared-memory mbarrier (transaction count in bytes).
+// Addresses and sizes must be multiples of 16 bytes.
+__device__ __forceinline__ unsigned smem_u32(const void *p) { return (unsigned)__cvta_generic_to_shared(p); }
+__device__ __forceinline__ void mbar_init(unsigned long long *mbar, unsigned count) {
+  asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;\n" ::"r"(smem_u32(mbar)), "r"(count) : "memory");
+  asm volatile("fence.mbarrier_init.release.cluster;\n" ::: "memory");
+  asm volatile("fence.proxy.async.shared::cta;\n" ::: "memory");
+}
+// Arms the barrier's current phase for `bytes` and issues the copy (one thread).
+__device__ __forceinline__ void bulk_g2s(void *dst, const void *src, unsigned bytes, unsigned long long *mbar) {
+  asm volatile("cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];\n" ::"r"(
+                   smem_u32(dst)),
+               "l"(src), "r"(bytes), "r"(smem_u32(mbar))
+               : "memory");
+}
+__device__ __forceinline__ void mbar_expect_tx(unsigned long long *mbar, unsigned bytes) {
+  asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;\n" ::"r"(smem_u32(mbar)), "r"(bytes)
+               : "memory");
+}
+// Waits, at most max_tries polls, for the phase of parity `parity` to complete.
+__device__ __forceinline__ bool mbar_wait(unsigned long long *mbar, unsigned parity, int max_tries) {
+  for (int i = 0; i < max_tries; ++i) {
+    unsigned done;
+    asm volatile(
+        "{\n .reg .pred p;\n mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n selp.u32 %0, 1, 0, p;\n}\n"
+        : "=r"(done)
+        : "r"(smem_u32(mbar)), "r"(parity)
+        : "memory");
+    if (done) return true;
+  }
+  return false;
+}
+
 // Stores the values v[0..3] of row positions g[0..3]: plain, or the fused PCG
 // update (all loads of the four positions before any store; see x3_stage1).
+// pl / xl: the tile's p and x rows staged in shared memory (element g at
+// g - base), or null to read them from global memory.
 template <typename T, int STOREM>
-__device__ __forceinline__ void x3_put4(const DhtTile<T> &a, const size_t (&g)[4], const T (&v)[4]) {
+__device__ __forceinline__ void x3_put4(const DhtTile<T> &a, const size_t (&g)[4], const T (&v)[4],
+                                        const T *pl = nullptr, const T *xl = nullptr, size_t base = 0) {
   if (STOREM == SO_PCG) {
     if (a.first) {
 #pragma unroll
       for (int i = 0; i < 4; ++i) a.p[g[i]] = v[i];
     } else {
       T po[4], xo[4];
+      if (pl) {
 #pragma unroll
-      for (int i = 0; i < 4; ++i) {
-        po[i] = a.p[g[i]];
-        xo[i] = a.x[g[i]];
+        for (int i = 0; i < 4; ++i) {
+          po[i] = pl[g[i] - base];
+          xo[i] = xl[g[i] - base];
+        }
+      } else {
+#pragma unroll
+        for (int i = 0; i < 4; ++i) {
+          po[i] = a.p[g[i]];
+          xo[i] = a.x[g[i]];
+        }
       }
 #pragma unroll
       for (int i = 0; i < 4; ++i) {
@@ -707,7 +755,8 @@ __device__ __forceinline__ void x3_put4(const DhtTile<T> &a, const size_t (&g)[4
 }
 
 template <typename T, typename C, int N, int P, int STOREM>
-__device__ __forceinline__ void x3_combine(const DhtTile<T> &a, size_t row0, const C *sm) {
+__device__ __forceinline__ void x3_combine(const DhtTile<T> &a, size_t row0, const C *sm, const T *pl = nullptr,
+                                           const T *xl = nullptr) {
   constexpr int H = N / 2;
   constexpr int SJ = x3pos(N);
   for (int t = threadIdx.x; t < H * P; t += kThreads) {
@@ -720,7 +769,7 @@ __device__ __forceinline__ void x3_combine(const DhtTile<T> &a, size_t row0, con
     const C hk = hartley_pair(X, k == 0 ? X : Y), hm = hartley_pair(Y, k == 0 ? Y : X);
     const size_t g[4] = {ga + k, gb + k, ga + km, gb + km};
     const T v[4] = {hk.x, hk.y, hm.x, hm.y};
-    x3_put4<T, STOREM>(a, g, v);
+    x3_put4<T, STOREM>(a, g, v, pl, xl, row0 * N);
   }
 }
 

@@ -552,6 +552,7 @@ int solve_fp32_refine(const sq_coeffs *c, const sq_precond *pc, sq_workspace *w,
     SQ_LAUNCH(PC_VECTOR, s, launch_add_f32_to_f64(psi, d, n3, s));
     st = read_scalars(hi, ri.st, s);
     if (st != SQ_OK) return st;
+    if (hi->fault) return SQ_ETIMEOUT;  // a bounded wait in a kernel gave up (results are still complete)
     relres_in = (hi->bb > 0.0) ? std::sqrt(hi->rr / hi->bb) : 0.0;
     total_inner += hi->iter;
     ++outer;
