@@ -353,8 +353,9 @@ enum StencilMode : int { ST_MATVEC = 0, ST_RESID = 1, ST_RHS = 2 };
 template <typename Ti, typename To>
 cudaError_t launch_stencil(const CellsDev &c, int mode, int dir, const Ti *x, To *y, RedBuf rb, int fin,
                            bool check_done, cudaStream_t s);
+// energy: also the six sums of the energy form (quantities 12..17)
 cudaError_t launch_ahom(const CellsDev &c, const double *p0, const double *p1, const double *p2, RedBuf rb,
-                        cudaStream_t s);
+                        bool energy, cudaStream_t s);
 template <typename T>
 cudaError_t launch_x_final_sum(T *x, const T *p, RedBuf rb, long long n, cudaStream_t s);
 template <typename T>

@@ -112,7 +112,7 @@ extern "C" int sq_homogenized_matrix_noalloc(int L, int n, const uint8_t *phase,
   RedBuf rb;
   rb.st = sc;
   rb.partials = scratch + kScalarsDoubles;
-  if (launch_ahom(c, psi0, psi1, psi2, rb, s) != cudaSuccess) return SQ_ECUDA;
+  if (launch_ahom(c, psi0, psi1, psi2, rb, true, s) != cudaSuccess) return SQ_ECUDA;
   const double nn = (double)c.N * c.N * c.N;
   k_ahom_finish<<<1, 32, 0, s>>>(scratch, nn, out);
   if (cudaGetLastError() != cudaSuccess) return SQ_ECUDA;

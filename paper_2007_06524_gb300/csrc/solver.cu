@@ -533,7 +533,11 @@ int solve_fp32_refine(const sq_coeffs *c, const sq_precond *pc, sq_workspace *w,
   double relres_in = 0.0;
   for (;;) {
     // FP64 true residual, stored as the FP32 right-hand side of the correction
-    SQ_LAUNCH(PC_RESID, s, (launch_stencil<double, float>(cd, ST_RESID, dir, psi, r, ro, FIN_RESID, false, s)));
+    // (from psi = 0 it is b itself: the right-hand-side sweep, no operator)
+    if (outer == 0 && !used_guess)
+      SQ_LAUNCH(PC_RESID, s, (launch_stencil<double, float>(cd, ST_RHS, dir, nullptr, r, ro, FIN_RESID, false, s)));
+    else
+      SQ_LAUNCH(PC_RESID, s, (launch_stencil<double, float>(cd, ST_RESID, dir, psi, r, ro, FIN_RESID, false, s)));
     int st = read_scalars(ho, ro.st, s);
     if (st != SQ_OK) return st;
     if (ho->done || total_inner >= max_iter || outer >= 30) break;
@@ -1105,7 +1109,7 @@ int sq_homogenized_matrix(const sq_coeffs *c, const double *psi0, const double *
   if (!c || !psi0 || !psi1 || !psi2 || !A_hom) return SQ_EINVAL;
   cudaStream_t s = reinterpret_cast<cudaStream_t>(stream);
   const RedBuf rb = redbuf<double>(c->d_st, c->d_partials);
-  SQ_LAUNCH(PC_AHOM, s, launch_ahom(cells_dev(c), psi0, psi1, psi2, rb, s));
+  SQ_LAUNCH(PC_AHOM, s, launch_ahom(cells_dev(c), psi0, psi1, psi2, rb, A_energy != nullptr, s));
   int st = read_scalars(c->h_st, c->d_st, s);
   if (st != SQ_OK) return st;
   const double nn = (double)c->N * c->N * c->N;

@@ -292,6 +292,9 @@ template cudaError_t launch_stencil<double, float>(const CellsDev &, int, int, c
 // E_ij = mean(sum_d a_d (delta_id + D_d psi_i)(delta_jd + D_d psi_j)).
 // Reduced quantities: 0..8 M[i][j] = sum a_j D_j psi_i, 9..11 sum a_j,
 // 12..17 energy sums for (i,j) in (00,01,02,11,12,22).
+// ENERGY = false skips the six energy sums (most of the kernel's FP64 work)
+// when the caller only wants the edge form.
+template <bool ENERGY>
 __global__ void __launch_bounds__(kThreads) k_ahom(CellsDev c, const double *__restrict__ p0,
                                                    const double *__restrict__ p1, const double *__restrict__ p2,
                                                    RedBuf rb, int zc) {
@@ -348,17 +351,19 @@ __global__ void __launch_bounds__(kThreads) k_ahom(CellsDev c, const double *__r
         for (int d = 0; d < 3; ++d) acc[3 * i + d] = fma(a[d], g[i][d], acc[3 * i + d]);
 #pragma unroll
       for (int d = 0; d < 3; ++d) acc[9 + d] += a[d];
-      int q = 12;
+      if constexpr (ENERGY) {
+        int q = 12;
 #pragma unroll
-      for (int i = 0; i < 3; ++i)
+        for (int i = 0; i < 3; ++i)
 #pragma unroll
-        for (int jj = i; jj < 3; ++jj) {
-          double e = 0.0;
+          for (int jj = i; jj < 3; ++jj) {
+            double e = 0.0;
 #pragma unroll
-          for (int d = 0; d < 3; ++d)
-            e += a[d] * ((i == d ? 1.0 : 0.0) + g[i][d]) * ((jj == d ? 1.0 : 0.0) + g[jj][d]);
-          acc[q++] += e;
-        }
+            for (int d = 0; d < 3; ++d)
+              e += a[d] * ((i == d ? 1.0 : 0.0) + g[i][d]) * ((jj == d ? 1.0 : 0.0) + g[jj][d]);
+            acc[q++] += e;
+          }
+      }
     }
   }
   double s[18];
@@ -378,15 +383,16 @@ static int ahom_zc(int N) {
 }
 
 cudaError_t launch_ahom(const CellsDev &c, const double *p0, const double *p1, const double *p2, RedBuf rb,
-                        cudaStream_t s) {
+                        bool energy, cudaStream_t s) {
   const int N = c.N;
   const int zc = ahom_zc(N);
   dim3 grid((N + 31) / 32, (N + 7) / 8, (N + zc - 1) / zc);
   if ((long long)grid.x * grid.y * grid.z > kMaxPartials) return cudaErrorInvalidConfiguration;
   const size_t smem = tab_bytes<double>(c.layers);
-  const cudaError_t e = allow_dynamic_smem((const void *)k_ahom, smem);
+  auto kern = energy ? k_ahom<true> : k_ahom<false>;
+  const cudaError_t e = allow_dynamic_smem((const void *)kern, smem);
   if (e != cudaSuccess) return e;
-  k_ahom<<<grid, dim3(32, 8, 1), smem, s>>>(c, p0, p1, p2, rb, zc);
+  kern<<<grid, dim3(32, 8, 1), smem, s>>>(c, p0, p1, p2, rb, zc);
   return cudaGetLastError();
 }
 

@@ -417,13 +417,16 @@ def sq_pcg_solve(c, pc, w, dir, tol, max_iter, precision, x0, psi, stream=None) 
     return {k: getattr(info, k) for k, _ in SolveInfo._fields_}
 
 
-def sq_homogenized_matrix(c, psi0, psi1, psi2, stream=None):
+def sq_homogenized_matrix(c, psi0, psi1, psi2, stream=None, energy=True):
+    """(A_hom edge form, energy form); energy=False skips the energy form
+    (returned as None), which is most of the kernel's FP64 work."""
     A = np.zeros(9)
-    E = np.zeros(9)
+    E = np.zeros(9) if energy else None
     _check(load_library().sq_homogenized_matrix(c, _ptr(psi0), _ptr(psi1), _ptr(psi2),
-                                                A.ctypes.data_as(C.c_void_p), E.ctypes.data_as(C.c_void_p),
+                                                A.ctypes.data_as(C.c_void_p),
+                                                E.ctypes.data_as(C.c_void_p) if energy else None,
                                                 _stream(stream)), "sq_homogenized_matrix")
-    return A.reshape(3, 3), E.reshape(3, 3)
+    return A.reshape(3, 3), (E.reshape(3, 3) if energy else None)
 
 
 def sq_homogenized_matrix_noalloc(L, n, phase, a_lo, a_hi, psi0, psi1, psi2, out, stream=None):
