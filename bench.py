@@ -145,15 +145,18 @@ def _algorithmic(N, elem, rank_r):
 
     bytes: the fields each kernel must read and write once (N^3 elements of
     `elem` bytes); flops: one real 1D Hartley pass = 2.5 log2 N + 3 per point
-    (half-length complex FFT convention + the Hartley combine)."""
+    (half-length complex FFT convention + the Hartley combine). Pass C does two
+    transforms with no combine (the scaling is applied to the complex
+    spectrum): 2 x 2.5 log2 N, plus the multiplier (2R, or 4 for the exact
+    1/x) and 6 for the scaling and the r.z sum."""
     n3 = N ** 3
     f = 2.5 * math.log2(N) + 3.0
-    scale = (2 * rank_r + 3) if rank_r else 7
+    scale = (2 * rank_r + 6) if rank_r else 10
     return {
         "stencil_matvec": (2 * elem * n3, 15 * n3),
         "dht_x3_in": (4 * elem * n3, (f + 4) * n3),
         "dht_x2": (2 * elem * n3, f * n3),
-        "dht_x1_scale": (2 * elem * n3, (2 * f + scale) * n3),
+        "dht_x1_scale": (2 * elem * n3, (2 * (f - 3.0) + scale) * n3),
         "dht_x3_out": (5 * elem * n3, (f + 4) * n3),
     }
 

@@ -320,9 +320,7 @@ __device__ __forceinline__ void dht_tile(const SpectralDev &sp, const DhtTile<T>
       const int k = t >> logP;
       const int km = (k == 0) ? 0 : N - k;
       const C X = res[k * SP + p], Y = res[km * SP + p];
-      T ak = X.x - X.y + Y.x + Y.y, bk = X.x + X.y - Y.x + Y.y;
-      T akm = Y.x - Y.y + X.x + X.y, bkm = Y.x + Y.y - X.x + X.y;
-      if (SCALE) {
+      if (SCALE) {  // pass C: the Fourier-domain scaling described at s2_combine
         const int k3a = c0 + 2 * p, k3b = k3a + 1;
         T ga, gb;
         if (R == 0) {
@@ -340,32 +338,23 @@ __device__ __forceinline__ void dht_tile(const SpectralDev &sp, const DhtTile<T>
           ga = (k == 0 && k2 == 0 && k3a == 0) ? (T)0 : sa;
           gb = sb;  // k3b >= 1
         }
-        T e2 = fma(ga * ak, ak, gb * bk * bk);
-        if (km != k) e2 += fma(ga * akm, akm, gb * bkm * bkm);
+        const T sx = X.x + Y.x, dy = X.y - Y.y, dx = X.x - Y.x, sy = X.y + Y.y;
+        T e2 = fma(ga, fma(sx, sx, dy * dy), gb * fma(dx, dx, sy * sy));
+        if (km != k) e2 += e2;
         acc.add(e2);
-        ak *= ga;
-        akm *= ga;
-        bk *= gb;
-        bkm *= gb;
+        const T s4 = (T)2 * (ga + gb), d4 = (T)2 * (ga - gb);
+        res[k * SP + p] = C{fma(s4, X.x, d4 * Y.x), fma(d4, Y.y, -s4 * X.y)};
+        if (km != k) res[km * SP + p] = C{fma(s4, Y.x, d4 * X.x), fma(d4, X.y, -s4 * Y.y)};
+      } else {
+        res[k * SP + p] = C{X.x - X.y + Y.x + Y.y, X.x + X.y - Y.x + Y.y};
+        if (km != k) res[km * SP + p] = C{Y.x - Y.y + X.x + X.y, Y.x + Y.y - X.x + X.y};
       }
-      res[k * SP + p] = C{ak, bk};
-      if (km != k) res[km * SP + p] = C{akm, bkm};
     }
     __syncthreads();
   }
-  if (SCALE) {
+  if (SCALE) {  // the inverse: forward transform of conj(W), stored conjugated (below)
     C *other = (res == buf0) ? buf1 : buf0;
     res = fft_all<T, C>(res, other, tw, sp, SP, logP);
-    const int halfN = N >> 1;
-    for (int t = tid; t < ((halfN + 1) << logP); t += kThreads) {
-      const int p = t & (P - 1);
-      const int k = t >> logP;
-      const int km = (k == 0) ? 0 : N - k;
-      const C X = res[k * SP + p], Y = res[km * SP + p];
-      res[k * SP + p] = C{X.x - X.y + Y.x + Y.y, X.x + X.y - Y.x + Y.y};
-      if (km != k) res[km * SP + p] = C{Y.x - Y.y + X.x + X.y, Y.x + Y.y - X.x + X.y};
-    }
-    __syncthreads();
   }
   // ----------------------------------------------------------------- store
   if (AXIS == 3) {
@@ -401,7 +390,8 @@ __device__ __forceinline__ void dht_tile(const SpectralDev &sp, const DhtTile<T>
       const int p = e & (P - 1);
       const int j = e >> logP;
       const size_t g = base + (size_t)j * stride + 2 * p;
-      reinterpret_cast<C *>(a.out)[g >> 1] = res[j * SP + p];
+      const C v = res[j * SP + p];
+      reinterpret_cast<C *>(a.out)[g >> 1] = SCALE ? C{v.x, -v.y} : v;
     }
   }
 }
@@ -516,8 +506,20 @@ __device__ __forceinline__ void s2_multiplier(const SpectralDev &sp, int k, int 
   }
 }
 
-// MODE 0: store to global (rows of P complex values, coalesced); 1: scale by
-// G, reduce r.z into acc, write back in place for the second transform.
+// Pass C scales in the Fourier domain. Along x1 the multiplier g is even
+// (g(k) = g(N-k)), so H diag(g) H = F* diag(g) F: with the two real pencils
+// a, b of a complex pencil, Z = F(a + ib), A = F a = (Z_k + conj Z_{N-k}) / 2
+// and B = F b = (Z_k - conj Z_{N-k}) / 2i, the scaled spectrum is
+//   W_k = g_a A_k + i g_b B_k = s Z_k + d conj(Z_{N-k}),
+//   s = (g_a + g_b) / 2, d = (g_a - g_b) / 2,
+// and F*(W) = conj(F(conj W)) has the results for a and b as its real and
+// imaginary parts: the inverse is the forward transform of conj(W), stored
+// conjugated, with no Hartley combine on either side. The factor 4 of the
+// two Hartley combines this replaces is folded into s and d, so G's scale is
+// unchanged. r.z (Parseval): g_a |A_k|^2 + g_b |B_k|^2 per k.
+// s2_combine MODE 0: Hartley combine, store to global (rows of P complex
+// values, coalesced); 1: pass C's scaling above, reduce r.z into acc, write
+// conj(W) back in place for the second transform; 2: store the conjugate.
 template <typename T, typename C, int N, int P, int MODE, int RR, long long STRIDE>
 __device__ __forceinline__ void s2_combine(C *sm, C *__restrict__ gdst, size_t base, const SpectralDev &sp, int k2,
                                            int c0, const T *vtab, Accum<T> &acc) {
@@ -536,18 +538,21 @@ __device__ __forceinline__ void s2_combine(C *sm, C *__restrict__ gdst, size_t b
     const int k = t >> LP;
     const int km = (k == 0) ? 0 : N - k;
     const C X = sm[k * SP + p], Y = sm[km * SP + p];
-    C hk = hartley_pair(X, Y), hm = hartley_pair(Y, X);
     if (MODE == 1) {
       T ga, gb;
-      s2_multiplier<T, N, P, RR>(sp, k, k2, c0, p, vtab, va, vb, ga, gb);
-      T e2 = fma(ga * hk.x, hk.x, gb * hk.y * hk.y);
-      if (km != k) e2 += fma(ga * hm.x, hm.x, gb * hm.y * hm.y);
+      s2_multiplier<T, N, P, RR>(sp, k, k2, c0, p, vtab, va, vb, ga, gb);  // G(N - k) = G(k)
+      const T sx = X.x + Y.x, dy = X.y - Y.y, dx = X.x - Y.x, sy = X.y + Y.y;
+      T e2 = fma(ga, fma(sx, sx, dy * dy), gb * fma(dx, dx, sy * sy));
+      if (km != k) e2 += e2;  // the partner k' = N - k contributes the same
       acc.add(e2);
-      hk = C{hk.x * ga, hk.y * gb};
-      hm = C{hm.x * ga, hm.y * gb};  // G(N - k) = G(k)
-      sm[k * SP + p] = hk;
-      if (km != k) sm[km * SP + p] = hm;
+      const T s4 = (T)2 * (ga + gb), d4 = (T)2 * (ga - gb);
+      sm[k * SP + p] = C{fma(s4, X.x, d4 * Y.x), fma(d4, Y.y, -s4 * X.y)};
+      if (km != k) sm[km * SP + p] = C{fma(s4, Y.x, d4 * X.x), fma(d4, X.y, -s4 * Y.y)};
+    } else if (MODE == 2) {
+      g[(size_t)k * (STRIDE >> 1)] = C{X.x, -X.y};
+      if (km != k) g[(size_t)km * (STRIDE >> 1)] = C{Y.x, -Y.y};
     } else {
+      const C hk = hartley_pair(X, Y), hm = hartley_pair(Y, X);
       g[(size_t)k * (STRIDE >> 1)] = hk;
       if (km != k) g[(size_t)km * (STRIDE >> 1)] = hm;
     }
@@ -587,8 +592,10 @@ __device__ __forceinline__ void dht_tile_s2(const SpectralDev &sp, const DhtTile
     s2_combine<T, C, N, P, 1, RR, STRIDE>(sm, gout, base, sp, k2, c0, vtab, acc);
     s2_stage1<T, C, R0, R1, P, true, STRIDE>(gin, base, sm);
     s2_stage2<T, C, R0, R1, P>(sm, tw);
+    s2_combine<T, C, N, P, 2, RR, STRIDE>(sm, gout, base, sp, k2, c0, vtab, acc);
+  } else {
+    s2_combine<T, C, N, P, 0, RR, STRIDE>(sm, gout, base, sp, k2, c0, vtab, acc);
   }
-  s2_combine<T, C, N, P, 0, RR, STRIDE>(sm, gout, base, sp, k2, c0, vtab, acc);
 }
 
 // ----------------------------------------------------------------------------
