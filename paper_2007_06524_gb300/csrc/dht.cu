@@ -268,7 +268,9 @@ static cudaError_t launch_s3(const DhtArgs<float> &a, int grid, cudaStream_t s) 
   const size_t base = ((size_t)P * x3pos(R0 * R1) + (size_t)R0 * R1) * sizeof(float2);
   const size_t rows = 2 * (size_t)(2 * P * R0 * R1) * sizeof(float);
   DhtArgs<float> b = a;
-  b.stage = (STOREM == SO_PCG && !a.first && base + rows <= 110 * 1024) ? 1 : 0;
+  // bulk copies need 16-byte aligned rows (the workspace fields are)
+  const bool aligned = ((reinterpret_cast<uintptr_t>(a.p) | reinterpret_cast<uintptr_t>(a.x)) & 15) == 0;
+  b.stage = (STOREM == SO_PCG && !a.first && aligned && base + rows <= 110 * 1024) ? 1 : 0;
   const size_t smem = base + (b.stage ? rows : 0);
   auto kern = k_dht_s3<R0, R1, P, LOADM, STOREM>;
   cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);

@@ -46,3 +46,33 @@ def test_warm_start_weights_file():
     assert d["params"].shape == (n,) and d["params"].dtype == np.float32
     assert int(d["N"]) == 64 and float(d["scale"]) > 0
     assert np.all(np.isfinite(d["params"]))
+
+
+def test_bench_algorithmic_model():
+    import bench
+
+    N, R = 256, 8
+    alg = bench._algorithmic(N, 4, R)
+    n3 = N ** 3
+    # the fused iteration moves 17 field passes of 4-byte words
+    assert sum(b for b, _ in alg.values()) + alg["dht_x2"][0] == 17 * 4 * n3
+    # pass C: two transforms without combines, the rank-R multiplier, scaling and r.z
+    assert alg["dht_x1_scale"][1] == (2 * 2.5 * 8 + 2 * R + 6) * n3
+    assert bench._algorithmic(N, 8, 0)["dht_x1_scale"][1] == (2 * 2.5 * 8 + 10) * n3
+
+
+def test_new_bindings_reject_bad_arguments_before_calling_the_library():
+    from paper_2007_06524_gb300 import sq
+
+    with pytest.raises(ValueError):
+        sq.sq_build_coeffs_levels(4, 8, 0, (0.5, 0.5), (1.0, 2.0, 3.0))   # probs and values differ in length
+    with pytest.raises(ValueError):
+        sq.sq_coeffs_set_levels(None, (1.0,))                               # fewer than 2 levels
+    with pytest.raises(ValueError):
+        sq.sq_coeffs_set_levels(None, (1.0,) * 5)                           # more than 4 levels
+    with pytest.raises(ValueError):
+        sq.sq_coeffs_from_host_levels(4, 8, np.zeros(10, np.uint8), (1.0, 2.0))  # not L^3 bytes
+    with pytest.raises(ValueError):
+        sq.sq_precond_setup_canonical(32, np.ones((3, 32)), np.ones((4, 32)))     # factor shapes differ
+    with pytest.raises(ValueError):
+        sq.sq2d_coeffs_from_host(4, 4, np.zeros(15, np.uint8), 1.0, 2.0)         # not L^2 bytes
