@@ -15,6 +15,7 @@ namespace sq {
 
 constexpr int kThreads = 256;        // block size of every field kernel
 constexpr int kMaxPartials = 16384;  // max blocks of a reducing kernel
+constexpr int kPollChunk = 2;        // PCG iterations launched per host poll of the stop flag
 constexpr int kMaxQ = 24;            // max quantities reduced by one kernel
 constexpr int kMaxN = 512;
 constexpr int kMaxRank = 256;    // canonical terms of a preconditioner from given factors

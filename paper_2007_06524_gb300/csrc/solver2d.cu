@@ -300,10 +300,10 @@ int iteration2d(const Cells2D &cd, const sq2d_precond *pc, double *x, double *r,
   return SQ_OK;
 }
 
-// Iterations in chunks of 8, polling the device's stop flag one chunk behind.
+// Iterations in chunks of kPollChunk, polling the device's stop flag one chunk behind.
 int loop2d(sq2d_workspace *w, const Cells2D &cd, const sq2d_precond *pc, double *x, double *r, double *p, double *q,
            double *Y, RedBuf rb, int budget, cudaStream_t s) {
-  const int chunk = 8;
+  const int chunk = kPollChunk;
   int launched = 0, slot = 0;
   bool pending[2] = {false, false};
   w->h_poll[0] = w->h_poll[1] = 0;
