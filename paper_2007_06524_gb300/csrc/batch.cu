@@ -348,7 +348,9 @@ struct sq_batch {
 
 namespace {
 
-constexpr int kChunk = 8;
+// Inner iterations per graph replay (the host polls one replay behind):
+// 768 mixed solves measured 4315 / 4449 solves/s with 8 / 4.
+constexpr int kChunk = 4;
 constexpr size_t kStagedSmem = (size_t)kStages * kSlot * sizeof(float);  // ring of the staged inner operator
 
 #define SQB_CK(call)                        \
