@@ -30,7 +30,8 @@ coefficients", arXiv 2007.06524) by eye:
 * ``dual2d``       -- an independent 2D cell-centred scheme used only to pin the
                       node scheme through discrete Keller duality.
 
-Parity status of each function is stated in its docstring; the one reading
-with no external pin (the rank-R quadrature recipe) says "parity unpinned"
-where it applies.
+Parity status of each function is stated in its docstring. The rank-R
+quadrature's node placement is this build's reading (the paper gives none);
+the quadrature itself is pinned by its convergence to the exact G+ as R
+grows, and the Tucker route by the HOSVD error bounds (tests/test_oracle_*).
 """
