@@ -20,7 +20,9 @@
 //   A: x3 transform of r (PCG: r -= alpha q first, reducing ||r||^2)
 //   B: x2 transform, in place
 //   C: x1 transform, multiply by G on the fly (exact 1/(l1+l2+l3) or rank-R
-//      sum_r u_r u_r u_r), reduce r.z, x1 transform again, in place
+//      sum_r u1_r u2_r u3_r), reduce r.z, x1 transform again, in place; the
+//      scaling acts on the complex spectrum directly and the inverse is the
+//      conjugated forward transform (no Hartley combine; see s2_combine)
 //   D: x2 transform, in place
 //   E: x3 transform -> z (PCG: x += alpha p; p = z + beta p)
 // A tile is P complex pencils = 2P real pencils: 2P adjacent rows for x3,
