@@ -31,7 +31,7 @@ coefficients", arXiv 2007.06524) by eye:
                       node scheme through discrete Keller duality.
 
 Parity status of each function is stated in its docstring. The rank-R
-quadrature's node placement is this build's reading (the paper gives none);
+quadrature's node placement is a reading of ours (the paper gives none);
 the quadrature itself is pinned by its convergence to the exact G+ as R
 grows, and the Tucker route by the HOSVD error bounds (tests/test_oracle_*).
 """

@@ -23,7 +23,7 @@ Test infrastructure only (see ``oracle/__init__``).
   The node interval and step balance the truncation and step errors at one
   level (see :func:`rank_r_nodes`); x ranges over [lambda_min, 12] with
   lambda_min = 4 sin^2(pi/N). All w_r > 0, so G_R is positive on every
-  nonzero mode. The node placement is this build's reading (the paper gives
+  nonzero mode. The node placement is a reading of ours (the paper gives
   none); the quadrature is pinned by its convergence to the exact G+ as R
   grows.
 * Apply (Eq. 31): z = F^{-1} diag(G) F r with the 3D DFT (numpy), DC := 0.

@@ -5,7 +5,7 @@ Test infrastructure only (see ``oracle/__init__``).
 The paper (Sec. 2, Eq. 3) draws each cell of the L^3 lattice independently:
 ``a_m(x) = lambda + beta * ahat_m(x)`` with ``ahat`` in {0, 1} per cell, so a
 cell is either the low value ``lambda`` or the high value ``lambda + beta``.
-The paper names no generator. This build fixes one: the SplitMix64 stream of
+The paper names no generator. We fix one: the SplitMix64 stream of
 Steele, Lea & Flood ("Fast splittable pseudorandom number generators",
 OOPSLA 2014). The i-th output (i = 0, 1, ...) of the stream seeded with
 ``seed`` is ``mix64(seed + (i + 1) * GAMMA)`` mod 2^64, where ``mix64`` is the
