@@ -15,7 +15,9 @@ Test infrastructure only (see ``oracle/__init__``).
   existence through the Laplace transform 1/x = int_0^inf exp(-x t) dt (the
   printed 1/pi prefactor is dropped: the integral is exactly 1/x) and builds
   its factors by multigrid Tucker + Tucker-to-canonical, an algorithm it does
-  not state. This oracle follows the Laplace-transform route: substitute
+  not state (``oracle/tucker`` takes that route with the plain HOSVD and a
+  core-slice Tucker-to-canonical). This module follows the Laplace-transform
+  route: substitute
   t = e^s, so 1/x = int_R exp(s - x e^s) ds, and apply the trapezoid (sinc)
   rule on R equispaced nodes s_r. Because exp(-t x) with x = l1 + l2 + l3
   factorises, G_R(k1,k2,k3) = sum_r u_r(k1) u_r(k2) u_r(k3) with
