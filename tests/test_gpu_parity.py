@@ -462,3 +462,26 @@ def test_precond_cosine_modes_full_size(sq, N, rank):
             err = float((z.double().reshape(N, N, N) - zexp).abs().max() / zexp.abs().max())
             assert err <= tol, (prec, opt, err)
         del w_
+
+
+def test_inner_tolerance_option(sq):
+    """SQ_OPT_INNER_TOL_EXP: 2..7 accepted, others rejected; the refined
+    solution meets the tolerance at either end of the range."""
+    import torch
+
+    for bad in (1, 8):
+        with pytest.raises(sq.SqError):
+            sq.sq_set_option(sq.SQ_OPT_INNER_TOL_EXP, bad)
+    L, n = 4, 8
+    N = L * n
+    c = sq.sq_build_coeffs(L, n, 5, 0.5, 1.0, 100.0)
+    pc = sq.sq_precond_setup(N, 8)
+    w = sq.sq_workspace_create(N, sq.SQ_FP32_REFINE)
+    psi = torch.empty(N ** 3, dtype=torch.float64, device="cuda")
+    try:
+        for e in (2, 7):
+            sq.sq_set_option(sq.SQ_OPT_INNER_TOL_EXP, e)
+            info = sq.sq_pcg_solve(c, pc, w, 0, 1e-10, 4000, sq.SQ_FP32_REFINE, None, psi)
+            assert info["status"] == sq.SQ_OK and info["relres_true"] <= 1e-10
+    finally:
+        sq.sq_set_option(sq.SQ_OPT_INNER_TOL_EXP, 5)
