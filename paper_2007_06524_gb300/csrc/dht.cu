@@ -90,15 +90,18 @@ __global__ void __launch_bounds__(kThreads) k_dht(DhtArgs<T> a) {
 }
 
 // Two-stage passes (FP32; see dht_tile_s2 and x3_stage1). A tile holds ~38 KB
-// of shared memory at N = 256, P = 16: room for 5 blocks per SM; the register
-// cap keeps 3 of them resident (uncapped, pass C takes 128 registers).
+// of shared memory at N = 256, P = 16: room for 5 blocks per SM, of which the
+// register cap sets how many stay resident. Blocks per SM the cap aims at:
+// 4 (64 registers) for passes A, B and D, which fit that without spilling;
+// 3 (80 registers) for pass C, whose two transforms and multiplier spill at 64
+// (uncapped it takes 128), and for pass E, which its bulk-copy staging buffers
+// hold to 2 blocks per SM by shared memory anyway; 2 for the radix-32 stages
+// of N = 512 (up to 128 registers).
 // Strided axes x1 (pass C, SCALE) and x2 (passes B, D).
-// Blocks per SM the register cap aims at: 3 (80 registers), 2 for the
-// radix-32 stages of N = 512 (up to 128 registers).
-constexpr int s2_min_blocks(int n) { return n > 256 ? 2 : 3; }
+constexpr int s2_min_blocks(int n, bool cap80) { return n > 256 ? 2 : (cap80 ? 3 : 4); }
 
 template <int AXIS, int R0, int R1, int P, bool SCALE, int RR>
-__global__ void __launch_bounds__(kThreads, s2_min_blocks(R0 * R1)) k_dht_s2(DhtArgs<float> a) {
+__global__ void __launch_bounds__(kThreads, s2_min_blocks(R0 * R1, SCALE)) k_dht_s2(DhtArgs<float> a) {
   using C = float2;
   if (a.check_done && *(volatile int *)&a.rb.st->done) return;
   extern __shared__ __align__(16) unsigned char smem_raw[];
@@ -184,7 +187,7 @@ static cudaError_t launch_strided_fast(const DhtArgs<float> &a, int grid, cudaSt
 
 // Contiguous axis x3 (passes A and E).
 template <int R0, int R1, int P, int LOADM, int STOREM>
-__global__ void __launch_bounds__(kThreads, s2_min_blocks(R0 * R1)) k_dht_s3(DhtArgs<float> a) {
+__global__ void __launch_bounds__(kThreads, s2_min_blocks(R0 * R1, STOREM == SO_PCG)) k_dht_s3(DhtArgs<float> a) {
   using C = float2;
   if (a.check_done && *(volatile int *)&a.rb.st->done) return;
   extern __shared__ __align__(16) unsigned char smem_raw[];
