@@ -92,16 +92,16 @@ __global__ void __launch_bounds__(kThreads) k_dht(DhtArgs<T> a) {
 // Two-stage passes (FP32; see dht_tile_s2 and x3_stage1). A tile holds ~38 KB
 // of shared memory at N = 256, P = 16: room for 5 blocks per SM, of which the
 // register cap sets how many stay resident. Blocks per SM the cap aims at:
-// 4 (64 registers) for passes A, B and D, which fit that without spilling;
-// 3 (80 registers) for pass C, whose two transforms and multiplier spill at 64
-// (uncapped it takes 128), and for pass E, which its bulk-copy staging buffers
-// hold to 2 blocks per SM by shared memory anyway; 2 for the radix-32 stages
-// of N = 512 (up to 128 registers).
+// 4 (64 registers) for passes A to D: A, B and D fit that without spilling,
+// and pass C (128 registers uncapped) spills a few words but gains more from
+// the fourth block than the spills cost; 3 (80 registers) for pass E, which
+// its bulk-copy staging buffers hold to 2 blocks per SM by shared memory
+// anyway; 2 for the radix-32 stages of N = 512 (up to 128 registers).
 // Strided axes x1 (pass C, SCALE) and x2 (passes B, D).
 constexpr int s2_min_blocks(int n, bool cap80) { return n > 256 ? 2 : (cap80 ? 3 : 4); }
 
 template <int AXIS, int R0, int R1, int P, bool SCALE, int RR>
-__global__ void __launch_bounds__(kThreads, s2_min_blocks(R0 * R1, SCALE)) k_dht_s2(DhtArgs<float> a) {
+__global__ void __launch_bounds__(kThreads, s2_min_blocks(R0 * R1, false)) k_dht_s2(DhtArgs<float> a) {
   using C = float2;
   if (a.check_done && *(volatile int *)&a.rb.st->done) return;
   extern __shared__ __align__(16) unsigned char smem_raw[];
