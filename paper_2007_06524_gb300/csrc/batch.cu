@@ -180,11 +180,13 @@ __device__ __forceinline__ bool kb_fast_tile(const BSolve &B, const DhtTile<floa
 // Inner passes on the FP32 fields of every active solve. A block takes
 // kTilesPerBlock consecutive tiles of its solve, so that its fixed start-up
 // (finding the solve, its descriptor and stop flag, the twiddles) is paid
-// once per several tiles.
+// once per several tiles. The 64-register cap lets 4 blocks per SM stay
+// resident where shared memory allows (a tile of N = 96, 16 pencils, takes
+// 27 KB); only pass C, whose per-N variants are all inlined here, spills.
 constexpr int kTilesPerBlock = 4;
 
 template <int AXIS, int LOADM, int STOREM, bool SCALE>
-__global__ void __launch_bounds__(kThreads, 3) kb_dht(const BSolve *__restrict__ S, const int *__restrict__ pre,
+__global__ void __launch_bounds__(kThreads, 4) kb_dht(const BSolve *__restrict__ S, const int *__restrict__ pre,
                                                       int count, int first) {
   using C = float2;
   const int s = find_solve(pre, count, blockIdx.x);
