@@ -703,10 +703,16 @@ static int level_thresholds(int K, const double *probs, uint64_t *thr) {
   return SQ_OK;
 }
 
-int sq_coeffs_set_levels(sq_coeffs *c, int K, const double *values) {
-  if (!c || K < 2 || K > kMaxLevels || !values) return SQ_EINVAL;
+// K in [2, kMaxLevels] coefficient values, each positive and finite.
+static bool valid_level_values(int K, const double *values) {
+  if (K < 2 || K > kMaxLevels || !values) return false;
   for (int l = 0; l < K; ++l)
-    if (!(values[l] > 0.0) || !std::isfinite(values[l])) return SQ_EINVAL;
+    if (!(values[l] > 0.0) || !std::isfinite(values[l])) return false;
+  return true;
+}
+
+int sq_coeffs_set_levels(sq_coeffs *c, int K, const double *values) {
+  if (!c || !valid_level_values(K, values)) return SQ_EINVAL;
   c->levels = K;
   c->a_lo = values[0];
   c->a_hi = values[1];
@@ -719,7 +725,7 @@ int sq_build_coeffs_levels(int L, int n, uint64_t seed, int K, const double *pro
   if (!out) return SQ_EINVAL;
   *out = nullptr;
   uint64_t thr[3];
-  if (level_thresholds(K, probs, thr) != SQ_OK || !values) return SQ_EINVAL;
+  if (level_thresholds(K, probs, thr) != SQ_OK || !valid_level_values(K, values)) return SQ_EINVAL;
   cudaStream_t s = reinterpret_cast<cudaStream_t>(stream);
   int st = alloc_coeffs(L, n, values[0], values[1], s, out);
   if (st != SQ_OK) return st;
@@ -740,7 +746,7 @@ int sq_coeffs_from_host_levels(int L, int n, const uint8_t *host_level, int K, c
                                sq_stream_t stream, sq_coeffs **out) {
   if (!out) return SQ_EINVAL;
   *out = nullptr;
-  if (!host_level || !values || K < 2 || K > kMaxLevels) return SQ_EINVAL;
+  if (!host_level || !valid_level_values(K, values)) return SQ_EINVAL;
   cudaStream_t s = reinterpret_cast<cudaStream_t>(stream);
   int st = alloc_coeffs(L, n, values[0], values[1], s, out);
   if (st != SQ_OK) return st;
