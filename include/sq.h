@@ -33,6 +33,13 @@
  *    legacy default stream) unless marked "synchronizes".
  *  - On error nothing is guaranteed about the output buffers; a CUDA error
  *    that was raised by an earlier asynchronous call may surface as SQ_ECUDA.
+ *  - Handles carry reduction scratch. Calls that reduce through one
+ *    sq_coeffs (sq_homogenized_matrix, sq_apply_operator[_f32], sq_rhs), and
+ *    all calls on one sq_workspace, must be ordered on one stream. Solves only
+ *    read their sq_coeffs and sq_precond, so the three correctors of a
+ *    realization may run concurrently on separate workspaces and streams.
+ *  - Options and tile choices (sq_set_option, sq_set_tiles) are process-wide
+ *    and must not change while a solve runs.
  */
 #ifndef SQ_H
 #define SQ_H
