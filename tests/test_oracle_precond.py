@@ -77,3 +77,31 @@ def test_core_tensor_from_nodes_consistent():
     G = precond.core_tensor_rank_r(N, R)
     m = E > 0
     assert abs(precond.max_relative_error(N, t, w) - np.abs(G[m] / E[m] - 1).max()) < 1e-12
+
+
+@pytest.mark.parametrize("L,n,sub,lo", [(2, 4, None, 0.25), (4, 2, None, 0.1), (3, 4, 2, 0.4), (4, 3, None, 0.02)])
+def test_spectral_equivalence_interval(L, n, sub, lo):
+    """Lemma 4.1 in its sharp form: x'Ax = sum_e a_e (Dx)_e^2 and the exact
+    preconditioner is the pseudo-inverse of B with x'Bx = sum_e (Dx)_e^2, so
+    every nonzero eigenvalue of P A lies in [min a_e, max a_e] (hence
+    cond <= 1 / lambda for a in [lambda, 1]). The rank-8 tensor G_R is
+    diagonal in the same Fourier basis as B+, with g G_R in [1 - e, 1 + e]
+    (e its relative error), so its interval is [min a_e (1 - e),
+    max a_e (1 + e)]."""
+    from oracle import problem
+
+    re = problem.realization(L, n, 7, lo, 1.0, 0.5, sub=sub)
+    N = re.N
+    a = re.a_edges
+    A = re.A.toarray()
+    for rank in (0, 8):
+        G = precond.core_tensor(N, rank)
+        PA = np.stack([precond.apply_precond(G, A[:, j].reshape(N, N, N)).ravel() for j in range(N ** 3)], axis=1)
+        ev = np.linalg.eigvals(PA)
+        assert np.abs(ev.imag).max() <= 1e-9  # similar to a symmetric matrix
+        ev = np.sort(ev.real)
+        assert np.abs(ev[0]) <= 1e-10  # the constants
+        nz = ev[1:]
+        e = 0.0 if rank == 0 else precond.max_relative_error(N, *precond.rank_r_nodes(N, rank))
+        assert nz.min() >= a.min() * (1 - e) - 1e-10
+        assert nz.max() <= a.max() * (1 + e) + 1e-10
