@@ -21,6 +21,7 @@ import argparse
 import json
 import math
 import os
+import platform
 import statistics
 import subprocess
 import sys
@@ -690,9 +691,31 @@ def _oracle_sample(iters_mean, R, n_iter_sample=3):
     return t_setup, t_it, t_solve
 
 
+def _host_cpu(cpuinfo="/proc/cpuinfo"):
+    """CPU model of this host (x86 'model name', else the Arm implementer/part
+    codes) and the cores this process may use."""
+    info = {}
+    try:
+        with open(cpuinfo) as f:
+            for line in f:
+                k, _, v = line.partition(":")
+                k, v = k.strip().lower(), v.strip()
+                if v and k in ("model name", "cpu implementer", "cpu part") and k not in info:
+                    info[k] = v
+    except OSError:
+        pass
+    if "model name" in info:
+        model = info["model name"]
+    elif "cpu part" in info:
+        model = f"{platform.machine()} (CPU implementer {info.get('cpu implementer', '?')}, part {info['cpu part']})"
+    else:
+        model = platform.machine()
+    return {"cpu_model": model, "cores_available": len(os.sched_getaffinity(0))}
+
+
 def cpu_baseline(iters_mean, R):
     t_setup, t_it, t_solve = _oracle_sample(iters_mean, R)
-    return {"value": round(1.0 / t_solve, 6), "unit": UNIT, "cores": 1, "kind": "oracle",
+    return {"value": round(1.0 / t_solve, 6), "unit": UNIT, "cores": 1, "kind": "oracle", **_host_cpu(),
             "sample": f"oracle at N=256 (L=32, n=8, seed 0): assembly+RHS {t_setup:.1f} s (shared by 3 correctors) "
                       f"+ {t_it:.2f} s per PCG iteration (rank-{R}), measured on 3 iterations, extrapolated to "
                       f"{iters_mean:.1f} iterations per solve; single-threaded numpy/scipy on "
@@ -730,7 +753,7 @@ def run_reference(args):
            "warmup": args.warmup, "ms_per_step": round(t_it * 1e3, 3), "higher_is_better": True, "scaling": "weak",
            "vs_baseline": None, "dtype": "f64", "data": "synthetic", "impl": "reference",
            "config": workload_config(args, _dist()[0]),
-           "cpu_baseline": {"value": round(value, 6), "unit": UNIT, "cores": 1, "kind": "oracle",
+           "cpu_baseline": {"value": round(value, 6), "unit": UNIT, "cores": 1, "kind": "oracle", **_host_cpu(),
                             "sample": f"step = one PCG iteration of the oracle at N=256 ({t_it:.2f} s); assembly "
                                       f"{t_setup:.1f} s once; extrapolated to {iters_per_solve:.0f} iterations"},
            "e2e": {"value": round(value, 6), "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}

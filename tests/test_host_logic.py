@@ -76,3 +76,20 @@ def test_new_bindings_reject_bad_arguments_before_calling_the_library():
         sq.sq_precond_setup_canonical(32, np.ones((3, 32)), np.ones((4, 32)))     # factor shapes differ
     with pytest.raises(ValueError):
         sq.sq2d_coeffs_from_host(4, 4, np.zeros(15, np.uint8), 1.0, 2.0)         # not L^2 bytes
+
+
+def test_bench_host_cpu_description(tmp_path):
+    import bench
+
+    x86 = tmp_path / "x86"
+    x86.write_text("processor\t: 0\nvendor_id\t: GenuineIntel\nmodel name\t: Example Xeon 1234\n\n"
+                   "processor\t: 1\nmodel name\t: Example Xeon 1234\n")
+    arm = tmp_path / "arm"
+    arm.write_text("processor\t: 0\nBogoMIPS\t: 2000.00\nCPU implementer\t: 0x41\nCPU architecture: 8\n"
+                   "CPU part\t: 0xd4f\n\nprocessor\t: 1\nCPU implementer\t: 0x41\nCPU part\t: 0xd4f\n")
+    a = bench._host_cpu(str(x86))
+    assert a["cpu_model"] == "Example Xeon 1234" and a["cores_available"] >= 1
+    b = bench._host_cpu(str(arm))
+    assert "implementer 0x41" in b["cpu_model"] and "part 0xd4f" in b["cpu_model"]
+    c = bench._host_cpu(str(tmp_path / "missing"))
+    assert c["cpu_model"] and c["cores_available"] >= 1
