@@ -386,6 +386,17 @@ def run_native(args):
         torch.distributed.destroy_process_group()
 
 
+def batch_algorithmic(Ns, iters, seconds, hbm_gbs):
+    """Algorithmic traffic of a batch: 17 FP32 field passes (4 N^3 bytes each)
+    per inner PCG iteration of every solve, over the batch's wall time, and
+    that rate against the HBM peak. The fields of the small grids a batch
+    holds stay in L2 between passes, so this is not DRAM traffic."""
+    b = float(sum(17 * 4 * int(N) ** 3 * int(it) for N, it in zip(Ns, iters)))
+    gbs = b / seconds / 1e9
+    return {"algorithmic_bytes": b, "algorithmic_GBps": round(gbs, 1), "algorithmic_frac_of_hbm": round(gbs / hbm_gbs, 4),
+            "algorithmic_note": "17 FP32 field passes per inner iteration / wall time; fields are L2-resident"}
+
+
 def run_batch(sq, torch, stream, nseeds=256):
     """768 corrector solves (256 realizations x e_1..e_3) in one batch: L drawn
     from {8,12,16,24} per seed, n=4 (N = 32..96), Bernoulli(1/2) on {1,10},
@@ -395,7 +406,7 @@ def run_batch(sq, torch, stream, nseeds=256):
     from paper_2007_06524_gb300 import workloads
 
     wl = workloads.BATCH_MIXED
-    precs, descs, pl, coeffs = {}, [], [], []
+    precs, descs, pl, coeffs, Ns = {}, [], [], [], []
     for seed in range(nseeds):
         L = wl["Ls"][workloads.batch_L_index(seed)]
         N = L * wl["n"]
@@ -406,6 +417,7 @@ def run_batch(sq, torch, stream, nseeds=256):
         for i in range(3):
             descs.append((c, i, torch.empty(N ** 3, dtype=torch.float64, device="cuda")))
             pl.append(precs[N])
+            Ns.append(N)
     b = sq.sq_batch_create(descs, pl)
     sq.sq_pcg_solve_batched(b, wl["tol"], 2000)  # warm-up (graph capture, first touch)
     torch.cuda.synchronize()
@@ -418,9 +430,11 @@ def run_batch(sq, torch, stream, nseeds=256):
     its = np.array([i["iters"] for i in infos])
     ok = all(i["status"] == sq.SQ_OK for i in infos)
     unknowns = sum(d[2].numel() for d in descs)
-    return {"solves": len(descs), "solves_per_s": round(len(descs) / t, 1), "seconds": round(t, 4),
-            "iters_p50": float(np.percentile(its, 50)), "iters_p99": float(np.percentile(its, 99)),
-            "unknowns": unknowns, "converged": ok}
+    out = {"solves": len(descs), "solves_per_s": round(len(descs) / t, 1), "seconds": round(t, 4),
+           "iters_p50": float(np.percentile(its, 50)), "iters_p99": float(np.percentile(its, 99)),
+           "unknowns": unknowns, "converged": ok}
+    out.update(batch_algorithmic(Ns, its, t, _peaks()["hbm_gbs"]))
+    return out
 
 
 def run_warm_start(sq, torch, nseeds=64):

@@ -93,3 +93,51 @@ def test_bench_host_cpu_description(tmp_path):
     assert "implementer 0x41" in b["cpu_model"] and "part 0xd4f" in b["cpu_model"]
     c = bench._host_cpu(str(tmp_path / "missing"))
     assert c["cpu_model"] and c["cores_available"] >= 1
+
+
+def test_bench_batch_leg_on_fakes():
+    """run_batch end to end against stand-ins for the library and torch (no
+    GPU): the 768 descriptors, their grid sizes and the algorithmic traffic."""
+    import types
+
+    import bench
+    from paper_2007_06524_gb300 import workloads
+
+    class Buf:
+        def __init__(self, n):
+            self.n = n
+
+        def numel(self):
+            return self.n
+
+    class Event:
+        def __init__(self, enable_timing=False):
+            pass
+
+        def record(self, stream=None):
+            pass
+
+        def elapsed_time(self, other):
+            return 250.0  # ms
+
+    calls = {}
+    fake_sq = types.SimpleNamespace(
+        SQ_OK=0,
+        sq_build_coeffs=lambda L, n, seed, p, lo, hi: ("coeffs", L, n, seed),
+        sq_precond_setup=lambda N, r: ("precond", N, r),
+        sq_batch_create=lambda descs, pl: calls.setdefault("batch", (list(descs), list(pl))),
+        sq_pcg_solve_batched=lambda b, tol, mi: [{"iters": 20, "status": 0} for _ in b[0]],
+    )
+    fake_torch = types.SimpleNamespace(
+        float64="f64", empty=lambda n, dtype=None, device=None: Buf(n),
+        cuda=types.SimpleNamespace(synchronize=lambda: None, Event=Event))
+    out = bench.run_batch(fake_sq, fake_torch, stream=None)
+    descs, pl = calls["batch"]
+    Ns = [workloads.BATCH_MIXED["Ls"][workloads.batch_L_index(s)] * 4 for s in range(256) for _ in range(3)]
+    assert out["solves"] == 768 and [p[1] for p in pl] == Ns
+    assert [d[2].numel() for d in descs] == [N ** 3 for N in Ns]
+    assert out["converged"] and out["iters_p50"] == 20.0 and out["seconds"] == 0.25
+    want = sum(17 * 4 * N ** 3 * 20 for N in Ns)
+    assert out["algorithmic_bytes"] == want
+    assert abs(out["algorithmic_GBps"] - want / 0.25 / 1e9) <= 0.05
+    assert 0 < out["algorithmic_frac_of_hbm"] < 10 and "L2" in out["algorithmic_note"]
