@@ -141,3 +141,37 @@ def test_bench_batch_leg_on_fakes():
     assert out["algorithmic_bytes"] == want
     assert abs(out["algorithmic_GBps"] - want / 0.25 / 1e9) <= 0.05
     assert 0 < out["algorithmic_frac_of_hbm"] < 10 and "L2" in out["algorithmic_note"]
+
+
+def test_bench_roofline_selection():
+    """kernel_table: the dominant class by time, ALU- or HBM-bound by the larger
+    fraction, achieved = algorithmic bytes (flops) x working launches / their
+    time, and the ncu traffic attached only where a capture of that kernel at
+    N = 256 exists."""
+    import bench
+
+    N, R = 256, 8
+    names = ("stencil_matvec", "dht_x3_in", "dht_x2", "dht_x1_scale", "dht_x3_out")
+    # FP64: pass C dominates and is ALU-bound
+    us64 = {"stencil_matvec": 262.0, "dht_x3_in": 597.0, "dht_x2": 481.0, "dht_x1_scale": 1103.0, "dht_x3_out": 562.0}
+    prof = {k: (us64[k] * 100 / 1e3, 100) for k in names}
+    work = {k: (us64[k] * 90 / 1e3, 90) for k in names}
+    kernels, roof = bench.kernel_table(work, prof, N, 8, R, t_ms=400.0)
+    flops = bench._algorithmic(N, 8, R)["dht_x1_scale"][1]
+    assert roof["kernel"] == "dht_x1_scale" and roof["bound"] == "alu" and roof["unit"] == "TFLOP/s"
+    assert abs(roof["achieved"] - flops / 1103e-6 / 1e12) <= 1e-3
+    assert abs(roof["frac"] - roof["achieved"] / 1.25) <= 1e-3
+    assert roof["traffic"] == bench.PROFILED_TRAFFIC[("dht_x1_scale", 8)]
+    assert kernels["dht_x2"]["us_per_work_launch"] == 481.0
+    # FP32: pass E dominates and is HBM-bound
+    us32 = {"stencil_matvec": 41.0, "dht_x3_in": 52.0, "dht_x2": 24.5, "dht_x1_scale": 53.5, "dht_x3_out": 58.8}
+    prof = {k: (us32[k] * 100 / 1e3, 100) for k in names}
+    work = {k: (us32[k] * 90 / 1e3, 90) for k in names}
+    kernels, roof = bench.kernel_table(work, prof, N, 4, R, t_ms=30.0)
+    b = bench._algorithmic(N, 4, R)["dht_x3_out"][0]
+    assert roof["kernel"] == "dht_x3_out" and roof["bound"] == "hbm" and roof["unit"] == "GB/s"
+    assert abs(roof["achieved"] - b / 58.8e-6 / 1e9) <= 0.1
+    assert roof["traffic"] == bench.PROFILED_TRAFFIC[("dht_x3_out", 4)]
+    # no capture at other sizes
+    _, roof = bench.kernel_table(work, prof, 128, 4, R, t_ms=30.0)
+    assert roof["traffic"] is None
