@@ -31,7 +31,9 @@ coefficients", arXiv 2007.06524) by eye:
                       node scheme through discrete Keller duality.
 
 Parity status of each function is stated in its docstring. The rank-R
-quadrature's node placement is a reading of ours (the paper gives none);
-the quadrature itself is pinned by its convergence to the exact G+ as R
-grows, and the Tucker route by the HOSVD error bounds (tests/test_oracle_*).
+node placements (trapezoid rule, and geometric nodes with least-squares
+weights) are readings of ours (the paper gives none); both are pinned by
+their convergence to the exact G+ as R grows, the least-squares fit also by
+its normal equations and by beating the trapezoid rule, and the Tucker route
+by the HOSVD error bounds (tests/test_oracle_*).
 """

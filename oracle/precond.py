@@ -28,6 +28,13 @@ Test infrastructure only (see ``oracle/__init__``).
   nonzero mode. The node placement is a reading of ours (the paper gives
   none); the quadrature is pinned by its convergence to the exact G+ as R
   grows.
+* A second exponential sum, :func:`lsq_nodes`: geometric nodes with weights
+  fitted by least squares to the relative error over a log-uniform sample of
+  the discrete spectrum, kept only where it beats the trapezoid rule. It is
+  the rank-R construction the GPU library uses, written here independently in
+  numpy; it is pinned by positivity, by the least-squares normal equations,
+  by beating the trapezoid rule on every eigenvalue, and by its convergence
+  to 1/x as R grows (tests/test_oracle_precond).
 * Apply (Eq. 31): z = F^{-1} diag(G) F r with the 3D DFT (numpy), DC := 0.
 """
 from __future__ import annotations
@@ -62,12 +69,13 @@ def core_tensor_exact(N: int) -> np.ndarray:
     return G
 
 
-def rank_r_nodes(N: int, R: int):
+def rank_r_nodes(N: int, R: int, dim: int = 3):
     """Quadrature nodes t_r and weights w_r of the exponential sum (R >= 2).
 
-    Trapezoid rule for 1/x = int exp(s - x e^s) ds on x in [lambda_min, 12]
-    with three error sources balanced at one level eps:
-      lower truncation  ~ 12 e^{s_lo}            -> s_lo = ln(eps / 12)
+    Trapezoid rule for 1/x = int exp(s - x e^s) ds on x in [lambda_min, X]
+    (X = 4 dim, the largest eigenvalue of the dim-dimensional periodic
+    Laplacian: 12 in 3D) with three error sources balanced at one level eps:
+      lower truncation  ~ X e^{s_lo}             -> s_lo = ln(eps / X)
       upper truncation  ~ exp(-lambda_min e^{s_hi}) -> s_hi = ln(ln(1/eps) / lambda_min)
       step error        ~ exp(-pi^2 / eta)       (integrand analytic in the
                                                   strip |Im s| < pi/2)
@@ -80,7 +88,7 @@ def rank_r_nodes(N: int, R: int):
 
     def interval(le):
         eps = math.exp(le)
-        s_lo = le - math.log(12.0)
+        s_lo = le - math.log(4.0 * dim)
         s_hi = math.log(-le / lam_min)
         return s_lo, s_hi, (s_hi - s_lo) / (R - 1), eps
 
@@ -95,6 +103,95 @@ def rank_r_nodes(N: int, R: int):
     s_lo, _, eta, _ = interval(0.5 * (lo + hi))
     s = s_lo + eta * np.arange(R)
     return np.exp(s), eta * np.exp(s)
+
+
+def spectrum_values(N: int, dim: int = 3) -> np.ndarray:
+    """The distinct nonzero eigenvalues of the dim-dimensional periodic
+    Laplacian, l_i + l_j (+ l_k), sorted ascending. Values within a relative
+    1e-12 of the last kept value count as one (equal sums of different index
+    triples differ only by rounding)."""
+    lam = laplacian_eigenvalues(N)[: N // 2 + 1]   # l_k = l_{N-k}: half the range holds every value
+    if dim == 2:
+        g = lam[:, None] + lam[None, :]
+    else:
+        g = lam[:, None, None] + lam[None, :, None] + lam[None, None, :]
+    g = np.sort(g.ravel())
+    g = g[g > 0.0]
+    keep = [g[0]]
+    for x in g[1:]:
+        if x > keep[-1] * (1.0 + 1e-12):
+            keep.append(x)
+    return np.array(keep)
+
+
+def log_uniform_sample(values: np.ndarray, K: int = 3000) -> np.ndarray:
+    """For each of K points of the geometric grid from values[0] to
+    values[-1], the nearest of the given (sorted, distinct) values; repeats
+    dropped, ascending."""
+    x0, x1 = values[0], values[-1]
+    out = []
+    for m in range(K):
+        target = x0 * (x1 / x0) ** (m / (K - 1))
+        i = int(np.searchsorted(values, target))
+        hi = values[min(i, len(values) - 1)]
+        lo = values[i - 1] if i > 0 else hi
+        pick = lo if (i > 0 and (i == len(values) or abs(lo - target) < abs(hi - target))) else hi
+        if not out or pick > out[-1]:
+            out.append(pick)
+    return np.array(out)
+
+
+def sampled_relative_error(x: np.ndarray, t, w) -> float:
+    """max over the values x of |x * sum_r w_r exp(-t_r x) - 1|."""
+    g = np.exp(-np.outer(x, np.asarray(t, dtype=np.float64))) @ np.asarray(w, dtype=np.float64)
+    return float(np.abs(x * g - 1.0).max())
+
+
+def lsq_nodes(N: int, R: int, dim: int = 3):
+    """Exponential sum for 1/x with geometric nodes and least-squares weights
+    (our reading of the rank-R construction; the paper states the Laplace
+    transform route of Eq. 34 and leaves the nodes open). Returns (t, w).
+
+    1. x ranges over the distinct nonzero Laplacian eigenvalues
+       (:func:`spectrum_values`), sampled log-uniformly at 3000 points
+       (:func:`log_uniform_sample`).
+    2. For each (a, b) on a grid, a in -ln(4 dim) - 6 + 7 i/(g-1) and
+       b in ln(1/lambda_min) - 1 + 5 j/(g-1) (g = 40 for R <= 16, else 20),
+       the nodes are t_r = exp(a + (b - a) r/(R-1)) and the weights solve
+       min_w || x exp(-x t) w - 1 ||_2 over the sample (numpy lstsq).
+    3. Fits with any w_r <= 0 are discarded (G_R must stay positive); of the
+       rest the one with the smallest largest sampled error is kept (the
+       first in (i, j) order on ties).
+    4. The fit replaces the trapezoid rule (:func:`rank_r_nodes`) only if its
+       largest error over every distinct eigenvalue is smaller; for R > 32,
+       or with fewer than 2R sample points, the trapezoid rule is returned.
+    """
+    t_trap, w_trap = rank_r_nodes(N, R, dim)
+    if R > 32:
+        return t_trap, w_trap
+    values = spectrum_values(N, dim)
+    x = log_uniform_sample(values)
+    if len(x) < 2 * R:
+        return t_trap, w_trap
+    lam_min = 4.0 * math.sin(math.pi / N) ** 2
+    g = 40 if R <= 16 else 20
+    best, best_t, best_w = np.inf, None, None
+    for i in range(g):
+        a = -math.log(4.0 * dim) - 6.0 + 7.0 * i / (g - 1)
+        for j in range(g):
+            b = math.log(1.0 / lam_min) - 1.0 + 5.0 * j / (g - 1)
+            t = np.exp(a + (b - a) * np.arange(R) / (R - 1))
+            E = x[:, None] * np.exp(-np.outer(x, t))
+            w = np.linalg.lstsq(E, np.ones(len(x)), rcond=None)[0]
+            if not np.all(w > 0.0):
+                continue
+            err = float(np.abs(E @ w - 1.0).max())
+            if err < best:
+                best, best_t, best_w = err, t, w
+    if best_t is not None and sampled_relative_error(values, best_t, best_w) < sampled_relative_error(
+            values, t_trap, w_trap):
+        return best_t, best_w
+    return t_trap, w_trap
 
 
 def rank_r_factors(N: int, R: int) -> np.ndarray:

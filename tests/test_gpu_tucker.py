@@ -164,12 +164,11 @@ def test_invalid_arguments(sq):
 @pytest.mark.parametrize("N,R", [(32, 0), (64, 4), (256, 8), (96, 16)])
 def test_info_of_exponential_sums(sq, N, R):
     """sq_precond_info on the default preconditioners: rank, and the relative
-    error the oracle computes from the library's nodes and weights."""
+    error of the oracle's own exponential sum of that rank."""
     pc = sq.sq_precond_setup(N, R)
     rank, err = sq.sq_precond_info(pc)
     assert rank == R
     if R == 0:
         assert err <= 1e-12
     else:
-        t, w = sq.sq_precond_factors(pc, R)
-        assert abs(err - precond.max_relative_error(N, t, w)) <= 1e-9 + 1e-7 * err
+        assert abs(err - precond.max_relative_error(N, *precond.lsq_nodes(N, R))) <= 1e-9 + 1e-7 * err

@@ -105,3 +105,75 @@ def test_spectral_equivalence_interval(L, n, sub, lo):
         e = 0.0 if rank == 0 else precond.max_relative_error(N, *precond.rank_r_nodes(N, rank))
         assert nz.min() >= a.min() * (1 - e) - 1e-10
         assert nz.max() <= a.max() * (1 + e) + 1e-10
+
+
+# ----------------------------------------------- least-squares exponential sum
+@pytest.mark.parametrize("N,dim", [(6, 3), (8, 3), (12, 3), (8, 2), (18, 2)])
+def test_spectrum_values_brute_force(N, dim):
+    """The distinct nonzero eigenvalues from the half index range equal the
+    distinct values of the full Kronecker-sum spectrum (brute force over all
+    N^dim index tuples, deduplicated by rounding)."""
+    lam = precond.laplacian_eigenvalues(N)
+    full = lam[:, None] + lam[None, :] if dim == 2 else lam[:, None, None] + lam[None, :, None] + lam[None, None, :]
+    ref = np.unique(np.round(full.ravel(), 10))
+    ref = ref[ref > 0]
+    got = precond.spectrum_values(N, dim)
+    assert len(got) == len(ref) and np.allclose(got, ref, rtol=0, atol=1e-9)
+
+
+def test_log_uniform_sample_members():
+    v = precond.spectrum_values(64)
+    x = precond.log_uniform_sample(v)
+    assert x[0] == v[0] and x[-1] == v[-1]
+    assert np.all(np.diff(x) > 0) and np.all(np.isin(x, v))
+    # nearest value to each point of a geometric grid of 3000 points: a value
+    # farther than two grid steps (in log x) from both neighbours is always
+    # picked
+    step = np.log(v[-1] / v[0]) / 2999
+    lv = np.log(v)
+    gap = np.minimum(np.diff(lv, prepend=-np.inf), -np.diff(lv, append=np.inf))
+    assert np.all(np.isin(v[gap > 2 * step], x))
+    assert len(x) <= 3000
+
+
+@pytest.mark.parametrize("N,R,dim", [(16, 6, 3), (64, 8, 3), (256, 8, 3), (64, 16, 3), (256, 8, 2), (48, 4, 3)])
+def test_lsq_sum_positive_geometric_and_better_than_trapezoid(N, R, dim):
+    t, w = precond.lsq_nodes(N, R, dim)
+    assert np.all(t > 0) and np.all(w > 0)
+    assert np.allclose(t[1:] / t[:-1], t[1] / t[0], rtol=1e-12)      # geometric nodes
+    v = precond.spectrum_values(N, dim)
+    e_fit = precond.sampled_relative_error(v, t, w)
+    e_trap = precond.sampled_relative_error(v, *precond.rank_r_nodes(N, R, dim))
+    assert e_fit <= e_trap
+
+
+@pytest.mark.parametrize("N,R", [(64, 8), (256, 8), (32, 16)])
+def test_lsq_weights_satisfy_normal_equations(N, R):
+    """Least squares (textbook): at the fitted weights the residual of
+    min ||E w - 1|| on the sample is orthogonal to the columns of E, and any
+    other weights on the same nodes (e.g. the trapezoid weights rescaled)
+    give a larger residual."""
+    t, w = precond.lsq_nodes(N, R)
+    x = precond.log_uniform_sample(precond.spectrum_values(N))
+    E = x[:, None] * np.exp(-np.outer(x, t))
+    res = E @ w - 1.0
+    assert np.abs(E.T @ res).max() <= 1e-9 * np.linalg.norm(E, axis=0).max() * max(np.linalg.norm(res), 1e-300) * 1e3
+    rng_ = np.random.default_rng(0)
+    for _ in range(5):
+        dw = rng_.standard_normal(R) * 1e-3 * w
+        assert np.linalg.norm(E @ (w + dw) - 1.0) >= np.linalg.norm(res)
+
+
+@pytest.mark.parametrize("N", [32, 64, 256])
+def test_lsq_sum_converges_to_exact(N):
+    """More terms, smaller error: the fit approaches G+ = 1/x (Eq. 33)."""
+    v = precond.spectrum_values(N)
+    errs = [precond.sampled_relative_error(v, *precond.lsq_nodes(N, R)) for R in (4, 8, 16)]
+    assert errs[0] > errs[1] > errs[2]
+    assert errs[2] < 1e-3
+
+
+def test_lsq_above_32_terms_is_the_trapezoid_rule():
+    t, w = precond.lsq_nodes(16, 40)
+    ts, ws = precond.rank_r_nodes(16, 40)
+    assert np.array_equal(t, ts) and np.array_equal(w, ws)
