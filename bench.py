@@ -37,16 +37,54 @@ UNIT = "corrector solves/s"
 
 
 def _peaks():
+    """HBM peak: the driver's measured copy bandwidth (MEASURED_PEAKS.json)
+    where present, else the fallback figure of one earlier GB300
+    measurement."""
     p = os.path.join(ROOT, "MEASURED_PEAKS.json")
     if os.path.exists(p):
         d = json.load(open(p))
-        return {"hbm_gbs": d.get("hbm_gbs", 6800.0), "src": "measured"}
-    return {"hbm_gbs": 6800.0, "src": "fallback"}
+        return {"hbm_gbs": d.get("hbm_gbs", 6800.0), "src": "measured (MEASURED_PEAKS.json copy)"}
+    return {"hbm_gbs": 6800.0, "src": "fallback (6.8 TB/s, an earlier GB300 copy measurement)"}
 
 
-# nominal FP64 rate of one GB300 (dense, non-tensor and tensor alike)
-FP64_PEAK_TFLOPS = 1.25
-FP32_PEAK_TFLOPS = 152 * 128 * 2 * 2.07e9 / 1e12  # 152 SMs x 128 FP32 lanes x FMA x max clock
+# nominal rates, used only where no probe ran (host-only tests)
+FP64_NOMINAL_TFLOPS = 1.25
+FP32_NOMINAL_TFLOPS = 152 * 128 * 2 * 2.07e9 / 1e12  # 152 SMs x 128 FP32 lanes x FMA x max clock
+
+
+def default_peaks():
+    """Peaks without a GPU probe: HBM as _peaks(), FMA rates nominal."""
+    pk = _peaks()
+    return {"hbm_gbs": pk["hbm_gbs"], "hbm_src": pk["src"],
+            "fp64_tflops": FP64_NOMINAL_TFLOPS, "fp64_src": "nominal FP64 rate of GB300 (1.25 TFLOP/s)",
+            "fp32_tflops": FP32_NOMINAL_TFLOPS, "fp32_src": "nominal: 152 SMs x 128 FMA x 2.07 GHz"}
+
+
+def measure_peaks(sq, torch):
+    """The roofline denominators measured on this GPU by the library's probes:
+    FP64 and FP32 fused multiply-add throughput (eight independent chains per
+    thread, a full grid) and a copy of 2 x 2 GiB (HBM) and of 2 x 16 MiB (L2)
+    buffers. The HBM peak stays the driver's measurement where present; the
+    probe's copy figure is reported beside it."""
+    pk = default_peaks()
+    fp64, _ = sq.sq_probe_fma(0)
+    fp32, _ = sq.sq_probe_fma(1)
+    pk.update({"fp64_tflops": round(fp64, 4), "fp64_src": "measured: FP64 FMA probe (sq_probe_fma)",
+               "fp32_tflops": round(fp32, 3), "fp32_src": "measured: FP32 FMA probe (sq_probe_fma)"})
+    big = 2 << 30
+    a = torch.empty(big // 4, dtype=torch.float32, device="cuda")
+    b = torch.empty_like(a)
+    pk["copy_hbm_gbs"] = round(sq.sq_probe_copy(a, b, 5), 1)
+    del a, b
+    small = 16 << 20
+    a = torch.empty(small // 4, dtype=torch.float32, device="cuda")
+    b = torch.empty_like(a)
+    pk["copy_l2_gbs"] = round(sq.sq_probe_copy(a, b, 200), 1)
+    del a, b
+    if not os.path.exists(os.path.join(ROOT, "MEASURED_PEAKS.json")):
+        pk["hbm_gbs"] = pk["copy_hbm_gbs"]
+        pk["hbm_src"] = "measured: copy probe of this run (sq_probe_copy, 2 x 2 GiB)"
+    return pk
 
 
 class ClockSampler:
@@ -169,13 +207,14 @@ def _algorithmic(N, elem, rank_r):
 PROFILED_TRAFFIC = {("dht_x1_scale", 8): 134.59e6 + 72.85e6, ("dht_x3_out", 4): 201.36e6 + 76.13e6}
 
 
-def kernel_table(work, prof, N, elem, R, t_ms):
+def kernel_table(work, prof, N, elem, R, t_ms, peaks=None):
     """Per-class table and the dominant class's roofline from the library's
     event profile: achieved = algorithmic bytes (flops) per launch x launches
     that did work / their summed duration (launches that returned at entry,
-    their solve having stopped, excluded by sq_profile_work)."""
+    their solve having stopped, excluded by sq_profile_work). The bound is the
+    larger of the HBM and FMA-pipe fractions; both are reported."""
     alg = _algorithmic(N, elem, R)
-    peaks = _peaks()
+    pk = peaks or default_peaks()
     kernels = {}
     for name, (ms, cnt) in prof.items():
         if ms <= 0:
@@ -189,17 +228,16 @@ def kernel_table(work, prof, N, elem, R, t_ms):
         kernels[name] = k
     dom = max((k for k in kernels if "GBps" in kernels[k]), key=lambda k: kernels[k]["ms"])
     kd = kernels[dom]
-    fp_peak = FP64_PEAK_TFLOPS if elem == 8 else FP32_PEAK_TFLOPS
-    frac_hbm = kd["GBps"] / peaks["hbm_gbs"]
+    fp_peak, fp_src = (pk["fp64_tflops"], pk["fp64_src"]) if elem == 8 else (pk["fp32_tflops"], pk["fp32_src"])
+    frac_hbm = kd["GBps"] / pk["hbm_gbs"]
     frac_alu = kd["GFLOPps"] / (fp_peak * 1e3)
     if frac_alu > frac_hbm:
         roof = {"kernel": dom, "bound": "alu", "achieved": round(kd["GFLOPps"] / 1e3, 4), "peak": fp_peak,
-                "unit": "TFLOP/s", "frac": round(frac_alu, 4),
-                "peak_src": "nominal FP64 rate of GB300 (1.25 TFLOP/s)" if elem == 8 else "152 SMs x 128 FMA x 2.07 GHz",
-                "hbm_frac": round(frac_hbm, 4)}
+                "unit": "TFLOP/s", "frac": round(frac_alu, 4), "peak_src": fp_src,
+                "hbm_frac": round(frac_hbm, 4), "hbm_peak_gbs": pk["hbm_gbs"]}
     else:
-        roof = {"kernel": dom, "bound": "hbm", "achieved": kd["GBps"], "peak": peaks["hbm_gbs"], "unit": "GB/s",
-                "frac": round(frac_hbm, 4), "peak_src": peaks["src"], "alu_frac": round(frac_alu, 4)}
+        roof = {"kernel": dom, "bound": "hbm", "achieved": kd["GBps"], "peak": pk["hbm_gbs"], "unit": "GB/s",
+                "frac": round(frac_hbm, 4), "peak_src": pk["hbm_src"], "alu_frac": round(frac_alu, 4)}
     # DRAM bytes per launch (read + write) from the ncu capture of this kernel
     # at N = 256 (profiles/); None where no capture of the current kernel exists
     tr = PROFILED_TRAFFIC.get((dom, elem)) if N == 256 else None
@@ -261,11 +299,12 @@ def run_native(args):
     torch.cuda.synchronize()
     if ws > 1:
         torch.distributed.barrier()
+    # --- the timed region: K realizations, no profiling events
     sampler = ClockSampler(local)
     sampler.start()
-    sq.sq_profile_enable(True)
     e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
     torch.cuda.synchronize()
+    launches0 = sq.sq_launch_count()
     e0.record(stream)
     all_infos, As = [], []
     for sd in seeds:
@@ -274,40 +313,15 @@ def run_native(args):
         As.append(A)
     e1.record(stream)
     torch.cuda.synchronize()
-    prof = sq.sq_profile_read()
-    sq.sq_profile_enable(False)
+    gpu_launches = sq.sq_launch_count() - launches0
     clocks = sampler.stop()
     t_ms, value = aggregate(e0.elapsed_time(e1), args.steps, ws, "cuda")
     iters = [i["iters"] for i in all_infos]
     ok = all(i["status"] == sq.SQ_OK and i["relres_true"] <= tol for i in all_infos)
-
-    # --- roofline of the dominant kernel class
     elem = 8 if prec == sq.SQ_FP64 else 4
-    kernels, roof = kernel_table(sq.sq_profile_work(), prof, N, elem, R, t_ms)
-    gpu_launches = int(sum(cnt for _, cnt in prof.values()))
-
-    # whole-solve HBM fraction: the fused iteration's 17 field passes (operator
-    # 2, x3 in 4, x2 2 + 2, x1 2, x3 out 5) of s-byte words per PCG iteration,
-    # against the solve's wall time (setup passes, residual recomputations
-    # and A_hom are not counted: a lower bound on the bytes moved)
-    def solve_hbm(its_mean, solves_per_s, s_bytes):
-        gbs = 17 * s_bytes * N ** 3 * its_mean * solves_per_s / 1e9
-        pk = _peaks()
-        return {"algorithmic_GBps": round(gbs, 1), "peak": pk["hbm_gbs"], "peak_src": pk["src"],
-                "frac": round(gbs / pk["hbm_gbs"], 4), "bytes_per_iteration": 17 * s_bytes * N ** 3}
-
-    out = {"metric": METRIC, "value": round(value, 4), "unit": UNIT, "n_gpus": ws, "steps": args.steps,
-           "warmup": args.warmup, "ms_per_step": round(t_ms / args.steps, 3), "higher_is_better": True,
-           "scaling": "weak", "vs_baseline": None, "dtype": "f64" if elem == 8 else "f32+f64",
-           "data": "synthetic",
-           "config": workload_config(args, ws),
-           "clocks": clocks, "gpu_launches": gpu_launches, "roofline": roof, "kernels": kernels,
-           "iters": {"mean": round(statistics.mean(iters), 2), "min": min(iters), "max": max(iters)},
-           "solve_hbm": solve_hbm(statistics.mean(iters), value / max(ws, 1), elem),
-           "converged": ok, "tiles": {"dht_pencils_fp32": tiles[0], "stencil_planes": tiles[1],
-                                                "stencil_rows_fp32": tiles[2]}}
 
     # --- end to end through the C ABI with pinned host inputs
+    e2e = None
     rng = np.random.default_rng(12345 + rank)
     if not args.no_e2e:
         host = [torch.from_numpy(rng.integers(0, 2, L ** 3, dtype=np.uint8)).pin_memory() for _ in range(args.steps)]
@@ -317,8 +331,48 @@ def run_native(args):
             step(None, upload=host[k])
         torch.cuda.synchronize()
         t_e2e = time.perf_counter() - t0
-        out["e2e"] = {"value": round(3 * args.steps / t_e2e, 4), "unit": UNIT, "h2d_bytes_per_step": L ** 3,
-                      "d2h_bytes_per_step": 2 * 9 * 8}
+        e2e = {"value": round(3 * args.steps / t_e2e, 4), "unit": UNIT, "h2d_bytes_per_step": L ** 3,
+               "d2h_bytes_per_step": 2 * 9 * 8}
+
+    # --- per-kernel profile from one more realization (untimed: the event
+    # pairs around every launch would slow the timed steps), and the measured
+    # roofline denominators
+    peaks = measure_peaks(sq, torch)
+    sq.sq_coeffs_regenerate(c, replica_seeds(rank, ws, 1, offset=10 ** 7)[0], wl["p_hi"])
+    sq.sq_profile_enable(True)
+    ep0, ep1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    ep0.record(stream)
+    for i in range(3):
+        sq.sq_pcg_solve(c, pc, w, i, tol, max_iter, prec, None, psis[i])
+    sq.sq_homogenized_matrix(c, *psis, energy=False)
+    ep1.record(stream)
+    torch.cuda.synchronize()
+    prof = sq.sq_profile_read()
+    sq.sq_profile_enable(False)
+    kernels, roof = kernel_table(sq.sq_profile_work(), prof, N, elem, R, ep0.elapsed_time(ep1), peaks)
+
+    # whole-solve HBM fraction: the fused iteration's 17 field passes (operator
+    # 2, x3 in 4, x2 2 + 2, x1 2, x3 out 5) of s-byte words per PCG iteration,
+    # against the solve's wall time (setup passes, residual recomputations
+    # and A_hom are not counted: a lower bound on the bytes moved)
+    def solve_hbm(its_mean, solves_per_s, s_bytes):
+        gbs = 17 * s_bytes * N ** 3 * its_mean * solves_per_s / 1e9
+        return {"algorithmic_GBps": round(gbs, 1), "peak": peaks["hbm_gbs"], "peak_src": peaks["hbm_src"],
+                "frac": round(gbs / peaks["hbm_gbs"], 4), "bytes_per_iteration": 17 * s_bytes * N ** 3}
+
+    out = {"metric": METRIC, "value": round(value, 4), "unit": UNIT, "n_gpus": ws, "steps": args.steps,
+           "warmup": args.warmup, "ms_per_step": round(t_ms / args.steps, 3), "higher_is_better": True,
+           "scaling": "weak", "vs_baseline": None, "dtype": "f64" if elem == 8 else "f32+f64",
+           "data": "synthetic",
+           "config": workload_config(args, ws),
+           "clocks": clocks, "gpu_launches": gpu_launches, "roofline": roof}
+    if e2e:
+        out["e2e"] = e2e
+    out.update({"peaks": peaks, "kernels": kernels,
+                "iters": {"mean": round(statistics.mean(iters), 2), "min": min(iters), "max": max(iters)},
+                "solve_hbm": solve_hbm(statistics.mean(iters), value / max(ws, 1), elem),
+                "converged": ok, "tiles": {"dht_pencils_fp32": tiles[0], "stencil_planes": tiles[1],
+                                           "stencil_rows_fp32": tiles[2]}})
 
     # --- variants on the same workload (2 steps each)
     if not args.no_variants and rank == 0:
@@ -349,8 +403,7 @@ def run_native(args):
                                "solve_hbm": solve_hbm(statistics.mean(its), 3 * nst / (tv / 1e3),
                                                       4 if pp == sq.SQ_FP32_REFINE else 8)}
             if label == "fp32_refine_rank8":
-                # per-kernel table from one more, profiled realization (the
-                # event pairs around every launch would slow the timed steps)
+                # per-kernel table from one more, profiled realization
                 sq.sq_coeffs_regenerate(c, replica_seeds(rank, ws, 1, offset=10 ** 7)[0], wl["p_hi"])
                 sq.sq_profile_enable(True)
                 evp0, evp1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
@@ -361,49 +414,131 @@ def run_native(args):
                 torch.cuda.synchronize()
                 pv = sq.sq_profile_read()
                 sq.sq_profile_enable(False)
-                kv, rv = kernel_table(sq.sq_profile_work(), pv, N, 4, rr, evp0.elapsed_time(evp1))
+                kv, rv = kernel_table(sq.sq_profile_work(), pv, N, 4, rr, evp0.elapsed_time(evp1), peaks)
                 variants[label]["kernels"] = kv
+                variants[label]["iteration_hbm"] = fused_iteration_hbm(kv, N, 4, peaks["hbm_gbs"])
                 out["roofline_fp32_refine"] = rv
             del pcv
         out["variants"] = variants
-
-    if not args.no_variants and rank == 0:
-        out.setdefault("variants", {})["batch_768_mixed"] = run_batch(sq, torch, stream)
-        out["variants"]["warm_start_n64"] = run_warm_start(sq, torch)
-        out["variants"]["refine_n512"] = run_refine_n512(sq, torch, stream)
-        out["variants"]["ensemble"] = run_ensemble(sq, torch)
-        out["variants"]["inclusions_alpha_quarter"] = run_inclusions(sq, torch, stream)
-        out["variants"]["two_contrasts_alpha_quarter"] = run_two_contrasts(sq, torch, stream)
-        out["variants"]["precond_routes_n256"] = run_precond_routes(sq, torch, stream)
-        out["variants"]["table_2d_alpha_quarter"] = run_2d_table(sq, torch, stream)
+        del w
+        torch.cuda.empty_cache()
+        variants["refine_error_n128"] = run_refine_error_n128(sq, torch)
+        variants["batch_768_mixed"] = run_batch(sq, torch, stream, peaks=peaks)
+        variants["warm_start_n64"] = run_warm_start(sq, torch)
+        variants["refine_n512"] = run_refine_n512(sq, torch, stream)
+        variants["ensemble"] = run_ensemble(sq, torch)
+        variants["inclusions_alpha_quarter"] = run_inclusions(sq, torch, stream)
+        variants["two_contrasts_alpha_quarter"] = run_two_contrasts(sq, torch, stream)
+        variants["precond_routes_n256"] = run_precond_routes(sq, torch, stream)
+        variants["table_2d_alpha_quarter"] = run_2d_table(sq, torch, stream)
 
     if rank == 0 and not args.no_cpu_baseline and ws == 1:
-        out["cpu_baseline"] = cpu_baseline(statistics.mean(iters), R)
+        out["cpu_baseline"] = cpu_baseline(R)
     if rank == 0:
+        out["summary"] = summarize(out)
         print(json.dumps(out))
     if ws > 1:
         torch.distributed.barrier()
         torch.distributed.destroy_process_group()
 
 
+def fused_iteration_hbm(kernels, N, elem, hbm_gbs):
+    """One fused PCG iteration from the per-class times of launches that did
+    work: operator + x3-in + 2 x x2 + x1 + x3-out, 17 field passes of
+    elem-byte words, against the HBM peak."""
+    need = ("stencil_matvec", "dht_x3_in", "dht_x2", "dht_x1_scale", "dht_x3_out")
+    if not all(k in kernels and "us_per_work_launch" in kernels[k] for k in need):
+        return None
+    us = sum(kernels[k]["us_per_work_launch"] for k in need) + kernels["dht_x2"]["us_per_work_launch"]
+    b = 17 * elem * N ** 3
+    return {"us": round(us, 1), "bytes": b, "GBps": round(b / (us * 1e-6) / 1e9, 1),
+            "frac": round(b / (us * 1e-6) / 1e9 / hbm_gbs, 4)}
+
+
+def summarize(out):
+    """The figures a reader needs first, repeated at the end of the line."""
+    v = out.get("variants", {})
+    sm = {"fp64_rank8_solves_per_s": out["value"], "e2e": (out.get("e2e") or {}).get("value"),
+          "roofline": {k: out["roofline"].get(k) for k in ("kernel", "bound", "frac", "peak", "peak_src", "hbm_frac")},
+          "peaks": {k: out.get("peaks", {}).get(k) for k in ("fp64_tflops", "fp32_tflops", "hbm_gbs", "copy_hbm_gbs",
+                                                              "copy_l2_gbs")}}
+    if "fp32_refine_rank8" in v:
+        sm["fp32_refine_rank8_solves_per_s"] = v["fp32_refine_rank8"]["solves_per_s"]
+        sm["fp32_refine_exact_solves_per_s"] = v["fp32_refine_exact"]["solves_per_s"]
+        sm["fp32_iteration_hbm"] = v["fp32_refine_rank8"].get("iteration_hbm")
+        sm["fp32_solve_hbm_frac"] = v["fp32_refine_rank8"]["solve_hbm"]["frac"]
+    if "roofline_fp32_refine" in out:
+        r = out["roofline_fp32_refine"]
+        sm["roofline_fp32_refine"] = {k: r.get(k) for k in ("kernel", "bound", "frac")}
+    if "batch_768_mixed" in v:
+        b = v["batch_768_mixed"]
+        sm["batch"] = {k: b.get(k) for k in ("solves_per_s", "iters_p50", "iters_p99", "hbm_frac")}
+    if "warm_start_n64" in v:
+        sm["warm_start"] = v["warm_start_n64"].get("summary")
+    if "refine_error_n128" in v:
+        sm["refine_error_n128"] = v["refine_error_n128"].get("max_rel_err")
+    if "cpu_baseline" in out:
+        sm["cpu_baseline"] = out["cpu_baseline"]["value"]
+    return sm
+
+
+def run_refine_error_n128(sq, torch, seeds=(0, 1, 2, 3)):
+    """The precision configuration's subsample (L = 16, n = 8, N = 128,
+    Bernoulli(1/2) on {1,100}): FP32 PCG inside FP64 refinement to 1e-10
+    against the FP64 PCG solve to 1e-12 on the same GPU, per corrector and
+    preconditioner (exact, rank 8): rel. L2 difference of psi and max
+    difference of A_hom relative to its largest entry. (The FP64 solve itself
+    matches the CPU oracle to 1e-9 in the parity tests.)"""
+    import numpy as np
+
+    L, n, N = 16, 8, 128
+    c = sq.sq_build_coeffs(L, n, 0, 0.5, 1.0, 100.0)
+    w64, w32 = sq.sq_workspace_create(N, sq.SQ_FP64), sq.sq_workspace_create(N, sq.SQ_FP32_REFINE)
+    p64 = [torch.empty(N ** 3, dtype=torch.float64, device="cuda") for _ in range(3)]
+    p32 = [torch.empty(N ** 3, dtype=torch.float64, device="cuda") for _ in range(3)]
+    res, worst = {}, 0.0
+    for rank in (0, 8):
+        pc = sq.sq_precond_setup(N, rank)
+        rows = []
+        for sd in seeds:
+            sq.sq_coeffs_regenerate(c, sd, 0.5)
+            errs = []
+            for i in range(3):
+                sq.sq_pcg_solve(c, pc, w64, i, 1e-12, 4000, sq.SQ_FP64, None, p64[i])
+                sq.sq_pcg_solve(c, pc, w32, i, 1e-10, 4000, sq.SQ_FP32_REFINE, None, p32[i])
+                errs.append(float(torch.linalg.norm(p32[i] - p64[i]) / torch.linalg.norm(p64[i])))
+            A64, _ = sq.sq_homogenized_matrix(c, *p64, energy=False)
+            A32, _ = sq.sq_homogenized_matrix(c, *p32, energy=False)
+            ea = float(np.abs(A32 - A64).max() / np.abs(A64).max())
+            rows.append({"seed": sd, "psi": [float(f"{e:.3g}") for e in errs], "A_hom": float(f"{ea:.3g}")})
+            worst = max(worst, max(errs), ea)
+        res[f"rank{rank}"] = rows
+    res["max_rel_err"] = float(f"{worst:.3g}")
+    return res
+
+
 def batch_algorithmic(Ns, iters, seconds, hbm_gbs):
     """Algorithmic traffic of a batch: 17 FP32 field passes (4 N^3 bytes each)
     per inner PCG iteration of every solve, over the batch's wall time, and
-    that rate against the HBM peak. The fields of the small grids a batch
-    holds stay in L2 between passes, so this is not DRAM traffic."""
+    that rate against the HBM peak. Every kernel of the batch sweeps all its
+    solves, whose fields (5 N^3 floats per solve) together far exceed L2, so
+    these passes are HBM traffic."""
     b = float(sum(17 * 4 * int(N) ** 3 * int(it) for N, it in zip(Ns, iters)))
+    ws = float(sum(5 * 4 * int(N) ** 3 for N in Ns))
     gbs = b / seconds / 1e9
-    return {"algorithmic_bytes": b, "algorithmic_GBps": round(gbs, 1), "algorithmic_frac_of_hbm": round(gbs / hbm_gbs, 4),
-            "algorithmic_note": "17 FP32 field passes per inner iteration / wall time; fields are L2-resident"}
+    return {"algorithmic_bytes": b, "algorithmic_GBps": round(gbs, 1), "hbm_frac": round(gbs / hbm_gbs, 4),
+            "working_set_GB": round(ws / 1e9, 2),
+            "algorithmic_note": "17 FP32 field passes per inner iteration / wall time; working set far above L2"}
 
 
-def run_batch(sq, torch, stream, nseeds=256):
+def run_batch(sq, torch, stream, nseeds=256, peaks=None):
     """768 corrector solves (256 realizations x e_1..e_3) in one batch: L drawn
     from {8,12,16,24} per seed, n=4 (N = 32..96), Bernoulli(1/2) on {1,10},
-    exact preconditioner, FP32 PCG in FP64 refinement to 1e-8."""
+    exact preconditioner, FP32 PCG in FP64 refinement to 1e-8; tiles per N
+    from the batch autotuner (each N's sub-batch timed per candidate)."""
     import numpy as np
 
-    from paper_2007_06524_gb300 import workloads
+    from paper_2007_06524_gb300 import autotune, workloads
 
     wl = workloads.BATCH_MIXED
     precs, descs, pl, coeffs, Ns = {}, [], [], [], []
@@ -418,26 +553,35 @@ def run_batch(sq, torch, stream, nseeds=256):
             descs.append((c, i, torch.empty(N ** 3, dtype=torch.float64, device="cuda")))
             pl.append(precs[N])
             Ns.append(N)
-    b = sq.sq_batch_create(descs, pl)
-    sq.sq_pcg_solve_batched(b, wl["tol"], 2000)  # warm-up (graph capture, first touch)
-    torch.cuda.synchronize()
-    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
-    e0.record(stream)
-    infos = sq.sq_pcg_solve_batched(b, wl["tol"], 2000)
-    e1.record(stream)
-    torch.cuda.synchronize()
-    t = e0.elapsed_time(e1) / 1e3
+    t0 = time.perf_counter()
+    tiles, tune_ms = autotune.tune_batch(torch, descs, pl, wl["tol"])
+    tune_s = time.perf_counter() - t0
+    res = {}
+    for label, tl in (("default_tiles", None), ("tuned_tiles", tiles)):
+        b = sq.sq_batch_create(descs, pl, tiles=tl)
+        sq.sq_pcg_solve_batched(b, wl["tol"], 2000)  # warm-up (graph capture, first touch)
+        torch.cuda.synchronize()
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        infos = sq.sq_pcg_solve_batched(b, wl["tol"], 2000)
+        e1.record(stream)
+        torch.cuda.synchronize()
+        del b
+        res[label] = (e0.elapsed_time(e1) / 1e3, infos)
+    t, infos = res["tuned_tiles"]
     its = np.array([i["iters"] for i in infos])
     ok = all(i["status"] == sq.SQ_OK for i in infos)
     unknowns = sum(d[2].numel() for d in descs)
     out = {"solves": len(descs), "solves_per_s": round(len(descs) / t, 1), "seconds": round(t, 4),
            "iters_p50": float(np.percentile(its, 50)), "iters_p99": float(np.percentile(its, 99)),
-           "unknowns": unknowns, "converged": ok}
-    out.update(batch_algorithmic(Ns, its, t, _peaks()["hbm_gbs"]))
+           "unknowns": unknowns, "converged": ok, "tiles": [list(x) for x in tiles],
+           "default_tiles_solves_per_s": round(len(descs) / res["default_tiles"][0], 1),
+           "tune_seconds": round(tune_s, 2), "tune_ms": tune_ms}
+    out.update(batch_algorithmic(Ns, its, t, (peaks or default_peaks())["hbm_gbs"]))
     return out
 
 
-def run_warm_start(sq, torch, nseeds=64):
+def run_warm_start(sq, torch, nseeds=512):
     """Zero start vs learned start (committed weights, trained on seeds 1000..5095)
     on held-out seeds 6000.. at L=16, n=4 (N=64), Bernoulli(1/2) on {1,10},
     exact preconditioner, tol 1e-8: FP32+FP64 refinement and plain FP64."""
@@ -448,9 +592,17 @@ def run_warm_start(sq, torch, nseeds=64):
     wl = workloads.WARM_N64
     net = warmstart.load(warmstart.DEFAULT_WEIGHTS)
     seeds = wl["eval_seeds"][:nseeds]
-    res = {"eval_seeds": f"{seeds[0]}..{seeds[-1]}"}
+    res = {"eval_seeds": f"{seeds[0]}..{seeds[-1]} ({len(seeds)})"}
     res["fp32_refine"] = warmstart.evaluate(torch, wl, net, seeds, sq.SQ_FP32_REFINE)
-    res["fp64"] = warmstart.evaluate(torch, wl, net, seeds[:16], sq.SQ_FP64)
+    res["fp64"] = warmstart.evaluate(torch, wl, net, seeds, sq.SQ_FP64)
+    base = res["fp64"]["zero"]["solves_per_s"]
+    res["summary"] = {"seeds": len(seeds), "plain_fp64_zero": base,
+                      "fp64_learned": res["fp64"]["learned"]["solves_per_s"],
+                      "fp32_refine_zero": res["fp32_refine"]["zero"]["solves_per_s"],
+                      "fp32_refine_learned": res["fp32_refine"]["learned"]["solves_per_s"],
+                      "iters_fp64_zero_learned": [res["fp64"]["zero"]["iters_mean"], res["fp64"]["learned"]["iters_mean"]],
+                      "iters_fp32_zero_learned": [res["fp32_refine"]["zero"]["iters_mean"],
+                                                  res["fp32_refine"]["learned"]["iters_mean"]]}
     return res
 
 
@@ -686,23 +838,46 @@ def run_refine_n512(sq, torch, stream):
     return res
 
 
-def _oracle_sample(iters_mean, R, n_iter_sample=3):
-    """Times the oracle (FP64 CSR + numpy FFT PCG) on one N=256 realization:
-    assembly + RHS, then `n_iter_sample` PCG iterations of e_1; extrapolates to
-    corrector solves/s with the GPU's mean iteration count."""
+def _oracle_precond(N, R, workers):
+    """The oracle's preconditioner with the same construction as the GPU path
+    (the exact diagonal, or the least-squares exponential sum), its FFTs on
+    `workers` threads."""
+    from oracle import precond
+
+    G = precond.core_tensor_exact(N) if R == 0 else precond.core_tensor_from_nodes(N, *precond.lsq_nodes(N, R))
+    return lambda r: precond.apply_precond(G, r.reshape(N, N, N), workers).ravel()
+
+
+def _oracle_iterations(R, workers):
+    """The oracle's own PCG iteration count on this workload's cells at a size
+    it solves in seconds: L = 8, n = 8 (N = 64), Bernoulli(1/2) on {1,100},
+    seed 0, e_1, tol 1e-8 (counts are nearly flat in N, Lemma 4.1)."""
+    from oracle import pcg, problem
+
+    re = problem.realization(8, 8, 0, 1.0, 100.0)
+    _, it, _ = pcg.pcg(re.A, re.b[0], _oracle_precond(re.N, R, workers), tol=1e-8)
+    return it
+
+
+def _oracle_sample(R, workers, n_iter_sample=3):
+    """Times the oracle (FP64 scipy CSR SpMV + scipy.fft PCG on `workers`
+    threads) on one N=256 realization: assembly + RHS, then `n_iter_sample`
+    PCG iterations of e_1; a solve is the oracle's own iteration count at
+    N = 64 (see _oracle_iterations) plus one preconditioner apply."""
     from oracle import pcg, problem
     from paper_2007_06524_gb300 import workloads
 
     wl = workloads.PLAIN_N256
+    its = _oracle_iterations(R, workers)
     t0 = time.perf_counter()
     re = problem.realization(wl["L"], wl["n"], 0, wl["a_lo"], wl["a_hi"])
     t_setup = time.perf_counter() - t0
-    P = pcg.fft_preconditioner(re.N, R)
+    P = _oracle_precond(re.N, R, workers)
     t0 = time.perf_counter()
     pcg.pcg(re.A, re.b[0], P, tol=1e-30, maxit=n_iter_sample)
     t_it = (time.perf_counter() - t0) / (n_iter_sample + 1)  # + initial preconditioner apply
-    t_solve = t_setup / 3.0 + (iters_mean + 1) * t_it
-    return t_setup, t_it, t_solve
+    t_solve = t_setup / 3.0 + (its + 1) * t_it
+    return t_setup, t_it, t_solve, its
 
 
 def _host_cpu(cpuinfo="/proc/cpuinfo"):
@@ -727,17 +902,20 @@ def _host_cpu(cpuinfo="/proc/cpuinfo"):
     return {"cpu_model": model, "cores_available": len(os.sched_getaffinity(0))}
 
 
-def cpu_baseline(iters_mean, R):
-    t_setup, t_it, t_solve = _oracle_sample(iters_mean, R)
-    return {"value": round(1.0 / t_solve, 6), "unit": UNIT, "cores": 1, "kind": "oracle", **_host_cpu(),
+def cpu_baseline(R):
+    workers = len(os.sched_getaffinity(0))
+    t_setup, t_it, t_solve, its = _oracle_sample(R, workers)
+    return {"value": round(1.0 / t_solve, 6), "unit": UNIT, "cores": workers, "kind": "oracle", **_host_cpu(),
             "sample": f"oracle at N=256 (L=32, n=8, seed 0): assembly+RHS {t_setup:.1f} s (shared by 3 correctors) "
-                      f"+ {t_it:.2f} s per PCG iteration (rank-{R}), measured on 3 iterations, extrapolated to "
-                      f"{iters_mean:.1f} iterations per solve; single-threaded numpy/scipy on "
-                      f"{len(os.sched_getaffinity(0))} available host cores"}
+                      f"+ {t_it:.2f} s per PCG iteration (rank-{R}), measured on 3 iterations, times the oracle's "
+                      f"own {its} iterations (its PCG at N=64, same cells and tolerance); FFTs on {workers} threads "
+                      f"(scipy.fft), CSR SpMV single-threaded"}
 
 
 def run_reference(args):
-    """The oracle as the reference arm, on this arm's workload and metric."""
+    """The oracle as the reference arm, on this arm's workload and metric:
+    each step times one oracle PCG iteration at N = 256; a solve is the
+    oracle's own iteration count at N = 64 plus the assembly's share."""
     ws, rank, _ = _dist()
     if rank != 0:
         return
@@ -746,13 +924,12 @@ def run_reference(args):
 
     wl = workloads.PLAIN_N256
     R = args.rank
+    workers = len(os.sched_getaffinity(0))
+    its = _oracle_iterations(R, workers)
     t0 = time.perf_counter()
     re = problem.realization(wl["L"], wl["n"], 0, wl["a_lo"], wl["a_hi"])
     t_setup = time.perf_counter() - t0
-    P = pcg.fft_preconditioner(re.N, R)
-    # PCG iterations per solve on this workload (FP64, tol 1e-8, measured with
-    # the same method on the GPU; the oracle's PCG takes the same iterations)
-    iters_per_solve = {0: 42.5, 4: 84.0, 8: 57.0, 16: 49.3}.get(R, 57.0)
+    P = _oracle_precond(re.N, R, workers)
     times = []
     for k in range(args.warmup + args.steps):
         t0 = time.perf_counter()
@@ -761,15 +938,17 @@ def run_reference(args):
         if k >= args.warmup:
             times.append(dt / 2)  # one preconditioner apply before + one PCG iteration
     t_it = statistics.mean(times)
-    t_solve = t_setup / 3.0 + (iters_per_solve + 1) * t_it
+    t_solve = t_setup / 3.0 + (its + 1) * t_it
     value = 1.0 / t_solve
     out = {"metric": METRIC, "value": round(value, 6), "unit": UNIT, "n_gpus": ws, "steps": args.steps,
            "warmup": args.warmup, "ms_per_step": round(t_it * 1e3, 3), "higher_is_better": True, "scaling": "weak",
            "vs_baseline": None, "dtype": "f64", "data": "synthetic", "impl": "reference",
            "config": workload_config(args, _dist()[0]),
-           "cpu_baseline": {"value": round(value, 6), "unit": UNIT, "cores": 1, "kind": "oracle", **_host_cpu(),
-                            "sample": f"step = one PCG iteration of the oracle at N=256 ({t_it:.2f} s); assembly "
-                                      f"{t_setup:.1f} s once; extrapolated to {iters_per_solve:.0f} iterations"},
+           "cpu_baseline": {"value": round(value, 6), "unit": UNIT, "cores": workers, "kind": "oracle", **_host_cpu(),
+                            "sample": f"step = one PCG iteration of the oracle at N=256 ({t_it:.2f} s; FFTs on "
+                                      f"{workers} threads, CSR SpMV single-threaded); assembly {t_setup:.1f} s "
+                                      f"once; a solve = the oracle's own {its} iterations (its PCG at N=64, same "
+                                      f"cells and tolerance)"},
            "e2e": {"value": round(value, 6), "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
     print(json.dumps(out))
 

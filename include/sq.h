@@ -76,7 +76,7 @@ typedef struct sq_workspace sq_workspace;
 typedef struct sq_solve_info {
   int iters;          /* PCG iterations (x updates); summed over inner solves   */
   int outer_steps;    /* refinement steps (1 for SQ_FP64)                       */
-  int status;         /* SQ_OK or SQ_ENOCONV                                     */
+  int status;         /* SQ_OK, SQ_ENOCONV or SQ_ETIMEOUT (the call's return)   */
   int used_guess;     /* 1 if x0 was used                                        */
   double relres;      /* last recurrence residual ||r||/||b||                    */
   double relres_true; /* ||b - A psi||/||b||, recomputed in FP64 after the solve */
@@ -216,8 +216,14 @@ void sq_workspace_destroy(sq_workspace *w);
  * FP64 residual (continuing from the current iterate if that fails). The
  * result psi (device, N^3 doubles, may alias x0) is projected to zero mean.
  * SQ_FP32_REFINE: psi is refined in FP64, each correction solved in FP32 to
- * relative residual 1e-4 (at most max_iter inner iterations in total).
- * Synchronizes `stream` (the host checks convergence). info may be NULL. */
+ * relative residual 1e-5 by default (SQ_OPT_INNER_TOL_EXP; at most max_iter
+ * inner iterations in total). Returns SQ_OK, SQ_ENOCONV (tolerance missed
+ * within max_iter; psi and info are valid) or SQ_ETIMEOUT: a bounded device
+ * wait (pass E's staging of p and x in the FP32 iteration, SQ_OPT_WAIT_POLLS)
+ * gave up; that kernel read its operands from global memory instead, the
+ * solve ran to the end, and psi (zero mean) and info are complete as for
+ * SQ_OK. Synchronizes `stream` (the host checks convergence). info may be
+ * NULL. */
 int sq_pcg_solve(const sq_coeffs *c, const sq_precond *pc, sq_workspace *w, int dir, double tol,
                  int max_iter, int precision, const double *x0, double *psi,
                  sq_solve_info *info, sq_stream_t stream);
@@ -270,8 +276,13 @@ int sq_set_tiles(const sq_tile_config *tiles, int ntiles);
  * SQ_OPT_INNER_TOL_EXP (default 5): each inner FP32 solve of SQ_FP32_REFINE
  * (single and batched) cuts its residual by 10^-value, or just enough for the
  * outer tolerance when that is less; 2 <= value <= 7.
+ * SQ_OPT_WAIT_POLLS (default 4194304 = 2^22): how many times the FP32 pass E
+ * of single solves polls the barrier of its bulk copies of p and x before it
+ * gives up, reads them from global memory, flags the solve (SQ_ETIMEOUT) and
+ * stops staging; 0 gives up at once. The block still waits (up to 2^24 polls)
+ * for its copies in flight before it exits. 0 <= value <= 2^24.
  */
-enum sq_option { SQ_OPT_STRIDED_TWO_STAGE = 1, SQ_OPT_STENCIL_ROWS = 2, SQ_OPT_INNER_TOL_EXP = 3 };
+enum sq_option { SQ_OPT_STRIDED_TWO_STAGE = 1, SQ_OPT_STENCIL_ROWS = 2, SQ_OPT_INNER_TOL_EXP = 3, SQ_OPT_WAIT_POLLS = 4 };
 int sq_set_option(int key, int value);
 
 /* Plans a batch of `count` solves; precs[k] is the preconditioner (same N) of
@@ -395,6 +406,25 @@ int sq_profile_read(double *ms, int64_t *launches, int max_classes);
  * sq_profile_read does; returns the number of classes. */
 int sq_profile_work(double *ms, int64_t *launches, int max_classes);
 const char *sq_profile_class_name(int k);
+/* Kernel launches the single-solve path (sq_pcg_solve, sq_homogenized_matrix,
+ * the coefficient and verification calls) has issued since the library was
+ * loaded, whether or not profiling is enabled (a host-side counter). */
+int64_t sq_launch_count(void);
+
+/* Throughput probes (measurement aids for rooflines; the paper has no
+ * counterpart). Both are synchronous on `stream`, time their own kernel with
+ * CUDA events after a warm-up launch, and report the rate at the clocks of
+ * that moment.
+ * sq_probe_fma: precision 0 = FP64, 1 = FP32; a grid at the occupancy limit,
+ * eight independent fused multiply-add chains per thread, about 30 ms of
+ * work; *tflops = 2 flops per FMA / time, *ms the kernel time (either may be
+ * NULL). Allocates 8 bytes per block (stream-ordered) for its guard output.
+ * sq_probe_copy: dst = src over `bytes` (device buffers, 16-byte aligned,
+ * bytes a multiple of 16), `reps` launches (1..10000); *gbps = 2 bytes reps /
+ * time (read + write, as a STREAM copy). Buffers far above the L2 size measure
+ * HBM; buffers that fit in L2 measure L2. */
+int sq_probe_fma(int precision, double *tflops, float *ms, sq_stream_t stream);
+int sq_probe_copy(const void *src, void *dst, size_t bytes, int reps, double *gbps, sq_stream_t stream);
 
 const char *sq_strerror(int status);
 

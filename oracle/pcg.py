@@ -56,12 +56,13 @@ def pcg(A, b: np.ndarray, apply_P=None, tol: float = 1e-10, maxit: int = 10000, 
     return x, it, float(np.linalg.norm(b - A @ x) / nb)
 
 
-def fft_preconditioner(N: int, rank: int):
-    """Flat-vector wrapper of the Sec. 4.2 preconditioner (exact if rank == 0)."""
+def fft_preconditioner(N: int, rank: int, workers: int | None = None):
+    """Flat-vector wrapper of the Sec. 4.2 preconditioner (exact if rank == 0);
+    workers: FFT threads (None = numpy's single-threaded FFT)."""
     G = _pc.core_tensor(N, rank)
 
     def apply(r):
-        return _pc.apply_precond(G, r.reshape(N, N, N)).ravel()
+        return _pc.apply_precond(G, r.reshape(N, N, N), workers).ravel()
 
     return apply
 

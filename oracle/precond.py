@@ -234,9 +234,14 @@ def core_tensor(N: int, rank: int) -> np.ndarray:
     return core_tensor_exact(N) if rank == 0 else core_tensor_rank_r(N, rank)
 
 
-def apply_precond(G: np.ndarray, r: np.ndarray) -> np.ndarray:
-    """z = F^{-1} (G * F r) on an (N,N,N) field (Eq. 31); zero-mean output."""
-    return np.real(np.fft.ifftn(G * np.fft.fftn(r)))
+def apply_precond(G: np.ndarray, r: np.ndarray, workers: int | None = None) -> np.ndarray:
+    """z = F^{-1} (G * F r) on an (N,N,N) field (Eq. 31); zero-mean output.
+    workers: threads of the FFT (scipy.fft); None = numpy's single-threaded FFT."""
+    if workers is None:
+        return np.real(np.fft.ifftn(G * np.fft.fftn(r)))
+    import scipy.fft
+
+    return np.real(scipy.fft.ifftn(G * scipy.fft.fftn(r, workers=workers), workers=workers))
 
 
 def spectral_ratio(N: int, R: int) -> float:

@@ -1,5 +1,6 @@
 """Tile autotuner: times candidate tile shapes through the C ABI and installs
-the fastest per grid size with sq_set_tiles.
+the fastest per grid size with sq_set_tiles (single solves), or returns the
+fastest per grid size of a batch for sq_batch_create (tune_batch).
 
 Tuned per N: the number of complex pencils of a Hartley-pass tile (FP32 passes;
 2P real pencils, 2P * 4 bytes per row segment), and jointly the node rows per
@@ -97,3 +98,49 @@ def tune(torch, N, L=None, n=None, cache=DEFAULT_CACHE, reps=5):
         os.makedirs(os.path.dirname(cache), exist_ok=True)
         json.dump(table, open(cache, "w"), indent=1)
     return bestP, bestZ, bestR
+
+
+def tune_batch(torch, descs, precs, tol, max_iter=2000, pencils=(4, 8, 16), planes=None, stream=None):
+    """Tile shapes for a batch, per grid size: for each N the batch holds, the
+    sub-batch of its solves with that N is planned with every candidate tile
+    (Hartley pencils P with 2P dividing N; operator planes per work item, by
+    default N/8, N/4 and N/2) and solved once after a warm-up solve; the
+    fastest (CUDA events on the launching stream) is kept. Returns the list of
+    (N, dht_pencils, stencil_planes) entries for sq_batch_create and the
+    per-candidate times in ms."""
+    byN = {}
+    for d, p in zip(descs, precs):
+        _, _, N = _sq.sq_coeffs_shape(d[0])
+        byN.setdefault(N, ([], []))
+        byN[N][0].append(d)
+        byN[N][1].append(p)
+    chosen, times = [], {}
+    for N, (ds, ps) in sorted(byN.items()):
+        cands = []
+        for P in pencils:
+            if N % (2 * P):
+                continue
+            for zc in (planes or sorted({max(2, N // 8), max(2, N // 4), max(2, N // 2)})):
+                cands.append((P, zc))
+        best, best_ms = None, float("inf")
+        for P, zc in cands:
+            try:
+                b = _sq.sq_batch_create(ds, ps, tiles=[(N, P, zc)])
+            except _sq.SqError:
+                continue
+            _sq.sq_pcg_solve_batched(b, tol, max_iter, stream)  # warm-up: graph capture, first touch
+            torch.cuda.synchronize()
+            e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            s = stream or torch.cuda.current_stream()
+            e0.record(s)
+            _sq.sq_pcg_solve_batched(b, tol, max_iter, stream)
+            e1.record(s)
+            torch.cuda.synchronize()
+            ms = e0.elapsed_time(e1)
+            times[f"{N}:{P}x{zc}"] = round(ms, 3)
+            del b
+            if ms < best_ms:
+                best, best_ms = (N, P, zc), ms
+        if best is not None:
+            chosen.append(best)
+    return chosen, times

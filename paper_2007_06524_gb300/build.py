@@ -17,7 +17,7 @@ CSRC = os.path.join(HERE, "csrc")
 INCLUDE = os.path.join(ROOT, "include")
 BUILD_DIR = os.path.join(ROOT, "_build")
 LIB = os.path.join(HERE, "libsq.so")
-SOURCES = ["stencil.cu", "dht.cu", "solver.cu", "noalloc.cu", "batch.cu", "warmstart.cu", "ensemble.cu", "canonical.cu", "solver2d.cu"]
+SOURCES = ["stencil.cu", "dht.cu", "solver.cu", "noalloc.cu", "batch.cu", "warmstart.cu", "ensemble.cu", "canonical.cu", "solver2d.cu", "probe.cu"]
 
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 FLAGS = ["-O3", "-lineinfo", "-std=c++17", "-Xcompiler", "-fPIC", "-Xcompiler", "-O2",

@@ -404,6 +404,9 @@ bool grid_size_ok(int N);
 // Residual reduction asked of each inner FP32 solve of the refinement (10^-e).
 int set_inner_tol_exp(int e);
 double inner_tol();
+// Polls of pass E's staging wait before it gives up (0: at once; default 2^22).
+int set_stage_wait_polls(int polls);
+int stage_wait_polls();
 // Exponential sum sum_r w_r exp(-t_r x) ~ 1/x over the dim-D spectrum of the
 // periodic Laplacian on N points per axis (dim = 2 or 3).
 void exp_sum_nodes(int N, int R, int dim, std::vector<double> &t, std::vector<double> &w);

@@ -46,6 +46,7 @@ struct DhtArgs {
   int logP;
   int ntiles;
   int stage;  // pass E with the PCG update: stage the tile's p and x rows (set by the launcher)
+  int wait_polls;  // polls of a staging wait before it gives up (set by the launcher)
 };
 
 template <typename T, int AXIS, int LOADM, int STOREM, bool SCALE>
@@ -243,7 +244,7 @@ __global__ void __launch_bounds__(kThreads, s2_min_blocks(R0 * R1, STOREM == SO_
     x3_stage1<float, C, R0, R1, P, LOADM>(t, row0, sm, acc);
     x3_stage2<float, C, R0, R1, P>(sm, tw);
     if (staged) {
-      const bool ok = mbar_wait(&mbar, phase, 1 << 22);
+      const bool ok = mbar_wait(&mbar, phase, a.wait_polls);
       phase ^= 1u;
       if (!ok) {
         a.rb.st->fault = 1;
@@ -255,7 +256,9 @@ __global__ void __launch_bounds__(kThreads, s2_min_blocks(R0 * R1, STOREM == SO_
       x3_combine<float, C, N, P, STOREM>(t, row0, sm);
     }
   }
-  if (late) mbar_wait(&mbar, phase ^ 1u, 1 << 24);  // do not leave with a copy into this block in flight
+  // do not leave with a copy into this block in flight (this drain keeps its
+  // own, long limit whatever the option says)
+  if (late) mbar_wait(&mbar, phase ^ 1u, 1 << 24);
   if (LOADM == LD_RESID) {
     FF v[1] = {acc.part()};
     double s[1];
@@ -276,6 +279,7 @@ static cudaError_t launch_s3(const DhtArgs<float> &a, int grid, cudaStream_t s) 
   // bulk copies need 16-byte aligned rows (the workspace fields are)
   const bool aligned = ((reinterpret_cast<uintptr_t>(a.p) | reinterpret_cast<uintptr_t>(a.x)) & 15) == 0;
   b.stage = (STOREM == SO_PCG && !a.first && aligned && base + rows <= 110 * 1024) ? 1 : 0;
+  b.wait_polls = sq::stage_wait_polls();
   const size_t smem = base + (b.stage ? rows : 0);
   auto kern = k_dht_s3<R0, R1, P, LOADM, STOREM>;
   cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);

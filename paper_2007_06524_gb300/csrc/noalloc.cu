@@ -23,6 +23,7 @@
 //  * the first call on each device looks up the array's device address with
 //    cudaGetSymbolAddress while that device is current; make that first call
 //    before any stream capture begins.
+#include <cmath>
 #include <mutex>
 
 #include "common.cuh"
@@ -94,7 +95,7 @@ extern "C" int sq_homogenized_matrix_noalloc(int L, int n, const uint8_t *phase,
                                              const double *psi0, const double *psi1, const double *psi2,
                                              double *out, sq_stream_t stream) {
   if (!grid_ok(L, n) || !phase || !psi0 || !psi1 || !psi2 || !out) return SQ_EINVAL;
-  if (!(a_lo > 0.0) || !(a_hi > 0.0)) return SQ_EINVAL;
+  if (!(a_lo > 0.0) || !(a_hi > 0.0) || !std::isfinite(a_lo) || !std::isfinite(a_hi)) return SQ_EINVAL;
   double *scratch = nullptr;
   int st = scratch_address(&scratch);
   if (st != SQ_OK) return st;

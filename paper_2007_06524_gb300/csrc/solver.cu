@@ -86,7 +86,10 @@ int64_t g_prof_work_n[PC_COUNT] = {0};
 
 const size_t kNoProf = (size_t)-1;
 
+int64_t g_launches = 0;  // every kernel launch through SQ_LAUNCH since the library was loaded
+
 size_t prof_begin(int cls, cudaStream_t s) {
+  ++g_launches;
   if (!g_prof.on) return kNoProf;
   while (g_prof.pool.size() < g_prof.used + 2) {
     cudaEvent_t e;
@@ -537,6 +540,7 @@ int solve_fp32_refine(const sq_coeffs *c, const sq_precond *pc, sq_workspace *w,
   if (!used_guess) SQ_CK(cudaMemsetAsync(psi, 0, sizeof(double) * n3, s));
   int total_inner = 0, outer = 0;
   double relres_in = 0.0;
+  bool timed_out = false;
   for (;;) {
     // FP64 true residual, stored as the FP32 right-hand side of the correction
     // (from psi = 0 it is b itself: the right-hand-side sweep, no operator)
@@ -562,7 +566,10 @@ int solve_fp32_refine(const sq_coeffs *c, const sq_precond *pc, sq_workspace *w,
     SQ_LAUNCH(PC_VECTOR, s, launch_add_f32_to_f64(psi, d, n3, s));
     st = read_scalars(hi, ri.st, s);
     if (st != SQ_OK) return st;
-    if (hi->fault) return SQ_ETIMEOUT;  // a bounded wait in a kernel gave up (results are still complete)
+    // a bounded staging wait gave up: the kernel read its operands from
+    // global memory instead, so the step is complete; the solve carries on
+    // and reports SQ_ETIMEOUT at the end
+    timed_out = timed_out || hi->fault;
     relres_in = (hi->bb > 0.0) ? std::sqrt(hi->rr / hi->bb) : 0.0;
     total_inner += hi->iter;
     ++outer;
@@ -572,15 +579,16 @@ int solve_fp32_refine(const sq_coeffs *c, const sq_precond *pc, sq_workspace *w,
   SQ_LAUNCH(PC_VECTOR, s, launch_sub_mean<double>(psi, ro, n3, s));
   SQ_CK(cudaStreamSynchronize(s));
   const double rel = (ho->bb > 0.0) ? std::sqrt(ho->rr_true / ho->bb) : 0.0;
+  const int status = timed_out ? SQ_ETIMEOUT : (ho->bb == 0.0 || rel <= tol) ? SQ_OK : SQ_ENOCONV;
   if (info) {
     info->iters = total_inner;
     info->outer_steps = outer;
     info->used_guess = used_guess ? 1 : 0;
     info->relres = relres_in;
     info->relres_true = rel;
-    info->status = (ho->bb == 0.0 || rel <= tol) ? SQ_OK : SQ_ENOCONV;
+    info->status = status;
   }
-  return (ho->bb == 0.0 || rel <= tol) ? SQ_OK : SQ_ENOCONV;
+  return status;
 }
 
 template <typename T>
@@ -606,6 +614,13 @@ int set_inner_tol_exp(int e) {
   return 0;
 }
 double inner_tol() { return std::pow(10.0, -(double)g_inner_tol_exp); }
+static int g_stage_wait_polls = 1 << 22;
+int set_stage_wait_polls(int polls) {
+  if (polls < 0 || polls > (1 << 24)) return 1;
+  g_stage_wait_polls = polls;
+  return 0;
+}
+int stage_wait_polls() { return g_stage_wait_polls; }
 bool grid_size_ok(int N) { return valid_N(N); }
 void exp_sum_nodes(int N, int R, int dim, std::vector<double> &t, std::vector<double> &w) {
   rank_r_nodes(N, R, t, w, dim);
@@ -837,6 +852,8 @@ int sq_profile_work(double *ms, int64_t *launches, int max_classes) {
 
 const char *sq_profile_class_name(int k) { return (k >= 0 && k < PC_COUNT) ? kProfNames[k] : "?"; }
 
+int64_t sq_launch_count(void) { return g_launches; }
+
 int sq_coeffs_set_subcell(sq_coeffs *c, int sub) {
   if (!c || sub < 1 || sub > c->n || (c->n - sub) % 2 != 0) return SQ_EINVAL;
   if (sub == c->n) {
@@ -1044,6 +1061,7 @@ int sq_set_option(int key, int value) {
   if (key == SQ_OPT_STRIDED_TWO_STAGE) return set_strided_fast(value) == 0 ? SQ_OK : SQ_EINVAL;
   if (key == SQ_OPT_STENCIL_ROWS) return set_stencil_rows(value) == 0 ? SQ_OK : SQ_EINVAL;
   if (key == SQ_OPT_INNER_TOL_EXP) return set_inner_tol_exp(value) == 0 ? SQ_OK : SQ_EINVAL;
+  if (key == SQ_OPT_WAIT_POLLS) return set_stage_wait_polls(value) == 0 ? SQ_OK : SQ_EINVAL;
   return SQ_EINVAL;
 }
 

@@ -16,6 +16,7 @@ SQ_FP64, SQ_FP32_REFINE = 0, 1
 SQ_OPT_STRIDED_TWO_STAGE = 1
 SQ_OPT_STENCIL_ROWS = 2
 SQ_OPT_INNER_TOL_EXP = 3
+SQ_OPT_WAIT_POLLS = 4
 
 _HERE = os.path.dirname(os.path.abspath(__file__))
 _LIB = None
@@ -75,6 +76,9 @@ def load_library():
         "sq_profile_read": (i, [vp, vp, i]),
         "sq_profile_work": (i, [vp, vp, i]),
         "sq_profile_class_name": (C.c_char_p, [i]),
+        "sq_launch_count": (C.c_int64, []),
+        "sq_probe_fma": (i, [i, p(d), p(C.c_float), vp]),
+        "sq_probe_copy": (i, [vp, vp, C.c_size_t, i, p(d), vp]),
         "sq_coeffs_shape": (i, [vp, p(i), p(i), p(i)]),
         "sq_coeffs_destroy": (None, [vp]),
         "sq_coeffs_set_subcell": (i, [vp, i]),
@@ -341,6 +345,32 @@ def sq_profile_class_name(k: int) -> str:
     return load_library().sq_profile_class_name(int(k)).decode()
 
 
+def sq_launch_count() -> int:
+    """Kernel launches of the single-solve path since the library was loaded."""
+    return int(load_library().sq_launch_count())
+
+
+def sq_probe_fma(precision: int, stream=None):
+    """(TFLOP/s, ms) of the FMA throughput probe: precision 0 = FP64, 1 = FP32."""
+    tf, ms = C.c_double(0.0), C.c_float(0.0)
+    _check(load_library().sq_probe_fma(int(precision), C.byref(tf), C.byref(ms), _stream(stream)), "sq_probe_fma")
+    return tf.value, ms.value
+
+
+def sq_probe_copy(src, dst, reps: int, stream=None) -> float:
+    """GB/s (read + write) of dst <- src repeated `reps` times; src and dst are
+    CUDA tensors of the same number of bytes (a multiple of 16)."""
+    if not (src.is_cuda and dst.is_cuda and src.is_contiguous() and dst.is_contiguous()):
+        raise ValueError("expected contiguous CUDA tensors")
+    nbytes = src.numel() * src.element_size()
+    if dst.numel() * dst.element_size() != nbytes:
+        raise ValueError("src and dst differ in size")
+    g = C.c_double(0.0)
+    _check(load_library().sq_probe_copy(C.c_void_p(src.data_ptr()), C.c_void_p(dst.data_ptr()), nbytes, int(reps),
+                                        C.byref(g), _stream(stream)), "sq_probe_copy")
+    return g.value
+
+
 def sq_coeffs_shape(c: Coeffs):
     L, n, N = C.c_int(), C.c_int(), C.c_int()
     _check(load_library().sq_coeffs_shape(c, C.byref(L), C.byref(n), C.byref(N)), "sq_coeffs_shape")
@@ -409,11 +439,12 @@ def sq_workspace_create(N, precision) -> Workspace:
 
 def sq_pcg_solve(c, pc, w, dir, tol, max_iter, precision, x0, psi, stream=None) -> dict:
     """Solves into psi (float64 CUDA tensor, N^3); returns the solve info.
-    SQ_ENOCONV is reported in info['status'], other errors raise."""
+    SQ_ENOCONV and SQ_ETIMEOUT (a bounded device wait gave up; the solve still
+    completed) are reported in info['status'], other errors raise."""
     info = SolveInfo()
     st = load_library().sq_pcg_solve(c, pc, w, int(dir), float(tol), int(max_iter), int(precision), _ptr(x0),
                                      _ptr(psi), C.byref(info), _stream(stream))
-    _check(st, "sq_pcg_solve", allow=(SQ_ENOCONV,))
+    _check(st, "sq_pcg_solve", allow=(SQ_ENOCONV, SQ_ETIMEOUT))
     return {k: getattr(info, k) for k, _ in SolveInfo._fields_}
 
 

@@ -148,7 +148,7 @@ def test_options_ranges_and_defaults(sq):
             sq.sq_set_option(sq.SQ_OPT_STENCIL_ROWS, v)
         for v in range(2, 8):
             sq.sq_set_option(sq.SQ_OPT_INNER_TOL_EXP, v)
-        for key in (0, 4, 99):
+        for key in (0, 5, 99):
             _einval(sq, sq.sq_set_option, key, 1)
     finally:  # the documented defaults
         sq.sq_set_option(sq.SQ_OPT_STRIDED_TWO_STAGE, 1)
@@ -172,3 +172,26 @@ def test_status_strings(sq):
     names = [sq.sq_strerror(c) for c in codes]
     assert all(names) and len(set(names)) == len(names)
     assert sq.sq_strerror(99) and sq.sq_strerror(99) not in names[1:]
+
+
+@pytest.mark.parametrize("a_lo,a_hi", [(float("inf"), 10.0), (1.0, float("inf")), (float("nan"), 1.0), (0.0, 1.0),
+                                       (1.0, -2.0)])
+def test_noalloc_rejects_bad_coefficients(sq, a_lo, a_hi):
+    """The allocation-free A_hom checks its coefficients like sq_build_coeffs
+    (finite and positive) before it looks at the device. The pointers are
+    never dereferenced on a rejected call, so placeholders stand in for them."""
+    import ctypes as C
+
+    lib = sq.load_library()
+    ptr = C.c_void_p(256)
+    st = lib.sq_homogenized_matrix_noalloc(4, 4, ptr, C.c_double(a_lo), C.c_double(a_hi), ptr, ptr, ptr, ptr,
+                                           C.c_void_p(0))
+    assert st == sq.SQ_EINVAL
+
+
+def test_wait_polls_option_range(sq):
+    """SQ_OPT_WAIT_POLLS accepts 0 .. 2^24 and restores its default."""
+    for bad in (-1, (1 << 24) + 1):
+        _einval(sq, sq.sq_set_option, sq.SQ_OPT_WAIT_POLLS, bad)
+    for ok in (0, 1, 1 << 24, 1 << 22):
+        sq.sq_set_option(sq.SQ_OPT_WAIT_POLLS, ok)

@@ -501,3 +501,63 @@ def test_inner_tolerance_option(sq):
             assert info["status"] == sq.SQ_OK and info["relres_true"] <= 1e-10
     finally:
         sq.sq_set_option(sq.SQ_OPT_INNER_TOL_EXP, 5)
+
+
+def test_bounded_staging_wait_gives_up_cleanly(sq):
+    """Failure detection without a GPU fault: SQ_OPT_WAIT_POLLS = 0 makes the
+    FP32 pass E give up on its bulk-copy barrier at once. The kernel falls
+    back to global-memory reads, so the solve still reaches the oracle's
+    corrector with zero mean and complete info, and reports SQ_ETIMEOUT; the
+    next solve with the default limit is clean."""
+    re = problem.realization(8, 8, 4, 1.0, 100.0)           # N = 64: two-stage x3 tiles, staged pass E
+    c = sq.sq_build_coeffs(8, 8, 4, 0.5, 1.0, 100.0)
+    ref = pcg.tight_solve(re.A, re.b[1], re.N)[0]
+    try:
+        sq.sq_set_option(sq.SQ_OPT_WAIT_POLLS, 0)
+        psi, info = _solve(sq, c, re.N, 1, 8, 1e-10, precision=sq.SQ_FP32_REFINE)
+    finally:
+        sq.sq_set_option(sq.SQ_OPT_WAIT_POLLS, 1 << 22)
+    x = _host(psi)
+    assert info["status"] == sq.SQ_ETIMEOUT
+    assert info["relres_true"] <= 1e-10 and info["iters"] > 0 and info["outer_steps"] >= 1
+    assert abs(x.mean()) <= 1e-14 * np.abs(x).max()
+    assert np.linalg.norm(x - ref) / np.linalg.norm(ref) <= 1e-6
+    psi2, info2 = _solve(sq, c, re.N, 1, 8, 1e-10, precision=sq.SQ_FP32_REFINE)
+    assert info2["status"] == sq.SQ_OK and info2["relres_true"] <= 1e-10
+    assert np.linalg.norm(_host(psi2) - ref) / np.linalg.norm(ref) <= 1e-6
+
+
+@pytest.mark.slow
+def test_full_size_n256_elementwise_against_oracle(sq):
+    """The timed configuration solved tight and compared element by element:
+    L = 32, n = 8 (N = 256), Bernoulli(1/2) on {1,100}, seed 0, the rank-8
+    preconditioner, FP64 PCG to 1e-12 for all three correctors, against the
+    oracle's tight solves (run in spawned CPU processes while the GPU works):
+    psi within 1e-9 (rel. L2) and A_hom within 1e-10 of its largest entry."""
+    import multiprocessing
+    import os
+    from concurrent.futures import ProcessPoolExecutor
+
+    from tests import oracle_jobs
+
+    L, n, seed = 32, 8, 0
+    N = L * n
+    workers = max(1, len(os.sched_getaffinity(0)) // 3)
+    with ProcessPoolExecutor(max_workers=3, mp_context=multiprocessing.get_context("spawn")) as ex:
+        futs = [ex.submit(oracle_jobs.tight_corrector, L, n, seed, 1.0, 100.0, i, workers) for i in range(3)]
+        c = sq.sq_build_coeffs(L, n, seed, 0.5, 1.0, 100.0)
+        psis, infos = [], []
+        for i in range(3):
+            psi, info = _solve(sq, c, N, i, 8, 1e-12)
+            psis.append(psi)
+            infos.append(info)
+        Ah, _ = sq.sq_homogenized_matrix(c, *psis, energy=False)
+        refs = [f.result()[0] for f in futs]
+    for info in infos:
+        assert info["status"] == sq.SQ_OK and info["relres_true"] <= 1e-12
+    for i in range(3):
+        x = _host(psis[i])
+        assert np.linalg.norm(x - refs[i]) / np.linalg.norm(refs[i]) <= 1e-9, i
+    a_edges = assembly.edge_coefficients(rng.cell_values(rng.cell_phases_vec(L, seed), 1.0, 100.0), n)
+    Ao = homogenized.ahom_edge(a_edges, [r.reshape(N, N, N) for r in refs])
+    assert np.abs(Ah - Ao).max() <= 1e-10 * np.abs(Ao).max()

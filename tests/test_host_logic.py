@@ -95,13 +95,17 @@ def test_bench_host_cpu_description(tmp_path):
     assert c["cpu_model"] and c["cores_available"] >= 1
 
 
-def test_bench_batch_leg_on_fakes():
-    """run_batch end to end against stand-ins for the library and torch (no
-    GPU): the 768 descriptors, their grid sizes and the algorithmic traffic."""
+def test_bench_batch_leg_on_fakes(monkeypatch):
+    """run_batch end to end against stand-ins for the library, the batch
+    autotuner and torch (no GPU): the 768 descriptors, their grid sizes, the
+    tuned tiles handed to the batch and the algorithmic traffic."""
     import types
 
     import bench
-    from paper_2007_06524_gb300 import workloads
+    from paper_2007_06524_gb300 import autotune, workloads
+
+    tuned = [(32, 8, 8), (48, 8, 12), (64, 16, 16), (96, 16, 24)]
+    monkeypatch.setattr(autotune, "tune_batch", lambda torch, descs, pl, tol: (tuned, {"32:8x8": 1.0}))
 
     class Buf:
         def __init__(self, n):
@@ -125,14 +129,16 @@ def test_bench_batch_leg_on_fakes():
         SQ_OK=0,
         sq_build_coeffs=lambda L, n, seed, p, lo, hi: ("coeffs", L, n, seed),
         sq_precond_setup=lambda N, r: ("precond", N, r),
-        sq_batch_create=lambda descs, pl: calls.setdefault("batch", (list(descs), list(pl))),
+        sq_batch_create=lambda descs, pl, tiles=None: calls.setdefault(tiles is not None, (list(descs), list(pl),
+                                                                                          tiles)),
         sq_pcg_solve_batched=lambda b, tol, mi: [{"iters": 20, "status": 0} for _ in b[0]],
     )
     fake_torch = types.SimpleNamespace(
         float64="f64", empty=lambda n, dtype=None, device=None: Buf(n),
         cuda=types.SimpleNamespace(synchronize=lambda: None, Event=Event))
     out = bench.run_batch(fake_sq, fake_torch, stream=None)
-    descs, pl = calls["batch"]
+    descs, pl, tiles = calls[True]
+    assert tiles == tuned and calls[False][2] is None and out["tiles"] == [list(t) for t in tuned]
     Ns = [workloads.BATCH_MIXED["Ls"][workloads.batch_L_index(s)] * 4 for s in range(256) for _ in range(3)]
     assert out["solves"] == 768 and [p[1] for p in pl] == Ns
     assert [d[2].numel() for d in descs] == [N ** 3 for N in Ns]
@@ -140,7 +146,8 @@ def test_bench_batch_leg_on_fakes():
     want = sum(17 * 4 * N ** 3 * 20 for N in Ns)
     assert out["algorithmic_bytes"] == want
     assert abs(out["algorithmic_GBps"] - want / 0.25 / 1e9) <= 0.05
-    assert 0 < out["algorithmic_frac_of_hbm"] < 10 and "L2" in out["algorithmic_note"]
+    assert 0 < out["hbm_frac"] < 10 and "L2" in out["algorithmic_note"]
+    assert out["working_set_GB"] == round(sum(20 * N ** 3 for N in Ns) / 1e9, 2)
 
 
 def test_bench_roofline_selection():
@@ -160,7 +167,12 @@ def test_bench_roofline_selection():
     flops = bench._algorithmic(N, 8, R)["dht_x1_scale"][1]
     assert roof["kernel"] == "dht_x1_scale" and roof["bound"] == "alu" and roof["unit"] == "TFLOP/s"
     assert abs(roof["achieved"] - flops / 1103e-6 / 1e12) <= 1e-3
-    assert abs(roof["frac"] - roof["achieved"] / 1.25) <= 1e-3
+    assert abs(roof["frac"] - roof["achieved"] / bench.FP64_NOMINAL_TFLOPS) <= 1e-3
+    # a measured peak replaces the nominal one
+    pk = dict(bench.default_peaks(), fp64_tflops=1.0, fp64_src="measured")
+    _, roof_m = bench.kernel_table(work, prof, N, 8, R, t_ms=400.0, peaks=pk)
+    assert roof_m["peak"] == 1.0 and roof_m["peak_src"] == "measured"
+    assert abs(roof_m["frac"] - roof["achieved"] / 1.0) <= 1e-3 and "hbm_frac" in roof_m
     assert roof["traffic"] == bench.PROFILED_TRAFFIC[("dht_x1_scale", 8)]
     assert kernels["dht_x2"]["us_per_work_launch"] == 481.0
     # FP32: pass E dominates and is HBM-bound

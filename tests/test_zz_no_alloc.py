@@ -64,3 +64,15 @@ def test_noalloc_rejects_oversized_grid(sq):
     with pytest.raises(sq.SqError) as e:
         sq.sq_homogenized_matrix_noalloc(128, 8, phase, 1.0, 10.0, f, f, f, out)   # N = 1024 > 512
     assert e.value.status == sq.SQ_EINVAL
+
+
+@pytest.mark.parametrize("a_lo,a_hi", [(float("inf"), 10.0), (1.0, float("inf"))])
+def test_noalloc_rejects_infinite_coefficient(sq, a_lo, a_hi):
+    import torch
+
+    phase = torch.zeros(64, dtype=torch.uint8, device="cuda")
+    f = torch.zeros(16 ** 3, dtype=torch.float64, device="cuda")
+    out = torch.zeros(18, dtype=torch.float64, device="cuda")
+    with pytest.raises(sq.SqError) as e:
+        sq.sq_homogenized_matrix_noalloc(4, 4, phase, a_lo, a_hi, f, f, f, out)
+    assert e.value.status == sq.SQ_EINVAL
