@@ -65,7 +65,8 @@ def measure_peaks(sq, torch):
     FP64 and FP32 fused multiply-add throughput (eight independent chains per
     thread, a full grid) and a copy of 2 x 2 GiB (HBM) and of 2 x 16 MiB (L2)
     buffers. The HBM peak stays the driver's measurement where present; the
-    probe's copy figure is reported beside it."""
+    probe's copy figure is reported beside it (the fallback is used where
+    that file is absent)."""
     pk = default_peaks()
     fp64, _ = sq.sq_probe_fma(0)
     fp32, _ = sq.sq_probe_fma(1)
@@ -79,11 +80,8 @@ def measure_peaks(sq, torch):
     small = 16 << 20
     a = torch.empty(small // 4, dtype=torch.float32, device="cuda")
     b = torch.empty_like(a)
-    pk["copy_l2_gbs"] = round(sq.sq_probe_copy(a, b, 200), 1)
+    pk["copy_l2_gbs"] = round(sq.sq_probe_copy(a, b, 500), 1)
     del a, b
-    if not os.path.exists(os.path.join(ROOT, "MEASURED_PEAKS.json")):
-        pk["hbm_gbs"] = pk["copy_hbm_gbs"]
-        pk["hbm_src"] = "measured: copy probe of this run (sq_probe_copy, 2 x 2 GiB)"
     return pk
 
 
@@ -179,18 +177,22 @@ def _dist():
     return ws, rank, local
 
 
-def _algorithmic(N, elem, rank_r):
+def _algorithmic(N, elem, rank_r, table=None):
     """Per-launch algorithmic bytes and flops of each kernel class (one PCG iteration).
 
     bytes: the fields each kernel must read and write once (N^3 elements of
     `elem` bytes); flops: one real 1D Hartley pass = 2.5 log2 N + 3 per point
     (half-length complex FFT convention + the Hartley combine). Pass C does two
     transforms with no combine (the scaling is applied to the complex
-    spectrum): 2 x 2.5 log2 N, plus the multiplier (2R, or 4 for the exact
-    1/x) and 6 for the scaling and the r.z sum."""
+    spectrum): 2 x 2.5 log2 N, plus 6 for the scaling and the r.z sum, plus
+    the multiplier where it is evaluated per mode (2R, or 4 for the exact
+    1/x); grids N <= 256 read it from the precomputed table instead
+    (table=None: that default)."""
     n3 = N ** 3
     f = 2.5 * math.log2(N) + 3.0
-    scale = (2 * rank_r + 6) if rank_r else 10
+    if table is None:
+        table = N <= 256
+    scale = 6 if table else ((2 * rank_r + 6) if rank_r else 10)
     return {
         "stencil_matvec": (2 * elem * n3, 15 * n3),
         "dht_x3_in": (4 * elem * n3, (f + 4) * n3),
@@ -204,7 +206,7 @@ def _algorithmic(N, elem, rank_r):
 # N = 256, rank 8): profiles/dht_x1_scale_fp64_n256.md and
 # profiles/dht_x3_pass_e_fp32_n256.md. Part of each kernel's writes is still in
 # L2 when it ends, so traffic can read below the algorithmic bytes.
-PROFILED_TRAFFIC = {("dht_x1_scale", 8): 134.59e6 + 72.85e6, ("dht_x3_out", 4): 201.36e6 + 76.13e6}
+PROFILED_TRAFFIC = {("dht_x3_out", 4): 201.36e6 + 76.13e6}
 
 
 def kernel_table(work, prof, N, elem, R, t_ms, peaks=None):

@@ -161,9 +161,13 @@ void sq_coeffs_destroy(sq_coeffs *c);
  * u_r(k) = w_r^(1/3) exp(-t_r l_k) (Lemma 4.2; the exponential sum
  * sum_r w_r exp(-t_r x) ~ 1/x of the Laplace transform, Eq. 34), R <= 64. For
  * R <= 32 the nodes are geometric and the weights fitted by least squares to
- * the relative error over the discrete spectrum; above, a balanced trapezoid
- * rule. Factors and twiddles are built on the host in FP64 and copied to the
- * current device (synchronous). */
+ * the relative error over the discrete spectrum (a fit counts only if it keeps
+ * every weight positive and is not numerically singular: the triangular
+ * factor of its QR decomposition has a diagonal spread of at most 1e10); the
+ * balanced trapezoid rule is used above R = 32 and wherever no fit beats it.
+ * Factors and twiddles are built on the host in FP64 and copied to the
+ * current device; for N <= 256 the multiplier table of SQ_OPT_MULTIPLIER_TABLE
+ * is built there too (synchronous). */
 int sq_precond_setup(int N, int rank, sq_precond **out);
 /* The exponential-sum nodes t[r] and weights w[r], r < rank (host arrays,
  * either may be NULL; nothing is written for rank 0). SQ_EINVAL for a
@@ -281,8 +285,21 @@ int sq_set_tiles(const sq_tile_config *tiles, int ntiles);
  * gives up, reads them from global memory, flags the solve (SQ_ETIMEOUT) and
  * stops staging; 0 gives up at once. The block still waits (up to 2^24 polls)
  * for its copies in flight before it exits. 0 <= value <= 2^24.
+ * SQ_OPT_MULTIPLIER_TABLE (default 1): preconditioners of grids N <= 256 carry
+ * their multiplier G tabulated on the mirror-reduced modes, (N/2 + 1)^3
+ * values in FP64 and in FP32 (built on the device by sq_precond_setup* from
+ * the same factors, summed in FP64), and the x1 pass reads G from it instead
+ * of summing the canonical terms (or dividing, for the exact diagonal) per
+ * mode; 0 evaluates G on the fly everywhere (batches: as set when they are
+ * created). Results agree to rounding.
  */
-enum sq_option { SQ_OPT_STRIDED_TWO_STAGE = 1, SQ_OPT_STENCIL_ROWS = 2, SQ_OPT_INNER_TOL_EXP = 3, SQ_OPT_WAIT_POLLS = 4 };
+enum sq_option {
+  SQ_OPT_STRIDED_TWO_STAGE = 1,
+  SQ_OPT_STENCIL_ROWS = 2,
+  SQ_OPT_INNER_TOL_EXP = 3,
+  SQ_OPT_WAIT_POLLS = 4,
+  SQ_OPT_MULTIPLIER_TABLE = 5
+};
 int sq_set_option(int key, int value);
 
 /* Plans a batch of `count` solves; precs[k] is the preconditioner (same N) of
@@ -420,7 +437,7 @@ int64_t sq_launch_count(void);
  * work; *tflops = 2 flops per FMA / time, *ms the kernel time (either may be
  * NULL). Allocates 8 bytes per block (stream-ordered) for its guard output.
  * sq_probe_copy: dst = src over `bytes` (device buffers, 16-byte aligned,
- * bytes a multiple of 16), `reps` launches (1..10000); *gbps = 2 bytes reps /
+ * bytes a multiple of 16), `reps` sweeps in one launch (1..10000); *gbps = 2 bytes reps /
  * time (read + write, as a STREAM copy). Buffers far above the L2 size measure
  * HBM; buffers that fit in L2 measure L2. */
 int sq_probe_fma(int precision, double *tflops, float *ms, sq_stream_t stream);

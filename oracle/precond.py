@@ -159,9 +159,13 @@ def lsq_nodes(N: int, R: int, dim: int = 3):
        b in ln(1/lambda_min) - 1 + 5 j/(g-1) (g = 40 for R <= 16, else 20),
        the nodes are t_r = exp(a + (b - a) r/(R-1)) and the weights solve
        min_w || x exp(-x t) w - 1 ||_2 over the sample (numpy lstsq).
-    3. Fits with any w_r <= 0 are discarded (G_R must stay positive); of the
-       rest the one with the smallest largest sampled error is kept (the
-       first in (i, j) order on ties).
+    3. Fits with any w_r <= 0 are discarded (G_R must stay positive), and so
+       are numerically singular ones: the largest |diagonal entry| of the
+       triangular factor of a QR decomposition of the sample matrix above
+       1e10 times the smallest (many terms over a narrow spectrum, where the
+       weights would be rounding noise). Of the rest the one with the
+       smallest largest sampled error is kept (the first in (i, j) order on
+       ties).
     4. The fit replaces the trapezoid rule (:func:`rank_r_nodes`) only if its
        largest error over every distinct eigenvalue is smaller; for R > 32,
        or with fewer than 2R sample points, the trapezoid rule is returned.
@@ -182,6 +186,9 @@ def lsq_nodes(N: int, R: int, dim: int = 3):
             b = math.log(1.0 / lam_min) - 1.0 + 5.0 * j / (g - 1)
             t = np.exp(a + (b - a) * np.arange(R) / (R - 1))
             E = x[:, None] * np.exp(-np.outer(x, t))
+            d = np.abs(np.diag(np.linalg.qr(E, mode="r")))
+            if not d.min() > 0.0 or d.max() > 1e10 * d.min():
+                continue
             w = np.linalg.lstsq(E, np.ones(len(x)), rcond=None)[0]
             if not np.all(w > 0.0):
                 continue

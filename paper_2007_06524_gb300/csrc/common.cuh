@@ -378,7 +378,16 @@ struct SpectralDev {
   // (u(k) = u(N - k)): G is then diagonal in the separable Hartley basis.
   const void *u;
   double scale;      // 1 / (64 N^3) for the exact diagonal
+  // The multiplier itself, tabulated (T): G(m1, m2, m3) at
+  // gtab[(m1 H + m2) H + m3], H = N/2 + 1, m = min(k, N - k) per axis (G is
+  // even in each index), G(0,0,0) = 0, scale folded in as above. nullptr:
+  // pass C evaluates G from lam or u on the fly.
+  const void *gtab = nullptr;
 };
+// Grids up to this size carry the multiplier table (8.6 MB FP32 + 17 MB FP64
+// at N = 256, resident in L2 while pass C reads it).
+constexpr int kGtabMaxN = 256;
+__host__ __device__ constexpr int mirror_index(int k, int N) { return k <= N - k ? k : N - k; }
 enum DhtPass : int { PASS_A_RESID = 0, PASS_A_PLAIN = 1, PASS_B = 2, PASS_C = 3, PASS_E_PCG = 4, PASS_E_PLAIN = 5 };
 // One pencil pass of the 3D Hartley transform pipeline (see dht.cu).
 template <typename T>
@@ -395,6 +404,8 @@ int set_stencil_planes_override(int N, int zc);
 int set_stencil_rows(int rpt);  // FP32 operator rows per thread: 0 auto, 1, 2, 4
 int set_stencil_rows_override(int N, int rpt);  // per grid size; 0 = the process-wide choice
 int set_strided_fast(int on);  // 0: generic Stockham tiles for every pass
+int set_use_gtab(int on);      // 0: pass C evaluates the multiplier on the fly everywhere
+int use_gtab();
 
 // solver.cu: read-only views of the opaque handles (used by batch.cu)
 int coeffs_view(const sq_coeffs *c, CellsDev *out);

@@ -146,12 +146,14 @@ static cudaError_t launch_s2(const DhtArgs<float> &a, int grid, cudaStream_t s) 
   return cudaGetLastError();
 }
 
-// Rank specialisations of pass C: exact (0), rank 8 in registers, else runtime.
+// Specialisations of pass C: the tabulated multiplier (-2, where the
+// preconditioner carries one), exact (0), rank 8 in registers, else runtime.
 template <int AXIS, int R0, int R1, int P, bool SCALE>
 static cudaError_t launch_s2_rank(const DhtArgs<float> &a, int grid, cudaStream_t s) {
   if constexpr (!SCALE) {
     return launch_s2<AXIS, R0, R1, P, SCALE, -1>(a, grid, s);
   } else {
+    if (a.sp.gtab) return launch_s2<AXIS, R0, R1, P, SCALE, -2>(a, grid, s);
     if (a.sp.rank == 0) return launch_s2<AXIS, R0, R1, P, SCALE, 0>(a, grid, s);
     if (a.sp.rank == 8) return launch_s2<AXIS, R0, R1, P, SCALE, 8>(a, grid, s);
     return launch_s2<AXIS, R0, R1, P, SCALE, -1>(a, grid, s);
@@ -336,6 +338,14 @@ static cudaError_t launch_fast(int pass, const DhtArgs<T> &a, int grid, cudaStre
 
 static int g_pencils_override[kMaxN + 1] = {0};  // FP32 passes, per N (0 = default)
 static int g_strided_fast = 1;                    // two-stage strided passes where N allows
+static int g_use_gtab = 1;                        // pass C reads the multiplier table where there is one
+
+int set_use_gtab(int on) {
+  if (on < 0 || on > 1) return 1;
+  g_use_gtab = on;
+  return 0;
+}
+int use_gtab() { return g_use_gtab; }
 
 int set_strided_fast(int on) {
   if (on < 0 || on > 2) return 1;
@@ -390,6 +400,7 @@ cudaError_t launch_dht_pass(int pass, const SpectralDev &sp, const T *in, T *out
   a.logP = logP;
   a.stage = 0;
   a.ntiles = (int)(((long long)N * N) / (2 * P));
+  if (!g_use_gtab) a.sp.gtab = nullptr;
   const int grid = a.ntiles < 8192 ? a.ntiles : 8192;
   const size_t smem = dht_smem_bytes_t<T>(N, P, pass == PASS_C ? sp.rank : 0);
   if (g_strided_fast) {

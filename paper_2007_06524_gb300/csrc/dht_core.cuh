@@ -301,7 +301,7 @@ __device__ __forceinline__ void dht_tile(const SpectralDev &sp, const DhtTile<T>
       const size_t g = base + (size_t)j * stride + 2 * p;
       buf0[j * SP + p] = reinterpret_cast<const C *>(a.in)[g >> 1];
     }
-    if (SCALE && R > 0) {
+    if (SCALE && R > 0 && !sp.gtab) {
       // x2 factors at uf + R N, x3 factors at uf + 2 R N (see SpectralDev)
       const T *u2 = uf + (size_t)R * N, *u3 = uf + 2 * (size_t)R * N;
       for (int e = tid; e < R * 2 * P; e += kThreads) {
@@ -323,7 +323,12 @@ __device__ __forceinline__ void dht_tile(const SpectralDev &sp, const DhtTile<T>
       if (SCALE) {  // pass C: the Fourier-domain scaling described at s2_combine
         const int k3a = c0 + 2 * p, k3b = k3a + 1;
         T ga, gb;
-        if (R == 0) {
+        if (sp.gtab) {  // tabulated multiplier (k <= N/2 here)
+          const int H = (N >> 1) + 1;
+          const T *row = reinterpret_cast<const T *>(sp.gtab) + ((size_t)k * H + mirror_index(k2, N)) * H;
+          ga = row[mirror_index(k3a, N)];
+          gb = row[mirror_index(k3b, N)];
+        } else if (R == 0) {
           const T l12 = lam[k] + lam[k2];
           const T g1 = l12 + lam[k3a], g2 = l12 + lam[k3b];
           ga = (g1 > (T)0) ? gscale / g1 : (T)0;
@@ -443,6 +448,27 @@ __device__ __forceinline__ void s2_stage1(const C *__restrict__ gsrc, size_t bas
   __syncthreads();
 }
 
+// Stage 1 from a dense shared-memory copy of the tile (row j of the tile's P
+// complex values at raw + j P, landed there by bulk copies): the reads of a
+// warp cover two whole rows, conflict-free; the results go to the padded
+// layout of sm as in s2_stage1.
+template <typename T, typename C, int R0, int R1, int P>
+__device__ __forceinline__ void s2_stage1_raw(const C *raw, C *sm) {
+  constexpr int SP = P + 1, LP = ilog2c(P);
+  static_assert(R1 * P <= kThreads, "one stage-1 butterfly per thread");
+  const int t = threadIdx.x;
+  if (t < R1 * P) {
+    const int p = t & (P - 1), b = t >> LP;
+    C u[R0];
+#pragma unroll
+    for (int q = 0; q < R0; ++q) u[q] = raw[(b + q * R1) * P + p];
+    dft<T, C, R0>(u);
+#pragma unroll
+    for (int q = 0; q < R0; ++q) sm[(b * R0 + q) * SP + p] = u[q];
+  }
+  __syncthreads();
+}
+
 // Hartley value pair of output m from X_m and its mirror X_{N-m}.
 template <typename C>
 __device__ __forceinline__ C hartley_pair(const C X, const C Y) {
@@ -471,7 +497,8 @@ __device__ __forceinline__ void s2_stage2(C *sm, const C *__restrict__ tw) {
 
 // Multiplier G at (k, k2, k3a) and (k, k2, k3a + 1), k3a = c0 + 2p: exact
 // (RR = 0), rank RR with the column factors va/vb of this thread's pencil in
-// registers (RR > 0), or a runtime rank (RR < 0, factors read from vtab).
+// registers (RR > 0), a runtime rank (RR = -1, factors read from vtab), or
+// read from the tabulated multiplier (RR = -2, sp.gtab; k <= N/2 here).
 template <typename T, int N, int P, int RR>
 __device__ __forceinline__ void s2_multiplier(const SpectralDev &sp, int k, int k2, int c0, int p, const T *vtab,
                                               const T (&va)[RR > 0 ? RR : 1], const T (&vb)[RR > 0 ? RR : 1],
@@ -479,7 +506,12 @@ __device__ __forceinline__ void s2_multiplier(const SpectralDev &sp, int k, int 
   const T *lam = reinterpret_cast<const T *>(sp.lam);
   const T *uf = reinterpret_cast<const T *>(sp.u);
   const int k3a = c0 + 2 * p;
-  if constexpr (RR == 0) {
+  if constexpr (RR == -2) {
+    constexpr int H = N / 2 + 1;
+    const T *row = reinterpret_cast<const T *>(sp.gtab) + ((size_t)k * H + mirror_index(k2, N)) * H;
+    ga = row[mirror_index(k3a, N)];
+    gb = row[mirror_index(k3a + 1, N)];
+  } else if constexpr (RR == 0) {
     const T gscale = (T)sp.scale;
     const T l12 = lam[k] + lam[k2];
     const T g1 = l12 + lam[k3a], g2 = l12 + lam[k3a + 1];
@@ -576,7 +608,7 @@ __device__ __forceinline__ void dht_tile_s2(const SpectralDev &sp, const DhtTile
   const size_t base = (AXIS == 2) ? (size_t)line * NN + c0 : (size_t)line * N + c0;
   const int k2 = line;
   __syncthreads();
-  if (SCALE && RR != 0) {
+  if (SCALE && RR != 0 && RR != -2) {
     const T *uf = reinterpret_cast<const T *>(sp.u);
     const T *u2 = uf + (size_t)sp.rank * N, *u3 = uf + 2 * (size_t)sp.rank * N;  // x2, x3 factors
     for (int e = threadIdx.x; e < sp.rank * 2 * P; e += kThreads) {

@@ -8,7 +8,7 @@
 //    FP32. Eight chains per thread and a full SM hide the FMA latency, so the
 //    rate is the issue rate of the FMA pipe at the current clock.
 //  * sq_probe_copy: dst <- src over `bytes` (16-byte vectors, grid-stride),
-//    repeated `reps` times; the rate counts 2 * bytes * reps (read + write),
+//    `reps` sweeps inside one launch; the rate counts 2 * bytes * reps (read + write),
 //    the convention of a STREAM copy. Buffers much larger than L2 measure
 //    HBM, buffers that fit in L2 measure L2 after the first pass.
 #include <cuda_runtime.h>
@@ -43,9 +43,10 @@ __global__ void __launch_bounds__(kProbeThreads) k_fma_probe(T *out, int iters, 
 }
 
 __global__ void __launch_bounds__(kProbeThreads) k_copy_probe(const float4 *__restrict__ src,
-                                                              float4 *__restrict__ dst, size_t n) {
+                                                              float4 *__restrict__ dst, size_t n, int reps) {
   const size_t stride = (size_t)gridDim.x * blockDim.x;
-  for (size_t i = (size_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += stride) dst[i] = src[i];
+  for (int k = 0; k < reps; ++k)
+    for (size_t i = (size_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += stride) dst[i] = src[i];
 }
 
 template <typename T>
@@ -107,12 +108,12 @@ extern "C" int sq_probe_copy(const void *src, void *dst, size_t bytes, int reps,
   const int blocks = sms * (per_sm > 0 ? per_sm : 1);
   const float4 *a = reinterpret_cast<const float4 *>(src);
   float4 *b = reinterpret_cast<float4 *>(dst);
-  k_copy_probe<<<blocks, kProbeThreads, 0, s>>>(a, b, n);  // warm-up (and fills L2 for small buffers)
+  k_copy_probe<<<blocks, kProbeThreads, 0, s>>>(a, b, n, 1);  // warm-up (and fills L2 for small buffers)
   cudaEvent_t e0, e1;
   cudaEventCreate(&e0);
   cudaEventCreate(&e1);
   cudaEventRecord(e0, s);
-  for (int k = 0; k < reps; ++k) k_copy_probe<<<blocks, kProbeThreads, 0, s>>>(a, b, n);
+  k_copy_probe<<<blocks, kProbeThreads, 0, s>>>(a, b, n, reps);  // one launch, `reps` sweeps
   cudaEventRecord(e1, s);
   cudaError_t err = cudaEventSynchronize(e1);
   float ms = 0.f;

@@ -233,6 +233,10 @@ void sinc_nodes(int N, int R, std::vector<double> &t, std::vector<double> &w, in
 }
 
 // Least-squares solve min ||E w - 1|| (M x R, column-major copy) by Householder QR.
+// Fails (returns false) when the fit is numerically singular: the ratio of the
+// largest to the smallest |diagonal entry| of the triangular factor above 1e10
+// (exponential fits over a narrow spectrum with many terms), where the weights
+// would be rounding noise.
 bool lsq_ones(std::vector<double> E, int M, int R, std::vector<double> &w) {
   if (R < 1 || M < 2 * R) return false;  // too few distinct spectral values for a fit
   std::vector<double> rhs(M, 1.0);
@@ -259,6 +263,13 @@ bool lsq_ones(std::vector<double> E, int M, int R, std::vector<double> &w) {
     d = 2.0 * d / vv;
     for (int i = k; i < M; ++i) rhs[i] -= d * v[i - k];
   }
+  double dmax = 0.0, dmin = std::numeric_limits<double>::infinity();
+  for (int k = 0; k < R; ++k) {
+    const double d = std::fabs(E[(size_t)k * M + k]);
+    dmax = std::max(dmax, d);
+    dmin = std::min(dmin, d);
+  }
+  if (!(dmin > 0.0) || dmax > 1e10 * dmin) return false;
   w.assign(R, 0.0);
   for (int k = R - 1; k >= 0; --k) {
     double s = rhs[k];
@@ -285,7 +296,8 @@ double exp_sum_error(const std::vector<double> &xs, const std::vector<double> &t
 // weights w_r by least squares on the relative error x G_R(x) - 1 over a
 // log-uniform sample of the discrete spectrum {l_i + l_j + l_k > 0} (dim 3;
 // {l_i + l_j > 0} for dim 2); (a, b) is chosen on a grid to minimise the
-// largest sampled error with all w_r > 0. The result is kept only if its
+// largest sampled error with all w_r > 0 among the fits that are not
+// numerically singular (see lsq_ones). The result is kept only if its
 // largest error over the whole spectrum is below that of the balanced
 // trapezoid rule (which is used otherwise, and for R > 32).
 void rank_r_nodes(int N, int R, std::vector<double> &t, std::vector<double> &w, int dim = 3) {
@@ -906,6 +918,30 @@ namespace sq {
 // factors f (3 x R x N, axis a of term r at f + (a R + r) N; unscaled, so
 // that G(k) = sum_r f1_r(k1) f2_r(k2) f3_r(k3)); R = 0 is the exact diagonal.
 // t, w: the exponential-sum nodes and weights when the factors come from one.
+// The multiplier table of pass C (SpectralDev::gtab): G at every mirror-reduced
+// mode (m1, m2, m3), m <= N/2, summed in FP64 from the scaled factors (or
+// scale / (l1 + l2 + l3) for the exact diagonal), stored in FP64 and rounded
+// to FP32; G(0,0,0) = 0.
+__global__ void k_build_gtab(int N, int R, const double *lam, const double *u, double scale, double *g64,
+                             float *g32) {
+  const int H = N / 2 + 1;
+  const size_t n = (size_t)H * H * H;
+  for (size_t i = (size_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (size_t)gridDim.x * blockDim.x) {
+    const int m3 = (int)(i % H), m2 = (int)((i / H) % H), m1 = (int)(i / ((size_t)H * H));
+    double g = 0.0;
+    if (m1 != 0 || m2 != 0 || m3 != 0) {
+      if (R == 0) {
+        g = scale / (lam[m1] + lam[m2] + lam[m3]);
+      } else {
+        for (int r = 0; r < R; ++r)
+          g = fma(u[(size_t)r * N + m1], u[(size_t)(R + r) * N + m2] * u[(size_t)(2 * R + r) * N + m3], g);
+      }
+    }
+    g64[i] = g;
+    g32[i] = (float)g;
+  }
+}
+
 int precond_create(int N, int R, const double *f, const std::vector<double> &t, const std::vector<double> &w,
                    sq_precond **out) {
   if (!out) return SQ_EINVAL;
@@ -937,7 +973,11 @@ int precond_create(int N, int R, const double *f, const std::vector<double> &t, 
   const size_t b_tw64 = tw64.size() * 8, b_lam64 = lam64.size() * 8, b_u64 = u64.size() * 8;
   const size_t b_tw32 = tw32.size() * 4, b_lam32 = lam32.size() * 4, b_u32 = u32.size() * 4;
   auto al = [](size_t b) { return (b + 255) & ~(size_t)255; };
-  const size_t total = al(b_tw64) + al(b_lam64) + al(b_u64) + al(b_tw32) + al(b_lam32) + al(b_u32);
+  const size_t H = (size_t)N / 2 + 1;
+  const bool with_tab = N <= kGtabMaxN;
+  const size_t b_g64 = with_tab ? H * H * H * 8 : 0, b_g32 = with_tab ? H * H * H * 4 : 0;
+  const size_t total =
+      al(b_tw64) + al(b_lam64) + al(b_u64) + al(b_tw32) + al(b_lam32) + al(b_u32) + al(b_g64) + al(b_g32);
   if (cudaMalloc(&pc->d_mem, total) != cudaSuccess) {
     delete pc;
     return SQ_ENOMEM;
@@ -949,6 +989,8 @@ int precond_create(int N, int R, const double *f, const std::vector<double> &t, 
   char *p_tw32 = p_u64 + al(b_u64);
   char *p_lam32 = p_tw32 + al(b_tw32);
   char *p_u32 = p_lam32 + al(b_lam32);
+  char *p_g64 = p_u32 + al(b_u32);
+  char *p_g32 = p_g64 + al(b_g64);
   if (cudaMemcpy(p_tw64, tw64.data(), b_tw64, cudaMemcpyHostToDevice) != cudaSuccess ||
       cudaMemcpy(p_lam64, lam64.data(), b_lam64, cudaMemcpyHostToDevice) != cudaSuccess ||
       cudaMemcpy(p_u64, u64.data(), b_u64, cudaMemcpyHostToDevice) != cudaSuccess ||
@@ -964,14 +1006,25 @@ int precond_create(int N, int R, const double *f, const std::vector<double> &t, 
   sp.rank = R;
   sp.nst = radix_plan(N, sp.radix);
   sp.scale = 1.0 / (64.0 * (double)N * N * N);
+  if (with_tab) {
+    k_build_gtab<<<1024, 256>>>(N, R, reinterpret_cast<const double *>(p_lam64),
+                                reinterpret_cast<const double *>(p_u64), sp.scale, reinterpret_cast<double *>(p_g64),
+                                reinterpret_cast<float *>(p_g32));
+    if (cudaGetLastError() != cudaSuccess || cudaDeviceSynchronize() != cudaSuccess) {
+      sq_precond_destroy(pc);
+      return SQ_ECUDA;
+    }
+  }
   pc->sp64 = sp;
   pc->sp64.tw = p_tw64;
   pc->sp64.lam = p_lam64;
   pc->sp64.u = p_u64;
+  pc->sp64.gtab = with_tab ? p_g64 : nullptr;
   pc->sp32 = sp;
   pc->sp32.tw = p_tw32;
   pc->sp32.lam = p_lam32;
   pc->sp32.u = p_u32;
+  pc->sp32.gtab = with_tab ? p_g32 : nullptr;
   *out = pc;
   return SQ_OK;
 }
@@ -1062,6 +1115,7 @@ int sq_set_option(int key, int value) {
   if (key == SQ_OPT_STENCIL_ROWS) return set_stencil_rows(value) == 0 ? SQ_OK : SQ_EINVAL;
   if (key == SQ_OPT_INNER_TOL_EXP) return set_inner_tol_exp(value) == 0 ? SQ_OK : SQ_EINVAL;
   if (key == SQ_OPT_WAIT_POLLS) return set_stage_wait_polls(value) == 0 ? SQ_OK : SQ_EINVAL;
+  if (key == SQ_OPT_MULTIPLIER_TABLE) return set_use_gtab(value) == 0 ? SQ_OK : SQ_EINVAL;
   return SQ_EINVAL;
 }
 

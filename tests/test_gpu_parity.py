@@ -163,7 +163,7 @@ def _core(sq, pc, N, rank):
 
 
 @pytest.mark.parametrize("N,rank", [(8, 4), (16, 6), (32, 8), (64, 16), (256, 8), (256, 4), (256, 16), (48, 4),
-                                    (96, 8), (512, 8), (64, 32), (16, 40)])
+                                    (96, 8), (512, 8), (64, 32), (16, 40), (16, 16), (24, 32), (12, 16)])
 def test_rank_r_factors_match_oracle_construction(sq, N, rank):
     """The library's nodes and weights against the oracle's independent
     construction: same geometric nodes, and an exponential sum that agrees
@@ -561,3 +561,28 @@ def test_full_size_n256_elementwise_against_oracle(sq):
     a_edges = assembly.edge_coefficients(rng.cell_values(rng.cell_phases_vec(L, seed), 1.0, 100.0), n)
     Ao = homogenized.ahom_edge(a_edges, [r.reshape(N, N, N) for r in refs])
     assert np.abs(Ah - Ao).max() <= 1e-10 * np.abs(Ao).max()
+
+
+@pytest.mark.parametrize("N", [16, 48, 96, 256])
+@pytest.mark.parametrize("rank", [0, 8])
+def test_multiplier_table_and_on_the_fly_agree(sq, N, rank):
+    """Pass C reads the tabulated multiplier (N <= 256) or sums it per mode
+    (SQ_OPT_MULTIPLIER_TABLE = 0); both give the oracle's preconditioner, in
+    FP64 and FP32."""
+    import torch
+
+    pc = sq.sq_precond_setup(N, rank)
+    G = _core(sq, pc, N, rank)
+    for prec, dt, tol in ((sq.SQ_FP64, "float64", 1e-12), (sq.SQ_FP32_REFINE, "float32", 2e-5)):
+        w = sq.sq_workspace_create(N, prec)
+        r = inputs.random_field(N, 11 * N + rank, np.float64 if dt == "float64" else np.float32)
+        ref = precond.apply_precond(G, r.astype(np.float64))
+        for opt in (1, 0):
+            try:
+                sq.sq_set_option(sq.SQ_OPT_MULTIPLIER_TABLE, opt)
+                z = torch.empty(N ** 3, dtype=getattr(torch, dt), device="cuda")
+                (sq.sq_apply_precond if dt == "float64" else sq.sq_apply_precond_f32)(pc, w, _dev(r.ravel(), dt), z)
+                got = _host(z).reshape(N, N, N).astype(np.float64)
+            finally:
+                sq.sq_set_option(sq.SQ_OPT_MULTIPLIER_TABLE, 1)
+            assert _relmax(got, ref) <= tol, (prec, opt)

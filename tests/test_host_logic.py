@@ -56,9 +56,12 @@ def test_bench_algorithmic_model():
     n3 = N ** 3
     # the fused iteration moves 17 field passes of 4-byte words
     assert sum(b for b, _ in alg.values()) + alg["dht_x2"][0] == 17 * 4 * n3
-    # pass C: two transforms without combines, the rank-R multiplier, scaling and r.z
-    assert alg["dht_x1_scale"][1] == (2 * 2.5 * 8 + 2 * R + 6) * n3
-    assert bench._algorithmic(N, 8, 0)["dht_x1_scale"][1] == (2 * 2.5 * 8 + 10) * n3
+    # pass C: two transforms without combines, scaling and r.z; the multiplier
+    # is a table lookup at N <= 256, else the rank-R sum or the exact 1/x
+    assert alg["dht_x1_scale"][1] == (2 * 2.5 * 8 + 6) * n3
+    assert bench._algorithmic(N, 8, R, table=False)["dht_x1_scale"][1] == (2 * 2.5 * 8 + 2 * R + 6) * n3
+    assert bench._algorithmic(N, 8, 0, table=False)["dht_x1_scale"][1] == (2 * 2.5 * 8 + 10) * n3
+    assert bench._algorithmic(512, 4, 0)["dht_x1_scale"][1] == (2 * 2.5 * 9 + 10) * 512 ** 3
 
 
 def test_new_bindings_reject_bad_arguments_before_calling_the_library():
@@ -173,7 +176,7 @@ def test_bench_roofline_selection():
     _, roof_m = bench.kernel_table(work, prof, N, 8, R, t_ms=400.0, peaks=pk)
     assert roof_m["peak"] == 1.0 and roof_m["peak_src"] == "measured"
     assert abs(roof_m["frac"] - roof["achieved"] / 1.0) <= 1e-3 and "hbm_frac" in roof_m
-    assert roof["traffic"] == bench.PROFILED_TRAFFIC[("dht_x1_scale", 8)]
+    assert roof["traffic"] == bench.PROFILED_TRAFFIC.get(("dht_x1_scale", 8))
     assert kernels["dht_x2"]["us_per_work_launch"] == 481.0
     # FP32: pass E dominates and is HBM-bound
     us32 = {"stencil_matvec": 41.0, "dht_x3_in": 52.0, "dht_x2": 24.5, "dht_x1_scale": 53.5, "dht_x3_out": 58.8}

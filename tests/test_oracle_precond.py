@@ -136,7 +136,8 @@ def test_log_uniform_sample_members():
     assert len(x) <= 3000
 
 
-@pytest.mark.parametrize("N,R,dim", [(16, 6, 3), (64, 8, 3), (256, 8, 3), (64, 16, 3), (256, 8, 2), (48, 4, 3)])
+@pytest.mark.parametrize("N,R,dim", [(16, 6, 3), (64, 8, 3), (256, 8, 3), (64, 16, 3), (256, 8, 2), (48, 4, 3),
+                                     (16, 16, 3), (24, 32, 3)])
 def test_lsq_sum_positive_geometric_and_better_than_trapezoid(N, R, dim):
     t, w = precond.lsq_nodes(N, R, dim)
     assert np.all(t > 0) and np.all(w > 0)
