@@ -384,8 +384,8 @@ struct SpectralDev {
   // pass C evaluates G from lam or u on the fly.
   const void *gtab = nullptr;
 };
-// Grids up to this size carry the multiplier table (8.6 MB FP32 + 17 MB FP64
-// at N = 256, resident in L2 while pass C reads it).
+// Grids up to this size carry the FP64 multiplier table (17 MB at N = 256,
+// resident in L2 while pass C reads it).
 constexpr int kGtabMaxN = 256;
 __host__ __device__ constexpr int mirror_index(int k, int N) { return k <= N - k ? k : N - k; }
 enum DhtPass : int { PASS_A_RESID = 0, PASS_A_PLAIN = 1, PASS_B = 2, PASS_C = 3, PASS_E_PCG = 4, PASS_E_PLAIN = 5 };
@@ -405,6 +405,7 @@ int set_stencil_rows(int rpt);  // FP32 operator rows per thread: 0 auto, 1, 2, 
 int set_stencil_rows_override(int N, int rpt);  // per grid size; 0 = the process-wide choice
 int set_strided_fast(int on);  // 0: generic Stockham tiles for every pass
 int set_use_gtab(int on);      // 0: pass C evaluates the multiplier on the fly everywhere
+int set_tile_prefetch(int v);  // FP32 strided passes in the persistent prefetching form: 0 none, 1 C, 2 B C D
 int use_gtab();
 
 // solver.cu: read-only views of the opaque handles (used by batch.cu)

@@ -451,17 +451,25 @@ __device__ __forceinline__ void s2_stage1(const C *__restrict__ gsrc, size_t bas
 // Stage 1 from a dense shared-memory copy of the tile (row j of the tile's P
 // complex values at raw + j P, landed there by bulk copies): the reads of a
 // warp cover two whole rows, conflict-free; the results go to the padded
-// layout of sm as in s2_stage1.
-template <typename T, typename C, int R0, int R1, int P>
-__device__ __forceinline__ void s2_stage1_raw(const C *raw, C *sm) {
+// layout of sm as in s2_stage1. A thread given raw = nullptr (its wait for the
+// copies gave up) reads the tile from global memory instead; the barrier at
+// the end is the same for both.
+template <typename T, typename C, int R0, int R1, int P, long long STRIDE>
+__device__ __forceinline__ void s2_stage1_raw(const C *raw, const C *__restrict__ gsrc, size_t base, C *sm) {
   constexpr int SP = P + 1, LP = ilog2c(P);
   static_assert(R1 * P <= kThreads, "one stage-1 butterfly per thread");
   const int t = threadIdx.x;
   if (t < R1 * P) {
     const int p = t & (P - 1), b = t >> LP;
     C u[R0];
+    if (raw) {
 #pragma unroll
-    for (int q = 0; q < R0; ++q) u[q] = raw[(b + q * R1) * P + p];
+      for (int q = 0; q < R0; ++q) u[q] = raw[(b + q * R1) * P + p];
+    } else {
+      const C *g = gsrc + (base >> 1) + (size_t)b * (STRIDE >> 1) + p;
+#pragma unroll
+      for (int q = 0; q < R0; ++q) u[q] = g[(size_t)q * R1 * (STRIDE >> 1)];
+    }
     dft<T, C, R0>(u);
 #pragma unroll
     for (int q = 0; q < R0; ++q) sm[(b * R0 + q) * SP + p] = u[q];
