@@ -223,9 +223,8 @@ void sq_workspace_destroy(sq_workspace *w);
  * relative residual 1e-5 by default (SQ_OPT_INNER_TOL_EXP; at most max_iter
  * inner iterations in total). Returns SQ_OK, SQ_ENOCONV (tolerance missed
  * within max_iter; psi and info are valid) or SQ_ETIMEOUT: a bounded device
- * wait (pass E's staging of p and x, or a prefetching strided pass, in the
- * FP32 iteration; SQ_OPT_WAIT_POLLS) gave up; that kernel read its operands
- * from global memory instead, the
+ * wait (pass E's staging of p and x in the FP32 iteration, SQ_OPT_WAIT_POLLS)
+ * gave up; that kernel read its operands from global memory instead, the
  * solve ran to the end, and psi (zero mean) and info are complete as for
  * SQ_OK. Synchronizes `stream` (the host checks convergence). info may be
  * NULL. */
@@ -282,10 +281,9 @@ int sq_set_tiles(const sq_tile_config *tiles, int ntiles);
  * (single and batched) cuts its residual by 10^-value, or just enough for the
  * outer tolerance when that is less; 2 <= value <= 7.
  * SQ_OPT_WAIT_POLLS (default 4194304 = 2^22): how many times the FP32 pass E
- * of single solves polls the barrier of its bulk copies of p and x (and a
- * prefetching strided pass that of its next tile, SQ_OPT_TILE_PREFETCH)
- * before it gives up, reads them from global memory, flags the solve
- * (SQ_ETIMEOUT) and stops staging; 0 gives up at once. The block still waits (up to 2^24 polls)
+ * of single solves polls the barrier of its bulk copies of p and x before it
+ * gives up, reads them from global memory, flags the solve (SQ_ETIMEOUT) and
+ * stops staging; 0 gives up at once. The block still waits (up to 2^24 polls)
  * for its copies in flight before it exits. 0 <= value <= 2^24.
  * SQ_OPT_MULTIPLIER_TABLE (default 1): preconditioners of grids N <= 256 carry
  * their multiplier G tabulated on the mirror-reduced modes, (N/2 + 1)^3 FP64
@@ -293,22 +291,13 @@ int sq_set_tiles(const sq_tile_config *tiles, int ntiles);
  * and the FP64 x1 pass reads G from it instead of summing the canonical terms
  * (or dividing, for the exact diagonal) per mode; 0 evaluates G on the fly.
  * FP32 passes always evaluate it on the fly. Results agree to rounding.
- * SQ_OPT_TILE_PREFETCH (default 1): FP32 strided passes of single solves run
- * in a persistent form (as many blocks as fit on the GPU, each walking its
- * tiles) that fetches the next tile with bulk copies into shared memory while
- * it transforms the current one: 0 for none, 1 for the x1 pass with the
- * multiplier, 2 also for both x2 passes. Used where a tile takes at most
- * 32 KB and the input is 16-byte aligned; the waits are bounded as for
- * SQ_OPT_WAIT_POLLS (a wait that gives up reads global memory and the solve
- * returns SQ_ETIMEOUT with a complete result). Results are identical.
  */
 enum sq_option {
   SQ_OPT_STRIDED_TWO_STAGE = 1,
   SQ_OPT_STENCIL_ROWS = 2,
   SQ_OPT_INNER_TOL_EXP = 3,
   SQ_OPT_WAIT_POLLS = 4,
-  SQ_OPT_MULTIPLIER_TABLE = 5,
-  SQ_OPT_TILE_PREFETCH = 6
+  SQ_OPT_MULTIPLIER_TABLE = 5
 };
 int sq_set_option(int key, int value);
 

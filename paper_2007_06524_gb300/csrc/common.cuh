@@ -405,7 +405,6 @@ int set_stencil_rows(int rpt);  // FP32 operator rows per thread: 0 auto, 1, 2, 
 int set_stencil_rows_override(int N, int rpt);  // per grid size; 0 = the process-wide choice
 int set_strided_fast(int on);  // 0: generic Stockham tiles for every pass
 int set_use_gtab(int on);      // 0: pass C evaluates the multiplier on the fly everywhere
-int set_tile_prefetch(int v);  // FP32 strided passes in the persistent prefetching form: 0 none, 1 C, 2 B C D
 int use_gtab();
 
 // solver.cu: read-only views of the opaque handles (used by batch.cu)

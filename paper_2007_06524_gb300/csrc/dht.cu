@@ -136,13 +136,7 @@ __global__ void __launch_bounds__(kThreads, s2_min_blocks(R0 * R1, false)) k_dht
 }
 
 template <int AXIS, int R0, int R1, int P, bool SCALE, int RR>
-static cudaError_t launch_s2_pf(const DhtArgs<float> &a, cudaStream_t s);
-template <int AXIS, int R0, int R1, int P, bool SCALE, int RR>
-static bool use_prefetch(const DhtArgs<float> &a);
-
-template <int AXIS, int R0, int R1, int P, bool SCALE, int RR>
 static cudaError_t launch_s2(const DhtArgs<float> &a, int grid, cudaStream_t s) {
-  if (use_prefetch<AXIS, R0, R1, P, SCALE, RR>(a)) return launch_s2_pf<AXIS, R0, R1, P, SCALE, RR>(a, s);
   const size_t smem = (size_t)R0 * R1 * (P + 1) * sizeof(float2) + (size_t)R0 * R1 * sizeof(float2) +
                       (size_t)a.sp.rank * 2 * P * sizeof(float);
   auto kern = k_dht_s2<AXIS, R0, R1, P, SCALE, RR>;
@@ -150,141 +144,6 @@ static cudaError_t launch_s2(const DhtArgs<float> &a, int grid, cudaStream_t s) 
   if (e != cudaSuccess) return e;
   kern<<<grid, kThreads, smem, s>>>(a);
   return cudaGetLastError();
-}
-
-// Persistent, prefetching form of the strided two-stage pass (FP32). Each
-// block walks the tiles blockIdx.x, + gridDim.x, ... with the grid sized to
-// the blocks that fit on the GPU at once. While it transforms one tile, the
-// next tile's N row segments (2P floats each) are already on their way into a
-// dense shared-memory buffer by bulk copies (issued by warp 0 once stage 1 has
-// read the buffer, completing on an mbarrier), so the wait for global memory
-// overlaps the shared-memory stages instead of stalling every block of a wave
-// at once. Every wait is bounded: a thread whose wait gives up reads the tile
-// from global memory, flags the solve (SQ_ETIMEOUT) and the block stops
-// prefetching; before it exits it waits (up to 2^24 polls) for the copies it
-// issued.
-template <int AXIS, int R0, int R1, int P, bool SCALE, int RR>
-__global__ void __launch_bounds__(kThreads, R0 * R1 > 256 ? 2 : 3) k_dht_s2_pf(DhtArgs<float> a) {
-  using C = float2;
-  if (a.check_done && *(volatile int *)&a.rb.st->done) return;
-  extern __shared__ __align__(128) unsigned char smem_raw[];
-  constexpr int N = R0 * R1;
-  constexpr long long NN = (long long)N * N;
-  constexpr long long STRIDE = (AXIS == 2) ? N : NN;
-  constexpr int nb2 = N / (2 * P);
-  constexpr unsigned kRowBytes = 2u * P * sizeof(float);
-  C *raw = reinterpret_cast<C *>(smem_raw);  // N rows of P complex values, dense
-  C *sm = raw + N * P;
-  C *tw = sm + N * (P + 1);
-  float *vtab = reinterpret_cast<float *>(tw + N);
-  __shared__ __align__(8) unsigned long long mbar;
-  __shared__ int s_off;
-  const C *twg = reinterpret_cast<const C *>(a.sp.tw);
-  for (int m = threadIdx.x; m < N; m += kThreads) tw[m] = twg[m];
-  if (threadIdx.x == 0) {
-    mbar_init(&mbar, 1);
-    s_off = 0;
-  }
-  Accum<float> acc;
-  const C *gin = reinterpret_cast<const C *>(a.in);
-  C *gout = reinterpret_cast<C *>(a.out);
-  auto tile_base = [&](int tile) {
-    const int line = tile / nb2, cb = tile - line * nb2;
-    return (AXIS == 2) ? (size_t)line * NN + (size_t)cb * 2 * P : (size_t)line * N + (size_t)cb * 2 * P;
-  };
-  // warp 0: arm the barrier for the whole tile, then one bulk copy per row
-  auto issue = [&](int tile) {
-    const size_t base = tile_base(tile);
-    const int lane = threadIdx.x & 31;
-    asm volatile("fence.proxy.async.shared::cta;\n" ::: "memory");
-    if (lane == 0) mbar_expect_tx(&mbar, N * kRowBytes);
-    __syncwarp();
-    for (int j = lane; j < N; j += 32) bulk_g2s(raw + (size_t)j * P, a.in + base + (size_t)j * STRIDE, kRowBytes, &mbar);
-  };
-  __syncthreads();  // barrier initialised, twiddles loaded
-  bool pf = true, late = false;
-  unsigned phase = 0;
-  if (threadIdx.x < 32 && (int)blockIdx.x < a.ntiles) issue(blockIdx.x);
-  for (int tile = blockIdx.x; tile < a.ntiles; tile += gridDim.x) {
-    const int line = tile / nb2, cb = tile - line * nb2;
-    const int c0 = cb * 2 * P, k2 = line;
-    const size_t base = tile_base(tile);
-    __syncthreads();  // the previous tile's last stage is done with sm and vtab
-    if (SCALE && RR != 0 && RR != -2) {
-      const float *uf = reinterpret_cast<const float *>(a.sp.u);
-      const float *u2 = uf + (size_t)a.sp.rank * N, *u3 = uf + 2 * (size_t)a.sp.rank * N;
-      for (int e = threadIdx.x; e < a.sp.rank * 2 * P; e += kThreads) {
-        const int rr = e / (2 * P), w = e - rr * 2 * P;
-        vtab[e] = u2[rr * N + k2] * u3[rr * N + c0 + w];
-      }
-    }
-    bool ok = false;
-    if (pf) {
-      ok = mbar_wait(&mbar, phase, a.wait_polls);
-      phase ^= 1u;
-      if (!ok) {
-        a.rb.st->fault = 1;
-        s_off = 1;
-        late = true;
-      }
-    }
-    s2_stage1_raw<float, C, R0, R1, P, STRIDE>(ok ? raw : nullptr, gin, base, sm);  // ends with a barrier
-    if (pf && s_off) pf = false;  // set before that barrier: the same choice in every thread
-    if (pf && threadIdx.x < 32 && tile + (int)gridDim.x < a.ntiles) issue(tile + gridDim.x);
-    s2_stage2<float, C, R0, R1, P>(sm, tw);
-    if (SCALE) {
-      s2_combine<float, C, N, P, 1, RR, STRIDE>(sm, gout, base, a.sp, k2, c0, vtab, acc);
-      s2_stage1<float, C, R0, R1, P, true, STRIDE>(gin, base, sm);
-      s2_stage2<float, C, R0, R1, P>(sm, tw);
-      s2_combine<float, C, N, P, 2, RR, STRIDE>(sm, gout, base, a.sp, k2, c0, vtab, acc);
-    } else {
-      s2_combine<float, C, N, P, 0, RR, STRIDE>(sm, gout, base, a.sp, k2, c0, vtab, acc);
-    }
-  }
-  if (late) mbar_wait(&mbar, phase ^ 1u, 1 << 24);  // no copy into this block may be in flight at exit
-  if (SCALE) {
-    FF v[1] = {acc.part()};
-    double s[1];
-    if (reduce_last_block<1>(v, a.rb.partials, &a.rb.st->ticket, s)) {
-      if (threadIdx.x == 0) finalize_scalars(a.rb.st, a.first ? FIN_RZ_FIRST : FIN_RZ_BETA, s, 1);
-    }
-  }
-}
-
-static int g_prefetch = 1;  // 0: none; 1: pass C; 2: passes B, C and D (persistent prefetching form)
-
-int set_tile_prefetch(int v) {
-  if (v < 0 || v > 2) return 1;
-  g_prefetch = v;
-  return 0;
-}
-
-template <int AXIS, int R0, int R1, int P, bool SCALE, int RR>
-static cudaError_t launch_s2_pf(const DhtArgs<float> &a, cudaStream_t s) {
-  const size_t smem = (size_t)R0 * R1 * P * sizeof(float2) + (size_t)R0 * R1 * (P + 1) * sizeof(float2) +
-                      (size_t)R0 * R1 * sizeof(float2) + (size_t)a.sp.rank * 2 * P * sizeof(float);
-  auto kern = k_dht_s2_pf<AXIS, R0, R1, P, SCALE, RR>;
-  cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
-  if (e != cudaSuccess) return e;
-  int dev = 0, sms = 0, per_sm = 0;
-  if ((e = cudaGetDevice(&dev)) != cudaSuccess) return e;
-  if ((e = cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev)) != cudaSuccess) return e;
-  if ((e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kern, kThreads, smem)) != cudaSuccess) return e;
-  const int resident = sms * (per_sm > 0 ? per_sm : 1);
-  const int grid = a.ntiles < resident ? a.ntiles : resident;
-  DhtArgs<float> b = a;
-  b.wait_polls = stage_wait_polls();
-  kern<<<grid, kThreads, smem, s>>>(b);
-  return cudaGetLastError();
-}
-
-// The prefetching form where it applies: FP32 strided passes chosen by
-// SQ_OPT_TILE_PREFETCH, a tile of at most 32 KB, 16-byte aligned input rows.
-template <int AXIS, int R0, int R1, int P, bool SCALE, int RR>
-static bool use_prefetch(const DhtArgs<float> &a) {
-  const bool pass_on = SCALE ? (g_prefetch >= 1) : (g_prefetch >= 2);
-  return pass_on && (size_t)R0 * R1 * P * sizeof(float2) <= 32 * 1024 &&
-         (reinterpret_cast<uintptr_t>(a.in) & 15) == 0;
 }
 
 // Specialisations of pass C: the tabulated multiplier (-2, where the
@@ -307,7 +166,7 @@ static cudaError_t launch_s2_p(const DhtArgs<float> &a, int grid, cudaStream_t s
   if constexpr ((R0 * R1) % 16 == 0) {
     if (a.logP == 3) return launch_s2_rank<AXIS, R0, R1, 8, SCALE>(a, grid, s);
   }
-  if constexpr ((R0 * R1) % 32 == 0 && R0 * 16 <= kThreads) {
+  if constexpr ((R0 * R1) % 32 == 0 && R1 * 16 <= kThreads) {
     if (a.logP == 4) return launch_s2_rank<AXIS, R0, R1, 16, SCALE>(a, grid, s);
   }
   return cudaErrorNotSupported;

@@ -448,47 +448,18 @@ __device__ __forceinline__ void s2_stage1(const C *__restrict__ gsrc, size_t bas
   __syncthreads();
 }
 
-// Stage 1 from a dense shared-memory copy of the tile (row j of the tile's P
-// complex values at raw + j P, landed there by bulk copies): the reads of a
-// warp cover two whole rows, conflict-free; the results go to the padded
-// layout of sm as in s2_stage1. A thread given raw = nullptr (its wait for the
-// copies gave up) reads the tile from global memory instead; the barrier at
-// the end is the same for both.
-template <typename T, typename C, int R0, int R1, int P, long long STRIDE>
-__device__ __forceinline__ void s2_stage1_raw(const C *raw, const C *__restrict__ gsrc, size_t base, C *sm) {
-  constexpr int SP = P + 1, LP = ilog2c(P);
-  static_assert(R1 * P <= kThreads, "one stage-1 butterfly per thread");
-  const int t = threadIdx.x;
-  if (t < R1 * P) {
-    const int p = t & (P - 1), b = t >> LP;
-    C u[R0];
-    if (raw) {
-#pragma unroll
-      for (int q = 0; q < R0; ++q) u[q] = raw[(b + q * R1) * P + p];
-    } else {
-      const C *g = gsrc + (base >> 1) + (size_t)b * (STRIDE >> 1) + p;
-#pragma unroll
-      for (int q = 0; q < R0; ++q) u[q] = g[(size_t)q * R1 * (STRIDE >> 1)];
-    }
-    dft<T, C, R0>(u);
-#pragma unroll
-    for (int q = 0; q < R0; ++q) sm[(b * R0 + q) * SP + p] = u[q];
-  }
-  __syncthreads();
-}
-
 // Hartley value pair of output m from X_m and its mirror X_{N-m}.
 template <typename C>
 __device__ __forceinline__ C hartley_pair(const C X, const C Y) {
   return C{X.x - X.y + Y.x + Y.y, X.x + X.y - Y.x + Y.y};
 }
 
+// (R0 P may exceed the block: a thread then takes several butterflies, each
+// reading and writing only its own positions.)
 template <typename T, typename C, int R0, int R1, int P>
 __device__ __forceinline__ void s2_stage2(C *sm, const C *__restrict__ tw) {
   constexpr int SP = P + 1, LP = ilog2c(P);
-  static_assert(R0 * P <= kThreads, "one stage-2 butterfly per thread");
-  const int t = threadIdx.x;
-  if (t < R0 * P) {
+  for (int t = threadIdx.x; t < R0 * P; t += kThreads) {
     const int p = t & (P - 1), b = t >> LP;
     C x[R1];
 #pragma unroll

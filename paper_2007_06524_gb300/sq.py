@@ -18,7 +18,6 @@ SQ_OPT_STENCIL_ROWS = 2
 SQ_OPT_INNER_TOL_EXP = 3
 SQ_OPT_WAIT_POLLS = 4
 SQ_OPT_MULTIPLIER_TABLE = 5
-SQ_OPT_TILE_PREFETCH = 6
 
 _HERE = os.path.dirname(os.path.abspath(__file__))
 _LIB = None

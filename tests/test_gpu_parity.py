@@ -466,19 +466,17 @@ def test_precond_cosine_modes_full_size(sq, N, rank):
         zexp += G * mode
     for prec, dt, tol in ((sq.SQ_FP64, torch.float64, 1e-12), (sq.SQ_FP32_REFINE, torch.float32, 1e-5)):
         w_ = sq.sq_workspace_create(N, prec)
-        for opt, pf in ((0, 1), (1, 0), (1, 1), (1, 2)):
+        for opt in (0, 1):
             try:
                 sq.sq_set_option(sq.SQ_OPT_STRIDED_TWO_STAGE, opt)
-                sq.sq_set_option(sq.SQ_OPT_TILE_PREFETCH, pf)
                 z = torch.empty(N ** 3, dtype=dt, device="cuda")
                 (sq.sq_apply_precond if dt == torch.float64 else sq.sq_apply_precond_f32)(
                     pc, w_, r.reshape(-1).to(dt).contiguous(), z)
                 torch.cuda.synchronize()
             finally:
                 sq.sq_set_option(sq.SQ_OPT_STRIDED_TWO_STAGE, 1)
-                sq.sq_set_option(sq.SQ_OPT_TILE_PREFETCH, 1)
             err = float((z.double().reshape(N, N, N) - zexp).abs().max() / zexp.abs().max())
-            assert err <= tol, (prec, opt, pf, err)
+            assert err <= tol, (prec, opt, err)
         del w_
 
 
@@ -505,24 +503,20 @@ def test_inner_tolerance_option(sq):
         sq.sq_set_option(sq.SQ_OPT_INNER_TOL_EXP, 5)
 
 
-@pytest.mark.parametrize("prefetch", [0, 1, 2])
-def test_bounded_staging_wait_gives_up_cleanly(sq, prefetch):
+def test_bounded_staging_wait_gives_up_cleanly(sq):
     """Failure detection without a GPU fault: SQ_OPT_WAIT_POLLS = 0 makes the
-    FP32 pass E give up on its bulk-copy barrier at once, and with
-    SQ_OPT_TILE_PREFETCH also the prefetching strided passes (1: x1, 2: x1
-    and x2). The kernels fall back to global-memory reads, so the solve still
-    reaches the oracle's corrector with zero mean and complete info, and
-    reports SQ_ETIMEOUT; the next solve with the default limit is clean."""
-    re = problem.realization(8, 8, 4, 1.0, 100.0)           # N = 64: two-stage tiles, staged pass E
+    FP32 pass E give up on its bulk-copy barrier at once. The kernel falls
+    back to global-memory reads, so the solve still reaches the oracle's
+    corrector with zero mean and complete info, and reports SQ_ETIMEOUT; the
+    next solve with the default limit is clean."""
+    re = problem.realization(8, 8, 4, 1.0, 100.0)           # N = 64: two-stage x3 tiles, staged pass E
     c = sq.sq_build_coeffs(8, 8, 4, 0.5, 1.0, 100.0)
     ref = pcg.tight_solve(re.A, re.b[1], re.N)[0]
     try:
-        sq.sq_set_option(sq.SQ_OPT_TILE_PREFETCH, prefetch)
         sq.sq_set_option(sq.SQ_OPT_WAIT_POLLS, 0)
         psi, info = _solve(sq, c, re.N, 1, 8, 1e-10, precision=sq.SQ_FP32_REFINE)
     finally:
         sq.sq_set_option(sq.SQ_OPT_WAIT_POLLS, 1 << 22)
-        sq.sq_set_option(sq.SQ_OPT_TILE_PREFETCH, 1)
     x = _host(psi)
     assert info["status"] == sq.SQ_ETIMEOUT
     assert info["relres_true"] <= 1e-10 and info["iters"] > 0 and info["outer_steps"] >= 1
@@ -594,41 +588,40 @@ def test_multiplier_table_and_on_the_fly_agree(sq, N, rank):
             assert _relmax(got, ref) <= tol, (prec, opt)
 
 
-@pytest.mark.parametrize("N", [16, 32, 48, 64, 96, 128, 256])
-@pytest.mark.parametrize("rank", [0, 8])
-def test_prefetching_strided_passes(sq, N, rank):
-    """The persistent prefetching form of the FP32 strided passes
-    (SQ_OPT_TILE_PREFETCH 0: none, 1: x1 pass, 2: x1 and x2 passes) gives the
-    oracle's preconditioner, and a refined solve with it the oracle's
-    corrector."""
+@pytest.mark.parametrize("P", [8, 16])
+def test_fp32_transform_tiles_at_n512(sq, P):
+    """N = 512 with 8- and 16-pencil tiles (the latter runs two radix-16
+    butterflies per thread in the strided passes' second stage): a sum of
+    cosine modes comes back scaled mode by mode by the oracle's multiplier,
+    exact and rank 8, through the FP32 transform passes."""
     import torch
 
-    pc = sq.sq_precond_setup(N, rank)
-    G = _core(sq, pc, N, rank)
-    w = sq.sq_workspace_create(N, sq.SQ_FP32_REFINE)
-    r = inputs.random_field(N, 13 * N + rank, np.float32)
-    ref = precond.apply_precond(G, r.astype(np.float64))
-    outs = []
-    try:
-        for opt in (0, 1, 2):
-            sq.sq_set_option(sq.SQ_OPT_TILE_PREFETCH, opt)
-            z = torch.empty(N ** 3, dtype=torch.float32, device="cuda")
-            sq.sq_apply_precond_f32(pc, w, _dev(r.ravel(), "float32"), z)
-            outs.append(_host(z).reshape(N, N, N).astype(np.float64))
-    finally:
-        sq.sq_set_option(sq.SQ_OPT_TILE_PREFETCH, 1)
-    for z in outs:
-        assert _relmax(z, ref) <= 2e-5
-    assert np.array_equal(outs[1], outs[2]) or _relmax(outs[1], outs[2]) <= 1e-6
-    if N in (32, 96):
-        L, n = N // 8 if N == 32 else 24, 8 if N == 32 else 4
-        re = problem.realization(L, n, 3, 1.0, 100.0)
-        c = sq.sq_build_coeffs(L, n, 3, 0.5, 1.0, 100.0)
-        sol = pcg.tight_solve(re.A, re.b[0], N)[0]
+    N, rank = 512, 8
+    t_, w_ = _oracle_nodes(N, rank)
+    lam = 4 * np.sin(np.pi * np.arange(N) / N) ** 2
+    ks = [(1, 0, 0), (3, 5, 7), (N // 2, N // 4, 1), (200, 17, 311)]
+    amps = [1.0, -0.5, 0.25, 0.125]
+    jj = torch.arange(N, dtype=torch.float64, device="cuda")
+    for rr in (0, rank):
+        pc = sq.sq_precond_setup(N, rr)
+        r = torch.zeros((N, N, N), dtype=torch.float64, device="cuda")
+        zexp = torch.zeros_like(r)
+        for k, a in zip(ks, amps):
+            th = 2 * np.pi * (k[0] * jj[:, None, None] + k[1] * jj[None, :, None] + k[2] * jj[None, None, :]) / N
+            mode = a * torch.cos(th)
+            g = lam[k[0]] + lam[k[1]] + lam[k[2]]
+            G = 1.0 / g if rr == 0 else float(np.sum(w_ * np.exp(-t_ * g)))
+            r += mode
+            zexp += G * mode
+        w = sq.sq_workspace_create(N, sq.SQ_FP32_REFINE)
+        z = torch.empty(N ** 3, dtype=torch.float32, device="cuda")
         try:
-            sq.sq_set_option(sq.SQ_OPT_TILE_PREFETCH, 2)
-            psi, info = _solve(sq, c, N, 0, rank, 1e-10, precision=sq.SQ_FP32_REFINE)
+            sq.sq_set_tiles([(N, P, 0, 0)])
+            sq.sq_apply_precond_f32(pc, w, r.reshape(-1).float().contiguous(), z)
+            torch.cuda.synchronize()
         finally:
-            sq.sq_set_option(sq.SQ_OPT_TILE_PREFETCH, 1)
-        assert info["status"] == sq.SQ_OK
-        assert np.linalg.norm(_host(psi) - sol) / np.linalg.norm(sol) <= 1e-6
+            sq.sq_set_tiles([])
+        err = float((z.double().reshape(N, N, N) - zexp).abs().max() / zexp.abs().max())
+        assert err <= 1e-5, (rr, err)
+        del w, z, r, zexp
+        torch.cuda.empty_cache()
