@@ -276,9 +276,10 @@ def run_native(args):
     from paper_2007_06524_gb300 import autotune
 
     if args.tiles:
-        tP, tZ, tR = (int(v) for v in args.tiles.split(","))
-        sq.sq_set_tiles([(N, tP, tZ, tR)])
-        tiles = (tP, tZ, tR)
+        tiles = tuple(int(v) for v in args.tiles.split(","))
+        if len(tiles) == 3:
+            tiles = tiles + (0,)
+        sq.sq_set_tiles([(N,) + tiles])
     else:
         tiles = autotune.tune(torch, N, L, n, cache=None)  # FP32 pass tile and operator planes for this grid
     c = sq.sq_build_coeffs(L, n, 0, wl["p_hi"], wl["a_lo"], wl["a_hi"])
@@ -374,7 +375,7 @@ def run_native(args):
                 "iters": {"mean": round(statistics.mean(iters), 2), "min": min(iters), "max": max(iters)},
                 "solve_hbm": solve_hbm(statistics.mean(iters), value / max(ws, 1), elem),
                 "converged": ok, "tiles": {"dht_pencils_fp32": tiles[0], "stencil_planes": tiles[1],
-                                           "stencil_rows_fp32": tiles[2]}})
+                                           "stencil_rows_fp32": tiles[2], "dht_pencils_e_fp32": tiles[3]}})
 
     # --- variants on the same workload (2 steps each)
     if not args.no_variants and rank == 0:
@@ -967,8 +968,8 @@ def main():
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--tiles", default=None,
-                    help="fixed FP32 tile shape 'P,planes,rows' (Hartley pencils, operator planes per item, operator "
-                         "rows per thread) instead of the autotuner")
+                    help="fixed FP32 tile shape 'P,planes,rows[,Pe]' (Hartley pencils, operator planes per item, "
+                         "operator rows per thread, pencils of the last pass of an iteration) instead of the autotuner")
     args = ap.parse_args()
     if args.warmup < 3 and args.impl == "native":
         args.warmup = 3

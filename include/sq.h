@@ -245,15 +245,18 @@ typedef struct sq_solve_desc {
 
 /* Tile shape per grid size (0 = default): Hartley-pass tile of `dht_pencils`
  * complex pencils (a power of two, 2*dht_pencils dividing N), operator work
- * items of `stencil_planes` x1-planes (register kernels), and the FP32
- * operator variant of single solves `stencil_rows` (1, 2, 4 node rows per
- * thread, or 8 for the shared-memory-staged kernel; see SQ_OPT_STENCIL_ROWS;
- * batches use 1). */
+ * items of `stencil_planes` x1-planes (register kernels), the FP32 operator
+ * variant of single solves `stencil_rows` (1, 2, 4 node rows per thread, or 8
+ * for the shared-memory-staged kernel; see SQ_OPT_STENCIL_ROWS; batches use
+ * 1), and `dht_pencils_e`, the tile of the last FP32 pass of a PCG iteration
+ * (x3 transform with the x and p updates, which stages p and x in shared
+ * memory; 0 = dht_pencils; single solves only). */
 typedef struct sq_tile_config {
   int N;
   int dht_pencils;
   int stencil_planes;
   int stencil_rows;
+  int dht_pencils_e;
 } sq_tile_config;
 
 /* Process-wide tile choice per grid size for single solves (FP32 Hartley

@@ -3,11 +3,14 @@ the fastest per grid size with sq_set_tiles (single solves), or returns the
 fastest per grid size of a batch for sq_batch_create (tune_batch).
 
 Tuned per N: the number of complex pencils of a Hartley-pass tile (FP32 passes;
-2P real pencils, 2P * 4 bytes per row segment), and jointly the node rows per
-thread and the x1-planes per work item of the FP32 operator. Each candidate is timed with CUDA events over a few
-repetitions of the kernel it drives (sq_apply_precond_f32 for the passes,
-sq_apply_operator_f32 for the operator), each after an L2 flush; results are cached in a JSON file
-keyed by N and the device name.
+2P real pencils, 2P * 4 bytes per row segment), jointly the node rows per
+thread and the x1-planes per work item of the FP32 operator, and the tile of the
+last pass of a PCG iteration (x3 transform with the x and p updates, which
+stages p and x in shared memory). Each candidate is timed with CUDA events over
+a few repetitions of the call it drives (sq_apply_precond_f32 for the passes,
+sq_apply_operator_f32 for the operator, 24 inner iterations of an FP32 solve for
+the last pass), each after an L2 flush; results are cached in a JSON file keyed
+by N and the device name.
 """
 from __future__ import annotations
 
@@ -45,8 +48,8 @@ def _time(torch, fn, reps=5):
 
 
 def tune(torch, N, L=None, n=None, cache=DEFAULT_CACHE, reps=5):
-    """Returns (dht_pencils, stencil_planes, stencil_rows) for grid N and
-    installs them with sq_set_tiles."""
+    """Returns (dht_pencils, stencil_planes, stencil_rows, dht_pencils_e) for
+    grid N and installs them with sq_set_tiles."""
     dev = torch.cuda.get_device_name()
     key = f"{dev}:{N}"
     table = {}
@@ -55,10 +58,11 @@ def tune(torch, N, L=None, n=None, cache=DEFAULT_CACHE, reps=5):
             table = json.load(open(cache))
         except Exception:
             table = {}
-    if key in table and "stencil_rows" in table[key]:
-        P, zc, rows = table[key]["dht_pencils"], table[key]["stencil_planes"], table[key]["stencil_rows"]
-        _sq.sq_set_tiles([(N, P, zc, rows)])
-        return P, zc, rows
+    if key in table and "dht_pencils_e" in table[key]:
+        e = table[key]
+        tile = (e["dht_pencils"], e["stencil_planes"], e["stencil_rows"], e["dht_pencils_e"])
+        _sq.sq_set_tiles([(N,) + tile])
+        return tile
     if L is None:
         n = 8 if N % 8 == 0 else 4
         L = N // n
@@ -90,14 +94,31 @@ def tune(torch, N, L=None, n=None, cache=DEFAULT_CACHE, reps=5):
                 continue
             times_z[(rows, zc)] = _time(torch, lambda: _sq.sq_apply_operator_f32(c, r, z), reps)
     bestR, bestZ = min(times_z, key=times_z.get)
-    _sq.sq_set_tiles([(N, bestP, bestZ, bestR)])
-    table[key] = {"dht_pencils": bestP, "stencil_planes": bestZ, "stencil_rows": bestR,
+    # the last pass of an iteration, inside 24 inner iterations of an FP32
+    # solve (tol 1e-30: the iteration cap ends it; the FP64 sweeps around the
+    # inner solve are the same for every candidate)
+    wr = _sq.sq_workspace_create(N, _sq.SQ_FP32_REFINE)
+    psi = torch.empty(N ** 3, dtype=torch.float64, device="cuda")
+    times_e = {}
+    for Pe in sorted({bestP, bestP // 2, bestP // 4}):
+        if Pe < 2 or N % (2 * Pe) != 0:
+            continue
+        try:
+            _sq.sq_set_tiles([(N, bestP, bestZ, bestR, Pe)])
+        except _sq.SqError:
+            continue
+        times_e[Pe] = _time(torch, lambda: _sq.sq_pcg_solve(c, pc, wr, 0, 1e-30, 24, _sq.SQ_FP32_REFINE, None, psi),
+                            reps)
+    bestE = min(times_e, key=times_e.get)
+    _sq.sq_set_tiles([(N, bestP, bestZ, bestR, bestE)])
+    table[key] = {"dht_pencils": bestP, "stencil_planes": bestZ, "stencil_rows": bestR, "dht_pencils_e": bestE,
                   "precond_ms": {str(k): round(v, 4) for k, v in times_p.items()},
-                  "operator_ms": {f"{k[0]}x{k[1]}": round(v, 4) for k, v in times_z.items()}}
+                  "operator_ms": {f"{k[0]}x{k[1]}": round(v, 4) for k, v in times_z.items()},
+                  "solve24_ms": {str(k): round(v, 4) for k, v in times_e.items()}}
     if cache:
         os.makedirs(os.path.dirname(cache), exist_ok=True)
         json.dump(table, open(cache, "w"), indent=1)
-    return bestP, bestZ, bestR
+    return bestP, bestZ, bestR, bestE
 
 
 def tune_batch(torch, descs, precs, tol, max_iter=2000, pencils=(4, 8, 16), planes=None, stream=None):

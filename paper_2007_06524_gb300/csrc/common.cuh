@@ -400,6 +400,7 @@ cudaError_t launch_dht_pass_2d(int pass, const SpectralDev &sp, const T *in, T *
                                RedBuf rb, bool first, bool check_done, cudaStream_t s);
 // tile overrides (0 = default); return 0 on success
 int set_dht_pencils_override(int N, int P);
+int set_dht_pencils_e_override(int N, int P);  // pass E (FP32, PCG update) only
 int set_stencil_planes_override(int N, int zc);
 int set_stencil_rows(int rpt);  // FP32 operator rows per thread: 0 auto, 1, 2, 4
 int set_stencil_rows_override(int N, int rpt);  // per grid size; 0 = the process-wide choice

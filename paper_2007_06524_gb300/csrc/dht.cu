@@ -337,6 +337,7 @@ static cudaError_t launch_fast(int pass, const DhtArgs<T> &a, int grid, cudaStre
 }
 
 static int g_pencils_override[kMaxN + 1] = {0};  // FP32 passes, per N (0 = default)
+static int g_pencils_e_override[kMaxN + 1] = {0};  // FP32 pass E with the PCG update, per N (0 = as above)
 static int g_strided_fast = 1;                    // two-stage strided passes where N allows
 static int g_use_gtab = 1;                        // pass C reads the multiplier table where there is one
 
@@ -358,6 +359,14 @@ int set_dht_pencils_override(int N, int P) {
   if (P != 0 && (P < 1 || (P & (P - 1)) || N % (2 * P) != 0 || dht_smem_bytes_t<float>(N, P, kMaxRank) > 200 * 1024))
     return 1;
   g_pencils_override[N] = P;
+  return 0;
+}
+
+int set_dht_pencils_e_override(int N, int P) {
+  if (N < 8 || N > kMaxN) return 1;
+  if (P != 0 && (P < 1 || (P & (P - 1)) || N % (2 * P) != 0 || dht_smem_bytes_t<float>(N, P, 0) > 200 * 1024))
+    return 1;
+  g_pencils_e_override[N] = P;
   return 0;
 }
 
@@ -383,7 +392,10 @@ template <typename T>
 cudaError_t launch_dht_pass(int pass, const SpectralDev &sp, const T *in, T *out, T *r, const T *q, T *p, T *x,
                             RedBuf rb, bool first, bool check_done, cudaStream_t s) {
   const int N = sp.N;
-  const int P = dht_tile_pencils(N, (int)sizeof(T));
+  // pass E with the PCG update has a tile width of its own (its bulk-copy
+  // staging of p and x adds 16 P N bytes of shared memory per block)
+  const int Pe = (sizeof(T) == 4 && pass == PASS_E_PCG) ? g_pencils_e_override[N] : 0;
+  const int P = Pe ? Pe : dht_tile_pencils(N, (int)sizeof(T));
   int logP = 0;
   while ((1 << logP) < P) ++logP;
   DhtArgs<T> a;

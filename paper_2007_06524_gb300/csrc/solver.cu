@@ -1095,10 +1095,12 @@ int sq_set_tiles(const sq_tile_config *tiles, int ntiles) {
     if (tiles[k].dht_pencils && set_dht_pencils_override(N, tiles[k].dht_pencils) != 0) return SQ_EINVAL;
     if (tiles[k].stencil_planes && set_stencil_planes_override(N, tiles[k].stencil_planes) != 0) return SQ_EINVAL;
     if (tiles[k].stencil_rows && set_stencil_rows_override(N, tiles[k].stencil_rows) != 0) return SQ_EINVAL;
+    if (tiles[k].dht_pencils_e && set_dht_pencils_e_override(N, tiles[k].dht_pencils_e) != 0) return SQ_EINVAL;
   }
   if (ntiles == 0) {
     for (int N = 8; N <= kMaxN; ++N) {
       set_dht_pencils_override(N, 0);
+      set_dht_pencils_e_override(N, 0);
       set_stencil_planes_override(N, 0);
       set_stencil_rows_override(N, 0);
     }

@@ -43,17 +43,20 @@ class SolveDesc(C.Structure):
 
 
 class TileConfig(C.Structure):
-    _fields_ = [("N", C.c_int), ("dht_pencils", C.c_int), ("stencil_planes", C.c_int), ("stencil_rows", C.c_int)]
+    _fields_ = [("N", C.c_int), ("dht_pencils", C.c_int), ("stencil_planes", C.c_int), ("stencil_rows", C.c_int),
+                ("dht_pencils_e", C.c_int)]
 
 
 def _tile_array(tl):
-    """(N, dht_pencils, stencil_planes[, stencil_rows]) tuples -> TileConfig array."""
+    """(N, dht_pencils, stencil_planes[, stencil_rows[, dht_pencils_e]]) tuples
+    -> TileConfig array."""
     arr = (TileConfig * max(1, len(tl)))()
     for k, t in enumerate(tl):
-        if len(t) not in (3, 4):
-            raise ValueError("tile entries are (N, dht_pencils, stencil_planes[, stencil_rows])")
+        if len(t) not in (3, 4, 5):
+            raise ValueError("tile entries are (N, dht_pencils, stencil_planes[, stencil_rows[, dht_pencils_e]])")
         arr[k].N, arr[k].dht_pencils, arr[k].stencil_planes = int(t[0]), int(t[1]), int(t[2])
-        arr[k].stencil_rows = int(t[3]) if len(t) == 4 else 0
+        arr[k].stencil_rows = int(t[3]) if len(t) >= 4 else 0
+        arr[k].dht_pencils_e = int(t[4]) if len(t) == 5 else 0
     return arr
 
 
@@ -567,8 +570,8 @@ def sq_net_train_step(net: Net, coeffs, targets, lr, stream=None, loss_type=0) -
 
 
 def sq_set_tiles(tiles):
-    """tiles: list of (N, dht_pencils, stencil_planes[, stencil_rows]); 0 = default;
-    [] restores every default."""
+    """tiles: list of (N, dht_pencils, stencil_planes[, stencil_rows[, dht_pencils_e]]);
+    0 = default; [] restores every default."""
     tl = list(tiles)
     arr = _tile_array(tl)
     _check(load_library().sq_set_tiles(arr if tl else None, len(tl)), "sq_set_tiles")

@@ -198,3 +198,16 @@ def test_wait_polls_option_range(sq):
         _einval(sq, sq.sq_set_option, sq.SQ_OPT_WAIT_POLLS, bad)
     for ok in (0, 1, 1 << 24, 1 << 22):
         sq.sq_set_option(sq.SQ_OPT_WAIT_POLLS, ok)
+
+
+def test_pass_e_tile_override(sq):
+    """dht_pencils_e: a power of two with 2 P dividing N (0 = as dht_pencils)."""
+    try:
+        _einval(sq, sq.sq_set_tiles, [(64, 16, 0, 0, 5)])
+        _einval(sq, sq.sq_set_tiles, [(48, 16, 0, 0, 32)])
+        sq.sq_set_tiles([(64, 16, 0, 0, 8)])
+        sq.sq_set_tiles([(256, 16, 0, 8, 0)])
+        with pytest.raises(ValueError):
+            sq.sq_set_tiles([(64, 16, 0, 0, 8, 1)])
+    finally:
+        sq.sq_set_tiles([])

@@ -625,3 +625,20 @@ def test_fp32_transform_tiles_at_n512(sq, P):
         assert err <= 1e-5, (rr, err)
         del w, z, r, zexp
         torch.cuda.empty_cache()
+
+
+@pytest.mark.parametrize("Pe", [2, 4, 8, 16])
+def test_pass_e_tile_width(sq, Pe):
+    """The last pass of the FP32 iteration (x3 transform with x += alpha p,
+    p = z + beta p, staging p and x) with its own tile width: the refined
+    solve reaches the oracle's corrector for every width."""
+    re = problem.realization(8, 8, 6, 1.0, 100.0)
+    c = sq.sq_build_coeffs(8, 8, 6, 0.5, 1.0, 100.0)
+    ref = pcg.tight_solve(re.A, re.b[2], re.N)[0]
+    try:
+        sq.sq_set_tiles([(re.N, 16, 0, 0, Pe)])
+        psi, info = _solve(sq, c, re.N, 2, 8, 1e-10, precision=sq.SQ_FP32_REFINE)
+    finally:
+        sq.sq_set_tiles([])
+    assert info["status"] == sq.SQ_OK and info["relres_true"] <= 1e-10
+    assert np.linalg.norm(_host(psi) - ref) / np.linalg.norm(ref) <= 1e-6
