@@ -378,11 +378,18 @@ def run_native(args):
                                            "stencil_rows_fp32": tiles[2], "dht_pencils_e_fp32": tiles[3]}})
 
     # --- variants on the same workload (2 steps each)
+    want = None if args.variants is None else set(args.variants.split(","))
+
+    def on(name):
+        return want is None or name in want
+
     if not args.no_variants and rank == 0:
         variants = {}
         for label, rr, pp in (("fp32_refine_exact", 0, sq.SQ_FP32_REFINE), ("fp32_refine_rank8", 8, sq.SQ_FP32_REFINE),
                               ("fp64_exact", 0, sq.SQ_FP64), ("fp64_rank4", 4, sq.SQ_FP64),
                               ("fp64_rank16", 16, sq.SQ_FP64)):
+            if not on(label):
+                continue
             pcv = sq.sq_precond_setup(N, rr)
             wv = sq.sq_workspace_create(N, pp) if pp != prec else w
             sq.sq_coeffs_regenerate(c, 7, wl["p_hi"])
@@ -425,15 +432,18 @@ def run_native(args):
         out["variants"] = variants
         del w
         torch.cuda.empty_cache()
-        variants["refine_error_n128"] = run_refine_error_n128(sq, torch)
-        variants["batch_768_mixed"] = run_batch(sq, torch, stream, peaks=peaks)
-        variants["warm_start_n64"] = run_warm_start(sq, torch)
-        variants["refine_n512"] = run_refine_n512(sq, torch, stream)
-        variants["ensemble"] = run_ensemble(sq, torch)
-        variants["inclusions_alpha_quarter"] = run_inclusions(sq, torch, stream)
-        variants["two_contrasts_alpha_quarter"] = run_two_contrasts(sq, torch, stream)
-        variants["precond_routes_n256"] = run_precond_routes(sq, torch, stream)
-        variants["table_2d_alpha_quarter"] = run_2d_table(sq, torch, stream)
+        legs = (("refine_error_n128", lambda: run_refine_error_n128(sq, torch)),
+                ("batch_768_mixed", lambda: run_batch(sq, torch, stream, peaks=peaks)),
+                ("warm_start_n64", lambda: run_warm_start(sq, torch)),
+                ("refine_n512", lambda: run_refine_n512(sq, torch, stream)),
+                ("ensemble", lambda: run_ensemble(sq, torch)),
+                ("inclusions_alpha_quarter", lambda: run_inclusions(sq, torch, stream)),
+                ("two_contrasts_alpha_quarter", lambda: run_two_contrasts(sq, torch, stream)),
+                ("precond_routes_n256", lambda: run_precond_routes(sq, torch, stream)),
+                ("table_2d_alpha_quarter", lambda: run_2d_table(sq, torch, stream)))
+        for name, leg in legs:
+            if on(name):
+                variants[name] = leg()
 
     if rank == 0 and not args.no_cpu_baseline and ws == 1:
         out["cpu_baseline"] = cpu_baseline(R)
@@ -467,15 +477,17 @@ def summarize(out):
                                                               "copy_l2_gbs")}}
     if "fp32_refine_rank8" in v:
         sm["fp32_refine_rank8_solves_per_s"] = v["fp32_refine_rank8"]["solves_per_s"]
-        sm["fp32_refine_exact_solves_per_s"] = v["fp32_refine_exact"]["solves_per_s"]
         sm["fp32_iteration_hbm"] = v["fp32_refine_rank8"].get("iteration_hbm")
         sm["fp32_solve_hbm_frac"] = v["fp32_refine_rank8"]["solve_hbm"]["frac"]
+    if "fp32_refine_exact" in v:
+        sm["fp32_refine_exact_solves_per_s"] = v["fp32_refine_exact"]["solves_per_s"]
     if "roofline_fp32_refine" in out:
         r = out["roofline_fp32_refine"]
         sm["roofline_fp32_refine"] = {k: r.get(k) for k in ("kernel", "bound", "frac")}
     if "batch_768_mixed" in v:
         b = v["batch_768_mixed"]
         sm["batch"] = {k: b.get(k) for k in ("solves_per_s", "iters_p50", "iters_p99", "hbm_frac")}
+        sm["batch"]["inner_busy_frac"] = (b.get("inner_loop") or {}).get("busy_frac")
     if "warm_start_n64" in v:
         sm["warm_start"] = v["warm_start_n64"].get("summary")
     if "refine_error_n128" in v:
@@ -534,6 +546,21 @@ def batch_algorithmic(Ns, iters, seconds, hbm_gbs):
             "algorithmic_note": "17 FP32 field passes per inner iteration / wall time; working set far above L2"}
 
 
+def batch_busy(t_graph, t_profiled, prof):
+    """Kernel busy fraction of the batch's graph-replayed inner loops:
+    the inner-iteration kernels' summed event time (profiled solve) over the
+    inner loops' wall time in the graph solve, t_graph - (t_profiled -
+    profiled inner-loop time). 1 - busy bounds what a persistent kernel could
+    gain by removing kernel boundaries."""
+    k_ms, k_n = prof.get("batch_inner", (0.0, 0))
+    loop_ms, _ = prof.get("batch_inner_loop", (0.0, 0))
+    outside = t_profiled - loop_ms / 1e3
+    graph_loop = t_graph - outside
+    return {"kernel_s": round(k_ms / 1e3, 5), "kernel_launches": int(k_n), "graph_loop_s": round(graph_loop, 5),
+            "profiled_loop_s": round(loop_ms / 1e3, 5),
+            "busy_frac": round(k_ms / 1e3 / graph_loop, 4) if graph_loop > 0 else None}
+
+
 def run_batch(sq, torch, stream, nseeds=256, peaks=None):
     """768 corrector solves (256 realizations x e_1..e_3) in one batch: L drawn
     from {8,12,16,24} per seed, n=4 (N = 32..96), Bernoulli(1/2) on {1,10},
@@ -571,6 +598,24 @@ def run_batch(sq, torch, stream, nseeds=256, peaks=None):
         torch.cuda.synchronize()
         del b
         res[label] = (e0.elapsed_time(e1) / 1e3, infos)
+    # kernel busy time of the inner loop: one more solve with the library's
+    # event profile, which launches the graph's kernels one by one with an
+    # event pair each and times each whole inner loop. The graph-replayed inner
+    # loop's wall time is the graph solve's time minus the profiled solve's
+    # time outside its inner loops (the same launches in both).
+    b = sq.sq_batch_create(descs, pl, tiles=tiles)
+    sq.sq_pcg_solve_batched(b, wl["tol"], 2000)
+    torch.cuda.synchronize()
+    sq.sq_profile_enable(True)
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    e0.record(stream)
+    sq.sq_pcg_solve_batched(b, wl["tol"], 2000)
+    e1.record(stream)
+    torch.cuda.synchronize()
+    prof = sq.sq_profile_read()
+    sq.sq_profile_enable(False)
+    del b
+    busy = batch_busy(res["tuned_tiles"][0], e0.elapsed_time(e1) / 1e3, prof)
     t, infos = res["tuned_tiles"]
     its = np.array([i["iters"] for i in infos])
     ok = all(i["status"] == sq.SQ_OK for i in infos)
@@ -579,7 +624,7 @@ def run_batch(sq, torch, stream, nseeds=256, peaks=None):
            "iters_p50": float(np.percentile(its, 50)), "iters_p99": float(np.percentile(its, 99)),
            "unknowns": unknowns, "converged": ok, "tiles": [list(x) for x in tiles],
            "default_tiles_solves_per_s": round(len(descs) / res["default_tiles"][0], 1),
-           "tune_seconds": round(tune_s, 2), "tune_ms": tune_ms}
+           "tune_seconds": round(tune_s, 2), "tune_ms": tune_ms, "inner_loop": busy}
     out.update(batch_algorithmic(Ns, its, t, (peaks or default_peaks())["hbm_gbs"]))
     return out
 
@@ -965,6 +1010,8 @@ def main():
     ap.add_argument("--rank", type=int, default=8, help="preconditioner rank (0 = exact Fourier diagonal)")
     ap.add_argument("--precision", choices=["fp64", "fp32_refine"], default="fp64")
     ap.add_argument("--no-variants", action="store_true")
+    ap.add_argument("--variants", default=None,
+                    help="comma-separated subset of the variant legs to run (default: all), e.g. batch_768_mixed")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--tiles", default=None,

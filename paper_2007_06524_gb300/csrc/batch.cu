@@ -387,20 +387,31 @@ int precond_first_b(sq_batch *b, cudaStream_t s) {
   return launch_kb_dht<3, LD_PLAIN, SO_PCG, false>(b, 1, s);
 }
 
+// One inner PCG iteration of every active solve: six launches (each bracketed
+// by the kernel-event profile when it is on; outside a capture only).
 int iteration_b(sq_batch *b, cudaStream_t s) {
+  size_t pi = profile_begin_batch_inner(s);
   if (b->general)
     kb_stencil<1, true><<<b->tot_in, dim3(32, 8, 1), kStagedSmem + tab_bytes<float>(b->layers), s>>>(
         b->dS, b->d_pre + 3 * (b->count + 1), b->count);
   else
     kb_stencil<1, false><<<b->tot_in, dim3(32, 8, 1), kStagedSmem + tab_bytes<float>(1), s>>>(
         b->dS, b->d_pre + 3 * (b->count + 1), b->count);
+  profile_end(pi, s);
   if (cudaGetLastError() != cudaSuccess) return SQ_ECUDA;
   int st;
-  if ((st = launch_kb_dht<3, LD_RESID, SO_PLAIN, false>(b, 0, s)) != SQ_OK) return st;
-  if ((st = launch_kb_dht<2, LD_PLAIN, SO_PLAIN, false>(b, 0, s)) != SQ_OK) return st;
-  if ((st = launch_kb_dht<1, LD_PLAIN, SO_PLAIN, true>(b, 0, s)) != SQ_OK) return st;
-  if ((st = launch_kb_dht<2, LD_PLAIN, SO_PLAIN, false>(b, 0, s)) != SQ_OK) return st;
-  return launch_kb_dht<3, LD_PLAIN, SO_PCG, false>(b, 0, s);
+#define SQB_PROF(call)                       \
+  pi = profile_begin_batch_inner(s);         \
+  st = (call);                               \
+  profile_end(pi, s);                        \
+  if (st != SQ_OK) return st;
+  SQB_PROF((launch_kb_dht<3, LD_RESID, SO_PLAIN, false>(b, 0, s)));
+  SQB_PROF((launch_kb_dht<2, LD_PLAIN, SO_PLAIN, false>(b, 0, s)));
+  SQB_PROF((launch_kb_dht<1, LD_PLAIN, SO_PLAIN, true>(b, 0, s)));
+  SQB_PROF((launch_kb_dht<2, LD_PLAIN, SO_PLAIN, false>(b, 0, s)));
+  SQB_PROF((launch_kb_dht<3, LD_PLAIN, SO_PCG, false>(b, 0, s)));
+#undef SQB_PROF
+  return SQ_OK;
 }
 
 int capture_graph(sq_batch *b, cudaStream_t s) {
@@ -409,6 +420,7 @@ int capture_graph(sq_batch *b, cudaStream_t s) {
   cudaStream_t cs;
   SQB_CK(cudaStreamCreateWithFlags(&cs, cudaStreamNonBlocking));
   int st = SQ_OK;
+  profile_pause(true);  // no event records inside the capture
   if (cudaStreamBeginCapture(cs, cudaStreamCaptureModeThreadLocal) != cudaSuccess) st = SQ_ECUDA;
   for (int i = 0; st == SQ_OK && i < kChunk; ++i) st = iteration_b(b, cs);
   if (st == SQ_OK) {
@@ -422,6 +434,7 @@ int capture_graph(sq_batch *b, cudaStream_t s) {
   if (cudaStreamEndCapture(cs, &g) != cudaSuccess || !g) st = SQ_ECUDA;
   if (st == SQ_OK && cudaGraphInstantiate(&b->exec, g, 0) != cudaSuccess) st = SQ_ECUDA;
   b->graph = g;
+  profile_pause(false);
   cudaStreamDestroy(cs);
   (void)s;
   return st;
@@ -629,11 +642,21 @@ int sq_pcg_solve_batched(sq_batch *b, double tol, int max_iter, sq_solve_info *i
     kb_vec<1><<<b->tot_vec, kThreads, 0, s>>>(b->dS, pre_vec, count);
     SQB_CK(cudaGetLastError());
     if ((st = precond_first_b(b, s)) != SQ_OK) return st;
-    // inner iterations: graph chunks, polled one chunk behind
+    // inner iterations: graph chunks, polled one chunk behind (with the
+    // profile on: the same launches one by one, each and the loop timed)
     int launched = 0;
     bool pending = false;
+    const size_t ploop = profile_begin_batch_loop(s);
     while (launched < max_iter) {
-      SQB_CK(cudaGraphLaunch(b->exec, s));
+      if (profile_enabled()) {  // the graph's contents, launched one by one and timed by the profile
+        for (int i = 0; i < kChunk; ++i)
+          if ((st = iteration_b(b, s)) != SQ_OK) return st;
+        kb_count<<<1, kThreads, 0, s>>>(b->dS, b->count, 1, b->d_count);
+        SQB_CK(cudaGetLastError());
+        SQB_CK(cudaMemcpyAsync(b->h_count, b->d_count, sizeof(int), cudaMemcpyDeviceToHost, s));
+      } else {
+        SQB_CK(cudaGraphLaunch(b->exec, s));
+      }
       launched += kChunk;
       if (pending) {
         SQB_CK(cudaEventSynchronize(b->ev));
@@ -642,6 +665,7 @@ int sq_pcg_solve_batched(sq_batch *b, double tol, int max_iter, sq_solve_info *i
       SQB_CK(cudaEventRecord(b->ev, s));
       pending = true;
     }
+    profile_end(ploop, s);
     kb_vec<2><<<b->tot_vec, kThreads, 0, s>>>(b->dS, pre_vec, count);
     kb_accum_iters<<<tb, 128, 0, s>>>(b->dS, count, b->d_iters);
     SQB_CK(cudaGetLastError());

@@ -408,6 +408,15 @@ int set_strided_fast(int on);  // 0: generic Stockham tiles for every pass
 int set_use_gtab(int on);      // 0: pass C evaluates the multiplier on the fly everywhere
 int use_gtab();
 
+// solver.cu: the kernel-event profile (sq_profile_enable) as seen by batch.cu:
+// an event pair around a launch of the batch's inner iteration, or around a
+// whole inner loop (a no-op index when profiling is off), whether profiling is
+// on, and pausing it (true) and restoring it (false) around a graph capture.
+size_t profile_begin_batch_inner(cudaStream_t s);
+size_t profile_begin_batch_loop(cudaStream_t s);
+void profile_end(size_t i, cudaStream_t s);
+bool profile_enabled();
+bool profile_pause(bool pause);
 // solver.cu: read-only views of the opaque handles (used by batch.cu)
 int coeffs_view(const sq_coeffs *c, CellsDev *out);
 int precond_spec32(const sq_precond *p, SpectralDev *out, int *N);

@@ -69,11 +69,12 @@ namespace {
 // Optional CUDA-event pairs around every kernel launch, summed per class.
 enum ProfClass : int {
   PC_COEFF = 0, PC_MATVEC, PC_RESID, PC_DHT_A, PC_DHT_B, PC_DHT_C, PC_DHT_E, PC_VECTOR, PC_AHOM, PC_SCALAR,
-  PC_COUNT
+  PC_BATCH_INNER, PC_BATCH_LOOP, PC_COUNT
 };
 const char *const kProfNames[PC_COUNT] = {"coeff_gen",  "stencil_matvec", "stencil_resid_rhs", "dht_x3_in",
                                           "dht_x2",     "dht_x1_scale",   "dht_x3_out",        "vector",
-                                          "ahom",       "scalars"};
+                                          "ahom",       "scalars",        "batch_inner",
+                                          "batch_inner_loop"};
 struct Prof {
   bool on = false;
   std::vector<cudaEvent_t> pool;
@@ -619,6 +620,23 @@ int apply_precond_t(const sq_precond *pc, sq_workspace *w, const T *r, T *z, T *
 }  // namespace
 
 namespace sq {
+// The kernel-event profile for the batched solver (batch.cu): one class for
+// the kernels of its inner iterations, and a way to keep the profile out of a
+// graph capture.
+size_t profile_begin_batch_inner(cudaStream_t s) { return prof_begin(PC_BATCH_INNER, s); }
+size_t profile_begin_batch_loop(cudaStream_t s) { return prof_begin(PC_BATCH_LOOP, s); }
+void profile_end(size_t i, cudaStream_t s) { prof_end(i, s); }
+bool profile_enabled() { return g_prof.on; }
+bool profile_pause(bool pause) {
+  static bool saved = false;
+  if (pause) {
+    saved = g_prof.on;
+    g_prof.on = false;
+  } else {
+    g_prof.on = saved;
+  }
+  return saved;
+}
 static int g_inner_tol_exp = 5;
 int set_inner_tol_exp(int e) {
   if (e < 2 || e > 7) return 1;

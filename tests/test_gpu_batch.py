@@ -53,6 +53,19 @@ def test_mixed_size_batch_matches_oracle(sq):
     infos2 = sq.sq_pcg_solve_batched(b, 1e-10, 2000)
     for (c, i, psi), x1, i1, i2 in zip(descs, first, infos, infos2):
         assert np.array_equal(psi.cpu().numpy(), x1) and i1["iters"] == i2["iters"]
+    # with the kernel-event profile on, the graph's launches run one by one:
+    # the same result, and the profile sees 6 inner launches per iteration
+    sq.sq_profile_enable(True)
+    try:
+        infos3 = sq.sq_pcg_solve_batched(b, 1e-10, 2000)
+        prof = sq.sq_profile_read()
+    finally:
+        sq.sq_profile_enable(False)
+    for (c, i, psi), x1, i1, i3 in zip(descs, first, infos, infos3):
+        assert np.array_equal(psi.cpu().numpy(), x1) and i1["iters"] == i3["iters"]
+    ms, nl = prof["batch_inner"]
+    loop_ms, nloop = prof["batch_inner_loop"]
+    assert nl > 0 and nl % 6 == 0 and 0 < ms <= loop_ms and nloop == infos3[0]["outer_steps"]
 
 
 def test_batch_matches_single_solves(sq):

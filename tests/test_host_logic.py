@@ -136,6 +136,8 @@ def test_bench_batch_leg_on_fakes(monkeypatch):
         sq_batch_create=lambda descs, pl, tiles=None: calls.setdefault(tiles is not None, (list(descs), list(pl),
                                                                                           tiles)),
         sq_pcg_solve_batched=lambda b, tol, mi: [{"iters": 20, "status": 0} for _ in b[0]],
+        sq_profile_enable=lambda on: None,
+        sq_profile_read=lambda: {"batch_inner": (200.0, 600), "batch_inner_loop": (230.0, 3)},
     )
     fake_torch = types.SimpleNamespace(
         float64="f64", empty=lambda n, dtype=None, device=None: Buf(n),
@@ -152,6 +154,9 @@ def test_bench_batch_leg_on_fakes(monkeypatch):
     assert abs(out["algorithmic_GBps"] - want / 0.25 / 1e9) <= 0.05
     assert 0 < out["hbm_frac"] < 10 and "L2" in out["algorithmic_note"]
     assert out["working_set_GB"] == round(sum(20 * N ** 3 for N in Ns) / 1e9, 2)
+    # every fake solve takes 250 ms; the profiled one spends 230 ms in its inner
+    # loops, of which 200 ms in kernels: the graph's inner loops take 230 ms
+    assert out["inner_loop"]["graph_loop_s"] == 0.23 and out["inner_loop"]["busy_frac"] == round(0.2 / 0.23, 4)
 
 
 def test_bench_roofline_selection():
