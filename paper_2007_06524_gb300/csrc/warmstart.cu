@@ -17,8 +17,12 @@
 //    pre-activation and activation), bias only (FP32 output channels), or
 //    plain (data gradient). The data gradient of a layer is the same
 //    convolution with the weights flipped in space and transposed in channels.
-//  * conv_in (layer 1, one input channel) and the weight gradients run on the
-//    FP32 pipes (SIMT); weight gradients are reduced deterministically.
+//  * dw_mma: weight gradients of the 32-channel layers on the tensor cores
+//    (mma.sync m16n8k16, operands gathered from channel-last tiles by
+//    transposing ldmatrix, one block per (voxel chunk, dz) with its nine taps).
+//  * conv_in (layer 1, one input channel), its weight gradient and the bias
+//    gradients run on the FP32 pipes (SIMT); every weight gradient is reduced
+//    over the chunks in a fixed order (deterministic).
 #include <cmath>
 #include <cstring>
 #include <new>
@@ -310,11 +314,12 @@ __global__ void k_gelu_bwd(const __nv_bfloat16 *__restrict__ ga, const __nv_bflo
 // G: BF16 [B][N3][CGS], CG real channels.
 template <int CA, int CG>
 __global__ void __launch_bounds__(256) k_dw(const void *__restrict__ A, const __nv_bfloat16 *__restrict__ G, int CGS,
-                                            int N, long long total, int chunk, float *__restrict__ partials) {
+                                            int N, long long total, int chunk, float *__restrict__ partials,
+                                            int tap0) {
   constexpr int V = 64;
   __shared__ float sa[V][CA + 1];
   __shared__ float sg[V][CG + 1];
-  const int tap = blockIdx.y;
+  const int tap = tap0 + blockIdx.y;
   const long long v0 = (long long)blockIdx.x * chunk;
   const long long v1 = (v0 + chunk < total) ? v0 + chunk : total;
   const size_t N3 = (size_t)N * N * N;
@@ -367,6 +372,115 @@ __global__ void __launch_bounds__(256) k_dw(const void *__restrict__ A, const __
   for (int k = 0; k < PER; ++k) {
     const int o = threadIdx.x + k * 256;
     if (o < NOUT) partials[((size_t)blockIdx.x * 28 + tap) * NOUT + o] = acc[k];
+  }
+}
+
+__device__ __forceinline__ unsigned smem_addr(const void *p) { return (unsigned)__cvta_generic_to_shared(p); }
+// Four (two) 8 x 8 b16 matrices from shared memory, transposed: row addresses
+// from lanes 0-31 (0-15), 16-byte aligned.
+__device__ __forceinline__ void ldsm_x4_t(uint32_t (&r)[4], unsigned addr) {
+  asm volatile("ldmatrix.sync.aligned.m8n8.x4.trans.shared.b16 {%0,%1,%2,%3}, [%4];\n"
+               : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3])
+               : "r"(addr));
+}
+__device__ __forceinline__ void ldsm_x2_t(uint32_t (&r)[2], unsigned addr) {
+  asm volatile("ldmatrix.sync.aligned.m8n8.x2.trans.shared.b16 {%0,%1}, [%2];\n" : "=r"(r[0]), "=r"(r[1]) : "r"(addr));
+}
+
+// Weight gradient on the tensor cores (layers with 32 input channels):
+// dW[tap][co][ci] = sum_v G[v][co] A[v + off_tap][ci], one GEMM per tap with
+// M = co, N = ci and K running over the voxels of the chunk (mma.sync m16n8k16
+// BF16, FP32 accumulate). blockIdx.y fixes dz; the block's nine taps (dy, dx)
+// share each staged tile. A tile is TY = 4 consecutive x-rows of one plane of
+// G (CGM of its CGS channels) and the TY + 2 rows of A around it (plane
+// z + dz, periodic), in shared memory with rows padded to 80 (48) bytes so the
+// transposing ldmatrix reads are conflict-free. Both operands arrive
+// channel-last, so the K pairs of a fragment (two voxels) are gathered by
+// ldmatrix .trans; a shifted tap is only a different row address per lane
+// (the x wrap included). Warp w owns the fragments f = w + 8 j of the block's
+// 9 x NP (m-tile, n-tile) pairs. Partials go to the layout of k_dw
+// (chunk, tap, co, ci) for the same fixed-order reduction.
+template <int CGM>
+__global__ void __launch_bounds__(256) k_dw_mma(const __nv_bfloat16 *__restrict__ A,
+                                                const __nv_bfloat16 *__restrict__ G, int CGS, int CG, int N,
+                                                long long total, int chunk, float *__restrict__ partials) {
+  constexpr int TY = 4;
+  constexpr int SA = 40;        // bf16 per staged A row (32 + 8)
+  constexpr int SG = CGM + 8;   // bf16 per staged G row
+  constexpr int NP = (CGM / 16) * 4;
+  constexpr int F = 9 * NP;
+  constexpr int J = (F + 7) / 8;
+  extern __shared__ __align__(16) __nv_bfloat16 smw[];
+  const int TN = TY * N;
+  __nv_bfloat16 *sg = smw;                    // [TN][SG]
+  __nv_bfloat16 *sa = smw + (size_t)TN * SG;  // [(TY + 2) N][SA]
+  const int dz = (int)blockIdx.y - 1;
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  const int pair = warp % NP, mt = pair / 4, nt = pair % 4;
+  const size_t N3 = (size_t)N * N * N;
+  float acc[J][4];
+#pragma unroll
+  for (int j = 0; j < J; ++j)
+#pragma unroll
+    for (int i = 0; i < 4; ++i) acc[j][i] = 0.f;
+  const long long v0 = (long long)blockIdx.x * chunk;
+  const long long v1 = (v0 + chunk < total) ? v0 + chunk : total;
+  for (long long vt = v0; vt < v1; vt += TN) {
+    const long long smp = vt / (long long)N3;
+    const size_t vox0 = (size_t)(vt - smp * (long long)N3);
+    const int z = (int)(vox0 / ((size_t)N * N)), y0 = (int)((vox0 / N) % N);
+    __syncthreads();  // the previous tile's fragments are read
+    for (int e = threadIdx.x; e < TN * (CGM / 8); e += 256) {
+      const int v = e / (CGM / 8), c8 = e - v * (CGM / 8);
+      *reinterpret_cast<uint4 *>(sg + (size_t)v * SG + c8 * 8) =
+          *reinterpret_cast<const uint4 *>(G + (size_t)(vt + v) * CGS + c8 * 8);
+    }
+    const int za = wrap(z + dz, N);
+    for (int e = threadIdx.x; e < (TY + 2) * N * 4; e += 256) {
+      const int v = e >> 2, c8 = e & 3;
+      const int rr = v / N, x = v - rr * N;
+      const int ya = wrap(y0 - 1 + rr, N);
+      *reinterpret_cast<uint4 *>(sa + (size_t)v * SA + c8 * 8) = *reinterpret_cast<const uint4 *>(
+          A + ((size_t)smp * N3 + ((size_t)za * N + ya) * N + x) * 32 + c8 * 8);
+    }
+    __syncthreads();
+    for (int kv0 = 0; kv0 < TN; kv0 += 16) {  // 16 voxels of one row (16 | N)
+      const int ry = kv0 / N, x0 = kv0 - ry * N;
+      uint32_t af[4];
+      {
+        const int q = lane >> 3, r = lane & 7;
+        ldsm_x4_t(af, smem_addr(sg + (size_t)(kv0 + r + 8 * (q >> 1)) * SG + mt * 16 + 8 * (q & 1)));
+      }
+      const int kk = lane & 15;
+#pragma unroll
+      for (int j = 0; j < J; ++j) {
+        const int f = warp + 8 * j;
+        if (f < F) {
+          const int t9 = f / NP, dy = t9 / 3 - 1, dx = t9 % 3 - 1;
+          const int xs = wrap(x0 + kk + dx, N);
+          uint32_t bf[2];
+          ldsm_x2_t(bf, smem_addr(sa + (size_t)((ry + 1 + dy) * N + xs) * SA + nt * 8));
+          mma16816(acc[j], af, bf);
+        }
+      }
+    }
+  }
+  const int g = lane >> 2, t4 = lane & 3;
+  const int nout = CG * 32;
+#pragma unroll
+  for (int j = 0; j < J; ++j) {
+    const int f = warp + 8 * j;
+    if (f >= F) continue;
+    const int tap = (dz + 1) * 9 + f / NP;
+    float *pp = partials + ((size_t)blockIdx.x * 28 + tap) * nout;
+#pragma unroll
+    for (int h = 0; h < 2; ++h) {
+      const int co = mt * 16 + g + 8 * h, ci = nt * 8 + 2 * t4;
+      if (co < CG) {
+        pp[co * 32 + ci] = acc[j][2 * h];
+        pp[co * 32 + ci + 1] = acc[j][2 * h + 1];
+      }
+    }
   }
 }
 
@@ -508,7 +622,19 @@ int weight_grad(sq_net *net, int B, const void *A, const __nv_bfloat16 *G, int C
   const long long tot = (long long)B * N * N * N;
   const int nchunk = (int)((tot + net->chunk - 1) / net->chunk);
   if (nchunk > net->nchunk) return SQ_EINVAL;
-  k_dw<CA, CG><<<dim3(nchunk, 28), 256, 0, s>>>(A, G, CGS, N, tot, net->chunk, net->d_dwpart);
+  if constexpr (CA == 32) {
+    // taps on the tensor cores, the bias (tap 27) on the FP32 pipe
+    constexpr int CGM = CG > 16 ? 32 : 16;
+    const size_t smem = ((size_t)4 * N * (CGM + 8) + (size_t)6 * N * 40) * sizeof(__nv_bfloat16);
+    auto kern = k_dw_mma<CGM>;
+    SQN_CK(cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+    kern<<<dim3(nchunk, 3), 256, smem, s>>>(reinterpret_cast<const __nv_bfloat16 *>(A), G, CGS, CG, N, tot,
+                                            net->chunk, net->d_dwpart);
+    SQN_CK(cudaGetLastError());
+    k_dw<CA, CG><<<dim3(nchunk, 1), 256, 0, s>>>(A, G, CGS, N, tot, net->chunk, net->d_dwpart, 27);
+  } else {
+    k_dw<CA, CG><<<dim3(nchunk, 28), 256, 0, s>>>(A, G, CGS, N, tot, net->chunk, net->d_dwpart, 0);
+  }
   SQN_CK(cudaGetLastError());
   const int nout = CG * CA;
   k_dw_reduce<<<(28 * nout + 255) / 256, 256, 0, s>>>(net->d_dwpart, nchunk, nout, CA, net->d_g + net->woff[layer],
