@@ -203,10 +203,11 @@ def _algorithmic(N, elem, rank_r, table=None):
 
 
 # dram__bytes_read.sum + dram__bytes_write.sum of one launch (ncu --set full,
-# N = 256, rank 8): profiles/dht_x1_scale_fp64_n256.md and
-# profiles/dht_x3_pass_e_fp32_n256.md. Part of each kernel's writes is still in
-# L2 when it ends, so traffic can read below the algorithmic bytes.
-PROFILED_TRAFFIC = {("dht_x3_out", 4): 201.36e6 + 76.13e6}
+# N = 256, rank 8): profiles/dht_x1_scale_fp64_n256.md (multiplier table) and
+# profiles/dht_x3_pass_e_fp32_n256.md (8-pencil tiles). Part of each kernel's
+# writes is still in L2 when it ends, so traffic can read below the
+# algorithmic bytes.
+PROFILED_TRAFFIC = {("dht_x1_scale", 8): 159.88e6 + 74.97e6, ("dht_x3_out", 4): 201.35e6 + 76.39e6}
 
 
 def kernel_table(work, prof, N, elem, R, t_ms, peaks=None):
