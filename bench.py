@@ -642,7 +642,7 @@ def run_warm_start(sq, torch, nseeds=512):
     net = warmstart.load(warmstart.DEFAULT_WEIGHTS)
     seeds = wl["eval_seeds"][:nseeds]
     res = {"eval_seeds": f"{seeds[0]}..{seeds[-1]} ({len(seeds)})"}
-    res["fp32_refine"] = warmstart.evaluate(torch, wl, net, seeds, sq.SQ_FP32_REFINE)
+    res["fp32_refine"] = warmstart.evaluate(torch, wl, net, seeds, sq.SQ_FP32_REFINE, quality=False)
     res["fp64"] = warmstart.evaluate(torch, wl, net, seeds, sq.SQ_FP64)
     base = res["fp64"]["zero"]["solves_per_s"]
     res["summary"] = {"seeds": len(seeds), "plain_fp64_zero": base,
@@ -651,7 +651,8 @@ def run_warm_start(sq, torch, nseeds=512):
                       "fp32_refine_learned": res["fp32_refine"]["learned"]["solves_per_s"],
                       "iters_fp64_zero_learned": [res["fp64"]["zero"]["iters_mean"], res["fp64"]["learned"]["iters_mean"]],
                       "iters_fp32_zero_learned": [res["fp32_refine"]["zero"]["iters_mean"],
-                                                  res["fp32_refine"]["learned"]["iters_mean"]]}
+                                                  res["fp32_refine"]["learned"]["iters_mean"]],
+                      "guess": res["fp64"].get("guess_quality")}
     return res
 
 

@@ -373,8 +373,11 @@ int sq_net_predict(sq_net *net, const sq_coeffs *c, double *psi0, double *psi1, 
  * (device, N^3 doubles: psi_i of sample b) for the `batch` realizations
  * cs[b], with e = (prediction - target) / out_scale and loss_type 0: mean of
  * e^2; 1: mean of e . A e (the energy norm of the error under each sample's
- * own operator -- the norm PCG reduces). *loss (host, may be NULL) receives
- * that loss for the forward pass (synchronizes `stream`). */
+ * own operator -- the norm PCG reduces); 2: mean of r . r with r =
+ * (A prediction - b_i) / out_scale (the residual norm the solver's stopping
+ * rule measures; the targets are not read, but must be valid pointers).
+ * *loss (host, may be NULL) receives that loss for the forward pass
+ * (synchronizes `stream`). */
 int sq_net_train_step(sq_net *net, int batch, const sq_coeffs *const *cs, const double *const *targets,
                       float lr, int loss_type, double *loss, sq_stream_t stream);
 

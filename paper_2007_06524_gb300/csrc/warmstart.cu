@@ -263,6 +263,12 @@ __global__ void k_err(const float *__restrict__ y, const float *__restrict__ tgt
   if (i < n) e[i] = (y[i] - tgt[i]) * inv_scale;
 }
 
+// r = (a - b) * s, FP32 fields
+__global__ void k_sub_scale(const float *__restrict__ a, float *__restrict__ b, float s, long long n) {
+  const long long i = blockIdx.x * 256LL + threadIdx.x;
+  if (i < n) b[i] = (a[i] - b[i]) * s;
+}
+
 // per-block partial sums of a . b (fixed order inside the block)
 __global__ void __launch_bounds__(256) k_dot_partial(const float *__restrict__ a, const float *__restrict__ b,
                                                      double *__restrict__ partials, long long n) {
@@ -825,7 +831,7 @@ int sq_net_predict(sq_net *net, const sq_coeffs *c, double *psi0, double *psi1, 
 int sq_net_train_step(sq_net *net, int batch, const sq_coeffs *const *cs, const double *const *targets, float lr,
                       int loss_type, double *loss, sq_stream_t stream) {
   if (!net || !cs || !targets || batch < 1 || batch > net->max_batch || !(lr > 0.f) || loss_type < 0 ||
-      loss_type > 1)
+      loss_type > 2)
     return SQ_EINVAL;
   cudaStream_t s = reinterpret_cast<cudaStream_t>(stream);
   const long long N3 = (long long)net->N * net->N * net->N;
@@ -845,6 +851,37 @@ int sq_net_train_step(sq_net *net, int batch, const sq_coeffs *const *cs, const 
     lblocks = (int)((tot + 255) / 256);
     k_loss_grad<<<lblocks, 256, 0, s>>>(net->d_y, net->d_t, net->d_g6, (float)(1.0 / net->out_scale),
                                         net->d_lpart, N3, batch);
+    SQN_CK(cudaGetLastError());
+  } else if (loss_type == 2) {
+    // residual norm of the guess: L = sum_i r_i . r_i, r = (A y - b_i) / out_scale
+    // (the norm the solver's stopping rule measures; no targets needed), with
+    // dL/d(conv6 out) = 2 A r (A is symmetric)
+    const long long n = 3 * tot;
+    RedBuf rb;
+    rb.st = net->d_st;
+    rb.partials = net->d_partials;
+    for (int b = 0; b < batch; ++b) {
+      CellsDev c;
+      if (coeffs_view(cs[b], &c) != SQ_OK) return SQ_EINVAL;
+      for (int i = 0; i < 3; ++i) {
+        const long long o = (3LL * b + i) * N3;
+        SQN_CK((launch_stencil<float, float>(c, ST_MATVEC, 0, net->d_y + o, net->d_ae + o, rb, FIN_NONE, false, s)));
+        SQN_CK((launch_stencil<double, float>(c, ST_RHS, i, nullptr, net->d_e + o, rb, FIN_NONE, false, s)));
+      }
+    }
+    k_sub_scale<<<(unsigned)((n + 255) / 256), 256, 0, s>>>(net->d_ae, net->d_e, (float)(1.0 / net->out_scale), n);
+    SQN_CK(cudaGetLastError());
+    for (int b = 0; b < batch; ++b) {
+      CellsDev c;
+      if (coeffs_view(cs[b], &c) != SQ_OK) return SQ_EINVAL;
+      for (int i = 0; i < 3; ++i) {
+        const long long o = (3LL * b + i) * N3;
+        SQN_CK((launch_stencil<float, float>(c, ST_MATVEC, 0, net->d_e + o, net->d_ae + o, rb, FIN_NONE, false, s)));
+      }
+    }
+    lblocks = (int)((n + 255) / 256);
+    k_dot_partial<<<lblocks, 256, 0, s>>>(net->d_e, net->d_e, net->d_lpart, n);
+    k_pack_grad<<<(unsigned)((tot + 255) / 256), 256, 0, s>>>(net->d_ae, net->d_g6, N3, batch);
     SQN_CK(cudaGetLastError());
   } else {
     // energy norm of the error: L = sum_i e_i . A e_i, e = (y - t) / out_scale,

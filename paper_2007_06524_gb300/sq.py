@@ -557,7 +557,8 @@ def sq_net_predict(net: Net, c, psi0, psi1, psi2, stream=None):
 
 def sq_net_train_step(net: Net, coeffs, targets, lr, stream=None, loss_type=0) -> float:
     """coeffs: list of B Coeffs; targets: list of B triples of float64 CUDA
-    tensors (psi_1..3); loss_type 0 = squared error, 1 = energy norm e.Ae.
+    tensors (psi_1..3); loss_type 0 = squared error, 1 = energy norm e.Ae, 2 = residual
+    norm of the prediction (targets not read).
     Returns the loss of the forward pass."""
     B = len(coeffs)
     carr = (C.c_void_p * B)(*[c.ptr.value for c in coeffs])

@@ -23,7 +23,8 @@ def main():
     ap.add_argument("--batch", type=int, default=8)
     ap.add_argument("--lr", type=float, default=2e-3)
     ap.add_argument("--out", default=None)
-    ap.add_argument("--loss", type=int, default=1, help="0: squared error, 1: energy norm e.Ae")
+    ap.add_argument("--loss", type=int, default=1,
+                    help="0: squared error, 1: energy norm e.Ae, 2: residual norm |A y - b|^2")
     args = ap.parse_args()
     import numpy as np
     import torch

@@ -46,8 +46,8 @@ def generate_targets(torch, wl, seeds, chunk=256, tol=1e-10, stream=None):
 
 
 def train(torch, wl, targets, seeds, epochs=4, batch=8, lr=2e-3, seed=1, log_every=0, stream=None, loss_type=1):
-    """Adam on the energy norm of the error (loss_type 1; 0 = squared error);
-    returns (net, losses, seconds)."""
+    """Adam on the energy norm of the error (loss_type 1; 0 = squared error,
+    2 = residual norm of the prediction); returns (net, losses, seconds)."""
     L, n = wl["L"], wl["n"]
     N = L * n
     scale = float(targets.std())
@@ -86,7 +86,7 @@ def load(path, batch=1):
     return net
 
 
-def evaluate(torch, wl, net, seeds, precision, tol=1e-8, stream=None):
+def evaluate(torch, wl, net, seeds, precision, tol=1e-8, stream=None, quality=True):
     """Zero start vs learned start on the given seeds: per-solve iterations and
     solves/s of each (the learned figure includes the net's inference)."""
     L, n = wl["L"], wl["n"]
@@ -115,4 +115,36 @@ def evaluate(torch, wl, net, seeds, precision, tol=1e-8, stream=None):
         res[mode] = {"solves_per_s": round(3 * len(seeds) / dt, 2), "iters_mean": round(float(np.mean(its)), 2),
                      "iters_p50": float(np.percentile(its, 50)), "iters_p99": float(np.percentile(its, 99)),
                      "guesses_kept": used}
+    if quality:
+        res["guess_quality"] = guess_quality(torch, wl, net, seeds, stream)
     return res
+
+
+def guess_quality(torch, wl, net, seeds, stream=None, tol=1e-10):
+    """How good the learned guess x0 is before any iteration (untimed): the
+    mean over seeds and correctors of ||b - A x0|| / ||b|| (the stopping
+    rule's norm; zero start gives 1) and of the relative energy-norm error
+    sqrt(e.Ae / psi.b), e = x0 - psi, psi the solve's result (zero start
+    gives 1). Operator, right-hand side and solve run in libsq; the norms
+    and dot products of the resulting fields are taken with torch."""
+    L, n = wl["L"], wl["n"]
+    N = L * n
+    pc = _sq.sq_precond_setup(N, 0)
+    w = _sq.sq_workspace_create(N, _sq.SQ_FP64)
+    c = _sq.sq_build_coeffs(L, n, seeds[0], wl["p_hi"], wl["a_lo"], wl["a_hi"])
+    g = [torch.empty(N ** 3, dtype=torch.float64, device="cuda") for _ in range(3)]
+    psi, b, ax = (torch.empty(N ** 3, dtype=torch.float64, device="cuda") for _ in range(3))
+    rr, ee = [], []
+    for sd in seeds:
+        _sq.sq_coeffs_regenerate(c, sd, wl["p_hi"], stream)
+        _sq.sq_net_predict(net, c, *g, stream=stream)
+        for i in range(3):
+            _sq.sq_rhs(c, i, b, stream)
+            _sq.sq_apply_operator(c, g[i], ax, stream)
+            rr.append(float(torch.linalg.norm(b - ax) / torch.linalg.norm(b)))
+            _sq.sq_pcg_solve(c, pc, w, i, tol, 4000, _sq.SQ_FP64, None, psi, stream)
+            e = g[i] - psi
+            _sq.sq_apply_operator(c, e.contiguous(), ax, stream)
+            ee.append(float(torch.sqrt(torch.dot(e, ax) / torch.dot(psi, b))))
+    return {"init_relres_mean": round(float(np.mean(rr)), 4), "init_relres_max": round(float(np.max(rr)), 4),
+            "energy_err_mean": round(float(np.mean(ee)), 4), "samples": len(rr)}

@@ -185,3 +185,33 @@ def test_energy_loss_value_matches_oracle_operator(sq):
         ref += float(np.sum(e * assembly.apply_stencil(a, e)))
     ref /= 3 * N ** 3
     assert abs(loss - ref) <= 1e-2 * abs(ref), (loss, ref)
+
+
+def test_residual_loss_value_matches_oracle_operator(sq):
+    """loss_type 2 reports mean(r . r) with r = (A prediction - b_i)/out_scale,
+    the residual norm of the guess (targets not read); checked with the
+    oracle's operator and right-hand sides. One training step with it moves
+    the weights."""
+    import torch
+
+    from oracle import assembly, rng
+
+    L, n, seed = 8, 4, 32
+    N = L * n
+    scale = 1.3
+    net = sq.sq_net_create(N, 1, seed=9, out_scale=scale)
+    p0 = sq.sq_net_params(net)
+    c = sq.sq_build_coeffs(L, n, seed, 0.5, 1.0, 10.0)
+    g = [torch.empty(N ** 3, dtype=torch.float64, device="cuda") for _ in range(3)]
+    sq.sq_net_predict(net, c, *g)
+    dummy = [torch.zeros(N ** 3, dtype=torch.float64, device="cuda") for _ in range(3)]
+    loss = sq.sq_net_train_step(net, [c], [dummy], 1e-3, loss_type=2)
+    a = assembly.edge_coefficients(rng.cell_values(rng.cell_phases(L, seed), 1.0, 10.0), n)
+    ref = 0.0
+    for i in range(3):
+        y = g[i].cpu().numpy().reshape(N, N, N)
+        r = (assembly.apply_stencil(a, y).ravel() - assembly.rhs(a, i)) / scale
+        ref += float(r @ r)
+    ref /= 3 * N ** 3
+    assert abs(loss - ref) <= 1e-2 * abs(ref), (loss, ref)
+    assert np.abs(sq.sq_net_params(net) - p0).max() > 0
