@@ -166,8 +166,8 @@ void sq_coeffs_destroy(sq_coeffs *c);
  * factor of its QR decomposition has a diagonal spread of at most 1e10); the
  * balanced trapezoid rule is used above R = 32 and wherever no fit beats it.
  * Factors and twiddles are built on the host in FP64 and copied to the
- * current device; for N <= 256 the FP64 multiplier table of
- * SQ_OPT_MULTIPLIER_TABLE is built there too (synchronous). */
+ * current device; for N <= 256 the multiplier tables of
+ * SQ_OPT_MULTIPLIER_TABLE are built there too (synchronous). */
 int sq_precond_setup(int N, int rank, sq_precond **out);
 /* The exponential-sum nodes t[r] and weights w[r], r < rank (host arrays,
  * either may be NULL; nothing is written for rank 0). SQ_EINVAL for a
@@ -289,11 +289,13 @@ int sq_set_tiles(const sq_tile_config *tiles, int ntiles);
  * stops staging; 0 gives up at once. The block still waits (up to 2^24 polls)
  * for its copies in flight before it exits. 0 <= value <= 2^24.
  * SQ_OPT_MULTIPLIER_TABLE (default 1): preconditioners of grids N <= 256 carry
- * their multiplier G tabulated on the mirror-reduced modes, (N/2 + 1)^3 FP64
- * values (built on the device by sq_precond_setup* from the same factors),
- * and the FP64 x1 pass reads G from it instead of summing the canonical terms
- * (or dividing, for the exact diagonal) per mode; 0 evaluates G on the fly.
- * FP32 passes always evaluate it on the fly. Results agree to rounding.
+ * their multiplier G tabulated (built on the device by sq_precond_setup* from
+ * the same factors, summed in FP64): (N/2 + 1)^3 FP64 values on the
+ * mirror-reduced modes, and an FP32 copy of (N/2 + 1)^2 N values. The x1 pass
+ * of single solves reads G from it (FP32: each tile's slice prefetched into
+ * shared memory) instead of summing the canonical terms (or dividing, for the
+ * exact diagonal) per mode; 0 evaluates G on the fly. Batches always
+ * evaluate it on the fly. Results agree to rounding.
  */
 enum sq_option {
   SQ_OPT_STRIDED_TWO_STAGE = 1,

@@ -135,9 +135,7 @@ __device__ __forceinline__ void kb_tile(const BSolve &B, const DhtTile<float> &t
     x3_stage2<float, float2, R0, R1, P>(sm, tw);
     x3_combine<float, float2, R0 * R1, P, STOREM>(t, row0, sm);
   } else if constexpr (SCALE) {
-    if (B.sp.gtab)
-      dht_tile_s2<float, AXIS, R0, R1, P, true, -2>(B.sp, t, tile, sm, tw, vtab, acc);
-    else if (B.sp.rank == 0)
+    if (B.sp.rank == 0)
       dht_tile_s2<float, AXIS, R0, R1, P, true, 0>(B.sp, t, tile, sm, tw, vtab, acc);
     else
       dht_tile_s2<float, AXIS, R0, R1, P, true, -1>(B.sp, t, tile, sm, tw, vtab, acc);
@@ -489,7 +487,7 @@ int sq_batch_create(int count, const sq_solve_desc *descs, const sq_precond *con
     B.dir = descs[k].dir;
     B.x = descs[k].psi;
     B.sp = sp;
-    if (!use_gtab()) B.sp.gtab = nullptr;
+    B.sp.gtab = nullptr;  // the batch evaluates the multiplier on the fly (its shared memory has no table slot)
     const int N = cv.N;
     int P = dht_tile_pencils(N, 4);
     int zc = std::max(2, N / 4);

@@ -378,14 +378,15 @@ struct SpectralDev {
   // (u(k) = u(N - k)): G is then diagonal in the separable Hartley basis.
   const void *u;
   double scale;      // 1 / (64 N^3) for the exact diagonal
-  // The multiplier itself, tabulated (T): G(m1, m2, m3) at
-  // gtab[(m1 H + m2) H + m3], H = N/2 + 1, m = min(k, N - k) per axis (G is
-  // even in each index), G(0,0,0) = 0, scale folded in as above. nullptr:
-  // pass C evaluates G from lam or u on the fly.
+  // The multiplier itself, tabulated (T), scale folded in as above, G(0,0,0) =
+  // 0, with m = min(k, N - k) (G is even in each index) and H = N/2 + 1:
+  // FP64 at gtab[(m1 H + m2) H + m3]; FP32 at gtab[(m1 H + m2) N + k3] (the
+  // x3 index unreduced, so that a tile's 2P columns are one aligned run).
+  // nullptr: pass C evaluates G from lam or u on the fly.
   const void *gtab = nullptr;
 };
-// Grids up to this size carry the FP64 multiplier table (17 MB at N = 256,
-// resident in L2 while pass C reads it).
+// Grids up to this size carry the multiplier tables (FP64 17 MB, FP32 17 MB
+// at N = 256, resident in L2 while pass C reads them).
 constexpr int kGtabMaxN = 256;
 __host__ __device__ constexpr int mirror_index(int k, int N) { return k <= N - k ? k : N - k; }
 enum DhtPass : int { PASS_A_RESID = 0, PASS_A_PLAIN = 1, PASS_B = 2, PASS_C = 3, PASS_E_PCG = 4, PASS_E_PLAIN = 5 };

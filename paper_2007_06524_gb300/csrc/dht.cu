@@ -137,8 +137,9 @@ __global__ void __launch_bounds__(kThreads, s2_min_blocks(R0 * R1, false)) k_dht
 
 template <int AXIS, int R0, int R1, int P, bool SCALE, int RR>
 static cudaError_t launch_s2(const DhtArgs<float> &a, int grid, cudaStream_t s) {
+  const size_t vtab = (RR == -2) ? (size_t)(R0 * R1 / 2 + 1) * 2 * P : (size_t)a.sp.rank * 2 * P;
   const size_t smem = (size_t)R0 * R1 * (P + 1) * sizeof(float2) + (size_t)R0 * R1 * sizeof(float2) +
-                      (size_t)a.sp.rank * 2 * P * sizeof(float);
+                      vtab * sizeof(float);
   auto kern = k_dht_s2<AXIS, R0, R1, P, SCALE, RR>;
   cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
   if (e != cudaSuccess) return e;

@@ -323,11 +323,18 @@ __device__ __forceinline__ void dht_tile(const SpectralDev &sp, const DhtTile<T>
       if (SCALE) {  // pass C: the Fourier-domain scaling described at s2_combine
         const int k3a = c0 + 2 * p, k3b = k3a + 1;
         T ga, gb;
-        if (sp.gtab) {  // tabulated multiplier (k <= N/2 here)
+        if (sp.gtab) {  // tabulated multiplier (k <= N/2 here; FP64 (m1, m2, m3), FP32 (m1, m2, k3))
           const int H = (N >> 1) + 1;
-          const T *row = reinterpret_cast<const T *>(sp.gtab) + ((size_t)k * H + mirror_index(k2, N)) * H;
-          ga = row[mirror_index(k3a, N)];
-          gb = row[mirror_index(k3b, N)];
+          const T *tab = reinterpret_cast<const T *>(sp.gtab);
+          if (sizeof(T) == 8) {
+            const T *row = tab + ((size_t)k * H + mirror_index(k2, N)) * H;
+            ga = row[mirror_index(k3a, N)];
+            gb = row[mirror_index(k3b, N)];
+          } else {
+            const T *row = tab + ((size_t)k * H + mirror_index(k2, N)) * N;
+            ga = (k == 0 && k2 == 0 && k3a == 0) ? (T)0 : row[k3a];
+            gb = row[k3b];
+          }
         } else if (R == 0) {
           const T l12 = lam[k] + lam[k2];
           const T g1 = l12 + lam[k3a], g2 = l12 + lam[k3b];
@@ -477,7 +484,8 @@ __device__ __forceinline__ void s2_stage2(C *sm, const C *__restrict__ tw) {
 // Multiplier G at (k, k2, k3a) and (k, k2, k3a + 1), k3a = c0 + 2p: exact
 // (RR = 0), rank RR with the column factors va/vb of this thread's pencil in
 // registers (RR > 0), a runtime rank (RR = -1, factors read from vtab), or
-// read from the tabulated multiplier (RR = -2, sp.gtab; k <= N/2 here).
+// read from the tile's slice of the FP32 multiplier table that dht_tile_s2
+// prefetched into vtab (RR = -2: row k <= N/2, the tile's 2P columns).
 template <typename T, int N, int P, int RR>
 __device__ __forceinline__ void s2_multiplier(const SpectralDev &sp, int k, int k2, int c0, int p, const T *vtab,
                                               const T (&va)[RR > 0 ? RR : 1], const T (&vb)[RR > 0 ? RR : 1],
@@ -486,10 +494,9 @@ __device__ __forceinline__ void s2_multiplier(const SpectralDev &sp, int k, int 
   const T *uf = reinterpret_cast<const T *>(sp.u);
   const int k3a = c0 + 2 * p;
   if constexpr (RR == -2) {
-    constexpr int H = N / 2 + 1;
-    const T *row = reinterpret_cast<const T *>(sp.gtab) + ((size_t)k * H + mirror_index(k2, N)) * H;
-    ga = row[mirror_index(k3a, N)];
-    gb = row[mirror_index(k3a + 1, N)];
+    const T *tt = vtab + (size_t)k * 2 * P + 2 * p;
+    ga = (k == 0 && k2 == 0 && k3a == 0) ? (T)0 : tt[0];
+    gb = tt[1];
   } else if constexpr (RR == 0) {
     const T gscale = (T)sp.scale;
     const T l12 = lam[k] + lam[k2];
@@ -587,6 +594,20 @@ __device__ __forceinline__ void dht_tile_s2(const SpectralDev &sp, const DhtTile
   const size_t base = (AXIS == 2) ? (size_t)line * NN + c0 : (size_t)line * N + c0;
   const int k2 = line;
   __syncthreads();
+  if constexpr (SCALE && RR == -2) {
+    // the tile's slice of the multiplier table, rows m1 = 0..N/2 of its 2P
+    // columns at (m2 = mirror(k2), k3 = c0 ..), fetched while the first
+    // transform runs (16-byte cp.async; waited for before stage 2)
+    constexpr int H = N / 2 + 1, CH = 2 * P / 4;
+    const T *gt = reinterpret_cast<const T *>(sp.gtab) + (size_t)mirror_index(k2, N) * N + c0;
+    for (int e = threadIdx.x; e < H * CH; e += kThreads) {
+      const int m1 = e / CH, ch = e - m1 * CH;
+      const unsigned dst = (unsigned)__cvta_generic_to_shared(vtab + (size_t)m1 * 2 * P + 4 * ch);
+      const T *src = gt + (size_t)m1 * H * N + 4 * ch;
+      asm volatile("cp.async.cg.shared.global [%0], [%1], 16;\n" ::"r"(dst), "l"(src) : "memory");
+    }
+    asm volatile("cp.async.commit_group;\n" ::: "memory");
+  }
   if (SCALE && RR != 0 && RR != -2) {
     const T *uf = reinterpret_cast<const T *>(sp.u);
     const T *u2 = uf + (size_t)sp.rank * N, *u3 = uf + 2 * (size_t)sp.rank * N;  // x2, x3 factors
@@ -598,6 +619,7 @@ __device__ __forceinline__ void dht_tile_s2(const SpectralDev &sp, const DhtTile
   const C *gin = reinterpret_cast<const C *>(a.in);
   C *gout = reinterpret_cast<C *>(a.out);
   s2_stage1<T, C, R0, R1, P, false, STRIDE>(gin, base, sm);
+  if constexpr (SCALE && RR == -2) asm volatile("cp.async.wait_group 0;\n" ::: "memory");  // stage 2 ends with a barrier
   s2_stage2<T, C, R0, R1, P>(sm, tw);
   if (SCALE) {
     s2_combine<T, C, N, P, 1, RR, STRIDE>(sm, gout, base, sp, k2, c0, vtab, acc);

@@ -936,12 +936,13 @@ namespace sq {
 // factors f (3 x R x N, axis a of term r at f + (a R + r) N; unscaled, so
 // that G(k) = sum_r f1_r(k1) f2_r(k2) f3_r(k3)); R = 0 is the exact diagonal.
 // t, w: the exponential-sum nodes and weights when the factors come from one.
-// The multiplier table of the FP64 pass C (SpectralDev::gtab): G at every
+// The multiplier tables of pass C (SpectralDev::gtab): G at every
 // mirror-reduced mode (m1, m2, m3), m <= N/2, summed in FP64 from the scaled
 // factors (or scale / (l1 + l2 + l3) for the exact diagonal); G(0,0,0) = 0.
-// FP32 passes evaluate G on the fly: they are bound by memory latency, not by
-// the multiplier's arithmetic, and measured slower with the table's loads.
-__global__ void k_build_gtab(int N, int R, const double *lam, const double *u, double scale, double *g64) {
+// FP64 table indexed by (m1, m2, m3); FP32 copy by (m1, m2, k3) with k3 over
+// the whole axis (each FP32 tile prefetches its 2P columns into shared memory).
+__global__ void k_build_gtab(int N, int R, const double *lam, const double *u, double scale, double *g64,
+                             float *g32) {
   const int H = N / 2 + 1;
   const size_t n = (size_t)H * H * H;
   for (size_t i = (size_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (size_t)gridDim.x * blockDim.x) {
@@ -956,6 +957,9 @@ __global__ void k_build_gtab(int N, int R, const double *lam, const double *u, d
       }
     }
     g64[i] = g;
+    const size_t row = ((size_t)m1 * H + m2) * N;
+    g32[row + m3] = (float)g;
+    if (m3 != 0 && m3 != N - m3) g32[row + N - m3] = (float)g;
   }
 }
 
@@ -992,8 +996,9 @@ int precond_create(int N, int R, const double *f, const std::vector<double> &t, 
   auto al = [](size_t b) { return (b + 255) & ~(size_t)255; };
   const size_t H = (size_t)N / 2 + 1;
   const bool with_tab = N <= kGtabMaxN;
-  const size_t b_g64 = with_tab ? H * H * H * 8 : 0;
-  const size_t total = al(b_tw64) + al(b_lam64) + al(b_u64) + al(b_tw32) + al(b_lam32) + al(b_u32) + al(b_g64);
+  const size_t b_g64 = with_tab ? H * H * H * 8 : 0, b_g32 = with_tab ? H * H * (size_t)N * 4 : 0;
+  const size_t total =
+      al(b_tw64) + al(b_lam64) + al(b_u64) + al(b_tw32) + al(b_lam32) + al(b_u32) + al(b_g64) + al(b_g32);
   if (cudaMalloc(&pc->d_mem, total) != cudaSuccess) {
     delete pc;
     return SQ_ENOMEM;
@@ -1006,6 +1011,7 @@ int precond_create(int N, int R, const double *f, const std::vector<double> &t, 
   char *p_lam32 = p_tw32 + al(b_tw32);
   char *p_u32 = p_lam32 + al(b_lam32);
   char *p_g64 = p_u32 + al(b_u32);
+  char *p_g32 = p_g64 + al(b_g64);
   if (cudaMemcpy(p_tw64, tw64.data(), b_tw64, cudaMemcpyHostToDevice) != cudaSuccess ||
       cudaMemcpy(p_lam64, lam64.data(), b_lam64, cudaMemcpyHostToDevice) != cudaSuccess ||
       cudaMemcpy(p_u64, u64.data(), b_u64, cudaMemcpyHostToDevice) != cudaSuccess ||
@@ -1023,7 +1029,8 @@ int precond_create(int N, int R, const double *f, const std::vector<double> &t, 
   sp.scale = 1.0 / (64.0 * (double)N * N * N);
   if (with_tab) {
     k_build_gtab<<<1024, 256>>>(N, R, reinterpret_cast<const double *>(p_lam64),
-                                reinterpret_cast<const double *>(p_u64), sp.scale, reinterpret_cast<double *>(p_g64));
+                                reinterpret_cast<const double *>(p_u64), sp.scale, reinterpret_cast<double *>(p_g64),
+                                reinterpret_cast<float *>(p_g32));
     if (cudaGetLastError() != cudaSuccess || cudaDeviceSynchronize() != cudaSuccess) {
       sq_precond_destroy(pc);
       return SQ_ECUDA;
@@ -1038,7 +1045,7 @@ int precond_create(int N, int R, const double *f, const std::vector<double> &t, 
   pc->sp32.tw = p_tw32;
   pc->sp32.lam = p_lam32;
   pc->sp32.u = p_u32;
-  pc->sp32.gtab = nullptr;
+  pc->sp32.gtab = with_tab ? p_g32 : nullptr;
   *out = pc;
   return SQ_OK;
 }
