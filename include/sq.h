@@ -294,8 +294,9 @@ int sq_set_tiles(const sq_tile_config *tiles, int ntiles);
  * mirror-reduced modes, and an FP32 copy of (N/2 + 1)^2 N values. The x1 pass
  * of single solves reads G from it (FP32: each tile's slice prefetched into
  * shared memory) instead of summing the canonical terms (or dividing, for the
- * exact diagonal) per mode; 0 evaluates G on the fly. Batches always
- * evaluate it on the fly. Results agree to rounding.
+ * exact diagonal in FP64) per mode; 0 evaluates G on the fly. FP32 passes
+ * with the exact diagonal and batches always evaluate it on the fly. Results
+ * agree to rounding.
  */
 enum sq_option {
   SQ_OPT_STRIDED_TWO_STAGE = 1,
