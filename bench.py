@@ -186,12 +186,12 @@ def _algorithmic(N, elem, rank_r, table=None):
     transforms with no combine (the scaling is applied to the complex
     spectrum): 2 x 2.5 log2 N, plus 6 for the scaling and the r.z sum, plus
     the multiplier where it is evaluated per mode (2R, or 4 for the exact
-    1/x); FP64 passes on grids N <= 256 read it from the precomputed table
-    instead (table=None: that default)."""
+    1/x); on grids N <= 256 pass C reads it from the precomputed table
+    instead, except FP32 with the exact diagonal (table=None: that default)."""
     n3 = N ** 3
     f = 2.5 * math.log2(N) + 3.0
     if table is None:
-        table = N <= 256 and elem == 8
+        table = N <= 256 and (elem == 8 or rank_r > 0)
     scale = 6 if table else ((2 * rank_r + 6) if rank_r else 10)
     return {
         "stencil_matvec": (2 * elem * n3, 15 * n3),

@@ -57,9 +57,11 @@ def test_bench_algorithmic_model():
     # the fused iteration moves 17 field passes of 4-byte words
     assert sum(b for b, _ in alg.values()) + alg["dht_x2"][0] == 17 * 4 * n3
     # pass C: two transforms without combines, scaling and r.z; the multiplier
-    # is a table lookup in FP64 at N <= 256, else the rank-R sum or the exact 1/x
-    assert alg["dht_x1_scale"][1] == (2 * 2.5 * 8 + 2 * R + 6) * n3
+    # is a table lookup at N <= 256 (except FP32 exact), else the rank-R sum or
+    # the exact 1/x
+    assert alg["dht_x1_scale"][1] == (2 * 2.5 * 8 + 6) * n3
     assert bench._algorithmic(N, 8, R)["dht_x1_scale"][1] == (2 * 2.5 * 8 + 6) * n3
+    assert bench._algorithmic(N, 4, 0)["dht_x1_scale"][1] == (2 * 2.5 * 8 + 10) * n3
     assert bench._algorithmic(N, 8, R, table=False)["dht_x1_scale"][1] == (2 * 2.5 * 8 + 2 * R + 6) * n3
     assert bench._algorithmic(N, 8, 0, table=False)["dht_x1_scale"][1] == (2 * 2.5 * 8 + 10) * n3
     assert bench._algorithmic(512, 4, 0)["dht_x1_scale"][1] == (2 * 2.5 * 9 + 10) * 512 ** 3
