@@ -297,13 +297,20 @@ int sq_set_tiles(const sq_tile_config *tiles, int ntiles);
  * exact diagonal in FP64) per mode; 0 evaluates G on the fly. FP32 passes
  * with the exact diagonal and batches always evaluate it on the fly. Results
  * agree to rounding.
+ * SQ_OPT_CONV_TC (default 1): the warm-start net's 32 -> 32 channel
+ * convolutions (forward and data gradient) run as implicit GEMMs on the
+ * 5th-generation tensor cores (tcgen05.mma, M = 128 voxels, N = 32, K = 16,
+ * FP32 accumulator in tensor memory; bounded waits: a wait that gives up
+ * makes sq_net_predict / sq_net_train_step return SQ_ETIMEOUT); 0 uses the
+ * mma.sync kernels. Results agree to FP32 rounding of the same BF16 inputs.
  */
 enum sq_option {
   SQ_OPT_STRIDED_TWO_STAGE = 1,
   SQ_OPT_STENCIL_ROWS = 2,
   SQ_OPT_INNER_TOL_EXP = 3,
   SQ_OPT_WAIT_POLLS = 4,
-  SQ_OPT_MULTIPLIER_TABLE = 5
+  SQ_OPT_MULTIPLIER_TABLE = 5,
+  SQ_OPT_CONV_TC = 6
 };
 int sq_set_option(int key, int value);
 
@@ -369,7 +376,9 @@ int sq_net_set_params(sq_net *net, const float *host, int64_t count);
 /* Gradient of the last sq_net_train_step (same layout as the parameters). */
 int sq_net_grads(const sq_net *net, float *host, int64_t count);
 /* Guess for the three correctors of realization c (device outputs, N^3 doubles
- * each). Asynchronous on `stream`. */
+ * each). Asynchronous on `stream`, except with SQ_OPT_CONV_TC = 1, where it
+ * synchronizes `stream` to read back the tensor-core kernels' status
+ * (SQ_ETIMEOUT if a bounded wait gave up). */
 int sq_net_predict(sq_net *net, const sq_coeffs *c, double *psi0, double *psi1, double *psi2,
                    sq_stream_t stream);
 /* One Adam step (lr; beta 0.9 / 0.999) against the targets targets[3*b + i]

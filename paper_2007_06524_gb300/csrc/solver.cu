@@ -1139,6 +1139,7 @@ int sq_set_option(int key, int value) {
   if (key == SQ_OPT_INNER_TOL_EXP) return set_inner_tol_exp(value) == 0 ? SQ_OK : SQ_EINVAL;
   if (key == SQ_OPT_WAIT_POLLS) return set_stage_wait_polls(value) == 0 ? SQ_OK : SQ_EINVAL;
   if (key == SQ_OPT_MULTIPLIER_TABLE) return set_use_gtab(value) == 0 ? SQ_OK : SQ_EINVAL;
+  if (key == SQ_OPT_CONV_TC) return set_conv_tc(value) == 0 ? SQ_OK : SQ_EINVAL;
   return SQ_EINVAL;
 }
 

@@ -31,6 +31,7 @@
 #include <cuda_bf16.h>
 
 #include "common.cuh"
+#include "tcgen05.cuh"
 
 namespace sq {
 namespace {
@@ -160,6 +161,157 @@ __global__ void __launch_bounds__(256) k_conv_mma(const __nv_bfloat16 *__restric
         }
       }
     }
+  }
+}
+
+// ------------------------------------------------- tcgen05 implicit GEMM
+// The 32 -> 32 channel convolutions on the 5th-generation tensor cores: per
+// tile of 128 consecutive output voxels, D[128 x 32] = sum over 27 taps and two
+// 16-channel halves of A_tap[128 x 16] W_tap[32 x 16]^T, one tcgen05.mma
+// (M = 128, N = 32, K = 16) each, accumulated in 32 TMEM columns. The CTA is
+// persistent (tiles blockIdx.x, + gridDim.x, ...): the weights are put in
+// shared memory once, in the no-swizzle K-major layout (54 chunks of 32 x 16,
+// 1 KB each: SBO 128 B between 8-row groups, LBO 512 B between the K halves),
+// after the two A buffers.
+// A_tap is gathered (im2col, periodic wrap) by cp.async into one of two 8 KB
+// buffers (two 4 KB halves, SBO 128 B, LBO 2048 B) while the MMAs of the
+// previous tap run; a buffer is refilled only after the commit of the MMAs
+// that read it has arrived on its mbarrier. Epilogue: 4 warps read their 32
+// TMEM lanes (one voxel's 32 channels per thread), add the bias, apply GELU
+// (EPI_GELU: stores z and a) or not (EPI_PLAIN: stores the sum). Every wait is
+// bounded: a wait that gives up sets *err, the CTA stops issuing and drains.
+constexpr int kTcThreads = 128;
+constexpr int kTcWeightBytes = 27 * 2 * 1024;
+// + 1 KB of slack past the last weight chunk: its 32 x 16 operand read with
+// the descriptor's offsets swapped would reach 1.75 KB past the chunk's start
+constexpr int kTcSmem = 2 * 8192 + kTcWeightBytes + 1024;
+
+template <int EPI>
+__global__ void __launch_bounds__(kTcThreads) k_conv_tc(const __nv_bfloat16 *__restrict__ in,
+                                                        const __nv_bfloat16 *__restrict__ wt,
+                                                        const float *__restrict__ bias,
+                                                        __nv_bfloat16 *__restrict__ zout,
+                                                        __nv_bfloat16 *__restrict__ aout, int N, int ntiles,
+                                                        int wait_polls, int *__restrict__ err) {
+  extern __shared__ __align__(1024) unsigned char smc[];
+  __shared__ __align__(8) unsigned long long mbar[2];
+  __shared__ unsigned tmem_base;
+  __shared__ int s_fail;
+  const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
+  // A buffers first, weights after: every address a descriptor can describe
+  // (with either reading of its two byte offsets) stays inside this CTA's
+  // shared memory
+  unsigned char *abuf = smc, *wsm = smc + 2 * 8192;
+  // weights [tap][cout][cin] -> chunk (tap, cin half): row n = cout, 16-byte pieces of 8 cin
+  for (int e = tid; e < 27 * 32 * 4; e += kTcThreads) {
+    const int tap = e >> 7, r = e & 127, n = r >> 2, g8 = r & 3;
+    const uint4 v = *reinterpret_cast<const uint4 *>(wt + ((size_t)(tap * 32 + n) * 32 + g8 * 8));
+    *reinterpret_cast<uint4 *>(wsm + (tap * 2 + (g8 >> 1)) * 1024 + (n >> 3) * 128 + (g8 & 1) * 512 + (n & 7) * 16) = v;
+  }
+  if (warp == 0) {
+    tc::tmem_alloc(&tmem_base, 32);
+    tc::tmem_relinquish();
+  }
+  if (tid == 0) {
+    tc::mbar_init(&mbar[0]);
+    tc::mbar_init(&mbar[1]);
+    s_fail = 0;
+  }
+  asm volatile("fence.proxy.async.shared::cta;\n" ::: "memory");  // weights -> the tensor core's view
+  tc::fence_before_sync();
+  __syncthreads();
+  tc::fence_after_sync();
+  const unsigned tmem = tmem_base;
+  constexpr uint32_t idesc = tc::idesc_bf16_f32(128, 32);
+  const unsigned wsm_s = tc::smem_u32(wsm), abuf_s = tc::smem_u32(abuf);
+  const size_t NN = (size_t)N * N, N3 = NN * N;
+  unsigned it = 0;  // taps issued so far by this CTA: buffer it & 1, its (it >> 1)-th use
+  bool live = true;
+  for (int tile = blockIdx.x; live && tile < ntiles; tile += gridDim.x) {
+    const size_t v0 = (size_t)tile * 128;  // first output voxel (sample-major; a tile stays in one sample)
+    const size_t smp = v0 / N3, vox0 = v0 - smp * N3;
+    const __nv_bfloat16 *ins = in + smp * N3 * 32;
+    for (int tap = 0; tap < 27; ++tap, ++it) {
+      const unsigned buf = it & 1u;
+      if (it >= 2 && !tc::mbar_wait(&mbar[buf], ((it - 2) >> 1) & 1u, wait_polls)) s_fail = 1;
+      __syncthreads();  // every thread has seen the buffer free (or the failure)
+      if (s_fail) {
+        live = false;
+        break;
+      }
+      const int dz = tap / 9 - 1, dy = (tap / 3) % 3 - 1, dx = tap % 3 - 1;
+      for (int e = tid; e < 512; e += kTcThreads) {  // 128 voxels x 4 pieces of 8 channels
+        const int m = e >> 2, g8 = e & 3;
+        const size_t vox = vox0 + m;
+        const int x = (int)(vox % N), y = (int)((vox / N) % N), z = (int)(vox / NN);
+        const size_t nb = (size_t)wrap(z + dz, N) * NN + (size_t)wrap(y + dy, N) * N + wrap(x + dx, N);
+        const unsigned dst = abuf_s + buf * 8192u + (g8 >> 1) * 4096u + (g8 & 1) * 2048u + m * 16u;
+        asm volatile("cp.async.cg.shared.global [%0], [%1], 16;\n" ::"r"(dst), "l"(ins + nb * 32 + g8 * 8)
+                     : "memory");
+      }
+      asm volatile("cp.async.commit_group;\n" ::: "memory");
+      asm volatile("cp.async.wait_group 0;\n" ::: "memory");
+      asm volatile("fence.proxy.async.shared::cta;\n" ::: "memory");
+      __syncthreads();
+      if (tid == 0) {
+        tc::fence_after_sync();
+#pragma unroll
+        for (int kc = 0; kc < 2; ++kc) {
+          const uint64_t ad = tc::sdesc(abuf_s + buf * 8192u + kc * 4096u, 2048u, 128u);
+          const uint64_t bd = tc::sdesc(wsm_s + (tap * 2 + kc) * 1024u, 512u, 128u);
+          tc::mma_bf16(tmem, ad, bd, idesc, (tap > 0 || kc > 0) ? 1u : 0u);
+        }
+        tc::mma_commit(&mbar[buf]);
+      }
+    }
+    if (!live) break;
+    // the tile's last two commits (and so every MMA of the tile) have arrived
+    bool ok = tc::mbar_wait(&mbar[(it - 2) & 1u], ((it - 2) >> 1) & 1u, wait_polls);
+    ok = tc::mbar_wait(&mbar[(it - 1) & 1u], ((it - 1) >> 1) & 1u, wait_polls) && ok;
+    if (!ok) s_fail = 1;
+    __syncthreads();
+    if (s_fail) break;
+    tc::fence_after_sync();
+    {
+      float v[32];
+      tc::tmem_ld_32x32(tmem + ((unsigned)(32 * warp) << 16), v);
+      const size_t o = (v0 + 32 * warp + lane) * 32;
+      uint32_t zw[16], aw[16];
+#pragma unroll
+      for (int j = 0; j < 16; ++j) {
+        const float z0 = v[2 * j] + (EPI == EPI_GELU ? bias[2 * j] : 0.f);
+        const float z1 = v[2 * j + 1] + (EPI == EPI_GELU ? bias[2 * j + 1] : 0.f);
+        __nv_bfloat162 zb = __floats2bfloat162_rn(z0, z1);
+        zw[j] = *reinterpret_cast<uint32_t *>(&zb);
+        if (EPI == EPI_GELU) {
+          __nv_bfloat162 ab = __floats2bfloat162_rn(gelu(z0), gelu(z1));
+          aw[j] = *reinterpret_cast<uint32_t *>(&ab);
+        }
+      }
+      uint4 *zdst = reinterpret_cast<uint4 *>((EPI == EPI_GELU ? zout : aout) + o);
+#pragma unroll
+      for (int q = 0; q < 4; ++q) zdst[q] = make_uint4(zw[4 * q], zw[4 * q + 1], zw[4 * q + 2], zw[4 * q + 3]);
+      if (EPI == EPI_GELU) {
+        uint4 *adst = reinterpret_cast<uint4 *>(aout + o);
+#pragma unroll
+        for (int q = 0; q < 4; ++q) adst[q] = make_uint4(aw[4 * q], aw[4 * q + 1], aw[4 * q + 2], aw[4 * q + 3]);
+      }
+    }
+    tc::fence_before_sync();
+    __syncthreads();  // TMEM read before the next tile's MMAs overwrite it
+  }
+  // no MMA may be in flight at exit: wait (long limit) for the last commit of each buffer
+  if (tid == 0 && it >= 1) {
+    const bool a = tc::mbar_wait(&mbar[(it - 1) & 1u], ((it - 1) >> 1) & 1u, 1 << 24);
+    const bool b = it < 2 || tc::mbar_wait(&mbar[(it - 2) & 1u], ((it - 2) >> 1) & 1u, 1 << 24);
+    if (!a || !b) s_fail = 1;
+  }
+  tc::fence_before_sync();
+  __syncthreads();
+  if (s_fail && tid == 0) atomicExch(err, 1);
+  if (warp == 0) {
+    tc::fence_after_sync();
+    tc::tmem_dealloc(tmem, 32);
   }
 }
 
@@ -569,6 +721,7 @@ struct sq_net {
   Scalars *d_st = nullptr;
   double *d_partials = nullptr;           // reductions of the operator kernel
   double *d_lpart = nullptr, *h_lpart = nullptr;
+  int *d_err = nullptr, *h_err = nullptr;  // a bounded wait of the tcgen05 convolution gave up
   int nchunk = 0, chunk = 0;
   int step = 0;
   std::vector<void *> allocs;
@@ -594,6 +747,38 @@ int conv(const sq_net *net, int B, const __nv_bfloat16 *in, const __nv_bfloat16 
   return SQ_OK;
 }
 
+// The 32 -> 32 channel convolutions on tcgen05 (SQ_OPT_CONV_TC = 1) or on
+// mma.sync (0): same inputs, outputs and layouts.
+int g_conv_tc = 1;
+
+template <int EPI>
+int conv32(const sq_net *net, int B, const __nv_bfloat16 *in, const __nv_bfloat16 *wt, const float *bias,
+           __nv_bfloat16 *z, __nv_bfloat16 *a, cudaStream_t s) {
+  if (!g_conv_tc) return conv<32, 32, 32, EPI>(net, B, in, wt, bias, z, a, nullptr, s);
+  const int N = net->N;
+  const long long ntiles = (long long)B * N * N * N / 128;
+  auto kern = k_conv_tc<EPI>;
+  SQN_CK(cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, kTcSmem));
+  int dev = 0, sms = 0, per_sm = 0;
+  SQN_CK(cudaGetDevice(&dev));
+  SQN_CK(cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev));
+  SQN_CK(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kern, kTcThreads, kTcSmem));
+  const long long resident = (long long)sms * (per_sm > 0 ? per_sm : 1);
+  const int grid = (int)(ntiles < resident ? ntiles : resident);
+  kern<<<grid, kTcThreads, kTcSmem, s>>>(in, wt, bias, z, a, N, (int)ntiles, stage_wait_polls(), net->d_err);
+  SQN_CK(cudaGetLastError());
+  return SQ_OK;
+}
+
+// Reads back (and clears) the tcgen05 convolutions' failure flag: SQ_ETIMEOUT
+// if a bounded wait gave up since the last check. Synchronizes `s`.
+int check_conv_err(sq_net *net, cudaStream_t s) {
+  SQN_CK(cudaMemcpyAsync(net->h_err, net->d_err, sizeof(int), cudaMemcpyDeviceToHost, s));
+  SQN_CK(cudaMemsetAsync(net->d_err, 0, sizeof(int), s));
+  SQN_CK(cudaStreamSynchronize(s));
+  return *net->h_err ? SQ_ETIMEOUT : SQ_OK;
+}
+
 int pack_all(sq_net *net, cudaStream_t s) {
   for (int l = 1; l < kLayers; ++l) {
     const int coutp = (l == kLayers - 1) ? 8 : kC;
@@ -614,8 +799,8 @@ int forward(sq_net *net, int B, cudaStream_t s) {
   SQN_CK(cudaGetLastError());
   int st;
   for (int l = 1; l < 5; ++l) {
-    st = conv<32, 32, 32, EPI_GELU>(net, B, net->d_a[l - 1], net->d_wf[l], net->d_w + net->boff[l], net->d_z[l],
-                                    net->d_a[l], nullptr, s);
+    st = conv32<EPI_GELU>(net, B, net->d_a[l - 1], net->d_wf[l], net->d_w + net->boff[l], net->d_z[l], net->d_a[l],
+                          s);
     if (st != SQ_OK) return st;
   }
   return conv<32, 32, 8, EPI_OUT>(net, B, net->d_a[4], net->d_wf[5], net->d_w + net->boff[5], nullptr, nullptr,
@@ -664,8 +849,7 @@ int backward(sq_net *net, int B, cudaStream_t s) {
     k_gelu_bwd<<<(unsigned)((n2 + 255) / 256), 256, 0, s>>>(net->d_ga, net->d_z[l], net->d_gz, n2);
     SQN_CK(cudaGetLastError());
     if ((st = weight_grad<32, 32>(net, B, net->d_a[l - 1], net->d_gz, 32, l, s)) != SQ_OK) return st;
-    if ((st = conv<32, 32, 32, EPI_PLAIN>(net, B, net->d_gz, net->d_wb[l], nullptr, nullptr, net->d_ga, nullptr, s)) !=
-        SQ_OK)
+    if ((st = conv32<EPI_PLAIN>(net, B, net->d_gz, net->d_wb[l], nullptr, nullptr, net->d_ga, s)) != SQ_OK)
       return st;
   }
   // layer 1 (1 -> 32): weights only
@@ -711,6 +895,14 @@ int feature_all(sq_net *net, int B, const sq_coeffs *const *cs, cudaStream_t s) 
 }
 
 }  // namespace
+
+namespace sq {
+int set_conv_tc(int on) {
+  if (on < 0 || on > 1) return 1;
+  g_conv_tc = on;
+  return 0;
+}
+}  // namespace sq
 
 extern "C" {
 
@@ -764,6 +956,9 @@ int sq_net_create(int N, int max_batch, uint64_t seed, double out_scale, sq_net 
   const int lblocks = (int)((3 * BN + 255) / 256);
   net->d_lpart = nalloc<double>(net, lblocks, &ok);
   if (ok && cudaMallocHost(&net->h_lpart, sizeof(double) * lblocks) != cudaSuccess) ok = false;
+  net->d_err = nalloc<int>(net, 1, &ok);
+  if (ok && cudaMallocHost(&net->h_err, sizeof(int)) != cudaSuccess) ok = false;
+  if (ok && cudaMemset(net->d_err, 0, sizeof(int)) != cudaSuccess) ok = false;
   if (ok && cudaMemset(net->d_st, 0, sizeof(Scalars)) != cudaSuccess) ok = false;
   if (!ok) {
     sq_net_destroy(net);
@@ -788,6 +983,7 @@ void sq_net_destroy(sq_net *net) {
   if (!net) return;
   for (void *p : net->allocs) cudaFree(p);
   if (net->h_lpart) cudaFreeHost(net->h_lpart);
+  if (net->h_err) cudaFreeHost(net->h_err);
   delete net;
 }
 
@@ -825,7 +1021,7 @@ int sq_net_predict(sq_net *net, const sq_coeffs *c, double *psi0, double *psi1, 
   const long long N3 = (long long)net->N * net->N * net->N;
   k_to_psi<<<(unsigned)((N3 + 255) / 256), 256, 0, s>>>(net->d_y, psi0, psi1, psi2, N3);
   SQN_CK(cudaGetLastError());
-  return SQ_OK;
+  return g_conv_tc ? check_conv_err(net, s) : SQ_OK;
 }
 
 int sq_net_train_step(sq_net *net, int batch, const sq_coeffs *const *cs, const double *const *targets, float lr,
@@ -919,6 +1115,7 @@ int sq_net_train_step(sq_net *net, int batch, const sq_coeffs *const *cs, const 
     double t = 0.0;
     for (int i = 0; i < lblocks; ++i) t += net->h_lpart[i];
     *loss = t / (3.0 * (double)tot);
+    if (g_conv_tc) return check_conv_err(net, s);
   }
   return SQ_OK;
 }

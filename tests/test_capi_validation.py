@@ -148,8 +148,10 @@ def test_options_ranges_and_defaults(sq):
             sq.sq_set_option(sq.SQ_OPT_STENCIL_ROWS, v)
         for v in range(2, 8):
             sq.sq_set_option(sq.SQ_OPT_INNER_TOL_EXP, v)
-        for key in (0, 6, 99):
+        for key in (0, 7, 99):
             _einval(sq, sq.sq_set_option, key, 1)
+        for v in (-1, 2):
+            _einval(sq, sq.sq_set_option, sq.SQ_OPT_CONV_TC, v)
         for v in (-1, 2):
             _einval(sq, sq.sq_set_option, sq.SQ_OPT_MULTIPLIER_TABLE, v)
     finally:  # the documented defaults
@@ -157,6 +159,7 @@ def test_options_ranges_and_defaults(sq):
         sq.sq_set_option(sq.SQ_OPT_STENCIL_ROWS, 0)
         sq.sq_set_option(sq.SQ_OPT_INNER_TOL_EXP, 5)
         sq.sq_set_option(sq.SQ_OPT_MULTIPLIER_TABLE, 1)
+        sq.sq_set_option(sq.SQ_OPT_CONV_TC, 1)
 
 
 def test_tile_overrides_reject_bad_entries(sq):

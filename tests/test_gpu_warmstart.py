@@ -215,3 +215,67 @@ def test_residual_loss_value_matches_oracle_operator(sq):
     ref /= 3 * N ** 3
     assert abs(loss - ref) <= 1e-2 * abs(ref), (loss, ref)
     assert np.abs(sq.sq_net_params(net) - p0).max() > 0
+
+
+@pytest.mark.parametrize("N,L,n", [(32, 8, 4), (64, 16, 4)])
+def test_tcgen05_convolutions_match_mma_sync(sq, N, L, n):
+    """The 32 -> 32 convolutions on tcgen05 (tensor memory accumulator,
+    SQ_OPT_CONV_TC = 1) and on mma.sync (0) take the same BF16 inputs:
+    predictions agree to FP32 rounding of the accumulation order, and so do
+    the gradients of a training step (forward and data-gradient
+    convolutions both switch)."""
+    import torch
+
+    outs = {}
+    for opt in (0, 1):
+        try:
+            sq.sq_set_option(sq.SQ_OPT_CONV_TC, opt)
+            net = sq.sq_net_create(N, 2, seed=13, out_scale=1.2)
+            p = sq.sq_net_params(net)
+            offs, _ = _layers()
+            wo, bo, ci, co = offs[5]
+            p[wo:bo] *= 10.0
+            sq.sq_net_set_params(net, p)
+            c = sq.sq_build_coeffs(L, n, 41, 0.5, 1.0, 10.0)
+            g = [torch.empty(N ** 3, dtype=torch.float64, device="cuda") for _ in range(3)]
+            sq.sq_net_predict(net, c, *g)
+            cs = [c, sq.sq_build_coeffs(L, n, 42, 0.5, 1.0, 10.0)]
+            rng = np.random.default_rng(5)
+            tg = [[torch.from_numpy(rng.standard_normal(N ** 3)).cuda() for _ in range(3)] for _ in cs]
+            loss = sq.sq_net_train_step(net, cs, tg, 1e-3, loss_type=0)
+            outs[opt] = (np.stack([x.cpu().numpy() for x in g]), loss, sq.sq_net_grads(net))
+        finally:
+            sq.sq_set_option(sq.SQ_OPT_CONV_TC, 1)
+    (y0, l0, g0), (y1, l1, g1) = outs[0], outs[1]
+    assert np.linalg.norm(y1 - y0) / np.linalg.norm(y0) <= 1e-3
+    assert abs(l1 - l0) <= 1e-3 * abs(l0)
+    assert np.linalg.norm(g1 - g0) / np.linalg.norm(g0) <= 2e-2
+
+
+def test_tcgen05_bounded_wait_gives_up_cleanly(sq):
+    """SQ_OPT_WAIT_POLLS = 0 makes the tensor-core convolution give up on its
+    first MMA-completion wait: it stops issuing, waits for the MMAs it issued,
+    frees its tensor memory and the prediction reports SQ_ETIMEOUT; the next
+    prediction with the default limit is clean and matches mma.sync."""
+    import torch
+
+    N, L, n = 32, 8, 4
+    net = sq.sq_net_create(N, 1, seed=2, out_scale=1.0)
+    c = sq.sq_build_coeffs(L, n, 3, 0.5, 1.0, 10.0)
+    g = [torch.empty(N ** 3, dtype=torch.float64, device="cuda") for _ in range(3)]
+    try:
+        sq.sq_set_option(sq.SQ_OPT_WAIT_POLLS, 0)
+        with pytest.raises(sq.SqError) as e:
+            sq.sq_net_predict(net, c, *g)
+        assert e.value.status == sq.SQ_ETIMEOUT
+    finally:
+        sq.sq_set_option(sq.SQ_OPT_WAIT_POLLS, 1 << 22)
+    sq.sq_net_predict(net, c, *g)
+    y1 = np.stack([x.cpu().numpy() for x in g])
+    try:
+        sq.sq_set_option(sq.SQ_OPT_CONV_TC, 0)
+        sq.sq_net_predict(net, c, *g)
+    finally:
+        sq.sq_set_option(sq.SQ_OPT_CONV_TC, 1)
+    y0 = np.stack([x.cpu().numpy() for x in g])
+    assert np.linalg.norm(y1 - y0) / np.linalg.norm(y0) <= 1e-3
