@@ -28,6 +28,8 @@ def main():
     ap.add_argument("--out", default=None)
     ap.add_argument("--loss", type=int, default=1,
                     help="0: squared error, 1: energy norm e.Ae, 2: residual norm |A y - b|^2")
+    ap.add_argument("--conv", choices=["tc", "mma"], default="tc",
+                    help="32-channel convolutions on tcgen05 (tc) or mma.sync (mma)")
     args = ap.parse_args()
     import numpy as np
     import torch
@@ -38,6 +40,7 @@ def main():
     import paper_2007_06524_gb300 as sq
     from paper_2007_06524_gb300 import warmstart, workloads
 
+    sq.sq_set_option(sq.SQ_OPT_CONV_TC, 1 if args.conv == "tc" else 0)
     wl = workloads.WARM_N64
     seeds = wl["train_seeds"][: args.train]
     targets, gen_iters = warmstart.generate_targets(torch, wl, seeds)
