@@ -169,22 +169,25 @@ __global__ void __launch_bounds__(256) k_conv_mma(const __nv_bfloat16 *__restric
 // tile of 128 consecutive output voxels, D[128 x 32] = sum over 27 taps and two
 // 16-channel halves of A_tap[128 x 16] W_tap[32 x 16]^T, one tcgen05.mma
 // (M = 128, N = 32, K = 16) each, accumulated in 32 TMEM columns. The CTA is
-// persistent (tiles blockIdx.x, + gridDim.x, ...): the weights are put in
-// shared memory once, in the no-swizzle K-major layout (54 chunks of 32 x 16,
-// 1 KB each: SBO 128 B between 8-row groups, LBO 512 B between the K halves),
-// after the two A buffers.
-// A_tap is gathered (im2col, periodic wrap) by cp.async into one of two 8 KB
-// buffers (two 4 KB halves, SBO 128 B, LBO 2048 B) while the MMAs of the
-// previous tap run; a buffer is refilled only after the commit of the MMAs
-// that read it has arrived on its mbarrier. Epilogue: 4 warps read their 32
-// TMEM lanes (one voxel's 32 channels per thread), add the bias, apply GELU
-// (EPI_GELU: stores z and a) or not (EPI_PLAIN: stores the sum). Every wait is
-// bounded: a wait that gives up sets *err, the CTA stops issuing and drains.
+// persistent and walks a flat sequence of jobs (its tiles x 27 taps). The
+// weights are put in shared memory once, in the no-swizzle K-major layout (54
+// chunks of 32 x 16, 1 KB each: SBO 128 B between 8-row groups, LBO 512 B
+// between the K halves). A_tap is gathered (im2col, periodic wrap) by cp.async
+// into a ring of kTcSlots 8 KB slots (two 4 KB halves, SBO 128 B, LBO 2048 B),
+// kTcAhead jobs ahead of the MMAs that read it; a slot is refilled only after
+// the commit of the MMAs that read it last has arrived on its mbarrier. After
+// a tile's 27th tap, 4 warps read their 32 TMEM lanes (one voxel's 32
+// channels per thread), add the bias, apply GELU (EPI_GELU: stores z and a)
+// or not (EPI_PLAIN: stores the sum). Every wait is bounded: a wait that gives
+// up sets *err, the CTA stops issuing, waits for its MMAs and frees its TMEM.
 constexpr int kTcThreads = 128;
+constexpr int kTcSlots = 6, kTcAhead = kTcSlots - 2;
+constexpr int kTcSlotBytes = 8192;
 constexpr int kTcWeightBytes = 27 * 2 * 1024;
-// + 1 KB of slack past the last weight chunk: its 32 x 16 operand read with
-// the descriptor's offsets swapped would reach 1.75 KB past the chunk's start
-constexpr int kTcSmem = 2 * 8192 + kTcWeightBytes + 1024;
+// A slots first, weights after, + 1 KB of slack past the last weight chunk:
+// every address a descriptor can describe, read with either assignment of its
+// two byte offsets, stays inside the CTA's shared memory
+constexpr int kTcSmem = kTcSlots * kTcSlotBytes + kTcWeightBytes + 1024;
 
 template <int EPI>
 __global__ void __launch_bounds__(kTcThreads) k_conv_tc(const __nv_bfloat16 *__restrict__ in,
@@ -194,14 +197,11 @@ __global__ void __launch_bounds__(kTcThreads) k_conv_tc(const __nv_bfloat16 *__r
                                                         __nv_bfloat16 *__restrict__ aout, int N, int ntiles,
                                                         int wait_polls, int *__restrict__ err) {
   extern __shared__ __align__(1024) unsigned char smc[];
-  __shared__ __align__(8) unsigned long long mbar[2];
+  __shared__ __align__(8) unsigned long long mbar[kTcSlots];
   __shared__ unsigned tmem_base;
   __shared__ int s_fail;
   const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
-  // A buffers first, weights after: every address a descriptor can describe
-  // (with either reading of its two byte offsets) stays inside this CTA's
-  // shared memory
-  unsigned char *abuf = smc, *wsm = smc + 2 * 8192;
+  unsigned char *abuf = smc, *wsm = smc + kTcSlots * kTcSlotBytes;
   // weights [tap][cout][cin] -> chunk (tap, cin half): row n = cout, 16-byte pieces of 8 cin
   for (int e = tid; e < 27 * 32 * 4; e += kTcThreads) {
     const int tap = e >> 7, r = e & 127, n = r >> 2, g8 = r & 3;
@@ -213,8 +213,7 @@ __global__ void __launch_bounds__(kTcThreads) k_conv_tc(const __nv_bfloat16 *__r
     tc::tmem_relinquish();
   }
   if (tid == 0) {
-    tc::mbar_init(&mbar[0]);
-    tc::mbar_init(&mbar[1]);
+    for (int k = 0; k < kTcSlots; ++k) tc::mbar_init(&mbar[k]);
     s_fail = 0;
   }
   asm volatile("fence.proxy.async.shared::cta;\n" ::: "memory");  // weights -> the tensor core's view
@@ -225,67 +224,76 @@ __global__ void __launch_bounds__(kTcThreads) k_conv_tc(const __nv_bfloat16 *__r
   constexpr uint32_t idesc = tc::idesc_bf16_f32(128, 32);
   const unsigned wsm_s = tc::smem_u32(wsm), abuf_s = tc::smem_u32(abuf);
   const size_t NN = (size_t)N * N, N3 = NN * N;
-  unsigned it = 0;  // taps issued so far by this CTA: buffer it & 1, its (it >> 1)-th use
-  bool live = true;
-  for (int tile = blockIdx.x; live && tile < ntiles; tile += gridDim.x) {
-    const size_t v0 = (size_t)tile * 128;  // first output voxel (sample-major; a tile stays in one sample)
-    const size_t smp = v0 / N3, vox0 = v0 - smp * N3;
-    const __nv_bfloat16 *ins = in + smp * N3 * 32;
-    for (int tap = 0; tap < 27; ++tap, ++it) {
-      const unsigned buf = it & 1u;
-      if (it >= 2 && !tc::mbar_wait(&mbar[buf], ((it - 2) >> 1) & 1u, wait_polls)) s_fail = 1;
-      __syncthreads();  // every thread has seen the buffer free (or the failure)
-      if (s_fail) {
-        live = false;
-        break;
-      }
+  const int my_tiles = (ntiles > (int)blockIdx.x) ? (ntiles - 1 - (int)blockIdx.x) / (int)gridDim.x + 1 : 0;
+  const int jobs = my_tiles * 27;
+  // gathers A of job k into its ring slot (nothing past the last job)
+  auto gather = [&](int k) {
+    if (k < jobs) {
+      const int tap = k % 27;
+      const size_t v0 = (size_t)((int)blockIdx.x + (k / 27) * (int)gridDim.x) * 128;
+      const size_t smp = v0 / N3, vox0 = v0 - smp * N3;
+      const __nv_bfloat16 *ins = in + smp * N3 * 32;
       const int dz = tap / 9 - 1, dy = (tap / 3) % 3 - 1, dx = tap % 3 - 1;
+      const unsigned slot = abuf_s + (unsigned)(k % kTcSlots) * kTcSlotBytes;
       for (int e = tid; e < 512; e += kTcThreads) {  // 128 voxels x 4 pieces of 8 channels
         const int m = e >> 2, g8 = e & 3;
         const size_t vox = vox0 + m;
         const int x = (int)(vox % N), y = (int)((vox / N) % N), z = (int)(vox / NN);
         const size_t nb = (size_t)wrap(z + dz, N) * NN + (size_t)wrap(y + dy, N) * N + wrap(x + dx, N);
-        const unsigned dst = abuf_s + buf * 8192u + (g8 >> 1) * 4096u + (g8 & 1) * 2048u + m * 16u;
+        const unsigned dst = slot + (g8 >> 1) * 4096u + (g8 & 1) * 2048u + m * 16u;
         asm volatile("cp.async.cg.shared.global [%0], [%1], 16;\n" ::"r"(dst), "l"(ins + nb * 32 + g8 * 8)
                      : "memory");
       }
-      asm volatile("cp.async.commit_group;\n" ::: "memory");
-      asm volatile("cp.async.wait_group 0;\n" ::: "memory");
-      asm volatile("fence.proxy.async.shared::cta;\n" ::: "memory");
-      __syncthreads();
-      if (tid == 0) {
-        tc::fence_after_sync();
-#pragma unroll
-        for (int kc = 0; kc < 2; ++kc) {
-          const uint64_t ad = tc::sdesc(abuf_s + buf * 8192u + kc * 4096u, 2048u, 128u);
-          const uint64_t bd = tc::sdesc(wsm_s + (tap * 2 + kc) * 1024u, 512u, 128u);
-          tc::mma_bf16(tmem, ad, bd, idesc, (tap > 0 || kc > 0) ? 1u : 0u);
-        }
-        tc::mma_commit(&mbar[buf]);
-      }
     }
-    if (!live) break;
-    // the tile's last two commits (and so every MMA of the tile) have arrived
-    bool ok = tc::mbar_wait(&mbar[(it - 2) & 1u], ((it - 2) >> 1) & 1u, wait_polls);
-    ok = tc::mbar_wait(&mbar[(it - 1) & 1u], ((it - 1) >> 1) & 1u, wait_polls) && ok;
-    if (!ok) s_fail = 1;
-    __syncthreads();
+    asm volatile("cp.async.commit_group;\n" ::: "memory");  // one group per job, empty past the end
+  };
+  for (int k = 0; k < kTcAhead; ++k) gather(k);
+  int last = -1;  // the last job whose MMAs were issued
+  for (int j = 0; j < jobs; ++j) {
+    const int tap = j % 27;
+    // this thread's gathers of job j have landed (groups complete in order)
+    asm volatile("cp.async.wait_group %0;\n" ::"n"(kTcAhead - 1) : "memory");
+    asm volatile("fence.proxy.async.shared::cta;\n" ::: "memory");
+    __syncthreads();  // ... and everyone's
     if (s_fail) break;
-    tc::fence_after_sync();
-    {
+    if (tid == 0) {
+      tc::fence_after_sync();
+      const unsigned slot = abuf_s + (unsigned)(j % kTcSlots) * kTcSlotBytes;
+#pragma unroll
+      for (int kc = 0; kc < 2; ++kc) {
+        const uint64_t ad = tc::sdesc(slot + kc * 4096u, 2048u, 128u);
+        const uint64_t bd = tc::sdesc(wsm_s + (tap * 2 + kc) * 1024u, 512u, 128u);
+        tc::mma_bf16(tmem, ad, bd, idesc, (tap > 0 || kc > 0) ? 1u : 0u);
+      }
+      tc::mma_commit(&mbar[j % kTcSlots]);
+    }
+    last = j;
+    // refill the slot job j - 2 used (its MMAs were issued an iteration ago)
+    // with job j + kTcAhead
+    if (j >= 2 && j - 2 + kTcSlots < jobs + kTcSlots) {
+      const int u = j - 2;
+      if (!tc::mbar_wait(&mbar[u % kTcSlots], (unsigned)(u / kTcSlots) & 1u, wait_polls)) s_fail = 1;
+    }
+    gather(j + kTcAhead);
+    if (tap == 26) {  // the tile is complete once job j's MMAs are
+      if (!tc::mbar_wait(&mbar[j % kTcSlots], (unsigned)(j / kTcSlots) & 1u, wait_polls)) s_fail = 1;
+      __syncthreads();
+      if (s_fail) break;
+      tc::fence_after_sync();
+      const size_t v0 = (size_t)((int)blockIdx.x + (j / 27) * (int)gridDim.x) * 128;
       float v[32];
       tc::tmem_ld_32x32(tmem + ((unsigned)(32 * warp) << 16), v);
       const size_t o = (v0 + 32 * warp + lane) * 32;
       uint32_t zw[16], aw[16];
 #pragma unroll
-      for (int j = 0; j < 16; ++j) {
-        const float z0 = v[2 * j] + (EPI == EPI_GELU ? bias[2 * j] : 0.f);
-        const float z1 = v[2 * j + 1] + (EPI == EPI_GELU ? bias[2 * j + 1] : 0.f);
+      for (int q = 0; q < 16; ++q) {
+        const float z0 = v[2 * q] + (EPI == EPI_GELU ? bias[2 * q] : 0.f);
+        const float z1 = v[2 * q + 1] + (EPI == EPI_GELU ? bias[2 * q + 1] : 0.f);
         __nv_bfloat162 zb = __floats2bfloat162_rn(z0, z1);
-        zw[j] = *reinterpret_cast<uint32_t *>(&zb);
+        zw[q] = *reinterpret_cast<uint32_t *>(&zb);
         if (EPI == EPI_GELU) {
           __nv_bfloat162 ab = __floats2bfloat162_rn(gelu(z0), gelu(z1));
-          aw[j] = *reinterpret_cast<uint32_t *>(&ab);
+          aw[q] = *reinterpret_cast<uint32_t *>(&ab);
         }
       }
       uint4 *zdst = reinterpret_cast<uint4 *>((EPI == EPI_GELU ? zout : aout) + o);
@@ -296,16 +304,13 @@ __global__ void __launch_bounds__(kTcThreads) k_conv_tc(const __nv_bfloat16 *__r
 #pragma unroll
         for (int q = 0; q < 4; ++q) adst[q] = make_uint4(aw[4 * q], aw[4 * q + 1], aw[4 * q + 2], aw[4 * q + 3]);
       }
+      tc::fence_before_sync();  // the TMEM reads precede the next tile's MMAs (barrier at the next job)
     }
-    tc::fence_before_sync();
-    __syncthreads();  // TMEM read before the next tile's MMAs overwrite it
   }
-  // no MMA may be in flight at exit: wait (long limit) for the last commit of each buffer
-  if (tid == 0 && it >= 1) {
-    const bool a = tc::mbar_wait(&mbar[(it - 1) & 1u], ((it - 1) >> 1) & 1u, 1 << 24);
-    const bool b = it < 2 || tc::mbar_wait(&mbar[(it - 2) & 1u], ((it - 2) >> 1) & 1u, 1 << 24);
-    if (!a || !b) s_fail = 1;
-  }
+  asm volatile("cp.async.wait_group 0;\n" ::: "memory");  // no gather into this CTA's memory left in flight
+  // no MMA may be in flight at exit: the last commit covers every earlier MMA
+  if (tid == 0 && last >= 0 && !tc::mbar_wait(&mbar[last % kTcSlots], (unsigned)(last / kTcSlots) & 1u, 1 << 24))
+    s_fail = 1;
   tc::fence_before_sync();
   __syncthreads();
   if (s_fail && tid == 0) atomicExch(err, 1);
@@ -759,6 +764,7 @@ int conv32(const sq_net *net, int B, const __nv_bfloat16 *in, const __nv_bfloat1
   const long long ntiles = (long long)B * N * N * N / 128;
   auto kern = k_conv_tc<EPI>;
   SQN_CK(cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, kTcSmem));
+  SQN_CK(cudaFuncSetAttribute(kern, cudaFuncAttributePreferredSharedMemoryCarveout, cudaSharedmemCarveoutMaxShared));
   int dev = 0, sms = 0, per_sm = 0;
   SQN_CK(cudaGetDevice(&dev));
   SQN_CK(cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev));
