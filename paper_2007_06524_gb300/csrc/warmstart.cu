@@ -226,22 +226,36 @@ __global__ void __launch_bounds__(kTcThreads) k_conv_tc(const __nv_bfloat16 *__r
   const size_t NN = (size_t)N * N, N3 = NN * N;
   const int my_tiles = (ntiles > (int)blockIdx.x) ? (ntiles - 1 - (int)blockIdx.x) / (int)gridDim.x + 1 : 0;
   const int jobs = my_tiles * 27;
+  // This thread gathers piece g8 (8 channels) of voxels m = (tid >> 2) + 32 q,
+  // q < 4, of every tile; their coordinates are computed once per tile.
+  const int g8 = tid & 3, m0 = tid >> 2;
+  int gtile = -1, gx[4], gy[4], gz[4];
+  const __nv_bfloat16 *gin = in;
   // gathers A of job k into its ring slot (nothing past the last job)
   auto gather = [&](int k) {
     if (k < jobs) {
-      const int tap = k % 27;
-      const size_t v0 = (size_t)((int)blockIdx.x + (k / 27) * (int)gridDim.x) * 128;
-      const size_t smp = v0 / N3, vox0 = v0 - smp * N3;
-      const __nv_bfloat16 *ins = in + smp * N3 * 32;
+      const int t = k / 27, tap = k - t * 27;
+      if (t != gtile) {
+        gtile = t;
+        const long long v0 = (long long)((int)blockIdx.x + t * (int)gridDim.x) * 128;
+        const long long smp = v0 / (long long)N3;
+        const int vox0 = (int)(v0 - smp * (long long)N3);
+        gin = in + (size_t)smp * N3 * 32 + g8 * 8;
+#pragma unroll
+        for (int q = 0; q < 4; ++q) {
+          const int vox = vox0 + m0 + 32 * q;
+          gx[q] = vox % N;
+          gy[q] = (vox / N) % N;
+          gz[q] = vox / (N * N);
+        }
+      }
       const int dz = tap / 9 - 1, dy = (tap / 3) % 3 - 1, dx = tap % 3 - 1;
-      const unsigned slot = abuf_s + (unsigned)(k % kTcSlots) * kTcSlotBytes;
-      for (int e = tid; e < 512; e += kTcThreads) {  // 128 voxels x 4 pieces of 8 channels
-        const int m = e >> 2, g8 = e & 3;
-        const size_t vox = vox0 + m;
-        const int x = (int)(vox % N), y = (int)((vox / N) % N), z = (int)(vox / NN);
-        const size_t nb = (size_t)wrap(z + dz, N) * NN + (size_t)wrap(y + dy, N) * N + wrap(x + dx, N);
-        const unsigned dst = slot + (g8 >> 1) * 4096u + (g8 & 1) * 2048u + m * 16u;
-        asm volatile("cp.async.cg.shared.global [%0], [%1], 16;\n" ::"r"(dst), "l"(ins + nb * 32 + g8 * 8)
+      const unsigned dst0 = abuf_s + (unsigned)(k % kTcSlots) * kTcSlotBytes + (g8 >> 1) * 4096u + (g8 & 1) * 2048u;
+#pragma unroll
+      for (int q = 0; q < 4; ++q) {  // 128 voxels x 4 pieces of 8 channels over 128 threads
+        const int nb = (wrap(gz[q] + dz, N) * N + wrap(gy[q] + dy, N)) * N + wrap(gx[q] + dx, N);
+        asm volatile("cp.async.cg.shared.global [%0], [%1], 16;\n" ::"r"(dst0 + (unsigned)(m0 + 32 * q) * 16u),
+                     "l"(gin + (size_t)nb * 32)
                      : "memory");
       }
     }
