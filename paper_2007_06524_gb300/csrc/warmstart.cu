@@ -23,6 +23,7 @@
 //  * conv_in (layer 1, one input channel), its weight gradient and the bias
 //    gradients run on the FP32 pipes (SIMT); every weight gradient is reduced
 //    over the chunks in a fixed order (deterministic).
+#include <algorithm>
 #include <cmath>
 #include <cstring>
 #include <new>
@@ -164,44 +165,56 @@ __global__ void __launch_bounds__(256) k_conv_mma(const __nv_bfloat16 *__restric
   }
 }
 
-// ------------------------------------------------- tcgen05 implicit GEMM
-// The 32 -> 32 channel convolutions on the 5th-generation tensor cores: per
-// tile of 128 consecutive output voxels, D[128 x 32] = sum over 27 taps and two
-// 16-channel halves of A_tap[128 x 16] W_tap[32 x 16]^T, one tcgen05.mma
-// (M = 128, N = 32, K = 16) each, accumulated in 32 TMEM columns. The CTA is
-// persistent and walks a flat sequence of jobs (its tiles x 27 taps). The
-// weights are put in shared memory once, in the no-swizzle K-major layout (54
-// chunks of 32 x 16, 1 KB each: SBO 128 B between 8-row groups, LBO 512 B
-// between the K halves). A_tap is gathered (im2col, periodic wrap) by cp.async
-// into a ring of kTcSlots 8 KB slots (two 4 KB halves, SBO 128 B, LBO 2048 B),
-// kTcAhead jobs ahead of the MMAs that read it; a slot is refilled only after
-// the commit of the MMAs that read it last has arrived on its mbarrier. After
-// a tile's 27th tap, 4 warps read their 32 TMEM lanes (one voxel's 32
-// channels per thread), add the bias, apply GELU (EPI_GELU: stores z and a)
-// or not (EPI_PLAIN: stores the sum). Every wait is bounded: a wait that gives
-// up sets *err, the CTA stops issuing, waits for its MMAs and frees its TMEM.
-constexpr int kTcThreads = 128;
-constexpr int kTcSlots = 6, kTcAhead = kTcSlots - 2;
-constexpr int kTcSlotBytes = 8192;
+// ------------------------------------------------- tcgen05 direct convolution
+// The 32 -> 32 channel convolutions on the 5th-generation tensor cores, with
+// no im2col copy. A CTA tile is 8 (x) x 16 (y) x TZC (z) output voxels of one
+// sample. Its input halo, 10 x 18 x (TZC + 2) voxels with periodic wrap, is
+// staged once in shared memory as four planes of 8 channels (16 bytes per
+// voxel; x fastest, then y, then z). One z-plane of the tile is one M = 128
+// operand, row r = x + 8 y. In the no-swizzle K-major layout an 8-row group
+// is 8 consecutive 16-byte rows (here 8 consecutive x), and consecutive groups
+// (consecutive y) sit one halo row, 160 bytes, apart. So for every tap
+// (dz, dy, dx) and 16-channel half kc the A operand is the halo itself, read
+// through a descriptor whose start address carries the tap's offset (SBO =
+// 160 B between y rows, LBO = the plane stride between the two 8-channel
+// halves of K). Per plane, D[128 x 32] = sum over 27 taps and 2 halves of
+// A[128 x 16] W[32 x 16]^T: 54 tcgen05.mma (M = 128, N = 32, K = 16) into 32
+// TMEM columns. The weights are put in shared memory once per CTA (54 chunks
+// of 32 x 16, 1 KB each: SBO 128 B, LBO 512 B).
+// The CTA is persistent over its tiles, with two halo buffers and two sets of
+// accumulators: while the MMAs of tile t run, it stages the halo of tile t+1
+// by cp.async into the buffer tile t-1 used and reads out tile t-1 (8 warps:
+// warp w reads TMEM lanes 32 (w % 4) ..; bias, GELU for EPI_GELU (stores z and
+// a), or the plain sum for EPI_PLAIN). Every wait is bounded: a wait that
+// gives up sets *err; the CTA then stops issuing, waits for its MMAs and
+// frees its TMEM.
+constexpr int kTcThreads = 256;
 constexpr int kTcWeightBytes = 27 * 2 * 1024;
-// A slots first, weights after, + 1 KB of slack past the last weight chunk:
-// every address a descriptor can describe, read with either assignment of its
-// two byte offsets, stays inside the CTA's shared memory
-constexpr int kTcSmem = kTcSlots * kTcSlotBytes + kTcWeightBytes + 1024;
+template <int TZC>
+struct TcTile {
+  static constexpr int HV = (TZC + 2) * 18 * 10;                   // halo voxels
+  static constexpr int Plane = (HV * 16 + 127) / 128 * 128 + 32;   // bytes, 32 mod 128: conflict-free staging
+  static constexpr int Buf = 4 * Plane;                            // one halo: 4 planes of 8 channels
+  static constexpr int Smem = 2 * Buf + kTcWeightBytes + 1024;     // + 1 KB of alignment slack
+  static constexpr int Cols = 2 * TZC * 32;                        // two accumulator sets
+  // the last byte an A descriptor can reach (plane 2 kc + 1, last z-plane, tap
+  // (2, 2, 2), row 127, k 15) stays inside its halo buffer
+  static_assert(2 * Plane + ((TZC + 1) * 18 + 2) * 160 + 32 + 15 * 160 + Plane + 7 * 16 + 14 < Buf, "halo extent");
+};
 
-template <int EPI>
-__global__ void __launch_bounds__(kTcThreads) k_conv_tc(const __nv_bfloat16 *__restrict__ in,
+template <int EPI, int TZC>
+__global__ void __launch_bounds__(kTcThreads, 1) k_conv_tc(const __nv_bfloat16 *__restrict__ in,
                                                         const __nv_bfloat16 *__restrict__ wt,
                                                         const float *__restrict__ bias,
                                                         __nv_bfloat16 *__restrict__ zout,
                                                         __nv_bfloat16 *__restrict__ aout, int N, int ntiles,
                                                         int wait_polls, int *__restrict__ err) {
+  using T = TcTile<TZC>;
   extern __shared__ __align__(1024) unsigned char smc[];
-  __shared__ __align__(8) unsigned long long mbar[kTcSlots];
+  __shared__ __align__(8) unsigned long long mbar[2];
   __shared__ unsigned tmem_base;
-  __shared__ int s_fail;
   const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
-  unsigned char *abuf = smc, *wsm = smc + kTcSlots * kTcSlotBytes;
+  unsigned char *wsm = smc + 2 * T::Buf;
   // weights [tap][cout][cin] -> chunk (tap, cin half): row n = cout, 16-byte pieces of 8 cin
   for (int e = tid; e < 27 * 32 * 4; e += kTcThreads) {
     const int tap = e >> 7, r = e & 127, n = r >> 2, g8 = r & 3;
@@ -209,12 +222,12 @@ __global__ void __launch_bounds__(kTcThreads) k_conv_tc(const __nv_bfloat16 *__r
     *reinterpret_cast<uint4 *>(wsm + (tap * 2 + (g8 >> 1)) * 1024 + (n >> 3) * 128 + (g8 & 1) * 512 + (n & 7) * 16) = v;
   }
   if (warp == 0) {
-    tc::tmem_alloc(&tmem_base, 32);
+    tc::tmem_alloc(&tmem_base, T::Cols);
     tc::tmem_relinquish();
   }
   if (tid == 0) {
-    for (int k = 0; k < kTcSlots; ++k) tc::mbar_init(&mbar[k]);
-    s_fail = 0;
+    tc::mbar_init(&mbar[0]);
+    tc::mbar_init(&mbar[1]);
   }
   asm volatile("fence.proxy.async.shared::cta;\n" ::: "memory");  // weights -> the tensor core's view
   tc::fence_before_sync();
@@ -222,115 +235,132 @@ __global__ void __launch_bounds__(kTcThreads) k_conv_tc(const __nv_bfloat16 *__r
   tc::fence_after_sync();
   const unsigned tmem = tmem_base;
   constexpr uint32_t idesc = tc::idesc_bf16_f32(128, 32);
-  const unsigned wsm_s = tc::smem_u32(wsm), abuf_s = tc::smem_u32(abuf);
-  const size_t NN = (size_t)N * N, N3 = NN * N;
+  const unsigned smc_s = tc::smem_u32(smc), wsm_s = tc::smem_u32(wsm);
+  const int ntx = N >> 3, nty = N >> 4, ntz = N / TZC;
+  const size_t N3 = (size_t)N * N * N;
   const int my_tiles = (ntiles > (int)blockIdx.x) ? (ntiles - 1 - (int)blockIdx.x) / (int)gridDim.x + 1 : 0;
-  const int jobs = my_tiles * 27;
-  // This thread gathers piece g8 (8 channels) of voxels m = (tid >> 2) + 32 q,
-  // q < 4, of every tile; their coordinates are computed once per tile.
-  const int g8 = tid & 3, m0 = tid >> 2;
-  int gtile = -1, gx[4], gy[4], gz[4];
-  const __nv_bfloat16 *gin = in;
-  // gathers A of job k into its ring slot (nothing past the last job)
-  auto gather = [&](int k) {
-    if (k < jobs) {
-      const int t = k / 27, tap = k - t * 27;
-      if (t != gtile) {
-        gtile = t;
-        const long long v0 = (long long)((int)blockIdx.x + t * (int)gridDim.x) * 128;
-        const long long smp = v0 / (long long)N3;
-        const int vox0 = (int)(v0 - smp * (long long)N3);
-        gin = in + (size_t)smp * N3 * 32 + g8 * 8;
-#pragma unroll
-        for (int q = 0; q < 4; ++q) {
-          const int vox = vox0 + m0 + 32 * q;
-          gx[q] = vox % N;
-          gy[q] = (vox / N) % N;
-          gz[q] = vox / (N * N);
-        }
-      }
-      const int dz = tap / 9 - 1, dy = (tap / 3) % 3 - 1, dx = tap % 3 - 1;
-      const unsigned dst0 = abuf_s + (unsigned)(k % kTcSlots) * kTcSlotBytes + (g8 >> 1) * 4096u + (g8 & 1) * 2048u;
-#pragma unroll
-      for (int q = 0; q < 4; ++q) {  // 128 voxels x 4 pieces of 8 channels over 128 threads
-        const int nb = (wrap(gz[q] + dz, N) * N + wrap(gy[q] + dy, N)) * N + wrap(gx[q] + dx, N);
-        asm volatile("cp.async.cg.shared.global [%0], [%1], 16;\n" ::"r"(dst0 + (unsigned)(m0 + 32 * q) * 16u),
-                     "l"(gin + (size_t)nb * 32)
+  // origin of this CTA's tile t (tiles run x fastest, then y, z, sample)
+  auto origin = [&](int t, int &smp, int &x0, int &y0, int &z0) {
+    int b = (int)blockIdx.x + t * (int)gridDim.x;
+    x0 = (b % ntx) * 8;
+    b /= ntx;
+    y0 = (b % nty) * 16;
+    b /= nty;
+    z0 = (b % ntz) * TZC;
+    smp = b / ntz;
+  };
+  // halo of tile t -> buffer t & 1 (one cp.async group, empty past the last tile)
+  auto stage = [&](int t) {
+    if (t < my_tiles) {
+      int smp, x0, y0, z0;
+      origin(t, smp, x0, y0, z0);
+      const __nv_bfloat16 *gs = in + (size_t)smp * N3 * 32;
+      const unsigned dst = smc_s + (unsigned)(t & 1) * T::Buf;
+      for (int e = tid; e < 4 * T::HV; e += kTcThreads) {
+        const int g8 = e & 3, hv = e >> 2;
+        const int hx = hv % 10, hy = (hv / 10) % 18, hz = hv / 180;
+        const int gv = (wrap(z0 + hz - 1, N) * N + wrap(y0 + hy - 1, N)) * N + wrap(x0 + hx - 1, N);
+        asm volatile("cp.async.cg.shared.global [%0], [%1], 16;\n" ::"r"(dst + (unsigned)(g8 * T::Plane + hv * 16)),
+                     "l"(gs + (size_t)gv * 32 + g8 * 8)
                      : "memory");
       }
     }
-    asm volatile("cp.async.commit_group;\n" ::: "memory");  // one group per job, empty past the end
+    asm volatile("cp.async.commit_group;\n" ::: "memory");
   };
-  for (int k = 0; k < kTcAhead; ++k) gather(k);
-  int last = -1;  // the last job whose MMAs were issued
-  for (int j = 0; j < jobs; ++j) {
-    const int tap = j % 27;
-    // this thread's gathers of job j have landed (groups complete in order)
-    asm volatile("cp.async.wait_group %0;\n" ::"n"(kTcAhead - 1) : "memory");
-    asm volatile("fence.proxy.async.shared::cta;\n" ::: "memory");
-    __syncthreads();  // ... and everyone's
-    if (s_fail) break;
-    if (tid == 0) {
-      tc::fence_after_sync();
-      const unsigned slot = abuf_s + (unsigned)(j % kTcSlots) * kTcSlotBytes;
-#pragma unroll
-      for (int kc = 0; kc < 2; ++kc) {
-        const uint64_t ad = tc::sdesc(slot + kc * 4096u, 2048u, 128u);
-        const uint64_t bd = tc::sdesc(wsm_s + (tap * 2 + kc) * 1024u, 512u, 128u);
-        tc::mma_bf16(tmem, ad, bd, idesc, (tap > 0 || kc > 0) ? 1u : 0u);
-      }
-      tc::mma_commit(&mbar[j % kTcSlots]);
-    }
-    last = j;
-    // refill the slot job j - 2 used (its MMAs were issued an iteration ago)
-    // with job j + kTcAhead
-    if (j >= 2 && j - 2 + kTcSlots < jobs + kTcSlots) {
-      const int u = j - 2;
-      if (!tc::mbar_wait(&mbar[u % kTcSlots], (unsigned)(u / kTcSlots) & 1u, wait_polls)) s_fail = 1;
-    }
-    gather(j + kTcAhead);
-    if (tap == 26) {  // the tile is complete once job j's MMAs are
-      if (!tc::mbar_wait(&mbar[j % kTcSlots], (unsigned)(j / kTcSlots) & 1u, wait_polls)) s_fail = 1;
-      __syncthreads();
-      if (s_fail) break;
-      tc::fence_after_sync();
-      const size_t v0 = (size_t)((int)blockIdx.x + (j / 27) * (int)gridDim.x) * 128;
+  // accumulators of tile u -> bias, activation, stores
+  auto epilogue = [&](int u) {
+    int smp, x0, y0, z0;
+    origin(u, smp, x0, y0, z0);
+    const int q = warp & 3, r = 32 * q + lane;
+    const size_t row = (size_t)smp * N3 + (size_t)(y0 + (r >> 3)) * N + x0 + (r & 7);
+    const unsigned taddr = tmem + ((unsigned)(32 * q) << 16) + (unsigned)(u & 1) * (TZC * 32);
+#pragma unroll 1
+    for (int zl = warp >> 2; zl < TZC; zl += 2) {
       float v[32];
-      tc::tmem_ld_32x32(tmem + ((unsigned)(32 * warp) << 16), v);
-      const size_t o = (v0 + 32 * warp + lane) * 32;
+      tc::tmem_ld_32x32(taddr + zl * 32, v);
+      const size_t o = (row + (size_t)(z0 + zl) * N * N) * 32;
       uint32_t zw[16], aw[16];
 #pragma unroll
-      for (int q = 0; q < 16; ++q) {
-        const float z0 = v[2 * q] + (EPI == EPI_GELU ? bias[2 * q] : 0.f);
-        const float z1 = v[2 * q + 1] + (EPI == EPI_GELU ? bias[2 * q + 1] : 0.f);
-        __nv_bfloat162 zb = __floats2bfloat162_rn(z0, z1);
-        zw[q] = *reinterpret_cast<uint32_t *>(&zb);
+      for (int k = 0; k < 16; ++k) {
+        const float z0f = v[2 * k] + (EPI == EPI_GELU ? bias[2 * k] : 0.f);
+        const float z1f = v[2 * k + 1] + (EPI == EPI_GELU ? bias[2 * k + 1] : 0.f);
+        __nv_bfloat162 zb = __floats2bfloat162_rn(z0f, z1f);
+        zw[k] = *reinterpret_cast<uint32_t *>(&zb);
         if (EPI == EPI_GELU) {
-          __nv_bfloat162 ab = __floats2bfloat162_rn(gelu(z0), gelu(z1));
-          aw[q] = *reinterpret_cast<uint32_t *>(&ab);
+          __nv_bfloat162 ab = __floats2bfloat162_rn(gelu(z0f), gelu(z1f));
+          aw[k] = *reinterpret_cast<uint32_t *>(&ab);
         }
       }
       uint4 *zdst = reinterpret_cast<uint4 *>((EPI == EPI_GELU ? zout : aout) + o);
 #pragma unroll
-      for (int q = 0; q < 4; ++q) zdst[q] = make_uint4(zw[4 * q], zw[4 * q + 1], zw[4 * q + 2], zw[4 * q + 3]);
+      for (int k = 0; k < 4; ++k) zdst[k] = make_uint4(zw[4 * k], zw[4 * k + 1], zw[4 * k + 2], zw[4 * k + 3]);
       if (EPI == EPI_GELU) {
         uint4 *adst = reinterpret_cast<uint4 *>(aout + o);
 #pragma unroll
-        for (int q = 0; q < 4; ++q) adst[q] = make_uint4(aw[4 * q], aw[4 * q + 1], aw[4 * q + 2], aw[4 * q + 3]);
+        for (int k = 0; k < 4; ++k) adst[k] = make_uint4(aw[4 * k], aw[4 * k + 1], aw[4 * k + 2], aw[4 * k + 3]);
       }
-      tc::fence_before_sync();  // the TMEM reads precede the next tile's MMAs (barrier at the next job)
     }
+  };
+  bool bad = false, broke = false;
+  int last = -1;  // the last tile whose MMAs were issued
+  stage(0);
+  for (int t = 0; t < my_tiles; ++t) {
+    asm volatile("cp.async.wait_group 0;\n" ::: "memory");  // this thread's part of tile t's halo ...
+    asm volatile("fence.proxy.async.shared::cta;\n" ::: "memory");
+    __syncthreads();  // ... and everyone's
+    if (tid == 0) {
+      tc::fence_after_sync();
+      const uint64_t a0 = tc::sdesc(smc_s + (unsigned)(t & 1) * T::Buf, T::Plane, 160u);
+      const uint64_t b0 = tc::sdesc(wsm_s, 512u, 128u);
+      const unsigned d0 = tmem + (unsigned)(t & 1) * (TZC * 32);
+#pragma unroll 1
+      for (int zl = 0; zl < TZC; ++zl) {
+#pragma unroll 1
+        for (int tap = 0; tap < 27; ++tap) {
+          const int dz = tap / 9, dy = (tap / 3) % 3, dx = tap % 3;
+          const unsigned off = (unsigned)(((zl + dz) * 18 + dy) * 160 + dx * 16);
+#pragma unroll
+          for (int kc = 0; kc < 2; ++kc) {
+            // descriptor start fields are addresses >> 4: offsets add there
+            const uint64_t ad = a0 + ((off + (unsigned)kc * 2u * T::Plane) >> 4);
+            const uint64_t bd = b0 + (uint64_t)((tap * 2 + kc) * (1024 >> 4));
+            tc::mma_bf16(d0 + zl * 32, ad, bd, idesc, (tap | kc) ? 1u : 0u);
+          }
+        }
+      }
+      tc::mma_commit(&mbar[t & 1]);
+    }
+    last = t;
+    if (t >= 1) {
+      // tile t-1's MMAs are complete: its halo buffer is free, its accumulators readable
+      if (!tc::mbar_wait(&mbar[(t - 1) & 1], (unsigned)((t - 1) >> 1) & 1u, wait_polls)) bad = true;
+      if (__syncthreads_or(bad)) {
+        broke = true;
+        break;
+      }
+      tc::fence_after_sync();
+      stage(t + 1);
+      epilogue(t - 1);
+    } else {
+      stage(t + 1);
+    }
+    tc::fence_before_sync();  // the TMEM reads precede the MMAs issued after the next barrier
   }
-  asm volatile("cp.async.wait_group 0;\n" ::: "memory");  // no gather into this CTA's memory left in flight
-  // no MMA may be in flight at exit: the last commit covers every earlier MMA
-  if (tid == 0 && last >= 0 && !tc::mbar_wait(&mbar[last % kTcSlots], (unsigned)(last / kTcSlots) & 1u, 1 << 24))
-    s_fail = 1;
+  // the last commit covers every MMA this CTA issued: none may be in flight at exit
+  if (last >= 0 && !tc::mbar_wait(&mbar[last & 1], (unsigned)(last >> 1) & 1u, broke ? (1 << 24) : wait_polls))
+    bad = true;
+  asm volatile("cp.async.wait_group 0;\n" ::: "memory");  // no copy into this CTA's memory left in flight
+  const bool any_bad = __syncthreads_or(bad);
+  if (!any_bad && last >= 0) {
+    tc::fence_after_sync();
+    epilogue(last);
+  }
   tc::fence_before_sync();
   __syncthreads();
-  if (s_fail && tid == 0) atomicExch(err, 1);
+  if (any_bad && tid == 0) atomicExch(err, 1);
   if (warp == 0) {
     tc::fence_after_sync();
-    tc::tmem_dealloc(tmem, 32);
+    tc::tmem_dealloc(tmem, T::Cols);
   }
 }
 
@@ -766,28 +796,45 @@ int conv(const sq_net *net, int B, const __nv_bfloat16 *in, const __nv_bfloat16 
   return SQ_OK;
 }
 
-// The 32 -> 32 channel convolutions on tcgen05 (SQ_OPT_CONV_TC = 1) or on
-// mma.sync (0): same inputs, outputs and layouts.
+// The 32 -> 32 channel convolutions on tcgen05 (SQ_OPT_CONV_TC = 1: tile
+// depth chosen below; 2 or 4: that depth) or on mma.sync (0): same inputs,
+// outputs and layouts.
 int g_conv_tc = 1;
+
+template <int EPI, int TZC>
+int conv_tc(const sq_net *net, int B, const __nv_bfloat16 *in, const __nv_bfloat16 *wt, const float *bias,
+            __nv_bfloat16 *z, __nv_bfloat16 *a, int grid, cudaStream_t s) {
+  const int N = net->N;
+  const long long ntiles = (long long)B * N * N * N / (128 * TZC);
+  auto kern = k_conv_tc<EPI, TZC>;
+  SQN_CK(cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, TcTile<TZC>::Smem));
+  const int g = (int)(ntiles < grid ? ntiles : grid);
+  kern<<<g, kTcThreads, TcTile<TZC>::Smem, s>>>(in, wt, bias, z, a, N, (int)ntiles, stage_wait_polls(),
+                                                 net->d_err);
+  SQN_CK(cudaGetLastError());
+  return SQ_OK;
+}
 
 template <int EPI>
 int conv32(const sq_net *net, int B, const __nv_bfloat16 *in, const __nv_bfloat16 *wt, const float *bias,
            __nv_bfloat16 *z, __nv_bfloat16 *a, cudaStream_t s) {
   if (!g_conv_tc) return conv<32, 32, 32, EPI>(net, B, in, wt, bias, z, a, nullptr, s);
-  const int N = net->N;
-  const long long ntiles = (long long)B * N * N * N / 128;
-  auto kern = k_conv_tc<EPI>;
-  SQN_CK(cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, kTcSmem));
-  SQN_CK(cudaFuncSetAttribute(kern, cudaFuncAttributePreferredSharedMemoryCarveout, cudaSharedmemCarveoutMaxShared));
-  int dev = 0, sms = 0, per_sm = 0;
+  // one CTA per SM (the shared memory of either depth allows no second)
+  int dev = 0, sms = 0;
   SQN_CK(cudaGetDevice(&dev));
   SQN_CK(cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev));
-  SQN_CK(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kern, kTcThreads, kTcSmem));
-  const long long resident = (long long)sms * (per_sm > 0 ? per_sm : 1);
-  const int grid = (int)(ntiles < resident ? ntiles : resident);
-  kern<<<grid, kTcThreads, kTcSmem, s>>>(in, wt, bias, z, a, N, (int)ntiles, stage_wait_polls(), net->d_err);
-  SQN_CK(cudaGetLastError());
-  return SQ_OK;
+  int tz = g_conv_tc;
+  if (tz == 1) {
+    // depth 4 stages less halo per voxel (6/4 z-planes against 4/2); depth 2
+    // balances better when there are few tiles per SM: compare the planes the
+    // busiest SM computes, depth 2 charged 10 % for its larger halo
+    const long long vox = (long long)B * net->N * net->N * net->N;
+    const long long t4 = vox / 512, t2 = vox / 256;
+    const double w4 = 4.0 * (double)((t4 + sms - 1) / sms), w2 = 2.2 * (double)((t2 + sms - 1) / sms);
+    tz = (w2 < w4) ? 2 : 4;
+  }
+  return tz == 2 ? conv_tc<EPI, 2>(net, B, in, wt, bias, z, a, sms, s)
+                 : conv_tc<EPI, 4>(net, B, in, wt, bias, z, a, sms, s);
 }
 
 // Reads back (and clears) the tcgen05 convolutions' failure flag: SQ_ETIMEOUT
@@ -918,7 +965,7 @@ int feature_all(sq_net *net, int B, const sq_coeffs *const *cs, cudaStream_t s) 
 
 namespace sq {
 int set_conv_tc(int on) {
-  if (on < 0 || on > 1) return 1;
+  if (on != 0 && on != 1 && on != 2 && on != 4) return 1;
   g_conv_tc = on;
   return 0;
 }
@@ -966,7 +1013,11 @@ int sq_net_create(int N, int max_batch, uint64_t seed, double out_scale, sq_net 
   net->d_g6 = nalloc<__nv_bfloat16>(net, BN * 16, &ok);
   net->d_ga = nalloc<__nv_bfloat16>(net, BN * kC, &ok);
   net->d_gz = nalloc<__nv_bfloat16>(net, BN * kC, &ok);
-  net->chunk = 8192;
+  // about 8192 voxels, a multiple of 4 N: the tensor-core weight gradient
+  // stages whole 4-row tiles of one plane (N^2 is a multiple of 4 N, so a tile
+  // never crosses a plane, and B N^3 is one too, so the last tile ends at the
+  // last voxel)
+  net->chunk = 4 * N * std::max(1, 8192 / (4 * N));
   net->nchunk = (int)((BN + net->chunk - 1) / net->chunk);
   net->d_dwpart = nalloc<float>(net, (size_t)net->nchunk * 28 * kC * kC, &ok);
   net->d_e = nalloc<float>(net, 3 * BN, &ok);

@@ -150,7 +150,9 @@ def test_options_ranges_and_defaults(sq):
             sq.sq_set_option(sq.SQ_OPT_INNER_TOL_EXP, v)
         for key in (0, 7, 99):
             _einval(sq, sq.sq_set_option, key, 1)
-        for v in (-1, 2):
+        for v in (0, 2, 4, 1):
+            sq.sq_set_option(sq.SQ_OPT_CONV_TC, v)
+        for v in (-1, 3, 8):
             _einval(sq, sq.sq_set_option, sq.SQ_OPT_CONV_TC, v)
         for v in (-1, 2):
             _einval(sq, sq.sq_set_option, sq.SQ_OPT_MULTIPLIER_TABLE, v)
