@@ -89,6 +89,15 @@ __device__ __forceinline__ void mbar_init(unsigned long long *mbar) {
   asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;\n" ::"r"(smem_u32(mbar)) : "memory");
   asm volatile("fence.mbarrier_init.release.cluster;\n" ::: "memory");
 }
+// mbarrier expecting `count` arrivals per phase.
+__device__ __forceinline__ void mbar_init_count(unsigned long long *mbar, unsigned count) {
+  asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;\n" ::"r"(smem_u32(mbar)), "r"(count) : "memory");
+  asm volatile("fence.mbarrier_init.release.cluster;\n" ::: "memory");
+}
+// One arrival of this thread (release semantics at CTA scope).
+__device__ __forceinline__ void mbar_arrive(unsigned long long *mbar) {
+  asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];\n" ::"r"(smem_u32(mbar)) : "memory");
+}
 // Waits, at most max_tries polls, for the phase of the given parity to complete.
 __device__ __forceinline__ bool mbar_wait(unsigned long long *mbar, unsigned parity, int max_tries) {
   for (int i = 0; i < max_tries; ++i) {
@@ -99,6 +108,21 @@ __device__ __forceinline__ bool mbar_wait(unsigned long long *mbar, unsigned par
         : "r"(smem_u32(mbar)), "r"(parity)
         : "memory");
     if (done) return true;
+  }
+  return false;
+}
+// As mbar_wait, and gives up early once *fail is set (by another role of the CTA).
+__device__ __forceinline__ bool mbar_wait_or_fail(unsigned long long *mbar, unsigned parity, int max_tries,
+                                                  const volatile int *fail) {
+  for (int i = 0; i < max_tries; ++i) {
+    unsigned done;
+    asm volatile(
+        "{\n .reg .pred p;\n mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n selp.u32 %0, 1, 0, p;\n}\n"
+        : "=r"(done)
+        : "r"(smem_u32(mbar)), "r"(parity)
+        : "memory");
+    if (done) return true;
+    if (*fail) return false;
   }
   return false;
 }

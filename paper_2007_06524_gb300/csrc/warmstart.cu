@@ -9,6 +9,9 @@
 // BF16, accumulation FP32.
 //
 // Kernels:
+//  * conv_tc: the 32 -> 32 channel convolutions (forward and data gradient)
+//    as direct convolutions on the 5th-generation tensor cores (tcgen05.mma,
+//    accumulators in tensor memory; described at the kernel);
 //  * conv_mma: implicit GEMM on the tensor cores (mma.sync m16n8k16 BF16, FP32
 //    accumulate). Block = 2 x 4 x 32 output voxels, one warp per 32-voxel row
 //    (two 16-row m-tiles) and all output channels; the input halo tile
@@ -20,9 +23,9 @@
 //  * dw_mma: weight gradients of the 32-channel layers on the tensor cores
 //    (mma.sync m16n8k16, operands gathered from channel-last tiles by
 //    transposing ldmatrix, one block per (voxel chunk, dz) with its nine taps).
-//  * conv_in (layer 1, one input channel), its weight gradient and the bias
-//    gradients run on the FP32 pipes (SIMT); every weight gradient is reduced
-//    over the chunks in a fixed order (deterministic).
+//  * conv_in (layer 1, one input channel), its weight gradient (dw_in) and
+//    the bias gradients (db) run on the FP32 pipes; every weight gradient is
+//    reduced over the chunks in a fixed order (deterministic).
 #include <algorithm>
 #include <cmath>
 #include <cstring>
@@ -182,13 +185,23 @@ __global__ void __launch_bounds__(256) k_conv_mma(const __nv_bfloat16 *__restric
 // TMEM columns. The weights are put in shared memory once per CTA (54 chunks
 // of 32 x 16, 1 KB each: SBO 128 B, LBO 512 B).
 // The CTA is persistent over its tiles, with two halo buffers and two sets of
-// accumulators: while the MMAs of tile t run, it stages the halo of tile t+1
-// by cp.async into the buffer tile t-1 used and reads out tile t-1 (8 warps:
-// warp w reads TMEM lanes 32 (w % 4) ..; bias, GELU for EPI_GELU (stores z and
-// a), or the plain sum for EPI_PLAIN). Every wait is bounded: a wait that
-// gives up sets *err; the CTA then stops issuing, waits for its MMAs and
+// accumulators, and its warps have roles that meet on mbarriers only:
+//  * warp 0, one thread: waits until halo b is full and accumulator set b is
+//    drained, issues the tile's MMAs (fully unrolled per plane) and commits
+//    them to done[b];
+//  * warps 1-3 (staging): wait until the MMAs of the tile two back are done
+//    (buffer b free), stage the halo by cp.async, wait for their copies,
+//    fence them to the tensor core's view and arrive on full[b];
+//  * warps 4-11 (read-out): wait on done[b], read accumulator set b (warp w
+//    reads TMEM lanes 32 (w % 4) .. of every second plane), add the bias and
+//    apply GELU (EPI_GELU: stores z and a) or store the plain sum
+//    (EPI_PLAIN), and arrive on drained[b].
+// Every wait is bounded and gives up early once another role has given up:
+// *err is set, every role stops, the CTA waits for the MMAs it issued and
 // frees its TMEM.
-constexpr int kTcThreads = 256;
+constexpr int kTcThreads = 384;
+constexpr int kTcStageThreads = 96;  // warps 1-3
+constexpr int kTcReadWarps = 8;      // warps 4-11
 constexpr int kTcWeightBytes = 27 * 2 * 1024;
 template <int TZC>
 struct TcTile {
@@ -200,21 +213,25 @@ struct TcTile {
   // the last byte an A descriptor can reach (plane 2 kc + 1, last z-plane, tap
   // (2, 2, 2), row 127, k 15) stays inside its halo buffer
   static_assert(2 * Plane + ((TZC + 1) * 18 + 2) * 160 + 32 + 15 * 160 + Plane + 7 * 16 + 14 < Buf, "halo extent");
+  static_assert(kTcStageThreads >= 80, "staging: 20 threads per piece, 4 pieces");
 };
 
 template <int EPI, int TZC>
 __global__ void __launch_bounds__(kTcThreads, 1) k_conv_tc(const __nv_bfloat16 *__restrict__ in,
-                                                        const __nv_bfloat16 *__restrict__ wt,
-                                                        const float *__restrict__ bias,
-                                                        __nv_bfloat16 *__restrict__ zout,
-                                                        __nv_bfloat16 *__restrict__ aout, int N, int ntiles,
-                                                        int wait_polls, int *__restrict__ err) {
+                                                           const __nv_bfloat16 *__restrict__ wt,
+                                                           const float *__restrict__ bias,
+                                                           __nv_bfloat16 *__restrict__ zout,
+                                                           __nv_bfloat16 *__restrict__ aout, int N, int ntiles,
+                                                           int wait_polls, int *__restrict__ err) {
   using T = TcTile<TZC>;
   extern __shared__ __align__(1024) unsigned char smc[];
-  __shared__ __align__(8) unsigned long long mbar[2];
+  __shared__ __align__(8) unsigned long long full[2], done[2], drained[2];
   __shared__ unsigned tmem_base;
+  __shared__ volatile int s_fail;
+  __shared__ float s_bias[32];
   const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
   unsigned char *wsm = smc + 2 * T::Buf;
+  if (EPI == EPI_GELU && tid < 32) s_bias[tid] = bias[tid];
   // weights [tap][cout][cin] -> chunk (tap, cin half): row n = cout, 16-byte pieces of 8 cin
   for (int e = tid; e < 27 * 32 * 4; e += kTcThreads) {
     const int tap = e >> 7, r = e & 127, n = r >> 2, g8 = r & 3;
@@ -226,16 +243,19 @@ __global__ void __launch_bounds__(kTcThreads, 1) k_conv_tc(const __nv_bfloat16 *
     tc::tmem_relinquish();
   }
   if (tid == 0) {
-    tc::mbar_init(&mbar[0]);
-    tc::mbar_init(&mbar[1]);
+    for (int b = 0; b < 2; ++b) {
+      tc::mbar_init_count(&full[b], kTcStageThreads);
+      tc::mbar_init_count(&done[b], 1);
+      tc::mbar_init_count(&drained[b], kTcReadWarps);
+    }
+    s_fail = 0;
   }
   asm volatile("fence.proxy.async.shared::cta;\n" ::: "memory");  // weights -> the tensor core's view
   tc::fence_before_sync();
   __syncthreads();
   tc::fence_after_sync();
   const unsigned tmem = tmem_base;
-  constexpr uint32_t idesc = tc::idesc_bf16_f32(128, 32);
-  const unsigned smc_s = tc::smem_u32(smc), wsm_s = tc::smem_u32(wsm);
+  const unsigned smc_s = tc::smem_u32(smc);
   const int ntx = N >> 3, nty = N >> 4, ntz = N / TZC;
   const size_t N3 = (size_t)N * N * N;
   const int my_tiles = (ntiles > (int)blockIdx.x) ? (ntiles - 1 - (int)blockIdx.x) / (int)gridDim.x + 1 : 0;
@@ -249,115 +269,136 @@ __global__ void __launch_bounds__(kTcThreads, 1) k_conv_tc(const __nv_bfloat16 *
     z0 = (b % ntz) * TZC;
     smp = b / ntz;
   };
-  // halo of tile t -> buffer t & 1 (one cp.async group, empty past the last tile)
-  auto stage = [&](int t) {
-    if (t < my_tiles) {
-      int smp, x0, y0, z0;
-      origin(t, smp, x0, y0, z0);
-      const __nv_bfloat16 *gs = in + (size_t)smp * N3 * 32;
-      const unsigned dst = smc_s + (unsigned)(t & 1) * T::Buf;
-      for (int e = tid; e < 4 * T::HV; e += kTcThreads) {
-        const int g8 = e & 3, hv = e >> 2;
-        const int hx = hv % 10, hy = (hv / 10) % 18, hz = hv / 180;
-        const int gv = (wrap(z0 + hz - 1, N) * N + wrap(y0 + hy - 1, N)) * N + wrap(x0 + hx - 1, N);
-        asm volatile("cp.async.cg.shared.global [%0], [%1], 16;\n" ::"r"(dst + (unsigned)(g8 * T::Plane + hv * 16)),
-                     "l"(gs + (size_t)gv * 32 + g8 * 8)
-                     : "memory");
-      }
-    }
-    asm volatile("cp.async.commit_group;\n" ::: "memory");
-  };
-  // accumulators of tile u -> bias, activation, stores
-  auto epilogue = [&](int u) {
-    int smp, x0, y0, z0;
-    origin(u, smp, x0, y0, z0);
-    const int q = warp & 3, r = 32 * q + lane;
-    const size_t row = (size_t)smp * N3 + (size_t)(y0 + (r >> 3)) * N + x0 + (r & 7);
-    const unsigned taddr = tmem + ((unsigned)(32 * q) << 16) + (unsigned)(u & 1) * (TZC * 32);
-#pragma unroll 1
-    for (int zl = warp >> 2; zl < TZC; zl += 2) {
-      float v[32];
-      tc::tmem_ld_32x32(taddr + zl * 32, v);
-      const size_t o = (row + (size_t)(z0 + zl) * N * N) * 32;
-      uint32_t zw[16], aw[16];
-#pragma unroll
-      for (int k = 0; k < 16; ++k) {
-        const float z0f = v[2 * k] + (EPI == EPI_GELU ? bias[2 * k] : 0.f);
-        const float z1f = v[2 * k + 1] + (EPI == EPI_GELU ? bias[2 * k + 1] : 0.f);
-        __nv_bfloat162 zb = __floats2bfloat162_rn(z0f, z1f);
-        zw[k] = *reinterpret_cast<uint32_t *>(&zb);
-        if (EPI == EPI_GELU) {
-          __nv_bfloat162 ab = __floats2bfloat162_rn(gelu(z0f), gelu(z1f));
-          aw[k] = *reinterpret_cast<uint32_t *>(&ab);
+  int last = -1;  // (warp 0, lane 0) the last tile whose MMAs were issued
+  if (warp == 0) {
+    if (lane == 0) {
+      constexpr uint32_t idesc = tc::idesc_bf16_f32(128, 32);
+      // descriptors: the start address (>> 4) sits in the low 14 bits and no
+      // offset carries out of them (shared addresses < 256 KB), so a tap's
+      // offset is added to the low word only
+      const uint64_t b64 = tc::sdesc(tc::smem_u32(wsm), 512u, 128u);
+      const uint32_t b_lo = (uint32_t)b64, b_hi = (uint32_t)(b64 >> 32);
+      for (int t = 0; t < my_tiles; ++t) {
+        const int b = t & 1;
+        if (!tc::mbar_wait_or_fail(&full[b], (unsigned)(t >> 1) & 1u, wait_polls, &s_fail)) {
+          s_fail = 1;
+          break;
         }
-      }
-      uint4 *zdst = reinterpret_cast<uint4 *>((EPI == EPI_GELU ? zout : aout) + o);
+        if (t >= 2 && !tc::mbar_wait_or_fail(&drained[b], (unsigned)((t - 2) >> 1) & 1u, wait_polls, &s_fail)) {
+          s_fail = 1;
+          break;
+        }
+        tc::fence_after_sync();
+        const uint64_t a64 = tc::sdesc(smc_s + (unsigned)b * T::Buf, T::Plane, 160u);
+        const uint32_t a_hi = (uint32_t)(a64 >> 32);
+        const unsigned d0 = tmem + (unsigned)b * (TZC * 32);
+#pragma unroll 1
+        for (int zl = 0; zl < TZC; ++zl) {
+          const uint32_t a_lo = (uint32_t)a64 + (uint32_t)(zl * (18 * 160 / 16));
 #pragma unroll
-      for (int k = 0; k < 4; ++k) zdst[k] = make_uint4(zw[4 * k], zw[4 * k + 1], zw[4 * k + 2], zw[4 * k + 3]);
-      if (EPI == EPI_GELU) {
-        uint4 *adst = reinterpret_cast<uint4 *>(aout + o);
+          for (int tap = 0; tap < 27; ++tap) {
 #pragma unroll
-        for (int k = 0; k < 4; ++k) adst[k] = make_uint4(aw[4 * k], aw[4 * k + 1], aw[4 * k + 2], aw[4 * k + 3]);
+            for (int kc = 0; kc < 2; ++kc) {
+              const uint32_t aoff = (uint32_t)((((tap / 9) * 18 + (tap / 3) % 3) * 160 + (tap % 3) * 16 +
+                                                kc * 2 * T::Plane) >> 4);
+              const uint32_t boff = (uint32_t)((tap * 2 + kc) * (1024 >> 4));
+              tc::mma_bf16(d0 + zl * 32, ((uint64_t)a_hi << 32) | (a_lo + aoff),
+                           ((uint64_t)b_hi << 32) | (b_lo + boff), idesc, (tap | kc) ? 1u : 0u);
+            }
+          }
+        }
+        tc::mma_commit(&done[b]);
+        last = t;
       }
     }
-  };
-  bool bad = false, broke = false;
-  int last = -1;  // the last tile whose MMAs were issued
-  stage(0);
-  for (int t = 0; t < my_tiles; ++t) {
-    asm volatile("cp.async.wait_group 0;\n" ::: "memory");  // this thread's part of tile t's halo ...
-    asm volatile("fence.proxy.async.shared::cta;\n" ::: "memory");
-    __syncthreads();  // ... and everyone's
-    if (tid == 0) {
-      tc::fence_after_sync();
-      const uint64_t a0 = tc::sdesc(smc_s + (unsigned)(t & 1) * T::Buf, T::Plane, 160u);
-      const uint64_t b0 = tc::sdesc(wsm_s, 512u, 128u);
-      const unsigned d0 = tmem + (unsigned)(t & 1) * (TZC * 32);
-#pragma unroll 1
-      for (int zl = 0; zl < TZC; ++zl) {
-#pragma unroll 1
-        for (int tap = 0; tap < 27; ++tap) {
-          const int dz = tap / 9, dy = (tap / 3) % 3, dx = tap % 3;
-          const unsigned off = (unsigned)(((zl + dz) * 18 + dy) * 160 + dx * 16);
-#pragma unroll
-          for (int kc = 0; kc < 2; ++kc) {
-            // descriptor start fields are addresses >> 4: offsets add there
-            const uint64_t ad = a0 + ((off + (unsigned)kc * 2u * T::Plane) >> 4);
-            const uint64_t bd = b0 + (uint64_t)((tap * 2 + kc) * (1024 >> 4));
-            tc::mma_bf16(d0 + zl * 32, ad, bd, idesc, (tap | kc) ? 1u : 0u);
+  } else if (warp < 4) {
+    // staging: thread st copies piece g8 = st % 4 (channels 8 g8 ..) of halo
+    // column hx = j % 10 (j = st / 4 < 20) in every second halo row (y, z),
+    // starting at row j / 10
+    const int st = tid - 32, g8 = st & 3, j = st >> 2, hx = j % 10;
+    for (int t = 0; t < my_tiles; ++t) {
+      const int b = t & 1;
+      if (t >= 2 && !tc::mbar_wait_or_fail(&done[b], (unsigned)((t - 2) >> 1) & 1u, wait_polls, &s_fail)) {
+        s_fail = 1;
+        break;
+      }
+      if (j < 20) {
+        int smp, x0, y0, z0;
+        origin(t, smp, x0, y0, z0);
+        const __nv_bfloat16 *gs = in + (size_t)smp * N3 * 32 + (size_t)wrap(x0 + hx - 1, N) * 32 + g8 * 8;
+        const unsigned dst = smc_s + (unsigned)b * T::Buf + (unsigned)(g8 * T::Plane + hx * 16);
+        int hy = j / 10, hz = 0;
+#pragma unroll 2
+        for (int rr = j / 10; rr < (TZC + 2) * 18; rr += 2) {  // halo row rr = hy + 18 hz
+          const int row = wrap(z0 + hz - 1, N) * N + wrap(y0 + hy - 1, N);
+          asm volatile("cp.async.cg.shared.global [%0], [%1], 16;\n" ::"r"(dst + (unsigned)rr * 160u),
+                       "l"(gs + (size_t)row * N * 32)
+                       : "memory");
+          hy += 2;
+          if (hy >= 18) {
+            hy -= 18;
+            ++hz;
           }
         }
       }
-      tc::mma_commit(&mbar[t & 1]);
+      asm volatile("cp.async.wait_all;\n" ::: "memory");
+      asm volatile("fence.proxy.async.shared::cta;\n" ::: "memory");  // the copies -> the tensor core's view
+      tc::mbar_arrive(&full[b]);
     }
-    last = t;
-    if (t >= 1) {
-      // tile t-1's MMAs are complete: its halo buffer is free, its accumulators readable
-      if (!tc::mbar_wait(&mbar[(t - 1) & 1], (unsigned)((t - 1) >> 1) & 1u, wait_polls)) bad = true;
-      if (__syncthreads_or(bad)) {
-        broke = true;
+  } else {
+    // read-out: TMEM lane quarter q, planes h, h + 2, ...
+    const int q = warp & 3, h = (warp - 4) >> 2, r = 32 * q + lane;
+    for (int t = 0; t < my_tiles; ++t) {
+      const int b = t & 1;
+      // the warp gives up as one (its TMEM loads are warp-collective)
+      const bool ok = tc::mbar_wait_or_fail(&done[b], (unsigned)(t >> 1) & 1u, wait_polls, &s_fail);
+      if (!__all_sync(0xffffffffu, ok)) {
+        s_fail = 1;
         break;
       }
       tc::fence_after_sync();
-      stage(t + 1);
-      epilogue(t - 1);
-    } else {
-      stage(t + 1);
+      int smp, x0, y0, z0;
+      origin(t, smp, x0, y0, z0);
+      const size_t row = (size_t)smp * N3 + (size_t)(y0 + (r >> 3)) * N + x0 + (r & 7);
+      const unsigned taddr = tmem + ((unsigned)(32 * q) << 16) + (unsigned)b * (TZC * 32);
+#pragma unroll 1
+      for (int zl = h; zl < TZC; zl += 2) {
+        float v[32];
+        tc::tmem_ld_32x32(taddr + zl * 32, v);
+        const size_t o = (row + (size_t)(z0 + zl) * N * N) * 32;
+        uint32_t zw[16], aw[16];
+#pragma unroll
+        for (int k = 0; k < 16; ++k) {
+          const float z0f = v[2 * k] + (EPI == EPI_GELU ? s_bias[2 * k] : 0.f);
+          const float z1f = v[2 * k + 1] + (EPI == EPI_GELU ? s_bias[2 * k + 1] : 0.f);
+          __nv_bfloat162 zb = __floats2bfloat162_rn(z0f, z1f);
+          zw[k] = *reinterpret_cast<uint32_t *>(&zb);
+          if (EPI == EPI_GELU) {
+            __nv_bfloat162 ab = __floats2bfloat162_rn(gelu(z0f), gelu(z1f));
+            aw[k] = *reinterpret_cast<uint32_t *>(&ab);
+          }
+        }
+        uint4 *zdst = reinterpret_cast<uint4 *>((EPI == EPI_GELU ? zout : aout) + o);
+#pragma unroll
+        for (int k = 0; k < 4; ++k) zdst[k] = make_uint4(zw[4 * k], zw[4 * k + 1], zw[4 * k + 2], zw[4 * k + 3]);
+        if (EPI == EPI_GELU) {
+          uint4 *adst = reinterpret_cast<uint4 *>(aout + o);
+#pragma unroll
+          for (int k = 0; k < 4; ++k) adst[k] = make_uint4(aw[4 * k], aw[4 * k + 1], aw[4 * k + 2], aw[4 * k + 3]);
+        }
+      }
+      tc::fence_before_sync();  // the TMEM reads precede the MMAs that overwrite set b
+      __syncwarp();
+      if (lane == 0) tc::mbar_arrive(&drained[b]);
     }
-    tc::fence_before_sync();  // the TMEM reads precede the MMAs issued after the next barrier
   }
+  asm volatile("cp.async.wait_all;\n" ::: "memory");  // no copy into this CTA's memory left in flight
+  __syncthreads();
   // the last commit covers every MMA this CTA issued: none may be in flight at exit
-  if (last >= 0 && !tc::mbar_wait(&mbar[last & 1], (unsigned)(last >> 1) & 1u, broke ? (1 << 24) : wait_polls))
-    bad = true;
-  asm volatile("cp.async.wait_group 0;\n" ::: "memory");  // no copy into this CTA's memory left in flight
-  const bool any_bad = __syncthreads_or(bad);
-  if (!any_bad && last >= 0) {
-    tc::fence_after_sync();
-    epilogue(last);
-  }
+  if (tid == 0 && last >= 0 && !tc::mbar_wait(&done[last & 1], (unsigned)(last >> 1) & 1u, 1 << 24)) s_fail = 1;
   tc::fence_before_sync();
   __syncthreads();
-  if (any_bad && tid == 0) atomicExch(err, 1);
+  if (s_fail && tid == 0) atomicExch(err, 1);
   if (warp == 0) {
     tc::fence_after_sync();
     tc::tmem_dealloc(tmem, T::Cols);
@@ -505,80 +546,127 @@ __global__ void k_pack_grad(const float *__restrict__ ae, __nv_bfloat16 *__restr
   dst[1] = make_uint4(w[4], w[5], w[6], w[7]);
 }
 
-// gz = ga * gelu'(z), 32 channels BF16
+// gz = ga * gelu'(z), 32 channels BF16; one thread per 8 values (16-byte
+// accesses), n8 = values / 8.
 __global__ void k_gelu_bwd(const __nv_bfloat16 *__restrict__ ga, const __nv_bfloat16 *__restrict__ z,
-                           __nv_bfloat16 *__restrict__ gz, long long n2) {
-  const long long i = blockIdx.x * 256LL + threadIdx.x;  // pairs
-  if (i >= n2) return;
-  const float2 a = __bfloat1622float2(reinterpret_cast<const __nv_bfloat162 *>(ga)[i]);
-  const float2 zz = __bfloat1622float2(reinterpret_cast<const __nv_bfloat162 *>(z)[i]);
-  reinterpret_cast<__nv_bfloat162 *>(gz)[i] = __floats2bfloat162_rn(a.x * gelu_grad(zz.x), a.y * gelu_grad(zz.y));
+                           __nv_bfloat16 *__restrict__ gz, long long n8) {
+  const long long i = blockIdx.x * 256LL + threadIdx.x;
+  if (i >= n8) return;
+  const uint4 a4 = reinterpret_cast<const uint4 *>(ga)[i];
+  const uint4 z4 = reinterpret_cast<const uint4 *>(z)[i];
+  const __nv_bfloat162 *a2 = reinterpret_cast<const __nv_bfloat162 *>(&a4);
+  const __nv_bfloat162 *z2 = reinterpret_cast<const __nv_bfloat162 *>(&z4);
+  uint4 o4;
+  __nv_bfloat162 *o2 = reinterpret_cast<__nv_bfloat162 *>(&o4);
+#pragma unroll
+  for (int k = 0; k < 4; ++k) {
+    const float2 a = __bfloat1622float2(a2[k]);
+    const float2 zz = __bfloat1622float2(z2[k]);
+    o2[k] = __floats2bfloat162_rn(a.x * gelu_grad(zz.x), a.y * gelu_grad(zz.y));
+  }
+  reinterpret_cast<uint4 *>(gz)[i] = o4;
 }
 
-// Weight (and bias, tap 27) gradient partials: dW[tap][co][ci] = sum_v
-// A[v + off_tap][ci] G[v][co] over the voxels of one chunk (FP32 SIMT).
-// A: BF16 [B][N3][32] (CA = 32) or FP32 feature [B][N3] (CA = 1).
-// G: BF16 [B][N3][CGS], CG real channels.
-template <int CA, int CG>
-__global__ void __launch_bounds__(256) k_dw(const void *__restrict__ A, const __nv_bfloat16 *__restrict__ G, int CGS,
-                                            int N, long long total, int chunk, float *__restrict__ partials,
-                                            int tap0) {
-  constexpr int V = 64;
-  __shared__ float sa[V][CA + 1];
-  __shared__ float sg[V][CG + 1];
-  const int tap = tap0 + blockIdx.y;
+// Weight and bias gradient partials of layer 1 (one input channel, the FP32
+// feature f): dW[tap][co] = sum_v f[v + off_tap] G[v][co] and dB[co] =
+// sum_v G[v][co] over the voxels of one chunk (FP32 pipes). Per tile of 128
+// voxels the block stages G transposed (channel rows, padded: conflict-free
+// 16-byte reads) and f at the 27 tap offsets of every voxel (slot 27 holds
+// ones: the bias); thread (co = lane, slots warp + 8 k) then runs a
+// 4 x 4 register block over the voxels. Partials go to the layout
+// (chunk, tap, co) that k_dw_reduce sums in a fixed order. The chunk is a
+// multiple of 128 voxels (of 4 N, N a multiple of 32).
+__global__ void __launch_bounds__(256) k_dw_in(const float *__restrict__ f, const __nv_bfloat16 *__restrict__ G,
+                                               int N, long long total, int chunk, float *__restrict__ partials) {
+  constexpr int V = 128;
+  __shared__ __align__(16) float sf[28][V];
+  __shared__ __align__(16) float sg[32][V + 4];
+  const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
   const long long v0 = (long long)blockIdx.x * chunk;
   const long long v1 = (v0 + chunk < total) ? v0 + chunk : total;
   const size_t N3 = (size_t)N * N * N;
-  const int dz = tap / 9 - 1, dy = (tap / 3) % 3 - 1, dx = tap % 3 - 1;
-  constexpr int NOUT = CG * CA;
-  constexpr int PER = (NOUT + 255) / 256;
-  float acc[PER];
-#pragma unroll
-  for (int k = 0; k < PER; ++k) acc[k] = 0.f;
+  float acc[4] = {0.f, 0.f, 0.f, 0.f};
   for (long long vb = v0; vb < v1; vb += V) {
-    __syncthreads();
-    for (int e = threadIdx.x; e < V * CA; e += 256) {
-      const int vi = e / CA, ci = e - vi * CA;
+    __syncthreads();  // the previous tile is consumed
+    for (int e = tid; e < V * 16; e += 256) {  // G: 128 voxels x 16 channel pairs
+      const int vi = e >> 4, c2 = e & 15;
+      const float2 g = __bfloat1622float2(reinterpret_cast<const __nv_bfloat162 *>(G)[(vb + vi) * 16 + c2]);
+      sg[2 * c2][vi] = g.x;
+      sg[2 * c2 + 1][vi] = g.y;
+    }
+    {  // f at the tap offsets: thread = (voxel tid % 128, taps tid / 128 + 2 k)
+      const int vi = tid & (V - 1);
       const long long v = vb + vi;
-      float val = 0.f;
-      if (v < v1) {
-        if (tap == 27) {
-          val = (ci == 0) ? 1.f : 0.f;
-        } else {
-          const long long smp = v / N3;
-          const size_t vox = v - smp * N3;
-          const int x = vox % N, y = (vox / N) % N, z = vox / ((size_t)N * N);
-          const size_t nb = smp * N3 + (size_t)wrap(z + dz, N) * N * N + (size_t)wrap(y + dy, N) * N + wrap(x + dx, N);
-          if (CA == 1)
-            val = reinterpret_cast<const float *>(A)[nb];
-          else
-            val = __bfloat162float(reinterpret_cast<const __nv_bfloat16 *>(A)[nb * CA + ci]);
+      const long long smp = v / (long long)N3;
+      const int vox = (int)(v - smp * (long long)N3);
+      const int x = vox % N, y = (vox / N) % N, z = vox / (N * N);
+      const float *fs = f + smp * (long long)N3;
+      for (int tap = tid >> 7; tap < 28; tap += 2) {
+        float val = 1.f;
+        if (tap < 27) {
+          const int dz = tap / 9 - 1, dy = (tap / 3) % 3 - 1, dx = tap % 3 - 1;
+          val = fs[((size_t)wrap(z + dz, N) * N + wrap(y + dy, N)) * N + wrap(x + dx, N)];
         }
+        sf[tap][vi] = val;
       }
-      sa[vi][ci] = val;
-    }
-    for (int e = threadIdx.x; e < V * CG; e += 256) {
-      const int vi = e / CG, co = e - vi * CG;
-      const long long v = vb + vi;
-      sg[vi][co] = (v < v1) ? __bfloat162float(G[v * CGS + co]) : 0.f;
     }
     __syncthreads();
+#pragma unroll 2
+    for (int vi = 0; vi < V; vi += 4) {
+      const float4 g = *reinterpret_cast<const float4 *>(&sg[lane][vi]);
 #pragma unroll
-    for (int k = 0; k < PER; ++k) {
-      const int o = threadIdx.x + k * 256;
-      if (o < NOUT) {
-        const int co = o / CA, ci = o - co * CA;
-        float s = acc[k];
-        for (int vi = 0; vi < V; ++vi) s = fmaf(sa[vi][ci], sg[vi][co], s);
-        acc[k] = s;
+      for (int k = 0; k < 4; ++k) {
+        const int tap = warp + 8 * k;
+        if (tap < 28) {
+          const float4 a = *reinterpret_cast<const float4 *>(&sf[tap][vi]);
+          acc[k] = fmaf(a.x, g.x, fmaf(a.y, g.y, fmaf(a.z, g.z, fmaf(a.w, g.w, acc[k]))));
+        }
       }
     }
   }
 #pragma unroll
-  for (int k = 0; k < PER; ++k) {
-    const int o = threadIdx.x + k * 256;
-    if (o < NOUT) partials[((size_t)blockIdx.x * 28 + tap) * NOUT + o] = acc[k];
+  for (int k = 0; k < 4; ++k) {
+    const int tap = warp + 8 * k;
+    if (tap < 28) partials[((size_t)blockIdx.x * 28 + tap) * 32 + lane] = acc[k];
+  }
+}
+
+// Bias gradient partials of a layer with CG output channels stored with
+// stride CGS (BF16, a multiple of 8): dB[co] = sum_v G[v][co] over one
+// chunk, written to the bias slot (tap 27, input channel 0) of the chunk's
+// partials (nout = CG CA entries per tap). Thread t reads the 8 channels
+// 8 (t % 4) .. of voxels t / 4 + 64 k (16-byte loads); the 64 voxel lanes are
+// added in a fixed order.
+__global__ void __launch_bounds__(256) k_db(const __nv_bfloat16 *__restrict__ G, int CGS, int CG, long long total,
+                                            int chunk, int nout, int ca, float *__restrict__ partials) {
+  __shared__ float red[64][33];
+  const int c8 = threadIdx.x & 3, vl = threadIdx.x >> 2;
+  const long long v0 = (long long)blockIdx.x * chunk;
+  const long long v1 = (v0 + chunk < total) ? v0 + chunk : total;
+  float acc[8];
+#pragma unroll
+  for (int k = 0; k < 8; ++k) acc[k] = 0.f;
+  if (c8 * 8 < CGS) {
+#pragma unroll 4
+    for (long long v = v0 + vl; v < v1; v += 64) {
+      const uint4 g4 = *reinterpret_cast<const uint4 *>(G + v * CGS + c8 * 8);
+      const __nv_bfloat162 *g2 = reinterpret_cast<const __nv_bfloat162 *>(&g4);
+#pragma unroll
+      for (int k = 0; k < 4; ++k) {
+        const float2 g = __bfloat1622float2(g2[k]);
+        acc[2 * k] += g.x;
+        acc[2 * k + 1] += g.y;
+      }
+    }
+  }
+#pragma unroll
+  for (int k = 0; k < 8; ++k) red[vl][c8 * 8 + k] = acc[k];
+  __syncthreads();
+  const int co = threadIdx.x;
+  if (co < CG) {
+    float t = 0.f;
+    for (int w = 0; w < 64; ++w) t += red[w][co];
+    partials[((size_t)blockIdx.x * 28 + 27) * nout + (size_t)co * ca] = t;
   }
 }
 
@@ -881,7 +969,7 @@ int weight_grad(sq_net *net, int B, const void *A, const __nv_bfloat16 *G, int C
   const int nchunk = (int)((tot + net->chunk - 1) / net->chunk);
   if (nchunk > net->nchunk) return SQ_EINVAL;
   if constexpr (CA == 32) {
-    // taps on the tensor cores, the bias (tap 27) on the FP32 pipe
+    // taps on the tensor cores, the bias (tap 27) by a plain reduction
     constexpr int CGM = CG > 16 ? 32 : 16;
     const size_t smem = ((size_t)4 * N * (CGM + 8) + (size_t)6 * N * 40) * sizeof(__nv_bfloat16);
     auto kern = k_dw_mma<CGM>;
@@ -889,9 +977,10 @@ int weight_grad(sq_net *net, int B, const void *A, const __nv_bfloat16 *G, int C
     kern<<<dim3(nchunk, 3), 256, smem, s>>>(reinterpret_cast<const __nv_bfloat16 *>(A), G, CGS, CG, N, tot,
                                             net->chunk, net->d_dwpart);
     SQN_CK(cudaGetLastError());
-    k_dw<CA, CG><<<dim3(nchunk, 1), 256, 0, s>>>(A, G, CGS, N, tot, net->chunk, net->d_dwpart, 27);
+    k_db<<<nchunk, 256, 0, s>>>(G, CGS, CG, tot, net->chunk, CG * CA, CA, net->d_dwpart);
   } else {
-    k_dw<CA, CG><<<dim3(nchunk, 28), 256, 0, s>>>(A, G, CGS, N, tot, net->chunk, net->d_dwpart, 0);
+    static_assert(CA == 1 && CG == 32, "layer 1: one input channel, 32 output channels");
+    k_dw_in<<<nchunk, 256, 0, s>>>(reinterpret_cast<const float *>(A), G, N, tot, net->chunk, net->d_dwpart);
   }
   SQN_CK(cudaGetLastError());
   const int nout = CG * CA;
@@ -904,7 +993,7 @@ int weight_grad(sq_net *net, int B, const void *A, const __nv_bfloat16 *G, int C
 int backward(sq_net *net, int B, cudaStream_t s) {
   const int N = net->N;
   const long long N3 = (long long)N * N * N;
-  const long long n2 = (long long)B * N3 * kC / 2;
+  const long long n8 = (long long)B * N3 * kC / 8;
   int st;
   // layer 6 (32 -> 3): weights from a5 and g6, data gradient g6 -> ga
   if ((st = weight_grad<32, 3>(net, B, net->d_a[4], net->d_g6, 16, 5, s)) != SQ_OK) return st;
@@ -913,14 +1002,14 @@ int backward(sq_net *net, int B, cudaStream_t s) {
     return st;
   // layers 5..2 (32 -> 32)
   for (int l = 4; l >= 1; --l) {
-    k_gelu_bwd<<<(unsigned)((n2 + 255) / 256), 256, 0, s>>>(net->d_ga, net->d_z[l], net->d_gz, n2);
+    k_gelu_bwd<<<(unsigned)((n8 + 255) / 256), 256, 0, s>>>(net->d_ga, net->d_z[l], net->d_gz, n8);
     SQN_CK(cudaGetLastError());
     if ((st = weight_grad<32, 32>(net, B, net->d_a[l - 1], net->d_gz, 32, l, s)) != SQ_OK) return st;
     if ((st = conv32<EPI_PLAIN>(net, B, net->d_gz, net->d_wb[l], nullptr, nullptr, net->d_ga, s)) != SQ_OK)
       return st;
   }
   // layer 1 (1 -> 32): weights only
-  k_gelu_bwd<<<(unsigned)((n2 + 255) / 256), 256, 0, s>>>(net->d_ga, net->d_z[0], net->d_gz, n2);
+  k_gelu_bwd<<<(unsigned)((n8 + 255) / 256), 256, 0, s>>>(net->d_ga, net->d_z[0], net->d_gz, n8);
   SQN_CK(cudaGetLastError());
   return weight_grad<1, 32>(net, B, net->d_f, net->d_gz, 32, 0, s);
 }
