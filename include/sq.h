@@ -306,6 +306,14 @@ int sq_set_tiles(const sq_tile_config *tiles, int ntiles);
  * up makes sq_net_predict / sq_net_train_step return SQ_ETIMEOUT). 1 picks
  * the tile depth D in {2, 4} from the tile count, 2 or 4 fixes it; 0 uses the
  * mma.sync kernels. Results agree to FP32 rounding of the same BF16 inputs.
+ * SQ_OPT_PCG_GRAPHS (default 1): sq_pcg_solve replays a CUDA graph of two
+ * PCG iterations (twelve kernels) per host step instead of launching each
+ * kernel, captured on first use for the solve's fields, coefficients,
+ * preconditioner and options, and kept in the workspace (up to 8 graphs;
+ * any sq_set_option or sq_set_tiles call makes later solves capture anew).
+ * While profiling is enabled, or when the stream is being captured by the
+ * caller, kernels are launched one by one. 0 always launches them one by
+ * one. Results are identical.
  */
 enum sq_option {
   SQ_OPT_STRIDED_TWO_STAGE = 1,
@@ -313,7 +321,8 @@ enum sq_option {
   SQ_OPT_INNER_TOL_EXP = 3,
   SQ_OPT_WAIT_POLLS = 4,
   SQ_OPT_MULTIPLIER_TABLE = 5,
-  SQ_OPT_CONV_TC = 6
+  SQ_OPT_CONV_TC = 6,
+  SQ_OPT_PCG_GRAPHS = 7
 };
 int sq_set_option(int key, int value);
 

@@ -13,6 +13,7 @@ from .sq import (  # noqa: F401
     sq_coeffs_regenerate, sq_coeffs_set_subcell, sq_coeffs_set_levels, sq_build_coeffs_levels, sq_coeffs_regenerate_levels, sq_coeffs_from_host_levels, sq_coeffs_shape, sq_ensemble_ahom, sq_coeffs_upload, sq_homogenized_matrix, sq_homogenized_matrix_noalloc, sq_profile_class_name,
     sq_profile_enable, sq_profile_read, sq_profile_work, sq_pcg_solve, sq_precond_factors, sq_precond_setup, sq_precond_setup_canonical, sq_precond_setup_tucker, sq_precond_info, sq_rhs, sq_set_option, sq_set_tiles, sq_strerror, SQ_OPT_STRIDED_TWO_STAGE,
     SQ_OPT_STENCIL_ROWS, SQ_OPT_INNER_TOL_EXP, SQ_OPT_WAIT_POLLS, SQ_OPT_MULTIPLIER_TABLE, SQ_OPT_CONV_TC,
+    SQ_OPT_PCG_GRAPHS,
     sq_workspace_create, sq_launch_count, sq_probe_fma, sq_probe_copy,
     Coeffs2D, Precond2D, Workspace2D, sq2d_build_coeffs, sq2d_coeffs_from_host, sq2d_coeffs_set_subcell,
     sq2d_coeffs_cells, sq2d_precond_setup, sq2d_precond_factors, sq2d_workspace_create, sq2d_pcg_solve,

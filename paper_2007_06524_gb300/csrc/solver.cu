@@ -55,6 +55,15 @@ struct sq_workspace {
   Scalars *h_st;  // pinned copies of the two scalar blocks
   int *h_poll;    // pinned, 2 slots
   cudaEvent_t ev[2];
+  // CUDA graphs of kPollChunk steady-state PCG iterations (see pcg_loop),
+  // each with the signature of the launch parameters it bakes in
+  struct IterGraph {
+    std::vector<uint64_t> sig;
+    cudaGraph_t graph;
+    cudaGraphExec_t exec;
+    int kernels;
+  };
+  std::vector<IterGraph> graphs;
 };
 
 namespace {
@@ -443,6 +452,86 @@ int pcg_iteration(const sq_coeffs *c, const sq_precond *pc, T *x, T *r, T *p, T 
   return SQ_OK;
 }
 
+// ------------------------------------------------------- iteration graphs
+// Single solves replay a CUDA graph of kPollChunk steady-state iterations
+// (six kernels each) instead of launching every kernel from the host: at
+// small N the host's launch rate, not the GPU, paced a solve. A graph bakes in
+// every launch parameter, so it is found by a signature of them: the field
+// pointers, the reduction buffers, the coefficient and spectral descriptors
+// (field by field) and the option epoch, which every option or tile change
+// bumps. A workspace keeps the last kMaxGraphs graphs (one per output field
+// and precision in typical use). Profiling launches directly (its events
+// cannot sit inside a graph), and so does a call whose stream is being
+// captured already.
+int g_option_epoch = 0;  // bumped by sq_set_option and sq_set_tiles
+int g_pcg_graphs = 1;    // SQ_OPT_PCG_GRAPHS
+constexpr size_t kMaxGraphs = 8;
+
+template <typename T>
+std::vector<uint64_t> iter_signature(const sq_coeffs *c, const sq_precond *pc, const T *x, const T *r, const T *p,
+                                     const T *q, const T *Y, RedBuf rb) {
+  std::vector<uint64_t> v;
+  auto add = [&](uint64_t u) { v.push_back(u); };
+  auto addp = [&](const void *ptr) { add((uint64_t)(uintptr_t)ptr); };
+  auto addd = [&](double d) {
+    uint64_t u;
+    memcpy(&u, &d, sizeof(u));
+    add(u);
+  };
+  add(sizeof(T));
+  add((uint64_t)g_option_epoch);
+  addp(x), addp(r), addp(p), addp(q), addp(Y), addp(rb.st), addp(rb.partials);
+  const CellsDev cd = cells_dev(c);
+  addp(cd.phase), add(cd.L), add(cd.n), add(cd.N), addd(cd.a_lo), addd(cd.a_hi), add((uint64_t)cd.sub_lo);
+  add((uint64_t)cd.sub_hi), add(cd.layers);
+  for (double a : cd.a_up) addd(a);
+  const SpectralDev &sp = spec<T>(pc);
+  add(sp.N), add(sp.rank), addp(sp.tw), addp(sp.lam), addp(sp.u), addd(sp.scale), addp(sp.gtab);
+  return v;
+}
+
+// The graph for these launch parameters: found in the workspace, or
+// captured (on a private stream) and instantiated.
+template <typename T>
+int iter_graph(sq_workspace *w, const sq_coeffs *c, const sq_precond *pc, T *x, T *r, T *p, T *q, T *Y, RedBuf rb,
+               cudaGraphExec_t *exec, int *kernels) {
+  std::vector<uint64_t> sig = iter_signature<T>(c, pc, x, r, p, q, Y, rb);
+  for (const sq_workspace::IterGraph &e : w->graphs) {
+    if (e.sig == sig) {
+      *exec = e.exec;
+      *kernels = e.kernels;
+      return SQ_OK;
+    }
+  }
+  if (w->graphs.size() >= kMaxGraphs) {
+    cudaGraphExecDestroy(w->graphs.front().exec);
+    cudaGraphDestroy(w->graphs.front().graph);
+    w->graphs.erase(w->graphs.begin());
+  }
+  cudaStream_t cs;
+  SQ_CK(cudaStreamCreateWithFlags(&cs, cudaStreamNonBlocking));
+  const int64_t l0 = g_launches;
+  int st = SQ_OK;
+  if (cudaStreamBeginCapture(cs, cudaStreamCaptureModeThreadLocal) != cudaSuccess) st = SQ_ECUDA;
+  for (int i = 0; st == SQ_OK && i < kPollChunk; ++i) st = pcg_iteration<T>(c, pc, x, r, p, q, Y, rb, cs);
+  cudaGraph_t g = nullptr;
+  if (cudaStreamEndCapture(cs, &g) != cudaSuccess || !g) st = SQ_ECUDA;
+  cudaGraphExec_t ge = nullptr;
+  if (st == SQ_OK && cudaGraphInstantiate(&ge, g, 0) != cudaSuccess) st = SQ_ECUDA;
+  cudaStreamDestroy(cs);
+  const int nk = (int)(g_launches - l0);
+  g_launches = l0;  // counted when replayed
+  if (st != SQ_OK) {
+    if (ge) cudaGraphExecDestroy(ge);
+    if (g) cudaGraphDestroy(g);
+    return st;
+  }
+  w->graphs.push_back(sq_workspace::IterGraph{std::move(sig), g, ge, nk});
+  *exec = ge;
+  *kernels = nk;
+  return SQ_OK;
+}
+
 // Runs PCG iterations until the device sets `done` (converged, max_iter or
 // breakdown) or `budget` iterations were launched. Polls one chunk behind.
 template <typename T>
@@ -459,11 +548,26 @@ int pcg_loop(sq_workspace *w, const sq_coeffs *c, const sq_precond *pc, T *x, T 
   bool pending[2] = {false, false};
   w->h_poll[0] = w->h_poll[1] = 0;
   const size_t done_off = offsetof(Scalars, done);
+  cudaGraphExec_t gx = nullptr;
+  int gk = 0;
+  if (g_pcg_graphs && !g_prof.on && budget >= chunk) {
+    cudaStreamCaptureStatus cap = cudaStreamCaptureStatusNone;
+    SQ_CK(cudaStreamIsCapturing(s, &cap));
+    if (cap == cudaStreamCaptureStatusNone) {
+      const int st = iter_graph<T>(w, c, pc, x, r, p, q, Y, rb, &gx, &gk);
+      if (st != SQ_OK) return st;
+    }
+  }
   while (launched < budget) {
     const int nb = (budget - launched < chunk) ? budget - launched : chunk;
-    for (int i = 0; i < nb; ++i) {
-      int st = pcg_iteration<T>(c, pc, x, r, p, q, Y, rb, s);
-      if (st != SQ_OK) return st;
+    if (gx && nb == chunk) {
+      SQ_CK(cudaGraphLaunch(gx, s));
+      g_launches += gk;
+    } else {
+      for (int i = 0; i < nb; ++i) {
+        int st = pcg_iteration<T>(c, pc, x, r, p, q, Y, rb, s);
+        if (st != SQ_OK) return st;
+      }
     }
     launched += nb;
     SQ_CK(cudaMemcpyAsync(&w->h_poll[slot], reinterpret_cast<char *>(rb.st) + done_off, sizeof(int),
@@ -1114,6 +1218,7 @@ int sq_precond_info(const sq_precond *p, int *rank, double *max_rel_err) {
 
 int sq_set_tiles(const sq_tile_config *tiles, int ntiles) {
   if (ntiles < 0 || (ntiles > 0 && !tiles)) return SQ_EINVAL;
+  ++g_option_epoch;  // launch parameters may change: no stored iteration graph applies
   for (int k = 0; k < ntiles; ++k) {
     const int N = tiles[k].N;
     if (!valid_N(N)) return SQ_EINVAL;
@@ -1134,6 +1239,12 @@ int sq_set_tiles(const sq_tile_config *tiles, int ntiles) {
 }
 
 int sq_set_option(int key, int value) {
+  ++g_option_epoch;  // launch parameters may change: no stored iteration graph applies
+  if (key == SQ_OPT_PCG_GRAPHS) {
+    if (value < 0 || value > 1) return SQ_EINVAL;
+    g_pcg_graphs = value;
+    return SQ_OK;
+  }
   if (key == SQ_OPT_STRIDED_TWO_STAGE) return set_strided_fast(value) == 0 ? SQ_OK : SQ_EINVAL;
   if (key == SQ_OPT_STENCIL_ROWS) return set_stencil_rows(value) == 0 ? SQ_OK : SQ_EINVAL;
   if (key == SQ_OPT_INNER_TOL_EXP) return set_inner_tol_exp(value) == 0 ? SQ_OK : SQ_EINVAL;
@@ -1197,6 +1308,10 @@ void sq_workspace_destroy(sq_workspace *w) {
   if (w->h_poll) cudaFreeHost(w->h_poll);
   if (w->ev[0]) cudaEventDestroy(w->ev[0]);
   if (w->ev[1]) cudaEventDestroy(w->ev[1]);
+  for (sq_workspace::IterGraph &e : w->graphs) {
+    cudaGraphExecDestroy(e.exec);
+    cudaGraphDestroy(e.graph);
+  }
   delete w;
 }
 

@@ -19,6 +19,7 @@ SQ_OPT_INNER_TOL_EXP = 3
 SQ_OPT_WAIT_POLLS = 4
 SQ_OPT_MULTIPLIER_TABLE = 5
 SQ_OPT_CONV_TC = 6
+SQ_OPT_PCG_GRAPHS = 7
 
 _HERE = os.path.dirname(os.path.abspath(__file__))
 _LIB = None

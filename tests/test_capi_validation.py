@@ -148,8 +148,12 @@ def test_options_ranges_and_defaults(sq):
             sq.sq_set_option(sq.SQ_OPT_STENCIL_ROWS, v)
         for v in range(2, 8):
             sq.sq_set_option(sq.SQ_OPT_INNER_TOL_EXP, v)
-        for key in (0, 7, 99):
+        for key in (0, 8, 99):
             _einval(sq, sq.sq_set_option, key, 1)
+        for v in (0, 1):
+            sq.sq_set_option(sq.SQ_OPT_PCG_GRAPHS, v)
+        for v in (-1, 2):
+            _einval(sq, sq.sq_set_option, sq.SQ_OPT_PCG_GRAPHS, v)
         for v in (0, 2, 4, 1):
             sq.sq_set_option(sq.SQ_OPT_CONV_TC, v)
         for v in (-1, 3, 8):
@@ -162,6 +166,7 @@ def test_options_ranges_and_defaults(sq):
         sq.sq_set_option(sq.SQ_OPT_INNER_TOL_EXP, 5)
         sq.sq_set_option(sq.SQ_OPT_MULTIPLIER_TABLE, 1)
         sq.sq_set_option(sq.SQ_OPT_CONV_TC, 1)
+        sq.sq_set_option(sq.SQ_OPT_PCG_GRAPHS, 1)
 
 
 def test_tile_overrides_reject_bad_entries(sq):

@@ -642,3 +642,41 @@ def test_pass_e_tile_width(sq, Pe):
         sq.sq_set_tiles([])
     assert info["status"] == sq.SQ_OK and info["relres_true"] <= 1e-10
     assert np.linalg.norm(_host(psi) - ref) / np.linalg.norm(ref) <= 1e-6
+
+
+@pytest.mark.parametrize("precision", [0, 1])
+def test_iteration_graphs_match_direct_launches(sq, precision):
+    """Single solves replay a CUDA graph of two PCG iterations (SQ_OPT_PCG_GRAPHS
+    = 1) or launch every kernel (0): the same kernels with the same parameters,
+    so psi, the iteration counts and the number of kernels launched agree
+    exactly, for a second output field (a second stored graph) and after an
+    option change (a new capture); and the result matches the oracle."""
+    import torch
+
+    L, n, seed, rank = 8, 8, 4, 8
+    N = L * n
+    re = problem.realization(L, n, seed, 1.0, 100.0)
+    ref = pcg.tight_solve(re.A, re.b[2], re.N)[0]
+    c = sq.sq_build_coeffs(L, n, seed, 0.5, 1.0, 100.0)
+    pc = sq.sq_precond_setup(N, rank)
+    w = sq.sq_workspace_create(N, precision)
+    outs = {}
+    try:
+        for mode in (0, 1):
+            sq.sq_set_option(sq.SQ_OPT_PCG_GRAPHS, mode)
+            runs = []
+            for k in range(3):
+                if k == 2:  # a new option epoch: the next solve captures again
+                    sq.sq_set_option(sq.SQ_OPT_MULTIPLIER_TABLE, 1)
+                psi = torch.full((N ** 3,), float(k), dtype=torch.float64, device="cuda")
+                l0 = sq.sq_launch_count()
+                info = sq.sq_pcg_solve(c, pc, w, 2, 1e-10, 2000, precision, None, psi)
+                runs.append((_host(psi), info["iters"], info["status"], sq.sq_launch_count() - l0))
+            outs[mode] = runs
+    finally:
+        sq.sq_set_option(sq.SQ_OPT_PCG_GRAPHS, 1)
+    for (x0, it0, st0, l0), (x1, it1, st1, l1) in zip(outs[0], outs[1]):
+        assert st0 == st1 == sq.SQ_OK
+        assert it0 == it1 and l0 == l1
+        assert np.array_equal(x0, x1)
+        assert np.linalg.norm(x1 - ref) / np.linalg.norm(ref) <= 1e-6
