@@ -307,8 +307,9 @@ int sq_set_tiles(const sq_tile_config *tiles, int ntiles);
  * the tile depth D in {2, 4} from the tile count, 2 or 4 fixes it; 0 uses the
  * mma.sync kernels. Results agree to FP32 rounding of the same BF16 inputs.
  * SQ_OPT_PCG_GRAPHS (default 1): sq_pcg_solve replays a CUDA graph of two
- * PCG iterations (twelve kernels) per host step instead of launching each
- * kernel, captured on first use for the solve's fields, coefficients,
+ * PCG iterations (twelve kernels; eight for sq2d_pcg_solve) per host step
+ * instead of launching each kernel, captured on first use for the solve's
+ * fields, coefficients,
  * preconditioner and options, and kept in the workspace (up to 8 graphs;
  * any sq_set_option or sq_set_tiles call makes later solves capture anew).
  * While profiling is enabled, or when the stream is being captured by the

@@ -407,6 +407,8 @@ int set_stencil_rows(int rpt);  // FP32 operator rows per thread: 0 auto, 1, 2, 
 int set_stencil_rows_override(int N, int rpt);  // per grid size; 0 = the process-wide choice
 int set_strided_fast(int on);  // 0: generic Stockham tiles for every pass
 int set_use_gtab(int on);      // 0: pass C evaluates the multiplier on the fly everywhere
+int pcg_graphs_enabled();     // single solves replay iteration graphs (SQ_OPT_PCG_GRAPHS)
+int option_epoch();           // bumped by every option or tile change
 int set_conv_tc(int on);       // warm-start net: 32 -> 32 convolutions on tcgen05 (1) or mma.sync (0)
 int use_gtab();
 

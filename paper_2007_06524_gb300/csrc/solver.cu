@@ -466,6 +466,14 @@ int pcg_iteration(const sq_coeffs *c, const sq_precond *pc, T *x, T *r, T *p, T 
 int g_option_epoch = 0;  // bumped by sq_set_option and sq_set_tiles
 int g_pcg_graphs = 1;    // SQ_OPT_PCG_GRAPHS
 constexpr size_t kMaxGraphs = 8;
+}  // namespace
+
+namespace sq {
+int pcg_graphs_enabled() { return g_pcg_graphs; }
+int option_epoch() { return g_option_epoch; }
+}  // namespace sq
+
+namespace {
 
 template <typename T>
 std::vector<uint64_t> iter_signature(const sq_coeffs *c, const sq_precond *pc, const T *x, const T *r, const T *p,

@@ -236,6 +236,13 @@ struct sq2d_workspace {
   Scalars *h_st = nullptr;
   int *h_poll = nullptr;
   cudaEvent_t ev[2] = {nullptr, nullptr};
+  // CUDA graphs of kPollChunk iterations (see loop2d) with their signatures
+  struct IterGraph {
+    std::vector<uint64_t> sig;
+    cudaGraph_t graph;
+    cudaGraphExec_t exec;
+  };
+  std::vector<IterGraph> graphs;
 };
 
 namespace {
@@ -300,6 +307,58 @@ int iteration2d(const Cells2D &cd, const sq2d_precond *pc, double *x, double *r,
   return SQ_OK;
 }
 
+// A chunk of iterations as one replayed CUDA graph, as for the 3D solves
+// (SQ_OPT_PCG_GRAPHS): found by a signature of every launch parameter it
+// bakes in (fields, reduction buffers, the cell and spectral descriptors,
+// the option epoch), or captured on a private stream.
+int graph2d(sq2d_workspace *w, const Cells2D &cd, const sq2d_precond *pc, double *x, double *r, double *p, double *q,
+            double *Y, RedBuf rb, cudaGraphExec_t *exec) {
+  std::vector<uint64_t> sig;
+  auto add = [&](uint64_t u) { sig.push_back(u); };
+  auto addp = [&](const void *ptr) { add((uint64_t)(uintptr_t)ptr); };
+  auto addd = [&](double d) {
+    uint64_t u;
+    memcpy(&u, &d, sizeof(u));
+    add(u);
+  };
+  add((uint64_t)option_epoch());
+  addp(x), addp(r), addp(p), addp(q), addp(Y), addp(rb.st), addp(rb.partials);
+  addp(cd.phase), add(cd.L), add(cd.n), add(cd.N), add((uint64_t)cd.sub_lo), add((uint64_t)cd.sub_hi);
+  for (double e : cd.edge) addd(e);
+  for (double e : cd.diag) addd(e);
+  add(pc->sp.N), add(pc->sp.rank), addp(pc->sp.tw), addp(pc->sp.lam), addp(pc->sp.u), addd(pc->sp.scale);
+  addp(pc->sp.gtab);
+  for (const sq2d_workspace::IterGraph &e : w->graphs) {
+    if (e.sig == sig) {
+      *exec = e.exec;
+      return SQ_OK;
+    }
+  }
+  if (w->graphs.size() >= 8) {
+    cudaGraphExecDestroy(w->graphs.front().exec);
+    cudaGraphDestroy(w->graphs.front().graph);
+    w->graphs.erase(w->graphs.begin());
+  }
+  cudaStream_t cs;
+  SQ2_CK(cudaStreamCreateWithFlags(&cs, cudaStreamNonBlocking));
+  int st = SQ_OK;
+  if (cudaStreamBeginCapture(cs, cudaStreamCaptureModeThreadLocal) != cudaSuccess) st = SQ_ECUDA;
+  for (int i = 0; st == SQ_OK && i < kPollChunk; ++i) st = iteration2d(cd, pc, x, r, p, q, Y, rb, cs);
+  cudaGraph_t g = nullptr;
+  if (cudaStreamEndCapture(cs, &g) != cudaSuccess || !g) st = SQ_ECUDA;
+  cudaGraphExec_t ge = nullptr;
+  if (st == SQ_OK && cudaGraphInstantiate(&ge, g, 0) != cudaSuccess) st = SQ_ECUDA;
+  cudaStreamDestroy(cs);
+  if (st != SQ_OK) {
+    if (ge) cudaGraphExecDestroy(ge);
+    if (g) cudaGraphDestroy(g);
+    return st;
+  }
+  w->graphs.push_back(sq2d_workspace::IterGraph{std::move(sig), g, ge});
+  *exec = ge;
+  return SQ_OK;
+}
+
 // Iterations in chunks of kPollChunk, polling the device's stop flag one chunk behind.
 int loop2d(sq2d_workspace *w, const Cells2D &cd, const sq2d_precond *pc, double *x, double *r, double *p, double *q,
            double *Y, RedBuf rb, int budget, cudaStream_t s) {
@@ -308,11 +367,24 @@ int loop2d(sq2d_workspace *w, const Cells2D &cd, const sq2d_precond *pc, double 
   bool pending[2] = {false, false};
   w->h_poll[0] = w->h_poll[1] = 0;
   const size_t done_off = offsetof(Scalars, done);
+  cudaGraphExec_t gx = nullptr;
+  if (pcg_graphs_enabled() && budget >= chunk) {
+    cudaStreamCaptureStatus cap = cudaStreamCaptureStatusNone;
+    SQ2_CK(cudaStreamIsCapturing(s, &cap));
+    if (cap == cudaStreamCaptureStatusNone) {
+      const int st = graph2d(w, cd, pc, x, r, p, q, Y, rb, &gx);
+      if (st != SQ_OK) return st;
+    }
+  }
   while (launched < budget) {
     const int nb = (budget - launched < chunk) ? budget - launched : chunk;
-    for (int i = 0; i < nb; ++i) {
-      const int st = iteration2d(cd, pc, x, r, p, q, Y, rb, s);
-      if (st != SQ_OK) return st;
+    if (gx && nb == chunk) {
+      SQ2_CK(cudaGraphLaunch(gx, s));
+    } else {
+      for (int i = 0; i < nb; ++i) {
+        const int st = iteration2d(cd, pc, x, r, p, q, Y, rb, s);
+        if (st != SQ_OK) return st;
+      }
     }
     launched += nb;
     SQ2_CK(cudaMemcpyAsync(&w->h_poll[slot], reinterpret_cast<char *>(rb.st) + done_off, sizeof(int),
@@ -520,6 +592,10 @@ void sq2d_workspace_destroy(sq2d_workspace *w) {
   if (w->h_poll) cudaFreeHost(w->h_poll);
   for (int i = 0; i < 2; ++i)
     if (w->ev[i]) cudaEventDestroy(w->ev[i]);
+  for (sq2d_workspace::IterGraph &e : w->graphs) {
+    cudaGraphExecDestroy(e.exec);
+    cudaGraphDestroy(e.graph);
+  }
   delete w;
 }
 

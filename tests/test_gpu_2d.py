@@ -228,3 +228,40 @@ def test_invalid_arguments(sq):
         sq.sq2d_pcg_solve(c, pc, w, 0, 1e-8, 100, psi)  # N mismatch
     with pytest.raises(sq.SqError):
         sq.sq2d_pcg_solve(c, sq.sq2d_precond_setup(32, 0), w, 2, 1e-8, 100, psi)
+
+
+def test_iteration_graphs_match_direct_launches_2d(sq):
+    """2D solves replay a CUDA graph of two iterations (SQ_OPT_PCG_GRAPHS = 1)
+    or launch every kernel (0): identical psi and iteration counts, for both
+    directions (two stored graphs) and after an option change (a new
+    capture); both match the oracle."""
+    import torch
+
+    L, n, rank = 32, 4, 8
+    N = L * n
+    ph = solver2d.cell_phases_2d_vec(L, 9)
+    c = sq.sq2d_build_coeffs(L, n, 9, 0.5, 0.4, 1.0)
+    sq.sq2d_coeffs_set_subcell(c, 2)
+    V = solver2d.voxel_field_2d(ph, n, 0.4, 1.0, 2)
+    psis_o = solver2d.solve_2d(V, tol=1e-13)[0]
+    pc = sq.sq2d_precond_setup(N, rank)
+    w = sq.sq2d_workspace_create(N)
+    outs = {}
+    try:
+        for mode in (0, 1):
+            sq.sq_set_option(sq.SQ_OPT_PCG_GRAPHS, mode)
+            runs = []
+            for k in range(3):
+                if k == 2:
+                    sq.sq_set_option(sq.SQ_OPT_MULTIPLIER_TABLE, 1)
+                psi = torch.full((N * N,), float(k), dtype=torch.float64, device="cuda")
+                info = sq.sq2d_pcg_solve(c, pc, w, k % 2, 1e-12, 4000, psi)
+                runs.append((psi.cpu().numpy(), info["iters"], info["status"]))
+            outs[mode] = runs
+    finally:
+        sq.sq_set_option(sq.SQ_OPT_PCG_GRAPHS, 1)
+    for k, ((x0, it0, st0), (x1, it1, st1)) in enumerate(zip(outs[0], outs[1])):
+        assert st0 == st1 == sq.SQ_OK and it0 == it1
+        assert np.array_equal(x0, x1)
+        ref = psis_o[k % 2].ravel()
+        assert np.linalg.norm(x1 - ref) / np.linalg.norm(ref) <= 1e-9
