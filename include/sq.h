@@ -243,9 +243,12 @@ typedef struct sq_solve_desc {
   double *psi;             /* device, N^3 doubles: the solution (zero mean)     */
 } sq_solve_desc;
 
-/* Tile shape per grid size (0 = default): Hartley-pass tile of `dht_pencils`
+/* Tile shape per grid size; an entry sets every field for its N, and 0
+ * restores that field's default. Hartley-pass tile of `dht_pencils`
  * complex pencils (a power of two, 2*dht_pencils dividing N), operator work
- * items of `stencil_planes` x1-planes (register kernels), the FP32 operator
+ * items of `stencil_planes` x1-planes (register kernels; for the staged
+ * kernel, the planes each block marches, at least 4; its default fills one
+ * wave of blocks), the FP32 operator
  * variant of single solves `stencil_rows` (1, 2, 4 node rows per thread, or 8
  * for the shared-memory-staged kernel; see SQ_OPT_STENCIL_ROWS; batches use
  * 1), and `dht_pencils_e`, the tile of the last FP32 pass of a PCG iteration

@@ -85,7 +85,7 @@ def tune(torch, N, L=None, n=None, cache=DEFAULT_CACHE, reps=5):
     for rows in (1, 2, 4, 8):
         if N % (32 if rows == 8 else rows) != 0:
             continue
-        for zc in ((0,) if rows == 8 else (4, 8, 16, 32)):  # the staged kernel sizes its own plane runs
+        for zc in ((0,) if rows == 8 else (4, 8, 16, 32)):  # the staged kernel's runs are tuned in solves below
             if zc > N:
                 continue
             try:
@@ -110,11 +110,26 @@ def tune(torch, N, L=None, n=None, cache=DEFAULT_CACHE, reps=5):
         times_e[Pe] = _time(torch, lambda: _sq.sq_pcg_solve(c, pc, wr, 0, 1e-30, 24, _sq.SQ_FP32_REFINE, None, psi),
                             reps)
     bestE = min(times_e, key=times_e.get)
+    # The staged operator's plane run per block, also inside solves: its
+    # default fills one wave of blocks, and shorter or longer runs trade the
+    # per-block set-up against the block count. (Timed alone after an L2
+    # flush, the ranking did not carry over into solves.)
+    times_s = {}
+    if bestR == 8:
+        times_s[0] = times_e[bestE]
+        for zc in (N // 8, N // 4, N // 2):
+            if zc < 4:
+                continue
+            _sq.sq_set_tiles([(N, bestP, zc, bestR, bestE)])
+            times_s[zc] = _time(torch, lambda: _sq.sq_pcg_solve(c, pc, wr, 0, 1e-30, 24, _sq.SQ_FP32_REFINE, None,
+                                                                psi), reps)
+        bestZ = min(times_s, key=times_s.get)
     _sq.sq_set_tiles([(N, bestP, bestZ, bestR, bestE)])
     table[key] = {"dht_pencils": bestP, "stencil_planes": bestZ, "stencil_rows": bestR, "dht_pencils_e": bestE,
                   "precond_ms": {str(k): round(v, 4) for k, v in times_p.items()},
                   "operator_ms": {f"{k[0]}x{k[1]}": round(v, 4) for k, v in times_z.items()},
-                  "solve24_ms": {str(k): round(v, 4) for k, v in times_e.items()}}
+                  "solve24_ms": {str(k): round(v, 4) for k, v in times_e.items()},
+                  "staged_runs_solve24_ms": {str(k): round(v, 4) for k, v in times_s.items()}}
     if cache:
         os.makedirs(os.path.dirname(cache), exist_ok=True)
         json.dump(table, open(cache, "w"), indent=1)

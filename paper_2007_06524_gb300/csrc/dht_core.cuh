@@ -658,8 +658,13 @@ __device__ __forceinline__ void x3_stage1(const DhtTile<T> &a, size_t row0, C *s
   constexpr int SJ = x3pos(N);
   constexpr int HC = R0 > 8 ? 8 : R0;
   const T alpha = a.alpha;
-  const T *inp = a.in;
-  const T *qp = a.q;
+  // With the residual update r is read and written through one pointer (the
+  // offsets of a butterfly's chunks are distinct constants, so the compiler
+  // may issue a chunk's loads ahead of the previous chunk's stores), and q,
+  // which nothing writes during the pass, through a restricted one.
+  const bool resid = LOADM == LD_RESID && !a.first;
+  const T *inp = resid ? a.r : a.in;
+  const T *__restrict__ qp = a.q;
   for (int t = threadIdx.x; t < R1 * P; t += kThreads) {
     const int p = t / R1, b = t - p * R1;
     const size_t ga = (row0 + 2 * p) * N + b, gb = ga + N;

@@ -1230,10 +1230,11 @@ int sq_set_tiles(const sq_tile_config *tiles, int ntiles) {
   for (int k = 0; k < ntiles; ++k) {
     const int N = tiles[k].N;
     if (!valid_N(N)) return SQ_EINVAL;
-    if (tiles[k].dht_pencils && set_dht_pencils_override(N, tiles[k].dht_pencils) != 0) return SQ_EINVAL;
-    if (tiles[k].stencil_planes && set_stencil_planes_override(N, tiles[k].stencil_planes) != 0) return SQ_EINVAL;
-    if (tiles[k].stencil_rows && set_stencil_rows_override(N, tiles[k].stencil_rows) != 0) return SQ_EINVAL;
-    if (tiles[k].dht_pencils_e && set_dht_pencils_e_override(N, tiles[k].dht_pencils_e) != 0) return SQ_EINVAL;
+    // an entry sets every field of its grid size, 0 restoring the default
+    if (set_dht_pencils_override(N, tiles[k].dht_pencils) != 0) return SQ_EINVAL;
+    if (set_stencil_planes_override(N, tiles[k].stencil_planes) != 0) return SQ_EINVAL;
+    if (set_stencil_rows_override(N, tiles[k].stencil_rows) != 0) return SQ_EINVAL;
+    if (set_dht_pencils_e_override(N, tiles[k].dht_pencils_e) != 0) return SQ_EINVAL;
   }
   if (ntiles == 0) {
     for (int N = 8; N <= kMaxN; ++N) {

@@ -144,6 +144,8 @@ static int resident_blocks(const void *kern, int threads, size_t smem) {
   return blocks;
 }
 
+static int g_planes_override[kMaxN + 1] = {0};  // FP32 operator planes per work item, per N (0 = default)
+
 // Staged FP32 operator over one (tile, plane run) per block; see stencil_staged_run.
 template <bool GEN>
 __global__ void __launch_bounds__(kThreads, 3) k_stencil_staged(CellsDev c, const float *__restrict__ x,
@@ -180,7 +182,8 @@ static cudaError_t launch_stencil_staged(const CellsDev &c, const float *x, floa
   int nz = resident / ntiles;
   if (nz > N / 4) nz = N / 4;  // at least 4 planes per block
   if (nz < 1) nz = 1;
-  const int zc = (N + nz - 1) / nz;
+  int zc = (N + nz - 1) / nz;  // one wave of resident blocks
+  if (g_planes_override[N] >= 4) zc = g_planes_override[N];  // a tuned plane run (longer runs, fewer blocks)
   nz = (N + zc - 1) / zc;
   const long long grid = (long long)ntiles * nz;
   if (grid > kMaxPartials) return cudaErrorInvalidConfiguration;
@@ -188,7 +191,6 @@ static cudaError_t launch_stencil_staged(const CellsDev &c, const float *x, floa
   return cudaGetLastError();
 }
 
-static int g_planes_override[kMaxN + 1] = {0};
 static int g_stencil_rows = 0;  // FP32 operator: 0 automatic, 1 / 2 / 4 rows per thread, 8 staged
 
 static int g_rows_override[kMaxN + 1] = {0};

@@ -125,6 +125,26 @@ def test_operator_fp32_rows_per_thread(sq, rows, L, n, seed):
     assert _relmax(_host(y).astype(np.float64), re.A @ psi.ravel().astype(np.float64)) <= 1e-5
 
 
+@pytest.mark.parametrize("zc", [4, 7, 64])
+def test_staged_operator_plane_runs(sq, zc):
+    """The staged FP32 operator with a tuned plane run per block (4, 7 which
+    does not divide N, and the whole axis) against the oracle's operator."""
+    import torch
+
+    L, n, seed = 8, 8, 5
+    N = L * n
+    re = problem.realization(L, n, seed, 1.0, 100.0)
+    c = sq.sq_build_coeffs(L, n, seed, 0.5, 1.0, 100.0)
+    psi = inputs.random_field(N, seed + 3, np.float32)
+    y = torch.empty(N ** 3, dtype=torch.float32, device="cuda")
+    try:
+        sq.sq_set_tiles([(N, 0, zc, 8)])
+        sq.sq_apply_operator_f32(c, _dev(psi.ravel(), "float32"), y)
+    finally:
+        sq.sq_set_tiles([])
+    assert _relmax(_host(y).astype(np.float64), re.A @ psi.ravel().astype(np.float64)) <= 1e-5
+
+
 @pytest.mark.parametrize("rows", [1, 2, 4, 8])
 def test_fp32_refinement_rows_per_thread(sq, rows):
     # p.Ap of the inner FP32 iteration comes from the operator's reduction
