@@ -301,8 +301,9 @@ int sq_set_tiles(const sq_tile_config *tiles, int ntiles);
  * with the exact diagonal and batches always evaluate it on the fly. Results
  * agree to rounding.
  * SQ_OPT_CONV_TC (default 1): the warm-start net's 32 -> 32 channel
- * convolutions (forward and data gradient) run on the 5th-generation tensor
- * cores as direct convolutions: the input halo of a tile of 8 x 16 x D output
+ * convolutions (forward and data gradient) and the output layer's forward
+ * convolution (32 -> 3 channels, 16 accumulator columns) run on the
+ * 5th-generation tensor cores as direct convolutions: the input halo of a tile of 8 x 16 x D output
  * voxels is staged once in shared memory and every tap's A operand is that
  * halo read through a shifted descriptor (tcgen05.mma, M = 128 voxels, N = 32,
  * K = 16, FP32 accumulator in tensor memory; bounded waits: a wait that gives

@@ -202,28 +202,38 @@ __global__ void __launch_bounds__(256) k_conv_mma(const __nv_bfloat16 *__restric
 constexpr int kTcThreads = 384;
 constexpr int kTcStageThreads = 96;  // warps 1-3
 constexpr int kTcReadWarps = 8;      // warps 4-11
-constexpr int kTcWeightBytes = 27 * 2 * 1024;
-template <int TZC>
+// weights of a layer with COUT output channels: 54 chunks (tap, K half) of
+// COUT rows x 16 input channels
+__host__ __device__ constexpr int tc_weight_bytes(int cout) { return 27 * 2 * cout * 32; }
+template <int TZC, int COUT = 32>
 struct TcTile {
   static constexpr int HV = (TZC + 2) * 18 * 10;                   // halo voxels
   static constexpr int Plane = (HV * 16 + 127) / 128 * 128 + 32;   // bytes, 32 mod 128: conflict-free staging
   static constexpr int Buf = 4 * Plane;                            // one halo: 4 planes of 8 channels
-  static constexpr int Smem = 2 * Buf + kTcWeightBytes + 1024;     // + 1 KB of alignment slack
-  static constexpr int Cols = 2 * TZC * 32;                        // two accumulator sets
+  static constexpr int Smem = 2 * Buf + tc_weight_bytes(COUT) + 1024;  // + 1 KB of alignment slack
+  static constexpr int Cols = 2 * TZC * COUT;                           // two accumulator sets
+  static_assert(Cols >= 32 && (Cols & (Cols - 1)) == 0, "TMEM allocation: a power of two >= 32 columns");
   // the last byte an A descriptor can reach (plane 2 kc + 1, last z-plane, tap
   // (2, 2, 2), row 127, k 15) stays inside its halo buffer
   static_assert(2 * Plane + ((TZC + 1) * 18 + 2) * 160 + 32 + 15 * 160 + Plane + 7 * 16 + 14 < Buf, "halo extent");
   static_assert(kTcStageThreads >= 80, "staging: 20 threads per piece, 4 pieces");
 };
 
-template <int EPI, int TZC>
+// COUT = 16 with EPI_OUT is the output layer: weights [tap][wrows][32] with
+// rows >= wrows zero, bias and out_scale for channels 0..2, FP32 fields
+// fout[sample][channel][voxel].
+template <int EPI, int TZC, int COUT = 32>
 __global__ void __launch_bounds__(kTcThreads, 1) k_conv_tc(const __nv_bfloat16 *__restrict__ in,
                                                            const __nv_bfloat16 *__restrict__ wt,
                                                            const float *__restrict__ bias,
                                                            __nv_bfloat16 *__restrict__ zout,
                                                            __nv_bfloat16 *__restrict__ aout, int N, int ntiles,
-                                                           int wait_polls, int *__restrict__ err) {
-  using T = TcTile<TZC>;
+                                                           int wait_polls, int *__restrict__ err,
+                                                           float *__restrict__ fout = nullptr, float out_scale = 1.f,
+                                                           int wrows = 32) {
+  using T = TcTile<TZC, COUT>;
+  static_assert(COUT == 32 || (COUT == 16 && EPI == EPI_OUT), "32-channel layers, or the output layer");
+  constexpr int kChunk = COUT * 32, kLbo = COUT * 16;  // weight chunk bytes; offset of its second K half
   extern __shared__ __align__(1024) unsigned char smc[];
   __shared__ __align__(8) unsigned long long full[2], done[2], drained[2];
   __shared__ unsigned tmem_base;
@@ -232,11 +242,14 @@ __global__ void __launch_bounds__(kTcThreads, 1) k_conv_tc(const __nv_bfloat16 *
   const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
   unsigned char *wsm = smc + 2 * T::Buf;
   if (EPI == EPI_GELU && tid < 32) s_bias[tid] = bias[tid];
+  if (EPI == EPI_OUT && tid < 3) s_bias[tid] = bias[tid];
   // weights [tap][cout][cin] -> chunk (tap, cin half): row n = cout, 16-byte pieces of 8 cin
-  for (int e = tid; e < 27 * 32 * 4; e += kTcThreads) {
-    const int tap = e >> 7, r = e & 127, n = r >> 2, g8 = r & 3;
-    const uint4 v = *reinterpret_cast<const uint4 *>(wt + ((size_t)(tap * 32 + n) * 32 + g8 * 8));
-    *reinterpret_cast<uint4 *>(wsm + (tap * 2 + (g8 >> 1)) * 1024 + (n >> 3) * 128 + (g8 & 1) * 512 + (n & 7) * 16) = v;
+  for (int e = tid; e < 27 * COUT * 4; e += kTcThreads) {
+    const int tap = e / (COUT * 4), r = e - tap * (COUT * 4), n = r >> 2, g8 = r & 3;
+    const uint4 v = (n < wrows) ? *reinterpret_cast<const uint4 *>(wt + ((size_t)(tap * wrows + n) * 32 + g8 * 8))
+                                : make_uint4(0u, 0u, 0u, 0u);
+    *reinterpret_cast<uint4 *>(wsm + (tap * 2 + (g8 >> 1)) * kChunk + (n >> 3) * 128 + (g8 & 1) * kLbo +
+                               (n & 7) * 16) = v;
   }
   if (warp == 0) {
     tc::tmem_alloc(&tmem_base, T::Cols);
@@ -272,11 +285,11 @@ __global__ void __launch_bounds__(kTcThreads, 1) k_conv_tc(const __nv_bfloat16 *
   int last = -1;  // (warp 0, lane 0) the last tile whose MMAs were issued
   if (warp == 0) {
     if (lane == 0) {
-      constexpr uint32_t idesc = tc::idesc_bf16_f32(128, 32);
+      constexpr uint32_t idesc = tc::idesc_bf16_f32(128, COUT);
       // descriptors: the start address (>> 4) sits in the low 14 bits and no
       // offset carries out of them (shared addresses < 256 KB), so a tap's
       // offset is added to the low word only
-      const uint64_t b64 = tc::sdesc(tc::smem_u32(wsm), 512u, 128u);
+      const uint64_t b64 = tc::sdesc(tc::smem_u32(wsm), (unsigned)kLbo, 128u);
       const uint32_t b_lo = (uint32_t)b64, b_hi = (uint32_t)(b64 >> 32);
       for (int t = 0; t < my_tiles; ++t) {
         const int b = t & 1;
@@ -291,7 +304,7 @@ __global__ void __launch_bounds__(kTcThreads, 1) k_conv_tc(const __nv_bfloat16 *
         tc::fence_after_sync();
         const uint64_t a64 = tc::sdesc(smc_s + (unsigned)b * T::Buf, T::Plane, 160u);
         const uint32_t a_hi = (uint32_t)(a64 >> 32);
-        const unsigned d0 = tmem + (unsigned)b * (TZC * 32);
+        const unsigned d0 = tmem + (unsigned)b * (TZC * COUT);
 #pragma unroll 1
         for (int zl = 0; zl < TZC; ++zl) {
           const uint32_t a_lo = (uint32_t)a64 + (uint32_t)(zl * (18 * 160 / 16));
@@ -301,8 +314,8 @@ __global__ void __launch_bounds__(kTcThreads, 1) k_conv_tc(const __nv_bfloat16 *
             for (int kc = 0; kc < 2; ++kc) {
               const uint32_t aoff = (uint32_t)((((tap / 9) * 18 + (tap / 3) % 3) * 160 + (tap % 3) * 16 +
                                                 kc * 2 * T::Plane) >> 4);
-              const uint32_t boff = (uint32_t)((tap * 2 + kc) * (1024 >> 4));
-              tc::mma_bf16(d0 + zl * 32, ((uint64_t)a_hi << 32) | (a_lo + aoff),
+              const uint32_t boff = (uint32_t)((tap * 2 + kc) * (kChunk >> 4));
+              tc::mma_bf16(d0 + zl * COUT, ((uint64_t)a_hi << 32) | (a_lo + aoff),
                            ((uint64_t)b_hi << 32) | (b_lo + boff), idesc, (tap | kc) ? 1u : 0u);
             }
           }
@@ -360,9 +373,16 @@ __global__ void __launch_bounds__(kTcThreads, 1) k_conv_tc(const __nv_bfloat16 *
       int smp, x0, y0, z0;
       origin(t, smp, x0, y0, z0);
       const size_t row = (size_t)smp * N3 + (size_t)(y0 + (r >> 3)) * N + x0 + (r & 7);
-      const unsigned taddr = tmem + ((unsigned)(32 * q) << 16) + (unsigned)b * (TZC * 32);
+      const unsigned taddr = tmem + ((unsigned)(32 * q) << 16) + (unsigned)b * (TZC * COUT);
 #pragma unroll 1
       for (int zl = h; zl < TZC; zl += 2) {
+        if constexpr (EPI == EPI_OUT) {
+          float v[16];
+          tc::tmem_ld_32x16(taddr + zl * COUT, v);
+          const size_t vox = row - (size_t)smp * N3 + (size_t)(z0 + zl) * N * N;
+#pragma unroll
+          for (int co = 0; co < 3; ++co) fout[((size_t)smp * 3 + co) * N3 + vox] = (v[co] + s_bias[co]) * out_scale;
+        } else {
         float v[32];
         tc::tmem_ld_32x32(taddr + zl * 32, v);
         const size_t o = (row + (size_t)(z0 + zl) * N * N) * 32;
@@ -385,6 +405,7 @@ __global__ void __launch_bounds__(kTcThreads, 1) k_conv_tc(const __nv_bfloat16 *
           uint4 *adst = reinterpret_cast<uint4 *>(aout + o);
 #pragma unroll
           for (int k = 0; k < 4; ++k) adst[k] = make_uint4(aw[4 * k], aw[4 * k + 1], aw[4 * k + 2], aw[4 * k + 3]);
+        }
         }
       }
       tc::fence_before_sync();  // the TMEM reads precede the MMAs that overwrite set b
@@ -409,7 +430,7 @@ __global__ void __launch_bounds__(kTcThreads, 1) k_conv_tc(const __nv_bfloat16 *
 __global__ void __launch_bounds__(256) k_conv_in(const float *__restrict__ f, const float *__restrict__ w,
                                                  const float *__restrict__ bias, __nv_bfloat16 *__restrict__ zout,
                                                  __nv_bfloat16 *__restrict__ aout, int N, long long total) {
-  __shared__ float sw[kTaps * kC];
+  __shared__ __align__(16) float sw[kTaps * kC];  // [tap][co]
   __shared__ float sb[kC];
   for (int e = threadIdx.x; e < kTaps * kC; e += 256) sw[e] = w[e];
   if (threadIdx.x < kC) sb[threadIdx.x] = bias[threadIdx.x];
@@ -421,19 +442,43 @@ __global__ void __launch_bounds__(256) k_conv_in(const float *__restrict__ f, co
   const size_t vox = i - sample * N3;
   const int x = vox % N, y = (vox / N) % N, z = vox / ((size_t)N * N);
   float nb[kTaps];
+#pragma unroll
   for (int tap = 0; tap < kTaps; ++tap) {
     const int dz = tap / 9 - 1, dy = (tap / 3) % 3 - 1, dx = tap % 3 - 1;
     nb[tap] = f[sample * N3 + (size_t)wrap(z + dz, N) * N * N + (size_t)wrap(y + dy, N) * N + wrap(x + dx, N)];
   }
-  for (int co = 0; co < kC; co += 2) {
-    float v0 = sb[co], v1 = sb[co + 1];
+  // eight output channels per round: 16-byte weight reads (a broadcast) and
+  // 16-byte stores; each output sums bias + w nb over the taps in tap order
+  const float4 *sw4 = reinterpret_cast<const float4 *>(sw);
+#pragma unroll 1
+  for (int cb = 0; cb < kC / 8; ++cb) {
+    float v[8];
+#pragma unroll
+    for (int k = 0; k < 8; ++k) v[k] = sb[cb * 8 + k];
+#pragma unroll
     for (int tap = 0; tap < kTaps; ++tap) {
-      v0 = fmaf(sw[tap * kC + co], nb[tap], v0);
-      v1 = fmaf(sw[tap * kC + co + 1], nb[tap], v1);
+      const float4 wa = sw4[tap * (kC / 4) + cb * 2], wb = sw4[tap * (kC / 4) + cb * 2 + 1];
+      const float t = nb[tap];
+      v[0] = fmaf(wa.x, t, v[0]);
+      v[1] = fmaf(wa.y, t, v[1]);
+      v[2] = fmaf(wa.z, t, v[2]);
+      v[3] = fmaf(wa.w, t, v[3]);
+      v[4] = fmaf(wb.x, t, v[4]);
+      v[5] = fmaf(wb.y, t, v[5]);
+      v[6] = fmaf(wb.z, t, v[6]);
+      v[7] = fmaf(wb.w, t, v[7]);
     }
-    const size_t o = (size_t)i * kC + co;
-    *reinterpret_cast<__nv_bfloat162 *>(zout + o) = __floats2bfloat162_rn(v0, v1);
-    *reinterpret_cast<__nv_bfloat162 *>(aout + o) = __floats2bfloat162_rn(gelu(v0), gelu(v1));
+    uint32_t zw[4], aw[4];
+#pragma unroll
+    for (int k = 0; k < 4; ++k) {
+      __nv_bfloat162 zb = __floats2bfloat162_rn(v[2 * k], v[2 * k + 1]);
+      __nv_bfloat162 ab = __floats2bfloat162_rn(gelu(v[2 * k]), gelu(v[2 * k + 1]));
+      zw[k] = *reinterpret_cast<uint32_t *>(&zb);
+      aw[k] = *reinterpret_cast<uint32_t *>(&ab);
+    }
+    const size_t o = (size_t)i * kC + cb * 8;
+    *reinterpret_cast<uint4 *>(zout + o) = make_uint4(zw[0], zw[1], zw[2], zw[3]);
+    *reinterpret_cast<uint4 *>(aout + o) = make_uint4(aw[0], aw[1], aw[2], aw[3]);
   }
 }
 
@@ -889,16 +934,17 @@ int conv(const sq_net *net, int B, const __nv_bfloat16 *in, const __nv_bfloat16 
 // outputs and layouts.
 int g_conv_tc = 1;
 
-template <int EPI, int TZC>
+template <int EPI, int TZC, int COUT = 32>
 int conv_tc(const sq_net *net, int B, const __nv_bfloat16 *in, const __nv_bfloat16 *wt, const float *bias,
-            __nv_bfloat16 *z, __nv_bfloat16 *a, int grid, cudaStream_t s) {
+            __nv_bfloat16 *z, __nv_bfloat16 *a, int grid, cudaStream_t s, float *fo = nullptr, int wrows = 32) {
   const int N = net->N;
   const long long ntiles = (long long)B * N * N * N / (128 * TZC);
-  auto kern = k_conv_tc<EPI, TZC>;
-  SQN_CK(cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, TcTile<TZC>::Smem));
+  auto kern = k_conv_tc<EPI, TZC, COUT>;
+  constexpr int smem = TcTile<TZC, COUT>::Smem;
+  SQN_CK(cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, smem));
   const int g = (int)(ntiles < grid ? ntiles : grid);
-  kern<<<g, kTcThreads, TcTile<TZC>::Smem, s>>>(in, wt, bias, z, a, N, (int)ntiles, stage_wait_polls(),
-                                                 net->d_err);
+  kern<<<g, kTcThreads, smem, s>>>(in, wt, bias, z, a, N, (int)ntiles, stage_wait_polls(), net->d_err, fo,
+                                    (float)net->out_scale, wrows);
   SQN_CK(cudaGetLastError());
   return SQ_OK;
 }
@@ -923,6 +969,24 @@ int conv32(const sq_net *net, int B, const __nv_bfloat16 *in, const __nv_bfloat1
   }
   return tz == 2 ? conv_tc<EPI, 2>(net, B, in, wt, bias, z, a, sms, s)
                  : conv_tc<EPI, 4>(net, B, in, wt, bias, z, a, sms, s);
+}
+
+// The output layer (32 -> 3 channels, FP32 fields times out_scale): on
+// tcgen05 with 16 accumulator columns per plane (channels 3..15 zero) where
+// the convolutions run there, else on mma.sync. Its packed weights have 8
+// rows per tap.
+int conv_out(const sq_net *net, int B, const __nv_bfloat16 *in, const __nv_bfloat16 *wt, const float *bias,
+             float *fo, cudaStream_t s) {
+  if (!g_conv_tc) return conv<32, 32, 8, EPI_OUT>(net, B, in, wt, bias, nullptr, nullptr, fo, s);
+  int dev = 0, sms = 0;
+  SQN_CK(cudaGetDevice(&dev));
+  SQN_CK(cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev));
+  const long long vox = (long long)B * net->N * net->N * net->N;
+  const long long t4 = vox / 512, t2 = vox / 256;
+  const double w4 = 4.0 * (double)((t4 + sms - 1) / sms), w2 = 2.2 * (double)((t2 + sms - 1) / sms);
+  const int tz = (g_conv_tc == 2 || g_conv_tc == 4) ? g_conv_tc : ((w2 < w4) ? 2 : 4);
+  return tz == 2 ? conv_tc<EPI_OUT, 2, 16>(net, B, in, wt, bias, nullptr, nullptr, sms, s, fo, 8)
+                 : conv_tc<EPI_OUT, 4, 16>(net, B, in, wt, bias, nullptr, nullptr, sms, s, fo, 8);
 }
 
 // Reads back (and clears) the tcgen05 convolutions' failure flag: SQ_ETIMEOUT
@@ -958,8 +1022,7 @@ int forward(sq_net *net, int B, cudaStream_t s) {
                           s);
     if (st != SQ_OK) return st;
   }
-  return conv<32, 32, 8, EPI_OUT>(net, B, net->d_a[4], net->d_wf[5], net->d_w + net->boff[5], nullptr, nullptr,
-                                  net->d_y, s);
+  return conv_out(net, B, net->d_a[4], net->d_wf[5], net->d_w + net->boff[5], net->d_y, s);
 }
 
 template <int CA, int CG>
