@@ -276,6 +276,8 @@ def run_native(args):
 
     from paper_2007_06524_gb300 import autotune
 
+    if args.no_graphs:  # the same kernels, launched one by one (for profilers that cannot replay graph nodes)
+        sq.sq_set_option(sq.SQ_OPT_PCG_GRAPHS, 0)
     if args.tiles:
         tiles = tuple(int(v) for v in args.tiles.split(","))
         if len(tiles) == 3:
@@ -1016,6 +1018,9 @@ def main():
                     help="comma-separated subset of the variant legs to run (default: all), e.g. batch_768_mixed")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-e2e", action="store_true")
+    ap.add_argument("--no-graphs", action="store_true",
+                    help="launch the PCG iterations' kernels one by one instead of replaying iteration graphs "
+                         "(same kernels; for profiling tools)")
     ap.add_argument("--tiles", default=None,
                     help="fixed FP32 tile shape 'P,planes,rows[,Pe]' (Hartley pencils, operator planes per item, "
                          "operator rows per thread, pencils of the last pass of an iteration) instead of the autotuner")
