@@ -165,6 +165,61 @@ __device__ __forceinline__ void dft(C (&u)[R]) {
   }
 }
 
+// Twiddled butterflies with the complex products fused into the first layer
+// of sums (FP64 stages): a + w b costs four FMAs (a complex product and a sum
+// would cost six), and its partner a - w b = 2a - (a + w b) two more.
+template <typename C>
+__device__ __forceinline__ C cfma(C w, C b, C a) {
+  return C{fma(w.x, b.x, fma(-w.y, b.y, a.x)), fma(w.x, b.y, fma(w.y, b.x, a.y))};
+}
+template <typename T, typename C>
+__device__ __forceinline__ C ctwice_minus(C a, C s) {
+  return C{fma((T)2, a.x, -s.x), fma((T)2, a.y, -s.y)};
+}
+// The 4-point DFT of (u0, w1 u1, w2 u2, w3 u3), in place (dft4's order).
+template <typename T, typename C>
+__device__ __forceinline__ void dft4_tw(C &u0, C &u1, C &u2, C &u3, C w1, C w2, C w3) {
+  const C t0 = cfma(w2, u2, u0);                        // u0 + w2 u2
+  const C t1 = ctwice_minus<T>(u0, t0);                 // u0 - w2 u2
+  const C c = cmul(u1, w1);
+  const C t2 = cfma(w3, u3, c);                         // w1 u1 + w3 u3
+  const C t3 = mul_mi(ctwice_minus<T>(c, t2));          // -i (w1 u1 - w3 u3)
+  u0 = cadd(t0, t2);
+  u2 = csub(t0, t2);
+  u1 = cadd(t1, t3);
+  u3 = csub(t1, t3);
+}
+// dft<R> of (u0, w[1] u1, .., w[R-1] u_{R-1}) for R = 2, 4, 8 (dft's output order).
+template <typename T, typename C, int R>
+__device__ __forceinline__ void dft_tw(C (&u)[R], const C (&w)[R]) {
+  if constexpr (R == 2) {
+    const C s = cfma(w[1], u[1], u[0]);
+    u[1] = ctwice_minus<T>(u[0], s);
+    u[0] = s;
+  } else if constexpr (R == 4) {
+    dft4_tw<T, C>(u[0], u[1], u[2], u[3], w[1], w[2], w[3]);
+  } else {
+    static_assert(R == 8, "twiddled butterflies of radix 2, 4, 8");
+    // dft<8>'s split: the 4-point DFTs of the even and of the odd inputs
+    const T h = (T)0.70710678118654752440;  // sqrt(2)/2
+    C e0 = u[0], e1 = u[2], e2 = u[4], e3 = u[6];
+    dft4_tw<T, C>(e0, e1, e2, e3, w[2], w[4], w[6]);
+    C o0 = cmul(u[1], w[1]), o1 = u[3], o2 = u[5], o3 = u[7];
+    dft4_tw<T, C>(o0, o1, o2, o3, w[3], w[5], w[7]);
+    const C v1 = C{h * (o1.x + o1.y), h * (o1.y - o1.x)};
+    const C v2 = mul_mi(o2);
+    const C v3 = C{h * (o3.y - o3.x), -h * (o3.x + o3.y)};
+    u[0] = cadd(e0, o0);
+    u[4] = csub(e0, o0);
+    u[1] = cadd(e1, v1);
+    u[5] = csub(e1, v1);
+    u[2] = cadd(e2, v2);
+    u[6] = csub(e2, v2);
+    u[3] = cadd(e3, v3);
+    u[7] = csub(e3, v3);
+  }
+}
+
 // One radix-R Stockham stage over P pencils stored [j][p] with row stride SP.
 // ps = product of the radices of the previous stages.
 template <typename T, typename C, int R>
@@ -181,12 +236,25 @@ __device__ __forceinline__ void fft_stage(const C *__restrict__ in, C *__restric
     C u[R];
 #pragma unroll
     for (int q = 0; q < R; ++q) u[q] = in[(b + q * NR) * SP + p];
-    if (ps > 1) {
-      const int step = k * tstride;
+    if constexpr (sizeof(T) == 8 && R != 3) {
+      if (ps > 1) {
+        const int step = k * tstride;
+        C w[R];
+        w[0] = C{(T)1, (T)0};
 #pragma unroll
-      for (int q = 1; q < R; ++q) u[q] = cmul(u[q], tw[q * step]);
+        for (int q = 1; q < R; ++q) w[q] = tw[q * step];
+        dft_tw<T, C, R>(u, w);
+      } else {
+        dft<T, C, R>(u);
+      }
+    } else {
+      if (ps > 1) {
+        const int step = k * tstride;
+#pragma unroll
+        for (int q = 1; q < R; ++q) u[q] = cmul(u[q], tw[q * step]);
+      }
+      dft<T, C, R>(u);
     }
-    dft<T, C, R>(u);
     const int j = (b - k) * R + k;
 #pragma unroll
     for (int q = 0; q < R; ++q) out[(j + q * ps) * SP + p] = u[q];
