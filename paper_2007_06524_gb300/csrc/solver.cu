@@ -561,9 +561,9 @@ int pcg_loop(sq_workspace *w, const sq_coeffs *c, const sq_precond *pc, T *x, T 
   if (g_pcg_graphs && !g_prof.on && budget >= chunk) {
     cudaStreamCaptureStatus cap = cudaStreamCaptureStatusNone;
     SQ_CK(cudaStreamIsCapturing(s, &cap));
-    if (cap == cudaStreamCaptureStatusNone) {
-      const int st = iter_graph<T>(w, c, pc, x, r, p, q, Y, rb, &gx, &gk);
-      if (st != SQ_OK) return st;
+    if (cap == cudaStreamCaptureStatusNone && iter_graph<T>(w, c, pc, x, r, p, q, Y, rb, &gx, &gk) != SQ_OK) {
+      gx = nullptr;  // no graph (capture or instantiation failed): launch one by one
+      (void)cudaGetLastError();
     }
   }
   while (launched < budget) {

@@ -371,9 +371,9 @@ int loop2d(sq2d_workspace *w, const Cells2D &cd, const sq2d_precond *pc, double 
   if (pcg_graphs_enabled() && budget >= chunk) {
     cudaStreamCaptureStatus cap = cudaStreamCaptureStatusNone;
     SQ2_CK(cudaStreamIsCapturing(s, &cap));
-    if (cap == cudaStreamCaptureStatusNone) {
-      const int st = graph2d(w, cd, pc, x, r, p, q, Y, rb, &gx);
-      if (st != SQ_OK) return st;
+    if (cap == cudaStreamCaptureStatusNone && graph2d(w, cd, pc, x, r, p, q, Y, rb, &gx) != SQ_OK) {
+      gx = nullptr;  // no graph (capture or instantiation failed): launch one by one
+      (void)cudaGetLastError();
     }
   }
   while (launched < budget) {
