@@ -430,6 +430,8 @@ def run_native(args):
                 kv, rv = kernel_table(sq.sq_profile_work(), pv, N, 4, rr, evp0.elapsed_time(evp1), peaks)
                 variants[label]["kernels"] = kv
                 variants[label]["iteration_hbm"] = fused_iteration_hbm(kv, N, 4, peaks["hbm_gbs"])
+                variants[label]["iteration_slope"] = iteration_by_slope(sq, torch, c, pcv, wv, N, stream,
+                                                                        peaks["hbm_gbs"])
                 out["roofline_fp32_refine"] = rv
             del pcv
         out["variants"] = variants
@@ -438,7 +440,7 @@ def run_native(args):
         legs = (("refine_error_n128", lambda: run_refine_error_n128(sq, torch)),
                 ("batch_768_mixed", lambda: run_batch(sq, torch, stream, peaks=peaks)),
                 ("warm_start_n64", lambda: run_warm_start(sq, torch)),
-                ("refine_n512", lambda: run_refine_n512(sq, torch, stream)),
+                ("refine_n512", lambda: run_refine_n512(sq, torch, stream, peaks["hbm_gbs"])),
                 ("ensemble", lambda: run_ensemble(sq, torch)),
                 ("inclusions_alpha_quarter", lambda: run_inclusions(sq, torch, stream)),
                 ("two_contrasts_alpha_quarter", lambda: run_two_contrasts(sq, torch, stream)),
@@ -481,6 +483,7 @@ def summarize(out):
     if "fp32_refine_rank8" in v:
         sm["fp32_refine_rank8_solves_per_s"] = v["fp32_refine_rank8"]["solves_per_s"]
         sm["fp32_iteration_hbm"] = v["fp32_refine_rank8"].get("iteration_hbm")
+        sm["fp32_iteration_slope"] = v["fp32_refine_rank8"].get("iteration_slope")
         sm["fp32_solve_hbm_frac"] = v["fp32_refine_rank8"]["solve_hbm"]["frac"]
     if "fp32_refine_exact" in v:
         sm["fp32_refine_exact_solves_per_s"] = v["fp32_refine_exact"]["solves_per_s"]
@@ -858,7 +861,7 @@ def run_2d_table(sq, torch, stream):
     return res
 
 
-def run_refine_n512(sq, torch, stream):
+def run_refine_n512(sq, torch, stream, hbm_gbs):
     """L=64, n=8 (N=512, 134 M unknowns), Bernoulli(1/2) on {1,100}, three
     correctors: FP32 PCG inside FP64 refinement to rel. residual 1e-10, exact
     and rank-8 preconditioners (one realization, seed 0)."""
@@ -885,9 +888,45 @@ def run_refine_n512(sq, torch, stream):
         res[f"rank{rank}"] = {"solves_per_s": round(3 / t, 3), "iters_mean": round(statistics.mean(i["iters"] for i in infos), 1),
                               "outer_steps": [i["outer_steps"] for i in infos],
                               "relres_true_max": max(i["relres_true"] for i in infos),
-                              "converged": all(i["status"] == sq.SQ_OK for i in infos)}
+                              "converged": all(i["status"] == sq.SQ_OK for i in infos),
+                              "iteration_slope": iteration_by_slope(sq, torch, c, pc, w, N, stream,
+                                                                    hbm_gbs, reps=3)}
         del pc
     return res
+
+
+def iteration_by_slope(sq, torch, c, pc, w, N, stream, hbm_gbs, Ks=(4, 8, 12, 16, 20), reps=5):
+    """The FP32 PCG iteration as solves run it (graph-replayed, the gaps
+    between kernels included), event-timed: FP32-refinement solves capped at
+    K inner iterations (tol 1e-30, so the cap ends the first inner solve, all
+    K iterations in one inner PCG), timed for several K; the slope of the
+    median times is one iteration. The per-kernel event pairs of the
+    profiled run time each launch with its own start and drain, so their sum
+    reads a few us per kernel above this."""
+    import numpy as np
+
+    psi = torch.empty(N ** 3, dtype=torch.float64, device="cuda")
+    ts = []
+    for K in Ks:
+        sq.sq_pcg_solve(c, pc, w, 0, 1e-30, K, sq.SQ_FP32_REFINE, None, psi)  # warm (graph capture)
+        rt = []
+        for _ in range(reps):
+            torch.cuda.synchronize()
+            e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            e0.record(stream)
+            inf = sq.sq_pcg_solve(c, pc, w, 0, 1e-30, K, sq.SQ_FP32_REFINE, None, psi)
+            e1.record(stream)
+            torch.cuda.synchronize()
+            if inf["iters"] != K:
+                return None  # the inner solve converged before the cap: no clean slope
+            rt.append(e0.elapsed_time(e1))
+        ts.append(statistics.median(rt))
+    slope, icpt = np.polyfit(list(Ks), ts, 1)
+    resid = max(abs(t - (slope * k + icpt)) for k, t in zip(Ks, ts))
+    b = 17 * 4 * N ** 3
+    gbps = b / (slope * 1e-3) / 1e9
+    return {"us": round(slope * 1e3, 1), "fit_residual_us": round(resid * 1e3, 1), "bytes": b,
+            "GBps": round(gbps, 1), "frac": round(gbps / hbm_gbs, 4), "Ks": list(Ks)}
 
 
 def _oracle_precond(N, R, workers):
