@@ -378,8 +378,9 @@ struct SpectralDev {
   // (u(k) = u(N - k)): G is then diagonal in the separable Hartley basis.
   const void *u;
   double scale;      // 1 / (64 N^3) for the exact diagonal
-  // The multiplier itself, tabulated (T), scale folded in as above, G(0,0,0) =
-  // 0, with m = min(k, N - k) (G is even in each index) and H = N/2 + 1:
+  // The multiplier itself, tabulated (T) as 2 G (the factor pass C applies
+  // per mode), scale folded in as above, G(0,0,0) = 0, with m = min(k, N - k)
+  // (G is even in each index) and H = N/2 + 1:
   // FP64 at gtab[(m1 H + m2) H + m3]; FP32 at gtab[(m1 H + m2) N + k3] (the
   // x3 index unreduced, so that a tile's 2P columns are one aligned run).
   // nullptr: pass C evaluates G from lam or u on the fly.

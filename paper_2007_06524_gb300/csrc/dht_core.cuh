@@ -299,6 +299,17 @@ struct DhtTile {
   int logP;
 };
 
+// Hartley value pairs of outputs m and N - m from X = X_m and Y = X_{N-m}:
+// hk = (X.x - X.y + Y.x + Y.y, X.x + X.y - Y.x + Y.y) and hm the same with X and
+// Y swapped, from four shared sums (8 adds instead of 12). X = Y (a
+// self-paired output) gives hk = hm = 2 X.
+template <typename C>
+__device__ __forceinline__ void hartley_both(const C X, const C Y, C &hk, C &hm) {
+  const auto u = X.x + Y.x, v = X.y - Y.y, w = X.x - Y.x, z = X.y + Y.y;
+  hk = C{u - v, w + z};
+  hm = C{u + v, z - w};
+}
+
 // Shared-memory layout: two ping-pong buffers of N (P+1) complex values, N
 // twiddles, then rank x 2P column factors (pass C with a rank-R tensor).
 template <typename T>
@@ -326,7 +337,7 @@ __device__ __forceinline__ void dht_tile(const SpectralDev &sp, const DhtTile<T>
   const T *lam = reinterpret_cast<const T *>(sp.lam);
   const T *uf = reinterpret_cast<const T *>(sp.u);
   const int R = sp.rank;
-  const T gscale = (T)sp.scale;
+  const T gscale = (T)2 * (T)sp.scale;  // pass C works with 2 G, as the tables hold it
 
   __syncthreads();
   // ------------------------------------------------------------------ load
@@ -374,7 +385,7 @@ __device__ __forceinline__ void dht_tile(const SpectralDev &sp, const DhtTile<T>
       const T *u2 = uf + (size_t)R * N, *u3 = uf + 2 * (size_t)R * N;
       for (int e = tid; e < R * 2 * P; e += kThreads) {
         const int rr = e / (2 * P), w = e - rr * 2 * P;
-        vtab[e] = u2[rr * N + k2] * u3[rr * N + c0 + w];
+        vtab[e] = (T)2 * (u2[rr * N + k2] * u3[rr * N + c0 + w]);  // 2 G, as above
       }
     }
   }
@@ -418,16 +429,23 @@ __device__ __forceinline__ void dht_tile(const SpectralDev &sp, const DhtTile<T>
           ga = (k == 0 && k2 == 0 && k3a == 0) ? (T)0 : sa;
           gb = sb;  // k3b >= 1
         }
-        const T sx = X.x + Y.x, dy = X.y - Y.y, dx = X.x - Y.x, sy = X.y + Y.y;
-        T e2 = fma(ga, fma(sx, sx, dy * dy), gb * fma(dx, dx, sy * sy));
-        if (km != k) e2 += e2;
+        // ga, gb are 2 G. The pair's share of r.z is G_a |X + conj Y|^2 + G_b |X - conj Y|^2,
+        // doubled for k != N - k (both modes); with S = |X|^2 + |Y|^2 and Re(X Y) it is
+        // ((ga + gb) S + 2 (ga - gb) Re(X Y)) / 2, which needs two products of the data
+        // instead of four (the sums X + conj Y, X - conj Y are not formed).
+        const T s4 = ga + gb, d4 = ga - gb;
+        const T S = fma(X.x, X.x, fma(X.y, X.y, fma(Y.x, Y.x, Y.y * Y.y)));
+        const T ReXY = fma(X.x, Y.x, -(X.y * Y.y));
+        T e2 = fma(s4, S, (d4 + d4) * ReXY);
+        if (km == k) e2 *= (T)0.5;
         acc.add(e2);
-        const T s4 = (T)2 * (ga + gb), d4 = (T)2 * (ga - gb);
         res[k * SP + p] = C{fma(s4, X.x, d4 * Y.x), fma(d4, Y.y, -s4 * X.y)};
         if (km != k) res[km * SP + p] = C{fma(s4, Y.x, d4 * X.x), fma(d4, X.y, -s4 * Y.y)};
       } else {
-        res[k * SP + p] = C{X.x - X.y + Y.x + Y.y, X.x + X.y - Y.x + Y.y};
-        if (km != k) res[km * SP + p] = C{Y.x - Y.y + X.x + X.y, Y.x + Y.y - X.x + X.y};
+        C hk, hm;
+        hartley_both(X, Y, hk, hm);
+        res[k * SP + p] = hk;
+        if (km != k) res[km * SP + p] = hm;
       }
     }
     __syncthreads();
@@ -523,11 +541,6 @@ __device__ __forceinline__ void s2_stage1(const C *__restrict__ gsrc, size_t bas
   __syncthreads();
 }
 
-// Hartley value pair of output m from X_m and its mirror X_{N-m}.
-template <typename C>
-__device__ __forceinline__ C hartley_pair(const C X, const C Y) {
-  return C{X.x - X.y + Y.x + Y.y, X.x + X.y - Y.x + Y.y};
-}
 
 // (R0 P may exceed the block: a thread then takes several butterflies, each
 // reading and writing only its own positions.)
@@ -553,11 +566,12 @@ __device__ __forceinline__ void s2_stage2(C *sm, const C *__restrict__ tw) {
 // (RR = 0), rank RR with the column factors va/vb of this thread's pencil in
 // registers (RR > 0), a runtime rank (RR = -1, factors read from vtab), or
 // read from the tile's slice of the FP32 multiplier table that dht_tile_s2
-// prefetched into vtab (RR = -2: row k <= N/2, the tile's 2P columns).
+// prefetched into vtab (RR = -2: row k <= N/2, the tile's 2P columns). Every
+// form yields 2 G, as the tables hold it (the factor is exact).
 template <typename T, int N, int P, int RR>
 __device__ __forceinline__ void s2_multiplier(const SpectralDev &sp, int k, int k2, int c0, int p, const T *vtab,
                                               const T (&va)[RR > 0 ? RR : 1], const T (&vb)[RR > 0 ? RR : 1],
-                                              T &ga, T &gb) {
+                                              T gscale, T &ga, T &gb) {
   const T *lam = reinterpret_cast<const T *>(sp.lam);
   const T *uf = reinterpret_cast<const T *>(sp.u);
   const int k3a = c0 + 2 * p;
@@ -565,8 +579,7 @@ __device__ __forceinline__ void s2_multiplier(const SpectralDev &sp, int k, int 
     const T *tt = vtab + (size_t)k * 2 * P + 2 * p;
     ga = (k == 0 && k2 == 0 && k3a == 0) ? (T)0 : tt[0];
     gb = tt[1];
-  } else if constexpr (RR == 0) {
-    const T gscale = (T)sp.scale;
+  } else if constexpr (RR == 0) {  // gscale: 2 / (64 N^3), in T
     const T l12 = lam[k] + lam[k2];
     const T g1 = l12 + lam[k3a], g2 = l12 + lam[k3a + 1];
     ga = (g1 > (T)0) ? gscale / g1 : (T)0;
@@ -601,8 +614,9 @@ __device__ __forceinline__ void s2_multiplier(const SpectralDev &sp, int k, int 
 // and F*(W) = conj(F(conj W)) has the results for a and b as its real and
 // imaginary parts: the inverse is the forward transform of conj(W), stored
 // conjugated, with no Hartley combine on either side. The factor 4 of the
-// two Hartley combines this replaces is folded into s and d, so G's scale is
-// unchanged. r.z (Parseval): g_a |A_k|^2 + g_b |B_k|^2 per k.
+// two Hartley combines this replaces is folded into s and d: the multiplier
+// arrives as 2 G, so 4 s = 2G_a + 2G_b and 4 d = 2G_a - 2G_b with no further
+// product. r.z (Parseval): g_a |A_k|^2 + g_b |B_k|^2 per k.
 // s2_combine MODE 0: Hartley combine, store to global (rows of P complex
 // values, coalesced); 1: pass C's scaling above, reduce r.z into acc, write
 // conj(W) back in place for the second transform; 2: store the conjugate.
@@ -620,25 +634,28 @@ __device__ __forceinline__ void s2_combine(C *sm, C *__restrict__ gdst, size_t b
     }
   }
   C *g = gdst + (base >> 1) + p;
+  const T gscale = (T)2 * (T)sp.scale;  // converted once, outside the loop (the FP64 pipe is narrow)
   for (int t = threadIdx.x; t < ((N / 2 + 1) << LP); t += kThreads) {
     const int k = t >> LP;
     const int km = (k == 0) ? 0 : N - k;
     const C X = sm[k * SP + p], Y = sm[km * SP + p];
     if (MODE == 1) {
       T ga, gb;
-      s2_multiplier<T, N, P, RR>(sp, k, k2, c0, p, vtab, va, vb, ga, gb);  // G(N - k) = G(k)
+      s2_multiplier<T, N, P, RR>(sp, k, k2, c0, p, vtab, va, vb, gscale, ga, gb);  // G(N - k) = G(k)
+      // ga, gb are 2 G: e2 below is already doubled, the share of both modes k, N - k
       const T sx = X.x + Y.x, dy = X.y - Y.y, dx = X.x - Y.x, sy = X.y + Y.y;
       T e2 = fma(ga, fma(sx, sx, dy * dy), gb * fma(dx, dx, sy * sy));
-      if (km != k) e2 += e2;  // the partner k' = N - k contributes the same
+      if (km == k) e2 *= (T)0.5;
       acc.add(e2);
-      const T s4 = (T)2 * (ga + gb), d4 = (T)2 * (ga - gb);
+      const T s4 = ga + gb, d4 = ga - gb;
       sm[k * SP + p] = C{fma(s4, X.x, d4 * Y.x), fma(d4, Y.y, -s4 * X.y)};
       if (km != k) sm[km * SP + p] = C{fma(s4, Y.x, d4 * X.x), fma(d4, X.y, -s4 * Y.y)};
     } else if (MODE == 2) {
       g[(size_t)k * (STRIDE >> 1)] = C{X.x, -X.y};
       if (km != k) g[(size_t)km * (STRIDE >> 1)] = C{Y.x, -Y.y};
     } else {
-      const C hk = hartley_pair(X, Y), hm = hartley_pair(Y, X);
+      C hk, hm;
+      hartley_both(X, Y, hk, hm);
       g[(size_t)k * (STRIDE >> 1)] = hk;
       if (km != k) g[(size_t)km * (STRIDE >> 1)] = hm;
     }
@@ -681,7 +698,7 @@ __device__ __forceinline__ void dht_tile_s2(const SpectralDev &sp, const DhtTile
     const T *u2 = uf + (size_t)sp.rank * N, *u3 = uf + 2 * (size_t)sp.rank * N;  // x2, x3 factors
     for (int e = threadIdx.x; e < sp.rank * 2 * P; e += kThreads) {
       const int rr = e / (2 * P), w = e - rr * 2 * P;
-      vtab[e] = u2[rr * N + k2] * u3[rr * N + c0 + w];
+      vtab[e] = (T)2 * (u2[rr * N + k2] * u3[rr * N + c0 + w]);  // 2 G, as the tables hold it
     }
   }
   const C *gin = reinterpret_cast<const C *>(a.in);
@@ -878,8 +895,10 @@ __device__ __forceinline__ void x3_combine(const DhtTile<T> &a, size_t row0, con
     const size_t ga = (row0 + 2 * p) * N, gb = ga + N;
     const int km = (k == 0) ? H : N - k;  // k = 0: the second self-paired output is N/2
     const C X = sp[x3pos(k)], Y = sp[x3pos(km)];
-    // k = 0: outputs 0 and N/2 are their own mirrors
-    const C hk = hartley_pair(X, k == 0 ? X : Y), hm = hartley_pair(Y, k == 0 ? Y : X);
+    // k = 0: outputs 0 and N/2 are their own mirrors (2 X and 2 Y)
+    C hk, hm;
+    hartley_both(X, k == 0 ? X : Y, hk, hm);
+    if (k == 0) hm = C{Y.x + Y.x, Y.y + Y.y};
     const size_t g[4] = {ga + k, gb + k, ga + km, gb + km};
     const T v[4] = {hk.x, hk.y, hm.x, hm.y};
     x3_put4<T, STOREM>(a, g, v, pl, xl, row0 * N);

@@ -1051,8 +1051,9 @@ namespace sq {
 // The multiplier tables of pass C (SpectralDev::gtab): G at every
 // mirror-reduced mode (m1, m2, m3), m <= N/2, summed in FP64 from the scaled
 // factors (or scale / (l1 + l2 + l3) for the exact diagonal); G(0,0,0) = 0.
-// FP64 table indexed by (m1, m2, m3); FP32 copy by (m1, m2, k3) with k3 over
-// the whole axis (each FP32 tile prefetches its 2P columns into shared memory).
+// Both hold 2 G, the factor pass C would otherwise apply per mode (doubling is
+// exact): FP64 indexed by (m1, m2, m3); FP32 by (m1, m2, k3) with k3 over the
+// whole axis (each FP32 tile prefetches its 2P columns into shared memory).
 __global__ void k_build_gtab(int N, int R, const double *lam, const double *u, double scale, double *g64,
                              float *g32) {
   const int H = N / 2 + 1;
@@ -1068,10 +1069,10 @@ __global__ void k_build_gtab(int N, int R, const double *lam, const double *u, d
           g = fma(u[(size_t)r * N + m1], u[(size_t)(R + r) * N + m2] * u[(size_t)(2 * R + r) * N + m3], g);
       }
     }
-    g64[i] = g;
+    g64[i] = 2.0 * g;
     const size_t row = ((size_t)m1 * H + m2) * N;
-    g32[row + m3] = (float)g;
-    if (m3 != 0 && m3 != N - m3) g32[row + N - m3] = (float)g;
+    g32[row + m3] = (float)(2.0 * g);
+    if (m3 != 0 && m3 != N - m3) g32[row + N - m3] = (float)(2.0 * g);
   }
 }
 
