@@ -207,7 +207,7 @@ def _algorithmic(N, elem, rank_r, table=None):
 # profiles/dht_x3_pass_e_fp32_n256.md (8-pencil tiles). Part of each kernel's
 # writes is still in L2 when it ends, so traffic can read below the
 # algorithmic bytes.
-PROFILED_TRAFFIC = {("dht_x1_scale", 8): 159.91e6 + 75.41e6, ("dht_x3_out", 4): 201.35e6 + 76.39e6}
+PROFILED_TRAFFIC = {("dht_x1_scale", 8): 159.80e6 + 75.00e6, ("dht_x3_out", 4): 201.35e6 + 76.52e6}
 
 
 def kernel_table(work, prof, N, elem, R, t_ms, peaks=None):
