@@ -378,8 +378,8 @@ struct SpectralDev {
   // (u(k) = u(N - k)): G is then diagonal in the separable Hartley basis.
   const void *u;
   double scale;      // 1 / (64 N^3) for the exact diagonal
-  // The multiplier itself, tabulated (T) as 2 G (the factor pass C applies
-  // per mode), scale folded in as above, G(0,0,0) = 0, with m = min(k, N - k)
+  // The multiplier itself, tabulated (T) times the factor pass C applies per
+  // mode (FP64 8 G, FP32 2 G; see dht_tile), scale folded in as above, G(0,0,0) = 0, with m = min(k, N - k)
   // (G is even in each index) and H = N/2 + 1:
   // FP64 at gtab[(m1 H + m2) H + m3]; FP32 at gtab[(m1 H + m2) N + k3] (the
   // x3 index unreduced, so that a tile's 2P columns are one aligned run).
@@ -390,7 +390,7 @@ struct SpectralDev {
 // at N = 256, resident in L2 while pass C reads them).
 constexpr int kGtabMaxN = 256;
 __host__ __device__ constexpr int mirror_index(int k, int N) { return k <= N - k ? k : N - k; }
-enum DhtPass : int { PASS_A_RESID = 0, PASS_A_PLAIN = 1, PASS_B = 2, PASS_C = 3, PASS_E_PCG = 4, PASS_E_PLAIN = 5 };
+enum DhtPass : int { PASS_A_RESID = 0, PASS_A_PLAIN = 1, PASS_B = 2, PASS_C = 3, PASS_E_PCG = 4, PASS_E_PLAIN = 5, PASS_D = 6 };
 // One pencil pass of the 3D Hartley transform pipeline (see dht.cu).
 template <typename T>
 cudaError_t launch_dht_pass(int pass, const SpectralDev &sp, const T *in, T *out, T *r, const T *q, T *p, T *x,

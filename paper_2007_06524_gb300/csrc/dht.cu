@@ -49,7 +49,7 @@ struct DhtArgs {
   int wait_polls;  // polls of a staging wait before it gives up (set by the launcher)
 };
 
-template <typename T, int AXIS, int LOADM, int STOREM, bool SCALE>
+template <typename T, int AXIS, int LOADM, int STOREM, bool SCALE, int XF = XF_HARTLEY>
 __global__ void __launch_bounds__(kThreads) k_dht(DhtArgs<T> a) {
   using C = typename Cx<T>::type;
   if (a.check_done && *(volatile int *)&a.rb.st->done) return;
@@ -75,7 +75,7 @@ __global__ void __launch_bounds__(kThreads) k_dht(DhtArgs<T> a) {
   t.logP = a.logP;
   Accum<T> acc;
   for (int tile = blockIdx.x; tile < a.ntiles; tile += gridDim.x)
-    dht_tile<T, AXIS, LOADM, STOREM, SCALE>(a.sp, t, tile, buf0, buf1, tw, vtab, acc);
+    dht_tile<T, AXIS, LOADM, STOREM, SCALE, XF>(a.sp, t, tile, buf0, buf1, tw, vtab, acc);
   if (LOADM == LD_RESID || SCALE) {
     typename Accum<T>::Part v[1] = {acc.part()};
     double s[1];
@@ -332,7 +332,8 @@ static cudaError_t launch_fast(int pass, const DhtArgs<T> &a, int grid, cudaStre
       case PASS_A_PLAIN: return launch_contig_fast<LD_PLAIN, SO_PLAIN>(a, grid, s);
       case PASS_E_PCG: return launch_contig_fast<LD_PLAIN, SO_PCG>(a, grid, s);
       case PASS_E_PLAIN: return launch_contig_fast<LD_PLAIN, SO_PLAIN>(a, grid, s);
-      case PASS_B: return launch_strided_fast<2, false>(a, grid, s);
+      case PASS_B:
+      case PASS_D: return launch_strided_fast<2, false>(a, grid, s);
       case PASS_C: return launch_strided_fast<1, true>(a, grid, s);
       default: return cudaErrorNotSupported;
     }
@@ -382,9 +383,9 @@ int dht_tile_pencils(int N, int elem_bytes) {
   return P;
 }
 
-template <typename T, int AXIS, int LOADM, int STOREM, bool SCALE>
+template <typename T, int AXIS, int LOADM, int STOREM, bool SCALE, int XF = XF_HARTLEY>
 static cudaError_t launch_one(const DhtArgs<T> &a, int grid, size_t smem, cudaStream_t s) {
-  auto kern = k_dht<T, AXIS, LOADM, STOREM, SCALE>;
+  auto kern = k_dht<T, AXIS, LOADM, STOREM, SCALE, XF>;
   cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
   if (e != cudaSuccess) return e;
   kern<<<grid, kThreads, smem, s>>>(a);
@@ -427,10 +428,24 @@ cudaError_t launch_dht_pass(int pass, const SpectralDev &sp, const T *in, T *out
     const cudaError_t e = launch_fast<T>(pass, a, grid, s);
     if (e != cudaErrorNotSupported) return e;
   }
+  // FP64: passes B, C, D take the complex x2 route (no Hartley combine in B
+  // and D; pass C pairs the mirror rows). Every valid N gives pass C at least
+  // 2 pencils, which its two halves need.
+  if constexpr (sizeof(T) == 8) {
+    if (dht_tile_pencils(N, 8) >= 2) {
+      switch (pass) {
+        case PASS_B: return launch_one<T, 2, LD_PLAIN, SO_PLAIN, false, XF_FWD>(a, grid, smem, s);
+        case PASS_C: return launch_one<T, 1, LD_PLAIN, SO_PLAIN, true, XF_MIRROR>(a, grid, smem, s);
+        case PASS_D: return launch_one<T, 2, LD_PLAIN, SO_PLAIN, false, XF_INV>(a, grid, smem, s);
+        default: break;
+      }
+    }
+  }
   switch (pass) {
     case PASS_A_RESID: return launch_one<T, 3, LD_RESID, SO_PLAIN, false>(a, grid, smem, s);
     case PASS_A_PLAIN: return launch_one<T, 3, LD_PLAIN, SO_PLAIN, false>(a, grid, smem, s);
-    case PASS_B: return launch_one<T, 2, LD_PLAIN, SO_PLAIN, false>(a, grid, smem, s);
+    case PASS_B:
+    case PASS_D: return launch_one<T, 2, LD_PLAIN, SO_PLAIN, false>(a, grid, smem, s);
     case PASS_C: return launch_one<T, 1, LD_PLAIN, SO_PLAIN, true>(a, grid, smem, s);
     case PASS_E_PCG: return launch_one<T, 3, LD_PLAIN, SO_PCG, false>(a, grid, smem, s);
     case PASS_E_PLAIN: return launch_one<T, 3, LD_PLAIN, SO_PLAIN, false>(a, grid, smem, s);

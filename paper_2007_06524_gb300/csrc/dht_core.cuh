@@ -318,13 +318,29 @@ __host__ __device__ inline size_t dht_smem_bytes_t(int N, int P, int rank) {
   return 2 * (size_t)N * (P + 1) * c + (size_t)N * c + (size_t)rank * 2 * P * sizeof(T);
 }
 
+// Routes of the x2 / x1 tiles (see dht.cu):
+//   XF_HARTLEY: Hartley transforms throughout (x2: FFT + Hartley combine);
+//   XF_FWD / XF_INV (x2, the complex route): the FFT of the packed pair, no
+//     combine; XF_INV stores output j from FFT index N - j, i.e. the inverse
+//     transform F* V = F V (-j), up to N;
+//   XF_MIRROR (x1 with SCALE): pass C of the complex route. Its input is the
+//     x2 spectrum Z(., k2) of packed pairs (a + i b), so the mirror of mode
+//     (k1, k2) is (N - k1, N - k2): a tile holds rows k2 and N - k2 (P/2
+//     pencils each, the same x3 columns), or P pencils of one of the
+//     self-mirrored rows 0 and N/2. The multiplier enters as 8 G: the two x2
+//     Hartley combines this route drops each carried a factor 2.
+enum DhtRoute { XF_HARTLEY = 0, XF_FWD = 1, XF_INV = 2, XF_MIRROR = 3 };
+
 // One tile: load (with the fused residual update), transform(s), store (with
 // the fused PCG update). Per-thread sums of ||r||^2 (LD_RESID) or r.z (SCALE)
 // go to acc. Starts with a barrier so consecutive tiles may reuse the buffers.
-template <typename T, int AXIS, int LOADM, int STOREM, bool SCALE>
+template <typename T, int AXIS, int LOADM, int STOREM, bool SCALE, int XF = XF_HARTLEY>
 __device__ __forceinline__ void dht_tile(const SpectralDev &sp, const DhtTile<T> &a, int tile,
                                          typename Cx<T>::type *buf0, typename Cx<T>::type *buf1,
                                          const typename Cx<T>::type *tw, T *vtab, Accum<T> &acc) {
+  static_assert(XF == XF_HARTLEY || (XF == XF_MIRROR) == (AXIS == 1 && SCALE), "route and pass disagree");
+  static_assert(XF != XF_MIRROR || sizeof(T) == 8, "the complex route is the FP64 one (its table holds 8 G)");
+  static_assert((XF != XF_FWD && XF != XF_INV) || AXIS == 2, "the complex x2 transforms");
   using C = typename Cx<T>::type;
   const int N = sp.N;
   const int logP = a.logP;
@@ -337,12 +353,29 @@ __device__ __forceinline__ void dht_tile(const SpectralDev &sp, const DhtTile<T>
   const T *lam = reinterpret_cast<const T *>(sp.lam);
   const T *uf = reinterpret_cast<const T *>(sp.u);
   const int R = sp.rank;
-  const T gscale = (T)2 * (T)sp.scale;  // pass C works with 2 G, as the tables hold it
+  // pass C works with 2 G (Hartley route) or 8 G (complex route), as the tables hold it
+  const T gfac = (XF == XF_MIRROR) ? (T)8 : (T)2;
+  const T gscale = gfac * (T)sp.scale;
 
   __syncthreads();
   // ------------------------------------------------------------------ load
   size_t base = 0, stride = 0;
   int k2 = 0, c0 = 0;
+  int rowA = 0, rowB = 0, colA = 0, colB = 0;  // XF_MIRROR: the tile's two halves
+  bool pair = false;                            // XF_MIRROR: rows k2 and N - k2
+  // x1 / x2 tiles: pencil p (a complex pair of x3 columns) starts at
+  // pencil_base(p), its x3 column (the Hartley index k3 of its real part) is
+  // pencil_col(p)
+  auto pencil_col = [&](int p) -> int {
+    if (XF != XF_MIRROR) return c0 + 2 * p;
+    const int hp = P >> 1;
+    return (p < hp) ? colA + 2 * p : colB + 2 * (p - hp);
+  };
+  auto pencil_base = [&](int p) -> size_t {
+    if (XF != XF_MIRROR) return base + 2 * p;
+    const int hp = P >> 1;
+    return (p < hp) ? (size_t)rowA * N + colA + 2 * p : (size_t)rowB * N + colB + 2 * (p - hp);
+  };
   if (AXIS == 3) {
     const size_t row0 = (size_t)tile * 2 * P;
     const int halfN = N >> 1;
@@ -363,85 +396,130 @@ __device__ __forceinline__ void dht_tile(const SpectralDev &sp, const DhtTile<T>
       bs[((jj + 1) * SP + (q >> 1)) * 2 + (q & 1)] = v.y;
     }
   } else {
-    const int line = tile / nb2;
-    const int cb = tile - line * nb2;
-    c0 = cb * 2 * P;
-    if (AXIS == 2) {
-      base = (size_t)line * NN + c0;
-      stride = N;
-    } else {
-      base = (size_t)line * N + c0;
+    if (XF == XF_MIRROR) {
+      const int tpg = N / P;  // tiles per group: a row pair, or the two self-mirrored rows
+      const int gi = tile / tpg, cb = tile - gi * tpg;
+      if (gi == 0) {  // rows 0 and N/2, P pencils of one row per tile
+        const int hr = tpg >> 1;
+        rowA = (cb < hr) ? 0 : (N >> 1);
+        colA = ((cb < hr) ? cb : cb - hr) * 2 * P;
+        rowB = rowA;
+        colB = colA + P;
+      } else {  // rows k2 and N - k2, P/2 pencils each
+        pair = true;
+        rowA = gi;
+        rowB = N - gi;
+        colA = colB = cb * P;
+      }
+      k2 = rowA;
+      c0 = colA;
       stride = NN;
-      k2 = line;
+    } else {
+      const int line = tile / nb2;
+      const int cb = tile - line * nb2;
+      c0 = cb * 2 * P;
+      if (AXIS == 2) {
+        base = (size_t)line * NN + c0;
+        stride = N;
+      } else {
+        base = (size_t)line * N + c0;
+        stride = NN;
+        k2 = line;
+      }
     }
     for (int e = tid; e < P * N; e += kThreads) {
       const int p = e & (P - 1);
       const int j = e >> logP;
-      const size_t g = base + (size_t)j * stride + 2 * p;
+      const size_t g = pencil_base(p) + (size_t)j * stride;
       buf0[j * SP + p] = reinterpret_cast<const C *>(a.in)[g >> 1];
     }
     if (SCALE && R > 0 && !sp.gtab) {
-      // x2 factors at uf + R N, x3 factors at uf + 2 R N (see SpectralDev)
+      // x2 factors at uf + R N, x3 factors at uf + 2 R N (see SpectralDev);
+      // entry 2p + b: pencil p's x3 column b (G, times gfac)
       const T *u2 = uf + (size_t)R * N, *u3 = uf + 2 * (size_t)R * N;
       for (int e = tid; e < R * 2 * P; e += kThreads) {
         const int rr = e / (2 * P), w = e - rr * 2 * P;
-        vtab[e] = (T)2 * (u2[rr * N + k2] * u3[rr * N + c0 + w]);  // 2 G, as above
+        vtab[e] = gfac * (u2[rr * N + k2] * u3[rr * N + pencil_col(w >> 1) + (w & 1)]);
       }
     }
   }
   __syncthreads();
   // --------------------------------------------------------- transform(s)
   C *res = fft_all<T, C>(buf0, buf1, tw, sp, SP, logP);
-  {
+  // the multiplier at modes (k, k2, k3a) and (k, k2, k3a + 1), k3a = pencil_col(p),
+  // times gfac (G(k) = G(N - k) in every index)
+  auto multiplier = [&](int k, int p, T &ga, T &gb) {
+    const int k3a = pencil_col(p), k3b = k3a + 1;
+    if (sp.gtab) {  // tabulated (FP64 (m1, m2, m3), FP32 (m1, m2, k3))
+      const int H = (N >> 1) + 1;
+      const T *tab = reinterpret_cast<const T *>(sp.gtab);
+      if (sizeof(T) == 8) {
+        const T *row = tab + ((size_t)mirror_index(k, N) * H + mirror_index(k2, N)) * H;
+        ga = row[mirror_index(k3a, N)];
+        gb = row[mirror_index(k3b, N)];
+      } else {
+        const T *row = tab + ((size_t)mirror_index(k, N) * H + mirror_index(k2, N)) * N;
+        ga = (k == 0 && k2 == 0 && k3a == 0) ? (T)0 : row[k3a];
+        gb = row[k3b];
+      }
+    } else if (R == 0) {
+      const T l12 = lam[k] + lam[k2];
+      const T g1 = l12 + lam[k3a], g2 = l12 + lam[k3b];
+      ga = (g1 > (T)0) ? gscale / g1 : (T)0;
+      gb = (g2 > (T)0) ? gscale / g2 : (T)0;
+    } else {
+      T sa = (T)0, sb = (T)0;
+      for (int rr = 0; rr < R; ++rr) {
+        const T uk = uf[rr * N + k];
+        sa = fma(uk, vtab[rr * 2 * P + 2 * p], sa);
+        sb = fma(uk, vtab[rr * 2 * P + 2 * p + 1], sb);
+      }
+      ga = (k == 0 && k2 == 0 && k3a == 0) ? (T)0 : sa;
+      gb = sb;  // k3b >= 1
+    }
+  };
+  // Pass C's scaling (described at s2_combine) of the mode pair X = Z(k),
+  // Y = Z(mirror of k), in place as conj(W) for the second transform. ga, gb
+  // are gfac G. The pair's share of r.z is G_a |X + conj Y|^2 + G_b |X - conj Y|^2
+  // (in units of the route's factor), doubled where the two modes differ; with
+  // S = |X|^2 + |Y|^2 and Re(X Y) it is ((ga + gb) S + 2 (ga - gb) Re(X Y)) / 2,
+  // which needs two products of the data instead of four.
+  auto scale_pair = [&](C *px, C *py, bool self, T ga, T gb) {
+    const C X = *px, Y = *py;
+    const T s4 = ga + gb, d4 = ga - gb;
+    const T S = fma(X.x, X.x, fma(X.y, X.y, fma(Y.x, Y.x, Y.y * Y.y)));
+    const T ReXY = fma(X.x, Y.x, -(X.y * Y.y));
+    T e2 = fma(s4, S, (d4 + d4) * ReXY);
+    if (self) e2 *= (T)0.5;
+    acc.add(e2);
+    *px = C{fma(s4, X.x, d4 * Y.x), fma(d4, Y.y, -s4 * X.y)};
+    if (!self) *py = C{fma(s4, Y.x, d4 * X.x), fma(d4, X.y, -s4 * Y.y)};
+  };
+  if (XF == XF_MIRROR && pair) {
+    // rows k2 (pencils p < P/2) and N - k2 (pencil p + P/2): Z(k, k2) pairs
+    // with Z(N - k, N - k2), every k, and the two modes always differ
+    const int hp = P >> 1;
+    for (int t = tid; t < (N << (logP - 1)); t += kThreads) {
+      const int p = t & (hp - 1);
+      const int k = t >> (logP - 1);
+      const int km = (k == 0) ? 0 : N - k;
+      T ga, gb;
+      multiplier(k, p, ga, gb);
+      scale_pair(&res[k * SP + p], &res[km * SP + p + hp], false, ga, gb);
+    }
+    __syncthreads();
+  } else if (SCALE || XF == XF_HARTLEY) {
     const int halfN = N >> 1;
     for (int t = tid; t < ((halfN + 1) << logP); t += kThreads) {
       const int p = t & (P - 1);
       const int k = t >> logP;
       const int km = (k == 0) ? 0 : N - k;
-      const C X = res[k * SP + p], Y = res[km * SP + p];
-      if (SCALE) {  // pass C: the Fourier-domain scaling described at s2_combine
-        const int k3a = c0 + 2 * p, k3b = k3a + 1;
+      if (SCALE) {
         T ga, gb;
-        if (sp.gtab) {  // tabulated multiplier (k <= N/2 here; FP64 (m1, m2, m3), FP32 (m1, m2, k3))
-          const int H = (N >> 1) + 1;
-          const T *tab = reinterpret_cast<const T *>(sp.gtab);
-          if (sizeof(T) == 8) {
-            const T *row = tab + ((size_t)k * H + mirror_index(k2, N)) * H;
-            ga = row[mirror_index(k3a, N)];
-            gb = row[mirror_index(k3b, N)];
-          } else {
-            const T *row = tab + ((size_t)k * H + mirror_index(k2, N)) * N;
-            ga = (k == 0 && k2 == 0 && k3a == 0) ? (T)0 : row[k3a];
-            gb = row[k3b];
-          }
-        } else if (R == 0) {
-          const T l12 = lam[k] + lam[k2];
-          const T g1 = l12 + lam[k3a], g2 = l12 + lam[k3b];
-          ga = (g1 > (T)0) ? gscale / g1 : (T)0;
-          gb = (g2 > (T)0) ? gscale / g2 : (T)0;
-        } else {
-          T sa = (T)0, sb = (T)0;
-          for (int rr = 0; rr < R; ++rr) {
-            const T uk = uf[rr * N + k];
-            sa = fma(uk, vtab[rr * 2 * P + 2 * p], sa);
-            sb = fma(uk, vtab[rr * 2 * P + 2 * p + 1], sb);
-          }
-          ga = (k == 0 && k2 == 0 && k3a == 0) ? (T)0 : sa;
-          gb = sb;  // k3b >= 1
-        }
-        // ga, gb are 2 G. The pair's share of r.z is G_a |X + conj Y|^2 + G_b |X - conj Y|^2,
-        // doubled for k != N - k (both modes); with S = |X|^2 + |Y|^2 and Re(X Y) it is
-        // ((ga + gb) S + 2 (ga - gb) Re(X Y)) / 2, which needs two products of the data
-        // instead of four (the sums X + conj Y, X - conj Y are not formed).
-        const T s4 = ga + gb, d4 = ga - gb;
-        const T S = fma(X.x, X.x, fma(X.y, X.y, fma(Y.x, Y.x, Y.y * Y.y)));
-        const T ReXY = fma(X.x, Y.x, -(X.y * Y.y));
-        T e2 = fma(s4, S, (d4 + d4) * ReXY);
-        if (km == k) e2 *= (T)0.5;
-        acc.add(e2);
-        res[k * SP + p] = C{fma(s4, X.x, d4 * Y.x), fma(d4, Y.y, -s4 * X.y)};
-        if (km != k) res[km * SP + p] = C{fma(s4, Y.x, d4 * X.x), fma(d4, X.y, -s4 * Y.y)};
+        multiplier(k, p, ga, gb);
+        scale_pair(&res[k * SP + p], &res[km * SP + p], km == k, ga, gb);
       } else {
+        const C X = res[k * SP + p], Y = res[km * SP + p];
         C hk, hm;
         hartley_both(X, Y, hk, hm);
         res[k * SP + p] = hk;
@@ -487,8 +565,9 @@ __device__ __forceinline__ void dht_tile(const SpectralDev &sp, const DhtTile<T>
     for (int e = tid; e < P * N; e += kThreads) {
       const int p = e & (P - 1);
       const int j = e >> logP;
-      const size_t g = base + (size_t)j * stride + 2 * p;
-      const C v = res[j * SP + p];
+      const size_t g = pencil_base(p) + (size_t)j * stride;
+      const int js = (XF == XF_INV && j != 0) ? N - j : j;
+      const C v = res[js * SP + p];
       reinterpret_cast<C *>(a.out)[g >> 1] = SCALE ? C{v.x, -v.y} : v;
     }
   }

@@ -433,7 +433,7 @@ int precond_first(const sq_precond *pc, T *r, T *Y, T *p, RedBuf rb, cudaStream_
   SQ_LAUNCH(PC_DHT_A, s, launch_dht_pass<T>(PASS_A_PLAIN, sp, r, Y, nullptr, nullptr, nullptr, nullptr, rb, true, true, s));
   SQ_LAUNCH(PC_DHT_B, s, launch_dht_pass<T>(PASS_B, sp, Y, Y, nullptr, nullptr, nullptr, nullptr, rb, true, true, s));
   SQ_LAUNCH(PC_DHT_C, s, launch_dht_pass<T>(PASS_C, sp, Y, Y, nullptr, nullptr, nullptr, nullptr, rb, true, true, s));
-  SQ_LAUNCH(PC_DHT_B, s, launch_dht_pass<T>(PASS_B, sp, Y, Y, nullptr, nullptr, nullptr, nullptr, rb, true, true, s));
+  SQ_LAUNCH(PC_DHT_B, s, launch_dht_pass<T>(PASS_D, sp, Y, Y, nullptr, nullptr, nullptr, nullptr, rb, true, true, s));
   SQ_LAUNCH(PC_DHT_E, s, launch_dht_pass<T>(PASS_E_PCG, sp, Y, nullptr, nullptr, nullptr, p, nullptr, rb, true, true, s));
   return SQ_OK;
 }
@@ -447,7 +447,7 @@ int pcg_iteration(const sq_coeffs *c, const sq_precond *pc, T *x, T *r, T *p, T 
   SQ_LAUNCH(PC_DHT_A, s, launch_dht_pass<T>(PASS_A_RESID, sp, r, Y, r, q, nullptr, nullptr, rb, false, true, s));
   SQ_LAUNCH(PC_DHT_B, s, launch_dht_pass<T>(PASS_B, sp, Y, Y, nullptr, nullptr, nullptr, nullptr, rb, false, true, s));
   SQ_LAUNCH(PC_DHT_C, s, launch_dht_pass<T>(PASS_C, sp, Y, Y, nullptr, nullptr, nullptr, nullptr, rb, false, true, s));
-  SQ_LAUNCH(PC_DHT_B, s, launch_dht_pass<T>(PASS_B, sp, Y, Y, nullptr, nullptr, nullptr, nullptr, rb, false, true, s));
+  SQ_LAUNCH(PC_DHT_B, s, launch_dht_pass<T>(PASS_D, sp, Y, Y, nullptr, nullptr, nullptr, nullptr, rb, false, true, s));
   SQ_LAUNCH(PC_DHT_E, s, launch_dht_pass<T>(PASS_E_PCG, sp, Y, nullptr, nullptr, nullptr, p, x, rb, false, true, s));
   return SQ_OK;
 }
@@ -724,7 +724,7 @@ int apply_precond_t(const sq_precond *pc, sq_workspace *w, const T *r, T *z, T *
   SQ_LAUNCH(PC_DHT_A, s, launch_dht_pass<T>(PASS_A_PLAIN, sp, r, Y, nullptr, nullptr, nullptr, nullptr, rb, true, false, s));
   SQ_LAUNCH(PC_DHT_B, s, launch_dht_pass<T>(PASS_B, sp, Y, Y, nullptr, nullptr, nullptr, nullptr, rb, true, false, s));
   SQ_LAUNCH(PC_DHT_C, s, launch_dht_pass<T>(PASS_C, sp, Y, Y, nullptr, nullptr, nullptr, nullptr, rb, true, false, s));
-  SQ_LAUNCH(PC_DHT_B, s, launch_dht_pass<T>(PASS_B, sp, Y, Y, nullptr, nullptr, nullptr, nullptr, rb, true, false, s));
+  SQ_LAUNCH(PC_DHT_B, s, launch_dht_pass<T>(PASS_D, sp, Y, Y, nullptr, nullptr, nullptr, nullptr, rb, true, false, s));
   SQ_LAUNCH(PC_DHT_E, s, launch_dht_pass<T>(PASS_E_PLAIN, sp, Y, z, nullptr, nullptr, nullptr, nullptr, rb, true, false, s));
   return SQ_OK;
 }
@@ -1051,9 +1051,10 @@ namespace sq {
 // The multiplier tables of pass C (SpectralDev::gtab): G at every
 // mirror-reduced mode (m1, m2, m3), m <= N/2, summed in FP64 from the scaled
 // factors (or scale / (l1 + l2 + l3) for the exact diagonal); G(0,0,0) = 0.
-// Both hold 2 G, the factor pass C would otherwise apply per mode (doubling is
-// exact): FP64 indexed by (m1, m2, m3); FP32 by (m1, m2, k3) with k3 over the
-// whole axis (each FP32 tile prefetches its 2P columns into shared memory).
+// They hold G times the factor pass C would otherwise apply per mode (exact
+// powers of 2): FP64 8 G (the complex x2 route), indexed by (m1, m2, m3); FP32
+// 2 G (the Hartley route) by (m1, m2, k3) with k3 over the whole axis (each
+// FP32 tile prefetches its 2P columns into shared memory).
 __global__ void k_build_gtab(int N, int R, const double *lam, const double *u, double scale, double *g64,
                              float *g32) {
   const int H = N / 2 + 1;
@@ -1069,7 +1070,7 @@ __global__ void k_build_gtab(int N, int R, const double *lam, const double *u, d
           g = fma(u[(size_t)r * N + m1], u[(size_t)(R + r) * N + m2] * u[(size_t)(2 * R + r) * N + m3], g);
       }
     }
-    g64[i] = 2.0 * g;
+    g64[i] = 8.0 * g;
     const size_t row = ((size_t)m1 * H + m2) * N;
     g32[row + m3] = (float)(2.0 * g);
     if (m3 != 0 && m3 != N - m3) g32[row + N - m3] = (float)(2.0 * g);
