@@ -400,11 +400,12 @@ cudaError_t launch_dht_pass(int pass, const SpectralDev &sp, const T *in, T *out
   // staging of p and x adds 16 P N bytes of shared memory per block)
   const int Pe = (sizeof(T) == 4 && pass == PASS_E_PCG) ? g_pencils_e_override[N] : 0;
   int P = Pe ? Pe : dht_tile_pencils(N, (int)sizeof(T));
-  // FP64 passes other than C take tiles of at most 4 complex pencils: half
-  // the shared memory, twice the blocks per SM to keep the FP64 pipe fed
-  // (at N = 256 the FP64 iteration went 3166 -> 3113 us; pass C is faster
-  // with 8, and 2 is slower than 4)
-  if (sizeof(T) == 8 && pass != PASS_C && P > 4) P = 4;
+  // FP64 passes take tiles of at most 4 complex pencils: half the shared
+  // memory, twice the blocks per SM to keep the FP64 pipe fed (at N = 256
+  // the passes other than C went 3166 -> 3113 us per iteration; 2 pencils
+  // are slower than 4). Pass C on the complex x2 route, 2 pencils per row:
+  // 837.9 -> 827.6 us.
+  if (sizeof(T) == 8 && P > 4) P = 4;
   int logP = 0;
   while ((1 << logP) < P) ++logP;
   DhtArgs<T> a;

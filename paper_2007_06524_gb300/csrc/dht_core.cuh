@@ -479,21 +479,25 @@ __device__ __forceinline__ void dht_tile(const SpectralDev &sp, const DhtTile<T>
     }
   };
   // Pass C's scaling (described at s2_combine) of the mode pair X = Z(k),
-  // Y = Z(mirror of k), in place as conj(W) for the second transform. ga, gb
-  // are gfac G. The pair's share of r.z is G_a |X + conj Y|^2 + G_b |X - conj Y|^2
-  // (in units of the route's factor), doubled where the two modes differ; with
-  // S = |X|^2 + |Y|^2 and Re(X Y) it is ((ga + gb) S + 2 (ga - gb) Re(X Y)) / 2,
-  // which needs two products of the data instead of four.
+  // Y = Z(mirror of k), in place as conj(W) for the second transform; ga, gb
+  // are gfac G. The pair's share of r.z, G_a |X + conj Y|^2 + G_b |X - conj Y|^2
+  // in units of the route's factor, equals Re(conj X W_X) + Re(conj Y W_Y)
+  // (W_X = s4 X + d4 conj Y, W_Y = s4 Y + d4 conj X: both sides are
+  // s4 (|X|^2 + |Y|^2) + 2 d4 Re(X Y)), so it is summed from the scaled values,
+  // two FMAs per mode. A self-mirrored mode (Y = X) counts once.
   auto scale_pair = [&](C *px, C *py, bool self, T ga, T gb) {
     const C X = *px, Y = *py;
     const T s4 = ga + gb, d4 = ga - gb;
-    const T S = fma(X.x, X.x, fma(X.y, X.y, fma(Y.x, Y.x, Y.y * Y.y)));
-    const T ReXY = fma(X.x, Y.x, -(X.y * Y.y));
-    T e2 = fma(s4, S, (d4 + d4) * ReXY);
-    if (self) e2 *= (T)0.5;
-    acc.add(e2);
-    *px = C{fma(s4, X.x, d4 * Y.x), fma(d4, Y.y, -s4 * X.y)};
-    if (!self) *py = C{fma(s4, Y.x, d4 * X.x), fma(d4, X.y, -s4 * Y.y)};
+    const C cwx = C{fma(s4, X.x, d4 * Y.x), fma(d4, Y.y, -s4 * X.y)};  // conj(W_X)
+    *px = cwx;
+    acc.add_prod(X.x, cwx.x);
+    acc.add_prod(-X.y, cwx.y);
+    if (!self) {
+      const C cwy = C{fma(s4, Y.x, d4 * X.x), fma(d4, X.y, -s4 * Y.y)};
+      *py = cwy;
+      acc.add_prod(Y.x, cwy.x);
+      acc.add_prod(-Y.y, cwy.y);
+    }
   };
   if (XF == XF_MIRROR && pair) {
     // rows k2 (pencils p < P/2) and N - k2 (pencil p + P/2): Z(k, k2) pairs
