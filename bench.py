@@ -182,8 +182,9 @@ def _algorithmic(N, elem, rank_r, table=None):
 
     bytes: the fields each kernel must read and write once (N^3 elements of
     `elem` bytes); flops: one real 1D Hartley pass = 2.5 log2 N + 3 per point
-    (half-length complex FFT convention + the Hartley combine). Pass C does two
-    transforms with no combine (the scaling is applied to the complex
+    (half-length complex FFT convention + the Hartley combine). The FP64
+    passes B and D take the complex x2 route (no combine): 2.5 log2 N. Pass C
+    does two transforms with no combine (the scaling is applied to the complex
     spectrum): 2 x 2.5 log2 N, plus 6 for the scaling and the r.z sum, plus
     the multiplier where it is evaluated per mode (2R, or 4 for the exact
     1/x); on grids N <= 256 pass C reads it from the precomputed table
@@ -196,7 +197,7 @@ def _algorithmic(N, elem, rank_r, table=None):
     return {
         "stencil_matvec": (2 * elem * n3, 15 * n3),
         "dht_x3_in": (4 * elem * n3, (f + 4) * n3),
-        "dht_x2": (2 * elem * n3, f * n3),
+        "dht_x2": (2 * elem * n3, (f - 3.0 if elem == 8 else f) * n3),
         "dht_x1_scale": (2 * elem * n3, (2 * (f - 3.0) + scale) * n3),
         "dht_x3_out": (5 * elem * n3, (f + 4) * n3),
     }
@@ -207,7 +208,7 @@ def _algorithmic(N, elem, rank_r, table=None):
 # profiles/dht_x3_pass_e_fp32_n256.md (8-pencil tiles). Part of each kernel's
 # writes is still in L2 when it ends, so traffic can read below the
 # algorithmic bytes.
-PROFILED_TRAFFIC = {("dht_x1_scale", 8): 159.80e6 + 75.00e6, ("dht_x3_out", 4): 201.35e6 + 76.52e6}
+PROFILED_TRAFFIC = {("dht_x1_scale", 8): 151.53e6 + 79.04e6, ("dht_x3_out", 4): 201.35e6 + 76.52e6}
 
 
 def kernel_table(work, prof, N, elem, R, t_ms, peaks=None):

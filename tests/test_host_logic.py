@@ -65,6 +65,10 @@ def test_bench_algorithmic_model():
     assert bench._algorithmic(N, 8, R, table=False)["dht_x1_scale"][1] == (2 * 2.5 * 8 + 2 * R + 6) * n3
     assert bench._algorithmic(N, 8, 0, table=False)["dht_x1_scale"][1] == (2 * 2.5 * 8 + 10) * n3
     assert bench._algorithmic(512, 4, 0)["dht_x1_scale"][1] == (2 * 2.5 * 9 + 10) * 512 ** 3
+    # the x2 passes: a Hartley transform (FFT + combine) in FP32, the FFT alone
+    # on the FP64 complex route
+    assert alg["dht_x2"][1] == (2.5 * 8 + 3) * n3
+    assert bench._algorithmic(N, 8, R)["dht_x2"][1] == 2.5 * 8 * n3
 
 
 def test_new_bindings_reject_bad_arguments_before_calling_the_library():
