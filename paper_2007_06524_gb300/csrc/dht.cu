@@ -27,6 +27,17 @@
 //   E: x3 transform -> z (PCG: x += alpha p; p = z + beta p)
 // A tile is P complex pencils = 2P real pencils: 2P adjacent rows for x3,
 // 2P adjacent x3-columns for x1 and x2 (coalesced 2P-wide row segments).
+//
+// FP64 takes a complex route through B, C and D. G is even in k2 too, so
+// the x2 Hartley pair around pass C equals F2* (.) F2: B stores the FFT of
+// each packed pair a + i b (two x3 Hartley columns) with no combine, D the
+// inverse (the forward FFT read from index N - j). Pass C then sees
+// Z(k1, k2) = A + i B with A, B the 2D FFTs of the real a, b, whose mirror
+// mode is (N - k1, N - k2): its tiles hold rows k2 and N - k2 together (rows
+// 0 and N/2 pair within themselves), and the scaling above applies unchanged
+// with the multiplier as 8 G (the two dropped combines each carried a factor
+// 2). The fields keep the same real layout in HBM; passes A and E keep their
+// combines, since the rows they pack are mixed by the later transforms.
 #include "dht_core.cuh"
 
 namespace sq {
