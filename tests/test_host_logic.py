@@ -202,3 +202,58 @@ def test_bench_roofline_selection():
     # no capture at other sizes
     _, roof = bench.kernel_table(work, prof, 128, 4, R, t_ms=30.0)
     assert roof["traffic"] is None
+
+
+def _complex_x2_route(r, G, scale):
+    """The FP64 preconditioner's five passes as numpy array operations: x3
+    Hartley transforms (2 H per pass) around an x2 FFT of packed column pairs
+    with no Hartley combine, the x1 scaling W = s Z(k) + d conj Z(-k) over
+    mirror modes (-k1, -k2) with the multiplier as 8 G, and the inverse x2
+    transform read from index N - j. Returns z and the pass-C r.z sum."""
+    import numpy as np
+
+    N = r.shape[0]
+
+    def hartley2(x):  # 2 H along x3 (real in, real out)
+        F = np.fft.fft(x, axis=2)
+        return 2 * (F.real - F.imag)
+
+    Y = hartley2(r)
+    Z = np.fft.fft(Y[:, :, 0::2] + 1j * Y[:, :, 1::2], axis=1)
+    Z = np.fft.fft(Z, axis=0)
+    m = (-np.arange(N)) % N
+    Zm = Z[m][:, m]  # Z(-k1, -k2)
+    ga, gb = 8 * scale * G[:, :, 0::2], 8 * scale * G[:, :, 1::2]
+    s4, d4 = ga + gb, ga - gb
+    W = s4 * Z + d4 * np.conj(Zm)
+    rz = float(np.sum((np.conj(Z) * W).real))  # Re(conj Z W) summed over every mode
+    V = np.conj(np.fft.fft(np.conj(W), axis=0))
+    D = np.fft.fft(V, axis=1)[:, m, :]
+    Y2 = np.empty_like(Y)
+    Y2[:, :, 0::2], Y2[:, :, 1::2] = D.real, D.imag
+    return hartley2(Y2), rz
+
+
+@pytest.mark.parametrize("N", [8, 12, 16])
+def test_complex_x2_route_is_the_fourier_multiplier(N):
+    """The FP64 route through passes B, C, D applies z = F^-1 G F r for a
+    multiplier even in every index, and its r.z sum is r . z (Parseval):
+    checked against numpy's 3D FFT for the exact diagonal and a rank-2
+    canonical G (Sec. 4.2, Eq. 31 and Eq. 34)."""
+    import numpy as np
+
+    rng = np.random.default_rng(N)
+    r = rng.standard_normal((N, N, N))
+    k = np.arange(N)
+    lam = 4 * np.sin(np.pi * k / N) ** 2
+    with np.errstate(divide="ignore"):
+        exact = 1.0 / (lam[:, None, None] + lam[None, :, None] + lam[None, None, :])
+    exact[0, 0, 0] = 0.0
+    u = [np.exp(-t * lam) for t in (0.3, 1.7)]
+    rank2 = sum(w * ui[:, None, None] * ui[None, :, None] * ui[None, None, :] for w, ui in zip((0.8, 0.5), u))
+    rank2[0, 0, 0] = 0.0
+    for G in (exact, rank2):
+        z, rz = _complex_x2_route(r, G, 1.0 / (64 * N ** 3))
+        zref = np.fft.ifftn(G * np.fft.fftn(r)).real
+        assert np.abs(z - zref).max() <= 1e-13 * np.abs(zref).max()
+        assert abs(rz - float(np.sum(r * zref))) <= 1e-12 * abs(float(np.sum(r * zref)))
