@@ -37,9 +37,9 @@ UNIT = "corrector solves/s"
 
 
 def _peaks():
-    """HBM peak: the driver's measured copy bandwidth (MEASURED_PEAKS.json)
-    where present, else the fallback figure of one earlier GB300
-    measurement."""
+    """HBM peak: the measured STREAM-style copy bandwidth of this GPU type
+    (MEASURED_PEAKS.json) where present, else the fallback figure of one
+    earlier GB300 measurement."""
     p = os.path.join(ROOT, "MEASURED_PEAKS.json")
     if os.path.exists(p):
         d = json.load(open(p))
@@ -64,8 +64,8 @@ def measure_peaks(sq, torch):
     """The roofline denominators measured on this GPU by the library's probes:
     FP64 and FP32 fused multiply-add throughput (eight independent chains per
     thread, a full grid) and a copy of 2 x 2 GiB (HBM) and of 2 x 16 MiB (L2)
-    buffers. The HBM peak stays the driver's measurement where present; the
-    probe's copy figure is reported beside it (the fallback is used where
+    buffers. The HBM peak stays the MEASURED_PEAKS.json figure where present;
+    the probe's copy figure is reported beside it (the fallback is used where
     that file is absent)."""
     pk = default_peaks()
     fp64, _ = sq.sq_probe_fma(0)
