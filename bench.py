@@ -904,8 +904,6 @@ def iteration_by_slope(sq, torch, c, pc, w, N, stream, hbm_gbs, Ks=(4, 8, 12, 16
     median times is one iteration. The per-kernel event pairs of the
     profiled run time each launch with its own start and drain, so their sum
     reads a few us per kernel above this."""
-    import numpy as np
-
     psi = torch.empty(N ** 3, dtype=torch.float64, device="cuda")
     ts = []
     for K in Ks:
@@ -922,8 +920,17 @@ def iteration_by_slope(sq, torch, c, pc, w, N, stream, hbm_gbs, Ks=(4, 8, 12, 16
                 return None  # the inner solve converged before the cap: no clean slope
             rt.append(e0.elapsed_time(e1))
         ts.append(statistics.median(rt))
-    slope, icpt = np.polyfit(list(Ks), ts, 1)
-    resid = max(abs(t - (slope * k + icpt)) for k, t in zip(Ks, ts))
+    return slope_fit(Ks, ts, N, hbm_gbs)
+
+
+def slope_fit(Ks, ts_ms, N, hbm_gbs):
+    """One FP32 iteration from solve times t(K) (ms) capped at K iterations:
+    the least-squares slope, its worst fit residual, and the 17 field passes
+    of 4-byte words it moves against the HBM peak."""
+    import numpy as np
+
+    slope, icpt = np.polyfit(list(Ks), list(ts_ms), 1)
+    resid = max(abs(t - (slope * k + icpt)) for k, t in zip(Ks, ts_ms))
     b = 17 * 4 * N ** 3
     gbps = b / (slope * 1e-3) / 1e9
     return {"us": round(slope * 1e3, 1), "fit_residual_us": round(resid * 1e3, 1), "bytes": b,

@@ -257,3 +257,22 @@ def test_complex_x2_route_is_the_fourier_multiplier(N):
         zref = np.fft.ifftn(G * np.fft.fftn(r)).real
         assert np.abs(z - zref).max() <= 1e-13 * np.abs(zref).max()
         assert abs(rz - float(np.sum(r * zref))) <= 1e-12 * abs(float(np.sum(r * zref)))
+
+
+def test_bench_slope_fit():
+    """The FP32 iteration from capped-solve times: a solve of K iterations
+    taking c + K t gives t back whatever the fixed cost c, with the 17 FP32
+    field passes of one iteration as its bytes."""
+    import bench
+
+    N, t_us, c_ms = 256, 226.0, 1.9
+    Ks = (4, 8, 12, 16, 20)
+    r = bench.slope_fit(Ks, [c_ms + k * t_us / 1e3 for k in Ks], N, 6690.5)
+    assert r["us"] == t_us and r["fit_residual_us"] == 0.0
+    assert r["bytes"] == 17 * 4 * N ** 3
+    assert abs(r["GBps"] - r["bytes"] / (t_us * 1e-6) / 1e9) < 0.1
+    assert abs(r["frac"] - r["GBps"] / 6690.5) < 1e-4
+    # a noisy point shows up as the fit residual
+    ts = [c_ms + k * t_us / 1e3 for k in Ks]
+    ts[2] += 0.005
+    assert bench.slope_fit(Ks, ts, N, 6690.5)["fit_residual_us"] > 2.0
